@@ -1,0 +1,211 @@
+"""FP64 CPU oracle of the DeepQMC-style VMC hot path (test infrastructure).
+
+Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The CUDA library never does, and the
+two share no code: the oracle is ``oracle.cpp`` (plain C++ on doubles,
+hyper-dual and dual numbers) plus the few numpy routines below.
+
+Functions, each following the paper's definitions:
+
+* :func:`evaluate` - log|psi| and sign psi (Sec. 3, Eqs. 13-28).
+* :func:`local_energy` - E_loc of Eq. (31), second derivatives one coordinate
+  at a time with hyper-dual numbers (the "serial" Laplacian of App. A.2).
+* :func:`grad_jvp`, :func:`grad_index` - derivatives of log|psi| along
+  parameter directions (dual numbers), the ingredient of Eq. (30).
+* :func:`metropolis_step` - one random-walk Metropolis step (Sec. 5) on
+  draws passed in.
+* :func:`clipped_loss_weights` - median/MAD clipping of Sec. 4.4 and the
+  per-walker weights of the gradient estimator, Eq. (30).
+* :func:`energy_estimate` - Eq. (33) and the batch-means error bar, Eq. (35).
+
+Parity status: all functions are pinned by the ``-m "not gpu"`` tests
+(closed forms, invariants, finite differences and brute force).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.cpp")
+
+
+def build(force=False):
+    """Compile ``liboracle.so`` with g++ (OpenMP over walkers)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Spec(ctypes.Structure):
+    _fields_ = [("n_nuc", ctypes.c_int32), ("Z", ctypes.c_void_p), ("R", ctypes.c_void_p),
+                ("n_up", ctypes.c_int32), ("n_dn", ctypes.c_int32),
+                ("D", ctypes.c_int32), ("L", ctypes.c_int32), ("K", ctypes.c_int32), ("Q", ctypes.c_int32),
+                ("rc", ctypes.c_double), ("use_jastrow", ctypes.c_int32), ("use_cusp", ctypes.c_int32),
+                ("alpha", ctypes.c_double)]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        P = ctypes.c_void_p
+        lib.oracle_param_count.argtypes = [P, P]
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.oracle_threads.restype = ctypes.c_int
+        lib.oracle_eval.argtypes = [P, P, P, ctypes.c_int64, P, P]
+        lib.oracle_local_energy.argtypes = [P, P, P, ctypes.c_int64, P, P, P, P, P]
+        lib.oracle_potential.argtypes = [P, P, ctypes.c_int64, P]
+        lib.oracle_grad_jvp.argtypes = [P, P, P, ctypes.c_int64, P, ctypes.c_int32, P]
+        lib.oracle_grad_index.argtypes = [P, P, P, ctypes.c_int64, P, ctypes.c_int32, P]
+        lib.oracle_metropolis_step.argtypes = [P, P, P, P, ctypes.c_int64, P, P, ctypes.c_double, P]
+        lib.oracle_intermediates.argtypes = [P, P, P, P, P]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+class Oracle:
+    """The oracle for one molecule and ansatz configuration."""
+
+    def __init__(self, system, cfg):
+        self.lib = _load()
+        self.system, self.cfg = system, cfg
+        self._Z = np.ascontiguousarray(system.Z, dtype=np.float64)
+        self._R = np.ascontiguousarray(system.R, dtype=np.float64)
+        self.spec = _Spec(len(self._Z), self._Z.ctypes.data, self._R.ctypes.data, system.n_up, system.n_down,
+                          cfg.width, cfg.n_layers, cfg.n_det, cfg.n_rbf, cfg.rbf_cutoff,
+                          int(cfg.use_jastrow), int(cfg.use_cusp), cfg.cusp_alpha)
+        self.N = system.n_up + system.n_down
+        P = ctypes.c_int64()
+        self.lib.oracle_param_count(ctypes.byref(self.spec), ctypes.byref(P))
+        self.P = P.value
+
+    @staticmethod
+    def set_threads(n):
+        _load().oracle_set_threads(int(n))
+
+    @staticmethod
+    def threads():
+        return int(_load().oracle_threads())
+
+    def _prep(self, theta, r):
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        assert theta.size == self.P, (theta.size, self.P)
+        r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, self.N, 3)
+        return theta, r
+
+    def evaluate(self, theta, r):
+        theta, r = self._prep(theta, r)
+        B = r.shape[0]
+        la = np.empty(B)
+        sg = np.empty(B, dtype=np.int8)
+        self.lib.oracle_eval(ctypes.byref(self.spec), _ptr(theta), _ptr(r), B, _ptr(la), _ptr(sg))
+        return la, sg
+
+    def local_energy(self, theta, r, with_grad=False):
+        theta, r = self._prep(theta, r)
+        B = r.shape[0]
+        la, el, lap = np.empty(B), np.empty(B), np.empty(B)
+        sg = np.empty(B, dtype=np.int8)
+        grad = np.empty((B, 3 * self.N)) if with_grad else None
+        self.lib.oracle_local_energy(ctypes.byref(self.spec), _ptr(theta), _ptr(r), B, _ptr(la), _ptr(sg),
+                                     _ptr(el), _ptr(grad), _ptr(lap))
+        out = {"logabs": la, "sign": sg, "e_loc": el, "lap": lap}
+        if with_grad:
+            out["grad"] = grad
+        return out
+
+    def potential(self, r):
+        r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, self.N, 3)
+        V = np.empty(r.shape[0])
+        self.lib.oracle_potential(ctypes.byref(self.spec), _ptr(r), r.shape[0], _ptr(V))
+        return V
+
+    def grad_jvp(self, theta, r, dirs):
+        theta, r = self._prep(theta, r)
+        dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, self.P)
+        out = np.empty((r.shape[0], dirs.shape[0]))
+        self.lib.oracle_grad_jvp(ctypes.byref(self.spec), _ptr(theta), _ptr(r), r.shape[0], _ptr(dirs),
+                                 dirs.shape[0], _ptr(out))
+        return out
+
+    def grad_index(self, theta, r, idx):
+        theta, r = self._prep(theta, r)
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        out = np.empty((r.shape[0], idx.size))
+        self.lib.oracle_grad_index(ctypes.byref(self.spec), _ptr(theta), _ptr(r), r.shape[0], _ptr(idx),
+                                   idx.size, _ptr(out))
+        return out
+
+    def metropolis_step(self, theta, r, logabs, xi, u, step):
+        """Returns (r_new, logabs_new, accepted) without modifying inputs."""
+        theta, r = self._prep(theta, r)
+        r = r.copy()
+        la = np.ascontiguousarray(logabs, dtype=np.float64).copy()
+        xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(r.shape)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        acc = np.empty(r.shape[0], dtype=np.int8)
+        self.lib.oracle_metropolis_step(ctypes.byref(self.spec), _ptr(theta), _ptr(r), _ptr(la), r.shape[0],
+                                        _ptr(xi), _ptr(u), float(step), _ptr(acc))
+        return r, la, acc
+
+    def intermediates(self, theta, r):
+        """Final embeddings f[N][D] and orbital matrices A[2][K][nmax][nmax] of one walker."""
+        theta, r = self._prep(theta, r)
+        nmax = max(self.system.n_up, self.system.n_down)
+        f = np.empty((self.N, self.cfg.width))
+        A = np.zeros((2, self.cfg.n_det, nmax, nmax))
+        self.lib.oracle_intermediates(ctypes.byref(self.spec), _ptr(theta), _ptr(r[0]), _ptr(f), _ptr(A))
+        return f, A
+
+
+# ----------------------------------------------------------------------------
+# Clipping and loss weights (Sec. 4.4, Eq. 30)
+# ----------------------------------------------------------------------------
+def clipped_loss_weights(e_loc, k=5.0):
+    """Clip local energies to median +- k * MAD and form gradient weights.
+
+    Centre = median (mean of the two middle values for even B); half-width
+    = k times the mean absolute deviation from the median (von Glehn et al.,
+    cited in Sec. 4.4).  Weights w_b = (2/B) (E^_b - mean E^), so that
+    sum_b w_b grad log|psi_b| is the estimator of Eq. (30) on clipped energies.
+    Returns (weights, clipped, centre, half_width).
+    """
+    e = np.asarray(e_loc, dtype=np.float64)
+    B = e.size
+    s = np.sort(e)
+    med = s[B // 2] if B % 2 else 0.5 * (s[B // 2 - 1] + s[B // 2])
+    mad = np.mean(np.abs(e - med))
+    lo, hi = med - k * mad, med + k * mad
+    clipped = np.minimum(np.maximum(e, lo), hi)
+    w = (2.0 / B) * (clipped - clipped.mean())
+    return w, clipped, med, k * mad
+
+
+def energy_estimate(e_loc_steps):
+    """Energy estimate (Eq. 33) and batch-means error (Eq. 35).
+
+    ``e_loc_steps``: array [n_b walkers][n_s steps].
+    """
+    e = np.asarray(e_loc_steps, dtype=np.float64)
+    nb = e.shape[0]
+    mean = e.mean()
+    batch = e.mean(axis=1)
+    err = np.sqrt(np.sum((batch - mean) ** 2) / (nb * (nb - 1)))
+    return mean, err

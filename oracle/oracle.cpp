@@ -1,0 +1,569 @@
+// FP64 CPU oracle of the DeepQMC-style VMC hot path.
+//
+// TEST INFRASTRUCTURE ONLY.  This file is the slow, plain reference that the
+// CUDA library is checked against.  Only the test-suite, the smoke check and
+// the CPU-baseline leg of the benchmark load it; the library never does.  It
+// shares no code, header or table with the CUDA path.
+//
+// What it computes (DeepQMC paper, Sec. 2-5):
+//   * log|psi| and sign psi of the ansatz instance below, for one walker at a
+//     time, straight from the definitions:
+//       - graph convolution messages, Eq. (17), normalised by the number of
+//         edges, and the concatenating residual update, Eq. (18) (Sec. 3.1);
+//       - spin-only initial electron embedding, Eq. (13) first case;
+//       - edge features: Gaussian expansion of the distance, reused in every
+//         layer, Eqs. (15)-(16) first case;
+//       - many-body orbitals kappa(f_i^L) (linear), Eq. (19), times isotropic
+//         Slater envelopes (alpha = 1, one exponential per nucleus), Eq. (20);
+//       - spin-factorised determinant pairs, Eq. (21);
+//       - learnable Jastrow factor, Eq. (24), and electron cusp, Eq. (25);
+//       - log-domain evaluation with log-sum-exp over determinants,
+//         Eqs. (27)-(28) (Sec. 3.5);
+//   * the local energy, Eq. (31), with the potential of Eq. (1) plus the
+//     constant nuclear repulsion.  The 3N second derivatives are taken one
+//     coordinate at a time with hyper-dual numbers (Fike & Alonso, 2011),
+//     seeding eps1 = eps2 = e_x: this is the "serial" forward-mode Laplacian
+//     of Appendix A.2, not the GPU's batched propagation;
+//   * directional derivatives of log|psi| in parameter space with dual
+//     numbers (for the gradient estimator, Eq. (30));
+//   * one random-walk Metropolis step (Sec. 5) on random draws passed in.
+//
+// Determinants: LU factorisation with partial pivoting on |value|.
+// Parity status: every function here is pinned by tests (closed forms,
+// invariants, finite differences, brute force); see the test-suite.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Number types
+// ---------------------------------------------------------------------------
+// Hyper-dual number x = v + a e1 + b e2 + ab e1e2, e1^2 = e2^2 = 0.
+struct HD {
+  double v = 0, a = 0, b = 0, ab = 0;
+  HD() = default;
+  HD(double x) : v(x) {}
+  HD(double v_, double a_, double b_, double ab_) : v(v_), a(a_), b(b_), ab(ab_) {}
+};
+inline HD operator+(const HD& x, const HD& y) { return {x.v + y.v, x.a + y.a, x.b + y.b, x.ab + y.ab}; }
+inline HD operator-(const HD& x, const HD& y) { return {x.v - y.v, x.a - y.a, x.b - y.b, x.ab - y.ab}; }
+inline HD operator-(const HD& x) { return {-x.v, -x.a, -x.b, -x.ab}; }
+inline HD operator*(const HD& x, const HD& y) {
+  return {x.v * y.v, x.v * y.a + x.a * y.v, x.v * y.b + x.b * y.v,
+          x.v * y.ab + x.a * y.b + x.b * y.a + x.ab * y.v};
+}
+inline HD& operator+=(HD& x, const HD& y) { x = x + y; return x; }
+inline HD& operator-=(HD& x, const HD& y) { x = x - y; return x; }
+// f(x) for a scalar function with value f, first derivative d1, second d2.
+inline HD chain(const HD& x, double f, double d1, double d2) {
+  return {f, d1 * x.a, d1 * x.b, d1 * x.ab + d2 * x.a * x.b};
+}
+inline HD inv(const HD& x) { double i = 1.0 / x.v; return chain(x, i, -i * i, 2 * i * i * i); }
+inline HD operator/(const HD& x, const HD& y) { return x * inv(y); }
+inline HD exp(const HD& x) { double e = std::exp(x.v); return chain(x, e, e, e); }
+inline HD log(const HD& x) { return chain(x, std::log(x.v), 1.0 / x.v, -1.0 / (x.v * x.v)); }
+inline HD sqrt(const HD& x) { double s = std::sqrt(x.v); return chain(x, s, 0.5 / s, -0.25 / (s * x.v)); }
+inline HD tanh(const HD& x) { double t = std::tanh(x.v); double d = 1 - t * t; return chain(x, t, d, -2 * t * d); }
+inline double val(const HD& x) { return x.v; }
+
+// Dual number x = v + d e, e^2 = 0.
+struct Dual {
+  double v = 0, d = 0;
+  Dual() = default;
+  Dual(double x) : v(x) {}
+  Dual(double v_, double d_) : v(v_), d(d_) {}
+};
+inline Dual operator+(const Dual& x, const Dual& y) { return {x.v + y.v, x.d + y.d}; }
+inline Dual operator-(const Dual& x, const Dual& y) { return {x.v - y.v, x.d - y.d}; }
+inline Dual operator-(const Dual& x) { return {-x.v, -x.d}; }
+inline Dual operator*(const Dual& x, const Dual& y) { return {x.v * y.v, x.v * y.d + x.d * y.v}; }
+inline Dual& operator+=(Dual& x, const Dual& y) { x = x + y; return x; }
+inline Dual& operator-=(Dual& x, const Dual& y) { x = x - y; return x; }
+inline Dual chain(const Dual& x, double f, double d1) { return {f, d1 * x.d}; }
+inline Dual inv(const Dual& x) { double i = 1.0 / x.v; return chain(x, i, -i * i); }
+inline Dual operator/(const Dual& x, const Dual& y) { return x * inv(y); }
+inline Dual exp(const Dual& x) { double e = std::exp(x.v); return chain(x, e, e); }
+inline Dual log(const Dual& x) { return chain(x, std::log(x.v), 1.0 / x.v); }
+inline Dual sqrt(const Dual& x) { double s = std::sqrt(x.v); return chain(x, s, 0.5 / s); }
+inline Dual tanh(const Dual& x) { double t = std::tanh(x.v); return chain(x, t, 1 - t * t); }
+inline double val(const Dual& x) { return x.v; }
+
+inline double val(double x) { return x; }
+using std::exp;
+using std::log;
+using std::sqrt;
+using std::tanh;
+
+template <class T> inline T absv(const T& x) { return val(x) < 0 ? -x : x; }
+
+// ---------------------------------------------------------------------------
+// System, hyper-parameters and the flat parameter layout
+// ---------------------------------------------------------------------------
+}  // namespace
+
+extern "C" {
+// Mirrors the Python-side ctypes structure in oracle/__init__.py.
+struct OracleSpec {
+  int32_t n_nuc;
+  const double* Z;  // [n_nuc]
+  const double* R;  // [n_nuc][3], bohr
+  int32_t n_up, n_dn;
+  int32_t D, L, K, Q;  // width, layers, determinant pairs, Gaussian features
+  double rc;           // Gaussian feature cutoff
+  int32_t use_jastrow, use_cusp;
+  double alpha;        // cusp width
+};
+}
+
+namespace {
+
+// Offsets of every block of the flat parameter vector.  Order: E_spin[2][D];
+// per layer: W_h[D][D], (W1[D][Q], b1[D], W2[D][D], b2[D]) for the
+// same-spin, opposite-spin and electron-nucleus edge types, Y[M][D],
+// W_g[D][3D], b_g[D]; per spin (up, down): W_o[K n_s][D], b_o[K n_s],
+// omega[K n_s][M], zeta[K n_s][M]; c[K]; W_J1[D][D], b_J1[D], w_J2[D].
+struct Layout {
+  int64_t E_spin;
+  struct Layer {
+    int64_t W_h, W1[3], b1[3], W2[3], b2[3], Y, W_g, b_g;
+  };
+  std::vector<Layer> layer;
+  int64_t W_o[2], b_o[2], omega[2], zeta[2], c, W_J1, b_J1, w_J2, total;
+
+  explicit Layout(const OracleSpec& s) {
+    const int64_t D = s.D, Q = s.Q, M = s.n_nuc, K = s.K;
+    int64_t o = 0;
+    E_spin = o; o += 2 * D;
+    layer.resize(s.L);
+    for (int l = 0; l < s.L; ++l) {
+      Layer& y = layer[l];
+      y.W_h = o; o += D * D;
+      for (int t = 0; t < 3; ++t) {
+        y.W1[t] = o; o += D * Q;
+        y.b1[t] = o; o += D;
+        y.W2[t] = o; o += D * D;
+        y.b2[t] = o; o += D;
+      }
+      y.Y = o; o += M * D;
+      y.W_g = o; o += D * 3 * D;
+      y.b_g = o; o += D;
+    }
+    const int64_t ns[2] = {s.n_up, s.n_dn};
+    for (int sg = 0; sg < 2; ++sg) {
+      W_o[sg] = o; o += K * ns[sg] * D;
+      b_o[sg] = o; o += K * ns[sg];
+      omega[sg] = o; o += K * ns[sg] * M;
+      zeta[sg] = o; o += K * ns[sg] * M;
+    }
+    c = o; o += K;
+    W_J1 = o; o += D * D;
+    b_J1 = o; o += D;
+    w_J2 = o; o += D;
+    total = o;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Pieces of the ansatz
+// ---------------------------------------------------------------------------
+// y = W x (+ b), W row-major [n_out][n_in].
+template <class T>
+void affine(const T* W, const T* b, const T* x, int n_out, int n_in, T* y) {
+  for (int a = 0; a < n_out; ++a) {
+    T acc = b ? b[a] : T(0.0);
+    const T* w = W + (int64_t)a * n_in;
+    for (int c = 0; c < n_in; ++c) acc += w[c] * x[c];
+    y[a] = acc;
+  }
+}
+
+// Gaussian expansion of a distance: e_q = exp(-(d - mu_q)^2 / (2 s^2)),
+// mu_q = q rc / (Q-1), s = rc / (Q-1) (Sec. 3.1, edge features).
+template <class T>
+void gaussian_features(const T& d, int Q, double rc, T* e) {
+  const double s = rc / (Q - 1);
+  for (int q = 0; q < Q; ++q) {
+    T x = d - T(q * s);
+    e[q] = exp(x * x * T(-0.5 / (s * s)));
+  }
+}
+
+// Edge filter w(e) = W2 tanh(W1 e + b1) + b2.
+template <class T>
+void edge_filter(const T* th, const Layout::Layer& y, int t, const T* e, int D, int Q, T* out) {
+  std::vector<T> h(D);
+  affine(th + y.W1[t], th + y.b1[t], e, D, Q, h.data());
+  for (int a = 0; a < D; ++a) h[a] = tanh(h[a]);
+  affine(th + y.W2[t], th + y.b2[t], h.data(), D, D, out);
+}
+
+// sign and log|det| of an n x n matrix by LU with partial pivoting.
+// A 0 x 0 determinant is 1.  A zero pivot gives sign 0, log|det| = -inf.
+template <class T>
+void slogdet(std::vector<T> A, int n, int* sign, T* logabs) {
+  int sg = 1;
+  T la(0.0);
+  for (int j = 0; j < n; ++j) {
+    int p = j;
+    for (int i = j + 1; i < n; ++i)
+      if (std::fabs(val(A[i * n + j])) > std::fabs(val(A[p * n + j]))) p = i;
+    if (val(A[p * n + j]) == 0.0) {
+      *sign = 0;
+      *logabs = T(-std::numeric_limits<double>::infinity());
+      return;
+    }
+    if (p != j) {
+      for (int k = 0; k < n; ++k) std::swap(A[p * n + k], A[j * n + k]);
+      sg = -sg;
+    }
+    const T piv = A[j * n + j];
+    for (int i = j + 1; i < n; ++i) {
+      const T f = A[i * n + j] / piv;
+      for (int k = j + 1; k < n; ++k) A[i * n + k] -= f * A[j * n + k];
+    }
+    if (val(piv) < 0) sg = -sg;
+    la += log(absv(piv));
+  }
+  *sign = sg;
+  *logabs = la;
+}
+
+template <class T>
+struct Walker {
+  int sign = 0;
+  T logabs;
+};
+
+// log|psi| and sign psi of one walker.  r: [N][3].  Optional debug outputs:
+// f_out [N][D] final embeddings, A_out [2][K][nmax][nmax] orbital matrices.
+template <class T>
+Walker<T> log_psi(const OracleSpec& s, const Layout& lay, const T* th, const T* r,
+                  double* f_out = nullptr, double* A_out = nullptr) {
+  const int N = s.n_up + s.n_dn, M = s.n_nuc, D = s.D, Q = s.Q, K = s.K;
+  auto spin = [&](int i) { return i < s.n_up ? 0 : 1; };
+
+  // Distances (Sec. 3.1, graph representation).
+  std::vector<T> dee(N * N, T(0.0)), den(N * M);
+  for (int i = 0; i < N; ++i)
+    for (int j = i + 1; j < N; ++j) {
+      T acc(0.0);
+      for (int x = 0; x < 3; ++x) {
+        T dx = r[3 * i + x] - r[3 * j + x];
+        acc += dx * dx;
+      }
+      dee[i * N + j] = dee[j * N + i] = sqrt(acc);
+    }
+  for (int i = 0; i < N; ++i)
+    for (int I = 0; I < M; ++I) {
+      T acc(0.0);
+      for (int x = 0; x < 3; ++x) {
+        T dx = r[3 * i + x] - T(s.R[3 * I + x]);
+        acc += dx * dx;
+      }
+      den[i * M + I] = sqrt(acc);
+    }
+
+  // Initial embeddings: f_i^0 = E_spin[sigma_i] (Eq. 13, first case).
+  std::vector<T> f(N * D);
+  for (int i = 0; i < N; ++i)
+    for (int a = 0; a < D; ++a) f[i * D + a] = th[lay.E_spin + spin(i) * D + a];
+
+  std::vector<T> e(Q), w(D), z(N * D), m(3 * D), u(D);
+  const int n_same[2] = {s.n_up, s.n_dn}, n_opp[2] = {s.n_dn, s.n_up};
+  for (int l = 0; l < s.L; ++l) {
+    const Layout::Layer& y = lay.layer[l];
+    for (int j = 0; j < N; ++j) affine(th + y.W_h, (const T*)nullptr, &f[j * D], D, D, &z[j * D]);
+    // Edge filters of the same-spin / opposite-spin e-e edges, per unordered pair.
+    std::vector<T> wee(N * N * D, T(0.0));
+    for (int i = 0; i < N; ++i)
+      for (int j = i + 1; j < N; ++j) {
+        gaussian_features(dee[i * N + j], Q, s.rc, e.data());
+        edge_filter(th, y, spin(i) == spin(j) ? 0 : 1, e.data(), D, Q, w.data());
+        for (int a = 0; a < D; ++a) wee[(i * N + j) * D + a] = wee[(j * N + i) * D + a] = w[a];
+      }
+    std::vector<T> fnew(N * D);
+    for (int i = 0; i < N; ++i) {
+      // Messages, Eq. (17), normalised by the number of edges of the type.
+      for (int a = 0; a < 3 * D; ++a) m[a] = T(0.0);
+      for (int j = 0; j < N; ++j) {
+        if (j == i) continue;
+        const int t = spin(i) == spin(j) ? 0 : 1;
+        for (int a = 0; a < D; ++a) m[t * D + a] += wee[(i * N + j) * D + a] * z[j * D + a];
+      }
+      for (int I = 0; I < M; ++I) {
+        gaussian_features(den[i * M + I], Q, s.rc, e.data());
+        edge_filter(th, y, 2, e.data(), D, Q, w.data());
+        for (int a = 0; a < D; ++a) m[2 * D + a] += w[a] * th[y.Y + I * D + a];
+      }
+      const double nu[3] = {1.0 / std::max(1, n_same[spin(i)] - 1), 1.0 / std::max(1, n_opp[spin(i)]),
+                            1.0 / M};
+      for (int t = 0; t < 3; ++t)
+        for (int a = 0; a < D; ++a) m[t * D + a] = m[t * D + a] * T(nu[t]);
+      // Residual update with concatenated messages, Eq. (18), third case.
+      affine(th + y.W_g, th + y.b_g, m.data(), D, 3 * D, u.data());
+      for (int a = 0; a < D; ++a) fnew[i * D + a] = f[i * D + a] + tanh(u[a]);
+    }
+    f.swap(fnew);
+  }
+  if (f_out)
+    for (int k = 0; k < N * D; ++k) f_out[k] = val(f[k]);
+
+  // Orbitals x envelopes (Eqs. 8, 19, 20) and determinants (Eq. 21).
+  const int ns[2] = {s.n_up, s.n_dn}, i0[2] = {0, s.n_up};
+  const int nmax = std::max(s.n_up, s.n_dn);
+  std::vector<int> sgn_p(K, 1);
+  std::vector<T> ld_p(K, T(0.0));
+  for (int sg = 0; sg < 2; ++sg) {
+    const int n = ns[sg];
+    std::vector<T> phi(K * n);
+    std::vector<std::vector<T>> A(K, std::vector<T>(n * n));
+    for (int ii = 0; ii < n; ++ii) {
+      const int i = i0[sg] + ii;
+      affine(th + lay.W_o[sg], th + lay.b_o[sg], &f[i * D], K * n, D, phi.data());
+      for (int p = 0; p < K; ++p)
+        for (int k = 0; k < n; ++k) {
+          const int o = p * n + k;
+          T env(0.0);
+          for (int I = 0; I < M; ++I)
+            env += th[lay.omega[sg] + o * M + I] * exp(-(th[lay.zeta[sg] + o * M + I] * den[i * M + I]));
+          A[p][ii * n + k] = phi[o] * env;
+        }
+    }
+    for (int p = 0; p < K; ++p) {
+      if (A_out)
+        for (int ii = 0; ii < n; ++ii)
+          for (int k = 0; k < n; ++k)
+            A_out[((sg * K + p) * nmax + ii) * nmax + k] = val(A[p][ii * n + k]);
+      int sd;
+      T ld;
+      slogdet(A[p], n, &sd, &ld);
+      sgn_p[p] *= sd;
+      ld_p[p] += ld;
+    }
+  }
+
+  // Sum over determinant pairs in the log domain (Eq. 28).
+  Walker<T> out;
+  int pmax = -1;
+  for (int p = 0; p < K; ++p) {
+    const double cp = val(th[lay.c + p]);
+    if (sgn_p[p] == 0 || cp == 0.0) continue;
+    ld_p[p] += log(absv(th[lay.c + p]));
+    if (cp < 0) sgn_p[p] = -sgn_p[p];
+    if (pmax < 0 || val(ld_p[p]) > val(ld_p[pmax])) pmax = p;
+  }
+  if (pmax < 0) {
+    out.sign = 0;
+    out.logabs = T(-std::numeric_limits<double>::infinity());
+    return out;
+  }
+  T acc(0.0);
+  for (int p = 0; p < K; ++p) {
+    if (sgn_p[p] == 0 || val(th[lay.c + p]) == 0.0) continue;
+    T term = exp(ld_p[p] - ld_p[pmax]);
+    acc += sgn_p[p] > 0 ? term : -term;
+  }
+  if (val(acc) == 0.0) {
+    out.sign = 0;
+    out.logabs = T(-std::numeric_limits<double>::infinity());
+    return out;
+  }
+  out.sign = val(acc) > 0 ? 1 : -1;
+  T logabs = ld_p[pmax] + log(absv(acc));
+
+  // Learnable Jastrow factor J = eta(sum_i f_i^L), eta = w_J2 . tanh(W_J1 x + b_J1)  (Eq. 24).
+  if (s.use_jastrow) {
+    std::vector<T> sum(D, T(0.0)), h(D);
+    for (int i = 0; i < N; ++i)
+      for (int a = 0; a < D; ++a) sum[a] += f[i * D + a];
+    affine(th + lay.W_J1, th + lay.b_J1, sum.data(), D, D, h.data());
+    T J(0.0);
+    for (int a = 0; a < D; ++a) J += th[lay.w_J2 + a] * tanh(h[a]);
+    logabs += J;
+  }
+  // Electron cusp, Eq. (25): c = 1/4 same spin, 1/2 opposite spin.
+  if (s.use_cusp) {
+    T g(0.0);
+    for (int i = 0; i < N; ++i)
+      for (int j = i + 1; j < N; ++j) {
+        const double c = spin(i) == spin(j) ? 0.25 : 0.5;
+        g -= T(s.alpha * c) / (T(1.0) + T(s.alpha) * dee[i * N + j]);
+      }
+    logabs += g;
+  }
+  out.logabs = logabs;
+  return out;
+}
+
+// Coulomb potential of Eq. (1) plus the constant nuclear repulsion.
+double potential(const OracleSpec& s, const double* r) {
+  const int N = s.n_up + s.n_dn, M = s.n_nuc;
+  auto dist = [](const double* a, const double* b) {
+    double acc = 0;
+    for (int x = 0; x < 3; ++x) acc += (a[x] - b[x]) * (a[x] - b[x]);
+    return std::sqrt(acc);
+  };
+  double V = 0;
+  for (int i = 0; i < N; ++i)
+    for (int j = i + 1; j < N; ++j) V += 1.0 / dist(r + 3 * i, r + 3 * j);
+  for (int i = 0; i < N; ++i)
+    for (int I = 0; I < M; ++I) V -= s.Z[I] / dist(r + 3 * i, s.R + 3 * I);
+  for (int I = 0; I < M; ++I)
+    for (int J = I + 1; J < M; ++J) V += s.Z[I] * s.Z[J] / dist(s.R + 3 * I, s.R + 3 * J);
+  return V;
+}
+
+template <class T>
+std::vector<T> lift(const double* x, int64_t n) {
+  std::vector<T> y(n);
+  for (int64_t k = 0; k < n; ++k) y[k] = T(x[k]);
+  return y;
+}
+
+int n_threads_setting = 0;
+
+}  // namespace
+
+extern "C" {
+
+int oracle_param_count(const OracleSpec* s, int64_t* P) {
+  *P = Layout(*s).total;
+  return 0;
+}
+
+void oracle_set_threads(int n) { n_threads_setting = n; }
+
+int oracle_threads() {
+#ifdef _OPENMP
+  return n_threads_setting > 0 ? n_threads_setting : omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+// log|psi|, sign psi for B walkers r[B][N][3].
+int oracle_eval(const OracleSpec* s, const double* theta, const double* r, int64_t B, double* logabs,
+                int8_t* sign) {
+  const Layout lay(*s);
+  const int N3 = 3 * (s->n_up + s->n_dn);
+#pragma omp parallel for schedule(dynamic) num_threads(oracle_threads())
+  for (int64_t b = 0; b < B; ++b) {
+    Walker<double> w = log_psi<double>(*s, lay, theta, r + b * N3);
+    logabs[b] = w.logabs;
+    sign[b] = (int8_t)w.sign;
+  }
+  return 0;
+}
+
+// Local energy E_loc = -1/2 sum_x (d_x^2 log|psi| + (d_x log|psi|)^2) + V (Eq. 31).
+// Optional grad[B][3N] and lap[B] (d_x log|psi| and sum_x d_x^2 log|psi|).
+int oracle_local_energy(const OracleSpec* s, const double* theta, const double* r, int64_t B,
+                        double* logabs, int8_t* sign, double* e_loc, double* grad, double* lap) {
+  const Layout lay(*s);
+  const int N3 = 3 * (s->n_up + s->n_dn);
+  const std::vector<HD> thh = lift<HD>(theta, lay.total);
+#pragma omp parallel for schedule(dynamic) num_threads(oracle_threads())
+  for (int64_t b = 0; b < B; ++b) {
+    const double* rb = r + b * N3;
+    Walker<double> w0 = log_psi<double>(*s, lay, theta, rb);
+    logabs[b] = w0.logabs;
+    sign[b] = (int8_t)w0.sign;
+    double sum_d2 = 0, sum_g2 = 0;
+    std::vector<HD> rh = lift<HD>(rb, N3);
+    for (int x = 0; x < N3; ++x) {
+      rh[x].a = rh[x].b = 1.0;
+      Walker<HD> w = log_psi<HD>(*s, lay, thh.data(), rh.data());
+      rh[x].a = rh[x].b = 0.0;
+      if (grad) grad[b * N3 + x] = w.logabs.a;
+      sum_d2 += w.logabs.ab;
+      sum_g2 += w.logabs.a * w.logabs.a;
+    }
+    if (lap) lap[b] = sum_d2;
+    e_loc[b] = (w0.sign == 0 ? std::numeric_limits<double>::quiet_NaN() : -0.5 * (sum_d2 + sum_g2)) +
+               potential(*s, rb);
+  }
+  return 0;
+}
+
+// Coulomb potential per walker.
+int oracle_potential(const OracleSpec* s, const double* r, int64_t B, double* V) {
+  const int N3 = 3 * (s->n_up + s->n_dn);
+  for (int64_t b = 0; b < B; ++b) V[b] = potential(*s, r + b * N3);
+  return 0;
+}
+
+// Directional derivatives of log|psi| in parameter space:
+// out[b][k] = sum_p dirs[k][p] d log|psi_b| / d theta_p, k < n_dir.
+int oracle_grad_jvp(const OracleSpec* s, const double* theta, const double* r, int64_t B,
+                    const double* dirs, int32_t n_dir, double* out) {
+  const Layout lay(*s);
+  const int N3 = 3 * (s->n_up + s->n_dn);
+  const int64_t P = lay.total;
+#pragma omp parallel for collapse(2) schedule(dynamic) num_threads(oracle_threads())
+  for (int64_t b = 0; b < B; ++b)
+    for (int k = 0; k < n_dir; ++k) {
+      std::vector<Dual> th(P);
+      for (int64_t p = 0; p < P; ++p) th[p] = Dual(theta[p], dirs[(int64_t)k * P + p]);
+      std::vector<Dual> rd = lift<Dual>(r + b * N3, N3);
+      out[b * n_dir + k] = log_psi<Dual>(*s, lay, th.data(), rd.data()).logabs.d;
+    }
+  return 0;
+}
+
+// Partial derivatives d log|psi_b| / d theta_idx[k]: out[b][k].
+int oracle_grad_index(const OracleSpec* s, const double* theta, const double* r, int64_t B,
+                      const int64_t* idx, int32_t n_idx, double* out) {
+  const Layout lay(*s);
+  const int N3 = 3 * (s->n_up + s->n_dn);
+  const int64_t P = lay.total;
+#pragma omp parallel for collapse(2) schedule(dynamic) num_threads(oracle_threads())
+  for (int64_t b = 0; b < B; ++b)
+    for (int k = 0; k < n_idx; ++k) {
+      std::vector<Dual> th = lift<Dual>(theta, P);
+      th[idx[k]].d = 1.0;
+      std::vector<Dual> rd = lift<Dual>(r + b * N3, N3);
+      out[b * n_idx + k] = log_psi<Dual>(*s, lay, th.data(), rd.data()).logabs.d;
+    }
+  return 0;
+}
+
+// One random-walk Metropolis step (Sec. 5) on given draws:
+// r' = r + step * xi;  accept iff log u < 2 (log|psi(r')| - log|psi(r)|), strict,
+// and psi(r') != 0.  r[B][N][3] and logabs[B] are updated in place.
+int oracle_metropolis_step(const OracleSpec* s, const double* theta, double* r, double* logabs, int64_t B,
+                           const double* xi, const double* u, double step, int8_t* accepted) {
+  const Layout lay(*s);
+  const int N3 = 3 * (s->n_up + s->n_dn);
+#pragma omp parallel for schedule(dynamic) num_threads(oracle_threads())
+  for (int64_t b = 0; b < B; ++b) {
+    std::vector<double> rp(N3);
+    for (int x = 0; x < N3; ++x) rp[x] = r[b * N3 + x] + step * xi[b * N3 + x];
+    Walker<double> w = log_psi<double>(*s, lay, theta, rp.data());
+    const bool acc = w.sign != 0 && std::log(u[b]) < 2.0 * (w.logabs - logabs[b]);
+    if (acc) {
+      for (int x = 0; x < N3; ++x) r[b * N3 + x] = rp[x];
+      logabs[b] = w.logabs;
+    }
+    accepted[b] = acc ? 1 : 0;
+  }
+  return 0;
+}
+
+// Debug views of one walker: final embeddings f[N][D] and orbital matrices
+// A[2][K][nmax][nmax] (rows = electrons of the spin channel, cols = orbitals).
+int oracle_intermediates(const OracleSpec* s, const double* theta, const double* r, double* f_out,
+                         double* A_out) {
+  const Layout lay(*s);
+  log_psi<double>(*s, lay, theta, r, f_out, A_out);
+  return 0;
+}
+
+}  // extern "C"

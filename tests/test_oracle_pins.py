@@ -1,0 +1,563 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Nothing here compares the oracle with itself: every expected value is a
+closed form (hydrogenic energies, Kato-cusp two-electron wave functions
+differentiated symbolically with sympy), a brute-force computation
+(Leibniz determinants), a finite difference, an exact invariance of the
+ansatz (antisymmetry Eq. 3, equivariance Eq. 9, rigid motions), a sampling
+statement with its batch-means error bar (Eq. 35), a published known-answer
+vector, or a hand-computable special case of the network with one-hot
+weights (which pins every layout and index convention).
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_14123_gb300 import fixtures as fx
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def setp(theta, system, cfg, name, value):
+    o, shape = fx.param_offsets(system, cfg)[name]
+    theta[o:o + int(np.prod(shape))] = np.broadcast_to(np.asarray(value, dtype=np.float64), shape).reshape(-1)
+
+
+def pidx(system, cfg, name, flat=0):
+    return fx.param_offsets(system, cfg)[name][0] + flat
+
+
+def rand_rotation(rng, reflect=False):
+    q, r = np.linalg.qr(rng.normal(size=(3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    if reflect:
+        q = q @ np.diag([1.0, 1.0, -1.0])
+    return q
+
+
+def small_system():
+    return fx.System(Z=np.array([2.0, 1.0]), R=np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 1.4]]), n_up=2, n_down=1)
+
+
+# ----------------------------------------------------------------------------
+# Inputs: Philox, Box-Muller, parameter count
+# ----------------------------------------------------------------------------
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if l.strip() and l[0] != "#"]
+    for row in rows:
+        v = [int(x, 16) for x in row]
+        out = fx.philox4x32_10(v[0:4], v[4:6])
+        assert [int(x) for x in out] == v[6:10]
+
+
+def test_box_muller_moments():
+    z = fx.walker_normals(7, np.arange(2000), 3, fx.TAG_PROPOSE, 64).ravel()
+    n = z.size
+    assert abs(z.mean()) < 5 / math.sqrt(n)
+    assert abs(z.var() - 1) < 5 * math.sqrt(2 / n)
+    assert abs(np.mean(z ** 4) - 3) < 5 * math.sqrt(96 / n)
+
+
+@pytest.mark.parametrize("name,P", [("lih_fp64", 19285), ("n2_fp32", 412656), ("c4h4_bf16", 2210720)])
+def test_param_count(name, P):
+    wl = fx.workload(name)
+    assert fx.param_count(wl.system, wl.cfg) == P
+    assert oracle.Oracle(wl.system, wl.cfg).P == P
+
+
+# ----------------------------------------------------------------------------
+# Closed-form wave functions (network switched off)
+# ----------------------------------------------------------------------------
+def test_hydrogen_network_off_exact():
+    """psi = exp(-r): E_loc = -1/2 at every r (Sec. 2.2: hydrogenic atoms are solvable)."""
+    H = fx.molecule("H")
+    cfg = fx.AnsatzCfg(8, 2, 1, use_cusp=0)
+    o = oracle.Oracle(H, cfg)
+    th = fx.network_off_params(H, cfg, 1.0)
+    r = fx.init_walkers(H, 64, 11, sigma=2.0)
+    out = o.local_energy(th, r)
+    rr = np.linalg.norm(r[:, 0], axis=1)
+    np.testing.assert_allclose(out["logabs"], -rr, rtol=0, atol=1e-13)
+    assert np.all(np.abs(out["e_loc"] + 0.5) <= 1e-12 * np.maximum(1, 1 / rr))
+    assert np.all(out["sign"] == 1)
+
+
+@pytest.mark.parametrize("Z", [2.0, 3.0])
+def test_hydrogenic_ion(Z):
+    sys_ = fx.System(Z=np.array([Z]), R=np.array([[0.1, -0.3, 0.2]]), n_up=1, n_down=0)
+    cfg = fx.AnsatzCfg(8, 1, 1, use_cusp=0)
+    o = oracle.Oracle(sys_, cfg)
+    th = fx.network_off_params(sys_, cfg, Z)
+    r = fx.init_walkers(sys_, 32, 5)
+    e = o.local_energy(th, r)["e_loc"]
+    np.testing.assert_allclose(e, -Z * Z / 2, rtol=0, atol=1e-11)
+
+
+def test_two_electron_product_no_cusp():
+    """psi = exp(-Z r1 - Z r2): E_loc = -Z^2 + 1/r12 (V_ee and the spin split)."""
+    Z = 2.0
+    sys_ = fx.System(Z=np.array([Z]), R=np.zeros((1, 3)), n_up=1, n_down=1)
+    cfg = fx.AnsatzCfg(8, 2, 1, use_cusp=0)
+    o = oracle.Oracle(sys_, cfg)
+    th = fx.network_off_params(sys_, cfg, Z)
+    r = fx.init_walkers(sys_, 32, 9)
+    e = o.local_energy(th, r)["e_loc"]
+    r12 = np.linalg.norm(r[:, 0] - r[:, 1], axis=1)
+    np.testing.assert_allclose(e, -Z * Z + 1 / r12, rtol=1e-12, atol=1e-11)
+
+
+def _sympy_eloc(psi_fn, n_elec, Zs, Rs):
+    """E_loc = -1/2 (Lap psi)/psi + V from a closed-form psi, by sympy."""
+    sp = pytest.importorskip("sympy")
+    xs = sp.symbols(" ".join(f"x{i}_{k}" for i in range(n_elec) for k in range(3)), real=True)
+    pos = [sp.Matrix(xs[3 * i:3 * i + 3]) for i in range(n_elec)]
+    psi = psi_fn(sp, pos)
+    lap = sum(sp.diff(psi, x, 2) for x in xs)
+    V = 0
+    for i in range(n_elec):
+        for j in range(i + 1, n_elec):
+            V += 1 / (pos[i] - pos[j]).norm()
+        for Z, R in zip(Zs, Rs):
+            V -= Z / (pos[i] - sp.Matrix(R)).norm()
+    eloc = -sp.Rational(1, 2) * lap / psi + V
+    return sp.lambdify(xs, eloc, "math"), sp.lambdify(xs, sp.log(sp.Abs(psi)), "math"), sp.lambdify(xs, psi, "math")
+
+
+def test_opposite_spin_cusp_closed_form():
+    """exp(-Z r1 - Z r2) times the electron cusp of Eq. (25) with c = 1/2, alpha = 1."""
+    Z = 2.0
+    sys_ = fx.System(Z=np.array([Z]), R=np.zeros((1, 3)), n_up=1, n_down=1)
+    cfg = fx.AnsatzCfg(8, 2, 1, use_cusp=1, cusp_alpha=1.0)
+    o = oracle.Oracle(sys_, cfg)
+    th = fx.network_off_params(sys_, cfg, Z)
+
+    def psi(sp, p):
+        r1, r2, r12 = p[0].norm(), p[1].norm(), (p[0] - p[1]).norm()
+        return sp.exp(-Z * r1 - Z * r2) * sp.exp(-sp.Rational(1, 2) / (1 + r12))
+
+    f_e, f_l, _ = _sympy_eloc(psi, 2, [Z], [[0, 0, 0]])
+    r = fx.init_walkers(sys_, 12, 21)
+    out = o.local_energy(th, r)
+    for b in range(r.shape[0]):
+        args = r[b].ravel()
+        assert out["e_loc"][b] == pytest.approx(f_e(*args), rel=1e-10, abs=1e-10)
+        assert out["logabs"][b] == pytest.approx(f_l(*args), rel=1e-12, abs=1e-12)
+
+
+def test_same_spin_pair_determinant_and_cusp():
+    """Two same-spin electrons, orbitals exp(-a r), exp(-b r):
+    psi = (e^{-a r1 - b r2} - e^{-b r1 - a r2}) exp(-1/4 / (1 + r12))."""
+    a, b = 1.7, 0.6
+    sys_ = fx.System(Z=np.array([2.0]), R=np.zeros((1, 3)), n_up=2, n_down=0)
+    cfg = fx.AnsatzCfg(8, 2, 1, use_cusp=1, cusp_alpha=1.0)
+    o = oracle.Oracle(sys_, cfg)
+    th = fx.network_off_params(sys_, cfg, 1.0)
+    setp(th, sys_, cfg, "zeta_up", [[a], [b]])
+
+    def psi(sp, p):
+        r1, r2, r12 = p[0].norm(), p[1].norm(), (p[0] - p[1]).norm()
+        return (sp.exp(-a * r1 - b * r2) - sp.exp(-b * r1 - a * r2)) * sp.exp(-sp.Rational(1, 4) / (1 + r12))
+
+    f_e, f_l, f_p = _sympy_eloc(psi, 2, [2.0], [[0, 0, 0]])
+    r = fx.init_walkers(sys_, 12, 4)
+    out = o.local_energy(th, r)
+    for k in range(r.shape[0]):
+        args = r[k].ravel()
+        assert out["e_loc"][k] == pytest.approx(f_e(*args), rel=1e-9, abs=1e-9)
+        assert out["logabs"][k] == pytest.approx(f_l(*args), rel=1e-12, abs=1e-12)
+        assert out["sign"][k] == np.sign(f_p(*args))
+
+
+# ----------------------------------------------------------------------------
+# Determinants against the Leibniz formula; envelope layout
+# ----------------------------------------------------------------------------
+def _leibniz(A):
+    n = A.shape[0]
+    tot = 0.0
+    for perm in itertools.permutations(range(n)):
+        inv = sum(1 for i in range(n) for j in range(i + 1, n) if perm[i] > perm[j])
+        tot += (-1) ** inv * np.prod([A[i, perm[i]] for i in range(n)])
+    return tot
+
+
+@pytest.mark.parametrize("n_up", [1, 3, 4])
+def test_multi_determinant_leibniz(n_up):
+    """psi = sum_p c_p det A^p with A^p_ik = sum_I omega exp(-zeta d_iI) (Eqs. 20-21), brute force."""
+    rng = np.random.default_rng(n_up)
+    sys_ = fx.System(Z=np.array([3.0, 1.0]), R=np.array([[0, 0, 0], [0.2, 0.5, 1.9]]), n_up=n_up, n_down=0)
+    K = 3
+    cfg = fx.AnsatzCfg(8, 1, K, use_cusp=0)
+    o = oracle.Oracle(sys_, cfg)
+    th = fx.network_off_params(sys_, cfg, 1.0)
+    om = rng.normal(size=(K * n_up, 2))
+    ze = rng.uniform(0.5, 2.0, size=(K * n_up, 2))
+    c = np.array([1.0, -0.7, 0.4])
+    setp(th, sys_, cfg, "omega_up", om)
+    setp(th, sys_, cfg, "zeta_up", ze)
+    setp(th, sys_, cfg, "c", c)
+    r = fx.init_walkers(sys_, 16, 8)
+    la, sg = o.evaluate(th, r)
+    for b in range(r.shape[0]):
+        d = np.linalg.norm(r[b][:, None, :] - sys_.R[None], axis=-1)  # [i][I]
+        psi = 0.0
+        for p in range(K):
+            A = np.array([[sum(om[p * n_up + k, I] * math.exp(-ze[p * n_up + k, I] * d[i, I]) for I in range(2))
+                           for k in range(n_up)] for i in range(n_up)])
+            if b == 0:
+                _, Ao = o.intermediates(th, r[b:b + 1])
+                np.testing.assert_allclose(Ao[0, p, :n_up, :n_up], A, rtol=1e-13)
+            psi += c[p] * _leibniz(A)
+        assert la[b] == pytest.approx(math.log(abs(psi)), rel=1e-12, abs=1e-12)
+        assert sg[b] == np.sign(psi)
+
+
+def test_singular_determinant():
+    """Two identical orbitals: det = 0, so sign 0, log|psi| = -inf, E_loc NaN."""
+    sys_ = fx.System(Z=np.array([2.0]), R=np.zeros((1, 3)), n_up=2, n_down=0)
+    cfg = fx.AnsatzCfg(8, 1, 1, use_cusp=0)
+    o = oracle.Oracle(sys_, cfg)
+    th = fx.network_off_params(sys_, cfg, 1.3)
+    r = fx.init_walkers(sys_, 4, 1)
+    out = o.local_energy(th, r)
+    assert np.all(out["sign"] == 0) and np.all(np.isneginf(out["logabs"])) and np.all(np.isnan(out["e_loc"]))
+
+
+# ----------------------------------------------------------------------------
+# Coulomb terms
+# ----------------------------------------------------------------------------
+def test_potential_hand_placed():
+    sys_ = fx.System(Z=np.array([1.0, 1.0]), R=np.array([[0, 0, 0], [0, 0, 2.0]]), n_up=1, n_down=1)
+    o = oracle.Oracle(sys_, fx.AnsatzCfg(8, 1, 1))
+    r = np.array([[[1.0, 0, 0], [-1.0, 0, 0]]])
+    expect = 1 / 2.0 - 2 * (1.0 + 1 / math.sqrt(5.0)) + 1 / 2.0
+    assert o.potential(r)[0] == pytest.approx(expect, rel=1e-15)
+
+
+@pytest.mark.parametrize("name,vnn", [("N2", 49 / 2.068), ("LiH", 3 / 3.015)])
+def test_nuclear_repulsion(name, vnn):
+    sys_ = fx.molecule(name)
+    o = oracle.Oracle(sys_, fx.AnsatzCfg(8, 1, 1))
+    N = sys_.n_elec
+    far = 1e16 * (np.arange(N)[:, None] + 1) * np.array([[1.0, 2.0, 3.0]])
+    assert o.potential(far[None])[0] == pytest.approx(vnn, rel=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# Symmetries of the full random-weight ansatz
+# ----------------------------------------------------------------------------
+def _random_case(name):
+    if name == "small":
+        sys_, cfg = small_system(), fx.AnsatzCfg(8, 2, 2)
+    else:
+        wl = fx.workload("lih_fp64")
+        sys_, cfg = wl.system, wl.cfg
+    th = fx.init_params(sys_, cfg, 3)
+    r = fx.init_walkers(sys_, 6, 3)
+    return sys_, cfg, th, r
+
+
+@pytest.mark.parametrize("name", ["small", "lih"])
+def test_antisymmetry(name):
+    """Exchange of two same-spin electrons flips the sign only (Eqs. 3, 9)."""
+    sys_, cfg, th, r = _random_case(name)
+    o = oracle.Oracle(sys_, cfg)
+    a = o.local_energy(th, r)
+    rs = r.copy()
+    rs[:, [0, 1]] = rs[:, [1, 0]]
+    b = o.local_energy(th, rs)
+    np.testing.assert_allclose(b["logabs"], a["logabs"], rtol=1e-12, atol=1e-12)
+    assert np.all(b["sign"] == -a["sign"])
+    np.testing.assert_allclose(b["e_loc"], a["e_loc"], rtol=1e-9, atol=1e-9)
+
+
+def test_opposite_spin_exchange_is_not_a_symmetry():
+    """Spins are fixed (Sec. 2.2): exchanging an up and a down electron changes psi."""
+    sys_, cfg, th, r = _random_case("small")
+    o = oracle.Oracle(sys_, cfg)
+    la, _ = o.evaluate(th, r)
+    rs = r.copy()
+    rs[:, [0, 2]] = rs[:, [2, 0]]
+    lb, _ = o.evaluate(th, rs)
+    assert np.all(np.abs(la - lb) > 1e-6)
+
+
+@pytest.mark.parametrize("reflect", [False, True])
+def test_rigid_motion_invariance(reflect):
+    sys_, cfg, th, r = _random_case("small")
+    o = oracle.Oracle(sys_, cfg)
+    a = o.local_energy(th, r)
+    rng = np.random.default_rng(5)
+    Q, t = rand_rotation(rng, reflect), rng.normal(size=3)
+    sys2 = fx.System(Z=sys_.Z, R=sys_.R @ Q.T + t, n_up=sys_.n_up, n_down=sys_.n_down)
+    b = oracle.Oracle(sys2, cfg).local_energy(th, r @ Q.T + t)
+    np.testing.assert_allclose(b["logabs"], a["logabs"], rtol=1e-11, atol=1e-11)
+    np.testing.assert_allclose(b["e_loc"], a["e_loc"], rtol=1e-9, atol=1e-9)
+    assert np.all(a["sign"] == b["sign"])
+
+
+def test_orbital_equivariance():
+    """Permuting same-spin electrons permutes rows of A and of the embeddings (Eq. 9)."""
+    sys_ = fx.molecule("N2")
+    cfg = fx.AnsatzCfg(16, 2, 2)
+    o = oracle.Oracle(sys_, cfg)
+    th = fx.init_params(sys_, cfg, 1)
+    r = fx.init_walkers(sys_, 1, 1)
+    perm_up = np.array([3, 0, 6, 1, 5, 2, 4])
+    perm_dn = np.array([2, 4, 0, 6, 1, 3, 5])
+    order = np.concatenate([perm_up, 7 + perm_dn])
+    f, A = o.intermediates(th, r)
+    f2, A2 = o.intermediates(th, r[:, order])
+    np.testing.assert_allclose(f2, f[order], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(A2[0], A[0][:, perm_up], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(A2[1], A[1][:, perm_dn], rtol=1e-12, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------
+# Derivatives against finite differences
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["small", "lih"])
+def test_coordinate_derivatives_finite_differences(name):
+    sys_, cfg, th, r = _random_case(name)
+    o = oracle.Oracle(sys_, cfg)
+    r = r[:3]
+    out = o.local_energy(th, r, with_grad=True)
+    N3 = 3 * sys_.n_elec
+    h1, h2 = 1e-5, 2e-3
+    for b in range(r.shape[0]):
+        lap_fd = 0.0
+        for x in range(N3):
+            def f(dx):
+                rr = r[b].ravel().copy()
+                rr[x] += dx
+                return o.evaluate(th, rr[None])[0][0]
+            f0 = f(0.0)
+            g = (f(h1) - f(-h1)) / (2 * h1)
+            d2 = (-f(2 * h2) + 16 * f(h2) - 30 * f0 + 16 * f(-h2) - f(-2 * h2)) / (12 * h2 * h2)
+            assert out["grad"][b, x] == pytest.approx(g, rel=1e-6, abs=1e-6)
+            lap_fd += d2
+        assert out["lap"][b] == pytest.approx(lap_fd, rel=1e-5, abs=1e-5)
+        V = o.potential(r[b:b + 1])[0]
+        e_fd = -0.5 * (lap_fd + np.sum(out["grad"][b] ** 2)) + V
+        assert out["e_loc"][b] == pytest.approx(e_fd, rel=1e-5, abs=1e-5)
+
+
+def test_parameter_gradient_finite_differences():
+    """d log|psi| / d theta by dual numbers vs central differences (h = 1e-4... 1e-5, FP64)."""
+    wl = fx.workload("lih_fp64")
+    sys_, cfg = wl.system, wl.cfg
+    o = oracle.Oracle(sys_, cfg)
+    th = fx.init_params(sys_, cfg, 0)
+    r = fx.init_walkers(sys_, 2, 0)
+    rng = np.random.default_rng(0)
+    idx = []
+    for name, (off, shape) in fx.param_offsets(sys_, cfg).items():
+        n = int(np.prod(shape))
+        idx += list(off + rng.choice(n, size=min(n, 4), replace=False))
+    idx = np.array(sorted(set(idx)))
+    g = o.grad_index(th, r, idx)
+    h = 1e-5
+    for k, p in enumerate(idx):
+        tp, tm = th.copy(), th.copy()
+        tp[p] += h
+        tm[p] -= h
+        fd = (o.evaluate(tp, r)[0] - o.evaluate(tm, r)[0]) / (2 * h)
+        np.testing.assert_allclose(g[:, k], fd, rtol=1e-6, atol=1e-7)
+    # directional derivatives agree with the sum of partials
+    dirs = np.zeros((2, o.P))
+    dirs[0, idx] = rng.normal(size=idx.size)
+    dirs[1] = rng.normal(size=o.P) * 1e-2
+    jv = o.grad_jvp(th, r, dirs)
+    np.testing.assert_allclose(jv[:, 0], g @ dirs[0, idx], rtol=1e-10, atol=1e-12)
+    fd = (o.evaluate(th + h * dirs[1], r)[0] - o.evaluate(th - h * dirs[1], r)[0]) / (2 * h)
+    np.testing.assert_allclose(jv[:, 1], fd, rtol=1e-6, atol=1e-7)
+
+
+def test_envelope_exponent_gradient_closed_form():
+    """For psi = exp(-zeta r), d log|psi| / d zeta = -r exactly."""
+    H = fx.molecule("H")
+    cfg = fx.AnsatzCfg(8, 1, 1, use_cusp=0)
+    o = oracle.Oracle(H, cfg)
+    th = fx.network_off_params(H, cfg, 1.3)
+    r = fx.init_walkers(H, 16, 2)
+    g = o.grad_index(th, r, [pidx(H, cfg, "zeta_up")])[:, 0]
+    np.testing.assert_allclose(g, -np.linalg.norm(r[:, 0], axis=1), rtol=1e-14)
+
+
+# ----------------------------------------------------------------------------
+# Network structure pinned by one-hot weights (layouts, normalisations, order)
+# ----------------------------------------------------------------------------
+def test_embedding_update_layout():
+    """W_h = I, constant edge filters (W2 = 0, b2 = beta_t): messages are
+    beta_t times the normalised sums of Eq. (17); W_g acts on [m_par; m_anti; m_nuc]."""
+    sys_ = small_system()  # 2 up, 1 down, 2 nuclei
+    D = 2
+    cfg = fx.AnsatzCfg(D, 1, 1, use_cusp=0)
+    rng = np.random.default_rng(1)
+    th = fx.init_params(sys_, cfg, 4)
+    setp(th, sys_, cfg, "W_h0", np.eye(D))
+    beta = {"par": np.array([0.7, -1.1]), "anti": np.array([1.3, 0.4]), "nuc": np.array([-0.5, 0.9])}
+    for t in beta:
+        setp(th, sys_, cfg, f"W2_{t}0", 0.0)
+        setp(th, sys_, cfg, f"b2_{t}0", beta[t])
+    Wg = rng.normal(size=(D, 3 * D))
+    bg = rng.normal(size=D)
+    setp(th, sys_, cfg, "W_g0", Wg)
+    setp(th, sys_, cfg, "b_g0", bg)
+    E = th[pidx(sys_, cfg, "E_spin"):][:2 * D].reshape(2, D)
+    Y = th[pidx(sys_, cfg, "Y0"):][:2 * D].reshape(2, D)
+    o = oracle.Oracle(sys_, cfg)
+    f, _ = o.intermediates(th, fx.init_walkers(sys_, 1, 0))
+    spins = [0, 0, 1]
+    for i in range(3):
+        same = [j for j in range(3) if j != i and spins[j] == spins[i]]
+        opp = [j for j in range(3) if spins[j] != spins[i]]
+        m_par = beta["par"] * sum((E[spins[j]] for j in same), np.zeros(D)) / max(1, len(same))
+        m_anti = beta["anti"] * sum((E[spins[j]] for j in opp), np.zeros(D)) / max(1, len(opp))
+        m_nuc = beta["nuc"] * (Y[0] + Y[1]) / 2
+        expect = E[spins[i]] + np.tanh(Wg @ np.concatenate([m_par, m_anti, m_nuc]) + bg)
+        np.testing.assert_allclose(f[i], expect, rtol=1e-13)
+
+
+def test_edge_filter_and_gaussian_features():
+    """One up and one down electron; W1 one-hot on Gaussian features 3 and 5,
+    W2 = I: w_anti(d) = tanh(e_{3,5}(d)), e_q(d) = exp(-(d - q rc/15)^2 / (2 (rc/15)^2))."""
+    sys_ = fx.System(Z=np.array([1.0]), R=np.array([[0.0, 0.0, 0.0]]), n_up=1, n_down=1)
+    D, Q, rc = 2, 16, 10.0
+    cfg = fx.AnsatzCfg(D, 1, 1, n_rbf=Q, rbf_cutoff=rc, use_cusp=0)
+    th = fx.init_params(sys_, cfg, 2)
+    Hm = np.array([[0.3, -1.2], [0.8, 0.5]])
+    G = np.array([[1.1, 0.2], [-0.4, 0.9]])
+    W1 = np.zeros((D, Q))
+    W1[0, 3] = 1.0
+    W1[1, 5] = 1.0
+    setp(th, sys_, cfg, "W_h0", Hm)
+    setp(th, sys_, cfg, "W1_anti0", W1)
+    setp(th, sys_, cfg, "b1_anti0", 0.0)
+    setp(th, sys_, cfg, "W2_anti0", np.eye(D))
+    setp(th, sys_, cfg, "b2_anti0", 0.0)
+    setp(th, sys_, cfg, "W2_nuc0", 0.0)
+    setp(th, sys_, cfg, "b2_nuc0", 0.0)
+    Wg = np.zeros((D, 3 * D))
+    Wg[:, D:2 * D] = G
+    setp(th, sys_, cfg, "W_g0", Wg)
+    setp(th, sys_, cfg, "b_g0", 0.0)
+    E = th[pidx(sys_, cfg, "E_spin"):][:2 * D].reshape(2, D)
+    r = np.array([[[0.4, -0.3, 1.0], [-1.2, 0.9, 2.1]]])
+    d = np.linalg.norm(r[0, 0] - r[0, 1])
+    s = rc / (Q - 1)
+    e = np.exp(-(d - np.arange(Q) * s) ** 2 / (2 * s * s))
+    w = np.tanh(np.array([e[3], e[5]]))
+    f, _ = oracle.Oracle(sys_, cfg).intermediates(th, r)
+    np.testing.assert_allclose(f[0], E[0] + np.tanh(G @ (w * (Hm @ E[1]))), rtol=1e-13)
+    np.testing.assert_allclose(f[1], E[1] + np.tanh(G @ (w * (Hm @ E[0]))), rtol=1e-13)
+
+
+def test_orbital_head_and_jastrow_layout():
+    """W_g = 0 keeps f^L = E_spin; then A_ik = (W_o f_i + b_o)_{p n + k} env and
+    J = w_J2 . tanh(W_J1 sum_i f_i + b_J1) (Eqs. 19, 24)."""
+    sys_ = small_system()
+    D, K = 4, 2
+    cfg = fx.AnsatzCfg(D, 2, K, use_cusp=0)
+    th = fx.init_params(sys_, cfg, 6)
+    for l in range(2):
+        setp(th, sys_, cfg, f"W_g{l}", 0.0)
+        setp(th, sys_, cfg, f"b_g{l}", 0.0)
+    rng = np.random.default_rng(3)
+    setp(th, sys_, cfg, "b_o_up", rng.normal(size=K * 2))
+    setp(th, sys_, cfg, "b_J1", rng.normal(size=D))
+    E = th[pidx(sys_, cfg, "E_spin"):][:2 * D].reshape(2, D)
+    off = fx.param_offsets(sys_, cfg)
+
+    def get(name):
+        o_, shape = off[name]
+        return th[o_:o_ + int(np.prod(shape))].reshape(shape)
+
+    o = oracle.Oracle(sys_, cfg)
+    r = fx.init_walkers(sys_, 1, 2)
+    f, A = o.intermediates(th, r)
+    np.testing.assert_allclose(f, E[[0, 0, 1]], rtol=1e-15)
+    Wo, bo, om, ze = get("W_o_up"), get("b_o_up"), get("omega_up"), get("zeta_up")
+    d = np.linalg.norm(r[0][:, None, :] - sys_.R[None], axis=-1)
+    for p in range(K):
+        for i in range(2):
+            for k in range(2):
+                row = p * 2 + k
+                env = np.sum(om[row] * np.exp(-ze[row] * d[i]))
+                assert A[0, p, i, k] == pytest.approx((Wo[row] @ E[0] + bo[row]) * env, rel=1e-13)
+    J = get("w_J2")[0] @ np.tanh(get("W_J1") @ (2 * E[0] + E[1]) + get("b_J1"))
+    la_on, _ = o.evaluate(th, r)
+    th_off = th.copy()
+    setp(th_off, sys_, cfg, "w_J2", 0.0)
+    la_off, _ = o.evaluate(th_off, r)
+    assert la_on[0] - la_off[0] == pytest.approx(J, rel=1e-12, abs=1e-13)
+
+
+# ----------------------------------------------------------------------------
+# Sampling statements (Sec. 5, Eq. 35) and the gradient estimator (Eq. 30)
+# ----------------------------------------------------------------------------
+def _sample_hydrogen(zeta, B, n_burn, n_keep, step, seed):
+    H = fx.molecule("H")
+    cfg = fx.AnsatzCfg(4, 1, 1, use_cusp=0)
+    o = oracle.Oracle(H, cfg)
+    th = fx.network_off_params(H, cfg, zeta)
+    r = fx.init_walkers(H, B, seed)
+    la, _ = o.evaluate(th, r)
+    rs, acc_tot = [], 0
+    for t in range(n_burn + n_keep):
+        xi, u = fx.metropolis_draws(seed, B, 1, t)
+        r, la, acc = o.metropolis_step(th, r, la, xi, u, step)
+        if t >= n_burn:
+            rs.append(r.copy())
+            acc_tot += acc.sum()
+    return o, th, H, cfg, np.stack(rs, axis=1), acc_tot / (B * n_keep)
+
+
+def test_metropolis_zero_variance_and_mean_radius():
+    """psi = exp(-r): E_loc has zero variance; <r> under |psi|^2 is 3/2 (within the Eq. 35 error bar)."""
+    o, th, H, cfg, rs, acc = _sample_hydrogen(1.0, 256, 100, 300, 0.6, 12)
+    e = o.local_energy(th, rs[:, -1])["e_loc"]
+    assert np.all(np.abs(e + 0.5) < 1e-11)
+    rad = np.linalg.norm(rs[:, :, 0], axis=-1)  # [B][steps]
+    mean, err = oracle.energy_estimate(rad)
+    assert 0.2 < acc < 0.95
+    assert abs(mean - 1.5) < 5 * err, (mean, err)
+
+
+def test_gradient_estimator_hydrogen():
+    """psi = exp(-zeta r): E(zeta) = zeta^2/2 - zeta, so dE/dzeta = zeta - 1; the
+    estimator 2 E[(E_loc - E) d log|psi|/d zeta] of Eq. (30) agrees within its error bar."""
+    zeta = 1.3
+    o, th, H, cfg, rs, _ = _sample_hydrogen(zeta, 256, 100, 200, 0.6, 13)
+    B, S = rs.shape[:2]
+    flat = rs.reshape(B * S, 1, 3)
+    e = o.local_energy(th, flat)["e_loc"].reshape(B, S)
+    g = o.grad_index(th, flat, [pidx(H, cfg, "zeta_up")])[:, 0].reshape(B, S)
+    contrib = np.empty((B, S))
+    for t in range(S):
+        w, _, _, _ = oracle.clipped_loss_weights(e[:, t], k=1e12)
+        contrib[:, t] = B * w * g[:, t]
+    est, err = oracle.energy_estimate(contrib)
+    assert abs(est - (zeta - 1)) < 5 * err + 1e-3, (est, err)
+    mean_e, err_e = oracle.energy_estimate(e)
+    assert abs(mean_e - (zeta ** 2 / 2 - zeta)) < 5 * err_e, (mean_e, err_e)
+
+
+def test_clipping_rule():
+    """Median / mean-absolute-deviation window (Sec. 4.4); brute force on a small batch."""
+    rng = np.random.default_rng(0)
+    for B in (7, 8):
+        e = rng.standard_cauchy(B)
+        w, c, med, hw = oracle.clipped_loss_weights(e, k=5.0)
+        s = sorted(e)
+        m = s[B // 2] if B % 2 else (s[B // 2 - 1] + s[B // 2]) / 2
+        assert med == m
+        assert hw == pytest.approx(5 * sum(abs(x - m) for x in e) / B)
+        assert np.all(c >= m - hw - 1e-15) and np.all(c <= m + hw + 1e-15)
+        assert np.allclose(w, 2 / B * (c - c.mean()))
+        assert abs(w.sum()) < 1e-14
