@@ -1,0 +1,400 @@
+"""Throughput of the VMC hot path on GB300: local energies per second.
+
+One step is one pass of the whole hot path over one batch of walkers:
+one Metropolis sweep (mcmc_step, Sec. 5), the local energies with value,
+Jacobian and Laplacian propagation (local_energy, Eq. 31), the clipped
+gradient weights (vmc_loss_weights, Sec. 4.4) and the weighted parameter
+gradient of log|psi| (grad_logpsi, Eq. 30) when the library provides it.
+``value`` = walkers processed per second over the timed steps (one local
+energy per walker per step), inputs resident in HBM; ``e2e`` = the same
+through the public API with host buffers and the copies inside the timed
+region.  Walkers are independent Markov chains, so with several GPUs each
+rank runs its own walkers (weak scaling, no collective on the data path).
+
+``--impl reference`` times the FP64 CPU oracle instead (host cores, bounded
+walker sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "local energies/sec (walker evals/s)"
+UNIT = "local_energies/s"
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="n2_fp32")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    p.add_argument("--profile-case", type=int, default=0, metavar="B",
+                   help="run one local_energy on B walkers of the workload and exit (small case for ncu)")
+    return p.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def workload_config(wl, world):
+    s, c = wl.system, wl.cfg
+    return {"workload": f"{wl.system.name} {s.n_elec}e, D={c.width}, L={c.n_layers}, K={c.n_det}, "
+                        f"{wl.B} walkers/GPU, {wl.precision.upper()}",
+            "molecule": s.name, "electrons": s.n_elec, "width": c.width, "layers": c.n_layers,
+            "det_pairs": c.n_det, "walkers_per_gpu": wl.B, "global_walkers": wl.B * world,
+            "precision": wl.precision, "parallelism": f"walker-sharded x{world}"}
+
+
+def oracle_sample(wl, seconds):
+    """Times the FP64 oracle's local energy on a bounded walker sample."""
+    import numpy as np
+
+    import oracle
+    from paper_2307_14123_gb300 import fixtures as fx
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.Oracle.set_threads(cores)
+    o = oracle.Oracle(wl.system, wl.cfg)
+    theta = fx.init_params(wl.system, wl.cfg, wl.param_seed)
+    n = cores
+    while True:
+        r = fx.init_walkers(wl.system, n, wl.walker_seed)
+        t0 = time.perf_counter()
+        o.local_energy(theta, r)
+        dt = time.perf_counter() - t0
+        if dt * 2 > seconds or n >= wl.B:
+            return n, dt, oracle.Oracle.threads()
+        n = min(wl.B, n * max(2, int(seconds / max(dt, 1e-3) / 2)))
+
+
+def run_reference(args):
+    from paper_2307_14123_gb300 import fixtures as fx
+
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return 0
+    wl = fx.workload(args.workload)
+    # size one step to ~4 s of host time so the whole run stays within minutes
+    n, dt, cores = oracle_sample(wl, 8.0)
+    per_walker = dt / n
+    step_n = max(1, min(wl.B, int(round(4.0 / per_walker))))
+    import numpy as np
+
+    import oracle
+
+    o = oracle.Oracle(wl.system, wl.cfg)
+    theta = fx.init_params(wl.system, wl.cfg, wl.param_seed)
+    r = fx.init_walkers(wl.system, step_n, wl.walker_seed)
+    for _ in range(args.warmup):
+        o.local_energy(theta, r)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.local_energy(theta, r)
+    total = time.perf_counter() - t0
+    value = step_n * args.steps / total
+    sample = f"oracle local_energy on {step_n} of the {wl.B} walkers per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded walkers and random-init weights)",
+            "config": workload_config(wl, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.path = None
+        self.dev = device_index
+
+    def start(self):
+        import torch
+
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        sel = []
+        try:
+            uuid = str(torch.cuda.get_device_properties(self.dev).uuid)
+            sel = ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            sel = []
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", *sel, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+def gemm_flops(kind, wl, chunk):
+    """Algorithmic FLOPs of one launch of a jet-forward GEMM over `chunk` walkers."""
+    s, c = wl.system, wl.cfg
+    N, D, K = s.n_elec, c.width, c.n_det
+    C = 3 * N + 2
+    if kind == "jet.gemm_update":
+        return 2.0 * chunk * N * C * 3 * D * D
+    if kind == "jet.gemm_node":
+        return 2.0 * chunk * N * C * D * D
+    return None
+
+
+def profile_case(args):
+    import torch
+
+    from paper_2307_14123_gb300 import Ansatz
+    from paper_2307_14123_gb300 import fixtures as fx
+
+    wl = fx.workload(args.workload)
+    dt = torch.float64 if wl.precision == "fp64" else torch.float32
+    h = Ansatz(wl.system, wl.cfg, "fp64" if wl.precision == "fp64" else "fp32", device="cuda:0")
+    theta = torch.tensor(fx.init_params(wl.system, wl.cfg, wl.param_seed), dtype=dt, device="cuda:0")
+    r = torch.tensor(fx.init_walkers(wl.system, args.profile_case, wl.walker_seed), dtype=dt, device="cuda:0")
+    la, sg, el = h.local_energy(theta, r)
+    torch.cuda.synchronize()
+    print("profile case done:", args.profile_case, "walkers, mean E_loc", float(el.double().mean()))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.profile_case:
+        return profile_case(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2307_14123_gb300 import Ansatz
+    from paper_2307_14123_gb300 import fixtures as fx
+    from paper_2307_14123_gb300.binding import DQError
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    wl = fx.workload(args.workload)
+    B = wl.B
+    dt = torch.float64 if wl.precision == "fp64" else torch.float32
+    h = Ansatz(wl.system, wl.cfg, "fp64" if wl.precision == "fp64" else "fp32", device=dev)
+    theta = torch.tensor(fx.init_params(wl.system, wl.cfg, wl.param_seed), dtype=dt, device=dev)
+    r0 = fx.init_walkers(wl.system, B, wl.walker_seed, walker_offset=rank * B)
+    r = torch.tensor(r0, dtype=dt, device=dev)
+    logabs, _ = h.ansatz_eval(theta, r)
+    step_size = wl.extra.get("step_size", 0.2)
+    try:
+        h.grad_logpsi(theta, r[:1], torch.ones(1, dtype=dt, device=dev), 0)
+        with_grad = True
+    except DQError:
+        with_grad = False
+    counter = [0]
+
+    def step(th, rr, la):
+        h.mcmc_step(th, rr, la, 1, step_size, wl.walker_seed, counter[0])
+        counter[0] += 1
+        la2, _, el, e2 = h.local_energy(th, rr, sums=True)
+        w, stats = h.vmc_loss_weights(el, 5.0)
+        g = h.grad_logpsi(th, rr, w, 0) if with_grad else None
+        return el, e2, g
+
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        step(theta, r, logabs)
+    torch.cuda.synchronize()
+
+    h.profile(True)
+    h.profile_reset()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step(theta, r, logabs)
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    h.profile(False)
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    prof = h.profile_read()
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = B * world * args.steps / (total_ms / 1e3)
+
+    # local_energy alone (same timed-kernel view, from the profile)
+    jet_ms = sum(ms for k, (ms, n) in prof.items() if k.startswith("jet.") or k == "esum")
+    launches = sum(n for _, (ms, n) in prof.items())
+    gpu_time_ms = sum(ms for _, (ms, n) in prof.items())
+
+    # roofline of the dominant kernel
+    pk, how = peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
+    roof = None
+    if dom is not None:
+        ms, n = prof[dom]
+        chunk = min(B, h.max_chunk())
+        flops = gemm_flops(dom, wl, chunk)
+        if flops is not None:
+            sm_mhz = pk.get("sm_max_mhz", 2070.0)
+            if wl.precision == "fp64":
+                peak = 1.25  # TFLOP/s FP64 (nominal, CUDA cores)
+            else:
+                peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 x max clock
+            ach = flops / (ms / n / 1e3) / 1e12
+            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None, "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"
+                    if wl.precision != "fp64" else "nominal FP64", "flops_per_launch": flops,
+                    "avg_launch_ms": ms / n, "share_of_gpu_time": ms / gpu_time_ms}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        th_h = theta.cpu().pin_memory()
+        r_h = r.cpu().pin_memory()
+        la_h = logabs.cpu().pin_memory()
+        el_h = torch.empty(B, dtype=dt).pin_memory()
+        g_h = torch.empty(h.P, dtype=dt).pin_memory() if with_grad else None
+        th_d, r_d, la_d = torch.empty_like(theta), torch.empty_like(r), torch.empty_like(logabs)
+        h2d = th_h.numel() * th_h.element_size() + r_h.numel() * r_h.element_size() + la_h.numel() * la_h.element_size()
+        d2h = r_h.numel() * r_h.element_size() + la_h.numel() * la_h.element_size() + el_h.numel() * el_h.element_size()
+        if with_grad:
+            d2h += g_h.numel() * g_h.element_size()
+
+        def e2e_step():
+            th_d.copy_(th_h, non_blocking=True)
+            r_d.copy_(r_h, non_blocking=True)
+            la_d.copy_(la_h, non_blocking=True)
+            el, _, g = step(th_d, r_d, la_d)
+            r_h.copy_(r_d, non_blocking=True)
+            la_h.copy_(la_d, non_blocking=True)
+            el_h.copy_(el, non_blocking=True)
+            if g is not None:
+                g_h.copy_(g, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            e2e_step()
+        b.record()
+        torch.cuda.synchronize()
+        t2 = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t2, op=dist.ReduceOp.MAX)
+        e2e = {"value": B * world * args.steps / (float(t2.item()) / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, dtc, cores = oracle_sample(wl, args.cpu_seconds)
+        cpu = {"value": n / dtc, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"FP64 oracle local_energy on {n} of the {B} walkers ({dtc:.1f} s); the oracle "
+                         f"has no reverse mode, so its Metropolis and gradient legs are not included"}
+
+    if rank == 0:
+        step_desc = "mcmc_step(1 sweep) + local_energy + vmc_loss_weights" + (" + grad_logpsi(weighted)" if with_grad
+                                                                             else " (grad_logpsi not built)")
+        cfg = workload_config(wl, world)
+        cfg.update({"step": step_desc, "l2": "flushed before every timed step (256 MB write)"})
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl.precision == "fp64" else "f32",
+                "data": "synthetic (seeded walkers and random-init weights)", "config": cfg,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk,
+                "local_energy_only": {"value": B * world * args.steps / (jet_ms / 1e3) if jet_ms else None,
+                                      "unit": UNIT, "note": "sum of the local_energy kernels' device time"},
+                "kernels_ms_per_step": {k: round(ms / args.steps, 4) for k, (ms, n) in
+                                        sorted(prof.items(), key=lambda kv: -kv[1][0])},
+                "peaks": how}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,218 @@
+/*
+ * dqmc.h - C ABI of the GB300 library for the data-parallel hot path of
+ * real-space variational Monte Carlo with a DeepQMC-style neural-network
+ * wave function (Schätzle, Szabó, Mezera, Hermann, Noé: "DeepQMC: an
+ * open-source software suite for variational optimization of deep-learning
+ * molecular wave functions", 2023).
+ *
+ * The ansatz instance (Sec. 3 of the paper):
+ *   - graph over electrons and nuclei; edge features are a Gaussian expansion
+ *     of the inter-particle distance (n_rbf Gaussians, centres q*rc/(n_rbf-1),
+ *     width rc/(n_rbf-1)), reused in every layer (Eqs. 15-16, first case);
+ *   - electron embeddings start from a spin-only embedding (Eq. 13, first
+ *     case) and are updated n_layers times by graph convolutions (Eq. 17)
+ *     over same-spin, opposite-spin and electron-nucleus edges, each sum
+ *     normalised by its number of edges, with the concatenating residual
+ *     update f <- f + tanh(W_g [m_par; m_anti; m_nuc] + b_g) (Eq. 18);
+ *     edge filters w(e) = W2 tanh(W1 e + b1) + b2; node map z_j = W_h f_j;
+ *     nucleus nodes carry a learnt vector Y_I per layer (Eq. 14);
+ *   - orbitals: linear head on f^L (Eq. 19) times isotropic Slater envelopes
+ *     sum_I omega exp(-zeta |r - R_I|) (Eq. 20);
+ *   - psi = sum_p c_p det A^{up,p} det A^{down,p} (Eq. 21) in the log domain
+ *     with log-sum-exp over p (Eqs. 27-28), times exp(J) with the learnable
+ *     Jastrow J = w_J2 . tanh(W_J1 sum_i f_i^L + b_J1) (Eq. 24) and the
+ *     electron cusp gamma = -sum_{i<j} alpha c_ij / (1 + alpha r_ij),
+ *     c = 1/4 (same spin) or 1/2 (opposite spin) (Eq. 25).
+ *
+ * Electrons are spin-sorted: the first n_up are spin up (Sec. 2.2).
+ * Units: bohr and hartree.
+ *
+ * Flat parameter vector (same dtype as the handle's arithmetic, see below),
+ * matrices [out][in] row-major, in this order:
+ *   E_spin[2][D];
+ *   per layer l < n_layers:
+ *     W_h[D][D];
+ *     for the edge types same-spin, opposite-spin, electron-nucleus:
+ *       W1[D][n_rbf], b1[D], W2[D][D], b2[D];
+ *     Y[n_nuc][D]; W_g[D][3D], b_g[D];
+ *   for spin up then spin down (n_s electrons of that spin):
+ *     W_o[K n_s][D], b_o[K n_s], omega[K n_s][n_nuc], zeta[K n_s][n_nuc]
+ *     (orbital row p*n_s + k is orbital k of determinant p);
+ *   c[K]; W_J1[D][D], b_J1[D], w_J2[D].
+ *
+ * Memory and dtypes.  Every array argument of a compute call is DEVICE memory
+ * owned by the caller, on the device that was current at dq_create.  The
+ * handle's precision fixes the dtype of params, r, logabs, e_loc, weights and
+ * grad_out: double for DQ_FP64, float for DQ_FP32 and DQ_BF16_MIXED.  sign is
+ * int8.  Sums written to double* arguments are FP64 in every mode.
+ *
+ * Workspace.  Compute calls allocate nothing: the caller passes a device
+ * workspace of at least dq_workspace_size() bytes (256-byte aligned).
+ * Walkers are processed in chunks of at most dq_max_chunk() walkers, so the
+ * workspace does not grow beyond one chunk.
+ *
+ * Streams and errors.  Calls enqueue work on `stream` (a cudaStream_t, NULL
+ * for the legacy default stream) and return without synchronising.
+ * Argument and shape errors are returned synchronously and nothing is
+ * enqueued.  Conditions found on the device never trap: a zero determinant
+ * gives sign 0 and logabs = -inf; a non-finite local energy is written as
+ * NaN; both are counted in a status word read by dq_last_device_status().
+ * The library never calls exit() or abort().
+ */
+#ifndef DQMC_H
+#define DQMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DQ_OK = 0,
+  DQ_ERR_ARG = 1,        /* null pointer, bad enum value, bad size      */
+  DQ_ERR_SHAPE = 2,      /* unsupported molecule / ansatz dimensions     */
+  DQ_ERR_CUDA = 3,       /* a CUDA runtime call failed                   */
+  DQ_ERR_NONFINITE = 4,  /* reserved: reported via dq_last_device_status */
+  DQ_ERR_WORKSPACE = 5,  /* workspace missing, too small or misaligned   */
+  DQ_ERR_TIMEOUT = 6,    /* a bounded device wait gave up                */
+  DQ_ERR_UNSUPPORTED = 7 /* operation not available in this precision    */
+} dq_status;
+
+typedef enum { DQ_FP64 = 0, DQ_FP32 = 1, DQ_BF16_MIXED = 2 } dq_precision;
+
+/* Operation codes for dq_workspace_size. */
+typedef enum {
+  DQ_OP_EVAL = 0,
+  DQ_OP_LOCAL_ENERGY = 1,
+  DQ_OP_MCMC = 2,
+  DQ_OP_GRAD = 3,
+  DQ_OP_LOSS_WEIGHTS = 4
+} dq_op;
+
+/* Device status flags (dq_last_device_status). */
+#define DQ_FLAG_SINGULAR 0x1u  /* some walker had psi = 0 (sign 0)          */
+#define DQ_FLAG_NONFINITE 0x2u /* some local energy or gradient not finite   */
+
+/* The molecule (Eq. 1).  Host memory; copied by dq_create. */
+typedef struct {
+  int32_t n_nuc;    /* M >= 1                        */
+  const double* Z;  /* [M] nuclear charges           */
+  const double* R;  /* [M][3] nuclear positions, bohr */
+  int32_t n_up;     /* spin-up electrons, >= 1        */
+  int32_t n_down;   /* spin-down electrons, >= 0      */
+} dq_system;
+
+/* Ansatz hyper-parameters (Sec. 3). */
+typedef struct {
+  int32_t width;      /* D: embedding width, multiple of 32, <= 512  */
+  int32_t n_layers;   /* L >= 1 message-passing layers                */
+  int32_t n_det;      /* K >= 1 determinant pairs                     */
+  int32_t n_rbf;      /* Gaussian distance features, multiple of 8    */
+  double rbf_cutoff;  /* rc: centre of the last Gaussian (bohr)       */
+  int32_t use_jastrow;
+  int32_t use_cusp;
+  double cusp_alpha;  /* alpha of Eq. (25); 1 gives the Kato cusp     */
+} dq_ansatz_cfg;
+
+typedef struct dq_handle_s* dq_handle;
+
+/* Create a handle on the current CUDA device.  Limits: n_up + n_down <= 64,
+ * max(n_up, n_down) <= 32, n_nuc <= 64.  Allocates small device tables (the
+ * only allocations of the library).  Returns DQ_ERR_SHAPE outside the limits. */
+dq_status dq_create(const dq_system* sys, const dq_ansatz_cfg* cfg, int32_t precision, dq_handle* out);
+dq_status dq_destroy(dq_handle h);
+
+/* Number of parameters P of the flat vector described above. */
+dq_status dq_param_count(dq_handle h, int64_t* P);
+
+/* Largest walker chunk processed at once (default 4096), and a setter
+ * (chunk >= 1).  Workspace sizes depend on min(B, chunk). */
+dq_status dq_max_chunk(dq_handle h, int64_t* chunk);
+dq_status dq_set_max_chunk(dq_handle h, int64_t chunk);
+
+/* Workspace bytes needed by operation `op` (dq_op) for B walkers. */
+dq_status dq_workspace_size(dq_handle h, int64_t B, int32_t op, size_t* bytes);
+
+/* ansatz_eval: log|psi| and sign psi for B walkers (Sec. 3, Eqs. 7-8, 21,
+ * 27-28).
+ *   params  [P]        flat parameter vector
+ *   r       [B][N][3]  electron positions, spin-sorted
+ *   logabs  [B]  out   log|psi| (-inf where psi = 0)
+ *   sign    [B]  out   +1, -1, or 0 where psi = 0                         */
+dq_status ansatz_eval(dq_handle h, const void* params, const void* r, int64_t B, void* logabs, int8_t* sign,
+                      void* ws, size_t ws_bytes, void* stream);
+
+/* local_energy: E_loc = -1/2 sum_i (Lap_i log|psi| + |grad_i log|psi||^2) + V
+ * (Sec. 4.2, Eq. 31), V = Coulomb potential of Eq. (1) plus the constant
+ * nuclear repulsion sum_{I<J} Z_I Z_J / R_IJ.  Also writes logabs and sign.
+ *   e_loc   [B]  out   NaN where psi = 0 or the result is not finite
+ *   e_sum2  [2]  out   nullable, device double: sum_b E_loc, sum_b E_loc^2
+ *                      (FP64 sums over the finite values)                  */
+dq_status local_energy(dq_handle h, const void* params, const void* r, int64_t B, void* logabs, int8_t* sign,
+                       void* e_loc, double* e_sum2, void* ws, size_t ws_bytes, void* stream);
+
+/* mcmc_step: n_steps random-walk Metropolis steps (Sec. 5) on B walkers.
+ * Step t = step_counter + s (s < n_steps) proposes r' = r + step_size * xi,
+ * xi ~ N(0, 1)^(3N), and accepts iff log u < 2 (log|psi(r')| - log|psi(r)|)
+ * (strict) and psi(r') != 0, u ~ U(0, 1).  xi and u are drawn from
+ * Philox4x32-10 (Salmon et al., SC'11) with key = seed and counter
+ * [walker, t mod 2^32, (tag << 24) | block, t >> 32], tag 1 for xi (Box-Muller
+ * pairs of words (x0, x1), (x2, x3) of block q/4 give xi_q), tag 2 for u
+ * (word x0 of block 0); uniforms are (x + 0.5) 2^-32.
+ *   r        [B][N][3] in/out    positions
+ *   logabs   [B]       in/out    log|psi| of r (as from ansatz_eval)
+ *   n_accepted         nullable, device int64: set to the number of
+ *                      accepted moves of this call                         */
+dq_status mcmc_step(dq_handle h, const void* params, void* r, void* logabs, int64_t B, int32_t n_steps,
+                    double step_size, uint64_t seed, uint64_t step_counter, int64_t* n_accepted, void* ws,
+                    size_t ws_bytes, void* stream);
+
+/* grad_logpsi: parameter gradient of log|psi| (Sec. 4.1, Eq. 30).
+ *   mode 0 (weighted): grad_out[P] = sum_b weights[b] d log|psi_b| / d theta
+ *                      (weights [B] required);
+ *   mode 1 (per walker): grad_out[B][P] = d log|psi_b| / d theta
+ *                      (weights ignored, may be NULL).
+ * Walkers with psi = 0 contribute zero.                                    */
+dq_status grad_logpsi(dq_handle h, const void* params, const void* r, int64_t B, const void* weights,
+                      int32_t mode, void* grad_out, void* ws, size_t ws_bytes, void* stream);
+
+/* vmc_loss_weights: clipped local energies and gradient weights (Sec. 4.4,
+ * Eq. 30).  Centre mu = median of e_loc (mean of the two middle values for
+ * even B), half-width = clip_k * mean |e_loc - mu|; E^_b = clamp(e_loc_b);
+ * weights[b] = (2/B)(E^_b - mean_b E^_b), so that grad_logpsi(mode 0) with
+ * these weights is the estimator of Eq. (30) on clipped energies.
+ *   e_loc   [B]   in, finite values expected (B <= 65536)
+ *   weights [B]   out
+ *   stats   [4]   nullable, device double out: mu, half-width, mean E^,
+ *                 mean of the unclipped e_loc                              */
+dq_status vmc_loss_weights(dq_handle h, const void* e_loc, int64_t B, double clip_k, void* weights,
+                           double* stats, void* ws, size_t ws_bytes, void* stream);
+
+/* Reads and clears the device status flags (DQ_FLAG_*) accumulated since the
+ * last read.  Synchronises `stream`. */
+dq_status dq_last_device_status(dq_handle h, void* stream, uint32_t* flags);
+
+/* Human-readable name of a status code (static string). */
+const char* dq_status_string(dq_status s);
+
+/* Measurement support (not part of the method): when enabled, every kernel
+ * launch of the handle is bracketed by two CUDA events recorded on the
+ * launching stream (from a pool of 32768 events created at the first
+ * enable, host-side driver objects only).  dq_profile_read synchronises on
+ * the recorded events and returns, for one kernel kind (0 <= kind <
+ * dq_profile_kind_count()), the summed device time in ms and the launch
+ * count since the last reset; it returns DQ_ERR_WORKSPACE if the pool ran
+ * out (later launches were not timed).  Kind names: dq_profile_kind_name. */
+dq_status dq_profile_enable(dq_handle h, int32_t on);
+dq_status dq_profile_reset(dq_handle h);
+dq_status dq_profile_read(dq_handle h, int32_t kind, double* total_ms, int64_t* launches);
+const char* dq_profile_kind_name(int32_t kind);
+int32_t dq_profile_kind_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DQMC_H */

@@ -30,37 +30,45 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.cpp")
+# The oracle proper (FP64) and the same source compiled with FP32 scalars,
+# which only serves to measure the rounding floor of an FP32 evaluation.
+_LIBS = {"fp64": os.path.join(_HERE, "liboracle.so"), "fp32": os.path.join(_HERE, "liboracle_fp32.so")}
+_DTYPES = {"fp64": np.float64, "fp32": np.float32}
 
 
-def build(force=False):
-    """Compile ``liboracle.so`` with g++ (OpenMP over walkers)."""
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+def build(force=False, real="fp64"):
+    """Compile the oracle library with g++ (OpenMP over walkers)."""
+    path = _LIBS[real]
+    if not force and os.path.exists(path) and os.path.getmtime(path) >= os.path.getmtime(_SRC):
+        return path
+    tmp = path + f".tmp{os.getpid()}"
     cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", _SRC, "-o", tmp]
+    if real == "fp32":
+        cmd.insert(1, "-DORACLE_REAL=float")
     subprocess.check_call(cmd)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
 
 
-class _Spec(ctypes.Structure):
-    _fields_ = [("n_nuc", ctypes.c_int32), ("Z", ctypes.c_void_p), ("R", ctypes.c_void_p),
-                ("n_up", ctypes.c_int32), ("n_dn", ctypes.c_int32),
-                ("D", ctypes.c_int32), ("L", ctypes.c_int32), ("K", ctypes.c_int32), ("Q", ctypes.c_int32),
-                ("rc", ctypes.c_double), ("use_jastrow", ctypes.c_int32), ("use_cusp", ctypes.c_int32),
-                ("alpha", ctypes.c_double)]
+def _spec_class(c_real):
+    class _Spec(ctypes.Structure):
+        _fields_ = [("n_nuc", ctypes.c_int32), ("Z", ctypes.c_void_p), ("R", ctypes.c_void_p),
+                    ("n_up", ctypes.c_int32), ("n_dn", ctypes.c_int32),
+                    ("D", ctypes.c_int32), ("L", ctypes.c_int32), ("K", ctypes.c_int32), ("Q", ctypes.c_int32),
+                    ("rc", c_real), ("use_jastrow", ctypes.c_int32), ("use_cusp", ctypes.c_int32),
+                    ("alpha", c_real)]
+    return _Spec
 
 
-_lib = None
+_SPECS = {"fp64": _spec_class(ctypes.c_double), "fp32": _spec_class(ctypes.c_float)}
+_libs = {}
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        build()
-        lib = ctypes.CDLL(_LIB_PATH)
+def _load(real="fp64"):
+    if real not in _libs:
+        build(real=real)
+        lib = ctypes.CDLL(_LIBS[real])
         P = ctypes.c_void_p
         lib.oracle_param_count.argtypes = [P, P]
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
@@ -72,8 +80,8 @@ def _load():
         lib.oracle_grad_index.argtypes = [P, P, P, ctypes.c_int64, P, ctypes.c_int32, P]
         lib.oracle_metropolis_step.argtypes = [P, P, P, P, ctypes.c_int64, P, P, ctypes.c_double, P]
         lib.oracle_intermediates.argtypes = [P, P, P, P, P]
-        _lib = lib
-    return _lib
+        _libs[real] = lib
+    return _libs[real]
 
 
 def _ptr(a):
@@ -83,12 +91,13 @@ def _ptr(a):
 class Oracle:
     """The oracle for one molecule and ansatz configuration."""
 
-    def __init__(self, system, cfg):
-        self.lib = _load()
+    def __init__(self, system, cfg, real="fp64"):
+        self.lib = _load(real)
+        self.real, self.dt = real, _DTYPES[real]
         self.system, self.cfg = system, cfg
-        self._Z = np.ascontiguousarray(system.Z, dtype=np.float64)
-        self._R = np.ascontiguousarray(system.R, dtype=np.float64)
-        self.spec = _Spec(len(self._Z), self._Z.ctypes.data, self._R.ctypes.data, system.n_up, system.n_down,
+        self._Z = np.ascontiguousarray(system.Z, dtype=self.dt)
+        self._R = np.ascontiguousarray(system.R, dtype=self.dt)
+        self.spec = _SPECS[real](len(self._Z), self._Z.ctypes.data, self._R.ctypes.data, system.n_up, system.n_down,
                           cfg.width, cfg.n_layers, cfg.n_det, cfg.n_rbf, cfg.rbf_cutoff,
                           int(cfg.use_jastrow), int(cfg.use_cusp), cfg.cusp_alpha)
         self.N = system.n_up + system.n_down
@@ -98,22 +107,28 @@ class Oracle:
 
     @staticmethod
     def set_threads(n):
-        _load().oracle_set_threads(int(n))
+        for real in _LIBS:
+            if real in _libs or real == "fp64":
+                _load(real).oracle_set_threads(int(n))
 
     @staticmethod
     def threads():
         return int(_load().oracle_threads())
 
+    def _fp64_only(self):
+        if self.real != "fp64":
+            raise ValueError("the FP32 build of the oracle only serves evaluate() and local_energy()")
+
     def _prep(self, theta, r):
-        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        theta = np.ascontiguousarray(theta, dtype=self.dt)
         assert theta.size == self.P, (theta.size, self.P)
-        r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, self.N, 3)
+        r = np.ascontiguousarray(r, dtype=self.dt).reshape(-1, self.N, 3)
         return theta, r
 
     def evaluate(self, theta, r):
         theta, r = self._prep(theta, r)
         B = r.shape[0]
-        la = np.empty(B)
+        la = np.empty(B, dtype=self.dt)
         sg = np.empty(B, dtype=np.int8)
         self.lib.oracle_eval(ctypes.byref(self.spec), _ptr(theta), _ptr(r), B, _ptr(la), _ptr(sg))
         return la, sg
@@ -121,9 +136,9 @@ class Oracle:
     def local_energy(self, theta, r, with_grad=False):
         theta, r = self._prep(theta, r)
         B = r.shape[0]
-        la, el, lap = np.empty(B), np.empty(B), np.empty(B)
+        la, el, lap = np.empty(B, self.dt), np.empty(B, self.dt), np.empty(B, self.dt)
         sg = np.empty(B, dtype=np.int8)
-        grad = np.empty((B, 3 * self.N)) if with_grad else None
+        grad = np.empty((B, 3 * self.N), self.dt) if with_grad else None
         self.lib.oracle_local_energy(ctypes.byref(self.spec), _ptr(theta), _ptr(r), B, _ptr(la), _ptr(sg),
                                      _ptr(el), _ptr(grad), _ptr(lap))
         out = {"logabs": la, "sign": sg, "e_loc": el, "lap": lap}
@@ -132,12 +147,14 @@ class Oracle:
         return out
 
     def potential(self, r):
+        self._fp64_only()
         r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, self.N, 3)
         V = np.empty(r.shape[0])
         self.lib.oracle_potential(ctypes.byref(self.spec), _ptr(r), r.shape[0], _ptr(V))
         return V
 
     def grad_jvp(self, theta, r, dirs):
+        self._fp64_only()
         theta, r = self._prep(theta, r)
         dirs = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, self.P)
         out = np.empty((r.shape[0], dirs.shape[0]))
@@ -146,6 +163,7 @@ class Oracle:
         return out
 
     def grad_index(self, theta, r, idx):
+        self._fp64_only()
         theta, r = self._prep(theta, r)
         idx = np.ascontiguousarray(idx, dtype=np.int64)
         out = np.empty((r.shape[0], idx.size))
@@ -155,6 +173,7 @@ class Oracle:
 
     def metropolis_step(self, theta, r, logabs, xi, u, step):
         """Returns (r_new, logabs_new, accepted) without modifying inputs."""
+        self._fp64_only()
         theta, r = self._prep(theta, r)
         r = r.copy()
         la = np.ascontiguousarray(logabs, dtype=np.float64).copy()
@@ -167,6 +186,7 @@ class Oracle:
 
     def intermediates(self, theta, r):
         """Final embeddings f[N][D] and orbital matrices A[2][K][nmax][nmax] of one walker."""
+        self._fp64_only()
         theta, r = self._prep(theta, r)
         nmax = max(self.system.n_up, self.system.n_down)
         f = np.empty((self.N, self.cfg.width))

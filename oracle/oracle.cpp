@@ -29,6 +29,10 @@
 //   * one random-walk Metropolis step (Sec. 5) on random draws passed in.
 //
 // Determinants: LU factorisation with partial pivoting on |value|.
+//
+// The base scalar is FP64.  Compiling with -DORACLE_REAL=float gives the same
+// algorithm in FP32; that build exists only to measure the rounding floor of
+// an FP32 evaluation of the method (it is never a reference).
 // Parity status: every function here is pinned by tests (closed forms,
 // invariants, finite differences, brute force); see the test-suite.
 #include <algorithm>
@@ -41,6 +45,11 @@
 #include <omp.h>
 #endif
 
+#ifndef ORACLE_REAL
+#define ORACLE_REAL double
+#endif
+typedef ORACLE_REAL real;
+
 namespace {
 
 // ---------------------------------------------------------------------------
@@ -48,10 +57,10 @@ namespace {
 // ---------------------------------------------------------------------------
 // Hyper-dual number x = v + a e1 + b e2 + ab e1e2, e1^2 = e2^2 = 0.
 struct HD {
-  double v = 0, a = 0, b = 0, ab = 0;
+  real v = 0, a = 0, b = 0, ab = 0;
   HD() = default;
-  HD(double x) : v(x) {}
-  HD(double v_, double a_, double b_, double ab_) : v(v_), a(a_), b(b_), ab(ab_) {}
+  HD(real x) : v(x) {}
+  HD(real v_, real a_, real b_, real ab_) : v(v_), a(a_), b(b_), ab(ab_) {}
 };
 inline HD operator+(const HD& x, const HD& y) { return {x.v + y.v, x.a + y.a, x.b + y.b, x.ab + y.ab}; }
 inline HD operator-(const HD& x, const HD& y) { return {x.v - y.v, x.a - y.a, x.b - y.b, x.ab - y.ab}; }
@@ -63,23 +72,23 @@ inline HD operator*(const HD& x, const HD& y) {
 inline HD& operator+=(HD& x, const HD& y) { x = x + y; return x; }
 inline HD& operator-=(HD& x, const HD& y) { x = x - y; return x; }
 // f(x) for a scalar function with value f, first derivative d1, second d2.
-inline HD chain(const HD& x, double f, double d1, double d2) {
+inline HD chain(const HD& x, real f, real d1, real d2) {
   return {f, d1 * x.a, d1 * x.b, d1 * x.ab + d2 * x.a * x.b};
 }
-inline HD inv(const HD& x) { double i = 1.0 / x.v; return chain(x, i, -i * i, 2 * i * i * i); }
+inline HD inv(const HD& x) { real i = 1.0 / x.v; return chain(x, i, -i * i, 2 * i * i * i); }
 inline HD operator/(const HD& x, const HD& y) { return x * inv(y); }
-inline HD exp(const HD& x) { double e = std::exp(x.v); return chain(x, e, e, e); }
+inline HD exp(const HD& x) { real e = std::exp(x.v); return chain(x, e, e, e); }
 inline HD log(const HD& x) { return chain(x, std::log(x.v), 1.0 / x.v, -1.0 / (x.v * x.v)); }
-inline HD sqrt(const HD& x) { double s = std::sqrt(x.v); return chain(x, s, 0.5 / s, -0.25 / (s * x.v)); }
-inline HD tanh(const HD& x) { double t = std::tanh(x.v); double d = 1 - t * t; return chain(x, t, d, -2 * t * d); }
-inline double val(const HD& x) { return x.v; }
+inline HD sqrt(const HD& x) { real s = std::sqrt(x.v); return chain(x, s, 0.5 / s, -0.25 / (s * x.v)); }
+inline HD tanh(const HD& x) { real t = std::tanh(x.v); real d = 1 - t * t; return chain(x, t, d, -2 * t * d); }
+inline real val(const HD& x) { return x.v; }
 
 // Dual number x = v + d e, e^2 = 0.
 struct Dual {
-  double v = 0, d = 0;
+  real v = 0, d = 0;
   Dual() = default;
-  Dual(double x) : v(x) {}
-  Dual(double v_, double d_) : v(v_), d(d_) {}
+  Dual(real x) : v(x) {}
+  Dual(real v_, real d_) : v(v_), d(d_) {}
 };
 inline Dual operator+(const Dual& x, const Dual& y) { return {x.v + y.v, x.d + y.d}; }
 inline Dual operator-(const Dual& x, const Dual& y) { return {x.v - y.v, x.d - y.d}; }
@@ -87,16 +96,16 @@ inline Dual operator-(const Dual& x) { return {-x.v, -x.d}; }
 inline Dual operator*(const Dual& x, const Dual& y) { return {x.v * y.v, x.v * y.d + x.d * y.v}; }
 inline Dual& operator+=(Dual& x, const Dual& y) { x = x + y; return x; }
 inline Dual& operator-=(Dual& x, const Dual& y) { x = x - y; return x; }
-inline Dual chain(const Dual& x, double f, double d1) { return {f, d1 * x.d}; }
-inline Dual inv(const Dual& x) { double i = 1.0 / x.v; return chain(x, i, -i * i); }
+inline Dual chain(const Dual& x, real f, real d1) { return {f, d1 * x.d}; }
+inline Dual inv(const Dual& x) { real i = 1.0 / x.v; return chain(x, i, -i * i); }
 inline Dual operator/(const Dual& x, const Dual& y) { return x * inv(y); }
-inline Dual exp(const Dual& x) { double e = std::exp(x.v); return chain(x, e, e); }
+inline Dual exp(const Dual& x) { real e = std::exp(x.v); return chain(x, e, e); }
 inline Dual log(const Dual& x) { return chain(x, std::log(x.v), 1.0 / x.v); }
-inline Dual sqrt(const Dual& x) { double s = std::sqrt(x.v); return chain(x, s, 0.5 / s); }
-inline Dual tanh(const Dual& x) { double t = std::tanh(x.v); return chain(x, t, 1 - t * t); }
-inline double val(const Dual& x) { return x.v; }
+inline Dual sqrt(const Dual& x) { real s = std::sqrt(x.v); return chain(x, s, 0.5 / s); }
+inline Dual tanh(const Dual& x) { real t = std::tanh(x.v); return chain(x, t, 1 - t * t); }
+inline real val(const Dual& x) { return x.v; }
 
-inline double val(double x) { return x; }
+inline real val(real x) { return x; }
 using std::exp;
 using std::log;
 using std::sqrt;
@@ -113,13 +122,13 @@ extern "C" {
 // Mirrors the Python-side ctypes structure in oracle/__init__.py.
 struct OracleSpec {
   int32_t n_nuc;
-  const double* Z;  // [n_nuc]
-  const double* R;  // [n_nuc][3], bohr
+  const real* Z;  // [n_nuc]
+  const real* R;  // [n_nuc][3], bohr
   int32_t n_up, n_dn;
   int32_t D, L, K, Q;  // width, layers, determinant pairs, Gaussian features
-  double rc;           // Gaussian feature cutoff
+  real rc;           // Gaussian feature cutoff
   int32_t use_jastrow, use_cusp;
-  double alpha;        // cusp width
+  real alpha;        // cusp width
 };
 }
 
@@ -188,8 +197,8 @@ void affine(const T* W, const T* b, const T* x, int n_out, int n_in, T* y) {
 // Gaussian expansion of a distance: e_q = exp(-(d - mu_q)^2 / (2 s^2)),
 // mu_q = q rc / (Q-1), s = rc / (Q-1) (Sec. 3.1, edge features).
 template <class T>
-void gaussian_features(const T& d, int Q, double rc, T* e) {
-  const double s = rc / (Q - 1);
+void gaussian_features(const T& d, int Q, real rc, T* e) {
+  const real s = rc / (Q - 1);
   for (int q = 0; q < Q; ++q) {
     T x = d - T(q * s);
     e[q] = exp(x * x * T(-0.5 / (s * s)));
@@ -214,10 +223,10 @@ void slogdet(std::vector<T> A, int n, int* sign, T* logabs) {
   for (int j = 0; j < n; ++j) {
     int p = j;
     for (int i = j + 1; i < n; ++i)
-      if (std::fabs(val(A[i * n + j])) > std::fabs(val(A[p * n + j]))) p = i;
+      if (std::abs(val(A[i * n + j])) > std::abs(val(A[p * n + j]))) p = i;
     if (val(A[p * n + j]) == 0.0) {
       *sign = 0;
-      *logabs = T(-std::numeric_limits<double>::infinity());
+      *logabs = T(-std::numeric_limits<real>::infinity());
       return;
     }
     if (p != j) {
@@ -246,7 +255,7 @@ struct Walker {
 // f_out [N][D] final embeddings, A_out [2][K][nmax][nmax] orbital matrices.
 template <class T>
 Walker<T> log_psi(const OracleSpec& s, const Layout& lay, const T* th, const T* r,
-                  double* f_out = nullptr, double* A_out = nullptr) {
+                  real* f_out = nullptr, real* A_out = nullptr) {
   const int N = s.n_up + s.n_dn, M = s.n_nuc, D = s.D, Q = s.Q, K = s.K;
   auto spin = [&](int i) { return i < s.n_up ? 0 : 1; };
 
@@ -303,7 +312,7 @@ Walker<T> log_psi(const OracleSpec& s, const Layout& lay, const T* th, const T* 
         edge_filter(th, y, 2, e.data(), D, Q, w.data());
         for (int a = 0; a < D; ++a) m[2 * D + a] += w[a] * th[y.Y + I * D + a];
       }
-      const double nu[3] = {1.0 / std::max(1, n_same[spin(i)] - 1), 1.0 / std::max(1, n_opp[spin(i)]),
+      const real nu[3] = {1.0 / std::max(1, n_same[spin(i)] - 1), 1.0 / std::max(1, n_opp[spin(i)]),
                             1.0 / M};
       for (int t = 0; t < 3; ++t)
         for (int a = 0; a < D; ++a) m[t * D + a] = m[t * D + a] * T(nu[t]);
@@ -354,7 +363,7 @@ Walker<T> log_psi(const OracleSpec& s, const Layout& lay, const T* th, const T* 
   Walker<T> out;
   int pmax = -1;
   for (int p = 0; p < K; ++p) {
-    const double cp = val(th[lay.c + p]);
+    const real cp = val(th[lay.c + p]);
     if (sgn_p[p] == 0 || cp == 0.0) continue;
     ld_p[p] += log(absv(th[lay.c + p]));
     if (cp < 0) sgn_p[p] = -sgn_p[p];
@@ -362,7 +371,7 @@ Walker<T> log_psi(const OracleSpec& s, const Layout& lay, const T* th, const T* 
   }
   if (pmax < 0) {
     out.sign = 0;
-    out.logabs = T(-std::numeric_limits<double>::infinity());
+    out.logabs = T(-std::numeric_limits<real>::infinity());
     return out;
   }
   T acc(0.0);
@@ -373,7 +382,7 @@ Walker<T> log_psi(const OracleSpec& s, const Layout& lay, const T* th, const T* 
   }
   if (val(acc) == 0.0) {
     out.sign = 0;
-    out.logabs = T(-std::numeric_limits<double>::infinity());
+    out.logabs = T(-std::numeric_limits<real>::infinity());
     return out;
   }
   out.sign = val(acc) > 0 ? 1 : -1;
@@ -394,7 +403,7 @@ Walker<T> log_psi(const OracleSpec& s, const Layout& lay, const T* th, const T* 
     T g(0.0);
     for (int i = 0; i < N; ++i)
       for (int j = i + 1; j < N; ++j) {
-        const double c = spin(i) == spin(j) ? 0.25 : 0.5;
+        const real c = spin(i) == spin(j) ? 0.25 : 0.5;
         g -= T(s.alpha * c) / (T(1.0) + T(s.alpha) * dee[i * N + j]);
       }
     logabs += g;
@@ -404,14 +413,14 @@ Walker<T> log_psi(const OracleSpec& s, const Layout& lay, const T* th, const T* 
 }
 
 // Coulomb potential of Eq. (1) plus the constant nuclear repulsion.
-double potential(const OracleSpec& s, const double* r) {
+real potential(const OracleSpec& s, const real* r) {
   const int N = s.n_up + s.n_dn, M = s.n_nuc;
-  auto dist = [](const double* a, const double* b) {
-    double acc = 0;
+  auto dist = [](const real* a, const real* b) {
+    real acc = 0;
     for (int x = 0; x < 3; ++x) acc += (a[x] - b[x]) * (a[x] - b[x]);
     return std::sqrt(acc);
   };
-  double V = 0;
+  real V = 0;
   for (int i = 0; i < N; ++i)
     for (int j = i + 1; j < N; ++j) V += 1.0 / dist(r + 3 * i, r + 3 * j);
   for (int i = 0; i < N; ++i)
@@ -422,7 +431,7 @@ double potential(const OracleSpec& s, const double* r) {
 }
 
 template <class T>
-std::vector<T> lift(const double* x, int64_t n) {
+std::vector<T> lift(const real* x, int64_t n) {
   std::vector<T> y(n);
   for (int64_t k = 0; k < n; ++k) y[k] = T(x[k]);
   return y;
@@ -450,13 +459,13 @@ int oracle_threads() {
 }
 
 // log|psi|, sign psi for B walkers r[B][N][3].
-int oracle_eval(const OracleSpec* s, const double* theta, const double* r, int64_t B, double* logabs,
+int oracle_eval(const OracleSpec* s, const real* theta, const real* r, int64_t B, real* logabs,
                 int8_t* sign) {
   const Layout lay(*s);
   const int N3 = 3 * (s->n_up + s->n_dn);
 #pragma omp parallel for schedule(dynamic) num_threads(oracle_threads())
   for (int64_t b = 0; b < B; ++b) {
-    Walker<double> w = log_psi<double>(*s, lay, theta, r + b * N3);
+    Walker<real> w = log_psi<real>(*s, lay, theta, r + b * N3);
     logabs[b] = w.logabs;
     sign[b] = (int8_t)w.sign;
   }
@@ -465,18 +474,18 @@ int oracle_eval(const OracleSpec* s, const double* theta, const double* r, int64
 
 // Local energy E_loc = -1/2 sum_x (d_x^2 log|psi| + (d_x log|psi|)^2) + V (Eq. 31).
 // Optional grad[B][3N] and lap[B] (d_x log|psi| and sum_x d_x^2 log|psi|).
-int oracle_local_energy(const OracleSpec* s, const double* theta, const double* r, int64_t B,
-                        double* logabs, int8_t* sign, double* e_loc, double* grad, double* lap) {
+int oracle_local_energy(const OracleSpec* s, const real* theta, const real* r, int64_t B,
+                        real* logabs, int8_t* sign, real* e_loc, real* grad, real* lap) {
   const Layout lay(*s);
   const int N3 = 3 * (s->n_up + s->n_dn);
   const std::vector<HD> thh = lift<HD>(theta, lay.total);
 #pragma omp parallel for schedule(dynamic) num_threads(oracle_threads())
   for (int64_t b = 0; b < B; ++b) {
-    const double* rb = r + b * N3;
-    Walker<double> w0 = log_psi<double>(*s, lay, theta, rb);
+    const real* rb = r + b * N3;
+    Walker<real> w0 = log_psi<real>(*s, lay, theta, rb);
     logabs[b] = w0.logabs;
     sign[b] = (int8_t)w0.sign;
-    double sum_d2 = 0, sum_g2 = 0;
+    real sum_d2 = 0, sum_g2 = 0;
     std::vector<HD> rh = lift<HD>(rb, N3);
     for (int x = 0; x < N3; ++x) {
       rh[x].a = rh[x].b = 1.0;
@@ -487,14 +496,14 @@ int oracle_local_energy(const OracleSpec* s, const double* theta, const double* 
       sum_g2 += w.logabs.a * w.logabs.a;
     }
     if (lap) lap[b] = sum_d2;
-    e_loc[b] = (w0.sign == 0 ? std::numeric_limits<double>::quiet_NaN() : -0.5 * (sum_d2 + sum_g2)) +
+    e_loc[b] = (w0.sign == 0 ? std::numeric_limits<real>::quiet_NaN() : -0.5 * (sum_d2 + sum_g2)) +
                potential(*s, rb);
   }
   return 0;
 }
 
 // Coulomb potential per walker.
-int oracle_potential(const OracleSpec* s, const double* r, int64_t B, double* V) {
+int oracle_potential(const OracleSpec* s, const real* r, int64_t B, real* V) {
   const int N3 = 3 * (s->n_up + s->n_dn);
   for (int64_t b = 0; b < B; ++b) V[b] = potential(*s, r + b * N3);
   return 0;
@@ -502,8 +511,8 @@ int oracle_potential(const OracleSpec* s, const double* r, int64_t B, double* V)
 
 // Directional derivatives of log|psi| in parameter space:
 // out[b][k] = sum_p dirs[k][p] d log|psi_b| / d theta_p, k < n_dir.
-int oracle_grad_jvp(const OracleSpec* s, const double* theta, const double* r, int64_t B,
-                    const double* dirs, int32_t n_dir, double* out) {
+int oracle_grad_jvp(const OracleSpec* s, const real* theta, const real* r, int64_t B,
+                    const real* dirs, int32_t n_dir, real* out) {
   const Layout lay(*s);
   const int N3 = 3 * (s->n_up + s->n_dn);
   const int64_t P = lay.total;
@@ -519,8 +528,8 @@ int oracle_grad_jvp(const OracleSpec* s, const double* theta, const double* r, i
 }
 
 // Partial derivatives d log|psi_b| / d theta_idx[k]: out[b][k].
-int oracle_grad_index(const OracleSpec* s, const double* theta, const double* r, int64_t B,
-                      const int64_t* idx, int32_t n_idx, double* out) {
+int oracle_grad_index(const OracleSpec* s, const real* theta, const real* r, int64_t B,
+                      const int64_t* idx, int32_t n_idx, real* out) {
   const Layout lay(*s);
   const int N3 = 3 * (s->n_up + s->n_dn);
   const int64_t P = lay.total;
@@ -538,15 +547,15 @@ int oracle_grad_index(const OracleSpec* s, const double* theta, const double* r,
 // One random-walk Metropolis step (Sec. 5) on given draws:
 // r' = r + step * xi;  accept iff log u < 2 (log|psi(r')| - log|psi(r)|), strict,
 // and psi(r') != 0.  r[B][N][3] and logabs[B] are updated in place.
-int oracle_metropolis_step(const OracleSpec* s, const double* theta, double* r, double* logabs, int64_t B,
-                           const double* xi, const double* u, double step, int8_t* accepted) {
+int oracle_metropolis_step(const OracleSpec* s, const real* theta, real* r, real* logabs, int64_t B,
+                           const real* xi, const real* u, real step, int8_t* accepted) {
   const Layout lay(*s);
   const int N3 = 3 * (s->n_up + s->n_dn);
 #pragma omp parallel for schedule(dynamic) num_threads(oracle_threads())
   for (int64_t b = 0; b < B; ++b) {
-    std::vector<double> rp(N3);
+    std::vector<real> rp(N3);
     for (int x = 0; x < N3; ++x) rp[x] = r[b * N3 + x] + step * xi[b * N3 + x];
-    Walker<double> w = log_psi<double>(*s, lay, theta, rp.data());
+    Walker<real> w = log_psi<real>(*s, lay, theta, rp.data());
     const bool acc = w.sign != 0 && std::log(u[b]) < 2.0 * (w.logabs - logabs[b]);
     if (acc) {
       for (int x = 0; x < N3; ++x) r[b * N3 + x] = rp[x];
@@ -559,10 +568,10 @@ int oracle_metropolis_step(const OracleSpec* s, const double* theta, double* r, 
 
 // Debug views of one walker: final embeddings f[N][D] and orbital matrices
 // A[2][K][nmax][nmax] (rows = electrons of the spin channel, cols = orbitals).
-int oracle_intermediates(const OracleSpec* s, const double* theta, const double* r, double* f_out,
-                         double* A_out) {
+int oracle_intermediates(const OracleSpec* s, const real* theta, const real* r, real* f_out,
+                         real* A_out) {
   const Layout lay(*s);
-  log_psi<double>(*s, lay, theta, r, f_out, A_out);
+  log_psi<real>(*s, lay, theta, r, f_out, A_out);
   return 0;
 }
 

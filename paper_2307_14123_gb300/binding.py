@@ -1,0 +1,299 @@
+"""Thin ctypes binding of libdqmc (include/dqmc.h).
+
+Argument marshalling only: tensors are checked for device, dtype and
+contiguity, their device pointers and the current CUDA stream are handed to
+the C ABI, and every step of the computation runs in the library's kernels.
+There is no CPU fallback: without the compiled library or a CUDA device every
+call raises.
+
+PyTorch provides device memory (outputs and the cached workspace) and
+streams.  Host (CPU) tensors are accepted by the methods of :class:`Ansatz`
+for an end-to-end call: they are copied to the device from pinned memory,
+the library runs, and results are copied back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdqmc.so")
+
+DQ_FP64, DQ_FP32, DQ_BF16_MIXED = 0, 1, 2
+OP_EVAL, OP_LOCAL_ENERGY, OP_MCMC, OP_GRAD, OP_LOSS_WEIGHTS = 0, 1, 2, 3, 4
+FLAG_SINGULAR, FLAG_NONFINITE = 0x1, 0x2
+PRECISIONS = {"fp64": DQ_FP64, "fp32": DQ_FP32, "bf16": DQ_BF16_MIXED}
+
+# Every symbol declared in include/dqmc.h.
+EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_max_chunk", "dq_workspace_size",
+           "ansatz_eval", "local_energy", "mcmc_step", "grad_logpsi", "vmc_loss_weights", "dq_last_device_status",
+           "dq_status_string", "dq_profile_enable", "dq_profile_reset", "dq_profile_read", "dq_profile_kind_name",
+           "dq_profile_kind_count"]
+
+
+class DQError(RuntimeError):
+    pass
+
+
+class _System(ctypes.Structure):
+    _fields_ = [("n_nuc", ctypes.c_int32), ("Z", ctypes.c_void_p), ("R", ctypes.c_void_p),
+                ("n_up", ctypes.c_int32), ("n_down", ctypes.c_int32)]
+
+
+class _Cfg(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("n_layers", ctypes.c_int32), ("n_det", ctypes.c_int32),
+                ("n_rbf", ctypes.c_int32), ("rbf_cutoff", ctypes.c_double), ("use_jastrow", ctypes.c_int32),
+                ("use_cusp", ctypes.c_int32), ("cusp_alpha", ctypes.c_double)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path=None):
+    """Loads libdqmc.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or LIB_PATH
+        if not os.path.exists(path):
+            raise DQError(f"libdqmc.so not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        P, i32, i64, u64, f64, sz = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                      ctypes.c_double, ctypes.c_size_t)
+        lib.dq_create.argtypes = [P, P, i32, P]
+        lib.dq_destroy.argtypes = [P]
+        lib.dq_param_count.argtypes = [P, P]
+        lib.dq_max_chunk.argtypes = [P, P]
+        lib.dq_set_max_chunk.argtypes = [P, i64]
+        lib.dq_workspace_size.argtypes = [P, i64, i32, P]
+        lib.ansatz_eval.argtypes = [P, P, P, i64, P, P, P, sz, P]
+        lib.local_energy.argtypes = [P, P, P, i64, P, P, P, P, P, sz, P]
+        lib.mcmc_step.argtypes = [P, P, P, P, i64, i32, f64, u64, u64, P, P, sz, P]
+        lib.grad_logpsi.argtypes = [P, P, P, i64, P, i32, P, P, sz, P]
+        lib.vmc_loss_weights.argtypes = [P, P, i64, f64, P, P, P, sz, P]
+        lib.dq_last_device_status.argtypes = [P, P, P]
+        lib.dq_status_string.argtypes = [ctypes.c_int]
+        lib.dq_profile_enable.argtypes = [P, i32]
+        lib.dq_profile_reset.argtypes = [P]
+        lib.dq_profile_read.argtypes = [P, i32, P, P]
+        lib.dq_profile_kind_name.argtypes = [i32]
+        lib.dq_profile_kind_count.argtypes = []
+        for name in EXPORTS:
+            getattr(lib, name).restype = ctypes.c_int
+        lib.dq_status_string.restype = ctypes.c_char_p
+        lib.dq_profile_kind_name.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(st):
+    if st != 0:
+        raise DQError(f"libdqmc: {_lib.dq_status_string(st).decode()} (status {st})")
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Ansatz:
+    """A handle of the library: one molecule, one ansatz, one precision, one device.
+
+    ``system`` needs ``Z``, ``R`` (bohr), ``n_up``, ``n_down``; ``cfg`` needs
+    ``width, n_layers, n_det, n_rbf, rbf_cutoff, use_jastrow, use_cusp,
+    cusp_alpha`` (see :mod:`paper_2307_14123_gb300.fixtures`).
+    """
+
+    def __init__(self, system, cfg, precision="fp32", device=None):
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise DQError("no CUDA device: the library has no CPU path")
+        device = torch.device("cuda") if device is None else torch.device(device)
+        if device.type != "cuda":
+            raise DQError("the library runs on CUDA devices only")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device.index is None else device.index)
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.N = int(system.n_up + system.n_down)
+        self._Z = (ctypes.c_double * len(system.Z))(*[float(z) for z in system.Z])
+        flatR = [float(x) for x in torch.as_tensor(system.R, dtype=torch.float64).reshape(-1).tolist()]
+        self._R = (ctypes.c_double * len(flatR))(*flatR)
+        sysc = _System(len(system.Z), ctypes.cast(self._Z, ctypes.c_void_p), ctypes.cast(self._R, ctypes.c_void_p),
+                       int(system.n_up), int(system.n_down))
+        cfgc = _Cfg(int(cfg.width), int(cfg.n_layers), int(cfg.n_det), int(cfg.n_rbf), float(cfg.rbf_cutoff),
+                    int(cfg.use_jastrow), int(cfg.use_cusp), float(cfg.cusp_alpha))
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.dq_create(ctypes.byref(sysc), ctypes.byref(cfgc), PRECISIONS[precision], ctypes.byref(h)))
+        self.h = h
+        P = ctypes.c_int64()
+        _check(self.lib.dq_param_count(self.h, ctypes.byref(P)))
+        self.P = P.value
+        self._ws = None
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.lib is not None:
+            try:
+                self.lib.dq_destroy(self.h)
+            except Exception:
+                pass
+            self.h = None
+
+    # -- plumbing -----------------------------------------------------------
+    def _stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def set_max_chunk(self, chunk):
+        _check(self.lib.dq_set_max_chunk(self.h, int(chunk)))
+
+    def max_chunk(self):
+        c = ctypes.c_int64()
+        _check(self.lib.dq_max_chunk(self.h, ctypes.byref(c)))
+        return c.value
+
+    def workspace_size(self, B, op):
+        n = ctypes.c_size_t()
+        _check(self.lib.dq_workspace_size(self.h, int(B), int(op), ctypes.byref(n)))
+        return n.value
+
+    def workspace(self, B, op):
+        n = max(self.workspace_size(B, op), 256)
+        if self._ws is None or self._ws.numel() < n:
+            self._ws = None
+            self._ws = torch.empty(n, dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def _dev(self, t, dtype=None, shape=None):
+        dtype = dtype or self.dtype
+        if not isinstance(t, torch.Tensor):
+            t = torch.as_tensor(t)
+        if t.device != self.device:
+            if t.device.type == "cpu" and not t.is_pinned():
+                t = t.to(dtype).contiguous().pin_memory()
+            t = t.to(self.device, dtype=dtype, non_blocking=True)
+        if t.dtype != dtype:
+            raise DQError(f"expected {dtype}, got {t.dtype}")
+        t = t.contiguous()
+        if shape is not None and tuple(t.shape) != tuple(shape):
+            t = t.reshape(shape)
+        return t
+
+    # -- the four calls of the hot path ---------------------------------------
+    def ansatz_eval(self, params, r):
+        host = isinstance(r, torch.Tensor) and r.device.type == "cpu"
+        params = self._dev(params, shape=(self.P,))
+        r = self._dev(r)
+        B = r.numel() // (3 * self.N)
+        logabs = torch.empty(B, dtype=self.dtype, device=self.device)
+        sign = torch.empty(B, dtype=torch.int8, device=self.device)
+        ws = self.workspace(B, OP_EVAL)
+        _check(self.lib.ansatz_eval(self.h, _ptr(params), _ptr(r), B, _ptr(logabs), _ptr(sign), _ptr(ws),
+                                    ws.numel(), self._stream()))
+        if host:
+            return logabs.cpu(), sign.cpu()
+        return logabs, sign
+
+    def local_energy(self, params, r, sums=False):
+        """Returns (logabs, sign, e_loc) and, with ``sums``, the FP64 [sum E, sum E^2]."""
+        host = isinstance(r, torch.Tensor) and r.device.type == "cpu"
+        params = self._dev(params, shape=(self.P,))
+        r = self._dev(r)
+        B = r.numel() // (3 * self.N)
+        logabs = torch.empty(B, dtype=self.dtype, device=self.device)
+        sign = torch.empty(B, dtype=torch.int8, device=self.device)
+        e_loc = torch.empty(B, dtype=self.dtype, device=self.device)
+        e2 = torch.empty(2, dtype=torch.float64, device=self.device) if sums else None
+        ws = self.workspace(B, OP_LOCAL_ENERGY)
+        _check(self.lib.local_energy(self.h, _ptr(params), _ptr(r), B, _ptr(logabs), _ptr(sign), _ptr(e_loc),
+                                     _ptr(e2), _ptr(ws), ws.numel(), self._stream()))
+        out = (logabs, sign, e_loc) + ((e2,) if sums else ())
+        if host:
+            out = tuple(t.cpu() for t in out)
+        return out
+
+    def mcmc_step(self, params, r, logabs, n_steps=1, step_size=0.2, seed=0, step_counter=0):
+        """In-place Metropolis update of device tensors r and logabs; returns the accepted count (device int64)."""
+        params = self._dev(params, shape=(self.P,))
+        for t in (r, logabs):
+            if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous():
+                raise DQError("mcmc_step updates r and logabs in place: pass contiguous device tensors")
+        B = r.numel() // (3 * self.N)
+        n_acc = torch.empty(1, dtype=torch.int64, device=self.device)
+        ws = self.workspace(B, OP_MCMC)
+        _check(self.lib.mcmc_step(self.h, _ptr(params), _ptr(r), _ptr(logabs), B, int(n_steps), float(step_size),
+                                  int(seed) & 0xFFFFFFFFFFFFFFFF, int(step_counter), _ptr(n_acc), _ptr(ws),
+                                  ws.numel(), self._stream()))
+        return n_acc
+
+    def grad_logpsi(self, params, r, weights=None, mode=0):
+        """mode 0: sum_b w_b d log|psi_b|/d theta -> [P]; mode 1: per walker -> [B][P]."""
+        params = self._dev(params, shape=(self.P,))
+        r = self._dev(r)
+        B = r.numel() // (3 * self.N)
+        w = self._dev(weights, shape=(B,)) if weights is not None else None
+        out = torch.empty((self.P,) if mode == 0 else (B, self.P), dtype=self.dtype, device=self.device)
+        ws = self.workspace(B, OP_GRAD)
+        _check(self.lib.grad_logpsi(self.h, _ptr(params), _ptr(r), B, _ptr(w), int(mode), _ptr(out), _ptr(ws),
+                                    ws.numel(), self._stream()))
+        return out
+
+    def vmc_loss_weights(self, e_loc, clip_k=5.0):
+        """Median/MAD-clipped gradient weights; returns (weights, stats[mu, half-width, mean E^, mean E])."""
+        e_loc = self._dev(e_loc)
+        B = e_loc.numel()
+        w = torch.empty(B, dtype=self.dtype, device=self.device)
+        stats = torch.empty(4, dtype=torch.float64, device=self.device)
+        ws = self.workspace(B, OP_LOSS_WEIGHTS)
+        _check(self.lib.vmc_loss_weights(self.h, _ptr(e_loc), B, float(clip_k), _ptr(w), _ptr(stats), _ptr(ws),
+                                         ws.numel(), self._stream()))
+        return w, stats
+
+    # -- measurement ---------------------------------------------------------
+    def profile(self, on=True):
+        """Enable or disable per-launch CUDA-event timing inside the library."""
+        _check(self.lib.dq_profile_enable(self.h, 1 if on else 0))
+
+    def profile_reset(self):
+        _check(self.lib.dq_profile_reset(self.h))
+
+    def profile_read(self):
+        """{kernel kind: (total ms, launches)} since the last reset (kinds with launches only)."""
+        out = {}
+        for k in range(self.lib.dq_profile_kind_count()):
+            ms, n = ctypes.c_double(), ctypes.c_int64()
+            st = self.lib.dq_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(n))
+            if st not in (0, 5):
+                _check(st)
+            if n.value:
+                out[self.lib.dq_profile_kind_name(k).decode()] = (ms.value, n.value)
+        return out
+
+    def device_status(self):
+        f = ctypes.c_uint32()
+        _check(self.lib.dq_last_device_status(self.h, self._stream(), ctypes.byref(f)))
+        return f.value
+
+
+# C-ABI names as free functions over a handle.
+def ansatz_eval(h: Ansatz, params, r):
+    return h.ansatz_eval(params, r)
+
+
+def local_energy(h: Ansatz, params, r, sums=False):
+    return h.local_energy(params, r, sums)
+
+
+def mcmc_step(h: Ansatz, params, r, logabs, n_steps=1, step_size=0.2, seed=0, step_counter=0):
+    return h.mcmc_step(params, r, logabs, n_steps, step_size, seed, step_counter)
+
+
+def grad_logpsi(h: Ansatz, params, r, weights=None, mode=0):
+    return h.grad_logpsi(params, r, weights, mode)
+
+
+def vmc_loss_weights(h: Ansatz, e_loc, clip_k=5.0):
+    return h.vmc_loss_weights(e_loc, clip_k)

@@ -1,0 +1,171 @@
+// Internal declarations shared by the CUDA translation units of libdqmc.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/dqmc.h"
+
+namespace dq {
+
+constexpr int kMaxElec = 64;   // n_up + n_down
+constexpr int kMaxSpin = 32;   // electrons per spin channel (one warp per matrix)
+constexpr int kMaxNuc = 64;
+
+// Element offsets of the blocks of the flat parameter vector (layout in dqmc.h).
+struct ParamOffsets {
+  int64_t E_spin;
+  struct Layer {
+    int64_t W_h, W1[3], b1[3], W2[3], b2[3], Y, W_g, b_g;
+  } layer[16];
+  int64_t W_o[2], b_o[2], omega[2], zeta[2], c, W_J1, b_J1, w_J2, total;
+};
+constexpr int kMaxLayers = 16;
+
+ParamOffsets make_offsets(int D, int L, int K, int Q, int M, int n_up, int n_dn);
+
+// Edge bookkeeping.  Electron-electron pairs (i < j) are ordered by type:
+// up-up pairs, down-down pairs (together: same spin), then up-down pairs
+// (opposite spin); electron-nucleus edges (i, I) follow at E_ee + i*M + I.
+struct Edges {
+  int n_par, n_anti, n_ee, n_en, n_all;
+};
+
+}  // namespace dq
+
+namespace dq {
+// Kernel kinds for the optional per-launch timing (dq_profile_*).  The
+// value-only forward (ansatz_eval, Metropolis) uses kind + kValueOffset.
+enum ProfKind {
+  PK_GEOMETRY = 0, PK_EDGE_HIDDEN, PK_GEMM_EDGE, PK_MESSAGES, PK_GEMM_NODE, PK_GEMM_UPDATE, PK_UPDATE,
+  PK_GEMM_ORBITAL, PK_ORBITAL_DET, PK_JASTROW_SUM, PK_GEMM_JASTROW, PK_COMBINE, PK_LAYER0, PK_FWD_KINDS,
+  PK_ESUM = 2 * PK_FWD_KINDS, PK_PROPOSE, PK_ACCEPT, PK_LOSS_WEIGHTS, PK_BWD_COMBINE, PK_BWD_DET, PK_BWD_GEMM,
+  PK_BWD_UPDATE, PK_BWD_MESSAGES, PK_BWD_EDGE, PK_BWD_REDUCE, PK_COUNT
+};
+constexpr int kValueOffset = PK_FWD_KINDS;
+const char* prof_kind_name(int k);
+
+struct Profiler {
+  bool on = false;
+  bool overflow = false;
+  std::vector<cudaEvent_t> pool;
+  size_t next = 0;
+  std::vector<int> kinds;  // kind of record r; events 2r, 2r+1 of the pool
+  void begin(int kind, cudaStream_t s) {
+    if (!on) return;
+    if (next + 2 > pool.size()) {
+      overflow = true;
+      return;
+    }
+    kinds.push_back(kind);
+    cudaEventRecord(pool[next], s);
+    next += 1;
+  }
+  void end(cudaStream_t s) {
+    if (!on || overflow) return;
+    cudaEventRecord(pool[next], s);
+    next += 1;
+  }
+};
+}  // namespace dq
+
+struct dq_handle_s {
+  int device = 0;
+  int precision = 0;
+  int n_up = 0, n_dn = 0, N = 0, M = 0;
+  int D = 0, L = 0, K = 0, Q = 0;
+  double rc = 10.0, alpha = 1.0;
+  int use_jastrow = 1, use_cusp = 1;
+  double Vnn = 0;
+  dq::ParamOffsets off{};
+  dq::Edges edges{};
+  int64_t max_chunk = 4096;
+  // device tables
+  double* d_R = nullptr;   // [M][3]
+  float* d_Rf = nullptr;   // [M][3]
+  double* d_Z = nullptr;   // [M]
+  int* d_pair_of = nullptr;  // [N][N] pair index of (i, j), -1 on the diagonal
+  int* d_pair_ij = nullptr;  // [n_ee][2] (i, j) with i < j
+  unsigned int* d_status = nullptr;
+  dq::Profiler* prof = nullptr;
+};
+
+namespace dq {
+
+// Row map of a row-major matrix stored in segments:
+// element offset of row r = (r / rows_per_seg) * seg_stride + (r % rows_per_seg) * ld.
+struct RowMap {
+  int64_t rows_per_seg;
+  int64_t seg_stride;
+  int64_t ld;
+};
+
+// Y[r][n] (+)= sum_k X[r][k] W[n][k] + (r % bias_period == 0 ? bias[n] : 0).
+// W is [n_out][K] row-major.  K % 8 == 0; X and Y rows 16-byte aligned.
+template <class T>
+cudaError_t gemm_nt(const T* X, RowMap mx, const T* W, const T* bias, int bias_period, T* Y, RowMap my,
+                    int64_t rows, int n_out, int K, bool accumulate, cudaStream_t s);
+
+// ---- forward kernels (forward.cu) ------------------------------------------
+// Sizes of one chunk of Bc walkers; C = channels (1 value-only, 3N+2 with jets).
+struct FwdDims {
+  int64_t Bc;
+  int N, n_up, n_dn, M, D, K, Q, C;
+};
+
+template <class T>
+struct FwdBuffers {
+  T* geo;    // [Bc][E][4]          distance and unit vector of every edge
+  T* rbf;    // [Bc][E][3][Q]       Gaussian features and d/dd, d2/dd2
+  T* eh;     // [Bc][E][3][D]       edge hidden layer jets (value, d/dd, d2/dd2)
+  T* ew;     // [Bc][E][3][D]       edge filter jets
+  T* F;      // [Bc][N][C][D]       embeddings with jets
+  T* Z;      // [Bc][N][C][D]       W_h f, then the update pre-activation
+  T* msg;    // [Bc][N][C][3D]      messages [par | anti | nuc]
+  T* phi;    // [Bc][N][C][K nmax]  orbital head output
+  double* det;  // [Bc][2][K][3N+3] sign, log|det|, grad, laplacian
+  T* js;     // [Bc][C][D]          sum_i f_i
+  T* jh;     // [Bc][C][D]          W_J1 (sum_i f_i) + b_J1
+  T* z0;     // [2][D]              W_h^0 E_spin
+};
+
+template <class T>
+cudaError_t launch_geometry(const dq_handle_s& h, const FwdDims& d, const T* r, FwdBuffers<T> b, cudaStream_t s);
+template <class T>
+cudaError_t launch_edge_hidden(const dq_handle_s& h, const FwdDims& d, const T* params, int layer,
+                               FwdBuffers<T> b, cudaStream_t s);
+template <class T>
+cudaError_t launch_layer0_node(const dq_handle_s& h, const FwdDims& d, const T* params, FwdBuffers<T> b,
+                               cudaStream_t s);
+template <class T>
+cudaError_t launch_messages(const dq_handle_s& h, const FwdDims& d, const T* params, int layer, bool z_const,
+                            FwdBuffers<T> b, cudaStream_t s);
+template <class T>
+cudaError_t launch_update(const dq_handle_s& h, const FwdDims& d, const T* params, bool from_spin,
+                          FwdBuffers<T> b, cudaStream_t s);
+template <class T>
+cudaError_t launch_orbital_det(const dq_handle_s& h, const FwdDims& d, const T* params, FwdBuffers<T> b,
+                               cudaStream_t s);
+template <class T>
+cudaError_t launch_jastrow_sum(const dq_handle_s& h, const FwdDims& d, FwdBuffers<T> b, cudaStream_t s);
+template <class T>
+cudaError_t launch_combine(const dq_handle_s& h, const FwdDims& d, const T* params, FwdBuffers<T> b,
+                           T* logabs, int8_t* sign, T* e_loc, cudaStream_t s);
+
+// ---- sampler, reductions, loss weights (mcmc.cu) ---------------------------
+template <class T>
+cudaError_t launch_propose(const dq_handle_s& h, int64_t B, const T* r, T* r_prop, double step, uint64_t seed,
+                           uint64_t t, cudaStream_t s);
+template <class T>
+cudaError_t launch_accept(const dq_handle_s& h, int64_t B, T* r, T* logabs, const T* r_prop,
+                          const T* logabs_prop, const int8_t* sign_prop, uint64_t seed, uint64_t t,
+                          unsigned long long* n_acc, cudaStream_t s);
+template <class T>
+cudaError_t launch_esum(const T* e, int64_t B, double* out2, unsigned int* status, cudaStream_t s);
+template <class T>
+cudaError_t launch_loss_weights(const T* e, int64_t B, double k, T* w, double* stats, double* scratch,
+                                cudaStream_t s);
+
+}  // namespace dq

@@ -1,0 +1,221 @@
+// Random-walk Metropolis sampler (Sec. 5), FP64 walker-sum of local energies
+// and the clipped-energy weights of the gradient estimator (Sec. 4.4, Eq. 30).
+//
+// Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), written
+// from its published definition: ten rounds of two 32x32->64-bit products with
+// multipliers 0xD2511F53 and 0xCD9E8D57, key schedule bumped by the Weyl
+// constants 0x9E3779B9 and 0xBB67AE85.  Counter [walker, t_lo, (tag << 24) |
+// block, t_hi], key [seed_lo, seed_hi]; uniforms (x + 0.5) 2^-32; normals by
+// Box-Muller in FP64 from the word pairs (x0, x1) and (x2, x3).
+#include <math.h>
+
+#include "common.cuh"
+
+namespace dq {
+namespace {
+
+constexpr uint32_t kTagPropose = 1, kTagAccept = 2;
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k.x += 0x9E3779B9u;
+      k.y += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ double unit_uniform(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386963e-10; }
+
+template <class T>
+__global__ void propose_kernel(const T* __restrict__ r, T* __restrict__ r_prop, int64_t B, int N3, double step,
+                               uint64_t seed, uint64_t t) {
+  const int nblk = (N3 + 3) / 4;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= B * nblk) return;
+  const int64_t b = gid / nblk;
+  const int blk = (int)(gid % nblk);
+  const uint4 ctr = make_uint4((uint32_t)b, (uint32_t)t, (kTagPropose << 24) | (uint32_t)blk, (uint32_t)(t >> 32));
+  const uint4 x = philox4x32_10(ctr, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const double ra = sqrt(-2.0 * log(unit_uniform(x.x))), ta = 2.0 * M_PI * unit_uniform(x.y);
+  const double rb = sqrt(-2.0 * log(unit_uniform(x.z))), tb = 2.0 * M_PI * unit_uniform(x.w);
+  double z[4];
+  sincos(ta, &z[1], &z[0]);
+  sincos(tb, &z[3], &z[2]);
+  z[0] *= ra;
+  z[1] *= ra;
+  z[2] *= rb;
+  z[3] *= rb;
+  for (int m = 0; m < 4; ++m) {
+    const int q = 4 * blk + m;
+    if (q < N3) r_prop[b * N3 + q] = r[b * N3 + q] + (T)(step * z[m]);
+  }
+}
+
+template <class T>
+__global__ void accept_kernel(T* __restrict__ r, T* __restrict__ logabs, const T* __restrict__ r_prop,
+                              const T* __restrict__ la_prop, const int8_t* __restrict__ sign_prop, int64_t B, int N3,
+                              uint64_t seed, uint64_t t, unsigned long long* __restrict__ n_acc) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool acc = false;
+  if (b < B) {
+    const uint4 ctr = make_uint4((uint32_t)b, (uint32_t)t, kTagAccept << 24, (uint32_t)(t >> 32));
+    const uint4 x = philox4x32_10(ctr, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const double lu = log(unit_uniform(x.x));
+    acc = sign_prop[b] != 0 && lu < 2.0 * ((double)la_prop[b] - (double)logabs[b]);
+    if (acc) {
+      for (int q = 0; q < N3; ++q) r[b * N3 + q] = r_prop[b * N3 + q];
+      logabs[b] = la_prop[b];
+    }
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, acc);
+  if ((threadIdx.x % 32) == 0 && m && n_acc) atomicAdd(n_acc, (unsigned long long)__popc(m));
+}
+
+// Deterministic FP64 sums of the finite local energies: one CTA, fixed order.
+constexpr int kRedThreads = 1024;
+
+template <class T>
+__global__ void __launch_bounds__(kRedThreads)
+    esum_kernel(const T* __restrict__ e, int64_t B, double* __restrict__ out2, unsigned int* status) {
+  __shared__ double s1[kRedThreads], s2[kRedThreads];
+  double a = 0, q = 0;
+  bool bad = false;
+  for (int64_t i = threadIdx.x; i < B; i += kRedThreads) {
+    const double v = (double)e[i];
+    if (isfinite(v)) {
+      a += v;
+      q += v * v;
+    } else {
+      bad = true;
+    }
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = q;
+  if (bad) atomicOr(status, (unsigned)DQ_FLAG_NONFINITE);
+  __syncthreads();
+  for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out2[0] = s1[0];
+    out2[1] = s2[0];
+  }
+}
+
+__device__ double block_sum_det(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = kRedThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Median / mean-absolute-deviation clipping and gradient weights (Sec. 4.4).
+// One CTA: bitonic sort of a padded FP64 copy in global scratch, then
+// block reductions in a fixed order.
+template <class T>
+__global__ void __launch_bounds__(kRedThreads)
+    loss_weights_kernel(const T* __restrict__ e, int64_t B, int64_t Bp, double k, T* __restrict__ w,
+                        double* __restrict__ stats, double* __restrict__ srt) {
+  __shared__ double sh[kRedThreads];
+  for (int64_t i = threadIdx.x; i < Bp; i += kRedThreads) srt[i] = i < B ? (double)e[i] : INFINITY;
+  __syncthreads();
+  for (int64_t size = 2; size <= Bp; size <<= 1) {
+    for (int64_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int64_t i = threadIdx.x; i < Bp; i += kRedThreads) {
+        const int64_t j = i ^ stride;
+        if (j > i) {
+          const bool up = (i & size) == 0;
+          const double a = srt[i], c = srt[j];
+          if ((a > c) == up) {
+            srt[i] = c;
+            srt[j] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const double med = (B % 2) ? srt[B / 2] : 0.5 * (srt[B / 2 - 1] + srt[B / 2]);
+  double part = 0, raw = 0;
+  for (int64_t i = threadIdx.x; i < B; i += kRedThreads) {
+    const double v = (double)e[i];
+    part += fabs(v - med);
+    raw += v;
+  }
+  const double mad = block_sum_det(part, sh) / (double)B;
+  const double mean_raw = block_sum_det(raw, sh) / (double)B;
+  const double lo = med - k * mad, hi = med + k * mad;
+  double cs = 0;
+  for (int64_t i = threadIdx.x; i < B; i += kRedThreads) cs += fmin(fmax((double)e[i], lo), hi);
+  const double mean_c = block_sum_det(cs, sh) / (double)B;
+  for (int64_t i = threadIdx.x; i < B; i += kRedThreads)
+    w[i] = (T)((2.0 / (double)B) * (fmin(fmax((double)e[i], lo), hi) - mean_c));
+  if (threadIdx.x == 0 && stats) {
+    stats[0] = med;
+    stats[1] = k * mad;
+    stats[2] = mean_c;
+    stats[3] = mean_raw;
+  }
+}
+
+}  // namespace
+
+template <class T>
+cudaError_t launch_propose(const dq_handle_s& h, int64_t B, const T* r, T* r_prop, double step, uint64_t seed,
+                           uint64_t t, cudaStream_t s) {
+  const int N3 = 3 * h.N, nblk = (N3 + 3) / 4;
+  const int64_t n = B * nblk;
+  propose_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(r, r_prop, B, N3, step, seed, t);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_accept(const dq_handle_s& h, int64_t B, T* r, T* logabs, const T* r_prop, const T* logabs_prop,
+                          const int8_t* sign_prop, uint64_t seed, uint64_t t, unsigned long long* n_acc,
+                          cudaStream_t s) {
+  accept_kernel<T><<<(unsigned)((B + 255) / 256), 256, 0, s>>>(r, logabs, r_prop, logabs_prop, sign_prop, B, 3 * h.N,
+                                                               seed, t, n_acc);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_esum(const T* e, int64_t B, double* out2, unsigned int* status, cudaStream_t s) {
+  esum_kernel<T><<<1, kRedThreads, 0, s>>>(e, B, out2, status);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_loss_weights(const T* e, int64_t B, double k, T* w, double* stats, double* scratch,
+                                cudaStream_t s) {
+  int64_t Bp = 1;
+  while (Bp < B) Bp <<= 1;
+  loss_weights_kernel<T><<<1, kRedThreads, 0, s>>>(e, B, Bp, k, w, stats, scratch);
+  return cudaGetLastError();
+}
+
+#define DQ_INST(T)                                                                                                 \
+  template cudaError_t launch_propose<T>(const dq_handle_s&, int64_t, const T*, T*, double, uint64_t, uint64_t,    \
+                                         cudaStream_t);                                                           \
+  template cudaError_t launch_accept<T>(const dq_handle_s&, int64_t, T*, T*, const T*, const T*, const int8_t*,    \
+                                        uint64_t, uint64_t, unsigned long long*, cudaStream_t);                   \
+  template cudaError_t launch_esum<T>(const T*, int64_t, double*, unsigned int*, cudaStream_t);                   \
+  template cudaError_t launch_loss_weights<T>(const T*, int64_t, double, T*, double*, double*, cudaStream_t);
+DQ_INST(float)
+DQ_INST(double)
+
+}  // namespace dq

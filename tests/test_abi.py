@@ -1,0 +1,65 @@
+"""Host-side checks of the C ABI: the library builds, loads and exports every
+symbol that include/dqmc.h declares; the binding refuses to run without a GPU
+(there is no CPU fallback)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dqmc.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s+([a-z_0-9]+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2307_14123_gb300 import _build
+    _build.build()
+    from paper_2307_14123_gb300 import binding
+    return binding.load_library()
+
+
+def test_header_declares_the_hot_path():
+    names = declared_functions()
+    for n in ("ansatz_eval", "local_energy", "mcmc_step", "grad_logpsi", "vmc_loss_weights", "dq_create"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2307_14123_gb300 import binding
+    names = declared_functions()
+    assert sorted(binding.EXPORTS) == names
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if l.strip()}
+    for n in names:
+        assert n in exported, n
+        assert hasattr(lib, n)
+
+
+def test_status_strings(lib):
+    lib.dq_status_string.restype = ctypes.c_char_p
+    assert lib.dq_status_string(0) == b"ok"
+    assert b"workspace" in lib.dq_status_string(5)
+
+
+def test_null_arguments_are_rejected_without_touching_the_device(lib):
+    assert lib.dq_create(None, None, 1, None) == 1
+    assert lib.dq_param_count(None, None) == 1
+    assert lib.dq_destroy(None) == 1
+
+
+@pytest.mark.skipif(__import__("torch").cuda.is_available(), reason="checks the behaviour without a GPU")
+def test_no_cpu_fallback():
+    from paper_2307_14123_gb300 import Ansatz, DQError
+    from paper_2307_14123_gb300 import fixtures as fx
+    wl = fx.workload("lih_fp64")
+    with pytest.raises(DQError):
+        Ansatz(wl.system, wl.cfg, "fp64")

@@ -1,0 +1,302 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Inputs are the seeded fixtures; for FP32 handles the oracle receives the
+same FP32-rounded parameters and positions, so both sides see identical
+inputs.  Tolerances (stated per test):
+  FP64: |d log|psi|| and |d E_loc| <= 1e-10 max(1, |x|) per walker;
+  FP32: |d E_loc| <= max(1e-4 Ha, 1e-5 S_b) with S_b = (|Lap log|psi|| +
+        |grad log|psi||^2)/2 the size of the kinetic terms whose difference is
+        E_loc, and |d log|psi|| <= 1e-4 max(1, |log|psi||), on every walker;
+        signs equal.  The bound is derived from the rounding floor of an FP32
+        evaluation of the method (tests/test_fp32_floor.py).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2307_14123_gb300 import fixtures as fx
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2307_14123_gb300 import _build
+    _build.build()
+    oracle.build()
+    oracle.Oracle.set_threads(os.cpu_count() or 1)
+
+
+def _handle(system, cfg, precision):
+    from paper_2307_14123_gb300 import Ansatz
+    return Ansatz(system, cfg, precision, device="cuda:0")
+
+
+def _inputs(system, cfg, precision, B, pseed, wseed):
+    theta = fx.init_params(system, cfg, pseed)
+    r = fx.init_walkers(system, B, wseed)
+    if precision != "fp64":
+        theta = theta.astype(np.float32).astype(np.float64)
+        r = r.astype(np.float32).astype(np.float64)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    return theta, r, torch.tensor(theta, dtype=dt, device="cuda:0"), torch.tensor(r, dtype=dt, device="cuda:0")
+
+
+def _np(*ts):
+    return [t.detach().cpu().numpy().astype(np.float64) if t.dtype != torch.int8 else t.cpu().numpy() for t in ts]
+
+
+def _report(name, got, ref):
+    err = np.abs(got - ref)
+    print(f"{name}: max err {np.nanmax(err):.3e}, mean err {np.nanmean(err):.3e}")
+    return err
+
+
+def _check_fp64(la, sg, el, ref, tol=1e-10):
+    assert np.array_equal(sg, ref["sign"])
+    e1 = _report("logabs", la, ref["logabs"])
+    assert np.all(e1 <= tol * np.maximum(1, np.abs(ref["logabs"])))
+    if el is not None:
+        e2 = _report("e_loc", el, ref["e_loc"])
+        assert np.all(e2 <= tol * np.maximum(1, np.abs(ref["e_loc"])))
+
+
+# ----------------------------------------------------------------------------
+# LiH, FP64, full batch of 512 (the small FP64 workload)
+# ----------------------------------------------------------------------------
+def test_lih_fp64_full_batch():
+    wl = fx.workload("lih_fp64")
+    h = _handle(wl.system, wl.cfg, "fp64")
+    theta, r, th_t, r_t = _inputs(wl.system, wl.cfg, "fp64", wl.B, wl.param_seed, wl.walker_seed)
+    la, sg, el, e2 = h.local_energy(th_t, r_t, sums=True)
+    la, sg, el, e2 = _np(la, sg, el, e2)
+    ref = oracle.Oracle(wl.system, wl.cfg).local_energy(theta, r)
+    _check_fp64(la, sg, el, ref)
+    assert e2[0] == pytest.approx(np.sum(ref["e_loc"]), rel=1e-10)
+    assert e2[1] == pytest.approx(np.sum(ref["e_loc"] ** 2), rel=1e-10)
+    la2, sg2 = _np(*h.ansatz_eval(th_t, r_t))
+    _check_fp64(la2, sg2, None, ref)
+    assert h.device_status() == 0
+
+
+@pytest.mark.parametrize("B", [1, 3, 129])
+def test_lih_fp64_ragged_batches(B):
+    wl = fx.workload("lih_fp64")
+    h = _handle(wl.system, wl.cfg, "fp64")
+    theta, r, th_t, r_t = _inputs(wl.system, wl.cfg, "fp64", B, 0, 5)
+    la, sg, el = _np(*h.local_energy(th_t, r_t))
+    _check_fp64(la, sg, el, oracle.Oracle(wl.system, wl.cfg).local_energy(theta, r))
+
+
+def test_chunked_equals_unchunked():
+    wl = fx.workload("lih_fp64")
+    h = _handle(wl.system, wl.cfg, "fp64")
+    _, _, th_t, r_t = _inputs(wl.system, wl.cfg, "fp64", 512, 0, 0)
+    a = _np(*h.local_energy(th_t, r_t))
+    h.set_max_chunk(100)  # five full chunks and a ragged one of 12
+    b = _np(*h.local_energy(th_t, r_t))
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_empty_batch():
+    wl = fx.workload("lih_fp64")
+    h = _handle(wl.system, wl.cfg, "fp64")
+    _, _, th_t, _ = _inputs(wl.system, wl.cfg, "fp64", 1, 0, 0)
+    r0 = torch.empty((0, wl.system.n_elec, 3), dtype=torch.float64, device="cuda:0")
+    la, sg, el, e2 = h.local_energy(th_t, r0, sums=True)
+    assert la.numel() == 0 and e2.cpu().tolist() == [0.0, 0.0]
+
+
+# ----------------------------------------------------------------------------
+# Closed forms on the GPU
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 2e-5)])
+def test_hydrogen_network_off(precision, tol):
+    H = fx.molecule("H")
+    cfg = fx.AnsatzCfg(32, 2, 1, use_cusp=0)
+    h = _handle(H, cfg, precision)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    th = torch.tensor(fx.network_off_params(H, cfg, 1.0), dtype=dt, device="cuda:0")
+    r = fx.init_walkers(H, 256, 3, sigma=2.0)
+    la, sg, el = _np(*h.local_energy(th, torch.tensor(r, dtype=dt, device="cuda:0")))
+    rr = np.linalg.norm(r[:, 0], axis=1)
+    assert np.all(sg == 1)
+    assert np.all(np.abs(el + 0.5) <= tol * np.maximum(1, 1 / rr))
+    assert np.all(np.abs(la + rr) <= tol * np.maximum(1, rr))
+
+
+def test_two_electron_product_gpu():
+    Z = 2.0
+    sys_ = fx.System(Z=np.array([Z]), R=np.zeros((1, 3)), n_up=1, n_down=1)
+    cfg = fx.AnsatzCfg(32, 2, 1, use_cusp=0)
+    h = _handle(sys_, cfg, "fp64")
+    th = torch.tensor(fx.network_off_params(sys_, cfg, Z), device="cuda:0")
+    r = fx.init_walkers(sys_, 128, 9)
+    _, _, el = _np(*h.local_energy(th, torch.tensor(r, device="cuda:0")))
+    r12 = np.linalg.norm(r[:, 0] - r[:, 1], axis=1)
+    np.testing.assert_allclose(el, -Z * Z + 1 / r12, rtol=1e-11, atol=1e-11)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_singular_determinant_gpu(precision):
+    """Two same-spin electrons mirrored through the nucleus: psi = 0 exactly
+    for any weights (antisymmetry plus reflection invariance)."""
+    sys_ = fx.System(Z=np.array([2.0]), R=np.zeros((1, 3)), n_up=2, n_down=0)
+    cfg = fx.AnsatzCfg(32, 2, 2)
+    h = _handle(sys_, cfg, precision)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    th = torch.tensor(fx.init_params(sys_, cfg, 1), dtype=dt, device="cuda:0")
+    r = fx.init_walkers(sys_, 8, 1)
+    r[:, 1] = r[:, 0] * np.array([-1.0, 1.0, 1.0])
+    h.device_status()
+    la, sg, el = _np(*h.local_energy(th, torch.tensor(r, dtype=dt, device="cuda:0")))
+    assert np.all(sg == 0) and np.all(np.isneginf(la)) and np.all(np.isnan(el))
+    from paper_2307_14123_gb300.binding import FLAG_SINGULAR
+    assert h.device_status() & FLAG_SINGULAR
+    assert h.device_status() == 0  # reading clears
+
+
+def test_antisymmetry_gpu():
+    wl = fx.workload("lih_fp64")
+    h = _handle(wl.system, wl.cfg, "fp64")
+    _, r, th_t, r_t = _inputs(wl.system, wl.cfg, "fp64", 64, 0, 2)
+    a = _np(*h.local_energy(th_t, r_t))
+    rs = r.copy()
+    rs[:, [2, 3]] = rs[:, [3, 2]]  # the two spin-down electrons
+    b = _np(*h.local_energy(th_t, torch.tensor(rs, device="cuda:0")))
+    np.testing.assert_allclose(b[0], a[0], rtol=1e-12)
+    assert np.all(b[1] == -a[1])
+    np.testing.assert_allclose(b[2], a[2], rtol=1e-9, atol=1e-9)
+
+
+# ----------------------------------------------------------------------------
+# N2 (14 electrons, D=128, 3 layers, 16 determinant pairs)
+# ----------------------------------------------------------------------------
+def test_n2_fp64_jets():
+    wl = fx.workload("n2_fp32")
+    h = _handle(wl.system, wl.cfg, "fp64")
+    theta, r, th_t, r_t = _inputs(wl.system, wl.cfg, "fp64", 16, wl.param_seed, wl.walker_seed)
+    la, sg, el = _np(*h.local_energy(th_t, r_t))
+    _check_fp64(la, sg, el, oracle.Oracle(wl.system, wl.cfg).local_energy(theta, r))
+
+
+def _check_fp32(la, sg, el, ref, r, label):
+    assert np.array_equal(sg, ref["sign"])
+    e_la = _report(f"{label} logabs", la, ref["logabs"])
+    assert np.all(e_la <= 1e-4 * np.maximum(1, np.abs(ref["logabs"])))
+    print(f"{label}: logabs within 1e-5 relative on {np.mean(e_la <= 1e-5 * np.maximum(1, np.abs(ref['logabs']))):.3f}")
+    S = 0.5 * (np.abs(ref["lap"]) + np.sum(ref["grad"] ** 2, axis=1))
+    tol = np.maximum(1e-4, 1e-5 * S)
+    e_el = _report(f"{label} e_loc", el, ref["e_loc"])
+    print(f"{label}: |dE|/S max {np.max(e_el / S):.2e} median {np.median(e_el / S):.2e}; "
+          f"within 1e-4 Ha: {np.mean(e_el <= 1e-4):.3f}")
+    assert np.all(e_el <= tol), (e_el / S)[e_el > tol]
+
+
+def test_n2_fp32_sample():
+    wl = fx.workload("n2_fp32")
+    h = _handle(wl.system, wl.cfg, "fp32")
+    theta, r, th_t, r_t = _inputs(wl.system, wl.cfg, "fp32", 48, wl.param_seed, wl.walker_seed)
+    la, sg, el = _np(*h.local_energy(th_t, r_t))
+    _check_fp32(la, sg, el, oracle.Oracle(wl.system, wl.cfg).local_energy(theta, r, with_grad=True), r, "n2 fp32")
+
+
+def test_n2_fp32_full_batch_sampled():
+    """The benchmark launch (4096 walkers, one chunk); oracle on sampled walkers."""
+    wl = fx.workload("n2_fp32")
+    h = _handle(wl.system, wl.cfg, "fp32")
+    theta, r, th_t, r_t = _inputs(wl.system, wl.cfg, "fp32", wl.B, wl.param_seed, wl.walker_seed)
+    la, sg, el, e2 = h.local_energy(th_t, r_t, sums=True)
+    la, sg, el, e2 = _np(la, sg, el, e2)
+    idx = np.unique(np.concatenate([[0, 1, wl.B - 1], np.random.default_rng(0).choice(wl.B, 29, replace=False)]))
+    ref = oracle.Oracle(wl.system, wl.cfg).local_energy(theta, r[idx], with_grad=True)
+    _check_fp32(la[idx], sg[idx], el[idx], ref, r[idx], "n2 fp32 full")
+    fin = np.isfinite(el)
+    assert e2[0] == pytest.approx(np.sum(el[fin].astype(np.float64)), rel=1e-9)
+
+
+# ----------------------------------------------------------------------------
+# Metropolis sampler, teacher-forced against the oracle
+# ----------------------------------------------------------------------------
+def _mcmc_teacher_forced(name, precision, B, steps, pos_tol, flip_band, la_rtol):
+    wl = fx.workload(name)
+    h = _handle(wl.system, wl.cfg, precision)
+    o = oracle.Oracle(wl.system, wl.cfg)
+    theta, r, th_t, r_t = _inputs(wl.system, wl.cfg, precision, B, wl.param_seed, wl.walker_seed)
+    la_t, _ = h.ansatz_eval(th_t, r_t)
+    step = wl.extra["step_size"]
+    flips = 0
+    for t in range(steps):
+        r_prev, la_prev = _np(r_t, la_t)
+        n_acc = h.mcmc_step(th_t, r_t, la_t, n_steps=1, step_size=step, seed=wl.walker_seed, step_counter=t)
+        r_new, la_new = _np(r_t, la_t)
+        xi, u = fx.metropolis_draws(wl.walker_seed, B, wl.system.n_elec, t)
+        ro, lo, acc = o.metropolis_step(theta, r_prev, la_prev, xi, u, step)
+        gpu_acc = np.any(r_new != r_prev, axis=(1, 2))
+        assert int(n_acc.item()) == int(gpu_acc.sum())
+        diff = gpu_acc != acc.astype(bool)
+        if diff.any():  # only allowed where the decision sits on the threshold
+            rp = r_prev[diff] + step * xi[diff]
+            lp, _ = o.evaluate(theta, rp)
+            margin = np.abs(np.log(u[diff]) - 2 * (lp - la_prev[diff]))
+            assert np.all(margin < flip_band), margin
+            flips += int(diff.sum())
+        same = ~diff
+        np.testing.assert_allclose(r_new[same], ro[same], rtol=0, atol=pos_tol)
+        ok = same & gpu_acc
+        np.testing.assert_allclose(la_new[ok], lo[ok], rtol=la_rtol, atol=la_rtol)
+    print(f"{name}: {flips} near-threshold flips over {steps} steps")
+    return h, th_t, r_t, la_t
+
+
+def test_mcmc_lih_fp64_teacher_forced():
+    _mcmc_teacher_forced("lih_fp64", "fp64", 512, 10, 1e-12, 1e-8, 1e-10)
+
+
+def test_mcmc_n2_fp32_teacher_forced():
+    _mcmc_teacher_forced("n2_fp32", "fp32", 4096, 1, 1e-5, 1e-3, 1e-4)
+
+
+def test_mcmc_multi_step_equals_single_steps():
+    wl = fx.workload("lih_fp64")
+    h = _handle(wl.system, wl.cfg, "fp64")
+    _, _, th_t, r_t = _inputs(wl.system, wl.cfg, "fp64", 256, 0, 0)
+    la_t, _ = h.ansatz_eval(th_t, r_t)
+    r2, la2 = r_t.clone(), la_t.clone()
+    n5 = h.mcmc_step(th_t, r_t, la_t, n_steps=5, step_size=0.2, seed=7, step_counter=100)
+    tot = 0
+    for k in range(5):
+        tot += int(h.mcmc_step(th_t, r2, la2, n_steps=1, step_size=0.2, seed=7, step_counter=100 + k).item())
+    assert torch.equal(r_t, r2) and torch.equal(la_t, la2)
+    assert int(n5.item()) == tot
+
+
+# ----------------------------------------------------------------------------
+# Clipped loss weights (Sec. 4.4)
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("B", [1, 7, 4096, 5000])
+def test_loss_weights_gpu(B):
+    wl = fx.workload("lih_fp64")
+    h = _handle(wl.system, wl.cfg, "fp64")
+    e = np.random.default_rng(B).standard_cauchy(B) * 3 - 50
+    w, stats = h.vmc_loss_weights(torch.tensor(e, device="cuda:0"), clip_k=5.0)
+    w_ref, _, med, hw = oracle.clipped_loss_weights(e, 5.0)
+    np.testing.assert_allclose(w.cpu().numpy(), w_ref, rtol=1e-12, atol=1e-15)
+    s = stats.cpu().numpy()
+    assert s[0] == med and s[1] == pytest.approx(hw, rel=1e-13)
+
+
+def test_host_tensors_end_to_end():
+    wl = fx.workload("lih_fp64")
+    h = _handle(wl.system, wl.cfg, "fp64")
+    theta, r, th_t, r_t = _inputs(wl.system, wl.cfg, "fp64", 64, 0, 0)
+    a = _np(*h.local_energy(th_t, r_t))
+    b = h.local_energy(torch.tensor(theta), torch.tensor(r))
+    assert b[0].device.type == "cpu"
+    for x, y in zip(a, _np(*b)):
+        assert np.array_equal(x, y)

@@ -217,14 +217,22 @@ def test_multi_determinant_leibniz(n_up):
         assert sg[b] == np.sign(psi)
 
 
+def mirrored_pair_walkers(B, seed):
+    """Two same-spin electrons mirrored through the nucleus at the origin:
+    (r1, r2) -> (R r1, R r2) with R the reflection x -> -x swaps them, so a
+    distance-only ansatz gives psi = -psi = 0 exactly (Eq. 3)."""
+    r = fx.init_walkers(fx.System(Z=np.array([2.0]), R=np.zeros((1, 3)), n_up=2, n_down=0), B, seed)
+    r[:, 1] = r[:, 0] * np.array([-1.0, 1.0, 1.0])
+    return r
+
+
 def test_singular_determinant():
-    """Two identical orbitals: det = 0, so sign 0, log|psi| = -inf, E_loc NaN."""
+    """psi = 0 exactly: sign 0, log|psi| = -inf, E_loc NaN (full random-weight network)."""
     sys_ = fx.System(Z=np.array([2.0]), R=np.zeros((1, 3)), n_up=2, n_down=0)
-    cfg = fx.AnsatzCfg(8, 1, 1, use_cusp=0)
+    cfg = fx.AnsatzCfg(8, 2, 2)
     o = oracle.Oracle(sys_, cfg)
-    th = fx.network_off_params(sys_, cfg, 1.3)
-    r = fx.init_walkers(sys_, 4, 1)
-    out = o.local_energy(th, r)
+    th = fx.init_params(sys_, cfg, 1)
+    out = o.local_energy(th, mirrored_pair_walkers(4, 1))
     assert np.all(out["sign"] == 0) and np.all(np.isneginf(out["logabs"])) and np.all(np.isnan(out["e_loc"]))
 
 
