@@ -190,6 +190,22 @@ dq_status grad_logpsi(dq_handle h, const void* params, const void* r, int64_t B,
 dq_status vmc_loss_weights(dq_handle h, const void* e_loc, int64_t B, double clip_k, void* weights,
                            double* stats, void* ws, size_t ws_bytes, void* stream);
 
+/* vmc_loss_weights_noalloc: the same weights and stats as vmc_loss_weights,
+ * for callers that cannot allocate device memory and so cannot supply a
+ * workspace (for example a plugin whose host framework owns all device
+ * allocations, or a service that must not allocate after start-up).  The
+ * paper has no counterpart; this is a deployment convenience.
+ * The sort scratch is a fixed 512 KB array inside the library (one per GPU
+ * that loads it, kept until exit), so B must not exceed 65536; larger B
+ * returns DQ_ERR_SHAPE and nothing is enqueued.  No call allocates.
+ * The first call on a device (with that device current) looks up the
+ * array's device address; it may load the library's module, so make it
+ * before any stream capture.  All calls on a device share the array: calls
+ * whose kernels overlap on the GPU (unordered streams) race and give wrong
+ * results.  Arguments as for vmc_loss_weights.                              */
+dq_status vmc_loss_weights_noalloc(dq_handle h, const void* e_loc, int64_t B, double clip_k, void* weights,
+                                   double* stats, void* stream);
+
 /* Reads and clears the device status flags (DQ_FLAG_*) accumulated since the
  * last read.  Synchronises `stream`. */
 dq_status dq_last_device_status(dq_handle h, void* stream, uint32_t* flags);

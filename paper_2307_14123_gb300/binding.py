@@ -31,7 +31,7 @@ PRECISIONS = {"fp64": DQ_FP64, "fp32": DQ_FP32, "bf16": DQ_BF16_MIXED}
 EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_max_chunk", "dq_workspace_size",
            "ansatz_eval", "local_energy", "mcmc_step", "grad_logpsi", "vmc_loss_weights", "dq_last_device_status",
            "dq_status_string", "dq_profile_enable", "dq_profile_reset", "dq_profile_read", "dq_profile_kind_name",
-           "dq_profile_kind_count"]
+           "dq_profile_kind_count", "vmc_loss_weights_noalloc"]
 
 
 class DQError(RuntimeError):
@@ -76,6 +76,7 @@ def load_library(path=None):
         lib.mcmc_step.argtypes = [P, P, P, P, i64, i32, f64, u64, u64, P, P, sz, P]
         lib.grad_logpsi.argtypes = [P, P, P, i64, P, i32, P, P, sz, P]
         lib.vmc_loss_weights.argtypes = [P, P, i64, f64, P, P, P, sz, P]
+        lib.vmc_loss_weights_noalloc.argtypes = [P, P, i64, f64, P, P, P]
         lib.dq_last_device_status.argtypes = [P, P, P]
         lib.dq_status_string.argtypes = [ctypes.c_int]
         lib.dq_profile_enable.argtypes = [P, i32]
