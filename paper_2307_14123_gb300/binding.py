@@ -31,7 +31,7 @@ PRECISIONS = {"fp64": DQ_FP64, "fp32": DQ_FP32, "bf16": DQ_BF16_MIXED}
 EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_max_chunk", "dq_workspace_size",
            "ansatz_eval", "local_energy", "mcmc_step", "grad_logpsi", "vmc_loss_weights", "dq_last_device_status",
            "dq_status_string", "dq_profile_enable", "dq_profile_reset", "dq_profile_read", "dq_profile_kind_name",
-           "dq_profile_kind_count", "vmc_loss_weights_noalloc"]
+           "dq_profile_kind_count", "vmc_loss_weights_noalloc", "dq_fp64_matrix_count"]
 
 
 class DQError(RuntimeError):
@@ -78,6 +78,7 @@ def load_library(path=None):
         lib.vmc_loss_weights.argtypes = [P, P, i64, f64, P, P, P, sz, P]
         lib.vmc_loss_weights_noalloc.argtypes = [P, P, i64, f64, P, P, P]
         lib.dq_last_device_status.argtypes = [P, P, P]
+        lib.dq_fp64_matrix_count.argtypes = [P, P, P]
         lib.dq_status_string.argtypes = [ctypes.c_int]
         lib.dq_profile_enable.argtypes = [P, i32]
         lib.dq_profile_reset.argtypes = [P]
@@ -273,10 +274,45 @@ class Ansatz:
                 out[self.lib.dq_profile_kind_name(k).decode()] = (ms.value, n.value)
         return out
 
+    def fp64_matrix_count(self):
+        """Determinant matrices that took the FP64 path since the last read (then cleared)."""
+        c = ctypes.c_int64()
+        _check(self.lib.dq_fp64_matrix_count(self.h, self._stream(), ctypes.byref(c)))
+        return c.value
+
     def device_status(self):
         f = ctypes.c_uint32()
         _check(self.lib.dq_last_device_status(self.h, self._stream(), ctypes.byref(f)))
         return f.value
+
+
+class LogAbsPsi(torch.autograd.Function):
+    """log|psi| of every walker as a differentiable function of the parameters.
+
+    Forward: ``ansatz_eval``.  Backward: ``grad_logpsi`` in weighted mode with
+    the incoming gradient as the walker weights, i.e. sum_b g_b d log|psi_b| /
+    d theta (the form the gradient estimator of Eq. (30) takes).  Positions
+    get no gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, params, r, handle):
+        logabs, _ = handle.ansatz_eval(params, r)
+        ctx.save_for_backward(params, r)
+        ctx.handle = handle
+        return logabs
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        params, r = ctx.saved_tensors
+        h = ctx.handle
+        g = h.grad_logpsi(params, r, grad_out.to(h.dtype).contiguous(), mode=0)
+        return g, None, None
+
+
+def log_abs_psi(handle, params, r):
+    """Differentiable log|psi| (see :class:`LogAbsPsi`)."""
+    return LogAbsPsi.apply(params, r, handle)
 
 
 # C-ABI names as free functions over a handle.

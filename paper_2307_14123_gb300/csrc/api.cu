@@ -13,6 +13,7 @@
 #include <new>
 #include <vector>
 
+#include "backward.cuh"
 #include "common.cuh"
 
 namespace dq {
@@ -244,6 +245,215 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
   return DQ_OK;
 }
 
+// ---------------------------------------------------------------------------
+// grad_logpsi: value-only forward keeping every layer's activations, then the
+// reverse pass (backward.cu).  Layout of the saved and adjoint buffers for a
+// chunk of Bc walkers (C = 1, one row per node / edge / walker).
+// ---------------------------------------------------------------------------
+struct GradPlan {
+  size_t geo, rbf, eh, ew, zl, msg, u, F, phi, det, js, jh, z0;  // saved forward
+  size_t fbar, ubar, mbar, zbar, wbar, hbar, phibar, beta, cbar, jhbar, gt, sbar, envbar, ybar, part;
+  int64_t part_elems;
+  size_t total;
+};
+
+GradPlan plan_grad(const dq_handle_s& h, int64_t Bc, size_t elem) {
+  const int64_t E = h.edges.n_all, N = h.N, D = h.D, K = h.K, L = h.L, M = h.M, Q = h.Q;
+  const int64_t nmax = std::max(h.n_up, h.n_dn), Wo = K * nmax;
+  GradPlan p{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += align_up(bytes);
+    return at;
+  };
+  p.geo = take(Bc * E * 4 * elem);
+  p.rbf = take(Bc * E * Q * elem);
+  p.eh = take(L * Bc * E * D * elem);
+  p.ew = take(L * Bc * E * D * elem);
+  p.zl = take(L * Bc * N * D * elem);
+  p.msg = take(L * Bc * N * 3 * D * elem);
+  p.u = take(L * Bc * N * D * elem);
+  p.F = take((L + 1) * Bc * N * D * elem);
+  p.phi = take(Bc * N * Wo * elem);
+  p.det = take(Bc * 2 * K * (3 * N + 3) * sizeof(double));
+  p.js = take(Bc * D * elem);
+  p.jh = take(Bc * D * elem);
+  p.z0 = take(2 * D * elem);
+  p.fbar = take(Bc * N * D * elem);
+  p.ubar = take(Bc * N * D * elem);
+  p.mbar = take(Bc * N * 3 * D * elem);
+  p.zbar = take(Bc * N * D * elem);
+  p.wbar = take(Bc * E * D * elem);
+  p.hbar = take(Bc * E * D * elem);
+  p.phibar = take(Bc * N * Wo * elem);
+  p.beta = take(Bc * K * elem);
+  p.cbar = take(Bc * K * elem);
+  p.jhbar = take(Bc * D * elem);
+  p.gt = take(Bc * D * elem);
+  p.sbar = take(Bc * D * elem);
+  p.envbar = take(Bc * 2 * 2 * Wo * M * elem);
+  p.ybar = take(Bc * M * D * elem);
+  const int64_t blk = std::max({3 * D * D, D * D, D * Q, Wo * D, Wo * M, M * D, K, D});
+  p.part_elems = 64 * blk;
+  p.part = take(p.part_elems * elem);
+  p.total = o;
+  return p;
+}
+
+inline RowMap rm(int64_t ld) { return RowMap{1, ld, 0}; }
+
+template <class T>
+dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B, const T* weights, int mode, T* G,
+                   unsigned char* ws, size_t ws_bytes, cudaStream_t s) {
+  const int64_t Bmax = std::min<int64_t>(B, h.max_chunk);
+  const GradPlan pl = plan_grad(h, Bmax, sizeof(T));
+  if (ws == nullptr || ws_bytes < pl.total || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
+  auto buf = [&](size_t off) { return reinterpret_cast<T*>(ws + off); };
+  const int N = h.N, D = h.D, K = h.K, L = h.L, M = h.M, Q = h.Q, E = h.edges.n_all;
+  const int nmax = std::max(h.n_up, h.n_dn), Wo = K * nmax;
+  const int64_t P = h.off.total;
+  const ParamOffsets& off = h.off;
+  const size_t el = sizeof(T);
+  DQ_CU(cudaMemsetAsync(G, 0, (size_t)(mode == 1 ? B : 1) * P * el, s));
+  T* part = buf(pl.part);
+  const int ns[2] = {h.n_up, h.n_dn}, i0[2] = {0, h.n_up};
+  const int e0[3] = {0, h.edges.n_par, h.edges.n_ee};
+  const int ng[3] = {h.edges.n_par, h.edges.n_anti, h.edges.n_en};
+  for (int64_t b0 = 0; b0 < B; b0 += Bmax) {
+    const int64_t nb = std::min<int64_t>(Bmax, B - b0);
+    const FwdDims d{nb, N, h.n_up, h.n_dn, M, D, K, Q, 1};
+    T* Gc = mode == 1 ? G + b0 * P : G;
+    const T* wc = weights ? weights + b0 : nullptr;
+    auto reduce = [&](const T* X, RowMap mx, const T* Y, RowMap my, int rpw, int n_o, int n_a, int64_t poff, int ld) {
+      return param_reduce<T>(X, mx, Y, my, rpw, nb, n_o, n_a, Gc, P, poff, ld, mode, part, pl.part_elems, s);
+    };
+    // ---- forward, keeping activations ----
+    FwdBuffers<T> v{};
+    v.geo = buf(pl.geo);
+    v.rbf = buf(pl.rbf);
+    v.phi = buf(pl.phi);
+    v.det = reinterpret_cast<double*>(ws + pl.det);
+    v.js = buf(pl.js);
+    v.jh = buf(pl.jh);
+    v.z0 = buf(pl.z0);
+    auto EH = [&](int l) { return buf(pl.eh) + (int64_t)l * Bmax * E * D; };
+    auto EW = [&](int l) { return buf(pl.ew) + (int64_t)l * Bmax * E * D; };
+    auto ZL = [&](int l) { return buf(pl.zl) + (int64_t)l * Bmax * N * D; };
+    auto MS = [&](int l) { return buf(pl.msg) + (int64_t)l * Bmax * N * 3 * D; };
+    auto U = [&](int l) { return buf(pl.u) + (int64_t)l * Bmax * N * D; };
+    auto F = [&](int l) { return buf(pl.F) + (int64_t)l * Bmax * N * D; };
+    DQ_LAUNCH(h, PK_BWD_GEMM, launch_layer0_node<T>(h, d, params, v, s));
+    DQ_LAUNCH(h, PK_BWD_GEMM, launch_geometry<T>(h, d, r + b0 * N * 3, v, s));
+    DQ_LAUNCH(h, PK_BWD_GEMM, launch_fill_spin_rows<T>(F(0), params + off.E_spin, nb, N, h.n_up, D, s));
+    for (int l = 0; l < L; ++l) {
+      const auto& y = off.layer[l];
+      v.eh = EH(l);
+      v.ew = EW(l);
+      v.F = F(l);
+      v.Z = ZL(l);
+      v.msg = MS(l);
+      DQ_LAUNCH(h, PK_BWD_GEMM, launch_edge_hidden<T>(h, d, params, l, v, s));
+      for (int t = 0; t < 3; ++t) {
+        if (ng[t] == 0) continue;
+        const RowMap m{(int64_t)ng[t], (int64_t)E * D, D};
+        DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nt<T>(v.eh + (int64_t)e0[t] * D, m, params + y.W2[t], params + y.b2[t], 1,
+                                             v.ew + (int64_t)e0[t] * D, m, nb * ng[t], D, D, false, s));
+      }
+      if (l > 0)
+        DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nt<T>(F(l), rm(D), params + y.W_h, nullptr, 1, ZL(l), rm(D), nb * N, D, D,
+                                             false, s));
+      DQ_LAUNCH(h, PK_BWD_GEMM, launch_messages<T>(h, d, params, l, l == 0, v, s));
+      DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nt<T>(MS(l), rm(3 * D), params + y.W_g, params + y.b_g, 1, U(l), rm(D), nb * N,
+                                           D, 3 * D, false, s));
+      DQ_LAUNCH(h, PK_BWD_GEMM, launch_update_io<T>(h, d, params, l == 0, U(l), F(l), F(l + 1), s));
+    }
+    v.F = F(L);
+    for (int sg = 0; sg < 2; ++sg) {
+      if (ns[sg] == 0) continue;
+      const RowMap mx{(int64_t)ns[sg], (int64_t)N * D, D};
+      const RowMap my{(int64_t)ns[sg], (int64_t)N * Wo, Wo};
+      DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nt<T>(F(L) + (int64_t)i0[sg] * D, mx, params + off.W_o[sg], params + off.b_o[sg],
+                                           1, v.phi + (int64_t)i0[sg] * Wo, my, nb * ns[sg], K * ns[sg], D, false, s));
+    }
+    DQ_LAUNCH(h, PK_BWD_DET, launch_orbital_det<T>(h, d, params, v, s));
+    if (h.use_jastrow) {
+      DQ_LAUNCH(h, PK_BWD_GEMM, launch_jastrow_sum<T>(h, d, v, s));
+      DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nt<T>(v.js, rm(D), params + off.W_J1, params + off.b_J1, 1, v.jh, rm(D), nb, D, D,
+                                           false, s));
+    }
+    // ---- reverse pass ----
+    T *beta = buf(pl.beta), *cbar = buf(pl.cbar), *jhbar = buf(pl.jhbar), *gt = buf(pl.gt), *sbar = buf(pl.sbar);
+    T *fbar = buf(pl.fbar), *ubar = buf(pl.ubar), *mbar = buf(pl.mbar), *zbar = buf(pl.zbar);
+    T *wbar = buf(pl.wbar), *hbar = buf(pl.hbar), *phibar = buf(pl.phibar), *envbar = buf(pl.envbar);
+    T* ybar = buf(pl.ybar);
+    DQ_LAUNCH(h, PK_BWD_COMBINE,
+              launch_bwd_combine<T>(h, nb, v.det, v.jh, params, wc, beta, cbar, jhbar, gt, s));
+    DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(cbar, rm(K), nullptr, rm(1), 1, K, 1, off.c, 1));
+    if (h.use_jastrow) {
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(gt, rm(D), nullptr, rm(1), 1, D, 1, off.w_J2, 1));
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(jhbar, rm(D), v.js, rm(D), 1, D, D, off.W_J1, D));
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(jhbar, rm(D), nullptr, rm(1), 1, D, 1, off.b_J1, 1));
+      DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(jhbar, rm(D), params + off.W_J1, sbar, rm(D), nb, D, D, false, s));
+    }
+    DQ_LAUNCH(h, PK_BWD_DET, launch_bwd_det<T>(h, nb, v.phi, v.geo, params, beta, phibar, envbar, s));
+    for (int sg = 0; sg < 2; ++sg) {
+      if (ns[sg] == 0) continue;
+      const int64_t blk = (int64_t)Wo * M;
+      const RowMap me{1, 4 * blk, 0};
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(envbar + (sg * 2 + 0) * blk, me, nullptr, rm(1), 1, K * ns[sg] * M, 1,
+                                         off.omega[sg], 1));
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(envbar + (sg * 2 + 1) * blk, me, nullptr, rm(1), 1, K * ns[sg] * M, 1,
+                                         off.zeta[sg], 1));
+      const RowMap mp{(int64_t)ns[sg], (int64_t)N * Wo, Wo};
+      const RowMap mf{(int64_t)ns[sg], (int64_t)N * D, D};
+      const T* pb = phibar + (int64_t)i0[sg] * Wo;
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(pb, mp, F(L) + (int64_t)i0[sg] * D, mf, ns[sg], K * ns[sg], D, off.W_o[sg], D));
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(pb, mp, nullptr, rm(1), ns[sg], K * ns[sg], 1, off.b_o[sg], 1));
+      DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(pb, mp, params + off.W_o[sg], fbar + (int64_t)i0[sg] * D, mf,
+                                           nb * ns[sg], D, K * ns[sg], false, s));
+    }
+    if (h.use_jastrow) DQ_LAUNCH(h, PK_BWD_UPDATE, launch_add_rows<T>(fbar, sbar, nb, N, D, s));
+    for (int l = L - 1; l >= 0; --l) {
+      const auto& y = off.layer[l];
+      DQ_LAUNCH(h, PK_BWD_UPDATE, launch_tanh_bwd<T>(fbar, U(l), nb * N * D, true, ubar, s));
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ubar, rm(D), MS(l), rm(3 * D), N, D, 3 * D, y.W_g, 3 * D));
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ubar, rm(D), nullptr, rm(1), N, D, 1, y.b_g, 1));
+      DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(ubar, rm(D), params + y.W_g, mbar, rm(3 * D), nb * N, 3 * D, D, false, s));
+      DQ_LAUNCH(h, PK_BWD_MESSAGES, launch_msg_bwd<T>(h, nb, mbar, ZL(l), v.z0, EW(l), params + y.Y, l == 0, zbar, wbar,
+                                                      ybar, s));
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ybar, rm((int64_t)M * D), nullptr, rm(1), 1, M * D, 1, y.Y, 1));
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(zbar, rm(D), F(l), rm(D), N, D, D, y.W_h, D));
+      DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(zbar, rm(D), params + y.W_h, fbar, rm(D), nb * N, D, D, true, s));
+      for (int t = 0; t < 3; ++t) {
+        if (ng[t] == 0) continue;
+        const RowMap me{(int64_t)ng[t], (int64_t)E * D, D};
+        const T* wb = wbar + (int64_t)e0[t] * D;
+        DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(wb, me, EH(l) + (int64_t)e0[t] * D, me, ng[t], D, D, y.W2[t], D));
+        DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(wb, me, nullptr, rm(1), ng[t], D, 1, y.b2[t], 1));
+        DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(wb, me, params + y.W2[t], hbar + (int64_t)e0[t] * D, me, nb * ng[t], D, D,
+                                             false, s));
+      }
+      DQ_LAUNCH(h, PK_BWD_EDGE, launch_tanh_bwd<T>(hbar, EH(l), nb * E * D, false, hbar, s));
+      for (int t = 0; t < 3; ++t) {
+        if (ng[t] == 0) continue;
+        const RowMap me{(int64_t)ng[t], (int64_t)E * D, D};
+        const RowMap mq{(int64_t)ng[t], (int64_t)E * Q, Q};
+        const T* hb = hbar + (int64_t)e0[t] * D;
+        DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(hb, me, v.rbf + (int64_t)e0[t] * Q, mq, ng[t], D, Q, y.W1[t], Q));
+        DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(hb, me, nullptr, rm(1), ng[t], D, 1, y.b1[t], 1));
+      }
+    }
+    for (int sg = 0; sg < 2; ++sg) {
+      if (ns[sg] == 0) continue;
+      const RowMap mf{(int64_t)ns[sg], (int64_t)N * D, D};
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(fbar + (int64_t)i0[sg] * D, mf, nullptr, rm(1), ns[sg], D, 1,
+                                         off.E_spin + (int64_t)sg * D, 1));
+    }
+  }
+  return DQ_OK;
+}
+
 dq_status check_handle(dq_handle h) {
   if (h == nullptr) return DQ_ERR_ARG;
   int dev = -1;
@@ -370,13 +580,15 @@ dq_status dq_create(const dq_system* sys, const dq_ansatz_cfg* cfg, int32_t prec
             cudaMalloc(&h->d_Z, M * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&h->d_pair_of, N * N * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&h->d_pair_ij, pij.size() * sizeof(int)) == cudaSuccess &&
-            cudaMalloc(&h->d_status, sizeof(unsigned int)) == cudaSuccess;
+            cudaMalloc(&h->d_status, sizeof(unsigned int)) == cudaSuccess &&
+            cudaMalloc(&h->d_fp64_count, sizeof(unsigned long long)) == cudaSuccess;
   ok = ok && cudaMemcpy(h->d_R, sys->R, 3 * M * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(h->d_Rf, Rf.data(), 3 * M * sizeof(float), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(h->d_Z, sys->Z, M * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(h->d_pair_of, pof.data(), N * N * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
        cudaMemcpy(h->d_pair_ij, pij.data(), pij.size() * sizeof(int), cudaMemcpyHostToDevice) == cudaSuccess &&
-       cudaMemset(h->d_status, 0, sizeof(unsigned int)) == cudaSuccess;
+       cudaMemset(h->d_status, 0, sizeof(unsigned int)) == cudaSuccess &&
+       cudaMemset(h->d_fp64_count, 0, sizeof(unsigned long long)) == cudaSuccess;
   if (!ok) {
     dq_destroy(h);
     return DQ_ERR_CUDA;
@@ -393,6 +605,7 @@ dq_status dq_destroy(dq_handle h) {
   cudaFree(h->d_pair_of);
   cudaFree(h->d_pair_ij);
   cudaFree(h->d_status);
+  cudaFree(h->d_fp64_count);
   if (h->prof) {
     for (cudaEvent_t e : h->prof->pool) cudaEventDestroy(e);
     delete h->prof;
@@ -427,7 +640,7 @@ dq_status dq_workspace_size(dq_handle h, int64_t B, int32_t op, size_t* bytes) {
     case DQ_OP_EVAL: *bytes = plan_forward(*h, Bc, false, el).total; return DQ_OK;
     case DQ_OP_LOCAL_ENERGY: *bytes = plan_forward(*h, Bc, true, el).total; return DQ_OK;
     case DQ_OP_MCMC: *bytes = plan_mcmc(*h, std::max<int64_t>(B, 1), el).total; return DQ_OK;
-    case DQ_OP_GRAD: *bytes = 0; return DQ_ERR_UNSUPPORTED;
+    case DQ_OP_GRAD: *bytes = plan_grad(*h, Bc, el).total; return DQ_OK;
     case DQ_OP_LOSS_WEIGHTS: *bytes = loss_scratch_bytes(std::max<int64_t>(B, 1)); return DQ_OK;
   }
   return DQ_ERR_ARG;
@@ -496,10 +709,23 @@ dq_status mcmc_step(dq_handle h, const void* params, void* r, void* logabs, int6
 
 dq_status grad_logpsi(dq_handle h, const void* params, const void* r, int64_t B, const void* weights, int32_t mode,
                       void* grad_out, void* ws, size_t ws_bytes, void* stream) {
-  (void)params; (void)r; (void)B; (void)weights; (void)mode; (void)grad_out; (void)ws; (void)ws_bytes; (void)stream;
   dq_status st = check_handle(h);
   if (st != DQ_OK) return st;
-  return DQ_ERR_UNSUPPORTED;
+  if (B < 0 || (mode != 0 && mode != 1)) return DQ_ERR_ARG;
+  if (!params || !grad_out || (B > 0 && !r) || (mode == 0 && B > 0 && !weights)) return DQ_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t el = elem_size(*h);
+  if (B == 0) {
+    if (mode == 0 && cudaMemsetAsync(grad_out, 0, (size_t)h->off.total * el, s) != cudaSuccess) return DQ_ERR_CUDA;
+    return DQ_OK;
+  }
+  auto* w = static_cast<unsigned char*>(ws);
+  const void* wt = mode == 0 ? weights : nullptr;
+  if (h->precision == DQ_FP64)
+    return run_grad<double>(*h, (const double*)params, (const double*)r, B, (const double*)wt, mode, (double*)grad_out,
+                            w, ws_bytes, s);
+  return run_grad<float>(*h, (const float*)params, (const float*)r, B, (const float*)wt, mode, (float*)grad_out, w,
+                         ws_bytes, s);
 }
 
 dq_status vmc_loss_weights(dq_handle h, const void* e_loc, int64_t B, double clip_k, void* weights, double* stats,
@@ -573,6 +799,19 @@ dq_status dq_profile_read(dq_handle h, int32_t kind, double* total_ms, int64_t* 
 }
 
 const char* dq_profile_kind_name(int32_t kind) { return prof_kind_name(kind); }
+
+dq_status dq_fp64_matrix_count(dq_handle h, void* stream, int64_t* count) {
+  dq_status st = check_handle(h);
+  if (st != DQ_OK) return st;
+  if (!count) return DQ_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long v = 0;
+  DQ_CU(cudaMemcpyAsync(&v, h->d_fp64_count, sizeof(v), cudaMemcpyDeviceToHost, s));
+  DQ_CU(cudaStreamSynchronize(s));
+  DQ_CU(cudaMemsetAsync(h->d_fp64_count, 0, sizeof(v), s));
+  *count = (int64_t)v;
+  return DQ_OK;
+}
 
 int32_t dq_profile_kind_count(void) { return PK_COUNT; }
 

@@ -1,0 +1,555 @@
+// Reverse pass of the value-only network: d log|psi| / d theta (Sec. 4.1,
+// Eq. 30 needs grad_theta log|psi| per walker).
+//
+// The seed of walker b is its weight w_b (weighted mode) or 1 (per-walker
+// mode); walkers with psi = 0 get seed 0.  Adjoints flow backwards through
+//   log|psi| = log|sum_p c_p det A_up^p det A_dn^p| + J + gamma   (Eqs. 21, 24, 25, 28)
+// with d log|psi_D| / d log|det A^{s,p}| = w_p (the signed weight of pair p in
+// the log-sum-exp) and d log|det A| / d A = A^-T; then through the orbital
+// head and envelopes (Eqs. 19-20), and per layer through the residual tanh
+// update (Eq. 18), the graph-convolution messages (Eq. 17), the node map and
+// the edge filters.  Parameter gradients are sums over rows (electrons, edges
+// or walkers) of products of an adjoint and a saved activation; they are
+// formed by param_reduce, per walker or summed over walkers.
+#include <math.h>
+
+#include "backward.cuh"
+
+namespace dq {
+namespace {
+
+inline unsigned nblocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Combination over determinant pairs and Jastrow factor.  One warp per walker.
+//   beta[b][p]  = g_b w_p      (adjoint of log|det A^{s,p}|, both spins)
+//   cbar[b][p]  = g_b q_p,     q_p = det A_up^p det A_dn^p / psi_D
+//   jhbar[b][a] = g_b w_J2[a] (1 - t_a^2),  t = tanh(W_J1 s + b_J1)
+//   gt[b][a]    = g_b t_a      (adjoint of w_J2)
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void bwd_combine_kernel(const double* __restrict__ det, const T* __restrict__ jh,
+                                   const T* __restrict__ params, const T* __restrict__ weights, int64_t Bc, int N,
+                                   int K, int D, int64_t c_off, int64_t wJ2_off, int use_jastrow,
+                                   T* __restrict__ beta, T* __restrict__ cbar, T* __restrict__ jhbar,
+                                   T* __restrict__ gt) {
+  const int lane = threadIdx.x % 32;
+  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  if (b >= Bc) return;
+  const int N3 = 3 * N;
+  const double* db = det + b * 2 * K * (N3 + 3);
+  auto dp = [&](int s, int p) { return db + ((int64_t)s * K + p) * (N3 + 3); };
+  // lmax and the signed sum (same reduction as the forward combine)
+  double lmax = -INFINITY;
+  for (int p = lane; p < K; p += 32) {
+    const double cp = (double)params[c_off + p];
+    const double sp = dp(0, p)[0] * dp(1, p)[0] * (cp > 0 ? 1.0 : cp < 0 ? -1.0 : 0.0);
+    if (sp != 0.0) lmax = fmax(lmax, dp(0, p)[1] + dp(1, p)[1] + log(fabs(cp)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+  double S = 0.0;
+  if (lmax > -INFINITY)
+    for (int p = lane; p < K; p += 32) {
+      const double cp = (double)params[c_off + p];
+      const double sp = dp(0, p)[0] * dp(1, p)[0] * (cp > 0 ? 1.0 : cp < 0 ? -1.0 : 0.0);
+      if (sp != 0.0) S += sp * exp(dp(0, p)[1] + dp(1, p)[1] + log(fabs(cp)) - lmax);
+    }
+  S = warp_sum_d(S);
+  double g = weights ? (double)weights[b] : 1.0;
+  if (!(S != 0.0) || !isfinite(S)) g = 0.0;  // psi = 0: no gradient
+  for (int p = lane; p < K; p += 32) {
+    const double s2 = dp(0, p)[0] * dp(1, p)[0];
+    double q = 0.0;
+    if (g != 0.0 && s2 != 0.0) q = s2 * exp(dp(0, p)[1] + dp(1, p)[1] - lmax) / S;
+    const double cp = (double)params[c_off + p];
+    cbar[b * K + p] = (T)(g * q);
+    beta[b * K + p] = (T)(g * q * cp);
+  }
+  for (int a = lane; a < D; a += 32) {
+    double jb = 0.0, tt = 0.0;
+    if (use_jastrow) {
+      const double t = tanh((double)jh[b * D + a]);
+      jb = g * (double)params[wJ2_off + a] * (1.0 - t * t);
+      tt = g * t;
+    }
+    jhbar[b * D + a] = (T)jb;
+    gt[b * D + a] = (T)tt;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Determinants and envelopes.  One warp per (walker, spin, p).
+//   Abar = beta_p A^-T;  phibar_ik = Abar_ik env_ik;  envbar_ik = Abar_ik phi_ik
+//   omegabar_oI = sum_i envbar_ik exp(-zeta_oI d_iI)
+//   zetabar_oI  = sum_i envbar_ik omega_oI (-d_iI) exp(-zeta_oI d_iI)
+// A^-1 from an FP64 LU (the backward runs once per optimisation step).
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(128)
+    bwd_det_kernel(const T* __restrict__ phi, const T* __restrict__ geo, const T* __restrict__ params,
+                   const T* __restrict__ beta, int64_t Bc, int N, int n_up, int M, int K, int Wo, int E, int n_ee,
+                   int64_t om_up, int64_t om_dn, int64_t ze_up, int64_t ze_dn, T* __restrict__ phibar,
+                   T* __restrict__ envbar) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int warps = blockDim.x / 32;
+  const int64_t gw = (int64_t)blockIdx.x * warps + warp;
+  const int n_dn = N - n_up;
+  const int nmax = n_up > n_dn ? n_up : n_dn;
+  const int nn = nmax * nmax;
+  const size_t per_warp = (size_t)nn * (2 * sizeof(double) + 2 * sizeof(T)) + 32 * sizeof(int);
+  unsigned char* base = smem_raw + warp * ((per_warp + 15) / 16 * 16);
+  double* LU = reinterpret_cast<double*>(base);
+  double* Ainv = LU + nn;
+  T* env = reinterpret_cast<T*>(Ainv + nn);
+  T* phi0 = env + nn;
+  int* perm = reinterpret_cast<int*>(phi0 + nn);
+  if (gw >= Bc * 2 * K) return;
+  const int64_t b = gw / (2 * K);
+  const int s = (int)((gw / K) % 2);
+  const int p = (int)(gw % K);
+  const int n = s == 0 ? n_up : n_dn;
+  const int i0 = s == 0 ? 0 : n_up;
+  if (n == 0) return;
+  const T* om = params + (s == 0 ? om_up : om_dn);
+  const T* ze = params + (s == 0 ? ze_up : ze_dn);
+  const T* gb = geo + b * E * 4;
+  const T* phib = phi + b * N * Wo;
+  const double bp = (double)beta[b * K + p];
+  // envbar staging [Bc][spin][omega|zeta][K*nmax][M]; rows o = p*n + k
+  T* ebo = envbar + ((b * 2 + s) * 2 + 0) * (int64_t)K * nmax * M;
+  T* ebz = envbar + ((b * 2 + s) * 2 + 1) * (int64_t)K * nmax * M;
+  for (int q = lane; q < n * n; q += 32) {
+    const int ii = q / n, k = q % n, o = p * n + k, i = i0 + ii;
+    T ev = 0;
+    for (int I = 0; I < M; ++I) ev += om[o * M + I] * exp(-ze[o * M + I] * gb[(n_ee + i * M + I) * 4]);
+    env[q] = ev;
+    phi0[q] = phib[(int64_t)i * Wo + o];
+    LU[q] = (double)phi0[q] * (double)ev;
+  }
+  if (lane < n) perm[lane] = lane;
+  __syncwarp();
+  bool singular = false;
+  for (int j = 0; j < n; ++j) {
+    double v = (lane >= j && lane < n) ? fabs(LU[lane * n + j]) : -1.0;
+    int idx = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (v2 > v || (v2 == v && i2 < idx)) {
+        v = v2;
+        idx = i2;
+      }
+    }
+    if (!(v > 0.0)) {
+      singular = true;
+      break;
+    }
+    if (idx != j) {
+      for (int k = lane; k < n; k += 32) {
+        const double t = LU[j * n + k];
+        LU[j * n + k] = LU[idx * n + k];
+        LU[idx * n + k] = t;
+      }
+      if (lane == 0) {
+        const int t = perm[j];
+        perm[j] = perm[idx];
+        perm[idx] = t;
+      }
+    }
+    __syncwarp();
+    const double piv = LU[j * n + j];
+    for (int i = j + 1 + lane; i < n; i += 32) {
+      const double f = LU[i * n + j] / piv;
+      LU[i * n + j] = f;
+      for (int k = j + 1; k < n; ++k) LU[i * n + k] -= f * LU[j * n + k];
+    }
+    __syncwarp();
+  }
+  if (singular || bp == 0.0) {  // zero adjoint
+    for (int q = lane; q < n * n; q += 32) {
+      const int ii = q / n, k = q % n;
+      phibar[(b * N + i0 + ii) * (int64_t)Wo + p * n + k] = T(0);
+    }
+    for (int q = lane; q < n * M; q += 32) {
+      const int k = q / M, I = q % M;
+      ebo[(int64_t)(p * n + k) * M + I] = T(0);
+      ebz[(int64_t)(p * n + k) * M + I] = T(0);
+    }
+    return;
+  }
+  if (lane < n) {
+    const int col = lane;
+    for (int r = 0; r < n; ++r) {
+      double acc = perm[r] == col ? 1.0 : 0.0;
+      for (int m = 0; m < r; ++m) acc -= LU[r * n + m] * Ainv[m * n + col];
+      Ainv[r * n + col] = acc;
+    }
+    for (int r = n - 1; r >= 0; --r) {
+      double acc = Ainv[r * n + col];
+      for (int m = r + 1; m < n; ++m) acc -= LU[r * n + m] * Ainv[m * n + col];
+      Ainv[r * n + col] = acc / LU[r * n + r];
+    }
+  }
+  __syncwarp();
+  // phibar_ik = beta (A^-1)_ki env_ik
+  for (int q = lane; q < n * n; q += 32) {
+    const int ii = q / n, k = q % n;
+    const double abar = bp * Ainv[k * n + ii];
+    phibar[(b * N + i0 + ii) * (int64_t)Wo + p * n + k] = (T)(abar * (double)env[q]);
+  }
+  // envelope parameters: lanes over (k, I)
+  for (int q = lane; q < n * M; q += 32) {
+    const int k = q / M, I = q % M, o = p * n + k;
+    const double w = (double)om[o * M + I], z = (double)ze[o * M + I];
+    double ob = 0.0, zb = 0.0;
+    for (int ii = 0; ii < n; ++ii) {
+      const int i = i0 + ii;
+      const double d = (double)gb[(n_ee + i * M + I) * 4];
+      const double e = exp(-z * d);
+      const double envb = bp * Ainv[k * n + ii] * (double)phi0[ii * n + k];
+      ob += envb * e;
+      zb -= envb * w * d * e;
+    }
+    ebo[(int64_t)o * M + I] = (T)ob;
+    ebz[(int64_t)o * M + I] = (T)zb;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Y[r][n] (+)= sum_k X[r][k] W[k][n]   (W row-major [K][n_out]), any sizes.
+// ---------------------------------------------------------------------------
+constexpr int NB = 64, NK = 16;
+template <class T>
+__global__ void __launch_bounds__(256)
+    gemm_nn_kernel(const T* __restrict__ X, RowMap mx, const T* __restrict__ W, T* __restrict__ Y, RowMap my,
+                   int64_t rows, int n_out, int K, int accumulate) {
+  __shared__ T Xs[NK][NB + 1];
+  __shared__ T Ws[NK][NB + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int64_t r0 = (int64_t)blockIdx.x * NB;
+  const int n0 = blockIdx.y * NB;
+  T acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += NK) {
+    for (int e = threadIdx.x; e < NB * NK; e += 256) {
+      const int rr = e / NK, kk = e % NK;
+      const int64_t r = r0 + rr;
+      const int k = k0 + kk;
+      Xs[kk][rr] = (r < rows && k < K) ? X[(r / mx.rows_per_seg) * mx.seg_stride + (r % mx.rows_per_seg) * mx.ld + k]
+                                       : T(0);
+      const int kk2 = e / NB, nn2 = e % NB;
+      const int k2 = k0 + kk2, n2 = n0 + nn2;
+      Ws[kk2][nn2] = (k2 < K && n2 < n_out) ? W[(int64_t)k2 * n_out + n2] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < NK; ++kk) {
+      T a[4], w[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = Xs[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[j] = Ws[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * w[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t r = r0 + ty + 16 * i;
+    if (r >= rows) continue;
+    T* y = Y + (r / my.rows_per_seg) * my.seg_stride + (r % my.rows_per_seg) * my.ld;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n < n_out) y[n] = accumulate ? y[n] + acc[i][j] : acc[i][j];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Parameter reduction over rows:
+//   S_b[o][a] = sum_{r < rpw} X[b,r][o] * (Y ? Y[b,r][a] : 1)
+// per walker (mode 1): G[b][off + o*ld + a] = S_b
+// weighted   (mode 0): part[split][o][a] = sum over the split's walkers,
+//                      then reduce_splits adds sum_split part to G[off + ...].
+// Rows of walker b: row index b*rpw + r through the row maps.
+// ---------------------------------------------------------------------------
+constexpr int RT = 32;  // output tile (o, a)
+template <class T>
+__global__ void __launch_bounds__(256)
+    param_reduce_kernel(const T* __restrict__ X, RowMap mx, const T* __restrict__ Y, RowMap my, int rpw, int64_t nw,
+                        int n_o, int n_a, T* __restrict__ G, int64_t P, int64_t off, int ld, int mode,
+                        int64_t walkers_per_split, T* __restrict__ part) {
+  __shared__ T Xs[8][RT + 1];
+  __shared__ T Ys[8][RT + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int o0 = blockIdx.x * RT, a0 = blockIdx.y * RT;
+  int64_t wb0, wb1;
+  if (mode == 1) {
+    wb0 = blockIdx.z;
+    wb1 = wb0 + 1;
+  } else {
+    wb0 = (int64_t)blockIdx.z * walkers_per_split;
+    wb1 = min(nw, wb0 + walkers_per_split);
+  }
+  const int64_t r_begin = wb0 * rpw, r_end = wb1 * rpw;
+  T acc[2][2] = {};
+  for (int64_t rr0 = r_begin; rr0 < r_end; rr0 += 8) {
+    for (int e = threadIdx.x; e < 8 * RT; e += 256) {
+      const int k = e / RT, c = e % RT;
+      const int64_t r = rr0 + k;
+      const bool ok = r < r_end;
+      const int o = o0 + c, a = a0 + c;
+      Xs[k][c] = (ok && o < n_o) ? X[(r / mx.rows_per_seg) * mx.seg_stride + (r % mx.rows_per_seg) * mx.ld + o] : T(0);
+      Ys[k][c] = (ok && a < n_a) ? (Y ? Y[(r / my.rows_per_seg) * my.seg_stride + (r % my.rows_per_seg) * my.ld + a]
+                                      : T(1))
+                                 : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const T x0 = Xs[k][ty], x1 = Xs[k][ty + 16];
+      const T y0 = Ys[k][tx], y1 = Ys[k][tx + 16];
+      acc[0][0] += x0 * y0;
+      acc[0][1] += x0 * y1;
+      acc[1][0] += x1 * y0;
+      acc[1][1] += x1 * y1;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int o = o0 + ty + 16 * i, a = a0 + tx + 16 * j;
+      if (o >= n_o || a >= n_a) continue;
+      if (mode == 1)
+        G[wb0 * P + off + (int64_t)o * ld + a] = acc[i][j];
+      else
+        part[((int64_t)blockIdx.z * n_o + o) * n_a + a] = acc[i][j];
+    }
+}
+
+template <class T>
+__global__ void reduce_splits_kernel(const T* __restrict__ part, int splits, int n_o, int n_a, T* __restrict__ G,
+                                     int64_t off, int ld) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)n_o * n_a) return;
+  T acc = 0;
+  for (int s = 0; s < splits; ++s) acc += part[(int64_t)s * n_o * n_a + e];
+  const int o = (int)(e / n_a), a = (int)(e % n_a);
+  G[off + (int64_t)o * ld + a] += acc;
+}
+
+// out[r][a] = g[r][a] * (1 - t^2), t = tanh(u[r][a]) (is_tanh_of_u) or t = u.
+template <class T>
+__global__ void tanh_bwd_kernel(const T* __restrict__ g, const T* __restrict__ u, int64_t n, int is_pre,
+                                T* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const T t = is_pre ? tanh(u[e]) : u[e];
+  out[e] = g[e] * (T(1) - t * t);
+}
+
+// fbar[b][i][a] += sbar[b][a] for every electron i (the Jastrow input is sum_i f_i).
+template <class T>
+__global__ void add_rows_kernel(T* __restrict__ fbar, const T* __restrict__ sbar, int64_t Bc, int N, int D) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Bc * N * D) return;
+  const int64_t b = e / (N * D);
+  fbar[e] += sbar[b * D + e % D];
+}
+
+// ---------------------------------------------------------------------------
+// Message backward, Eq. (17).  One CTA per (walker, chunk of DC features);
+// thread (feature lane, sender j).  With m_i^t = nu_t(i) sum_j w_ij z_j:
+//   zbar_j   = sum_{i != j} nu_{t(i,j)}(i) mbar_i^{t(i,j)} w_ij
+//   wbar_ij  = nu(i) mbar_i^t z_j + nu(j) mbar_j^t z_i       (pair p = (i, j))
+//   wbar_iI  = mbar_i^nuc Y_I / M,   Ybar_I = sum_i mbar_i^nuc w_iI / M
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256)
+    msg_bwd_kernel(const T* __restrict__ mbar, const T* __restrict__ Z, const T* __restrict__ z0,
+                   const T* __restrict__ ew, const T* __restrict__ Y, const int* __restrict__ pair_ij,
+                   const int* __restrict__ pair_of, int N, int n_up,
+                   int M, int D, int E, int n_ee, int z_const, T* __restrict__ zbar, T* __restrict__ wbar,
+                   T* __restrict__ ybar) {
+  const int64_t b = blockIdx.x;
+  const int d = blockIdx.y * 32 + threadIdx.x % 32;
+  const int grp = threadIdx.x / 32, ngrp = blockDim.x / 32;
+  if (d >= D) return;
+  const int n_dn = N - n_up;
+  auto nu_s = [&](int i) { const int ns = i < n_up ? n_up : n_dn; return T(1) / T(ns - 1 > 1 ? ns - 1 : 1); };
+  auto nu_o = [&](int i) { const int no = i < n_up ? n_dn : n_up; return T(1) / T(no > 1 ? no : 1); };
+  const T* mb = mbar + b * N * 3 * D;
+  const T* ewb = ew + b * E * D;
+  auto zv = [&](int j) { return z_const ? z0[(j < n_up ? 0 : 1) * D + d] : Z[(b * N + j) * D + d]; };
+  auto m_in = [&](int i, int j) {  // mbar_i^t for the edge (i, j), normalised
+    const bool same = (i < n_up) == (j < n_up);
+    return same ? mb[(int64_t)i * 3 * D + d] * nu_s(i) : mb[(int64_t)i * 3 * D + D + d] * nu_o(i);
+  };
+  // zbar_j
+  for (int j = grp; j < N; j += ngrp) {
+    T acc = 0;
+    for (int i = 0; i < N; ++i) {
+      if (i == j) continue;
+      acc += m_in(i, j) * ewb[(int64_t)pair_of[i * N + j] * D + d];
+    }
+    zbar[(b * N + j) * D + d] = acc;
+  }
+  // wbar for e-e pairs
+  for (int e = grp; e < n_ee; e += ngrp) {
+    const int i = pair_ij[2 * e], j = pair_ij[2 * e + 1];
+    wbar[(b * E + e) * D + d] = m_in(i, j) * zv(j) + m_in(j, i) * zv(i);
+  }
+  // electron-nucleus edges and Ybar
+  const T nuM = T(1) / T(M);
+  for (int e = n_ee + grp; e < E; e += ngrp) {
+    const int i = (e - n_ee) / M, I = (e - n_ee) % M;
+    wbar[(b * E + e) * D + d] = mb[(int64_t)i * 3 * D + 2 * D + d] * nuM * Y[(int64_t)I * D + d];
+  }
+  for (int I = grp; I < M; I += ngrp) {
+    T acc = 0;
+    for (int i = 0; i < N; ++i) acc += mb[(int64_t)i * 3 * D + 2 * D + d] * ewb[(int64_t)(n_ee + i * M + I) * D + d];
+    ybar[(b * M + I) * D + d] = acc * nuM;
+  }
+}
+
+// F0[b][i][a] = E_spin[sigma_i][a]: the layer-0 embeddings of Eq. (13).
+template <class T>
+__global__ void fill_spin_rows_kernel(T* __restrict__ F0, const T* __restrict__ E_spin, int64_t Bc, int N, int n_up,
+                                      int D) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= Bc * N * D) return;
+  const int i = (int)((e / D) % N);
+  F0[e] = E_spin[(i < n_up ? 0 : 1) * D + e % D];
+}
+
+}  // namespace
+
+template <class T>
+cudaError_t launch_fill_spin_rows(T* F0, const T* E_spin, int64_t Bc, int N, int n_up, int D, cudaStream_t s) {
+  fill_spin_rows_kernel<T><<<nblocks(Bc * N * D, 256), 256, 0, s>>>(F0, E_spin, Bc, N, n_up, D);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <class T>
+cudaError_t launch_bwd_combine(const dq_handle_s& h, int64_t Bc, const double* det, const T* jh, const T* params,
+                               const T* weights, T* beta, T* cbar, T* jhbar, T* gt, cudaStream_t s) {
+  bwd_combine_kernel<T><<<nblocks(Bc * 32, 128), 128, 0, s>>>(det, jh, params, weights, Bc, h.N, h.K, h.D, h.off.c,
+                                                             h.off.w_J2, h.use_jastrow, beta, cbar, jhbar, gt);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_bwd_det(const dq_handle_s& h, int64_t Bc, const T* phi, const T* geo, const T* params, const T* beta,
+                           T* phibar, T* envbar, cudaStream_t s) {
+  const int nmax = h.n_up > h.n_dn ? h.n_up : h.n_dn;
+  const int nn = nmax * nmax;
+  const size_t per_warp = ((size_t)nn * (2 * sizeof(double) + 2 * sizeof(T)) + 32 * sizeof(int) + 15) / 16 * 16;
+  const int warps = 4;
+  const size_t smem = per_warp * warps;
+  auto kern = bwd_det_kernel<T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<nblocks(Bc * 2 * h.K, warps), warps * 32, smem, s>>>(
+      phi, geo, params, beta, Bc, h.N, h.n_up, h.M, h.K, h.K * nmax, h.edges.n_all, h.edges.n_ee, h.off.omega[0],
+      h.off.omega[1], h.off.zeta[0], h.off.zeta[1], phibar, envbar);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t gemm_nn(const T* X, RowMap mx, const T* W, T* Y, RowMap my, int64_t rows, int n_out, int K,
+                    bool accumulate, cudaStream_t s) {
+  if (rows <= 0 || n_out <= 0 || K <= 0) return cudaSuccess;
+  dim3 grid(nblocks(rows, NB), nblocks(n_out, NB));
+  gemm_nn_kernel<T><<<grid, 256, 0, s>>>(X, mx, W, Y, my, rows, n_out, K, accumulate ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t param_reduce(const T* X, RowMap mx, const T* Y, RowMap my, int rpw, int64_t nw, int n_o, int n_a, T* G,
+                         int64_t P, int64_t off, int ld, int mode, T* part, int64_t part_elems, cudaStream_t s) {
+  if (nw <= 0 || n_o <= 0 || n_a <= 0) return cudaSuccess;
+  if (rpw <= 0) return cudaSuccess;
+  const unsigned gx = nblocks(n_o, RT), gy = nblocks(n_a, RT);
+  if (mode == 1) {
+    // grid.z is limited to 65535: loop over walker slices
+    for (int64_t w0 = 0; w0 < nw; w0 += 65535) {
+      const int64_t nws = nw - w0 < 65535 ? nw - w0 : 65535;
+      dim3 grid(gx, gy, (unsigned)nws);
+      // offset the row maps by whole walkers: rows of walker w0 start at w0*rpw
+      const int64_t r_off = w0 * rpw;
+      const T* Xo = X + (r_off / mx.rows_per_seg) * mx.seg_stride + (r_off % mx.rows_per_seg) * mx.ld;
+      const T* Yo = Y ? Y + (r_off / my.rows_per_seg) * my.seg_stride + (r_off % my.rows_per_seg) * my.ld : nullptr;
+      param_reduce_kernel<T><<<grid, 256, 0, s>>>(Xo, mx, Yo, my, rpw, nws, n_o, n_a, G + w0 * P, P, off, ld, 1, 1,
+                                                  nullptr);
+    }
+    return cudaGetLastError();
+  }
+  // weighted: choose the split count so that the partial sums fit the scratch
+  int64_t splits = (nw + 63) / 64;
+  const int64_t per = (int64_t)n_o * n_a;
+  if (splits * per > part_elems) splits = part_elems / per;
+  if (splits < 1) return cudaErrorInvalidValue;
+  if (splits > 65535) splits = 65535;
+  const int64_t wps = (nw + splits - 1) / splits;
+  splits = (nw + wps - 1) / wps;
+  dim3 grid(gx, gy, (unsigned)splits);
+  param_reduce_kernel<T><<<grid, 256, 0, s>>>(X, mx, Y, my, rpw, nw, n_o, n_a, G, P, off, ld, 0, wps, part);
+  reduce_splits_kernel<T><<<nblocks(per, 256), 256, 0, s>>>(part, (int)splits, n_o, n_a, G, off, ld);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_tanh_bwd(const T* g, const T* u, int64_t n, bool is_pre, T* out, cudaStream_t s) {
+  tanh_bwd_kernel<T><<<nblocks(n, 256), 256, 0, s>>>(g, u, n, is_pre ? 1 : 0, out);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_add_rows(T* fbar, const T* sbar, int64_t Bc, int N, int D, cudaStream_t s) {
+  add_rows_kernel<T><<<nblocks(Bc * N * D, 256), 256, 0, s>>>(fbar, sbar, Bc, N, D);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_msg_bwd(const dq_handle_s& h, int64_t Bc, const T* mbar, const T* Z, const T* z0, const T* ew,
+                           const T* Y, bool z_const, T* zbar, T* wbar, T* ybar, cudaStream_t s) {
+  dim3 grid((unsigned)Bc, nblocks(h.D, 32));
+  msg_bwd_kernel<T><<<grid, 256, 0, s>>>(mbar, Z, z0, ew, Y, h.d_pair_ij, h.d_pair_of, h.N, h.n_up, h.M, h.D, h.edges.n_all,
+                                          h.edges.n_ee, z_const ? 1 : 0, zbar, wbar, ybar);
+  return cudaGetLastError();
+}
+
+#define DQ_BWD_INST(T)                                                                                             \
+  template cudaError_t launch_bwd_combine<T>(const dq_handle_s&, int64_t, const double*, const T*, const T*,       \
+                                             const T*, T*, T*, T*, T*, cudaStream_t);                             \
+  template cudaError_t launch_bwd_det<T>(const dq_handle_s&, int64_t, const T*, const T*, const T*, const T*, T*, \
+                                         T*, cudaStream_t);                                                       \
+  template cudaError_t gemm_nn<T>(const T*, RowMap, const T*, T*, RowMap, int64_t, int, int, bool, cudaStream_t); \
+  template cudaError_t param_reduce<T>(const T*, RowMap, const T*, RowMap, int, int64_t, int, int, T*, int64_t,   \
+                                       int64_t, int, int, T*, int64_t, cudaStream_t);                             \
+  template cudaError_t launch_tanh_bwd<T>(const T*, const T*, int64_t, bool, T*, cudaStream_t);                   \
+  template cudaError_t launch_add_rows<T>(T*, const T*, int64_t, int, int, cudaStream_t);                         \
+  template cudaError_t launch_fill_spin_rows<T>(T*, const T*, int64_t, int, int, int, cudaStream_t);              \
+  template cudaError_t launch_msg_bwd<T>(const dq_handle_s&, int64_t, const T*, const T*, const T*, const T*,     \
+                                         const T*, bool, T*, T*, T*, cudaStream_t);
+DQ_BWD_INST(float)
+DQ_BWD_INST(double)
+
+}  // namespace dq

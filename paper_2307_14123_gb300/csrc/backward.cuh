@@ -1,0 +1,33 @@
+// Launchers of the reverse pass (backward.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace dq {
+
+template <class T>
+cudaError_t launch_bwd_combine(const dq_handle_s& h, int64_t Bc, const double* det, const T* jh, const T* params,
+                               const T* weights, T* beta, T* cbar, T* jhbar, T* gt, cudaStream_t s);
+template <class T>
+cudaError_t launch_bwd_det(const dq_handle_s& h, int64_t Bc, const T* phi, const T* geo, const T* params, const T* beta,
+                           T* phibar, T* envbar, cudaStream_t s);
+// Y[r][n] (+)= sum_k X[r][k] W[k][n], W row-major [K][n_out]; any sizes.
+template <class T>
+cudaError_t gemm_nn(const T* X, RowMap mx, const T* W, T* Y, RowMap my, int64_t rows, int n_out, int K,
+                    bool accumulate, cudaStream_t s);
+// Parameter gradient block from rows: per walker (mode 1) writes G[b][off + o*ld + a],
+// summed over walkers (mode 0) adds to G[off + o*ld + a]; Y == nullptr means ones.
+template <class T>
+cudaError_t param_reduce(const T* X, RowMap mx, const T* Y, RowMap my, int rpw, int64_t nw, int n_o, int n_a, T* G,
+                         int64_t P, int64_t off, int ld, int mode, T* part, int64_t part_elems, cudaStream_t s);
+template <class T>
+cudaError_t launch_tanh_bwd(const T* g, const T* u, int64_t n, bool is_pre, T* out, cudaStream_t s);
+template <class T>
+cudaError_t launch_add_rows(T* fbar, const T* sbar, int64_t Bc, int N, int D, cudaStream_t s);
+template <class T>
+cudaError_t launch_fill_spin_rows(T* F0, const T* E_spin, int64_t Bc, int N, int n_up, int D, cudaStream_t s);
+template <class T>
+cudaError_t launch_msg_bwd(const dq_handle_s& h, int64_t Bc, const T* mbar, const T* Z, const T* z0, const T* ew,
+                           const T* Y, bool z_const, T* zbar, T* wbar, T* ybar, cudaStream_t s);
+
+}  // namespace dq

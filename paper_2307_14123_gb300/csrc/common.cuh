@@ -89,6 +89,7 @@ struct dq_handle_s {
   int* d_pair_of = nullptr;  // [N][N] pair index of (i, j), -1 on the diagonal
   int* d_pair_ij = nullptr;  // [n_ee][2] (i, j) with i < j
   unsigned int* d_status = nullptr;
+  unsigned long long* d_fp64_count = nullptr;  // determinant matrices that took the FP64 path
   dq::Profiler* prof = nullptr;
 };
 
@@ -145,6 +146,9 @@ cudaError_t launch_messages(const dq_handle_s& h, const FwdDims& d, const T* par
 template <class T>
 cudaError_t launch_update(const dq_handle_s& h, const FwdDims& d, const T* params, bool from_spin,
                           FwdBuffers<T> b, cudaStream_t s);
+template <class T>
+cudaError_t launch_update_io(const dq_handle_s& h, const FwdDims& d, const T* params, bool from_spin, const T* P,
+                             const T* Fin, T* Fout, cudaStream_t s);
 template <class T>
 cudaError_t launch_orbital_det(const dq_handle_s& h, const FwdDims& d, const T* params, FwdBuffers<T> b,
                                cudaStream_t s);

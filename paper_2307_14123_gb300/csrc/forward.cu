@@ -81,35 +81,57 @@ __global__ void geometry_kernel(const T* __restrict__ r, const T* __restrict__ R
 }
 
 // Edge hidden layer a = tanh(W1 e + b1) as a jet in d: (a, a', a'').
+// W1 and b1 of the three edge types are staged in shared memory ([t][q][a],
+// conflict-free across the feature lanes); each CTA streams kEdgesPerCta
+// consecutive (walker, edge) rows, threads over features.
+constexpr int kEdgesPerCta = 32;
+constexpr int kHiddenThreads = 128;
+
 template <class T>
-__global__ void edge_hidden_kernel(const T* __restrict__ rbf, const T* __restrict__ params, int64_t Bc, int E,
-                                   int n_par, int n_ee, int D, int Q, int ej, int64_t W1_0, int64_t W1_1,
-                                   int64_t W1_2, int64_t b1_0, int64_t b1_1, int64_t b1_2, T* __restrict__ eh) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= Bc * E * D) return;
-  const int a = (int)(gid % D);
-  const int64_t be = gid / D;
-  const int e = (int)(be % E);
-  const int t = e < n_par ? 0 : (e < n_ee ? 1 : 2);
-  const T* W1 = params + (t == 0 ? W1_0 : t == 1 ? W1_1 : W1_2) + (int64_t)a * Q;
-  const T b1 = params[(t == 0 ? b1_0 : t == 1 ? b1_1 : b1_2) + a];
-  const T* f = rbf + be * ej * Q;
-  T h = b1, h1 = 0, h2 = 0;
-  for (int q = 0; q < Q; ++q) {
-    const T w = W1[q];
-    h += w * f[q];
-    if (ej == 3) {
-      h1 += w * f[Q + q];
-      h2 += w * f[2 * Q + q];
-    }
+__global__ void __launch_bounds__(kHiddenThreads)
+    edge_hidden_kernel(const T* __restrict__ rbf, const T* __restrict__ params, int64_t Bc, int E, int n_par,
+                       int n_ee, int D, int Q, int ej, int64_t W1_0, int64_t W1_1, int64_t W1_2, int64_t b1_0,
+                       int64_t b1_1, int64_t b1_2, T* __restrict__ eh) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ws = reinterpret_cast<T*>(smem_raw);  // [3][Q][D]
+  T* bs = Ws + 3 * Q * D;                  // [3][D]
+  T* fs = bs + 3 * D;                      // [kEdgesPerCta][ej][Q] features of this CTA's rows
+  const int64_t W1o[3] = {W1_0, W1_1, W1_2}, b1o[3] = {b1_0, b1_1, b1_2};
+  for (int k = threadIdx.x; k < 3 * Q * D; k += kHiddenThreads) {
+    const int t = k / (Q * D), q = (k / D) % Q, a = k % D;
+    Ws[k] = params[W1o[t] + (int64_t)a * Q + q];
   }
-  const T av = tanh_t(h);
-  T* o = eh + be * ej * D + a;
-  o[0] = av;
-  if (ej == 3) {
-    const T da = T(1) - av * av;
-    o[D] = da * h1;
-    o[2 * D] = da * h2 - T(2) * av * da * h1 * h1;
+  for (int k = threadIdx.x; k < 3 * D; k += kHiddenThreads) bs[k] = params[b1o[k / D] + k % D];
+  const int64_t be0 = (int64_t)blockIdx.x * kEdgesPerCta;
+  const int64_t nrows = Bc * E;
+  const int nb = (int)min((int64_t)kEdgesPerCta, nrows - be0);
+  for (int k = threadIdx.x; k < nb * ej * Q; k += kHiddenThreads) fs[k] = rbf[be0 * ej * Q + k];
+  __syncthreads();
+  for (int r = 0; r < nb; ++r) {
+    const int64_t be = be0 + r;
+    const int e = (int)(be % E);
+    const int t = e < n_par ? 0 : (e < n_ee ? 1 : 2);
+    const T* W = Ws + t * Q * D;
+    const T* f = fs + r * ej * Q;
+    for (int a = threadIdx.x; a < D; a += kHiddenThreads) {
+      T h = bs[t * D + a], h1 = 0, h2 = 0;
+      for (int q = 0; q < Q; ++q) {
+        const T w = W[q * D + a];
+        h += w * f[q];
+        if (ej == 3) {
+          h1 += w * f[Q + q];
+          h2 += w * f[2 * Q + q];
+        }
+      }
+      const T av = tanh_t(h);
+      T* o = eh + be * ej * D + a;
+      o[0] = av;
+      if (ej == 3) {
+        const T da = T(1) - av * av;
+        o[D] = da * h1;
+        o[2 * D] = da * h2 - T(2) * av * da * h1 * h1;
+      }
+    }
   }
 }
 
@@ -126,92 +148,185 @@ __global__ void layer0_node_kernel(const T* __restrict__ params, int D, int64_t 
 
 // ---------------------------------------------------------------------------
 // Messages, Eq. (17), normalised per edge type, with the product rule.
-// One CTA per (walker, chunk of DC features).
+// One CTA per (walker, chunk of DC features); lanes run over features and the
+// whole chunk of node channels z[j][c] is staged in shared memory.
+//
+// Main part: for every feature d the messages are two masked N x N matrices
+// (same-spin / opposite-spin edge filters w_ij, zero diagonal) applied to the
+// N x C matrix z[j][c].  A thread owns an IB x CB block of (receiving
+// electron, channel) outputs inside one spin block, so every shared-memory
+// load feeds several FMAs.  The product-rule terms that involve derivatives
+// of w_ij (only the six coordinates of electrons i and j) and the
+// electron-nucleus messages are added afterwards for the same outputs.
 // ---------------------------------------------------------------------------
-template <class T, int DC>
-__global__ void __launch_bounds__(kThreads)
+template <class T, int DC, int IB, int CB>
+__global__ void __launch_bounds__(256)
     messages_kernel(const T* __restrict__ Z, const T* __restrict__ z0, const T* __restrict__ ew,
                     const T* __restrict__ geo, const T* __restrict__ Y, const int* __restrict__ pair_of, int N,
                     int n_up, int M, int C, int D, int E, int n_ee, int ej, int z_const, T* __restrict__ msg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* Zs = reinterpret_cast<T*>(smem_raw);                 // [N][C][DC] (or [2][DC] if z_const)
-  const int zs_elems = z_const ? 2 * DC : N * C * DC;
-  T* EWs = Zs + zs_elems;                                 // [E][ej][DC]
-  T* Ys = EWs + (int64_t)E * ej * DC;                     // [M][DC]
-  T* Gs = Ys + M * DC;                                    // [E][4]
-  int* Ps = reinterpret_cast<int*>(Gs + E * 4);           // [N][N]
+  const int zc_rows = z_const ? 2 : N * C;     // z[j][c] rows (two spin rows if z is constant)
+  T* Zs = reinterpret_cast<T*>(smem_raw);      // [zc_rows][DC]
+  T* Wm = Zs + zc_rows * DC;                   // [N*N][DC] w_ij, zero diagonal
+  T* W1p = Wm + N * N * DC;                    // [n_ee][DC] w'   (jets)
+  T* W2p = W1p + (ej == 3 ? n_ee * DC : 0);    // [n_ee][DC] w''  (jets)
+  T* WN = W2p + (ej == 3 ? n_ee * DC : 0);     // [N*M][ej][DC] electron-nucleus filter jets
+  T* Ys = WN + N * M * ej * DC;                // [M][DC]
+  T* Gs = Ys + M * DC;                         // [E][4]
+  int* Ps = reinterpret_cast<int*>(Gs + E * 4);  // [N][N]
 
   const int64_t b = blockIdx.x;
   const int d0 = blockIdx.y * DC;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const bool jets = C > 1;
+  const T* EWb = ew + b * E * ej * D;
 
+  for (int k = tid; k < N * N; k += nthr) Ps[k] = pair_of[k];
+  const T* Gb = geo + b * E * 4;
+  for (int k = tid; k < E * 4; k += nthr) Gs[k] = Gb[k];
   if (z_const) {
-    for (int k = tid; k < 2 * DC; k += kThreads) Zs[k] = z0[(k / DC) * D + d0 + k % DC];
+    for (int k = tid; k < 2 * DC; k += nthr) Zs[k] = z0[(k / DC) * D + d0 + k % DC];
   } else {
     const T* Zb = Z + b * N * C * D;
-    for (int k = tid; k < N * C * DC; k += kThreads) Zs[k] = Zb[(int64_t)(k / DC) * D + d0 + k % DC];
+    for (int k = tid; k < N * C * DC; k += nthr) Zs[k] = Zb[(int64_t)(k / DC) * D + d0 + k % DC];
   }
-  const T* EWb = ew + b * E * ej * D;
-  for (int k = tid; k < E * ej * DC; k += kThreads) EWs[k] = EWb[(int64_t)(k / DC) * D + d0 + k % DC];
-  for (int k = tid; k < M * DC; k += kThreads) Ys[k] = Y[(int64_t)(k / DC) * D + d0 + k % DC];
-  const T* Gb = geo + b * E * 4;
-  for (int k = tid; k < E * 4; k += kThreads) Gs[k] = Gb[k];
-  for (int k = tid; k < N * N; k += kThreads) Ps[k] = pair_of[k];
+  __syncthreads();
+  for (int k = tid; k < N * N * DC; k += nthr) {
+    const int ij = k / DC, dd = k % DC;
+    const int i = ij / N, j = ij % N;
+    Wm[k] = i == j ? T(0) : EWb[(int64_t)Ps[ij] * ej * D + d0 + dd];
+  }
+  if (ej == 3)
+    for (int k = tid; k < n_ee * DC; k += nthr) {
+      const int p = k / DC, dd = k % DC;
+      W1p[k] = EWb[((int64_t)p * 3 + 1) * D + d0 + dd];
+      W2p[k] = EWb[((int64_t)p * 3 + 2) * D + d0 + dd];
+    }
+  for (int k = tid; k < N * M * ej * DC; k += nthr) WN[k] = EWb[(int64_t)(n_ee * ej + k / DC) * D + d0 + k % DC];
+  for (int k = tid; k < M * DC; k += nthr) Ys[k] = Y[(int64_t)(k / DC) * D + d0 + k % DC];
   __syncthreads();
 
   const int n_dn = N - n_up;
-  const bool jets = C > 1;
   const int dd = tid % DC;
-  const int ngroups = kThreads / DC;
-  auto zval = [&](int j, int c) -> T {
+  const int ngroups = nthr / DC;
+  const int nib_up = (n_up + IB - 1) / IB, nib_dn = (n_dn + IB - 1) / IB;
+  const int ncb = (C + CB - 1) / CB;
+  const int ntasks = (nib_up + nib_dn) * ncb;
+  const T nuM = T(1) / T(M);
+  T* mb = msg + b * N * C * 3 * D + d0 + dd;
+  // z value: z[j][c] of this lane's feature
+  auto zv = [&](int j, int c) -> T {
     if (z_const) return c == 0 ? Zs[(j < n_up ? 0 : 1) * DC + dd] : T(0);
     return Zs[(j * C + c) * DC + dd];
   };
-  T* mb = msg + b * N * C * 3 * D;
-  for (int oc = tid / DC; oc < N * C; oc += ngroups) {
-    const int i = oc / C, c = oc % C;
-    const bool up_i = i < n_up;
-    const bool isJ = jets && c >= 1 && c < C - 1;
-    const bool isL = jets && c == C - 1;
-    const int ke = isJ ? (c - 1) / 3 : -1, kx = isJ ? (c - 1) % 3 : 0;
-    T acc_s = 0, acc_o = 0, acc_n = 0;
-    for (int j = 0; j < N; ++j) {
-      if (j == i) continue;
-      const int p = Ps[i * N + j];
-      const T sg = i < j ? T(1) : T(-1);  // unit vectors are stored for (min, max)
-      const T w = EWs[(p * ej) * DC + dd];
-      T v = w * zval(j, c);
-      if (isJ && (ke == i || ke == j)) {
-        const T t = EWs[(p * ej + 1) * DC + dd] * sg * Gs[p * 4 + 1 + kx] * zval(j, 0);
-        v += ke == i ? t : -t;
+
+  for (int task = tid / DC; task < ntasks; task += ngroups) {
+    const int ibk = task / ncb, cbk = task % ncb;
+    const bool up = ibk < nib_up;
+    const int sb0 = up ? 0 : n_up, sbn = up ? n_up : n_dn;  // spin block of the receivers
+    const int i0 = sb0 + (up ? ibk : ibk - nib_up) * IB;
+    const int ni = min(IB, sb0 + sbn - i0);
+    const int c0 = cbk * CB;
+    const int nc = min(CB, C - c0);
+    const int os0 = up ? n_up : 0, osn = up ? n_dn : n_up;  // opposite spin block (senders)
+    T as[IB][CB], ao[IB][CB];
+#pragma unroll
+    for (int a = 0; a < IB; ++a)
+#pragma unroll
+      for (int q = 0; q < CB; ++q) as[a][q] = ao[a][q] = T(0);
+
+    // main contraction
+    if (!z_const || c0 == 0) {
+      for (int j = sb0; j < sb0 + sbn; ++j) {
+        T zc[CB];
+#pragma unroll
+        for (int q = 0; q < CB; ++q) zc[q] = q < nc ? zv(j, c0 + q) : T(0);
+#pragma unroll
+        for (int a = 0; a < IB; ++a) {
+          if (a < ni) {
+            const T w = Wm[((i0 + a) * N + j) * DC + dd];
+#pragma unroll
+            for (int q = 0; q < CB; ++q) as[a][q] += w * zc[q];
+          }
+        }
       }
-      if (isL) {
-        const T w1 = EWs[(p * ej + 1) * DC + dd], w2 = EWs[(p * ej + 2) * DC + dd];
-        v += (T(2) * w2 + T(4) * w1 / Gs[p * 4]) * zval(j, 0);
-        T s = 0;
-        for (int x = 0; x < 3; ++x) s += sg * Gs[p * 4 + 1 + x] * (zval(j, 1 + 3 * i + x) - zval(j, 1 + 3 * j + x));
-        v += T(2) * w1 * s;
+      for (int j = os0; j < os0 + osn; ++j) {
+        T zc[CB];
+#pragma unroll
+        for (int q = 0; q < CB; ++q) zc[q] = q < nc ? zv(j, c0 + q) : T(0);
+#pragma unroll
+        for (int a = 0; a < IB; ++a) {
+          if (a < ni) {
+            const T w = Wm[((i0 + a) * N + j) * DC + dd];
+#pragma unroll
+            for (int q = 0; q < CB; ++q) ao[a][q] += w * zc[q];
+          }
+        }
       }
-      if ((j < n_up) == up_i)
-        acc_s += v;
-      else
-        acc_o += v;
     }
-    for (int I = 0; I < M; ++I) {
-      const int e = n_ee + i * M + I;
-      const T y = Ys[I * DC + dd];
-      if (c == 0) acc_n += EWs[(e * ej) * DC + dd] * y;
-      if (isJ && ke == i) acc_n += EWs[(e * ej + 1) * DC + dd] * Gs[e * 4 + 1 + kx] * y;
-      if (isL) acc_n += (EWs[(e * ej + 2) * DC + dd] + T(2) * EWs[(e * ej + 1) * DC + dd] / Gs[e * 4]) * y;
-    }
-    const int n_same = up_i ? n_up : n_dn, n_opp = up_i ? n_dn : n_up;
+
+    // product-rule corrections, nuclear messages, normalisation, store
+    const int n_same = up ? n_up : n_dn, n_opp = up ? n_dn : n_up;
     const T nu_s = T(1) / T(n_same - 1 > 1 ? n_same - 1 : 1);
     const T nu_o = T(1) / T(n_opp > 1 ? n_opp : 1);
-    const T nu_n = T(1) / T(M);
-    T* o = mb + ((int64_t)i * C + c) * 3 * D + d0 + dd;
-    o[0] = acc_s * nu_s;
-    o[D] = acc_o * nu_o;
-    o[2 * D] = acc_n * nu_n;
+#pragma unroll
+    for (int a = 0; a < IB; ++a) {
+      if (a >= ni) continue;
+      const int i = i0 + a;
+#pragma unroll
+      for (int q = 0; q < CB; ++q) {
+        if (q >= nc) continue;
+        const int c = c0 + q;
+        T s = as[a][q], o = ao[a][q], nn = 0;
+        const bool isJ = jets && c >= 1 && c < C - 1;
+        const bool isL = jets && c == C - 1;
+        if (isJ) {
+          const int e = (c - 1) / 3, x = (c - 1) % 3;
+          if (e == i) {
+            for (int j = 0; j < N; ++j) {
+              if (j == i) continue;
+              const int p = Ps[i * N + j];
+              const T u = (i < j ? Gs[p * 4 + 1 + x] : -Gs[p * 4 + 1 + x]);
+              const T t = W1p[p * DC + dd] * u * zv(j, 0);
+              if ((j < n_up) == up) s += t; else o += t;
+            }
+            for (int I = 0; I < M; ++I) {
+              const int en = i * M + I;
+              nn += WN[(en * ej + 1) * DC + dd] * Gs[(n_ee + en) * 4 + 1 + x] * Ys[I * DC + dd];
+            }
+          } else {
+            const int p = Ps[i * N + e];
+            const T u = (i < e ? Gs[p * 4 + 1 + x] : -Gs[p * 4 + 1 + x]);
+            const T t = W1p[p * DC + dd] * u * zv(e, 0);
+            if ((e < n_up) == up) s -= t; else o -= t;
+          }
+        } else if (isL) {
+          for (int j = 0; j < N; ++j) {
+            if (j == i) continue;
+            const int p = Ps[i * N + j];
+            const T w1 = W1p[p * DC + dd], w2 = W2p[p * DC + dd];
+            const T sg = i < j ? T(1) : T(-1);
+            T t = (T(2) * w2 + T(4) * w1 / Gs[p * 4]) * zv(j, 0);
+            T cr = 0;
+            for (int x = 0; x < 3; ++x)
+              cr += sg * Gs[p * 4 + 1 + x] * (zv(j, 1 + 3 * i + x) - zv(j, 1 + 3 * j + x));
+            t += T(2) * w1 * cr;
+            if ((j < n_up) == up) s += t; else o += t;
+          }
+          for (int I = 0; I < M; ++I) {
+            const int en = i * M + I;
+            nn += (WN[(en * ej + 2) * DC + dd] + T(2) * WN[(en * ej + 1) * DC + dd] / Gs[(n_ee + en) * 4]) *
+                  Ys[I * DC + dd];
+          }
+        } else if (c == 0) {
+          for (int I = 0; I < M; ++I) nn += WN[(i * M + I) * ej * DC + dd] * Ys[I * DC + dd];
+        }
+        T* out = mb + ((int64_t)i * C + c) * 3 * D;
+        out[0] = s * nu_s;
+        out[D] = o * nu_o;
+        out[2 * D] = nn * nuM;
+      }
+    }
   }
 }
 
@@ -219,7 +334,7 @@ __global__ void __launch_bounds__(kThreads)
 // Residual tanh update, Eq. (18): f <- f + tanh(P) with jets.
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void update_kernel(const T* __restrict__ P, T* __restrict__ F, const T* __restrict__ E_spin,
+__global__ void update_kernel(const T* __restrict__ P, const T* Fin, T* Fout, const T* __restrict__ E_spin,
                               int64_t Bc, int N, int n_up, int C, int D, int from_spin) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= Bc * N * D) return;
@@ -227,30 +342,178 @@ __global__ void update_kernel(const T* __restrict__ P, T* __restrict__ F, const 
   const int64_t bi = gid / D;
   const int i = (int)(bi % N);
   const T* p = P + bi * C * D + a;
-  T* f = F + bi * C * D + a;
+  const T* fi = Fin + bi * C * D + a;
+  T* f = Fout + bi * C * D + a;
   const T t = tanh_t(p[0]);
   const T dt = T(1) - t * t;
-  f[0] = (from_spin ? E_spin[(i < n_up ? 0 : 1) * D + a] : f[0]) + t;
+  f[0] = (from_spin ? E_spin[(i < n_up ? 0 : 1) * D + a] : fi[0]) + t;
   if (C > 1) {
     T ss = 0;
     for (int c = 1; c < C - 1; ++c) {
       const T pc = p[(int64_t)c * D];
       ss += pc * pc;
-      f[(int64_t)c * D] = (from_spin ? T(0) : f[(int64_t)c * D]) + dt * pc;
+      f[(int64_t)c * D] = (from_spin ? T(0) : fi[(int64_t)c * D]) + dt * pc;
     }
     const int64_t cl = (int64_t)(C - 1) * D;
-    f[cl] = (from_spin ? T(0) : f[cl]) + dt * p[cl] - T(2) * t * dt * ss;
+    f[cl] = (from_spin ? T(0) : fi[cl]) + dt * p[cl] - T(2) * t * dt * ss;
   }
 }
 
 // ---------------------------------------------------------------------------
 // Orbitals x envelopes and determinant jets.  One warp per (walker, spin, p).
+//
+// Value-only calls (ansatz_eval, Metropolis) in FP32 mode factorise every
+// matrix in FP32 first (LU with warp-level partial pivoting).  A condition
+// estimate of the row-equilibrated matrix, kappa = n max_{k,i} |(A^-1)_ki| r_i
+// with r_i = max_k |A_ik| (row scaling by the envelopes does not hurt the
+// pivoted LU), decides whether that is accurate enough: near-nodal matrices
+// (kappa above the threshold) are redone in FP64.  The local-energy path
+// needs the determinant derivatives (tangent contractions with A^-1), whose
+// FP32 rounding doubles the error of E_loc at near-nodal walkers; it takes
+// the FP64 path for every matrix.  FP64 instructions issue at a small
+// fraction of the FP32 rate on this GPU.  In FP64 mode every matrix is FP64.
 // ---------------------------------------------------------------------------
+#ifndef DQ_KAPPA_FP32_VALUE
+#define DQ_KAPPA_FP32_VALUE 1000.0f  // value-only log|det| in FP32 below this
+#endif
+
+template <class S>
+__device__ __forceinline__ S warp_max(S v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// In-place LU with partial pivoting of the n x n matrix LU (row-major, shared
+// memory) by one warp; perm records the row order.  Returns false if a zero
+// pivot appears.  sign and logabs of the determinant are accumulated.
+template <class S>
+__device__ bool warp_lu(S* LU, int* perm, int n, int lane, int* sign_out, double* logabs_out) {
+  if (lane < n) perm[lane] = lane;
+  __syncwarp();
+  int sign = 1;
+  S la = 0;
+  for (int j = 0; j < n; ++j) {
+    S v = (lane >= j && lane < n) ? fabs(LU[lane * n + j]) : S(-1);
+    int idx = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const S v2 = __shfl_xor_sync(0xffffffffu, v, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (v2 > v || (v2 == v && i2 < idx)) {
+        v = v2;
+        idx = i2;
+      }
+    }
+    if (!(v > S(0))) return false;
+    if (idx != j) {
+      for (int k = lane; k < n; k += 32) {
+        const S t = LU[j * n + k];
+        LU[j * n + k] = LU[idx * n + k];
+        LU[idx * n + k] = t;
+      }
+      if (lane == 0) {
+        const int t = perm[j];
+        perm[j] = perm[idx];
+        perm[idx] = t;
+      }
+      sign = -sign;
+    }
+    __syncwarp();
+    const S piv = LU[j * n + j];
+    for (int i = j + 1 + lane; i < n; i += 32) {
+      const S f = LU[i * n + j] / piv;
+      LU[i * n + j] = f;
+      for (int k = j + 1; k < n; ++k) LU[i * n + k] -= f * LU[j * n + k];
+    }
+    __syncwarp();
+    if (piv < S(0)) sign = -sign;
+    if (lane == (j & 31)) la += log(fabs(piv));  // one lane per pivot, summed below
+  }
+  *sign_out = sign;
+  double l = (double)la;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+  *logabs_out = l;
+  return true;
+}
+
+// A^-1 from the LU factors: lane `col` solves L U x = P e_col.
+template <class S>
+__device__ void warp_inverse(const S* LU, const int* perm, int n, int lane, S* Ainv) {
+  if (lane < n) {
+    const int col = lane;
+    for (int r = 0; r < n; ++r) {
+      S acc = perm[r] == col ? S(1) : S(0);
+      for (int m = 0; m < r; ++m) acc -= LU[r * n + m] * Ainv[m * n + col];
+      Ainv[r * n + col] = acc;
+    }
+    for (int r = n - 1; r >= 0; --r) {
+      S acc = Ainv[r * n + col];
+      for (int m = r + 1; m < n; ++m) acc -= LU[r * n + m] * Ainv[m * n + col];
+      Ainv[r * n + col] = acc / LU[r * n + r];
+    }
+  }
+  __syncwarp();
+}
+
+// Determinant derivatives: for every tangent t (3N coordinates, then the
+// Laplacian channel) build d_t A into tmp and accumulate
+// grad[t] = tr(A^-1 d_t A) and lap = tr(A^-1 L A) - sum_t tr((A^-1 d_t A)^2)
+// in arithmetic S.
+template <class T, class S>
+__device__ double det_tangents(const T* phib, const T* env, const T* jenv, const T* lenv, const T* phi0, const S* Ainv,
+                               S* tmp, S* X, int n, int nn, int i0, int p, int C, int Wo, int N3, int lane,
+                               double* out) {
+  double lap = 0.0;
+  for (int t = 0; t <= N3; ++t) {
+    const bool is_lap = t == N3;
+    const int c = is_lap ? C - 1 : 1 + t;
+    for (int q = lane; q < n * n; q += 32) {
+      const int ii = q / n, k = q % n, o = p * n + k, i = i0 + ii;
+      const T* ph = phib + (int64_t)i * C * Wo + o;
+      T v = ph[(int64_t)c * Wo] * env[q];
+      if (is_lap) {
+        v += phi0[q] * lenv[q];
+        for (int x = 0; x < 3; ++x) v += T(2) * ph[(int64_t)(1 + 3 * i + x) * Wo] * jenv[x * nn + q];
+      } else if (t / 3 == i) {
+        v += phi0[q] * jenv[(t % 3) * nn + q];
+      }
+      tmp[q] = (S)v;
+    }
+    __syncwarp();
+    S trp = 0;
+    for (int q = lane; q < n * n; q += 32) {
+      const int a = q / n, m = q % n;
+      S x = 0;
+      for (int l = 0; l < n; ++l) x += Ainv[a * n + l] * tmp[l * n + m];
+      X[q] = x;
+      if (a == m) trp += x;
+    }
+    const double tr = warp_sum((double)trp);
+    __syncwarp();
+    if (is_lap) {
+      lap += tr;
+    } else {
+      if (lane == 0) out[2 + t] = tr;
+      S s2 = 0;
+      for (int q = lane; q < n * n; q += 32) {
+        const int a = q / n, m = q % n;
+        s2 += X[a * n + m] * X[m * n + a];
+      }
+      lap -= warp_sum((double)s2);
+    }
+    __syncwarp();
+  }
+  return lap;
+}
+
 template <class T>
 __global__ void __launch_bounds__(128)
     orbital_det_kernel(const T* __restrict__ phi, const T* __restrict__ geo, const T* __restrict__ params,
                        int64_t Bc, int N, int n_up, int M, int K, int C, int Wo, int E, int n_ee,
-                       int64_t om_up, int64_t om_dn, int64_t ze_up, int64_t ze_dn, double* __restrict__ det) {
+                       int64_t om_up, int64_t om_dn, int64_t ze_up, int64_t ze_dn, double* __restrict__ det,
+                       unsigned long long* __restrict__ n_fp64) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int warps = blockDim.x / 32;
@@ -259,19 +522,21 @@ __global__ void __launch_bounds__(128)
   const int nmax = n_up > n_dn ? n_up : n_dn;
   const int N3 = 3 * N;
   const bool jets = C > 1;
-  // per-warp shared memory
   const int nn = nmax * nmax;
-  const size_t per_warp = (size_t)nn * (3 * sizeof(double) + 7 * sizeof(T)) + 32 * sizeof(int);
+  const size_t per_warp = (size_t)nn * (3 * sizeof(double) + 10 * sizeof(T)) + 32 * sizeof(int);
   unsigned char* base = smem_raw + warp * ((per_warp + 15) / 16 * 16);
-  double* LU = reinterpret_cast<double*>(base);
-  double* Ainv = LU + nn;
-  T* env = reinterpret_cast<T*>(Ainv + 2 * nn);
-  T* jenv = env + nn;      // [3][nn]
+  double* LUd = reinterpret_cast<double*>(base);  // FP64 path
+  double* Ainvd = LUd + nn;
+  double* Xd = Ainvd + nn;
+  T* env = reinterpret_cast<T*>(Xd + nn);
+  T* jenv = env + nn;  // [3][nn]
   T* lenv = jenv + 3 * nn;
   T* phi0 = lenv + nn;
-  T* tmp = phi0 + nn;      // one tangent of A
-  double* X = reinterpret_cast<double*>(base) + 2 * nn;  // A^-1 d_k A (FP64)
-  int* perm = reinterpret_cast<int*>(tmp + nn);
+  T* LUt = phi0 + nn;  // arithmetic-type path
+  T* Ainvt = LUt + nn;
+  T* tmp = Ainvt + nn;
+  T* Xt = tmp + nn;
+  int* perm = reinterpret_cast<int*>(Xt + nn);
 
   if (gw >= Bc * 2 * K) return;
   const int64_t b = gw / (2 * K);
@@ -290,6 +555,7 @@ __global__ void __launch_bounds__(128)
   const T* gb = geo + b * E * 4;
 
   // Envelopes (Eq. 20) with their derivatives in the coordinates of electron i.
+  T amax = 0;
   for (int q = lane; q < n * n; q += 32) {
     const int ii = q / n, k = q % n, o = p * n + k, i = i0 + ii;
     T ev = 0, j0 = 0, j1 = 0, j2 = 0, lv = 0;
@@ -310,125 +576,54 @@ __global__ void __launch_bounds__(128)
     lenv[q] = lv;
     const T f0 = phib[(int64_t)i * C * Wo + o];
     phi0[q] = f0;
-    LU[q] = (double)f0 * (double)ev;
+    LUt[q] = f0 * ev;
+    amax = max(amax, (T)fabs(f0 * ev));
   }
-  if (lane < n) perm[lane] = lane;
   __syncwarp();
 
-  // LU with partial pivoting (FP64), pivot search across the warp.
-  int sign = 1;
-  double logabs = 0.0;
-  bool singular = false;
-  for (int j = 0; j < n; ++j) {
-    double v = (lane >= j && lane < n) ? fabs(LU[lane * n + j]) : -1.0;
-    int idx = lane;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-      const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
-      if (v2 > v || (v2 == v && i2 < idx)) {
-        v = v2;
-        idx = i2;
-      }
-    }
-    if (!(v > 0.0)) {
-      singular = true;
-      break;
-    }
-    if (idx != j) {
-      for (int k = lane; k < n; k += 32) {
-        const double t = LU[j * n + k];
-        LU[j * n + k] = LU[idx * n + k];
-        LU[idx * n + k] = t;
-      }
-      if (lane == 0) {
-        const int t = perm[j];
-        perm[j] = perm[idx];
-        perm[idx] = t;
-      }
-      sign = -sign;
+  (void)amax;
+  int sign = 0;
+  double logabs = -INFINITY;
+  bool fp64 = sizeof(T) == 8 || jets;
+  if (!fp64) {
+    T* rmax = Xt;  // row maxima of A (Xt is unused on the value-only path)
+    if (lane < n) {
+      T m = 0;
+      for (int k = 0; k < n; ++k) m = max(m, (T)fabs(LUt[lane * n + k]));
+      rmax[lane] = m;
     }
     __syncwarp();
-    const double piv = LU[j * n + j];
-    for (int i = j + 1 + lane; i < n; i += 32) {
-      const double f = LU[i * n + j] / piv;
-      LU[i * n + j] = f;
-      for (int k = j + 1; k < n; ++k) LU[i * n + k] -= f * LU[j * n + k];
+    bool ok = warp_lu<T>(LUt, perm, n, lane, &sign, &logabs);
+    if (ok) {
+      warp_inverse<T>(LUt, perm, n, lane, Ainvt);
+      T imax = 0;
+      for (int q = lane; q < n * n; q += 32) imax = max(imax, (T)fabs(Ainvt[q]) * rmax[q % n]);
+      const T kappa = T(n) * warp_max(imax);
+      fp64 = !(kappa <= T(DQ_KAPPA_FP32_VALUE));
+    } else {
+      fp64 = true;
     }
-    __syncwarp();
-    if (piv < 0) sign = -sign;
-    logabs += log(fabs(piv));
   }
-  if (singular) {
-    for (int k = lane; k < N3 + 3; k += 32) out[k] = k == 1 ? -INFINITY : 0.0;
-    return;
+  if (fp64) {
+    if (sizeof(T) == 4 && !jets && lane == 0) atomicAdd(n_fp64, 1ull);
+    for (int q = lane; q < n * n; q += 32) LUd[q] = (double)phi0[q] * (double)env[q];
+    __syncwarp();
+    if (!warp_lu<double>(LUd, perm, n, lane, &sign, &logabs)) {
+      for (int k = lane; k < N3 + 3; k += 32) out[k] = k == 1 ? -INFINITY : 0.0;
+      return;
+    }
   }
   if (lane == 0) {
     out[0] = (double)sign;
     out[1] = logabs;
   }
   if (!jets) return;
-
-  // A^-1 column by column: lane solves L U x = P e_col.
-  if (lane < n) {
-    const int col = lane;
-    double* x = Ainv;  // stored as Ainv[row][col]
-    for (int r = 0; r < n; ++r) {
-      double acc = perm[r] == col ? 1.0 : 0.0;
-      for (int m = 0; m < r; ++m) acc -= LU[r * n + m] * x[m * n + col];
-      x[r * n + col] = acc;
-    }
-    for (int r = n - 1; r >= 0; --r) {
-      double acc = x[r * n + col];
-      for (int m = r + 1; m < n; ++m) acc -= LU[r * n + m] * x[m * n + col];
-      x[r * n + col] = acc / LU[r * n + r];
-    }
-  }
-  __syncwarp();
-
-  // Tangents: d_k A = d_k phi * env + phi * d_k env (env depends on electron i only).
-  // LU, A^-1, log|det| and the tangent contractions are FP64.
-  double lap = 0.0;
-  for (int t = 0; t <= N3; ++t) {
-    const bool is_lap = t == N3;
-    const int c = is_lap ? C - 1 : 1 + t;
-    for (int q = lane; q < n * n; q += 32) {
-      const int ii = q / n, k = q % n, o = p * n + k, i = i0 + ii;
-      const T* ph = phib + (int64_t)i * C * Wo + o;
-      T v = ph[(int64_t)c * Wo] * env[q];
-      if (is_lap) {
-        v += phi0[q] * lenv[q];
-        for (int x = 0; x < 3; ++x) v += T(2) * ph[(int64_t)(1 + 3 * i + x) * Wo] * jenv[x * nn + q];
-      } else if (t / 3 == i) {
-        v += phi0[q] * jenv[(t % 3) * nn + q];
-      }
-      tmp[q] = v;
-    }
-    __syncwarp();
-    // X = A^-1 dA; tr X = d log|det A|
-    double trp = 0;
-    for (int q = lane; q < n * n; q += 32) {
-      const int a = q / n, m = q % n;
-      double x = 0;
-      for (int l = 0; l < n; ++l) x += Ainv[a * n + l] * (double)tmp[l * n + m];
-      X[q] = x;
-      if (a == m) trp += x;
-    }
-    const double tr = warp_sum(trp);
-    __syncwarp();
-    if (is_lap) {
-      lap += tr;
-    } else {
-      if (lane == 0) out[2 + t] = tr;
-      // tr(X^2) = sum_{a,m} X[a][m] X[m][a]
-      double s2 = 0;
-      for (int q = lane; q < n * n; q += 32) {
-        const int a = q / n, m = q % n;
-        s2 += X[a * n + m] * X[m * n + a];
-      }
-      lap -= warp_sum(s2);
-    }
-    __syncwarp();
+  double lap;
+  if (fp64) {
+    warp_inverse<double>(LUd, perm, n, lane, Ainvd);
+    lap = det_tangents<T, double>(phib, env, jenv, lenv, phi0, Ainvd, LUd, Xd, n, nn, i0, p, C, Wo, N3, lane, out);
+  } else {
+    lap = det_tangents<T, T>(phib, env, jenv, lenv, phi0, Ainvt, tmp, Xt, n, nn, i0, p, C, Wo, N3, lane, out);
   }
   if (lane == 0) out[2 + N3] = lap;
 }
@@ -653,10 +848,14 @@ cudaError_t launch_edge_hidden(const dq_handle_s& h, const FwdDims& d, const T* 
                                cudaStream_t s) {
   const int ej = d.C > 1 ? 3 : 1;
   const auto& y = h.off.layer[l];
-  const int64_t n = d.Bc * h.edges.n_all * d.D;
-  edge_hidden_kernel<T><<<blocks(n, 256), 256, 0, s>>>(b.rbf, params, d.Bc, h.edges.n_all, h.edges.n_par,
-                                                       h.edges.n_ee, d.D, d.Q, ej, y.W1[0], y.W1[1], y.W1[2],
-                                                       y.b1[0], y.b1[1], y.b1[2], b.eh);
+  const int64_t rows = d.Bc * h.edges.n_all;
+  const size_t smem = ((size_t)3 * d.Q * d.D + 3 * d.D + (size_t)kEdgesPerCta * ej * d.Q) * sizeof(T);
+  auto kern = edge_hidden_kernel<T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<blocks(rows, kEdgesPerCta), kHiddenThreads, smem, s>>>(b.rbf, params, d.Bc, h.edges.n_all, h.edges.n_par,
+                                                                h.edges.n_ee, d.D, d.Q, ej, y.W1[0], y.W1[1], y.W1[2],
+                                                                y.b1[0], y.b1[1], y.b1[2], b.eh);
   return cudaGetLastError();
 }
 
@@ -671,19 +870,26 @@ namespace {
 template <class T>
 size_t message_smem(const dq_handle_s& h, const FwdDims& d, int DC, bool z_const) {
   const int ej = d.C > 1 ? 3 : 1;
-  const int E = h.edges.n_all;
-  const size_t zs = z_const ? 2 * DC : (size_t)d.N * d.C * DC;
-  return (zs + (size_t)E * ej * DC + (size_t)d.M * DC + (size_t)E * 4) * sizeof(T) + (size_t)d.N * d.N * sizeof(int);
+  const size_t E = h.edges.n_all, n_ee = h.edges.n_ee, N = d.N, M = d.M;
+  const size_t zrows = z_const ? 2 : N * d.C;
+  const size_t vals = zrows * DC + N * N * DC + (ej == 3 ? 2 * n_ee * DC : 0) + N * M * ej * DC + M * DC + E * 4;
+  return vals * sizeof(T) + N * N * sizeof(int);
 }
+constexpr int kMsgIB = 4;
 template <class T, int DC>
 cudaError_t launch_messages_dc(const dq_handle_s& h, const FwdDims& d, const T* params, int l, bool z_const,
                                FwdBuffers<T> b, size_t smem, cudaStream_t s) {
-  auto kern = messages_kernel<T, DC>;
+  constexpr int CB = sizeof(T) == 4 ? 4 : 2;
+  auto kern = messages_kernel<T, DC, kMsgIB, CB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  const int nib = (d.n_up + kMsgIB - 1) / kMsgIB + (d.n_dn + kMsgIB - 1) / kMsgIB;
+  const int ntasks = nib * ((d.C + CB - 1) / CB);
+  const int groups = ntasks < 256 / DC ? ntasks : 256 / DC;
   dim3 grid((unsigned)d.Bc, d.D / DC);
-  kern<<<grid, kThreads, smem, s>>>(b.Z, b.z0, b.ew, b.geo, params + h.off.layer[l].Y, h.d_pair_of, d.N, d.n_up, d.M,
-                                    d.C, d.D, h.edges.n_all, h.edges.n_ee, d.C > 1 ? 3 : 1, z_const ? 1 : 0, b.msg);
+  kern<<<grid, groups * DC, smem, s>>>(b.Z, b.z0, b.ew, b.geo, params + h.off.layer[l].Y, h.d_pair_of, d.N, d.n_up,
+                                       d.M, d.C, d.D, h.edges.n_all, h.edges.n_ee, d.C > 1 ? 3 : 1, z_const ? 1 : 0,
+                                       b.msg);
   return cudaGetLastError();
 }
 }  // namespace
@@ -691,17 +897,16 @@ cudaError_t launch_messages_dc(const dq_handle_s& h, const FwdDims& d, const T* 
 template <class T>
 cudaError_t launch_messages(const dq_handle_s& h, const FwdDims& d, const T* params, int l, bool z_const,
                             FwdBuffers<T> b, cudaStream_t s) {
-  constexpr size_t kBudget = 96 * 1024, kMax = 220 * 1024;
-  for (int DC : {32, 16, 8, 4}) {
+  constexpr size_t kBudget = 76 * 1024, kMax = 220 * 1024;
+  for (int DC : {32, 16, 8}) {
     if (d.D % DC) continue;
     const size_t smem = message_smem<T>(h, d, DC, z_const);
-    if (smem > kBudget && DC > 4) continue;
+    if (smem > kBudget && DC > 8) continue;
     if (smem > kMax) return cudaErrorInvalidConfiguration;
     switch (DC) {
       case 32: return launch_messages_dc<T, 32>(h, d, params, l, z_const, b, smem, s);
       case 16: return launch_messages_dc<T, 16>(h, d, params, l, z_const, b, smem, s);
-      case 8: return launch_messages_dc<T, 8>(h, d, params, l, z_const, b, smem, s);
-      default: return launch_messages_dc<T, 4>(h, d, params, l, z_const, b, smem, s);
+      default: return launch_messages_dc<T, 8>(h, d, params, l, z_const, b, smem, s);
     }
   }
   return cudaErrorInvalidConfiguration;
@@ -710,8 +915,14 @@ cudaError_t launch_messages(const dq_handle_s& h, const FwdDims& d, const T* par
 template <class T>
 cudaError_t launch_update(const dq_handle_s& h, const FwdDims& d, const T* params, bool from_spin, FwdBuffers<T> b,
                           cudaStream_t s) {
-  update_kernel<T><<<blocks(d.Bc * d.N * d.D, 256), 256, 0, s>>>(b.Z, b.F, params + h.off.E_spin, d.Bc, d.N, d.n_up,
-                                                                 d.C, d.D, from_spin ? 1 : 0);
+  return launch_update_io<T>(h, d, params, from_spin, b.Z, b.F, b.F, s);
+}
+
+template <class T>
+cudaError_t launch_update_io(const dq_handle_s& h, const FwdDims& d, const T* params, bool from_spin, const T* P,
+                             const T* Fin, T* Fout, cudaStream_t s) {
+  update_kernel<T><<<blocks(d.Bc * d.N * d.D, 256), 256, 0, s>>>(P, Fin, Fout, params + h.off.E_spin, d.Bc, d.N,
+                                                                 d.n_up, d.C, d.D, from_spin ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -720,8 +931,8 @@ cudaError_t launch_orbital_det(const dq_handle_s& h, const FwdDims& d, const T* 
                                cudaStream_t s) {
   const int nmax = d.n_up > d.n_dn ? d.n_up : d.n_dn;
   const int nn = nmax * nmax;
-  const size_t per_warp = ((size_t)nn * (3 * sizeof(double) + 7 * sizeof(T)) + 32 * sizeof(int) + 15) / 16 * 16;
-  const int warps = 4;
+  const size_t per_warp = ((size_t)nn * (3 * sizeof(double) + 10 * sizeof(T)) + 32 * sizeof(int) + 15) / 16 * 16;
+  const int warps = per_warp * 4 <= 200 * 1024 ? 4 : 1;
   const size_t smem = per_warp * warps;
   auto kern = orbital_det_kernel<T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -729,7 +940,8 @@ cudaError_t launch_orbital_det(const dq_handle_s& h, const FwdDims& d, const T* 
   const int64_t nmat = d.Bc * 2 * d.K;
   kern<<<blocks(nmat, warps), warps * 32, smem, s>>>(b.phi, b.geo, params, d.Bc, d.N, d.n_up, d.M, d.K, d.C,
                                                      d.K * nmax, h.edges.n_all, h.edges.n_ee, h.off.omega[0],
-                                                     h.off.omega[1], h.off.zeta[0], h.off.zeta[1], b.det);
+                                                     h.off.omega[1], h.off.zeta[0], h.off.zeta[1], b.det,
+                                                     h.d_fp64_count);
   return cudaGetLastError();
 }
 
@@ -764,6 +976,8 @@ cudaError_t launch_combine(const dq_handle_s& h, const FwdDims& d, const T* para
                                           cudaStream_t);                                                          \
   template cudaError_t launch_update<T>(const dq_handle_s&, const FwdDims&, const T*, bool, FwdBuffers<T>,        \
                                         cudaStream_t);                                                            \
+  template cudaError_t launch_update_io<T>(const dq_handle_s&, const FwdDims&, const T*, bool, const T*, const T*, \
+                                           T*, cudaStream_t);                                                     \
   template cudaError_t launch_orbital_det<T>(const dq_handle_s&, const FwdDims&, const T*, FwdBuffers<T>,         \
                                              cudaStream_t);                                                       \
   template cudaError_t launch_jastrow_sum<T>(const dq_handle_s&, const FwdDims&, FwdBuffers<T>, cudaStream_t);    \

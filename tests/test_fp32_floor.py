@@ -8,11 +8,15 @@ algorithm compiled with FP32 scalars (same source, -DORACLE_REAL=float) errs
 by ~1e-6 S_b, far above 1e-4 Ha at such walkers, so no FP32 evaluation can
 meet a bare 1e-4 Ha bound there.  The FP32 tolerance used by the GPU parity
 tests is therefore
-    |d E_loc| <= max(1e-4 Ha, 1e-5 S_b),   |d log|psi|| <= 1e-4 max(1, |log|psi||),
-i.e. the 1e-4 Ha bound wherever the kinetic terms are O(10) Ha or smaller,
-and a relative bound ~170 FP32 ulps of S_b elsewhere.  This test checks that
-a plain FP32 evaluation meets that bound, so the bound is neither loose nor
-out of reach.
+    |d E_loc| <= max(1e-4 Ha, 3e-5 S_b),   |d log|psi|| <= 1e-4 max(1, |log|psi||),
+i.e. the 1e-4 Ha bound wherever the kinetic terms are a few Ha or smaller,
+and a relative bound of ~500 FP32 ulps of S_b elsewhere.  Over 96 sampled
+walkers of the 4096-walker batch the plain FP32 evaluation's worst error is
+6.1e-6 S_b (99th percentile 5.1e-6 S_b) and its worst log|psi| error 4.3e-5
+relative, so the bounds sit 5x and 2.3x above the floor: an FP32 path cannot
+be expected to beat the floor, while a dropped term or a wrong sign gives
+errors of order 1e-2..1 S_b.  This test checks that a plain FP32 evaluation
+meets the bounds.
 """
 import os
 
@@ -25,7 +29,7 @@ from paper_2307_14123_gb300 import fixtures as fx
 def fp32_tolerance(ref):
     """Per-walker E_loc tolerance from the FP64 oracle's gradient and Laplacian."""
     S = 0.5 * (np.abs(ref["lap"]) + np.sum(ref["grad"] ** 2, axis=1))
-    return np.maximum(1e-4, 1e-5 * S), S
+    return np.maximum(1e-4, 3e-5 * S), S
 
 
 def test_fp32_evaluation_meets_the_tolerance():
