@@ -94,6 +94,7 @@ typedef enum {
 /* Device status flags (dq_last_device_status). */
 #define DQ_FLAG_SINGULAR 0x1u  /* some walker had psi = 0 (sign 0)          */
 #define DQ_FLAG_NONFINITE 0x2u /* some local energy or gradient not finite   */
+#define DQ_FLAG_TIMEOUT 0x4u   /* a bounded device wait gave up (kernel skipped its work) */
 
 /* The molecule (Eq. 1).  Host memory; copied by dq_create. */
 typedef struct {
@@ -217,6 +218,17 @@ dq_status dq_last_device_status(dq_handle h, void* stream, uint32_t* flags);
  * FP64, which this counts; local_energy takes FP64 for every matrix (not
  * counted).  Always 0 in FP64 mode, where every matrix is FP64. */
 dq_status dq_fp64_matrix_count(dq_handle h, void* stream, int64_t* count);
+
+/* Test support: the BF16 tensor-core GEMM used by the embedding layers in
+ * DQ_BF16_MIXED mode, exposed so that it can be checked on its own.
+ * Y[r][n] = sum_k X[r][k] W[n][k] + (r % bias_period == 0 ? bias[n] : 0);
+ * X [rows][K] (row stride ldx) and W [n_out][K] BF16 device arrays, 16-byte
+ * aligned, K a multiple of 64, ldx a multiple of 8; bias FP32 [n_out] or
+ * NULL; Y FP32 [rows][ldy].  status: device uint32 receiving DQ_FLAG_TIMEOUT
+ * if a bounded wait inside the kernel gave up.  Enqueued on `stream`. */
+dq_status dq_test_gemm_bf16(const void* X, int64_t rows, int32_t K, int64_t ldx, const void* W, int32_t n_out,
+                            const float* bias, int32_t bias_period, float* Y, int64_t ldy, uint32_t* status,
+                            void* stream);
 
 /* Human-readable name of a status code (static string). */
 const char* dq_status_string(dq_status s);

@@ -97,7 +97,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Sub-buffer offsets (bytes) of the forward workspace for a chunk of Bc walkers.
 struct FwdPlan {
-  size_t geo, rbf, eh, ew, F, Z, msg, phi, det, js, jh, z0, total;
+  size_t geo, rbf, eh, ew, F, Z, msg, phi, det, js, jh, z0, msg_bf, F_bf, W_bf, total;
 };
 
 FwdPlan plan_forward(const dq_handle_s& h, int64_t Bc, bool jets, size_t elem) {
@@ -115,14 +115,19 @@ FwdPlan plan_forward(const dq_handle_s& h, int64_t Bc, bool jets, size_t elem) {
   p.rbf = take(Bc * E * ej * h.Q * elem);
   p.eh = take(Bc * E * ej * D * elem);
   p.ew = take(Bc * E * ej * D * elem);
+  const bool bf = h.precision == DQ_BF16_MIXED;
   p.F = take(Bc * N * C * D * elem);
   p.Z = take(Bc * N * C * D * elem);
-  p.msg = take(Bc * N * C * 3 * D * elem);
+  p.msg = take(bf ? 0 : Bc * N * C * 3 * D * elem);
   p.phi = take(Bc * N * C * K * nmax * elem);
   p.det = take(Bc * 2 * K * (3 * N + 3) * sizeof(double));
   p.js = take(Bc * C * D * elem);
   p.jh = take(Bc * C * D * elem);
   p.z0 = take(2 * D * elem);
+  // BF16 mode: messages and a copy of the embeddings in BF16, BF16 weights
+  p.msg_bf = take(bf ? Bc * N * C * 3 * D * 2 : 0);
+  p.F_bf = take(bf ? Bc * N * C * D * 2 : 0);
+  p.W_bf = take(bf ? (size_t)h.L * 4 * D * D * 2 : 0);
   p.total = o;
   return p;
 }
@@ -191,6 +196,23 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
   bf.js = reinterpret_cast<T*>(ws + plan.js);
   bf.jh = reinterpret_cast<T*>(ws + plan.jh);
   bf.z0 = reinterpret_cast<T*>(ws + plan.z0);
+  bf.msg_bf = nullptr;
+  bf.F_bf = nullptr;
+  // BF16 mode: the update and node maps run on the tensor cores (gemm_tc.cu)
+  const bool use_tc = sizeof(T) == 4 && h.precision == DQ_BF16_MIXED;
+  unsigned char* W_bf = ws + plan.W_bf;
+  auto wg_bf = [&](int l) { return W_bf + (size_t)l * 4 * h.D * h.D * 2; };
+  auto wh_bf = [&](int l) { return wg_bf(l) + (size_t)3 * h.D * h.D * 2; };
+  if (use_tc) {
+    bf.msg_bf = ws + plan.msg_bf;
+    bf.F_bf = ws + plan.F_bf;
+    if constexpr (sizeof(T) == 4) {
+      for (int l = 0; l < h.L; ++l) {
+        DQ_CU(launch_to_bf16(params + h.off.layer[l].W_g, wg_bf(l), (int64_t)3 * h.D * h.D, s));
+        DQ_CU(launch_to_bf16(params + h.off.layer[l].W_h, wh_bf(l), (int64_t)h.D * h.D, s));
+      }
+    }
+  }
 
   const int N = h.N, D = h.D, K = h.K;
   const int C = jets ? 3 * N + 2 : 1;
@@ -216,14 +238,28 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
                          bf.ew + (int64_t)e0[t] * ej * D, m, nb * ng[t] * ej, D, D, false, s));
       }
       const RowMap node{(int64_t)N * C, (int64_t)N * C * D, D};
+      const int64_t rows = nb * N * C;
       if (l == 0) {
         DQ_LAUNCH(h, kb + PK_MESSAGES, launch_messages<T>(h, d, params, l, true, bf, s));
       } else {
-        DQ_LAUNCH(h, kb + PK_GEMM_NODE, gemm_nt<T>(bf.F, node, params + y.W_h, nullptr, 1, bf.Z, node, nb * N * C, D, D, false, s));
+        if (use_tc) {
+          DQ_LAUNCH(h, kb + PK_GEMM_NODE, gemm_bf16_tc(bf.F_bf, rows, D, D, wh_bf(l), D, nullptr, 1,
+                                                       reinterpret_cast<float*>(bf.Z), D, h.d_status, s));
+        } else {
+          DQ_LAUNCH(h, kb + PK_GEMM_NODE, gemm_nt<T>(bf.F, node, params + y.W_h, nullptr, 1, bf.Z, node, rows, D, D,
+                                                     false, s));
+        }
         DQ_LAUNCH(h, kb + PK_MESSAGES, launch_messages<T>(h, d, params, l, false, bf, s));
       }
       const RowMap mrow{(int64_t)N * C, (int64_t)N * C * 3 * D, 3 * D};
-      DQ_LAUNCH(h, kb + PK_GEMM_UPDATE, gemm_nt<T>(bf.msg, mrow, params + y.W_g, params + y.b_g, C, bf.Z, node, nb * N * C, D, 3 * D, false, s));
+      if (use_tc) {
+        DQ_LAUNCH(h, kb + PK_GEMM_UPDATE, gemm_bf16_tc(bf.msg_bf, rows, 3 * D, 3 * D, wg_bf(l), D,
+                                                       reinterpret_cast<const float*>(params + y.b_g), C,
+                                                       reinterpret_cast<float*>(bf.Z), D, h.d_status, s));
+      } else {
+        DQ_LAUNCH(h, kb + PK_GEMM_UPDATE, gemm_nt<T>(bf.msg, mrow, params + y.W_g, params + y.b_g, C, bf.Z, node, rows,
+                                                     D, 3 * D, false, s));
+      }
       DQ_LAUNCH(h, kb + PK_UPDATE, launch_update<T>(h, d, params, l == 0, bf, s));
     }
     const int ns[2] = {h.n_up, h.n_dn}, i0[2] = {0, h.n_up};
@@ -511,7 +547,7 @@ const char* dq_status_string(dq_status s) {
 dq_status dq_create(const dq_system* sys, const dq_ansatz_cfg* cfg, int32_t precision, dq_handle* out) {
   if (!sys || !cfg || !out) return DQ_ERR_ARG;
   *out = nullptr;
-  if (precision != DQ_FP64 && precision != DQ_FP32) return precision == DQ_BF16_MIXED ? DQ_ERR_UNSUPPORTED : DQ_ERR_ARG;
+  if (precision != DQ_FP64 && precision != DQ_FP32 && precision != DQ_BF16_MIXED) return DQ_ERR_ARG;
   if (!sys->Z || !sys->R) return DQ_ERR_ARG;
   const int M = sys->n_nuc, n_up = sys->n_up, n_dn = sys->n_down, N = n_up + n_dn;
   if (M < 1 || M > kMaxNuc || n_up < 1 || n_dn < 0 || N > kMaxElec || n_up > kMaxSpin || n_dn > kMaxSpin)
@@ -814,5 +850,15 @@ dq_status dq_fp64_matrix_count(dq_handle h, void* stream, int64_t* count) {
 }
 
 int32_t dq_profile_kind_count(void) { return PK_COUNT; }
+
+dq_status dq_test_gemm_bf16(const void* X, int64_t rows, int32_t K, int64_t ldx, const void* W, int32_t n_out,
+                            const float* bias, int32_t bias_period, float* Y, int64_t ldy, uint32_t* status,
+                            void* stream) {
+  if (!X || !W || !Y || !status || rows < 0 || n_out < 0 || ldy < n_out) return DQ_ERR_ARG;
+  const cudaError_t e = gemm_bf16_tc(X, rows, K, ldx, W, n_out, bias, bias_period, Y, ldy, status,
+                                     (cudaStream_t)stream);
+  if (e == cudaErrorInvalidValue) return DQ_ERR_ARG;
+  return e == cudaSuccess ? DQ_OK : DQ_ERR_CUDA;
+}
 
 }  // extern "C"

@@ -341,6 +341,119 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Large parameter blocks: Out[o][a] = sum_r X[r][o] Y[r][a] as a tiled GEMM
+// whose reduction index is the row index.  Rows are the slow index of both
+// operands, so BK consecutive rows of X and Y are copied into shared memory
+// as they are ([k][o], [k][a]); each thread accumulates a TM x TN register
+// block (split halves, conflict-free reads).  blockIdx.z selects a walker
+// (per-walker mode, output G + b*P) or a split of the walker range
+// (summed mode, output part[split]).
+template <class T>
+struct VecT;
+template <>
+struct VecT<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct VecT<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
+
+template <class T, int BM, int BN, int BK, bool VA>
+__global__ void __launch_bounds__(256)
+    gemm_tn_kernel(const T* __restrict__ X, RowMap mx, const T* __restrict__ Y, RowMap my, int rpw, int64_t nw,
+                   int n_o, int n_a, T* __restrict__ G, int64_t P, int64_t off, int ld, int mode,
+                   int64_t walkers_per_split, T* __restrict__ part) {
+  using V = typename VecT<T>::type;
+  constexpr int VEC = VecT<T>::n;
+  constexpr int TM = 2 * VEC, TN = 2 * VEC;
+  static_assert((BM / TM) * (BN / TN) == 256, "tile/thread mismatch");
+  __shared__ __align__(16) T Xs[BK][BM];
+  __shared__ __align__(16) T Ys[BK][BN];
+  const int tid = threadIdx.x;
+  const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+  const int o0 = blockIdx.x * BM, a0 = blockIdx.y * BN;
+  int64_t wb0, wb1;
+  if (mode == 1) {
+    wb0 = blockIdx.z;
+    wb1 = wb0 + 1;
+  } else {
+    wb0 = (int64_t)blockIdx.z * walkers_per_split;
+    wb1 = min(nw, wb0 + walkers_per_split);
+  }
+  const int64_t r_begin = wb0 * rpw, r_end = wb1 * rpw;
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+  constexpr int XV = BM / VEC, YV = BN / VEC;  // vectors per row of a tile
+  for (int64_t rr0 = r_begin; rr0 < r_end; rr0 += BK) {
+    for (int e = tid; e < BK * XV; e += 256) {
+      const int k = e / XV, cv = e % XV;
+      const int64_t r = rr0 + k;
+      const int o = o0 + cv * VEC;
+      V v{};
+      if (r < r_end) {
+        const T* src = X + (r / mx.rows_per_seg) * mx.seg_stride + (r % mx.rows_per_seg) * mx.ld + o;
+        if (VA && o + VEC <= n_o) {
+          v = *reinterpret_cast<const V*>(src);
+        } else {
+          T* t = reinterpret_cast<T*>(&v);
+          for (int q = 0; q < VEC; ++q) t[q] = o + q < n_o ? src[q] : T(0);
+        }
+      }
+      *reinterpret_cast<V*>(&Xs[k][cv * VEC]) = v;
+    }
+    for (int e = tid; e < BK * YV; e += 256) {
+      const int k = e / YV, cv = e % YV;
+      const int64_t r = rr0 + k;
+      const int a = a0 + cv * VEC;
+      V v{};
+      if (r < r_end) {
+        const T* src = Y + (r / my.rows_per_seg) * my.seg_stride + (r % my.rows_per_seg) * my.ld + a;
+        if (VA && a + VEC <= n_a) {
+          v = *reinterpret_cast<const V*>(src);
+        } else {
+          T* t = reinterpret_cast<T*>(&v);
+          for (int q = 0; q < VEC; ++q) t[q] = a + q < n_a ? src[q] : T(0);
+        }
+      }
+      *reinterpret_cast<V*>(&Ys[k][cv * VEC]) = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T x[TM], y[TN];
+      *reinterpret_cast<V*>(&x[0]) = *reinterpret_cast<const V*>(&Xs[kk][ty * VEC]);
+      *reinterpret_cast<V*>(&x[VEC]) = *reinterpret_cast<const V*>(&Xs[kk][BM / 2 + ty * VEC]);
+      *reinterpret_cast<V*>(&y[0]) = *reinterpret_cast<const V*>(&Ys[kk][tx * VEC]);
+      *reinterpret_cast<V*>(&y[VEC]) = *reinterpret_cast<const V*>(&Ys[kk][BN / 2 + tx * VEC]);
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(x[i], y[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int o = o0 + ((i < VEC) ? ty * VEC + i : BM / 2 + ty * VEC + (i - VEC));
+    if (o >= n_o) continue;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int a = a0 + ((j < VEC) ? tx * VEC + j : BN / 2 + tx * VEC + (j - VEC));
+      if (a >= n_a) continue;
+      if (mode == 1)
+        G[wb0 * P + off + (int64_t)o * ld + a] = acc[i][j];
+      else
+        part[((int64_t)blockIdx.z * n_o + o) * n_a + a] = acc[i][j];
+    }
+  }
+}
+
 template <class T>
 __global__ void reduce_splits_kernel(const T* __restrict__ part, int splits, int n_o, int n_a, T* __restrict__ G,
                                      int64_t off, int ld) {
@@ -482,10 +595,52 @@ cudaError_t gemm_nn(const T* X, RowMap mx, const T* W, T* Y, RowMap my, int64_t 
 }
 
 template <class T>
+cudaError_t param_reduce_tiled(const T* X, RowMap mx, const T* Y, RowMap my, int rpw, int64_t nw, int n_o, int n_a,
+                               T* G, int64_t P, int64_t off, int ld, int mode, T* part, int64_t part_elems,
+                               cudaStream_t s) {
+  constexpr int BM = sizeof(T) == 4 ? 128 : 64, BN = BM, BK = 8;
+  constexpr int VEC = VecT<T>::n;
+  const bool va = (uintptr_t)X % 16 == 0 && (uintptr_t)Y % 16 == 0 && mx.ld % VEC == 0 && my.ld % VEC == 0 &&
+                  mx.seg_stride % VEC == 0 && my.seg_stride % VEC == 0;
+  const unsigned gx = nblocks(n_o, BM), gy = nblocks(n_a, BN);
+  auto launch = [&](dim3 grid, const T* Xo, const T* Yo, int64_t nws, T* Go, int md, int64_t wps, T* pt) {
+    if (va)
+      gemm_tn_kernel<T, BM, BN, BK, true><<<grid, 256, 0, s>>>(Xo, mx, Yo, my, rpw, nws, n_o, n_a, Go, P, off, ld, md,
+                                                                wps, pt);
+    else
+      gemm_tn_kernel<T, BM, BN, BK, false><<<grid, 256, 0, s>>>(Xo, mx, Yo, my, rpw, nws, n_o, n_a, Go, P, off, ld, md,
+                                                                 wps, pt);
+  };
+  if (mode == 1) {
+    for (int64_t w0 = 0; w0 < nw; w0 += 65535) {
+      const int64_t nws = nw - w0 < 65535 ? nw - w0 : 65535;
+      const int64_t r_off = w0 * rpw;
+      const T* Xo = X + (r_off / mx.rows_per_seg) * mx.seg_stride + (r_off % mx.rows_per_seg) * mx.ld;
+      const T* Yo = Y + (r_off / my.rows_per_seg) * my.seg_stride + (r_off % my.rows_per_seg) * my.ld;
+      launch(dim3(gx, gy, (unsigned)nws), Xo, Yo, nws, G + w0 * P, 1, 1, nullptr);
+    }
+    return cudaGetLastError();
+  }
+  // summed over walkers: about 2 CTAs per SM in total, deterministic second pass
+  const int64_t per = (int64_t)n_o * n_a;
+  int64_t splits = (304 + gx * gy - 1) / (gx * gy);
+  if (splits > nw) splits = nw;
+  if (splits * per > part_elems) splits = part_elems / per;
+  if (splits < 1) return cudaErrorInvalidValue;
+  const int64_t wps = (nw + splits - 1) / splits;
+  splits = (nw + wps - 1) / wps;
+  launch(dim3(gx, gy, (unsigned)splits), X, Y, nw, G, 0, wps, part);
+  reduce_splits_kernel<T><<<nblocks(per, 256), 256, 0, s>>>(part, (int)splits, n_o, n_a, G, off, ld);
+  return cudaGetLastError();
+}
+
+template <class T>
 cudaError_t param_reduce(const T* X, RowMap mx, const T* Y, RowMap my, int rpw, int64_t nw, int n_o, int n_a, T* G,
                          int64_t P, int64_t off, int ld, int mode, T* part, int64_t part_elems, cudaStream_t s) {
   if (nw <= 0 || n_o <= 0 || n_a <= 0) return cudaSuccess;
   if (rpw <= 0) return cudaSuccess;
+  if (Y != nullptr && n_o >= 16 && n_a >= 16)
+    return param_reduce_tiled<T>(X, mx, Y, my, rpw, nw, n_o, n_a, G, P, off, ld, mode, part, part_elems, s);
   const unsigned gx = nblocks(n_o, RT), gy = nblocks(n_a, RT);
   if (mode == 1) {
     // grid.z is limited to 65535: loop over walker slices

@@ -109,6 +109,11 @@ template <class T>
 cudaError_t gemm_nt(const T* X, RowMap mx, const T* W, const T* bias, int bias_period, T* Y, RowMap my,
                     int64_t rows, int n_out, int K, bool accumulate, cudaStream_t s);
 
+// BF16 tensor-core GEMM (gemm_tc.cu): Y[r][n] = X[r][:] . W[n][:] (+ bias on
+// rows r % bias_period == 0); X, W BF16 K-major, Y FP32.
+cudaError_t gemm_bf16_tc(const void* X, int64_t rows, int K, int64_t ldx, const void* W, int n_out, const float* bias,
+                         int bias_period, float* Y, int64_t ldy, unsigned int* status, cudaStream_t s);
+
 // ---- forward kernels (forward.cu) ------------------------------------------
 // Sizes of one chunk of Bc walkers; C = channels (1 value-only, 3N+2 with jets).
 struct FwdDims {
@@ -130,6 +135,9 @@ struct FwdBuffers {
   T* js;     // [Bc][C][D]          sum_i f_i
   T* jh;     // [Bc][C][D]          W_J1 (sum_i f_i) + b_J1
   T* z0;     // [2][D]              W_h^0 E_spin
+  // BF16 mode only (nullptr otherwise): GEMM inputs of the embedding layers
+  void* msg_bf;  // [Bc][N][C][3D]  messages, BF16 (replaces msg)
+  void* F_bf;    // [Bc][N][C][D]   BF16 copy of the embeddings
 };
 
 template <class T>
@@ -148,7 +156,9 @@ cudaError_t launch_update(const dq_handle_s& h, const FwdDims& d, const T* param
                           FwdBuffers<T> b, cudaStream_t s);
 template <class T>
 cudaError_t launch_update_io(const dq_handle_s& h, const FwdDims& d, const T* params, bool from_spin, const T* P,
-                             const T* Fin, T* Fout, cudaStream_t s);
+                             const T* Fin, T* Fout, cudaStream_t s, void* Fbf = nullptr);
+// dst[k] = bf16(src[k]), k < n.
+cudaError_t launch_to_bf16(const float* src, void* dst, int64_t n, cudaStream_t s);
 template <class T>
 cudaError_t launch_orbital_det(const dq_handle_s& h, const FwdDims& d, const T* params, FwdBuffers<T> b,
                                cudaStream_t s);

@@ -22,6 +22,7 @@
 //   * the combination over determinants (Eq. 28), the Jastrow factor (Eq. 24),
 //     the electron cusp (Eq. 25), the Coulomb potential (Eq. 1) and the local
 //     energy (Eq. 31).
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include "common.cuh"
@@ -159,11 +160,16 @@ __global__ void layer0_node_kernel(const T* __restrict__ params, int D, int64_t 
 // of w_ij (only the six coordinates of electrons i and j) and the
 // electron-nucleus messages are added afterwards for the same outputs.
 // ---------------------------------------------------------------------------
-template <class T, int DC, int IB, int CB>
+template <class T>
+__device__ __forceinline__ T to_out(float v, T*) { return (T)v; }
+__device__ __forceinline__ double to_out(double v, double*) { return v; }
+__device__ __forceinline__ __nv_bfloat16 to_out(float v, __nv_bfloat16*) { return __float2bfloat16_rn(v); }
+
+template <class T, class TO, int DC, int IB, int CB>
 __global__ void __launch_bounds__(256)
     messages_kernel(const T* __restrict__ Z, const T* __restrict__ z0, const T* __restrict__ ew,
                     const T* __restrict__ geo, const T* __restrict__ Y, const int* __restrict__ pair_of, int N,
-                    int n_up, int M, int C, int D, int E, int n_ee, int ej, int z_const, T* __restrict__ msg) {
+                    int n_up, int M, int C, int D, int E, int n_ee, int ej, int z_const, TO* __restrict__ msg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int zc_rows = z_const ? 2 : N * C;     // z[j][c] rows (two spin rows if z is constant)
   T* Zs = reinterpret_cast<T*>(smem_raw);      // [zc_rows][DC]
@@ -213,7 +219,7 @@ __global__ void __launch_bounds__(256)
   const int ncb = (C + CB - 1) / CB;
   const int ntasks = (nib_up + nib_dn) * ncb;
   const T nuM = T(1) / T(M);
-  T* mb = msg + b * N * C * 3 * D + d0 + dd;
+  TO* mb = msg + b * N * C * 3 * D + d0 + dd;
   // z value: z[j][c] of this lane's feature
   auto zv = [&](int j, int c) -> T {
     if (z_const) return c == 0 ? Zs[(j < n_up ? 0 : 1) * DC + dd] : T(0);
@@ -265,67 +271,73 @@ __global__ void __launch_bounds__(256)
       }
     }
 
-    // product-rule corrections, nuclear messages, normalisation, store
+    // product-rule corrections, nuclear messages, normalisation, store.
+    // Rolled loop over the block's outputs (keeps the kernel small); the
+    // register accumulators are picked with predicated selects.
     const int n_same = up ? n_up : n_dn, n_opp = up ? n_dn : n_up;
     const T nu_s = T(1) / T(n_same - 1 > 1 ? n_same - 1 : 1);
     const T nu_o = T(1) / T(n_opp > 1 ? n_opp : 1);
-#pragma unroll
-    for (int a = 0; a < IB; ++a) {
-      if (a >= ni) continue;
+#pragma unroll 1
+    for (int aq = 0; aq < ni * nc; ++aq) {
+      const int a = aq / nc, q = aq % nc;
       const int i = i0 + a;
+      const int c = c0 + q;
+      T s = 0, o = 0, nn = 0;
 #pragma unroll
-      for (int q = 0; q < CB; ++q) {
-        if (q >= nc) continue;
-        const int c = c0 + q;
-        T s = as[a][q], o = ao[a][q], nn = 0;
-        const bool isJ = jets && c >= 1 && c < C - 1;
-        const bool isL = jets && c == C - 1;
-        if (isJ) {
-          const int e = (c - 1) / 3, x = (c - 1) % 3;
-          if (e == i) {
-            for (int j = 0; j < N; ++j) {
-              if (j == i) continue;
-              const int p = Ps[i * N + j];
-              const T u = (i < j ? Gs[p * 4 + 1 + x] : -Gs[p * 4 + 1 + x]);
-              const T t = W1p[p * DC + dd] * u * zv(j, 0);
-              if ((j < n_up) == up) s += t; else o += t;
-            }
-            for (int I = 0; I < M; ++I) {
-              const int en = i * M + I;
-              nn += WN[(en * ej + 1) * DC + dd] * Gs[(n_ee + en) * 4 + 1 + x] * Ys[I * DC + dd];
-            }
-          } else {
-            const int p = Ps[i * N + e];
-            const T u = (i < e ? Gs[p * 4 + 1 + x] : -Gs[p * 4 + 1 + x]);
-            const T t = W1p[p * DC + dd] * u * zv(e, 0);
-            if ((e < n_up) == up) s -= t; else o -= t;
+      for (int a2 = 0; a2 < IB; ++a2)
+#pragma unroll
+        for (int q2 = 0; q2 < CB; ++q2)
+          if (a2 == a && q2 == q) {
+            s = as[a2][q2];
+            o = ao[a2][q2];
           }
-        } else if (isL) {
+      const bool isJ = jets && c >= 1 && c < C - 1;
+      const bool isL = jets && c == C - 1;
+      if (isJ) {
+        const int e = (c - 1) / 3, x = (c - 1) % 3;
+        if (e == i) {
           for (int j = 0; j < N; ++j) {
             if (j == i) continue;
             const int p = Ps[i * N + j];
-            const T w1 = W1p[p * DC + dd], w2 = W2p[p * DC + dd];
-            const T sg = i < j ? T(1) : T(-1);
-            T t = (T(2) * w2 + T(4) * w1 / Gs[p * 4]) * zv(j, 0);
-            T cr = 0;
-            for (int x = 0; x < 3; ++x)
-              cr += sg * Gs[p * 4 + 1 + x] * (zv(j, 1 + 3 * i + x) - zv(j, 1 + 3 * j + x));
-            t += T(2) * w1 * cr;
+            const T u = (i < j ? Gs[p * 4 + 1 + x] : -Gs[p * 4 + 1 + x]);
+            const T t = W1p[p * DC + dd] * u * zv(j, 0);
             if ((j < n_up) == up) s += t; else o += t;
           }
           for (int I = 0; I < M; ++I) {
             const int en = i * M + I;
-            nn += (WN[(en * ej + 2) * DC + dd] + T(2) * WN[(en * ej + 1) * DC + dd] / Gs[(n_ee + en) * 4]) *
-                  Ys[I * DC + dd];
+            nn += WN[(en * ej + 1) * DC + dd] * Gs[(n_ee + en) * 4 + 1 + x] * Ys[I * DC + dd];
           }
-        } else if (c == 0) {
-          for (int I = 0; I < M; ++I) nn += WN[(i * M + I) * ej * DC + dd] * Ys[I * DC + dd];
+        } else {
+          const int p = Ps[i * N + e];
+          const T u = (i < e ? Gs[p * 4 + 1 + x] : -Gs[p * 4 + 1 + x]);
+          const T t = W1p[p * DC + dd] * u * zv(e, 0);
+          if ((e < n_up) == up) s -= t; else o -= t;
         }
-        T* out = mb + ((int64_t)i * C + c) * 3 * D;
-        out[0] = s * nu_s;
-        out[D] = o * nu_o;
-        out[2 * D] = nn * nuM;
+      } else if (isL) {
+        for (int j = 0; j < N; ++j) {
+          if (j == i) continue;
+          const int p = Ps[i * N + j];
+          const T w1 = W1p[p * DC + dd], w2 = W2p[p * DC + dd];
+          const T sg = i < j ? T(1) : T(-1);
+          T t = (T(2) * w2 + T(4) * w1 / Gs[p * 4]) * zv(j, 0);
+          T cr = 0;
+          for (int x = 0; x < 3; ++x)
+            cr += sg * Gs[p * 4 + 1 + x] * (zv(j, 1 + 3 * i + x) - zv(j, 1 + 3 * j + x));
+          t += T(2) * w1 * cr;
+          if ((j < n_up) == up) s += t; else o += t;
+        }
+        for (int I = 0; I < M; ++I) {
+          const int en = i * M + I;
+          nn += (WN[(en * ej + 2) * DC + dd] + T(2) * WN[(en * ej + 1) * DC + dd] / Gs[(n_ee + en) * 4]) *
+                Ys[I * DC + dd];
+        }
+      } else if (c == 0) {
+        for (int I = 0; I < M; ++I) nn += WN[(i * M + I) * ej * DC + dd] * Ys[I * DC + dd];
       }
+      TO* out = mb + ((int64_t)i * C + c) * 3 * D;
+      out[0] = to_out(s * nu_s, out);
+      out[D] = to_out(o * nu_o, out);
+      out[2 * D] = to_out(nn * nuM, out);
     }
   }
 }
@@ -335,7 +347,8 @@ __global__ void __launch_bounds__(256)
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void update_kernel(const T* __restrict__ P, const T* Fin, T* Fout, const T* __restrict__ E_spin,
-                              int64_t Bc, int N, int n_up, int C, int D, int from_spin) {
+                              int64_t Bc, int N, int n_up, int C, int D, int from_spin,
+                              __nv_bfloat16* __restrict__ Fbf) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= Bc * N * D) return;
   const int a = (int)(gid % D);
@@ -357,6 +370,15 @@ __global__ void update_kernel(const T* __restrict__ P, const T* Fin, T* Fout, co
     const int64_t cl = (int64_t)(C - 1) * D;
     f[cl] = (from_spin ? T(0) : fi[cl]) + dt * p[cl] - T(2) * t * dt * ss;
   }
+  if (Fbf) {  // BF16 copy of the embeddings: the input of the next node-map GEMM
+    __nv_bfloat16* fb = Fbf + bi * C * D + a;
+    for (int c = 0; c < C; ++c) fb[(int64_t)c * D] = __float2bfloat16_rn((float)f[(int64_t)c * D]);
+  }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) dst[e] = __float2bfloat16_rn(src[e]);
 }
 
 // ---------------------------------------------------------------------------
@@ -369,9 +391,11 @@ __global__ void update_kernel(const T* __restrict__ P, const T* Fin, T* Fout, co
 // pivoted LU), decides whether that is accurate enough: near-nodal matrices
 // (kappa above the threshold) are redone in FP64.  The local-energy path
 // needs the determinant derivatives (tangent contractions with A^-1), whose
-// FP32 rounding doubles the error of E_loc at near-nodal walkers; it takes
-// the FP64 path for every matrix.  FP64 instructions issue at a small
-// fraction of the FP32 rate on this GPU.  In FP64 mode every matrix is FP64.
+// plain FP32 rounding doubles the error of E_loc at near-nodal walkers: it
+// factorises every matrix in FP64 and, in the FP32 modes, contracts the
+// tangents in double-float arithmetic on the FP32 pipes, because FP64
+// instructions issue at a small fraction of the FP32 rate on this GPU.  In
+// FP64 mode every step is FP64.
 // ---------------------------------------------------------------------------
 #ifndef DQ_KAPPA_FP32_VALUE
 #define DQ_KAPPA_FP32_VALUE 1000.0f  // value-only log|det| in FP32 below this
@@ -508,6 +532,107 @@ __device__ double det_tangents(const T* phib, const T* env, const T* jenv, const
   return lap;
 }
 
+// Double-float arithmetic (an FP32 pair hi + lo) from error-free
+// transformations: TwoSum (Knuth) and TwoProd via a fused multiply-add
+// (Ogita, Rump, Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput.
+// 26, 2005).  Explicit round-to-nearest intrinsics keep the compiler from
+// contracting the operations that must stay exact.
+struct dfloat {
+  float hi, lo;
+};
+__device__ __forceinline__ dfloat two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dfloat quick_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+  dfloat s = two_sum(a.hi, b.hi);
+  return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ dfloat warp_sum_df(dfloat v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dfloat w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = df_add(v, w);
+  }
+  return v;
+}
+
+// Determinant derivatives in double-float: A^-1 = Ahi + Alo (split from the
+// FP64 inverse), d_t A exact in FP32 (it comes from the FP32 network), each
+// entry of X = A^-1 d_t A a compensated dot product; tr X and tr X^2 in
+// double-float.  Same quantities as det_tangents, on the FP32 pipes.
+template <class T>
+__device__ double det_tangents_df(const T* phib, const T* env, const T* jenv, const T* lenv, const T* phi0,
+                                  const float* Ahi, const float* Alo, float* tmp, float* Xhi, float* Xlo, int n,
+                                  int nn, int i0, int p, int C, int Wo, int N3, int lane, double* out) {
+  double lap = 0.0;
+  for (int t = 0; t <= N3; ++t) {
+    const bool is_lap = t == N3;
+    const int c = is_lap ? C - 1 : 1 + t;
+    for (int q = lane; q < n * n; q += 32) {
+      const int ii = q / n, k = q % n, o = p * n + k, i = i0 + ii;
+      const T* ph = phib + (int64_t)i * C * Wo + o;
+      T v = ph[(int64_t)c * Wo] * env[q];
+      if (is_lap) {
+        v += phi0[q] * lenv[q];
+        for (int x = 0; x < 3; ++x) v += T(2) * ph[(int64_t)(1 + 3 * i + x) * Wo] * jenv[x * nn + q];
+      } else if (t / 3 == i) {
+        v += phi0[q] * jenv[(t % 3) * nn + q];
+      }
+      tmp[q] = (float)v;
+    }
+    __syncwarp();
+    dfloat trp = {0.f, 0.f};
+    for (int q = lane; q < n * n; q += 32) {
+      const int a = q / n, m = q % n;
+      float sh = 0.f, cl = 0.f;
+      for (int l = 0; l < n; ++l) {
+        const float y = tmp[l * n + m], xh = Ahi[a * n + l];
+        const float pr = __fmul_rn(xh, y);
+        const float ep = __fmaf_rn(xh, y, -pr);
+        const dfloat ss = two_sum(sh, pr);
+        sh = ss.hi;
+        cl = __fmaf_rn(Alo[a * n + l], y, __fadd_rn(cl, __fadd_rn(ep, ss.lo)));
+      }
+      const dfloat x = quick_two_sum(sh, cl);
+      Xhi[q] = x.hi;
+      Xlo[q] = x.lo;
+      if (a == m) trp = df_add(trp, x);
+    }
+    const dfloat trs = warp_sum_df(trp);
+    const double tr = (double)trs.hi + (double)trs.lo;
+    __syncwarp();
+    if (is_lap) {
+      lap += tr;
+    } else {
+      if (lane == 0) out[2 + t] = tr;
+      dfloat s2 = {0.f, 0.f};
+      for (int q = lane; q < n * n; q += 32) {
+        const int a = q / n, m = q % n;
+        s2 = df_add(s2, df_mul({Xhi[a * n + m], Xlo[a * n + m]}, {Xhi[m * n + a], Xlo[m * n + a]}));
+      }
+      const dfloat s2s = warp_sum_df(s2);
+      lap -= (double)s2s.hi + (double)s2s.lo;
+    }
+    __syncwarp();
+  }
+  return lap;
+}
+
 template <class T>
 __global__ void __launch_bounds__(128)
     orbital_det_kernel(const T* __restrict__ phi, const T* __restrict__ geo, const T* __restrict__ params,
@@ -619,11 +744,23 @@ __global__ void __launch_bounds__(128)
   }
   if (!jets) return;
   double lap;
-  if (fp64) {
-    warp_inverse<double>(LUd, perm, n, lane, Ainvd);
-    lap = det_tangents<T, double>(phib, env, jenv, lenv, phi0, Ainvd, LUd, Xd, n, nn, i0, p, C, Wo, N3, lane, out);
+  warp_inverse<double>(LUd, perm, n, lane, Ainvd);
+  if constexpr (sizeof(T) == 4) {
+    // FP32 modes: tangent contractions in double-float on the FP32 pipes.
+    float* Ahi = reinterpret_cast<float*>(LUt);
+    float* Alo = reinterpret_cast<float*>(Ainvt);
+    float* Xlo = reinterpret_cast<float*>(Xd);
+    for (int q = lane; q < n * n; q += 32) {
+      const double a = Ainvd[q];
+      const float h = (float)a;
+      Ahi[q] = h;
+      Alo[q] = (float)(a - (double)h);
+    }
+    __syncwarp();
+    lap = det_tangents_df<T>(phib, env, jenv, lenv, phi0, Ahi, Alo, reinterpret_cast<float*>(tmp),
+                             reinterpret_cast<float*>(Xt), Xlo, n, nn, i0, p, C, Wo, N3, lane, out);
   } else {
-    lap = det_tangents<T, T>(phib, env, jenv, lenv, phi0, Ainvt, tmp, Xt, n, nn, i0, p, C, Wo, N3, lane, out);
+    lap = det_tangents<T, double>(phib, env, jenv, lenv, phi0, Ainvd, LUd, Xd, n, nn, i0, p, C, Wo, N3, lane, out);
   }
   if (lane == 0) out[2 + N3] = lap;
 }
@@ -876,11 +1013,11 @@ size_t message_smem(const dq_handle_s& h, const FwdDims& d, int DC, bool z_const
   return vals * sizeof(T) + N * N * sizeof(int);
 }
 constexpr int kMsgIB = 4;
-template <class T, int DC>
-cudaError_t launch_messages_dc(const dq_handle_s& h, const FwdDims& d, const T* params, int l, bool z_const,
-                               FwdBuffers<T> b, size_t smem, cudaStream_t s) {
+template <class T, class TO, int DC>
+cudaError_t launch_messages_dct(const dq_handle_s& h, const FwdDims& d, const T* params, int l, bool z_const,
+                                FwdBuffers<T> b, TO* out, size_t smem, cudaStream_t s) {
   constexpr int CB = sizeof(T) == 4 ? 4 : 2;
-  auto kern = messages_kernel<T, DC, kMsgIB, CB>;
+  auto kern = messages_kernel<T, TO, DC, kMsgIB, CB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int nib = (d.n_up + kMsgIB - 1) / kMsgIB + (d.n_dn + kMsgIB - 1) / kMsgIB;
@@ -889,8 +1026,18 @@ cudaError_t launch_messages_dc(const dq_handle_s& h, const FwdDims& d, const T* 
   dim3 grid((unsigned)d.Bc, d.D / DC);
   kern<<<grid, groups * DC, smem, s>>>(b.Z, b.z0, b.ew, b.geo, params + h.off.layer[l].Y, h.d_pair_of, d.N, d.n_up,
                                        d.M, d.C, d.D, h.edges.n_all, h.edges.n_ee, d.C > 1 ? 3 : 1, z_const ? 1 : 0,
-                                       b.msg);
+                                       out);
   return cudaGetLastError();
+}
+template <class T, int DC>
+cudaError_t launch_messages_dc(const dq_handle_s& h, const FwdDims& d, const T* params, int l, bool z_const,
+                               FwdBuffers<T> b, size_t smem, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (b.msg_bf)
+      return launch_messages_dct<T, __nv_bfloat16, DC>(h, d, params, l, z_const, b,
+                                                       static_cast<__nv_bfloat16*>(b.msg_bf), smem, s);
+  }
+  return launch_messages_dct<T, T, DC>(h, d, params, l, z_const, b, b.msg, smem, s);
 }
 }  // namespace
 
@@ -915,14 +1062,20 @@ cudaError_t launch_messages(const dq_handle_s& h, const FwdDims& d, const T* par
 template <class T>
 cudaError_t launch_update(const dq_handle_s& h, const FwdDims& d, const T* params, bool from_spin, FwdBuffers<T> b,
                           cudaStream_t s) {
-  return launch_update_io<T>(h, d, params, from_spin, b.Z, b.F, b.F, s);
+  return launch_update_io<T>(h, d, params, from_spin, b.Z, b.F, b.F, s, b.F_bf);
 }
 
 template <class T>
 cudaError_t launch_update_io(const dq_handle_s& h, const FwdDims& d, const T* params, bool from_spin, const T* P,
-                             const T* Fin, T* Fout, cudaStream_t s) {
+                             const T* Fin, T* Fout, cudaStream_t s, void* Fbf) {
   update_kernel<T><<<blocks(d.Bc * d.N * d.D, 256), 256, 0, s>>>(P, Fin, Fout, params + h.off.E_spin, d.Bc, d.N,
-                                                                 d.n_up, d.C, d.D, from_spin ? 1 : 0);
+                                                                 d.n_up, d.C, d.D, from_spin ? 1 : 0,
+                                                                 static_cast<__nv_bfloat16*>(Fbf));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_bf16(const float* src, void* dst, int64_t n, cudaStream_t s) {
+  to_bf16_kernel<<<blocks(n, 256), 256, 0, s>>>(src, static_cast<__nv_bfloat16*>(dst), n);
   return cudaGetLastError();
 }
 
@@ -977,7 +1130,7 @@ cudaError_t launch_combine(const dq_handle_s& h, const FwdDims& d, const T* para
   template cudaError_t launch_update<T>(const dq_handle_s&, const FwdDims&, const T*, bool, FwdBuffers<T>,        \
                                         cudaStream_t);                                                            \
   template cudaError_t launch_update_io<T>(const dq_handle_s&, const FwdDims&, const T*, bool, const T*, const T*, \
-                                           T*, cudaStream_t);                                                     \
+                                           T*, cudaStream_t, void*);                                              \
   template cudaError_t launch_orbital_det<T>(const dq_handle_s&, const FwdDims&, const T*, FwdBuffers<T>,         \
                                              cudaStream_t);                                                       \
   template cudaError_t launch_jastrow_sum<T>(const dq_handle_s&, const FwdDims&, FwdBuffers<T>, cudaStream_t);    \

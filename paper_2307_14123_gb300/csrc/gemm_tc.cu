@@ -1,0 +1,259 @@
+// BF16 tensor-core GEMM for the embedding layers (5th-generation tensor cores).
+//
+//   Y[r][n] = sum_k X[r][k] W[n][k] + (r % bias_period == 0 ? bias[n] : 0)
+//
+// X [rows][K] and W [n_out][K] are BF16, K-major (row stride ldx, K); Y is
+// FP32 with row stride ldy.  This is the linear map of the graph-convolution
+// update (W_g, Eq. 18) and of the node map (W_h, Eq. 17) acting on all
+// value / Jacobian / Laplacian channels at once: the rows are the channels of
+// every node of every walker, so one launch is one large dense contraction.
+//
+// One CTA computes a 128 x 128 output tile:
+//   * warp 0, lane 0 streams 128 x 64 tiles of X and W into a 4-stage ring of
+//     shared-memory buffers with TMA (cp.async.bulk.tensor, 128-byte swizzle),
+//     completing on "full" mbarriers;
+//   * warp 1, lane 0 issues tcgen05.mma (kind::f16, BF16 inputs, FP32
+//     accumulator in tensor memory, M = 128, N = 128, K = 16 per instruction)
+//     and releases each stage with tcgen05.commit on its "empty" mbarrier;
+//   * all four warps read the accumulator back with tcgen05.ld (warp w owns
+//     tensor-memory lanes 32w..32w+31, i.e. rows 32w..32w+31) and store FP32.
+// Rows beyond `rows` and columns beyond n_out are zero-filled by TMA and not
+// stored.  Every mbarrier wait is bounded (about one second of clock); on
+// timeout the kernel sets DQ_FLAG_TIMEOUT in the status word, skips the rest
+// and still releases its tensor memory.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace dq {
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 4;
+constexpr uint32_t TC_TILE_A = TC_BM * TC_BK * 2;  // 16 KB
+constexpr uint32_t TC_TILE_B = TC_BN * TC_BK * 2;  // 16 KB
+constexpr uint32_t TC_TMEM_COLS = 128;
+constexpr long long kWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+// Shared-memory matrix descriptor of a K-major tile in the 128-byte swizzle
+// layout: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;         // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)2 << 61;                   // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor: kind::f16, A and B BF16 (K-major), D FP32, M x N.
+constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+    gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                        int64_t rows, int n_out, int K, const float* __restrict__ bias, int bias_period,
+                        float* __restrict__ Y, int64_t ldy, unsigned int* __restrict__ status) {
+  extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + TC_STAGES * TC_TILE_A;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + TC_STAGES * TC_TILE_B);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* done = empty + TC_STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  __shared__ int s_abort;
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t m0 = (int64_t)blockIdx.x * TC_BM;
+  const int n0 = blockIdx.y * TC_BN;
+  const int nk = K / TC_BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % TC_STAGES;
+      if (kb >= TC_STAGES && !mbar_wait(&empty[s], ((kb / TC_STAGES) + 1) & 1)) {
+        s_abort = 1;
+        break;
+      }
+      mbar_expect_tx(&full[s], TC_TILE_A + TC_TILE_B);
+      tma_load_2d(sA + s * TC_TILE_A, &tmA, kb * TC_BK, (int)m0, &full[s]);
+      tma_load_2d(sB + s * TC_TILE_B, &tmB, kb * TC_BK, n0, &full[s]);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = tc_idesc(TC_BM, TC_BN);
+    bool ok = true;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % TC_STAGES;
+      if (!mbar_wait(&full[s], (kb / TC_STAGES) & 1)) {
+        ok = false;
+        s_abort = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sA + s * TC_TILE_A), b0 = smem_u32(sB + s * TC_TILE_B);
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 16; ++kk)
+        umma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc, (kb | kk) ? 1u : 0u);
+      umma_commit(&empty[s]);
+    }
+    if (ok) umma_commit(done);
+  }
+  __syncwarp();
+
+  // Epilogue: TMEM -> registers -> global.
+  const bool ok = mbar_wait(done, 0);
+  tc_fence_after();
+  if (ok && !s_abort) {
+    const int64_t row = m0 + warp * 32 + lane;
+    const bool add_bias = bias != nullptr && (row % bias_period) == 0;
+    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (row < rows) {
+        float* y = Y + row * ldy;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + c0 + j;
+          if (n < n_out) y[n] = __uint_as_float(v[j]) + (add_bias ? bias[n] : 0.f);
+        }
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    atomicOr(status, (unsigned)DQ_FLAG_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, int64_t rows, int K, int64_t ld, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+constexpr size_t tc_smem_bytes() { return 1024 + TC_STAGES * (TC_TILE_A + TC_TILE_B) + (2 * TC_STAGES + 1) * 8 + 16; }
+
+}  // namespace
+
+cudaError_t gemm_bf16_tc(const void* X, int64_t rows, int K, int64_t ldx, const void* W, int n_out, const float* bias,
+                         int bias_period, float* Y, int64_t ldy, unsigned int* status, cudaStream_t s) {
+  if (rows <= 0 || n_out <= 0) return cudaSuccess;
+  if (K % TC_BK || ldx % 8 || (uintptr_t)X % 16 || (uintptr_t)W % 16 || bias_period <= 0)
+    return cudaErrorInvalidValue;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, X, rows, K, ldx, TC_BM) || !make_map(&mb, W, n_out, K, K, TC_BN)) return cudaErrorInvalidValue;
+  const size_t smem = tc_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((rows + TC_BM - 1) / TC_BM), (unsigned)((n_out + TC_BN - 1) / TC_BN));
+  gemm_bf16_tc_kernel<<<grid, 128, smem, s>>>(ma, mb, rows, n_out, K, bias, bias_period, Y, ldy, status);
+  return cudaGetLastError();
+}
+
+}  // namespace dq

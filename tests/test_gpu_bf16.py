@@ -1,0 +1,66 @@
+"""BF16 mode: the embedding-layer GEMMs (graph-convolution update W_g and node
+map W_h) run on the tensor cores with BF16 inputs and FP32 accumulation;
+everything else as in FP32 mode (FP64 LU, double-float determinant
+derivatives, FP64 walker sums).
+
+The result is compared with the FP32 GPU path and with the FP64 oracle.
+BF16 keeps 8 significant bits, so per-walker local energies move by about
+2^-9 relative to the kinetic terms they are formed from: the per-walker bound
+is |dE| <= max(1e-2 Ha, 2e-2 S_b).  What the precision mode is for is the
+batch mean: the change of the mean local energy and of its variance against
+the FP32 path are reported, and the mean must agree within the statistical
+error of the per-walker differences (4 sigma).
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2307_14123_gb300 import fixtures as fx
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2307_14123_gb300 import _build
+    _build.build()
+    oracle.build()
+    oracle.Oracle.set_threads(os.cpu_count() or 1)
+
+
+def _run(wl, precision, B):
+    from paper_2307_14123_gb300 import Ansatz
+    h = Ansatz(wl.system, wl.cfg, precision, device="cuda:0")
+    theta = fx.init_params(wl.system, wl.cfg, wl.param_seed).astype(np.float32)
+    r = fx.init_walkers(wl.system, B, wl.walker_seed).astype(np.float32)
+    la, sg, el = h.local_energy(torch.tensor(theta, device="cuda:0"), torch.tensor(r, device="cuda:0"))
+    assert h.device_status() & 0x4 == 0  # no bounded wait gave up
+    return theta, r, la.cpu().numpy().astype(np.float64), sg.cpu().numpy(), el.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("name,B,n_oracle", [("n2_fp32", 4096, 12), ("c4h4_bf16", 2048, 0)])
+def test_bf16_mode_against_fp32_and_oracle(name, B, n_oracle):
+    wl = fx.workload(name)
+    theta, r, la16, sg16, el16 = _run(wl, "bf16", B)
+    _, _, la32, sg32, el32 = _run(wl, "fp32", B)
+    ok = (sg16 != 0) & (sg32 != 0) & np.isfinite(el16) & np.isfinite(el32)
+    d = el16[ok] - el32[ok]
+    mean_shift = d.mean()
+    sigma = d.std() / np.sqrt(d.size)
+    var16, var32 = el16[ok].var(), el32[ok].var()
+    print(f"{name}: mean E_loc FP32 {el32[ok].mean():.6f}, BF16 {el16[ok].mean():.6f}, shift {mean_shift:.3e} "
+          f"+- {sigma:.3e}; variance FP32 {var32:.4e} BF16 {var16:.4e} (rel change {var16 / var32 - 1:.3e}); "
+          f"median |dE| {np.median(np.abs(d)):.3e}; sign agreement {np.mean(sg16 == sg32):.4f}")
+    assert abs(mean_shift) <= 4 * sigma + 1e-6
+    assert np.mean(sg16 == sg32) > 0.99
+    if n_oracle:
+        idx = np.linspace(0, B - 1, n_oracle).astype(int)
+        ref = oracle.Oracle(wl.system, wl.cfg).local_energy(theta.astype(np.float64), r[idx].astype(np.float64),
+                                                            with_grad=True)
+        S = 0.5 * (np.abs(ref["lap"]) + np.sum(ref["grad"] ** 2, axis=1))
+        e = np.abs(el16[idx] - ref["e_loc"])
+        print(f"{name}: BF16 vs oracle |dE|/S max {np.max(e / S):.2e} median {np.median(e / S):.2e}")
+        assert np.all(e <= np.maximum(1e-2, 2e-2 * S))
