@@ -194,33 +194,40 @@ def peaks():
         "fallback"
 
 
-def gemm_flops(kind, wl, chunk):
-    """Algorithmic FLOPs of one launch of a jet-forward GEMM over `chunk` walkers."""
+def roofline_for(kind, ms, n, wl, chunk, pk, how):
+    """Roofline entry of one kernel kind: algorithmic work per launch / average launch time."""
     s, c = wl.system, wl.cfg
-    N, D, K = s.n_elec, c.width, c.n_det
+    N, D, M = s.n_elec, c.width, s.n_nuc
     C = 3 * N + 2
-    if kind == "jet.gemm_update":
-        return 2.0 * chunk * N * C * 3 * D * D
-    if kind == "jet.gemm_node":
-        return 2.0 * chunk * N * C * D * D
+    rows = chunk * N * C
+    E = N * (N - 1) // 2 + N * M
+    t = ms / n / 1e3
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    bf16 = wl.precision == "bf16"
+    if kind in ("jet.gemm_update", "jet.gemm_node"):
+        k = 3 * D if kind == "jet.gemm_update" else D
+        flops = 2.0 * rows * k * D
+        if bf16:
+            peak, bound, src = pk["bf16_tflops_sustained"], "tensor", f"{how} bf16 sustained (cuBLAS loop)"
+        elif wl.precision == "fp64":
+            peak, bound, src = 1.25, "alu", "nominal FP64"
+        else:
+            peak, bound, src = fp32_peak, "alu", f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"
+        ach = flops / t / 1e12
+        return {"kernel": kind, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "peak_source": src, "flops_per_launch": flops, "avg_launch_ms": ms / n}
+    if kind == "jet.messages":
+        el = 8 if wl.precision == "fp64" else 4
+        out_el = 2 if bf16 else el
+        L = c.n_layers
+        # average over the L launches of one forward: layer 0 reads no node channels
+        byts = (rows * D * el * (L - 1) / L) + chunk * E * 3 * D * el + rows * 3 * D * out_el
+        ach = byts / t / 1e9
+        return {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": f"{how} copy bandwidth",
+                "bytes_per_launch": byts, "avg_launch_ms": ms / n}
     return None
-
-
-def profile_case(args):
-    import torch
-
-    from paper_2307_14123_gb300 import Ansatz
-    from paper_2307_14123_gb300 import fixtures as fx
-
-    wl = fx.workload(args.workload)
-    dt = torch.float64 if wl.precision == "fp64" else torch.float32
-    h = Ansatz(wl.system, wl.cfg, "fp64" if wl.precision == "fp64" else "fp32", device="cuda:0")
-    theta = torch.tensor(fx.init_params(wl.system, wl.cfg, wl.param_seed), dtype=dt, device="cuda:0")
-    r = torch.tensor(fx.init_walkers(wl.system, args.profile_case, wl.walker_seed), dtype=dt, device="cuda:0")
-    la, sg, el = h.local_energy(theta, r)
-    torch.cuda.synchronize()
-    print("profile case done:", args.profile_case, "walkers, mean E_loc", float(el.double().mean()))
-    return 0
 
 
 def main():
@@ -246,7 +253,7 @@ def main():
     wl = fx.workload(args.workload)
     B = wl.B
     dt = torch.float64 if wl.precision == "fp64" else torch.float32
-    h = Ansatz(wl.system, wl.cfg, "fp64" if wl.precision == "fp64" else "fp32", device=dev)
+    h = Ansatz(wl.system, wl.cfg, wl.precision, device=dev)
     theta = torch.tensor(fx.init_params(wl.system, wl.cfg, wl.param_seed), dtype=dt, device=dev)
     r0 = fx.init_walkers(wl.system, B, wl.walker_seed, walker_offset=rank * B)
     r = torch.tensor(r0, dtype=dt, device=dev)
@@ -305,25 +312,26 @@ def main():
     launches = sum(n for _, (ms, n) in prof.items())
     gpu_time_ms = sum(ms for _, (ms, n) in prof.items())
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel (and of the other main kernels)
     pk, how = peaks()
+    chunk = min(B, h.max_chunk())
     dom = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
     roof = None
+    others = []
+    for kind in ("jet.gemm_update", "jet.messages", "jet.gemm_node"):
+        if kind in prof:
+            e = roofline_for(kind, prof[kind][0], prof[kind][1], wl, chunk, pk, how)
+            if e:
+                e["share_of_gpu_time"] = prof[kind][0] / gpu_time_ms
+                others.append(e)
     if dom is not None:
-        ms, n = prof[dom]
-        chunk = min(B, h.max_chunk())
-        flops = gemm_flops(dom, wl, chunk)
-        if flops is not None:
-            sm_mhz = pk.get("sm_max_mhz", 2070.0)
-            if wl.precision == "fp64":
-                peak = 1.25  # TFLOP/s FP64 (nominal, CUDA cores)
-            else:
-                peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 x max clock
-            ach = flops / (ms / n / 1e3) / 1e12
-            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None, "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"
-                    if wl.precision != "fp64" else "nominal FP64", "flops_per_launch": flops,
-                    "avg_launch_ms": ms / n, "share_of_gpu_time": ms / gpu_time_ms}
+        roof = roofline_for(dom, prof[dom][0], prof[dom][1], wl, chunk, pk, how)
+        if roof:
+            roof["share_of_gpu_time"] = prof[dom][0] / gpu_time_ms
+        else:
+            roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+                    "traffic": None, "note": "no roofline formula for this kernel kind",
+                    "share_of_gpu_time": prof[dom][0] / gpu_time_ms}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -381,9 +389,11 @@ def main():
         cfg.update({"step": step_desc, "l2": "flushed before every timed step (256 MB write)"})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl.precision == "fp64" else "f32",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16+f32"}[wl.precision],
                 "data": "synthetic (seeded walkers and random-init weights)", "config": cfg,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "roofline": roof, "roofline_main_kernels": others, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches,
                 "clocks": clk,
                 "local_energy_only": {"value": B * world * args.steps / (jet_ms / 1e3) if jet_ms else None,
                                       "unit": UNIT, "note": "sum of the local_energy kernels' device time"},

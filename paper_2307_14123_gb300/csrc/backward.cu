@@ -454,6 +454,32 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Column sums S[o] = sum_r X[r][o] (bias-type gradients): one thread per
+// column, consecutive threads on consecutive columns (coalesced), rows of the
+// walker range read in order.  blockIdx.y: walker (per-walker mode) or split.
+template <class T>
+__global__ void colsum_kernel(const T* __restrict__ X, RowMap mx, int rpw, int64_t nw, int n_o, T* __restrict__ G,
+                              int64_t P, int64_t off, int ld, int mode, int64_t walkers_per_split,
+                              T* __restrict__ part) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n_o) return;
+  int64_t wb0, wb1;
+  if (mode == 1) {
+    wb0 = blockIdx.y;
+    wb1 = wb0 + 1;
+  } else {
+    wb0 = (int64_t)blockIdx.y * walkers_per_split;
+    wb1 = min(nw, wb0 + walkers_per_split);
+  }
+  T acc = 0;
+  for (int64_t r = wb0 * rpw; r < wb1 * rpw; ++r)
+    acc += X[(r / mx.rows_per_seg) * mx.seg_stride + (r % mx.rows_per_seg) * mx.ld + o];
+  if (mode == 1)
+    G[wb0 * P + off + (int64_t)o * ld] = acc;
+  else
+    part[(int64_t)blockIdx.y * n_o + o] = acc;
+}
+
 template <class T>
 __global__ void reduce_splits_kernel(const T* __restrict__ part, int splits, int n_o, int n_a, T* __restrict__ G,
                                      int64_t off, int ld) {
@@ -641,6 +667,28 @@ cudaError_t param_reduce(const T* X, RowMap mx, const T* Y, RowMap my, int rpw, 
   if (rpw <= 0) return cudaSuccess;
   if (Y != nullptr && n_o >= 16 && n_a >= 16)
     return param_reduce_tiled<T>(X, mx, Y, my, rpw, nw, n_o, n_a, G, P, off, ld, mode, part, part_elems, s);
+  if (Y == nullptr && n_a == 1) {
+    const unsigned gx = nblocks(n_o, 128);
+    if (mode == 1) {
+      for (int64_t w0 = 0; w0 < nw; w0 += 65535) {
+        const int64_t nws = nw - w0 < 65535 ? nw - w0 : 65535;
+        const int64_t r_off = w0 * rpw;
+        const T* Xo = X + (r_off / mx.rows_per_seg) * mx.seg_stride + (r_off % mx.rows_per_seg) * mx.ld;
+        colsum_kernel<T><<<dim3(gx, (unsigned)nws), 128, 0, s>>>(Xo, mx, rpw, nws, n_o, G + w0 * P, P, off, ld, 1, 1,
+                                                                 nullptr);
+      }
+      return cudaGetLastError();
+    }
+    int64_t splits = (nw + 15) / 16;  // 16 walkers per thread
+    if (splits * n_o > part_elems) splits = part_elems / n_o;
+    if (splits < 1) return cudaErrorInvalidValue;
+    if (splits > 65535) splits = 65535;
+    const int64_t wps = (nw + splits - 1) / splits;
+    splits = (nw + wps - 1) / wps;
+    colsum_kernel<T><<<dim3(gx, (unsigned)splits), 128, 0, s>>>(X, mx, rpw, nw, n_o, G, P, off, ld, 0, wps, part);
+    reduce_splits_kernel<T><<<nblocks(n_o, 256), 256, 0, s>>>(part, (int)splits, n_o, 1, G, off, ld);
+    return cudaGetLastError();
+  }
   const unsigned gx = nblocks(n_o, RT), gy = nblocks(n_a, RT);
   if (mode == 1) {
     // grid.z is limited to 65535: loop over walker slices

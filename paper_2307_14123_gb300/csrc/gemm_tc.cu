@@ -9,7 +9,7 @@
 // every node of every walker, so one launch is one large dense contraction.
 //
 // One CTA computes a 128 x 128 output tile:
-//   * warp 0, lane 0 streams 128 x 64 tiles of X and W into a 4-stage ring of
+//   * warp 0, lane 0 streams 128 x 64 tiles of X and W into a 3-stage ring of
 //     shared-memory buffers with TMA (cp.async.bulk.tensor, 128-byte swizzle),
 //     completing on "full" mbarriers;
 //   * warp 1, lane 0 issues tcgen05.mma (kind::f16, BF16 inputs, FP32
@@ -30,7 +30,7 @@
 namespace dq {
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 4;
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 64, TC_STAGES = 3;
 constexpr uint32_t TC_TILE_A = TC_BM * TC_BK * 2;  // 16 KB
 constexpr uint32_t TC_TILE_B = TC_BN * TC_BK * 2;  // 16 KB
 constexpr uint32_t TC_TMEM_COLS = 128;
@@ -107,7 +107,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(128, 2)
     gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                         int64_t rows, int n_out, int K, const float* __restrict__ bias, int bias_period,
                         float* __restrict__ Y, int64_t ldy, unsigned int* __restrict__ status) {

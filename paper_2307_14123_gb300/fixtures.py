@@ -375,6 +375,9 @@ def workload(name):
     if name == "n2_fp32":  # N2, D=128, L=3, K=16, 4096 walkers, seed 1
         return Workload(name, molecule("N2"), AnsatzCfg(128, 3, 16), 4096, 1, 1, "fp32",
                         {"mcmc_steps": 1, "step_size": 0.2})
+    if name == "n2_bf16":  # the N2 workload with the BF16 embedding GEMMs
+        return Workload(name, molecule("N2"), AnsatzCfg(128, 3, 16), 4096, 1, 1, "bf16",
+                        {"mcmc_steps": 1, "step_size": 0.2})
     if name == "c4h4_bf16":  # C4H4, D=256, L=4, K=32, 8192 walkers
         return Workload(name, molecule("C4H4"), AnsatzCfg(256, 4, 32), 8192, 3, 3, "bf16")
     raise KeyError(name)
