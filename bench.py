@@ -45,7 +45,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--profile-case", type=int, default=0, metavar="B",
-                   help="run one local_energy on B walkers of the workload and exit (small case for ncu)")
+                   help="run one call on B walkers of the workload and exit (small case for ncu)")
+    p.add_argument("--profile-op", default="local_energy", choices=["local_energy", "grad", "mcmc"])
     return p.parse_args()
 
 
@@ -228,6 +229,30 @@ def roofline_for(kind, ms, n, wl, chunk, pk, how):
                 "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": f"{how} copy bandwidth",
                 "bytes_per_launch": byts, "avg_launch_ms": ms / n}
     return None
+
+
+def profile_case(args):
+    import torch
+
+    from paper_2307_14123_gb300 import Ansatz
+    from paper_2307_14123_gb300 import fixtures as fx
+
+    wl = fx.workload(args.workload)
+    dt = torch.float64 if wl.precision == "fp64" else torch.float32
+    h = Ansatz(wl.system, wl.cfg, wl.precision, device="cuda:0")
+    theta = torch.tensor(fx.init_params(wl.system, wl.cfg, wl.param_seed), dtype=dt, device="cuda:0")
+    r = torch.tensor(fx.init_walkers(wl.system, args.profile_case, wl.walker_seed), dtype=dt, device="cuda:0")
+    if args.profile_op == "grad":
+        w = torch.full((args.profile_case,), 1.0 / args.profile_case, dtype=dt, device="cuda:0")
+        out = h.grad_logpsi(theta, r, w, 0)
+    elif args.profile_op == "mcmc":
+        la, _ = h.ansatz_eval(theta, r)
+        out = h.mcmc_step(theta, r, la, 1, 0.2, 1, 0)
+    else:
+        out = h.local_energy(theta, r)[2]
+    torch.cuda.synchronize()
+    print("profile case done:", args.profile_op, args.profile_case, "walkers", float(out.double().abs().sum()))
+    return 0
 
 
 def main():

@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include "backward.cuh"
+#include "det_util.cuh"
 
 namespace dq {
 namespace {
@@ -89,7 +90,8 @@ __global__ void bwd_combine_kernel(const double* __restrict__ det, const T* __re
 //   Abar = beta_p A^-T;  phibar_ik = Abar_ik env_ik;  envbar_ik = Abar_ik phi_ik
 //   omegabar_oI = sum_i envbar_ik exp(-zeta_oI d_iI)
 //   zetabar_oI  = sum_i envbar_ik omega_oI (-d_iI) exp(-zeta_oI d_iI)
-// A^-1 from an FP64 LU (the backward runs once per optimisation step).
+// A^-1 from an LU in the arithmetic type; in FP32 modes near-nodal matrices
+// (row-equilibrated condition estimate above 1000) are redone in FP64.
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(128)
@@ -104,13 +106,16 @@ __global__ void __launch_bounds__(128)
   const int n_dn = N - n_up;
   const int nmax = n_up > n_dn ? n_up : n_dn;
   const int nn = nmax * nmax;
-  const size_t per_warp = (size_t)nn * (2 * sizeof(double) + 2 * sizeof(T)) + 32 * sizeof(int);
+  const size_t per_warp = (size_t)nn * (2 * sizeof(double) + 5 * sizeof(T)) + 32 * sizeof(int);
   unsigned char* base = smem_raw + warp * ((per_warp + 15) / 16 * 16);
-  double* LU = reinterpret_cast<double*>(base);
-  double* Ainv = LU + nn;
-  T* env = reinterpret_cast<T*>(Ainv + nn);
+  double* LUd = reinterpret_cast<double*>(base);
+  double* Ainvd = LUd + nn;
+  T* env = reinterpret_cast<T*>(Ainvd + nn);
   T* phi0 = env + nn;
-  int* perm = reinterpret_cast<int*>(phi0 + nn);
+  T* LUt = phi0 + nn;
+  T* Ainvt = LUt + nn;
+  T* rmax = Ainvt + nn;
+  int* perm = reinterpret_cast<int*>(rmax + nn);
   if (gw >= Bc * 2 * K) return;
   const int64_t b = gw / (2 * K);
   const int s = (int)((gw / K) % 2);
@@ -132,49 +137,37 @@ __global__ void __launch_bounds__(128)
     for (int I = 0; I < M; ++I) ev += om[o * M + I] * exp(-ze[o * M + I] * gb[(n_ee + i * M + I) * 4]);
     env[q] = ev;
     phi0[q] = phib[(int64_t)i * Wo + o];
-    LU[q] = (double)phi0[q] * (double)ev;
+    LUt[q] = phi0[q] * ev;
   }
-  if (lane < n) perm[lane] = lane;
   __syncwarp();
-  bool singular = false;
-  for (int j = 0; j < n; ++j) {
-    double v = (lane >= j && lane < n) ? fabs(LU[lane * n + j]) : -1.0;
-    int idx = lane;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
-      const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
-      if (v2 > v || (v2 == v && i2 < idx)) {
-        v = v2;
-        idx = i2;
-      }
-    }
-    if (!(v > 0.0)) {
-      singular = true;
-      break;
-    }
-    if (idx != j) {
-      for (int k = lane; k < n; k += 32) {
-        const double t = LU[j * n + k];
-        LU[j * n + k] = LU[idx * n + k];
-        LU[idx * n + k] = t;
-      }
-      if (lane == 0) {
-        const int t = perm[j];
-        perm[j] = perm[idx];
-        perm[idx] = t;
-      }
+  int sign = 0;
+  double la = 0;
+  bool fp64 = sizeof(T) == 8, ok = false;
+  if (!fp64 && bp != 0.0) {
+    if (lane < n) {
+      T m = 0;
+      for (int k = 0; k < n; ++k) m = max(m, (T)fabs(LUt[lane * n + k]));
+      rmax[lane] = m;
     }
     __syncwarp();
-    const double piv = LU[j * n + j];
-    for (int i = j + 1 + lane; i < n; i += 32) {
-      const double f = LU[i * n + j] / piv;
-      LU[i * n + j] = f;
-      for (int k = j + 1; k < n; ++k) LU[i * n + k] -= f * LU[j * n + k];
+    ok = warp_lu<T>(LUt, perm, n, lane, &sign, &la);
+    if (ok) {
+      warp_inverse<T>(LUt, perm, n, lane, Ainvt);
+      T imax = 0;
+      for (int q = lane; q < n * n; q += 32) imax = max(imax, (T)fabs(Ainvt[q]) * rmax[q % n]);
+      fp64 = !(T(n) * warp_max(imax) <= T(1000));
+    } else {
+      fp64 = true;
     }
-    __syncwarp();
   }
-  if (singular || bp == 0.0) {  // zero adjoint
+  if (fp64 && bp != 0.0) {
+    for (int q = lane; q < n * n; q += 32) LUd[q] = (double)phi0[q] * (double)env[q];
+    __syncwarp();
+    ok = warp_lu<double>(LUd, perm, n, lane, &sign, &la);
+    if (ok) warp_inverse<double>(LUd, perm, n, lane, Ainvd);
+  }
+  auto ainv = [&](int r, int c) { return fp64 ? Ainvd[r * n + c] : (double)Ainvt[r * n + c]; };
+  if (!ok || bp == 0.0) {  // zero adjoint (psi = 0 or zero weight)
     for (int q = lane; q < n * n; q += 32) {
       const int ii = q / n, k = q % n;
       phibar[(b * N + i0 + ii) * (int64_t)Wo + p * n + k] = T(0);
@@ -186,41 +179,26 @@ __global__ void __launch_bounds__(128)
     }
     return;
   }
-  if (lane < n) {
-    const int col = lane;
-    for (int r = 0; r < n; ++r) {
-      double acc = perm[r] == col ? 1.0 : 0.0;
-      for (int m = 0; m < r; ++m) acc -= LU[r * n + m] * Ainv[m * n + col];
-      Ainv[r * n + col] = acc;
-    }
-    for (int r = n - 1; r >= 0; --r) {
-      double acc = Ainv[r * n + col];
-      for (int m = r + 1; m < n; ++m) acc -= LU[r * n + m] * Ainv[m * n + col];
-      Ainv[r * n + col] = acc / LU[r * n + r];
-    }
-  }
-  __syncwarp();
   // phibar_ik = beta (A^-1)_ki env_ik
   for (int q = lane; q < n * n; q += 32) {
     const int ii = q / n, k = q % n;
-    const double abar = bp * Ainv[k * n + ii];
-    phibar[(b * N + i0 + ii) * (int64_t)Wo + p * n + k] = (T)(abar * (double)env[q]);
+    phibar[(b * N + i0 + ii) * (int64_t)Wo + p * n + k] = (T)(bp * ainv(k, ii) * (double)env[q]);
   }
   // envelope parameters: lanes over (k, I)
   for (int q = lane; q < n * M; q += 32) {
     const int k = q / M, I = q % M, o = p * n + k;
-    const double w = (double)om[o * M + I], z = (double)ze[o * M + I];
-    double ob = 0.0, zb = 0.0;
+    const T w = om[o * M + I], z = ze[o * M + I];
+    T ob = 0, zb = 0;
     for (int ii = 0; ii < n; ++ii) {
       const int i = i0 + ii;
-      const double d = (double)gb[(n_ee + i * M + I) * 4];
-      const double e = exp(-z * d);
-      const double envb = bp * Ainv[k * n + ii] * (double)phi0[ii * n + k];
+      const T d = gb[(n_ee + i * M + I) * 4];
+      const T e = exp(-z * d);
+      const T envb = (T)(bp * ainv(k, ii)) * phi0[ii * n + k];
       ob += envb * e;
       zb -= envb * w * d * e;
     }
-    ebo[(int64_t)o * M + I] = (T)ob;
-    ebz[(int64_t)o * M + I] = (T)zb;
+    ebo[(int64_t)o * M + I] = ob;
+    ebz[(int64_t)o * M + I] = zb;
   }
 }
 
@@ -234,17 +212,23 @@ __global__ void __launch_bounds__(256)
                    int64_t rows, int n_out, int K, int accumulate) {
   __shared__ T Xs[NK][NB + 1];
   __shared__ T Ws[NK][NB + 1];
+  __shared__ int64_t xoff[NB], yoff[NB];  // row offsets of this tile (one division per row)
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int64_t r0 = (int64_t)blockIdx.x * NB;
   const int n0 = blockIdx.y * NB;
+  if (threadIdx.x < NB) {
+    const int64_t r = r0 + threadIdx.x;
+    xoff[threadIdx.x] = r < rows ? (r / mx.rows_per_seg) * mx.seg_stride + (r % mx.rows_per_seg) * mx.ld : -1;
+    yoff[threadIdx.x] = r < rows ? (r / my.rows_per_seg) * my.seg_stride + (r % my.rows_per_seg) * my.ld : -1;
+  }
+  __syncthreads();
   T acc[4][4] = {};
   for (int k0 = 0; k0 < K; k0 += NK) {
     for (int e = threadIdx.x; e < NB * NK; e += 256) {
       const int rr = e / NK, kk = e % NK;
-      const int64_t r = r0 + rr;
       const int k = k0 + kk;
-      Xs[kk][rr] = (r < rows && k < K) ? X[(r / mx.rows_per_seg) * mx.seg_stride + (r % mx.rows_per_seg) * mx.ld + k]
-                                       : T(0);
+      const int64_t xo = xoff[rr];
+      Xs[kk][rr] = (xo >= 0 && k < K) ? X[xo + k] : T(0);
       const int kk2 = e / NB, nn2 = e % NB;
       const int k2 = k0 + kk2, n2 = n0 + nn2;
       Ws[kk2][nn2] = (k2 < K && n2 < n_out) ? W[(int64_t)k2 * n_out + n2] : T(0);
@@ -266,9 +250,9 @@ __global__ void __launch_bounds__(256)
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int64_t r = r0 + ty + 16 * i;
-    if (r >= rows) continue;
-    T* y = Y + (r / my.rows_per_seg) * my.seg_stride + (r % my.rows_per_seg) * my.ld;
+    const int64_t yo = yoff[ty + 16 * i];
+    if (yo < 0) continue;
+    T* y = Y + yo;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int n = n0 + tx + 16 * j;
@@ -372,6 +356,7 @@ __global__ void __launch_bounds__(256)
   static_assert((BM / TM) * (BN / TN) == 256, "tile/thread mismatch");
   __shared__ __align__(16) T Xs[BK][BM];
   __shared__ __align__(16) T Ys[BK][BN];
+  __shared__ int64_t xoff[BK], yoff[BK];  // offsets of the BK rows of this step
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN), ty = tid / (BN / TN);
   const int o0 = blockIdx.x * BM, a0 = blockIdx.y * BN;
@@ -391,13 +376,18 @@ __global__ void __launch_bounds__(256)
     for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
   constexpr int XV = BM / VEC, YV = BN / VEC;  // vectors per row of a tile
   for (int64_t rr0 = r_begin; rr0 < r_end; rr0 += BK) {
+    if (tid < BK) {
+      const int64_t r = rr0 + tid;
+      xoff[tid] = r < r_end ? (r / mx.rows_per_seg) * mx.seg_stride + (r % mx.rows_per_seg) * mx.ld : -1;
+      yoff[tid] = r < r_end ? (r / my.rows_per_seg) * my.seg_stride + (r % my.rows_per_seg) * my.ld : -1;
+    }
+    __syncthreads();
     for (int e = tid; e < BK * XV; e += 256) {
       const int k = e / XV, cv = e % XV;
-      const int64_t r = rr0 + k;
       const int o = o0 + cv * VEC;
       V v{};
-      if (r < r_end) {
-        const T* src = X + (r / mx.rows_per_seg) * mx.seg_stride + (r % mx.rows_per_seg) * mx.ld + o;
+      if (xoff[k] >= 0) {
+        const T* src = X + xoff[k] + o;
         if (VA && o + VEC <= n_o) {
           v = *reinterpret_cast<const V*>(src);
         } else {
@@ -409,11 +399,10 @@ __global__ void __launch_bounds__(256)
     }
     for (int e = tid; e < BK * YV; e += 256) {
       const int k = e / YV, cv = e % YV;
-      const int64_t r = rr0 + k;
       const int a = a0 + cv * VEC;
       V v{};
-      if (r < r_end) {
-        const T* src = Y + (r / my.rows_per_seg) * my.seg_stride + (r % my.rows_per_seg) * my.ld + a;
+      if (yoff[k] >= 0) {
+        const T* src = Y + yoff[k] + a;
         if (VA && a + VEC <= n_a) {
           v = *reinterpret_cast<const V*>(src);
         } else {
@@ -472,8 +461,15 @@ __global__ void colsum_kernel(const T* __restrict__ X, RowMap mx, int rpw, int64
     wb1 = min(nw, wb0 + walkers_per_split);
   }
   T acc = 0;
-  for (int64_t r = wb0 * rpw; r < wb1 * rpw; ++r)
-    acc += X[(r / mx.rows_per_seg) * mx.seg_stride + (r % mx.rows_per_seg) * mx.ld + o];
+  const int64_t r_begin = wb0 * rpw, r_end = wb1 * rpw;
+  int64_t seg = r_begin / mx.rows_per_seg, in = r_begin % mx.rows_per_seg;  // one division, then increments
+  for (int64_t r = r_begin; r < r_end; ++r) {
+    acc += X[seg * mx.seg_stride + in * mx.ld + o];
+    if (++in == mx.rows_per_seg) {
+      in = 0;
+      ++seg;
+    }
+  }
   if (mode == 1)
     G[wb0 * P + off + (int64_t)o * ld] = acc;
   else
@@ -599,7 +595,7 @@ cudaError_t launch_bwd_det(const dq_handle_s& h, int64_t Bc, const T* phi, const
                            T* phibar, T* envbar, cudaStream_t s) {
   const int nmax = h.n_up > h.n_dn ? h.n_up : h.n_dn;
   const int nn = nmax * nmax;
-  const size_t per_warp = ((size_t)nn * (2 * sizeof(double) + 2 * sizeof(T)) + 32 * sizeof(int) + 15) / 16 * 16;
+  const size_t per_warp = ((size_t)nn * (2 * sizeof(double) + 5 * sizeof(T)) + 32 * sizeof(int) + 15) / 16 * 16;
   const int warps = 4;
   const size_t smem = per_warp * warps;
   auto kern = bwd_det_kernel<T>;

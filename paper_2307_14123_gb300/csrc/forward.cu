@@ -26,6 +26,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "det_util.cuh"
 
 namespace dq {
 namespace {
@@ -271,73 +272,129 @@ __global__ void __launch_bounds__(256)
       }
     }
 
-    // product-rule corrections, nuclear messages, normalisation, store.
-    // Rolled loop over the block's outputs (keeps the kernel small); the
-    // register accumulators are picked with predicated selects.
+    // Product-rule terms with derivatives of w_ij (only coordinates of i or j):
+    //  (a) channel of a SENDER's coordinate (c = 1 + 3j + x, j != i):
+    //      -w'_ij u_ij,x z_j[0]; a 4-channel block holds those of at most two senders;
+    //  (b) channel of the RECEIVER's own coordinate (c = 1 + 3i + x):
+    //      sum_j w'_ij u_ij,x z_j[0] (+ the electron-nucleus term);
+    //  (c) Laplacian channel: sum_j (2 w'' + 4 w'/d) z_j[0] + 2 w' u.(dz_j/dr_i - dz_j/dr_j);
+    //  (d) electron-nucleus messages of the value channel.
+    // Terms are added to the register accumulators with predicated selects.
     const int n_same = up ? n_up : n_dn, n_opp = up ? n_dn : n_up;
     const T nu_s = T(1) / T(n_same - 1 > 1 ? n_same - 1 : 1);
     const T nu_o = T(1) / T(n_opp > 1 ? n_opp : 1);
-#pragma unroll 1
-    for (int aq = 0; aq < ni * nc; ++aq) {
-      const int a = aq / nc, q = aq % nc;
-      const int i = i0 + a;
-      const int c = c0 + q;
-      T s = 0, o = 0, nn = 0;
+    T an[IB][CB];
+#pragma unroll
+    for (int a = 0; a < IB; ++a)
+#pragma unroll
+      for (int q = 0; q < CB; ++q) an[a][q] = T(0);
+    auto add_to = [&](int a, int q, bool same, T v) {
 #pragma unroll
       for (int a2 = 0; a2 < IB; ++a2)
 #pragma unroll
         for (int q2 = 0; q2 < CB; ++q2)
           if (a2 == a && q2 == q) {
-            s = as[a2][q2];
-            o = ao[a2][q2];
+            if (same) as[a2][q2] += v; else ao[a2][q2] += v;
           }
-      const bool isJ = jets && c >= 1 && c < C - 1;
-      const bool isL = jets && c == C - 1;
-      if (isJ) {
-        const int e = (c - 1) / 3, x = (c - 1) % 3;
-        if (e == i) {
+    };
+    auto add_nuc = [&](int a, int q, T v) {
+#pragma unroll
+      for (int a2 = 0; a2 < IB; ++a2)
+#pragma unroll
+        for (int q2 = 0; q2 < CB; ++q2)
+          if (a2 == a && q2 == q) an[a2][q2] += v;
+    };
+    if (jets) {
+      // coordinate channels in this block: 1 + 3e + x for e in [e_lo, e_hi]
+      const int cJ0 = c0 < 1 ? 1 : c0, cJ1 = min(c0 + nc, C - 1);  // [cJ0, cJ1)
+      if (cJ0 < cJ1) {
+        const int e_lo = (cJ0 - 1) / 3, e_hi = (cJ1 - 2) / 3;
+#pragma unroll 1
+        for (int e = e_lo; e <= e_hi; ++e) {
+          const bool e_same = (e < n_up) == up;
+#pragma unroll 1
+          for (int x = 0; x < 3; ++x) {
+            const int c = 1 + 3 * e + x;
+            if (c < cJ0 || c >= cJ1) continue;
+            const int q = c - c0;
+#pragma unroll 1
+            for (int a = 0; a < ni; ++a) {
+              const int i = i0 + a;
+              if (i != e) {  // (a) e is a sender
+                const int p = Ps[i * N + e];
+                const T u = (i < e ? Gs[p * 4 + 1 + x] : -Gs[p * 4 + 1 + x]);
+                add_to(a, q, e_same, -W1p[p * DC + dd] * u * zv(e, 0));
+              } else {  // (b) the receiver's own coordinate
+                T ss = 0, so = 0, sn = 0;
+                for (int j = 0; j < N; ++j) {
+                  if (j == i) continue;
+                  const int p = Ps[i * N + j];
+                  const T u = (i < j ? Gs[p * 4 + 1 + x] : -Gs[p * 4 + 1 + x]);
+                  const T t = W1p[p * DC + dd] * u * zv(j, 0);
+                  if ((j < n_up) == up) ss += t; else so += t;
+                }
+                for (int I = 0; I < M; ++I) {
+                  const int en = i * M + I;
+                  sn += WN[(en * ej + 1) * DC + dd] * Gs[(n_ee + en) * 4 + 1 + x] * Ys[I * DC + dd];
+                }
+                add_to(a, q, true, ss);
+                add_to(a, q, false, so);
+                add_nuc(a, q, sn);
+              }
+            }
+          }
+        }
+      }
+      if (c0 + nc == C) {  // (c) the Laplacian channel is the last of this block
+        const int q = C - 1 - c0;
+#pragma unroll 1
+        for (int a = 0; a < ni; ++a) {
+          const int i = i0 + a;
+          T ss = 0, so = 0, sn = 0;
           for (int j = 0; j < N; ++j) {
             if (j == i) continue;
             const int p = Ps[i * N + j];
-            const T u = (i < j ? Gs[p * 4 + 1 + x] : -Gs[p * 4 + 1 + x]);
-            const T t = W1p[p * DC + dd] * u * zv(j, 0);
-            if ((j < n_up) == up) s += t; else o += t;
+            const T w1 = W1p[p * DC + dd], w2 = W2p[p * DC + dd];
+            const T sg = i < j ? T(1) : T(-1);
+            T t = (T(2) * w2 + T(4) * w1 / Gs[p * 4]) * zv(j, 0);
+            T cr = 0;
+            for (int x = 0; x < 3; ++x)
+              cr += sg * Gs[p * 4 + 1 + x] * (zv(j, 1 + 3 * i + x) - zv(j, 1 + 3 * j + x));
+            t += T(2) * w1 * cr;
+            if ((j < n_up) == up) ss += t; else so += t;
           }
           for (int I = 0; I < M; ++I) {
             const int en = i * M + I;
-            nn += WN[(en * ej + 1) * DC + dd] * Gs[(n_ee + en) * 4 + 1 + x] * Ys[I * DC + dd];
+            sn += (WN[(en * ej + 2) * DC + dd] + T(2) * WN[(en * ej + 1) * DC + dd] / Gs[(n_ee + en) * 4]) *
+                  Ys[I * DC + dd];
           }
-        } else {
-          const int p = Ps[i * N + e];
-          const T u = (i < e ? Gs[p * 4 + 1 + x] : -Gs[p * 4 + 1 + x]);
-          const T t = W1p[p * DC + dd] * u * zv(e, 0);
-          if ((e < n_up) == up) s -= t; else o -= t;
+          add_to(a, q, true, ss);
+          add_to(a, q, false, so);
+          add_nuc(a, q, sn);
         }
-      } else if (isL) {
-        for (int j = 0; j < N; ++j) {
-          if (j == i) continue;
-          const int p = Ps[i * N + j];
-          const T w1 = W1p[p * DC + dd], w2 = W2p[p * DC + dd];
-          const T sg = i < j ? T(1) : T(-1);
-          T t = (T(2) * w2 + T(4) * w1 / Gs[p * 4]) * zv(j, 0);
-          T cr = 0;
-          for (int x = 0; x < 3; ++x)
-            cr += sg * Gs[p * 4 + 1 + x] * (zv(j, 1 + 3 * i + x) - zv(j, 1 + 3 * j + x));
-          t += T(2) * w1 * cr;
-          if ((j < n_up) == up) s += t; else o += t;
-        }
-        for (int I = 0; I < M; ++I) {
-          const int en = i * M + I;
-          nn += (WN[(en * ej + 2) * DC + dd] + T(2) * WN[(en * ej + 1) * DC + dd] / Gs[(n_ee + en) * 4]) *
-                Ys[I * DC + dd];
-        }
-      } else if (c == 0) {
-        for (int I = 0; I < M; ++I) nn += WN[(i * M + I) * ej * DC + dd] * Ys[I * DC + dd];
       }
-      TO* out = mb + ((int64_t)i * C + c) * 3 * D;
-      out[0] = to_out(s * nu_s, out);
-      out[D] = to_out(o * nu_o, out);
-      out[2 * D] = to_out(nn * nuM, out);
+    }
+    if (c0 == 0) {  // (d) value channel: electron-nucleus messages
+#pragma unroll 1
+      for (int a = 0; a < ni; ++a) {
+        T sn = 0;
+        for (int I = 0; I < M; ++I) sn += WN[((i0 + a) * M + I) * ej * DC + dd] * Ys[I * DC + dd];
+        add_nuc(a, 0, sn);
+      }
+    }
+    // normalisation and store
+#pragma unroll
+    for (int a = 0; a < IB; ++a) {
+      if (a >= ni) continue;
+      const int i = i0 + a;
+#pragma unroll
+      for (int q = 0; q < CB; ++q) {
+        if (q >= nc) continue;
+        TO* out = mb + ((int64_t)i * C + c0 + q) * 3 * D;
+        out[0] = to_out(as[a][q] * nu_s, out);
+        out[D] = to_out(ao[a][q] * nu_o, out);
+        out[2 * D] = to_out(an[a][q] * nuM, out);
+      }
     }
   }
 }
@@ -400,86 +457,6 @@ __global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __r
 #ifndef DQ_KAPPA_FP32_VALUE
 #define DQ_KAPPA_FP32_VALUE 1000.0f  // value-only log|det| in FP32 below this
 #endif
-
-template <class S>
-__device__ __forceinline__ S warp_max(S v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// In-place LU with partial pivoting of the n x n matrix LU (row-major, shared
-// memory) by one warp; perm records the row order.  Returns false if a zero
-// pivot appears.  sign and logabs of the determinant are accumulated.
-template <class S>
-__device__ bool warp_lu(S* LU, int* perm, int n, int lane, int* sign_out, double* logabs_out) {
-  if (lane < n) perm[lane] = lane;
-  __syncwarp();
-  int sign = 1;
-  S la = 0;
-  for (int j = 0; j < n; ++j) {
-    S v = (lane >= j && lane < n) ? fabs(LU[lane * n + j]) : S(-1);
-    int idx = lane;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const S v2 = __shfl_xor_sync(0xffffffffu, v, o);
-      const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
-      if (v2 > v || (v2 == v && i2 < idx)) {
-        v = v2;
-        idx = i2;
-      }
-    }
-    if (!(v > S(0))) return false;
-    if (idx != j) {
-      for (int k = lane; k < n; k += 32) {
-        const S t = LU[j * n + k];
-        LU[j * n + k] = LU[idx * n + k];
-        LU[idx * n + k] = t;
-      }
-      if (lane == 0) {
-        const int t = perm[j];
-        perm[j] = perm[idx];
-        perm[idx] = t;
-      }
-      sign = -sign;
-    }
-    __syncwarp();
-    const S piv = LU[j * n + j];
-    for (int i = j + 1 + lane; i < n; i += 32) {
-      const S f = LU[i * n + j] / piv;
-      LU[i * n + j] = f;
-      for (int k = j + 1; k < n; ++k) LU[i * n + k] -= f * LU[j * n + k];
-    }
-    __syncwarp();
-    if (piv < S(0)) sign = -sign;
-    if (lane == (j & 31)) la += log(fabs(piv));  // one lane per pivot, summed below
-  }
-  *sign_out = sign;
-  double l = (double)la;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-  *logabs_out = l;
-  return true;
-}
-
-// A^-1 from the LU factors: lane `col` solves L U x = P e_col.
-template <class S>
-__device__ void warp_inverse(const S* LU, const int* perm, int n, int lane, S* Ainv) {
-  if (lane < n) {
-    const int col = lane;
-    for (int r = 0; r < n; ++r) {
-      S acc = perm[r] == col ? S(1) : S(0);
-      for (int m = 0; m < r; ++m) acc -= LU[r * n + m] * Ainv[m * n + col];
-      Ainv[r * n + col] = acc;
-    }
-    for (int r = n - 1; r >= 0; --r) {
-      S acc = Ainv[r * n + col];
-      for (int m = r + 1; m < n; ++m) acc -= LU[r * n + m] * Ainv[m * n + col];
-      Ainv[r * n + col] = acc / LU[r * n + r];
-    }
-  }
-  __syncwarp();
-}
 
 // Determinant derivatives: for every tangent t (3N coordinates, then the
 // Laplacian channel) build d_t A into tmp and accumulate

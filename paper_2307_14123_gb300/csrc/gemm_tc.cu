@@ -8,15 +8,16 @@
 // value / Jacobian / Laplacian channels at once: the rows are the channels of
 // every node of every walker, so one launch is one large dense contraction.
 //
-// One CTA computes a 128 x 128 output tile:
+// A persistent grid (one CTA per SM) walks the 128 x 128 output tiles:
 //   * warp 0, lane 0 streams 128 x 64 tiles of X and W into a 3-stage ring of
 //     shared-memory buffers with TMA (cp.async.bulk.tensor, 128-byte swizzle),
 //     completing on "full" mbarriers;
 //   * warp 1, lane 0 issues tcgen05.mma (kind::f16, BF16 inputs, FP32
 //     accumulator in tensor memory, M = 128, N = 128, K = 16 per instruction)
 //     and releases each stage with tcgen05.commit on its "empty" mbarrier;
-//   * all four warps read the accumulator back with tcgen05.ld (warp w owns
-//     tensor-memory lanes 32w..32w+31, i.e. rows 32w..32w+31) and store FP32.
+//   * warps 2..5 read a finished accumulator back with tcgen05.ld (a warp
+//     reaches the 32 tensor-memory lanes of its index modulo 4) and store FP32
+//     while the next tile accumulates in the second accumulator.
 // Rows beyond `rows` and columns beyond n_out are zero-filled by TMA and not
 // stored.  Every mbarrier wait is bounded (about one second of clock); on
 // timeout the kernel sets DQ_FLAG_TIMEOUT in the status word, skips the rest
@@ -107,7 +108,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(128, 2)
+// Persistent kernel: CTA c processes output tiles c, c + gridDim.x, ... in
+// order (tile = m-tile * n_tiles + n-tile).  Warp roles: warp 0 lane 0 TMA
+// producer (continuous stream of k-blocks across tiles); warp 1 lane 0 MMA
+// issuer; warps 2..5 epilogue.  Two accumulators in tensor memory (2 x 128
+// columns): the MMA warp fills one while the epilogue warps drain the other
+// (acc_full / acc_empty mbarriers), so the epilogue of a tile overlaps the
+// loads and MMAs of the next.
+constexpr int TC_THREADS = 192;
+constexpr uint32_t TC_TMEM_ALLOC = 2 * TC_TMEM_COLS;
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_bf16_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                         int64_t rows, int n_out, int K, const float* __restrict__ bias, int bias_period,
                         float* __restrict__ Y, int64_t ldy, unsigned int* __restrict__ status) {
@@ -117,27 +128,31 @@ __global__ void __launch_bounds__(128, 2)
   uint8_t* sB = smem + TC_STAGES * TC_TILE_A;
   uint64_t* full = reinterpret_cast<uint64_t*>(sB + TC_STAGES * TC_TILE_B);
   uint64_t* empty = full + TC_STAGES;
-  uint64_t* done = empty + TC_STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
-  __shared__ int s_abort;
+  uint64_t* acc_full = empty + TC_STAGES;  // [2]
+  uint64_t* acc_empty = acc_full + 2;      // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int64_t m0 = (int64_t)blockIdx.x * TC_BM;
-  const int n0 = blockIdx.y * TC_BN;
   const int nk = K / TC_BK;
+  const int n_tiles_n = (n_out + TC_BN - 1) / TC_BN;
+  const int64_t n_tiles = ((rows + TC_BM - 1) / TC_BM) * n_tiles_n;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(done, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);  // one arrival per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TC_TMEM_COLS)
+                 "r"(TC_TMEM_ALLOC)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -146,65 +161,338 @@ __global__ void __launch_bounds__(128, 2)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // TMA producer
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % TC_STAGES;
-      if (kb >= TC_STAGES && !mbar_wait(&empty[s], ((kb / TC_STAGES) + 1) & 1)) {
-        s_abort = 1;
-        break;
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      int64_t g = 0;   // k-blocks issued so far
+      for (int64_t t = blockIdx.x; t < n_tiles && !s_abort; t += gridDim.x) {
+        const int64_t m0 = (t / n_tiles_n) * TC_BM;
+        const int n0 = (int)(t % n_tiles_n) * TC_BN;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = (int)(g % TC_STAGES);
+          const int64_t u = g / TC_STAGES;
+          if (u >= 1 && !mbar_wait(&empty[s], (uint32_t)((u - 1) & 1))) {
+            s_abort = 1;
+            break;
+          }
+          mbar_expect_tx(&full[s], TC_TILE_A + TC_TILE_B);
+          tma_load_2d(sA + s * TC_TILE_A, &tmA, kb * TC_BK, (int)m0, &full[s]);
+          tma_load_2d(sB + s * TC_TILE_B, &tmB, kb * TC_BK, n0, &full[s]);
+        }
       }
-      mbar_expect_tx(&full[s], TC_TILE_A + TC_TILE_B);
-      tma_load_2d(sA + s * TC_TILE_A, &tmA, kb * TC_BK, (int)m0, &full[s]);
-      tma_load_2d(sB + s * TC_TILE_B, &tmB, kb * TC_BK, n0, &full[s]);
     }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    constexpr uint32_t idesc = tc_idesc(TC_BM, TC_BN);
-    bool ok = true;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % TC_STAGES;
-      if (!mbar_wait(&full[s], (kb / TC_STAGES) & 1)) {
-        ok = false;
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      constexpr uint32_t idesc = tc_idesc(TC_BM, TC_BN);
+      int64_t g = 0, lt = 0;
+      for (int64_t t = blockIdx.x; t < n_tiles && !s_abort; t += gridDim.x, ++lt) {
+        const int a = (int)(lt & 1);
+        const int64_t v = lt >> 1;
+        if (v >= 1 && !mbar_wait(&acc_empty[a], (uint32_t)((v - 1) & 1))) {
+          s_abort = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(a * TC_TMEM_COLS);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = (int)(g % TC_STAGES);
+          if (!mbar_wait(&full[s], (uint32_t)((g / TC_STAGES) & 1))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sA + s * TC_TILE_A), b0 = smem_u32(sB + s * TC_TILE_B);
+#pragma unroll
+          for (int kk = 0; kk < TC_BK / 16; ++kk)
+            umma_bf16(d, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc, (kb | kk) ? 1u : 0u);
+          umma_commit(&empty[s]);
+        }
+        if (!ok) {
+          s_abort = 1;
+          break;
+        }
+        umma_commit(&acc_full[a]);
+      }
+    }
+  } else {
+    // Epilogue warps 2..5: warp w reads tensor-memory lanes 32 (w % 4) .. + 31.
+    const int q = warp % 4;
+    int64_t lt = 0;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
+      const int a = (int)(lt & 1);
+      const int64_t v = lt >> 1;
+      if (!mbar_wait(&acc_full[a], (uint32_t)(v & 1))) {
         s_abort = 1;
         break;
       }
       tc_fence_after();
-      const uint32_t a0 = smem_u32(sA + s * TC_TILE_A), b0 = smem_u32(sB + s * TC_TILE_B);
+      const int64_t m0 = (t / n_tiles_n) * TC_BM;
+      const int n0 = (int)(t % n_tiles_n) * TC_BN;
+      const int64_t row = m0 + q * 32 + lane;
+      const bool add_bias = bias != nullptr && (row % bias_period) == 0;
+      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+        uint32_t vv[32];
+        tmem_ld32(tmem + (uint32_t)(a * TC_TMEM_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, vv);
+        if (row < rows) {
+          float* y = Y + row * ldy + n0 + c0;
+          if (n0 + c0 + 32 <= n_out && !add_bias && (reinterpret_cast<uintptr_t>(y) & 15) == 0) {
 #pragma unroll
-      for (int kk = 0; kk < TC_BK / 16; ++kk)
-        umma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), idesc, (kb | kk) ? 1u : 0u);
-      umma_commit(&empty[s]);
-    }
-    if (ok) umma_commit(done);
-  }
-  __syncwarp();
-
-  // Epilogue: TMEM -> registers -> global.
-  const bool ok = mbar_wait(done, 0);
-  tc_fence_after();
-  if (ok && !s_abort) {
-    const int64_t row = m0 + warp * 32 + lane;
-    const bool add_bias = bias != nullptr && (row % bias_period) == 0;
-    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-      uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (row < rows) {
-        float* y = Y + row * ldy;
+            for (int j = 0; j < 32; j += 4)
+              *reinterpret_cast<float4*>(y + j) = make_float4(__uint_as_float(vv[j]), __uint_as_float(vv[j + 1]),
+                                                              __uint_as_float(vv[j + 2]), __uint_as_float(vv[j + 3]));
+          } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = n0 + c0 + j;
-          if (n < n_out) y[n] = __uint_as_float(v[j]) + (add_bias ? bias[n] : 0.f);
+            for (int j = 0; j < 32; ++j) {
+              const int n = n0 + c0 + j;
+              if (n < n_out) y[j] = __uint_as_float(vv[j]) + (add_bias ? bias[n] : 0.f);
+            }
+          }
         }
       }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[a])) : "memory");
     }
-  } else if (threadIdx.x == 0) {
-    atomicOr(status, (unsigned)DQ_FLAG_TIMEOUT);
+  }
+  __syncthreads();
+  if (s_abort && threadIdx.x == 0) atomicOr(status, (unsigned)DQ_FLAG_TIMEOUT);
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_ALLOC) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// FP32-accurate variant for the FP32 mode: 3 x TF32 splitting.
+//   x = x_big + x_small with x_big = tf32(x), x_small = tf32(x - x_big);
+//   x . w ~= x_big w_big + x_big w_small + x_small w_big   (error ~ 2^-22 |x||w|)
+// W is split once per call (split_tf32_kernel).  The FP32 X tile arrives by
+// TMA; four converter warps split it in shared memory (x_big in place, x_small
+// into a second buffer at the same positions: the split is elementwise, so the
+// 128-byte-swizzled layout carries over) and release it to the MMA warp after a
+// proxy fence.  Three tcgen05.mma.kind::tf32 (K = 8 per instruction) per
+// 8-element slice accumulate into one FP32 accumulator in tensor memory.
+// Warps: 0 TMA, 1 MMA, 2..5 epilogue, 6..9 converter.
+// ---------------------------------------------------------------------------
+constexpr int T3_BK = 32;                            // FP32 elements per 128-byte row
+constexpr int T3_STAGES = 3;
+constexpr uint32_t T3_TILE_A = TC_BM * T3_BK * 4;    // 16 KB
+constexpr uint32_t T3_TILE_B = TC_BN * T3_BK * 4;    // 16 KB
+constexpr int T3_THREADS = 320;
+
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t u = __float_as_uint(x);
+  u = (u + 0x1000u) & 0xFFFFE000u;  // round to nearest (ties away) at 10 explicit mantissa bits
+  return __uint_as_float(u);
+}
+
+__global__ void split_tf32_kernel(const float* __restrict__ W, float* __restrict__ big, float* __restrict__ small,
+                                  int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const float x = W[e], b = tf32_rn(x);
+  big[e] = b;
+  small[e] = tf32_rn(x - b);
+}
+
+// Instruction descriptor: kind::tf32, A and B TF32 (K-major), D FP32.
+constexpr uint32_t t3_idesc(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(T3_THREADS, 1)
+    gemm_tf32x3_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBb,
+                          const __grid_constant__ CUtensorMap tmBs, int64_t rows, int n_out, int K,
+                          const float* __restrict__ bias, int bias_period, float* __restrict__ Y, int64_t ldy,
+                          unsigned int* __restrict__ status) {
+  extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;                                  // [stage] X tile, x_big after conversion
+  uint8_t* sAs = sA + T3_STAGES * T3_TILE_A;           // [stage] x_small
+  uint8_t* sBb = sAs + T3_STAGES * T3_TILE_A;          // [stage] w_big
+  uint8_t* sBs = sBb + T3_STAGES * T3_TILE_B;          // [stage] w_small
+  uint64_t* full = reinterpret_cast<uint64_t*>(sBs + T3_STAGES * T3_TILE_B);
+  uint64_t* conv = full + T3_STAGES;
+  uint64_t* empty = conv + T3_STAGES;
+  uint64_t* acc_full = empty + T3_STAGES;  // [2]
+  uint64_t* acc_empty = acc_full + 2;      // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  __shared__ volatile int s_abort;
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int nk = K / T3_BK;
+  const int n_tiles_n = (n_out + TC_BN - 1) / TC_BN;
+  const int64_t n_tiles = ((rows + TC_BM - 1) / TC_BM) * n_tiles_n;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < T3_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&conv[s], 4);  // one arrival per converter warp
+      mbar_init(&empty[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TC_TMEM_ALLOC)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      int64_t g = 0;
+      for (int64_t t = blockIdx.x; t < n_tiles && !s_abort; t += gridDim.x) {
+        const int64_t m0 = (t / n_tiles_n) * TC_BM;
+        const int n0 = (int)(t % n_tiles_n) * TC_BN;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = (int)(g % T3_STAGES);
+          const int64_t u = g / T3_STAGES;
+          if (u >= 1 && !mbar_wait(&empty[s], (uint32_t)((u - 1) & 1))) {
+            s_abort = 1;
+            break;
+          }
+          mbar_expect_tx(&full[s], T3_TILE_A + 2 * T3_TILE_B);
+          tma_load_2d(sA + s * T3_TILE_A, &tmA, kb * T3_BK, (int)m0, &full[s]);
+          tma_load_2d(sBb + s * T3_TILE_B, &tmBb, kb * T3_BK, n0, &full[s]);
+          tma_load_2d(sBs + s * T3_TILE_B, &tmBs, kb * T3_BK, n0, &full[s]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      constexpr uint32_t idesc = t3_idesc(TC_BM, TC_BN);
+      int64_t g = 0, lt = 0;
+      for (int64_t t = blockIdx.x; t < n_tiles && !s_abort; t += gridDim.x, ++lt) {
+        const int a = (int)(lt & 1);
+        const int64_t v = lt >> 1;
+        if (v >= 1 && !mbar_wait(&acc_empty[a], (uint32_t)((v - 1) & 1))) {
+          s_abort = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(a * TC_TMEM_COLS);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = (int)(g % T3_STAGES);
+          if (!mbar_wait(&conv[s], (uint32_t)((g / T3_STAGES) & 1))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ab = smem_u32(sA + s * T3_TILE_A), as_ = smem_u32(sAs + s * T3_TILE_A);
+          const uint32_t bb = smem_u32(sBb + s * T3_TILE_B), bs = smem_u32(sBs + s * T3_TILE_B);
+#pragma unroll
+          for (int kk = 0; kk < T3_BK / 8; ++kk) {
+            const uint32_t o = kk * 32;
+            umma_tf32(d, sw128_desc(ab + o), sw128_desc(bb + o), idesc, (kb | kk) ? 1u : 0u);
+            umma_tf32(d, sw128_desc(ab + o), sw128_desc(bs + o), idesc, 1u);
+            umma_tf32(d, sw128_desc(as_ + o), sw128_desc(bb + o), idesc, 1u);
+          }
+          umma_commit(&empty[s]);
+        }
+        if (!ok) {
+          s_abort = 1;
+          break;
+        }
+        umma_commit(&acc_full[a]);
+      }
+    }
+  } else if (warp >= 6) {
+    // Converter warps 6..9: split each FP32 X tile into TF32 big (in place) and small.
+    const int ct = threadIdx.x - 6 * 32;  // 0..127
+    int64_t g = 0;
+    for (int64_t t = blockIdx.x; t < n_tiles && !s_abort; t += gridDim.x) {
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = (int)(g % T3_STAGES);
+        if (!mbar_wait(&full[s], (uint32_t)((g / T3_STAGES) & 1))) {
+          s_abort = 1;
+          break;
+        }
+        float4* src = reinterpret_cast<float4*>(sA + s * T3_TILE_A);
+        float4* dst = reinterpret_cast<float4*>(sAs + s * T3_TILE_A);
+#pragma unroll
+        for (int j = 0; j < (int)(T3_TILE_A / 16 / 128); ++j) {
+          const int idx = j * 128 + ct;
+          const float4 x = src[idx];
+          float4 b, sm;
+          b.x = tf32_rn(x.x);
+          b.y = tf32_rn(x.y);
+          b.z = tf32_rn(x.z);
+          b.w = tf32_rn(x.w);
+          sm.x = tf32_rn(x.x - b.x);
+          sm.y = tf32_rn(x.y - b.y);
+          sm.z = tf32_rn(x.z - b.z);
+          sm.w = tf32_rn(x.w - b.w);
+          src[idx] = b;
+          dst[idx] = sm;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&conv[s])) : "memory");
+      }
+    }
+  } else {
+    // Epilogue warps 2..5
+    const int q = warp % 4;
+    int64_t lt = 0;
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
+      const int a = (int)(lt & 1);
+      const int64_t v = lt >> 1;
+      if (!mbar_wait(&acc_full[a], (uint32_t)(v & 1))) {
+        s_abort = 1;
+        break;
+      }
+      tc_fence_after();
+      const int64_t m0 = (t / n_tiles_n) * TC_BM;
+      const int n0 = (int)(t % n_tiles_n) * TC_BN;
+      const int64_t row = m0 + q * 32 + lane;
+      const bool add_bias = bias != nullptr && (row % bias_period) == 0;
+      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+        uint32_t vv[32];
+        tmem_ld32(tmem + (uint32_t)(a * TC_TMEM_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, vv);
+        if (row < rows) {
+          float* y = Y + row * ldy + n0 + c0;
+          if (n0 + c0 + 32 <= n_out && !add_bias && (reinterpret_cast<uintptr_t>(y) & 15) == 0) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+              *reinterpret_cast<float4*>(y + j) = make_float4(__uint_as_float(vv[j]), __uint_as_float(vv[j + 1]),
+                                                              __uint_as_float(vv[j + 2]), __uint_as_float(vv[j + 3]));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int n = n0 + c0 + j;
+              if (n < n_out) y[j] = __uint_as_float(vv[j]) + (add_bias ? bias[n] : 0.f);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[a])) : "memory");
+    }
+  }
+  __syncthreads();
+  if (s_abort && threadIdx.x == 0) atomicOr(status, (unsigned)DQ_FLAG_TIMEOUT);
+  tc_fence_after();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_ALLOC) : "memory");
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
@@ -225,19 +513,23 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-bool make_map(CUtensorMap* m, const void* base, int64_t rows, int K, int64_t ld, int box_rows) {
+bool make_map(CUtensorMap* m, const void* base, int64_t rows, int K, int64_t ld, int box_rows, bool fp32 = false) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
+  const int el = fp32 ? 4 : 2;
   const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * el};
+  const cuuint32_t box[2] = {(cuuint32_t)(128 / el), (cuuint32_t)box_rows};  // one 128-byte row per box row
   const cuuint32_t estr[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return fn(m, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
+            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+constexpr size_t t3_smem_bytes() {
+  return 1024 + T3_STAGES * (2 * T3_TILE_A + 2 * T3_TILE_B) + (3 * T3_STAGES + 4) * 8 + 16;
 }
 
-constexpr size_t tc_smem_bytes() { return 1024 + TC_STAGES * (TC_TILE_A + TC_TILE_B) + (2 * TC_STAGES + 1) * 8 + 16; }
+constexpr size_t tc_smem_bytes() { return 1024 + TC_STAGES * (TC_TILE_A + TC_TILE_B) + (2 * TC_STAGES + 4) * 8 + 16; }
 
 }  // namespace
 
@@ -251,8 +543,42 @@ cudaError_t gemm_bf16_tc(const void* X, int64_t rows, int K, int64_t ldx, const 
   const size_t smem = tc_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(gemm_bf16_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)((rows + TC_BM - 1) / TC_BM), (unsigned)((n_out + TC_BN - 1) / TC_BN));
-  gemm_bf16_tc_kernel<<<grid, 128, smem, s>>>(ma, mb, rows, n_out, K, bias, bias_period, Y, ldy, status);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = ((rows + TC_BM - 1) / TC_BM) * ((n_out + TC_BN - 1) / TC_BN);
+  const int64_t grid = tiles < sms ? tiles : sms;
+  gemm_bf16_tc_kernel<<<(unsigned)grid, TC_THREADS, smem, s>>>(ma, mb, rows, n_out, K, bias, bias_period, Y, ldy,
+                                                             status);
+  return cudaGetLastError();
+}
+
+cudaError_t split_tf32(const float* W, float* big, float* small, int64_t n, cudaStream_t s) {
+  split_tf32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(W, big, small, n);
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_tf32x3_tc(const float* X, int64_t rows, int K, int64_t ldx, const float* Wbig, const float* Wsmall,
+                           int n_out, const float* bias, int bias_period, float* Y, int64_t ldy, unsigned int* status,
+                           cudaStream_t s) {
+  if (rows <= 0 || n_out <= 0) return cudaSuccess;
+  if (K % T3_BK || ldx % 4 || (uintptr_t)X % 16 || (uintptr_t)Wbig % 16 || (uintptr_t)Wsmall % 16 ||
+      bias_period <= 0)
+    return cudaErrorInvalidValue;
+  CUtensorMap ma, mbb, mbs;
+  if (!make_map(&ma, X, rows, K, ldx, TC_BM, true) || !make_map(&mbb, Wbig, n_out, K, K, TC_BN, true) ||
+      !make_map(&mbs, Wsmall, n_out, K, K, TC_BN, true))
+    return cudaErrorInvalidValue;
+  const size_t smem = t3_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = ((rows + TC_BM - 1) / TC_BM) * ((n_out + TC_BN - 1) / TC_BN);
+  const int64_t grid = tiles < sms ? tiles : sms;
+  gemm_tf32x3_tc_kernel<<<(unsigned)grid, T3_THREADS, smem, s>>>(ma, mbb, mbs, rows, n_out, K, bias, bias_period, Y,
+                                                                ldy, status);
   return cudaGetLastError();
 }
 
