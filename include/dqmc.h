@@ -230,6 +230,19 @@ dq_status dq_test_gemm_bf16(const void* X, int64_t rows, int32_t K, int64_t ldx,
                             const float* bias, int32_t bias_period, float* Y, int64_t ldy, uint32_t* status,
                             void* stream);
 
+/* Test support (not part of the method): the FP32-accurate tensor-core GEMM
+ * of the FP32 mode on its own.  Y[r][n] = sum_k X[r][k] W[n][k] (+ bias[n]
+ * when r % bias_period == 0), computed as three TF32 tensor-core products of
+ * the operands split into TF32 high and low parts (x_hi w_hi + x_hi w_lo +
+ * x_lo w_hi; relative error about 2^-21 of sum_k |x_k w_k|).  X FP32 device
+ * [rows][ldx], K a multiple of 32, ldx a multiple of 4, X and W 16-byte
+ * aligned; W FP32 device [n_out][K]; wsplit: device FP32 scratch of
+ * 2 * n_out * K elements that receives the split W; Y FP32 [rows][ldy];
+ * status as for dq_test_gemm_bf16.  Enqueued on `stream`. */
+dq_status dq_test_gemm_tf32x3(const float* X, int64_t rows, int32_t K, int64_t ldx, const float* W, int32_t n_out,
+                              const float* bias, int32_t bias_period, float* Y, int64_t ldy, float* wsplit,
+                              uint32_t* status, void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* dq_status_string(dq_status s);
 

@@ -31,7 +31,8 @@ PRECISIONS = {"fp64": DQ_FP64, "fp32": DQ_FP32, "bf16": DQ_BF16_MIXED}
 EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_max_chunk", "dq_workspace_size",
            "ansatz_eval", "local_energy", "mcmc_step", "grad_logpsi", "vmc_loss_weights", "dq_last_device_status",
            "dq_status_string", "dq_profile_enable", "dq_profile_reset", "dq_profile_read", "dq_profile_kind_name",
-           "dq_profile_kind_count", "vmc_loss_weights_noalloc", "dq_fp64_matrix_count", "dq_test_gemm_bf16"]
+           "dq_profile_kind_count", "vmc_loss_weights_noalloc", "dq_fp64_matrix_count", "dq_test_gemm_bf16",
+           "dq_test_gemm_tf32x3"]
 
 
 class DQError(RuntimeError):
@@ -80,6 +81,7 @@ def load_library(path=None):
         lib.dq_last_device_status.argtypes = [P, P, P]
         lib.dq_fp64_matrix_count.argtypes = [P, P, P]
         lib.dq_test_gemm_bf16.argtypes = [P, i64, i32, i64, P, i32, P, i32, P, i64, P, P]
+        lib.dq_test_gemm_tf32x3.argtypes = [P, i64, i32, i64, P, i32, P, i32, P, i64, P, P, P]
         lib.dq_status_string.argtypes = [ctypes.c_int]
         lib.dq_profile_enable.argtypes = [P, i32]
         lib.dq_profile_reset.argtypes = [P]
@@ -298,6 +300,22 @@ def test_gemm_bf16(X, W, bias=None, bias_period=1):
     stream = ctypes.c_void_p(torch.cuda.current_stream(X.device).cuda_stream)
     _check(lib.dq_test_gemm_bf16(_ptr(X), rows, K, X.stride(0), _ptr(W), n, _ptr(bias), bias_period, _ptr(Y), n,
                                  _ptr(st), stream))
+    return Y, st
+
+
+def test_gemm_tf32x3(X, W, bias=None, bias_period=1):
+    """Runs the FP32-accurate (3 x TF32) tensor-core GEMM on its own (test
+    support): X [rows][K], W [n][K] FP32 CUDA tensors; returns (Y FP32
+    [rows][n], status flags)."""
+    lib = load_library()
+    rows, K = X.shape
+    n = W.shape[0]
+    Y = torch.empty((rows, n), dtype=torch.float32, device=X.device)
+    st = torch.zeros(1, dtype=torch.int32, device=X.device)
+    wsplit = torch.empty(2 * n * K, dtype=torch.float32, device=X.device)
+    stream = ctypes.c_void_p(torch.cuda.current_stream(X.device).cuda_stream)
+    _check(lib.dq_test_gemm_tf32x3(_ptr(X), rows, K, X.stride(0), _ptr(W.contiguous()), n, _ptr(bias), bias_period,
+                                   _ptr(Y), n, _ptr(wsplit), _ptr(st), stream))
     return Y, st
 
 

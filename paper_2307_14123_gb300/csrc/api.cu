@@ -97,8 +97,12 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Sub-buffer offsets (bytes) of the forward workspace for a chunk of Bc walkers.
 struct FwdPlan {
-  size_t geo, rbf, eh, ew, F, Z, msg, phi, det, js, jh, z0, msg_bf, F_bf, W_bf, total;
+  size_t geo, rbf, eh, ew, F, Z, msg, phi, det, js, jh, z0, msg_bf, F_bf, W_bf, W_t3, total;
 };
+
+// FP32 mode: the node and update maps run on the tensor cores as 3 x TF32
+// products when the width allows the 128-byte TMA rows (D % 32 == 0).
+inline bool use_tf32x3(const dq_handle_s& h) { return h.precision == DQ_FP32 && h.D % 32 == 0; }
 
 FwdPlan plan_forward(const dq_handle_s& h, int64_t Bc, bool jets, size_t elem) {
   const int64_t E = h.edges.n_all, N = h.N, D = h.D, K = h.K;
@@ -128,6 +132,8 @@ FwdPlan plan_forward(const dq_handle_s& h, int64_t Bc, bool jets, size_t elem) {
   p.msg_bf = take(bf ? Bc * N * C * 3 * D * 2 : 0);
   p.F_bf = take(bf ? Bc * N * C * D * 2 : 0);
   p.W_bf = take(bf ? (size_t)h.L * 4 * D * D * 2 : 0);
+  // FP32 mode: TF32 high and low parts of W_g and W_h of every layer
+  p.W_t3 = take(use_tf32x3(h) ? (size_t)h.L * 8 * D * D * 4 : 0);
   p.total = o;
   return p;
 }
@@ -200,6 +206,20 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
   bf.F_bf = nullptr;
   // BF16 mode: the update and node maps run on the tensor cores (gemm_tc.cu)
   const bool use_tc = sizeof(T) == 4 && h.precision == DQ_BF16_MIXED;
+  const bool use_t3 = sizeof(T) == 4 && use_tf32x3(h);
+  float* W_t3 = reinterpret_cast<float*>(ws + plan.W_t3);
+  const int64_t DD = (int64_t)h.D * h.D;
+  // layer l: W_g high [3DD], W_g low [3DD], W_h high [DD], W_h low [DD]
+  auto wg_t3 = [&](int l, int part) { return W_t3 + (int64_t)l * 8 * DD + part * 3 * DD; };
+  auto wh_t3 = [&](int l, int part) { return W_t3 + (int64_t)l * 8 * DD + 6 * DD + part * DD; };
+  if (use_t3) {
+    if constexpr (sizeof(T) == 4) {
+      for (int l = 0; l < h.L; ++l) {
+        DQ_CU(split_tf32(params + h.off.layer[l].W_g, wg_t3(l, 0), wg_t3(l, 1), 3 * DD, s));
+        DQ_CU(split_tf32(params + h.off.layer[l].W_h, wh_t3(l, 0), wh_t3(l, 1), DD, s));
+      }
+    }
+  }
   unsigned char* W_bf = ws + plan.W_bf;
   auto wg_bf = [&](int l) { return W_bf + (size_t)l * 4 * h.D * h.D * 2; };
   auto wh_bf = [&](int l) { return wg_bf(l) + (size_t)3 * h.D * h.D * 2; };
@@ -245,6 +265,10 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
         if (use_tc) {
           DQ_LAUNCH(h, kb + PK_GEMM_NODE, gemm_bf16_tc(bf.F_bf, rows, D, D, wh_bf(l), D, nullptr, 1,
                                                        reinterpret_cast<float*>(bf.Z), D, h.d_status, s));
+        } else if (use_t3) {
+          DQ_LAUNCH(h, kb + PK_GEMM_NODE, gemm_tf32x3_tc(reinterpret_cast<const float*>(bf.F), rows, D, D, wh_t3(l, 0),
+                                                         wh_t3(l, 1), D, nullptr, 1, reinterpret_cast<float*>(bf.Z), D,
+                                                         h.d_status, s));
         } else {
           DQ_LAUNCH(h, kb + PK_GEMM_NODE, gemm_nt<T>(bf.F, node, params + y.W_h, nullptr, 1, bf.Z, node, rows, D, D,
                                                      false, s));
@@ -256,6 +280,11 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
         DQ_LAUNCH(h, kb + PK_GEMM_UPDATE, gemm_bf16_tc(bf.msg_bf, rows, 3 * D, 3 * D, wg_bf(l), D,
                                                        reinterpret_cast<const float*>(params + y.b_g), C,
                                                        reinterpret_cast<float*>(bf.Z), D, h.d_status, s));
+      } else if (use_t3) {
+        DQ_LAUNCH(h, kb + PK_GEMM_UPDATE, gemm_tf32x3_tc(reinterpret_cast<const float*>(bf.msg), rows, 3 * D, 3 * D,
+                                                         wg_t3(l, 0), wg_t3(l, 1), D,
+                                                         reinterpret_cast<const float*>(params + y.b_g), C,
+                                                         reinterpret_cast<float*>(bf.Z), D, h.d_status, s));
       } else {
         DQ_LAUNCH(h, kb + PK_GEMM_UPDATE, gemm_nt<T>(bf.msg, mrow, params + y.W_g, params + y.b_g, C, bf.Z, node, rows,
                                                      D, 3 * D, false, s));
@@ -857,6 +886,19 @@ dq_status dq_test_gemm_bf16(const void* X, int64_t rows, int32_t K, int64_t ldx,
   if (!X || !W || !Y || !status || rows < 0 || n_out < 0 || ldy < n_out) return DQ_ERR_ARG;
   const cudaError_t e = gemm_bf16_tc(X, rows, K, ldx, W, n_out, bias, bias_period, Y, ldy, status,
                                      (cudaStream_t)stream);
+  if (e == cudaErrorInvalidValue) return DQ_ERR_ARG;
+  return e == cudaSuccess ? DQ_OK : DQ_ERR_CUDA;
+}
+
+dq_status dq_test_gemm_tf32x3(const float* X, int64_t rows, int32_t K, int64_t ldx, const float* W, int32_t n_out,
+                              const float* bias, int32_t bias_period, float* Y, int64_t ldy, float* wsplit,
+                              uint32_t* status, void* stream) {
+  if (!X || !W || !Y || !wsplit || !status || rows < 0 || n_out < 0 || K <= 0 || ldy < n_out) return DQ_ERR_ARG;
+  const cudaStream_t s = (cudaStream_t)stream;
+  const int64_t nw = (int64_t)n_out * K;
+  cudaError_t e = split_tf32(W, wsplit, wsplit + nw, nw, s);
+  if (e == cudaSuccess)
+    e = gemm_tf32x3_tc(X, rows, K, ldx, wsplit, wsplit + nw, n_out, bias, bias_period, Y, ldy, status, s);
   if (e == cudaErrorInvalidValue) return DQ_ERR_ARG;
   return e == cudaSuccess ? DQ_OK : DQ_ERR_CUDA;
 }
