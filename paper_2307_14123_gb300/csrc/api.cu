@@ -408,9 +408,9 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
     auto MS = [&](int l) { return buf(pl.msg) + (int64_t)l * Bmax * N * 3 * D; };
     auto U = [&](int l) { return buf(pl.u) + (int64_t)l * Bmax * N * D; };
     auto F = [&](int l) { return buf(pl.F) + (int64_t)l * Bmax * N * D; };
-    DQ_LAUNCH(h, PK_BWD_GEMM, launch_layer0_node<T>(h, d, params, v, s));
-    DQ_LAUNCH(h, PK_BWD_GEMM, launch_geometry<T>(h, d, r + b0 * N * 3, v, s));
-    DQ_LAUNCH(h, PK_BWD_GEMM, launch_fill_spin_rows<T>(F(0), params + off.E_spin, nb, N, h.n_up, D, s));
+    DQ_LAUNCH(h, kValueOffset + PK_LAYER0, launch_layer0_node<T>(h, d, params, v, s));
+    DQ_LAUNCH(h, kValueOffset + PK_GEOMETRY, launch_geometry<T>(h, d, r + b0 * N * 3, v, s));
+    DQ_LAUNCH(h, kValueOffset + PK_UPDATE, launch_fill_spin_rows<T>(F(0), params + off.E_spin, nb, N, h.n_up, D, s));
     for (int l = 0; l < L; ++l) {
       const auto& y = off.layer[l];
       v.eh = EH(l);
@@ -418,33 +418,33 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
       v.F = F(l);
       v.Z = ZL(l);
       v.msg = MS(l);
-      DQ_LAUNCH(h, PK_BWD_GEMM, launch_edge_hidden<T>(h, d, params, l, v, s));
+      DQ_LAUNCH(h, kValueOffset + PK_EDGE_HIDDEN, launch_edge_hidden<T>(h, d, params, l, v, s));
       for (int t = 0; t < 3; ++t) {
         if (ng[t] == 0) continue;
         const RowMap m{(int64_t)ng[t], (int64_t)E * D, D};
-        DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nt<T>(v.eh + (int64_t)e0[t] * D, m, params + y.W2[t], params + y.b2[t], 1,
+        DQ_LAUNCH(h, kValueOffset + PK_GEMM_EDGE, gemm_nt<T>(v.eh + (int64_t)e0[t] * D, m, params + y.W2[t], params + y.b2[t], 1,
                                              v.ew + (int64_t)e0[t] * D, m, nb * ng[t], D, D, false, s));
       }
       if (l > 0)
-        DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nt<T>(F(l), rm(D), params + y.W_h, nullptr, 1, ZL(l), rm(D), nb * N, D, D,
+        DQ_LAUNCH(h, kValueOffset + PK_GEMM_NODE, gemm_nt<T>(F(l), rm(D), params + y.W_h, nullptr, 1, ZL(l), rm(D), nb * N, D, D,
                                              false, s));
-      DQ_LAUNCH(h, PK_BWD_GEMM, launch_messages<T>(h, d, params, l, l == 0, v, s));
-      DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nt<T>(MS(l), rm(3 * D), params + y.W_g, params + y.b_g, 1, U(l), rm(D), nb * N,
+      DQ_LAUNCH(h, kValueOffset + PK_MESSAGES, launch_messages<T>(h, d, params, l, l == 0, v, s));
+      DQ_LAUNCH(h, kValueOffset + PK_GEMM_UPDATE, gemm_nt<T>(MS(l), rm(3 * D), params + y.W_g, params + y.b_g, 1, U(l), rm(D), nb * N,
                                            D, 3 * D, false, s));
-      DQ_LAUNCH(h, PK_BWD_GEMM, launch_update_io<T>(h, d, params, l == 0, U(l), F(l), F(l + 1), s));
+      DQ_LAUNCH(h, kValueOffset + PK_UPDATE, launch_update_io<T>(h, d, params, l == 0, U(l), F(l), F(l + 1), s));
     }
     v.F = F(L);
     for (int sg = 0; sg < 2; ++sg) {
       if (ns[sg] == 0) continue;
       const RowMap mx{(int64_t)ns[sg], (int64_t)N * D, D};
       const RowMap my{(int64_t)ns[sg], (int64_t)N * Wo, Wo};
-      DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nt<T>(F(L) + (int64_t)i0[sg] * D, mx, params + off.W_o[sg], params + off.b_o[sg],
+      DQ_LAUNCH(h, kValueOffset + PK_GEMM_ORBITAL, gemm_nt<T>(F(L) + (int64_t)i0[sg] * D, mx, params + off.W_o[sg], params + off.b_o[sg],
                                            1, v.phi + (int64_t)i0[sg] * Wo, my, nb * ns[sg], K * ns[sg], D, false, s));
     }
-    DQ_LAUNCH(h, PK_BWD_DET, launch_orbital_det<T>(h, d, params, v, s));
+    DQ_LAUNCH(h, kValueOffset + PK_ORBITAL_DET, launch_orbital_det<T>(h, d, params, v, s));
     if (h.use_jastrow) {
-      DQ_LAUNCH(h, PK_BWD_GEMM, launch_jastrow_sum<T>(h, d, v, s));
-      DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nt<T>(v.js, rm(D), params + off.W_J1, params + off.b_J1, 1, v.jh, rm(D), nb, D, D,
+      DQ_LAUNCH(h, kValueOffset + PK_JASTROW_SUM, launch_jastrow_sum<T>(h, d, v, s));
+      DQ_LAUNCH(h, kValueOffset + PK_GEMM_JASTROW, gemm_nt<T>(v.js, rm(D), params + off.W_J1, params + off.b_J1, 1, v.jh, rm(D), nb, D, D,
                                            false, s));
     }
     // ---- reverse pass ----

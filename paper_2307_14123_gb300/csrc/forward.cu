@@ -150,85 +150,194 @@ __global__ void layer0_node_kernel(const T* __restrict__ params, int D, int64_t 
 
 // ---------------------------------------------------------------------------
 // Messages, Eq. (17), normalised per edge type, with the product rule.
-// One CTA per (walker, chunk of DC features); lanes run over features and the
-// whole chunk of node channels z[j][c] is staged in shared memory.
 //
-// Main part: for every feature d the messages are two masked N x N matrices
-// (same-spin / opposite-spin edge filters w_ij, zero diagonal) applied to the
-// N x C matrix z[j][c].  A thread owns an IB x CB block of (receiving
-// electron, channel) outputs inside one spin block, so every shared-memory
-// load feeds several FMAs.  The product-rule terms that involve derivatives
-// of w_ij (only the six coordinates of electrons i and j) and the
-// electron-nucleus messages are added afterwards for the same outputs.
+// For every feature d the messages of channel c are two masked N x N
+// matrices (same-spin / opposite-spin edge filters w_ij, zero diagonal)
+// applied to the node channels z[j][c], plus the product-rule terms with
+// derivatives of w_ij, which are nonzero only for the coordinates of i or j
+// (u_ij = (r_i - r_j) / d_ij, w' and w'' the radial derivatives):
+//  (a) channel of a SENDER's coordinate (c = 1 + 3e + x, e != i):
+//      -w'_ie u_ie,x z_e[0];
+//  (b) channel of the RECEIVER's own coordinate (c = 1 + 3i + x):
+//      sum_j w'_ij u_ij,x z_j[0], and sum_I w'_iI u_iI,x Y_I for the nuclei;
+//  (c) Laplacian channel: sum_j (2 w'' + 4 w'/d) z_j[0] + 2 w' u.(dz_j/dr_i - dz_j/dr_j),
+//      and sum_I (w''_iI + 2 w'_iI / d_iI) Y_I;
+//  (d) value channel: electron-nucleus messages sum_I w_iI Y_I.
+//
+// Jets: one CTA per (walker, chunk of 32 features), lanes over features.
+// The filters are symmetric in (i, j), so w and w' are staged as N x N
+// tables whose row j lists the receivers i: the IB receivers of a block sit
+// at fixed offsets.  Signed unit vectors u_ij and z_j[0] are staged too.
+// Phase 1 (all warps): the per-receiver terms (b), (c), (d) into shared
+// memory.  Phase 2: a warp owns IB receivers x CB channels of one spin block
+// and runs two passes (same-spin, opposite-spin senders) accumulating in
+// registers, adds (a), then the phase-1 terms, and stores.
 // ---------------------------------------------------------------------------
 template <class T>
 __device__ __forceinline__ T to_out(float v, T*) { return (T)v; }
 __device__ __forceinline__ double to_out(double v, double*) { return v; }
 __device__ __forceinline__ __nv_bfloat16 to_out(float v, __nv_bfloat16*) { return __float2bfloat16_rn(v); }
 
-template <class T, class TO, int DC, int IB, int CB>
-__global__ void __launch_bounds__(256)
+constexpr int kMsgLanes = 32;
+
+// Shared-memory layout of the jet message kernel (element offsets in T).
+struct MsgSmem {
+  int w0, w1, us, invd, z0c, sp, ps, total_bytes;
+};
+template <class T>
+__host__ __device__ inline MsgSmem msg_smem_layout(int N, int IB, bool stage_w1) {
+  MsgSmem m{};
+  int o = 0;
+  const int rows = N * N + IB;  // padded: receivers past the end read zeros
+  m.w0 = o; o += rows * kMsgLanes;
+  m.w1 = o; o += stage_w1 ? rows * kMsgLanes : 0;
+  m.us = o; o += (N + IB) * N * 3;  // u_ij,x (zero diagonal, zero padding)
+  m.invd = o; o += N * N;
+  m.z0c = o; o += N * kMsgLanes;   // z_j[0]
+  m.sp = o; o += 13 * N * kMsgLanes;  // (b) [N][3 x][3], (c) [N][3], (d) [N]
+  m.ps = o * (int)sizeof(T);       // byte offset of the int pair table
+  m.total_bytes = m.ps + N * N * (int)sizeof(int);
+  return m;
+}
+
+template <class T, class TO, int IB, int CB>
+__global__ void __launch_bounds__(256, 2)
     messages_kernel(const T* __restrict__ Z, const T* __restrict__ z0, const T* __restrict__ ew,
                     const T* __restrict__ geo, const T* __restrict__ Y, const int* __restrict__ pair_of, int N,
-                    int n_up, int M, int C, int D, int E, int n_ee, int ej, int z_const, TO* __restrict__ msg) {
+                    int n_up, int M, int C, int D, int E, int n_ee, int z_const, int stage_w1,
+                    TO* __restrict__ msg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int zc_rows = z_const ? 2 : N * C;     // z[j][c] rows (two spin rows if z is constant)
-  T* Zs = reinterpret_cast<T*>(smem_raw);      // [zc_rows][DC]
-  T* Wm = Zs + zc_rows * DC;                   // [N*N][DC] w_ij, zero diagonal
-  T* W1p = Wm + N * N * DC;                    // [n_ee][DC] w'   (jets)
-  T* W2p = W1p + (ej == 3 ? n_ee * DC : 0);    // [n_ee][DC] w''  (jets)
-  T* WN = W2p + (ej == 3 ? n_ee * DC : 0);     // [N*M][ej][DC] electron-nucleus filter jets
-  T* Ys = WN + N * M * ej * DC;                // [M][DC]
-  T* Gs = Ys + M * DC;                         // [E][4]
-  int* Ps = reinterpret_cast<int*>(Gs + E * 4);  // [N][N]
+  constexpr int L = kMsgLanes, ej = 3;
+  const MsgSmem lay = msg_smem_layout<T>(N, IB, stage_w1 != 0);
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  T* W0 = sm + lay.w0;  // [(j*N + i)][L]
+  T* W1 = sm + lay.w1;
+  T* Us = sm + lay.us;  // [(i*N + j)][3]
+  T* Id = sm + lay.invd;
+  T* Z0c = sm + lay.z0c;  // [j][L]
+  T* SP = sm + lay.sp;
+  int* Ps = reinterpret_cast<int*>(smem_raw + lay.ps);
+  T* SPb = SP;                      // [i][x][3]  (same, opposite, nucleus)
+  T* SPc = SP + 9 * N * L;          // [i][3]
+  T* SPd = SP + 12 * N * L;         // [i]
 
   const int64_t b = blockIdx.x;
-  const int d0 = blockIdx.y * DC;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const bool jets = C > 1;
-  const T* EWb = ew + b * E * ej * D;
-
-  for (int k = tid; k < N * N; k += nthr) Ps[k] = pair_of[k];
+  const int d0 = blockIdx.y * L;
+  const int tid = threadIdx.x, lane = tid % L, grp = tid / L, ngroups = blockDim.x / L;
+  const T* EWb = ew + b * E * ej * D + d0 + lane;  // this lane's feature of every edge filter
+  const T* Zb = Z + b * N * C * D + d0 + lane;
+  const T* Yd = Y + d0 + lane;
   const T* Gb = geo + b * E * 4;
-  for (int k = tid; k < E * 4; k += nthr) Gs[k] = Gb[k];
-  if (z_const) {
-    for (int k = tid; k < 2 * DC; k += nthr) Zs[k] = z0[(k / DC) * D + d0 + k % DC];
-  } else {
-    const T* Zb = Z + b * N * C * D;
-    for (int k = tid; k < N * C * DC; k += nthr) Zs[k] = Zb[(int64_t)(k / DC) * D + d0 + k % DC];
-  }
-  __syncthreads();
-  for (int k = tid; k < N * N * DC; k += nthr) {
-    const int ij = k / DC, dd = k % DC;
-    const int i = ij / N, j = ij % N;
-    Wm[k] = i == j ? T(0) : EWb[(int64_t)Ps[ij] * ej * D + d0 + dd];
-  }
-  if (ej == 3)
-    for (int k = tid; k < n_ee * DC; k += nthr) {
-      const int p = k / DC, dd = k % DC;
-      W1p[k] = EWb[((int64_t)p * 3 + 1) * D + d0 + dd];
-      W2p[k] = EWb[((int64_t)p * 3 + 2) * D + d0 + dd];
+  const int NN = N * N;
+
+  // ---- staging ----
+  for (int k = tid; k < NN; k += blockDim.x) {
+    const int i = k / N, j = k - (k / N) * N;
+    const int p = pair_of[k];
+    Ps[k] = p;
+    T u0 = 0, u1 = 0, u2 = 0, id = 0;
+    if (i != j) {
+      const T sg = i < j ? T(1) : T(-1);
+      u0 = sg * Gb[p * 4 + 1];
+      u1 = sg * Gb[p * 4 + 2];
+      u2 = sg * Gb[p * 4 + 3];
+      id = T(1) / Gb[p * 4];
     }
-  for (int k = tid; k < N * M * ej * DC; k += nthr) WN[k] = EWb[(int64_t)(n_ee * ej + k / DC) * D + d0 + k % DC];
-  for (int k = tid; k < M * DC; k += nthr) Ys[k] = Y[(int64_t)(k / DC) * D + d0 + k % DC];
+    Us[k * 3] = u0;
+    Us[k * 3 + 1] = u1;
+    Us[k * 3 + 2] = u2;
+    Id[k] = id;
+  }
+  for (int k = tid; k < IB * N * 3; k += blockDim.x) Us[NN * 3 + k] = T(0);
+  for (int r = grp; r < NN + IB; r += ngroups) {
+    T v0 = 0, v1 = 0;
+    if (r < NN) {
+      const int j = r / N, i = r - (r / N) * N;
+      if (i != j) {
+        const T* w = EWb + (int64_t)pair_of[r] * ej * D;
+        v0 = w[0];
+        v1 = w[D];
+      }
+    }
+    W0[r * L + lane] = v0;
+    if (stage_w1) W1[r * L + lane] = v1;
+  }
+  for (int j = grp; j < N; j += ngroups)
+    Z0c[j * L + lane] = z_const ? z0[(j < n_up ? 0 : D) + d0 + lane] : Zb[(int64_t)j * C * D];
   __syncthreads();
 
+  // w'_ij of this lane (i != j)
+  auto w1_at = [&](int i, int j) -> T {
+    if (stage_w1) return W1[(j * N + i) * L + lane];
+    return EWb[((int64_t)Ps[i * N + j] * ej + 1) * D];
+  };
+
+  // ---- phase 1: per-receiver terms (b), (c), (d) ----
+  const int n_items = 5 * N;  // 3N of kind (b), N of (c), N of (d)
+  for (int it = grp; it < n_items; it += ngroups) {
+    if (it < 3 * N) {  // (b) receiver i, axis x
+      const int i = it / 3, x = it - (it / 3) * 3;
+      const bool up = i < n_up;
+      T ss = 0, so = 0, sn = 0;
+      for (int j = 0; j < N; ++j) {
+        if (j == i) continue;
+        const T t = w1_at(i, j) * Us[(i * N + j) * 3 + x] * Z0c[j * L + lane];
+        if ((j < n_up) == up) ss += t; else so += t;
+      }
+      for (int I = 0; I < M; ++I) {
+        const int en = i * M + I;
+        sn += EWb[((int64_t)(n_ee + en) * ej + 1) * D] * Gb[(n_ee + en) * 4 + 1 + x] * Yd[(int64_t)I * D];
+      }
+      T* o = SPb + (i * 3 + x) * 3 * L + lane;
+      o[0] = ss;
+      o[L] = so;
+      o[2 * L] = sn;
+    } else if (it < 4 * N) {  // (c) Laplacian channel of receiver i
+      const int i = it - 3 * N;
+      const bool up = i < n_up;
+      T ss = 0, so = 0, sn = 0;
+      for (int j = 0; j < N; ++j) {
+        if (j == i) continue;
+        const T v1 = w1_at(i, j);
+        const T v2 = EWb[((int64_t)Ps[i * N + j] * ej + 2) * D];
+        T t = (T(2) * v2 + T(4) * v1 * Id[i * N + j]) * Z0c[j * L + lane];
+        if (!z_const) {
+          const T* zj = Zb + (int64_t)j * C * D;
+          const T* u = Us + (i * N + j) * 3;
+          T cr = 0;
+          for (int x = 0; x < 3; ++x) cr += u[x] * (zj[(int64_t)(1 + 3 * i + x) * D] - zj[(int64_t)(1 + 3 * j + x) * D]);
+          t += T(2) * v1 * cr;
+        }
+        if ((j < n_up) == up) ss += t; else so += t;
+      }
+      for (int I = 0; I < M; ++I) {
+        const int en = i * M + I;
+        const T* w = EWb + (int64_t)(n_ee + en) * ej * D;
+        sn += (w[2 * D] + T(2) * w[D] / Gb[(n_ee + en) * 4]) * Yd[(int64_t)I * D];
+      }
+      T* o = SPc + i * 3 * L + lane;
+      o[0] = ss;
+      o[L] = so;
+      o[2 * L] = sn;
+    } else {  // (d) value channel, nuclei
+      const int i = it - 4 * N;
+      T sn = 0;
+      for (int I = 0; I < M; ++I) sn += EWb[(int64_t)(n_ee + i * M + I) * ej * D] * Yd[(int64_t)I * D];
+      SPd[i * L + lane] = sn;
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 2: main contraction ----
   const int n_dn = N - n_up;
-  const int dd = tid % DC;
-  const int ngroups = nthr / DC;
   const int nib_up = (n_up + IB - 1) / IB, nib_dn = (n_dn + IB - 1) / IB;
   const int ncb = (C + CB - 1) / CB;
   const int ntasks = (nib_up + nib_dn) * ncb;
   const T nuM = T(1) / T(M);
-  TO* mb = msg + b * N * C * 3 * D + d0 + dd;
-  // z value: z[j][c] of this lane's feature
-  auto zv = [&](int j, int c) -> T {
-    if (z_const) return c == 0 ? Zs[(j < n_up ? 0 : 1) * DC + dd] : T(0);
-    return Zs[(j * C + c) * DC + dd];
-  };
-
-  for (int task = tid / DC; task < ntasks; task += ngroups) {
-    const int ibk = task / ncb, cbk = task % ncb;
+  TO* mb = msg + b * N * C * 3 * D + d0 + lane;
+  const int CD = C * D;
+  for (int task = grp; task < ntasks; task += ngroups) {
+    const int ibk = task / ncb, cbk = task - (task / ncb) * ncb;
     const bool up = ibk < nib_up;
     const int sb0 = up ? 0 : n_up, sbn = up ? n_up : n_dn;  // spin block of the receivers
     const int i0 = sb0 + (up ? ibk : ibk - nib_up) * IB;
@@ -236,167 +345,122 @@ __global__ void __launch_bounds__(256)
     const int c0 = cbk * CB;
     const int nc = min(CB, C - c0);
     const int os0 = up ? n_up : 0, osn = up ? n_dn : n_up;  // opposite spin block (senders)
-    T as[IB][CB], ao[IB][CB];
+    int eq[CB], xq[CB];  // electron / axis of the coordinate channels (-1: none)
 #pragma unroll
-    for (int a = 0; a < IB; ++a)
-#pragma unroll
-      for (int q = 0; q < CB; ++q) as[a][q] = ao[a][q] = T(0);
-
-    // main contraction
-    if (!z_const || c0 == 0) {
-      for (int j = sb0; j < sb0 + sbn; ++j) {
-        T zc[CB];
-#pragma unroll
-        for (int q = 0; q < CB; ++q) zc[q] = q < nc ? zv(j, c0 + q) : T(0);
-#pragma unroll
-        for (int a = 0; a < IB; ++a) {
-          if (a < ni) {
-            const T w = Wm[((i0 + a) * N + j) * DC + dd];
-#pragma unroll
-            for (int q = 0; q < CB; ++q) as[a][q] += w * zc[q];
-          }
-        }
-      }
-      for (int j = os0; j < os0 + osn; ++j) {
-        T zc[CB];
-#pragma unroll
-        for (int q = 0; q < CB; ++q) zc[q] = q < nc ? zv(j, c0 + q) : T(0);
-#pragma unroll
-        for (int a = 0; a < IB; ++a) {
-          if (a < ni) {
-            const T w = Wm[((i0 + a) * N + j) * DC + dd];
-#pragma unroll
-            for (int q = 0; q < CB; ++q) ao[a][q] += w * zc[q];
-          }
-        }
-      }
+    for (int q = 0; q < CB; ++q) {
+      const int c = c0 + q;
+      const bool coord = q < nc && c >= 1 && c < C - 1;
+      eq[q] = coord ? (c - 1) / 3 : -1;
+      xq[q] = coord ? (c - 1) - ((c - 1) / 3) * 3 : 0;
     }
-
-    // Product-rule terms with derivatives of w_ij (only coordinates of i or j):
-    //  (a) channel of a SENDER's coordinate (c = 1 + 3j + x, j != i):
-    //      -w'_ij u_ij,x z_j[0]; a 4-channel block holds those of at most two senders;
-    //  (b) channel of the RECEIVER's own coordinate (c = 1 + 3i + x):
-    //      sum_j w'_ij u_ij,x z_j[0] (+ the electron-nucleus term);
-    //  (c) Laplacian channel: sum_j (2 w'' + 4 w'/d) z_j[0] + 2 w' u.(dz_j/dr_i - dz_j/dr_j);
-    //  (d) electron-nucleus messages of the value channel.
-    // Terms are added to the register accumulators with predicated selects.
-    const int n_same = up ? n_up : n_dn, n_opp = up ? n_dn : n_up;
-    const T nu_s = T(1) / T(n_same - 1 > 1 ? n_same - 1 : 1);
-    const T nu_o = T(1) / T(n_opp > 1 ? n_opp : 1);
-    T an[IB][CB];
+    const bool zc_live = !z_const || c0 == 0;  // constant z: only the value channel
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      const int j0 = pass == 0 ? sb0 : os0, jn = pass == 0 ? sbn : osn;
+      T acc[IB][CB];
 #pragma unroll
-    for (int a = 0; a < IB; ++a)
+      for (int a = 0; a < IB; ++a)
 #pragma unroll
-      for (int q = 0; q < CB; ++q) an[a][q] = T(0);
-    auto add_to = [&](int a, int q, bool same, T v) {
+        for (int q = 0; q < CB; ++q) acc[a][q] = T(0);
+      if (zc_live && jn > 0) {
+        const T* zp = Zb + (int64_t)j0 * CD + c0 * D;
+        const T* wp = W0 + (j0 * N + i0) * L + lane;
+        T zn[CB];
 #pragma unroll
-      for (int a2 = 0; a2 < IB; ++a2)
+        for (int q = 0; q < CB; ++q) zn[q] = q < nc ? (z_const ? (q == 0 ? Z0c[j0 * L + lane] : T(0)) : zp[q * D]) : T(0);
+#pragma unroll 1
+        for (int jj = 0; jj < jn; ++jj) {
+          T zc[CB];
 #pragma unroll
-        for (int q2 = 0; q2 < CB; ++q2)
-          if (a2 == a && q2 == q) {
-            if (same) as[a2][q2] += v; else ao[a2][q2] += v;
+          for (int q = 0; q < CB; ++q) zc[q] = zn[q];
+          if (jj + 1 < jn) {
+            zp += CD;
+#pragma unroll
+            for (int q = 0; q < CB; ++q)
+              zn[q] = q < nc ? (z_const ? (q == 0 ? Z0c[(j0 + jj + 1) * L + lane] : T(0)) : zp[q * D]) : T(0);
           }
-    };
-    auto add_nuc = [&](int a, int q, T v) {
 #pragma unroll
-      for (int a2 = 0; a2 < IB; ++a2)
+          for (int a = 0; a < IB; ++a) {
+            const T w = wp[a * L];
 #pragma unroll
-        for (int q2 = 0; q2 < CB; ++q2)
-          if (a2 == a && q2 == q) an[a2][q2] += v;
-    };
-    if (jets) {
-      // coordinate channels in this block: 1 + 3e + x for e in [e_lo, e_hi]
-      const int cJ0 = c0 < 1 ? 1 : c0, cJ1 = min(c0 + nc, C - 1);  // [cJ0, cJ1)
-      if (cJ0 < cJ1) {
-        const int e_lo = (cJ0 - 1) / 3, e_hi = (cJ1 - 2) / 3;
-#pragma unroll 1
-        for (int e = e_lo; e <= e_hi; ++e) {
-          const bool e_same = (e < n_up) == up;
-#pragma unroll 1
-          for (int x = 0; x < 3; ++x) {
-            const int c = 1 + 3 * e + x;
-            if (c < cJ0 || c >= cJ1) continue;
-            const int q = c - c0;
-#pragma unroll 1
-            for (int a = 0; a < ni; ++a) {
-              const int i = i0 + a;
-              if (i != e) {  // (a) e is a sender
-                const int p = Ps[i * N + e];
-                const T u = (i < e ? Gs[p * 4 + 1 + x] : -Gs[p * 4 + 1 + x]);
-                add_to(a, q, e_same, -W1p[p * DC + dd] * u * zv(e, 0));
-              } else {  // (b) the receiver's own coordinate
-                T ss = 0, so = 0, sn = 0;
-                for (int j = 0; j < N; ++j) {
-                  if (j == i) continue;
-                  const int p = Ps[i * N + j];
-                  const T u = (i < j ? Gs[p * 4 + 1 + x] : -Gs[p * 4 + 1 + x]);
-                  const T t = W1p[p * DC + dd] * u * zv(j, 0);
-                  if ((j < n_up) == up) ss += t; else so += t;
-                }
-                for (int I = 0; I < M; ++I) {
-                  const int en = i * M + I;
-                  sn += WN[(en * ej + 1) * DC + dd] * Gs[(n_ee + en) * 4 + 1 + x] * Ys[I * DC + dd];
-                }
-                add_to(a, q, true, ss);
-                add_to(a, q, false, so);
-                add_nuc(a, q, sn);
-              }
-            }
+            for (int q = 0; q < CB; ++q) acc[a][q] += w * zc[q];
           }
+          wp += N * L;
         }
       }
-      if (c0 + nc == C) {  // (c) the Laplacian channel is the last of this block
-        const int q = C - 1 - c0;
-#pragma unroll 1
-        for (int a = 0; a < ni; ++a) {
-          const int i = i0 + a;
-          T ss = 0, so = 0, sn = 0;
-          for (int j = 0; j < N; ++j) {
-            if (j == i) continue;
-            const int p = Ps[i * N + j];
-            const T w1 = W1p[p * DC + dd], w2 = W2p[p * DC + dd];
-            const T sg = i < j ? T(1) : T(-1);
-            T t = (T(2) * w2 + T(4) * w1 / Gs[p * 4]) * zv(j, 0);
-            T cr = 0;
-            for (int x = 0; x < 3; ++x)
-              cr += sg * Gs[p * 4 + 1 + x] * (zv(j, 1 + 3 * i + x) - zv(j, 1 + 3 * j + x));
-            t += T(2) * w1 * cr;
-            if ((j < n_up) == up) ss += t; else so += t;
-          }
-          for (int I = 0; I < M; ++I) {
-            const int en = i * M + I;
-            sn += (WN[(en * ej + 2) * DC + dd] + T(2) * WN[(en * ej + 1) * DC + dd] / Gs[(n_ee + en) * 4]) *
-                  Ys[I * DC + dd];
-          }
-          add_to(a, q, true, ss);
-          add_to(a, q, false, so);
-          add_nuc(a, q, sn);
-        }
-      }
-    }
-    if (c0 == 0) {  // (d) value channel: electron-nucleus messages
-#pragma unroll 1
-      for (int a = 0; a < ni; ++a) {
-        T sn = 0;
-        for (int I = 0; I < M; ++I) sn += WN[((i0 + a) * M + I) * ej * DC + dd] * Ys[I * DC + dd];
-        add_nuc(a, 0, sn);
-      }
-    }
-    // normalisation and store
-#pragma unroll
-    for (int a = 0; a < IB; ++a) {
-      if (a >= ni) continue;
-      const int i = i0 + a;
+      // (a): channels holding a coordinate of a sender of this pass
 #pragma unroll
       for (int q = 0; q < CB; ++q) {
-        if (q >= nc) continue;
-        TO* out = mb + ((int64_t)i * C + c0 + q) * 3 * D;
-        out[0] = to_out(as[a][q] * nu_s, out);
-        out[D] = to_out(ao[a][q] * nu_o, out);
-        out[2 * D] = to_out(an[a][q] * nuM, out);
+        const int e = eq[q];
+        if (e < j0 || e >= j0 + jn) continue;
+        const T ze0 = Z0c[e * L + lane];
+        const T* ue = Us + (i0 * N + e) * 3 + xq[q];
+#pragma unroll
+        for (int a = 0; a < IB; ++a) {
+          const int i = i0 + a;
+          if (a < ni && i != e) acc[a][q] -= w1_at(i, e) * ue[a * N * 3] * ze0;
+        }
+      }
+      const T nu = T(1) / T(pass == 0 ? (sbn - 1 > 1 ? sbn - 1 : 1) : (osn > 1 ? osn : 1));
+#pragma unroll
+      for (int a = 0; a < IB; ++a) {
+        if (a >= ni) continue;
+        const int i = i0 + a;
+#pragma unroll
+        for (int q = 0; q < CB; ++q) {
+          if (q >= nc) continue;
+          const int c = c0 + q;
+          const T* sp = nullptr;  // phase-1 terms of this output
+          T nuc = 0;
+          if (c == 0) {
+            nuc = SPd[i * L + lane];
+          } else if (c == C - 1) {
+            sp = SPc + i * 3 * L + lane;
+          } else if (eq[q] == i) {
+            sp = SPb + (i * 3 + xq[q]) * 3 * L + lane;
+          }
+          T v = acc[a][q];
+          if (sp) {
+            v += sp[pass * L];
+            nuc = sp[2 * L];
+          }
+          TO* out = mb + ((int64_t)i * C + c) * 3 * D;
+          out[pass * D] = to_out(v * nu, out);
+          if (pass == 1) out[2 * D] = to_out(nuc * nuM, out);
+        }
       }
     }
   }
+}
+
+// Value-only messages (C = 1): one thread per (walker, receiver, feature).
+template <class T, class TO>
+__global__ void __launch_bounds__(256)
+    messages_value_kernel(const T* __restrict__ Z, const T* __restrict__ z0, const T* __restrict__ ew,
+                          const T* __restrict__ Y, const int* __restrict__ pair_of, int64_t Bc, int N, int n_up,
+                          int M, int D, int E, int n_ee, int z_const, TO* __restrict__ msg) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= Bc * N * D) return;
+  const int d = (int)(gid % D);
+  const int64_t bi = gid / D;
+  const int i = (int)(bi % N);
+  const int64_t b = bi / N;
+  const bool up = i < n_up;
+  const T* ewb = ew + b * E * D + d;
+  const T* zb = Z + b * N * D + d;
+  T ss = 0, so = 0, sn = 0;
+  for (int j = 0; j < N; ++j) {
+    if (j == i) continue;
+    const T w = ewb[(int64_t)pair_of[i * N + j] * D];
+    const T z = z_const ? z0[(j < n_up ? 0 : D) + d] : zb[(int64_t)j * D];
+    if ((j < n_up) == up) ss += w * z; else so += w * z;
+  }
+  for (int I = 0; I < M; ++I) sn += ewb[(int64_t)(n_ee + i * M + I) * D] * Y[(int64_t)I * D + d];
+  const int n_same = up ? n_up : N - n_up, n_opp = N - n_same;
+  TO* out = msg + bi * 3 * D + d;
+  out[0] = to_out(ss / T(n_same - 1 > 1 ? n_same - 1 : 1), out);
+  out[D] = to_out(so / T(n_opp > 1 ? n_opp : 1), out);
+  out[2 * D] = to_out(sn / T(M), out);
 }
 
 // ---------------------------------------------------------------------------
@@ -982,58 +1046,46 @@ cudaError_t launch_layer0_node(const dq_handle_s& h, const FwdDims& d, const T* 
 
 namespace {
 template <class T>
-size_t message_smem(const dq_handle_s& h, const FwdDims& d, int DC, bool z_const) {
-  const int ej = d.C > 1 ? 3 : 1;
-  const size_t E = h.edges.n_all, n_ee = h.edges.n_ee, N = d.N, M = d.M;
-  const size_t zrows = z_const ? 2 : N * d.C;
-  const size_t vals = zrows * DC + N * N * DC + (ej == 3 ? 2 * n_ee * DC : 0) + N * M * ej * DC + M * DC + E * 4;
-  return vals * sizeof(T) + N * N * sizeof(int);
-}
-constexpr int kMsgIB = 4;
-template <class T, class TO, int DC>
-cudaError_t launch_messages_dct(const dq_handle_s& h, const FwdDims& d, const T* params, int l, bool z_const,
-                                FwdBuffers<T> b, TO* out, size_t smem, cudaStream_t s) {
-  constexpr int CB = sizeof(T) == 4 ? 4 : 2;
-  auto kern = messages_kernel<T, TO, DC, kMsgIB, CB>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int nib = (d.n_up + kMsgIB - 1) / kMsgIB + (d.n_dn + kMsgIB - 1) / kMsgIB;
-  const int ntasks = nib * ((d.C + CB - 1) / CB);
-  const int groups = ntasks < 256 / DC ? ntasks : 256 / DC;
-  dim3 grid((unsigned)d.Bc, d.D / DC);
-  kern<<<grid, groups * DC, smem, s>>>(b.Z, b.z0, b.ew, b.geo, params + h.off.layer[l].Y, h.d_pair_of, d.N, d.n_up,
-                                       d.M, d.C, d.D, h.edges.n_all, h.edges.n_ee, d.C > 1 ? 3 : 1, z_const ? 1 : 0,
-                                       out);
-  return cudaGetLastError();
-}
-template <class T, int DC>
-cudaError_t launch_messages_dc(const dq_handle_s& h, const FwdDims& d, const T* params, int l, bool z_const,
-                               FwdBuffers<T> b, size_t smem, cudaStream_t s) {
-  if constexpr (sizeof(T) == 4) {
-    if (b.msg_bf)
-      return launch_messages_dct<T, __nv_bfloat16, DC>(h, d, params, l, z_const, b,
-                                                       static_cast<__nv_bfloat16*>(b.msg_bf), smem, s);
+constexpr int msg_ib() { return sizeof(T) == 4 ? 8 : 4; }
+template <class T, class TO>
+cudaError_t launch_messages_t(const dq_handle_s& h, const FwdDims& d, const T* params, int l, bool z_const,
+                              FwdBuffers<T> b, TO* out, cudaStream_t s) {
+  const T* Y = params + h.off.layer[l].Y;
+  if (d.C == 1) {
+    const int64_t n = d.Bc * d.N * d.D;
+    messages_value_kernel<T, TO><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        b.Z, b.z0, b.ew, Y, h.d_pair_of, d.Bc, d.N, d.n_up, d.M, d.D, h.edges.n_all, h.edges.n_ee, z_const ? 1 : 0,
+        out);
+    return cudaGetLastError();
   }
-  return launch_messages_dct<T, T, DC>(h, d, params, l, z_const, b, b.msg, smem, s);
+  if (d.D % kMsgLanes) return cudaErrorInvalidConfiguration;
+  constexpr int IB = msg_ib<T>(), CB = sizeof(T) == 4 ? 4 : 2;
+  auto kern = messages_kernel<T, TO, IB, CB>;
+  bool stage_w1 = true;
+  MsgSmem lay = msg_smem_layout<T>(d.N, IB, stage_w1);
+  if (lay.total_bytes > 200 * 1024) {
+    stage_w1 = false;
+    lay = msg_smem_layout<T>(d.N, IB, stage_w1);
+  }
+  if (lay.total_bytes > 220 * 1024) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total_bytes);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)d.Bc, d.D / kMsgLanes);
+  kern<<<grid, 256, lay.total_bytes, s>>>(b.Z, b.z0, b.ew, b.geo, Y, h.d_pair_of, d.N, d.n_up, d.M, d.C, d.D,
+                                          h.edges.n_all, h.edges.n_ee, z_const ? 1 : 0, stage_w1 ? 1 : 0, out);
+  return cudaGetLastError();
 }
 }  // namespace
 
 template <class T>
 cudaError_t launch_messages(const dq_handle_s& h, const FwdDims& d, const T* params, int l, bool z_const,
                             FwdBuffers<T> b, cudaStream_t s) {
-  constexpr size_t kBudget = 76 * 1024, kMax = 220 * 1024;
-  for (int DC : {32, 16, 8}) {
-    if (d.D % DC) continue;
-    const size_t smem = message_smem<T>(h, d, DC, z_const);
-    if (smem > kBudget && DC > 8) continue;
-    if (smem > kMax) return cudaErrorInvalidConfiguration;
-    switch (DC) {
-      case 32: return launch_messages_dc<T, 32>(h, d, params, l, z_const, b, smem, s);
-      case 16: return launch_messages_dc<T, 16>(h, d, params, l, z_const, b, smem, s);
-      default: return launch_messages_dc<T, 8>(h, d, params, l, z_const, b, smem, s);
-    }
+  if constexpr (sizeof(T) == 4) {
+    if (b.msg_bf)
+      return launch_messages_t<T, __nv_bfloat16>(h, d, params, l, z_const, b, static_cast<__nv_bfloat16*>(b.msg_bf),
+                                                 s);
   }
-  return cudaErrorInvalidConfiguration;
+  return launch_messages_t<T, T>(h, d, params, l, z_const, b, b.msg, s);
 }
 
 template <class T>
