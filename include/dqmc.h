@@ -212,11 +212,14 @@ dq_status vmc_loss_weights_noalloc(dq_handle h, const void* e_loc, int64_t B, do
 dq_status dq_last_device_status(dq_handle h, void* stream, uint32_t* flags);
 
 /* Number of determinant matrices factorised in FP64 since the last read
- * (then cleared; synchronises `stream`).  In FP32 mode, value-only calls
- * (ansatz_eval, mcmc_step) factorise each matrix in FP32 and redo near-nodal
- * ones (condition estimate of the row-equilibrated matrix above 1000) in
- * FP64, which this counts; local_energy takes FP64 for every matrix (not
- * counted).  Always 0 in FP64 mode, where every matrix is FP64. */
+ * (then cleared; synchronises `stream`).  In the FP32 modes every matrix is
+ * first factorised in FP32 and near-nodal ones are redone in FP64, which this
+ * counts: value-only calls (ansatz_eval, mcmc_step) when the condition
+ * estimate of the row-equilibrated matrix exceeds 1000; local_energy, for
+ * spin blocks of at most 8 electrons, when it exceeds 2000 (below that the
+ * FP32 inverse is refined once in double-float).  local_energy with larger
+ * spin blocks takes FP64 for every matrix (not counted).  Always 0 in FP64
+ * mode, where every matrix is FP64. */
 dq_status dq_fp64_matrix_count(dq_handle h, void* stream, int64_t* count);
 
 /* Test support: the BF16 tensor-core GEMM used by the embedding layers in

@@ -100,9 +100,49 @@ struct FwdPlan {
   size_t geo, rbf, eh, ew, F, Z, msg, phi, det, js, jh, z0, msg_bf, F_bf, W_bf, W_t3, total;
 };
 
-// FP32 mode: the node and update maps run on the tensor cores as 3 x TF32
-// products when the width allows the 128-byte TMA rows (D % 32 == 0).
-inline bool use_tf32x3(const dq_handle_s& h) { return h.precision == DQ_FP32 && h.D % 32 == 0; }
+// FP32 modes: the FP32 GEMMs (edge filters, node and update maps, orbitals)
+// run on the tensor cores as 3 x TF32 products when the width allows the
+// 128-byte TMA rows (D % 32 == 0); in BF16 mode the node and update maps take
+// the BF16 GEMM instead.
+inline bool use_tf32x3(const dq_handle_s& h) { return h.precision != DQ_FP64 && h.D % 32 == 0; }
+constexpr int kT3PerLayer = 14;  // D x D blocks per layer: W_g 2 x 3, W_h 2, W2 2 x 3
+// TF32 splits: the layers' blocks, then W_o of both spins (high, low; K * nmax x D each)
+inline int64_t t3_weight_floats(const dq_handle_s& h) {
+  const int64_t nmax = std::max(h.n_up, h.n_dn);
+  return (int64_t)h.L * kT3PerLayer * h.D * h.D + 4 * h.K * nmax * h.D;
+}
+// Views of the split weights; part 0 = TF32 high, 1 = low.
+struct T3Weights {
+  float* base;
+  int64_t DD, WoD;
+  int L;
+  // layer l: W_g high [3DD], W_g low [3DD], W_h high [DD], W_h low [DD], W2[t] high / low [DD]
+  float* wg(int l, int part) const { return base + (int64_t)l * kT3PerLayer * DD + part * 3 * DD; }
+  float* wh(int l, int part) const { return base + (int64_t)l * kT3PerLayer * DD + 6 * DD + part * DD; }
+  float* w2(int l, int t, int part) const { return base + (int64_t)l * kT3PerLayer * DD + (8 + 2 * t + part) * DD; }
+  float* wo(int sg, int part) const { return base + (int64_t)L * kT3PerLayer * DD + (2 * sg + part) * WoD; }
+};
+inline T3Weights t3_weights(const dq_handle_s& h, void* base) {
+  return T3Weights{static_cast<float*>(base), (int64_t)h.D * h.D, (int64_t)h.K * std::max(h.n_up, h.n_dn) * h.D,
+                   h.L};
+}
+// Splits every weight matrix that runs on the 3 x TF32 GEMM (once per call).
+cudaError_t split_t3_weights(const dq_handle_s& h, const float* params, const T3Weights& w, cudaStream_t s) {
+  for (int l = 0; l < h.L; ++l) {
+    cudaError_t e = split_tf32(params + h.off.layer[l].W_g, w.wg(l, 0), w.wg(l, 1), 3 * w.DD, s);
+    if (e == cudaSuccess) e = split_tf32(params + h.off.layer[l].W_h, w.wh(l, 0), w.wh(l, 1), w.DD, s);
+    for (int t = 0; t < 3 && e == cudaSuccess; ++t)
+      e = split_tf32(params + h.off.layer[l].W2[t], w.w2(l, t, 0), w.w2(l, t, 1), w.DD, s);
+    if (e != cudaSuccess) return e;
+  }
+  const int nsp[2] = {h.n_up, h.n_dn};
+  for (int sg = 0; sg < 2; ++sg) {
+    if (nsp[sg] == 0) continue;
+    const cudaError_t e = split_tf32(params + h.off.W_o[sg], w.wo(sg, 0), w.wo(sg, 1), (int64_t)h.K * nsp[sg] * h.D, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 FwdPlan plan_forward(const dq_handle_s& h, int64_t Bc, bool jets, size_t elem) {
   const int64_t E = h.edges.n_all, N = h.N, D = h.D, K = h.K;
@@ -132,8 +172,8 @@ FwdPlan plan_forward(const dq_handle_s& h, int64_t Bc, bool jets, size_t elem) {
   p.msg_bf = take(bf ? Bc * N * C * 3 * D * 2 : 0);
   p.F_bf = take(bf ? Bc * N * C * D * 2 : 0);
   p.W_bf = take(bf ? (size_t)h.L * 4 * D * D * 2 : 0);
-  // FP32 mode: TF32 high and low parts of W_g and W_h of every layer
-  p.W_t3 = take(use_tf32x3(h) ? (size_t)h.L * 8 * D * D * 4 : 0);
+  // FP32 mode: TF32 high and low parts of W_g, W_h and the three W2 of every layer
+  p.W_t3 = take(use_tf32x3(h) ? t3_weight_floats(h) * 4 : 0);
   p.total = o;
   return p;
 }
@@ -207,19 +247,14 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
   // BF16 mode: the update and node maps run on the tensor cores (gemm_tc.cu)
   const bool use_tc = sizeof(T) == 4 && h.precision == DQ_BF16_MIXED;
   const bool use_t3 = sizeof(T) == 4 && use_tf32x3(h);
-  float* W_t3 = reinterpret_cast<float*>(ws + plan.W_t3);
-  const int64_t DD = (int64_t)h.D * h.D;
-  // layer l: W_g high [3DD], W_g low [3DD], W_h high [DD], W_h low [DD]
-  auto wg_t3 = [&](int l, int part) { return W_t3 + (int64_t)l * 8 * DD + part * 3 * DD; };
-  auto wh_t3 = [&](int l, int part) { return W_t3 + (int64_t)l * 8 * DD + 6 * DD + part * DD; };
+  const T3Weights w3 = t3_weights(h, ws + plan.W_t3);
   if (use_t3) {
-    if constexpr (sizeof(T) == 4) {
-      for (int l = 0; l < h.L; ++l) {
-        DQ_CU(split_tf32(params + h.off.layer[l].W_g, wg_t3(l, 0), wg_t3(l, 1), 3 * DD, s));
-        DQ_CU(split_tf32(params + h.off.layer[l].W_h, wh_t3(l, 0), wh_t3(l, 1), DD, s));
-      }
-    }
+    if constexpr (sizeof(T) == 4) DQ_CU(split_t3_weights(h, params, w3, s));
   }
+  auto wg_t3 = [&](int l, int part) { return w3.wg(l, part); };
+  auto wh_t3 = [&](int l, int part) { return w3.wh(l, part); };
+  auto w2_t3 = [&](int l, int t, int part) { return w3.w2(l, t, part); };
+  auto wo_t3 = [&](int sg, int part) { return w3.wo(sg, part); };
   unsigned char* W_bf = ws + plan.W_bf;
   auto wg_bf = [&](int l) { return W_bf + (size_t)l * 4 * h.D * h.D * 2; };
   auto wh_bf = [&](int l) { return wg_bf(l) + (size_t)3 * h.D * h.D * 2; };
@@ -254,8 +289,19 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
       for (int t = 0; t < 3; ++t) {
         if (ng[t] == 0) continue;
         const RowMap m{(int64_t)ng[t] * ej, (int64_t)E * ej * D, D};
-        DQ_LAUNCH(h, kb + PK_GEMM_EDGE, gemm_nt<T>(bf.eh + (int64_t)e0[t] * ej * D, m, params + y.W2[t], params + y.b2[t], ej,
-                         bf.ew + (int64_t)e0[t] * ej * D, m, nb * ng[t] * ej, D, D, false, s));
+        if (use_t3) {
+          const int64_t seg = (int64_t)E * ej * D;
+          DQ_LAUNCH(h, kb + PK_GEMM_EDGE,
+                    gemm_tf32x3_tc_seg(reinterpret_cast<const float*>(bf.eh) + (int64_t)e0[t] * ej * D,
+                                       (int64_t)ng[t] * ej, nb, seg, D, D, w2_t3(l, t, 0), w2_t3(l, t, 1), D,
+                                       reinterpret_cast<const float*>(params + y.b2[t]), ej,
+                                       reinterpret_cast<float*>(bf.ew) + (int64_t)e0[t] * ej * D, D, seg,
+                                       h.d_status, s));
+        } else {
+          DQ_LAUNCH(h, kb + PK_GEMM_EDGE, gemm_nt<T>(bf.eh + (int64_t)e0[t] * ej * D, m, params + y.W2[t],
+                                                     params + y.b2[t], ej, bf.ew + (int64_t)e0[t] * ej * D, m,
+                                                     nb * ng[t] * ej, D, D, false, s));
+        }
       }
       const RowMap node{(int64_t)N * C, (int64_t)N * C * D, D};
       const int64_t rows = nb * N * C;
@@ -296,8 +342,18 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
       if (ns[sg] == 0) continue;
       const RowMap mx{(int64_t)ns[sg] * C, (int64_t)N * C * D, D};
       const RowMap my{(int64_t)ns[sg] * C, (int64_t)N * C * Wo, Wo};
-      DQ_LAUNCH(h, kb + PK_GEMM_ORBITAL, gemm_nt<T>(bf.F + (int64_t)i0[sg] * C * D, mx, params + h.off.W_o[sg], params + h.off.b_o[sg], C,
-                       bf.phi + (int64_t)i0[sg] * C * Wo, my, nb * ns[sg] * C, K * ns[sg], D, false, s));
+      if (use_t3) {
+        DQ_LAUNCH(h, kb + PK_GEMM_ORBITAL,
+                  gemm_tf32x3_tc_seg(reinterpret_cast<const float*>(bf.F) + (int64_t)i0[sg] * C * D,
+                                     (int64_t)ns[sg] * C, nb, (int64_t)N * C * D, D, D, wo_t3(sg, 0), wo_t3(sg, 1),
+                                     K * ns[sg], reinterpret_cast<const float*>(params + h.off.b_o[sg]), C,
+                                     reinterpret_cast<float*>(bf.phi) + (int64_t)i0[sg] * C * Wo, Wo,
+                                     (int64_t)N * C * Wo, h.d_status, s));
+      } else {
+        DQ_LAUNCH(h, kb + PK_GEMM_ORBITAL,
+                  gemm_nt<T>(bf.F + (int64_t)i0[sg] * C * D, mx, params + h.off.W_o[sg], params + h.off.b_o[sg], C,
+                             bf.phi + (int64_t)i0[sg] * C * Wo, my, nb * ns[sg] * C, K * ns[sg], D, false, s));
+      }
     }
     DQ_LAUNCH(h, kb + PK_ORBITAL_DET, launch_orbital_det<T>(h, d, params, bf, s));
     if (h.use_jastrow) {
@@ -317,7 +373,7 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
 // ---------------------------------------------------------------------------
 struct GradPlan {
   size_t geo, rbf, eh, ew, zl, msg, u, F, phi, det, js, jh, z0;  // saved forward
-  size_t fbar, ubar, mbar, zbar, wbar, hbar, phibar, beta, cbar, jhbar, gt, sbar, envbar, ybar, part;
+  size_t fbar, ubar, mbar, zbar, wbar, hbar, phibar, beta, cbar, jhbar, gt, sbar, envbar, ybar, part, wt3;
   int64_t part_elems;
   size_t total;
 };
@@ -362,6 +418,7 @@ GradPlan plan_grad(const dq_handle_s& h, int64_t Bc, size_t elem) {
   const int64_t blk = std::max({3 * D * D, D * D, D * Q, Wo * D, Wo * M, M * D, K, D});
   p.part_elems = 64 * blk;
   p.part = take(p.part_elems * elem);
+  p.wt3 = take(use_tf32x3(h) ? t3_weight_floats(h) * 4 : 0);
   p.total = o;
   return p;
 }
@@ -382,6 +439,11 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
   const size_t el = sizeof(T);
   DQ_CU(cudaMemsetAsync(G, 0, (size_t)(mode == 1 ? B : 1) * P * el, s));
   T* part = buf(pl.part);
+  const bool use_t3 = sizeof(T) == 4 && use_tf32x3(h);
+  const T3Weights w3 = t3_weights(h, ws + pl.wt3);
+  if (use_t3) {
+    if constexpr (sizeof(T) == 4) DQ_CU(split_t3_weights(h, params, w3, s));
+  }
   const int ns[2] = {h.n_up, h.n_dn}, i0[2] = {0, h.n_up};
   const int e0[3] = {0, h.edges.n_par, h.edges.n_ee};
   const int ng[3] = {h.edges.n_par, h.edges.n_anti, h.edges.n_en};
@@ -422,14 +484,34 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
       for (int t = 0; t < 3; ++t) {
         if (ng[t] == 0) continue;
         const RowMap m{(int64_t)ng[t], (int64_t)E * D, D};
-        DQ_LAUNCH(h, kValueOffset + PK_GEMM_EDGE, gemm_nt<T>(v.eh + (int64_t)e0[t] * D, m, params + y.W2[t], params + y.b2[t], 1,
-                                             v.ew + (int64_t)e0[t] * D, m, nb * ng[t], D, D, false, s));
+        if (use_t3) {
+          DQ_LAUNCH(h, kValueOffset + PK_GEMM_EDGE,
+                    gemm_tf32x3_tc_seg(reinterpret_cast<const float*>(v.eh) + (int64_t)e0[t] * D, ng[t], nb,
+                                       (int64_t)E * D, D, D, w3.w2(l, t, 0), w3.w2(l, t, 1), D,
+                                       reinterpret_cast<const float*>(params + y.b2[t]), 1,
+                                       reinterpret_cast<float*>(v.ew) + (int64_t)e0[t] * D, D, (int64_t)E * D,
+                                       h.d_status, s));
+        } else {
+          DQ_LAUNCH(h, kValueOffset + PK_GEMM_EDGE,
+                    gemm_nt<T>(v.eh + (int64_t)e0[t] * D, m, params + y.W2[t], params + y.b2[t], 1,
+                               v.ew + (int64_t)e0[t] * D, m, nb * ng[t], D, D, false, s));
+        }
       }
-      if (l > 0)
+      if (l > 0 && use_t3)
+        DQ_LAUNCH(h, kValueOffset + PK_GEMM_NODE,
+                  gemm_tf32x3_tc(reinterpret_cast<const float*>(F(l)), nb * N, D, D, w3.wh(l, 0), w3.wh(l, 1), D,
+                                 nullptr, 1, reinterpret_cast<float*>(ZL(l)), D, h.d_status, s));
+      else if (l > 0)
         DQ_LAUNCH(h, kValueOffset + PK_GEMM_NODE, gemm_nt<T>(F(l), rm(D), params + y.W_h, nullptr, 1, ZL(l), rm(D), nb * N, D, D,
                                              false, s));
       DQ_LAUNCH(h, kValueOffset + PK_MESSAGES, launch_messages<T>(h, d, params, l, l == 0, v, s));
-      DQ_LAUNCH(h, kValueOffset + PK_GEMM_UPDATE, gemm_nt<T>(MS(l), rm(3 * D), params + y.W_g, params + y.b_g, 1, U(l), rm(D), nb * N,
+      if (use_t3)
+        DQ_LAUNCH(h, kValueOffset + PK_GEMM_UPDATE,
+                  gemm_tf32x3_tc(reinterpret_cast<const float*>(MS(l)), nb * N, 3 * D, 3 * D, w3.wg(l, 0),
+                                 w3.wg(l, 1), D, reinterpret_cast<const float*>(params + y.b_g), 1,
+                                 reinterpret_cast<float*>(U(l)), D, h.d_status, s));
+      else
+        DQ_LAUNCH(h, kValueOffset + PK_GEMM_UPDATE, gemm_nt<T>(MS(l), rm(3 * D), params + y.W_g, params + y.b_g, 1, U(l), rm(D), nb * N,
                                            D, 3 * D, false, s));
       DQ_LAUNCH(h, kValueOffset + PK_UPDATE, launch_update_io<T>(h, d, params, l == 0, U(l), F(l), F(l + 1), s));
     }
@@ -438,7 +520,15 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
       if (ns[sg] == 0) continue;
       const RowMap mx{(int64_t)ns[sg], (int64_t)N * D, D};
       const RowMap my{(int64_t)ns[sg], (int64_t)N * Wo, Wo};
-      DQ_LAUNCH(h, kValueOffset + PK_GEMM_ORBITAL, gemm_nt<T>(F(L) + (int64_t)i0[sg] * D, mx, params + off.W_o[sg], params + off.b_o[sg],
+      if (use_t3)
+        DQ_LAUNCH(h, kValueOffset + PK_GEMM_ORBITAL,
+                  gemm_tf32x3_tc_seg(reinterpret_cast<const float*>(F(L)) + (int64_t)i0[sg] * D, ns[sg], nb,
+                                     (int64_t)N * D, D, D, w3.wo(sg, 0), w3.wo(sg, 1), K * ns[sg],
+                                     reinterpret_cast<const float*>(params + off.b_o[sg]), 1,
+                                     reinterpret_cast<float*>(v.phi) + (int64_t)i0[sg] * Wo, Wo, (int64_t)N * Wo,
+                                     h.d_status, s));
+      else
+        DQ_LAUNCH(h, kValueOffset + PK_GEMM_ORBITAL, gemm_nt<T>(F(L) + (int64_t)i0[sg] * D, mx, params + off.W_o[sg], params + off.b_o[sg],
                                            1, v.phi + (int64_t)i0[sg] * Wo, my, nb * ns[sg], K * ns[sg], D, false, s));
     }
     DQ_LAUNCH(h, kValueOffset + PK_ORBITAL_DET, launch_orbital_det<T>(h, d, params, v, s));

@@ -120,6 +120,13 @@ cudaError_t split_tf32(const float* W, float* big, float* small, int64_t n, cuda
 cudaError_t gemm_tf32x3_tc(const float* X, int64_t rows, int K, int64_t ldx, const float* Wbig, const float* Wsmall,
                            int n_out, const float* bias, int bias_period, float* Y, int64_t ldy, unsigned int* status,
                            cudaStream_t s);
+// Rows in n_seg segments of seg_rows rows (segment g starts at X + g * x_seg_stride
+// and Y + g * y_seg_stride; x_seg_stride % 4 == 0); the bias goes on the rows
+// whose index within the segment is a multiple of bias_period.
+cudaError_t gemm_tf32x3_tc_seg(const float* X, int64_t seg_rows, int64_t n_seg, int64_t x_seg_stride, int K,
+                               int64_t ldx, const float* Wbig, const float* Wsmall, int n_out, const float* bias,
+                               int bias_period, float* Y, int64_t ldy, int64_t y_seg_stride, unsigned int* status,
+                               cudaStream_t s);
 
 // ---- forward kernels (forward.cu) ------------------------------------------
 // Sizes of one chunk of Bc walkers; C = channels (1 value-only, 3N+2 with jets).

@@ -182,20 +182,22 @@ constexpr int kMsgLanes = 32;
 
 // Shared-memory layout of the jet message kernel (element offsets in T).
 struct MsgSmem {
-  int w0, w1, us, invd, z0c, sp, ps, total_bytes;
+  int w0, w1, w2, us, invd, z0c, zself, sp, ps, total_bytes;
 };
 template <class T>
-__host__ __device__ inline MsgSmem msg_smem_layout(int N, int IB, bool stage_w1) {
+__host__ __device__ inline MsgSmem msg_smem_layout(int N, int IB, bool stage_w12) {
   MsgSmem m{};
   int o = 0;
   const int rows = N * N + IB;  // padded: receivers past the end read zeros
   m.w0 = o; o += rows * kMsgLanes;
-  m.w1 = o; o += stage_w1 ? rows * kMsgLanes : 0;
+  m.w1 = o; o += stage_w12 ? rows * kMsgLanes : 0;
+  m.w2 = o; o += stage_w12 ? N * N * kMsgLanes : 0;
   m.us = o; o += (N + IB) * N * 3;  // u_ij,x (zero diagonal, zero padding)
   m.invd = o; o += N * N;
-  m.z0c = o; o += N * kMsgLanes;   // z_j[0]
-  m.sp = o; o += 13 * N * kMsgLanes;  // (b) [N][3 x][3], (c) [N][3], (d) [N]
-  m.ps = o * (int)sizeof(T);       // byte offset of the int pair table
+  m.z0c = o; o += N * kMsgLanes;       // z_j[0]
+  m.zself = o; o += 3 * N * kMsgLanes;  // dz_j / dr_j,x
+  m.sp = o; o += 13 * N * kMsgLanes;   // (b) [N][3 x][3], (c) [N][3], (d) [N]
+  m.ps = o * (int)sizeof(T);           // byte offset of the int pair table
   m.total_bytes = m.ps + N * N * (int)sizeof(int);
   return m;
 }
@@ -204,22 +206,24 @@ template <class T, class TO, int IB, int CB>
 __global__ void __launch_bounds__(256, 2)
     messages_kernel(const T* __restrict__ Z, const T* __restrict__ z0, const T* __restrict__ ew,
                     const T* __restrict__ geo, const T* __restrict__ Y, const int* __restrict__ pair_of, int N,
-                    int n_up, int M, int C, int D, int E, int n_ee, int z_const, int stage_w1,
+                    int n_up, int M, int C, int D, int E, int n_ee, int z_const, int stage_w12,
                     TO* __restrict__ msg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int L = kMsgLanes, ej = 3;
-  const MsgSmem lay = msg_smem_layout<T>(N, IB, stage_w1 != 0);
+  const MsgSmem lay = msg_smem_layout<T>(N, IB, stage_w12 != 0);
   T* sm = reinterpret_cast<T*>(smem_raw);
-  T* W0 = sm + lay.w0;  // [(j*N + i)][L]
-  T* W1 = sm + lay.w1;
+  T* W0 = sm + lay.w0;  // [(j*N + i)][L]  w_ij
+  T* W1 = sm + lay.w1;  //                 w'_ij
+  T* W2 = sm + lay.w2;  //                 w''_ij
   T* Us = sm + lay.us;  // [(i*N + j)][3]
   T* Id = sm + lay.invd;
   T* Z0c = sm + lay.z0c;  // [j][L]
+  T* Zsf = sm + lay.zself;  // [j][x][L]
   T* SP = sm + lay.sp;
   int* Ps = reinterpret_cast<int*>(smem_raw + lay.ps);
-  T* SPb = SP;                      // [i][x][3]  (same, opposite, nucleus)
-  T* SPc = SP + 9 * N * L;          // [i][3]
-  T* SPd = SP + 12 * N * L;         // [i]
+  T* SPb = SP;               // [i][x][3]  (same, opposite, nucleus)
+  T* SPc = SP + 9 * N * L;   // [i][3]
+  T* SPd = SP + 12 * N * L;  // [i]
 
   const int64_t b = blockIdx.x;
   const int d0 = blockIdx.y * L;
@@ -229,6 +233,13 @@ __global__ void __launch_bounds__(256, 2)
   const T* Yd = Y + d0 + lane;
   const T* Gb = geo + b * E * 4;
   const int NN = N * N;
+
+  // Pull this CTA's slices of the node channels and edge filters into L2.
+  if (!z_const)
+    for (int r = tid; r < N * C; r += blockDim.x)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(Z + (b * N * C + r) * D + d0));
+  for (int r = tid; r < E * ej; r += blockDim.x)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ew + (b * E * ej + r) * D + d0));
 
   // ---- staging ----
   for (int k = tid; k < NN; k += blockDim.x) {
@@ -250,65 +261,73 @@ __global__ void __launch_bounds__(256, 2)
   }
   for (int k = tid; k < IB * N * 3; k += blockDim.x) Us[NN * 3 + k] = T(0);
   for (int r = grp; r < NN + IB; r += ngroups) {
-    T v0 = 0, v1 = 0;
+    T v0 = 0, v1 = 0, v2 = 0;
     if (r < NN) {
       const int j = r / N, i = r - (r / N) * N;
       if (i != j) {
         const T* w = EWb + (int64_t)pair_of[r] * ej * D;
         v0 = w[0];
         v1 = w[D];
+        v2 = w[2 * D];
       }
     }
     W0[r * L + lane] = v0;
-    if (stage_w1) W1[r * L + lane] = v1;
+    if (stage_w12) {
+      W1[r * L + lane] = v1;
+      if (r < NN) W2[r * L + lane] = v2;
+    }
   }
-  for (int j = grp; j < N; j += ngroups)
-    Z0c[j * L + lane] = z_const ? z0[(j < n_up ? 0 : D) + d0 + lane] : Zb[(int64_t)j * C * D];
+  for (int j = grp; j < N; j += ngroups) {
+    const T* zj = Zb + (int64_t)j * C * D;
+    Z0c[j * L + lane] = z_const ? z0[(j < n_up ? 0 : D) + d0 + lane] : zj[0];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) Zsf[(j * 3 + x) * L + lane] = z_const ? T(0) : zj[(int64_t)(1 + 3 * j + x) * D];
+  }
   __syncthreads();
-
-  // w'_ij of this lane (i != j)
+  // w' and w'' of the edge (i, j) for this lane (zero on the diagonal)
   auto w1_at = [&](int i, int j) -> T {
-    if (stage_w1) return W1[(j * N + i) * L + lane];
-    return EWb[((int64_t)Ps[i * N + j] * ej + 1) * D];
+    if (stage_w12) return W1[(j * N + i) * L + lane];
+    return i == j ? T(0) : EWb[((int64_t)Ps[i * N + j] * ej + 1) * D];
+  };
+  auto w2_at = [&](int i, int j) -> T {
+    if (stage_w12) return W2[(j * N + i) * L + lane];
+    return i == j ? T(0) : EWb[((int64_t)Ps[i * N + j] * ej + 2) * D];
   };
 
   // ---- phase 1: per-receiver terms (b), (c), (d) ----
-  const int n_items = 5 * N;  // 3N of kind (b), N of (c), N of (d)
-  for (int it = grp; it < n_items; it += ngroups) {
+  const int n_dn = N - n_up;
+  for (int it = grp; it < 5 * N; it += ngroups) {
     if (it < 3 * N) {  // (b) receiver i, axis x
       const int i = it / 3, x = it - (it / 3) * 3;
       const bool up = i < n_up;
-      T ss = 0, so = 0, sn = 0;
-      for (int j = 0; j < N; ++j) {
-        if (j == i) continue;
-        const T t = w1_at(i, j) * Us[(i * N + j) * 3 + x] * Z0c[j * L + lane];
-        if ((j < n_up) == up) ss += t; else so += t;
-      }
+      T sa = 0, sb = 0, sn = 0;  // spin up senders, spin down senders
+      for (int j = 0; j < n_up; ++j) sa += w1_at(i, j) * Us[(i * N + j) * 3 + x] * Z0c[j * L + lane];
+      for (int j = n_up; j < N; ++j) sb += w1_at(i, j) * Us[(i * N + j) * 3 + x] * Z0c[j * L + lane];
       for (int I = 0; I < M; ++I) {
         const int en = i * M + I;
         sn += EWb[((int64_t)(n_ee + en) * ej + 1) * D] * Gb[(n_ee + en) * 4 + 1 + x] * Yd[(int64_t)I * D];
       }
       T* o = SPb + (i * 3 + x) * 3 * L + lane;
-      o[0] = ss;
-      o[L] = so;
+      o[0] = up ? sa : sb;
+      o[L] = up ? sb : sa;
       o[2 * L] = sn;
     } else if (it < 4 * N) {  // (c) Laplacian channel of receiver i
       const int i = it - 3 * N;
       const bool up = i < n_up;
-      T ss = 0, so = 0, sn = 0;
+      const T* zc = Zb + (int64_t)(1 + 3 * i) * D;  // dz_j / dr_i of sender j at zc + j * C * D
+      T sa = 0, sb = 0, sn = 0;
+#pragma unroll 2
       for (int j = 0; j < N; ++j) {
-        if (j == i) continue;
         const T v1 = w1_at(i, j);
-        const T v2 = EWb[((int64_t)Ps[i * N + j] * ej + 2) * D];
-        T t = (T(2) * v2 + T(4) * v1 * Id[i * N + j]) * Z0c[j * L + lane];
+        T t = (T(2) * w2_at(i, j) + T(4) * v1 * Id[i * N + j]) * Z0c[j * L + lane];
         if (!z_const) {
-          const T* zj = Zb + (int64_t)j * C * D;
           const T* u = Us + (i * N + j) * 3;
-          T cr = 0;
-          for (int x = 0; x < 3; ++x) cr += u[x] * (zj[(int64_t)(1 + 3 * i + x) * D] - zj[(int64_t)(1 + 3 * j + x) * D]);
+          const T* zj = zc + (int64_t)j * C * D;
+          const T cr = u[0] * (zj[0] - Zsf[(j * 3) * L + lane]) + u[1] * (zj[D] - Zsf[(j * 3 + 1) * L + lane]) +
+                       u[2] * (zj[2 * D] - Zsf[(j * 3 + 2) * L + lane]);
           t += T(2) * v1 * cr;
         }
-        if ((j < n_up) == up) ss += t; else so += t;
+        if (j < n_up) sa += t; else sb += t;
       }
       for (int I = 0; I < M; ++I) {
         const int en = i * M + I;
@@ -316,8 +335,8 @@ __global__ void __launch_bounds__(256, 2)
         sn += (w[2 * D] + T(2) * w[D] / Gb[(n_ee + en) * 4]) * Yd[(int64_t)I * D];
       }
       T* o = SPc + i * 3 * L + lane;
-      o[0] = ss;
-      o[L] = so;
+      o[0] = up ? sa : sb;
+      o[L] = up ? sb : sa;
       o[2 * L] = sn;
     } else {  // (d) value channel, nuclei
       const int i = it - 4 * N;
@@ -328,13 +347,24 @@ __global__ void __launch_bounds__(256, 2)
   }
   __syncthreads();
 
+  TO* mb = msg + b * N * C * 3 * D + d0 + lane;
+  // electron-nucleus part of every output (nonzero in the value, Laplacian and own-coordinate channels)
+  const T nuM = T(1) / T(M);
+  for (int i = grp; i < N; i += ngroups) {
+    TO* o = mb + (int64_t)i * C * 3 * D + 2 * D;
+    for (int c = 0; c < C; ++c) {
+      T v = 0;
+      if (c == 0) v = SPd[i * L + lane];
+      else if (c == C - 1) v = SPc[(i * 3 + 2) * L + lane];
+      else if ((c - 1) / 3 == i) v = SPb[((i * 3 + (c - 1) % 3) * 3 + 2) * L + lane];
+      o[(int64_t)c * 3 * D] = to_out(v * nuM, o);
+    }
+  }
+
   // ---- phase 2: main contraction ----
-  const int n_dn = N - n_up;
   const int nib_up = (n_up + IB - 1) / IB, nib_dn = (n_dn + IB - 1) / IB;
   const int ncb = (C + CB - 1) / CB;
   const int ntasks = (nib_up + nib_dn) * ncb;
-  const T nuM = T(1) / T(M);
-  TO* mb = msg + b * N * C * 3 * D + d0 + lane;
   const int CD = C * D;
   for (int task = grp; task < ntasks; task += ngroups) {
     const int ibk = task / ncb, cbk = task - (task / ncb) * ncb;
@@ -345,6 +375,7 @@ __global__ void __launch_bounds__(256, 2)
     const int c0 = cbk * CB;
     const int nc = min(CB, C - c0);
     const int os0 = up ? n_up : 0, osn = up ? n_dn : n_up;  // opposite spin block (senders)
+    const int qlap = c0 + nc == C ? C - 1 - c0 : -1;
     int eq[CB], xq[CB];  // electron / axis of the coordinate channels (-1: none)
 #pragma unroll
     for (int q = 0; q < CB; ++q) {
@@ -388,45 +419,41 @@ __global__ void __launch_bounds__(256, 2)
           wp += N * L;
         }
       }
-      // (a): channels holding a coordinate of a sender of this pass
 #pragma unroll
       for (int q = 0; q < CB; ++q) {
         const int e = eq[q];
-        if (e < j0 || e >= j0 + jn) continue;
-        const T ze0 = Z0c[e * L + lane];
-        const T* ue = Us + (i0 * N + e) * 3 + xq[q];
+        // (a): the channel holds a coordinate of a sender of this pass
+        if (e >= j0 && e < j0 + jn) {
+          const T ze0 = Z0c[e * L + lane];
+          const T* ue = Us + (i0 * N + e) * 3 + xq[q];
 #pragma unroll
-        for (int a = 0; a < IB; ++a) {
-          const int i = i0 + a;
-          if (a < ni && i != e) acc[a][q] -= w1_at(i, e) * ue[a * N * 3] * ze0;
+          for (int a = 0; a < IB; ++a)
+            if (a < ni) acc[a][q] -= w1_at(i0 + a, e) * ue[a * N * 3] * ze0;
+        }
+        // (b): the channel holds a coordinate of a receiver of this block
+        if (e >= i0 && e < i0 + ni) {
+          const T v = SPb[((e * 3 + xq[q]) * 3 + pass) * L + lane];
+#pragma unroll
+          for (int a = 0; a < IB; ++a)
+            if (i0 + a == e) acc[a][q] += v;
+        }
+        // (c): Laplacian channel
+        if (q == qlap) {
+#pragma unroll
+          for (int a = 0; a < IB; ++a)
+            if (a < ni) acc[a][q] += SPc[((i0 + a) * 3 + pass) * L + lane];
         }
       }
       const T nu = T(1) / T(pass == 0 ? (sbn - 1 > 1 ? sbn - 1 : 1) : (osn > 1 ? osn : 1));
+      TO* ob = mb + ((int64_t)i0 * C + c0) * 3 * D + pass * D;
 #pragma unroll
       for (int a = 0; a < IB; ++a) {
         if (a >= ni) continue;
-        const int i = i0 + a;
 #pragma unroll
         for (int q = 0; q < CB; ++q) {
           if (q >= nc) continue;
-          const int c = c0 + q;
-          const T* sp = nullptr;  // phase-1 terms of this output
-          T nuc = 0;
-          if (c == 0) {
-            nuc = SPd[i * L + lane];
-          } else if (c == C - 1) {
-            sp = SPc + i * 3 * L + lane;
-          } else if (eq[q] == i) {
-            sp = SPb + (i * 3 + xq[q]) * 3 * L + lane;
-          }
-          T v = acc[a][q];
-          if (sp) {
-            v += sp[pass * L];
-            nuc = sp[2 * L];
-          }
-          TO* out = mb + ((int64_t)i * C + c) * 3 * D;
-          out[pass * D] = to_out(v * nu, out);
-          if (pass == 1) out[2 * D] = to_out(nuc * nuM, out);
+          TO* o = ob + ((int64_t)a * C + q) * 3 * D;
+          *o = to_out(acc[a][q] * nu, o);
         }
       }
     }
@@ -806,6 +833,274 @@ __global__ void __launch_bounds__(128)
   if (lane == 0) out[2 + N3] = lap;
 }
 
+// ---------------------------------------------------------------------------
+// Determinant jets of the FP32 modes for spin blocks of at most kDetNR
+// electrons, one warp per matrix, on the FP32 pipes:
+//  * LU of A (FP32 entries, exact) with partial pivoting in FP32 and the
+//    inverse X0 from it;
+//  * one step of inverse refinement, X = X0 + X0 (I - A X0), with the
+//    residual as a compensated dot product (Ogita-Rump-Oishi Dot2), kept as a
+//    double-float pair Xhi + Xlo (error about (kappa u)^2 |A^-1|);
+//  * log|det A| = log|det LU| + tr(X P^T (P A - L U)), the first-order
+//    correction for the backward error of the FP32 factorisation;
+//  * the 3N + 1 tangents X_t = A^-1 d_t A as compensated dot products with
+//    the rows of Xhi / Xlo in registers; tr X_t from the diagonal in
+//    double-float, sum_t tr(X_t^2) accumulated per lane and reduced once.
+// Matrices whose row-equilibrated condition estimate exceeds
+// DQ_KAPPA_FP32_JET (or whose FP32 LU meets a zero pivot) take the FP64 LU
+// and inverse instead and are counted in n_fp64.
+// ---------------------------------------------------------------------------
+#ifndef DQ_KAPPA_FP32_JET
+#define DQ_KAPPA_FP32_JET 2000.0f
+#endif
+constexpr int kDetNR = 8;
+
+// sum_l a[l] b[l] as a double-float pair (Dot2)
+__device__ __forceinline__ dfloat dot2_step(dfloat acc, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const dfloat s = two_sum(acc.hi, p);
+  return {s.hi, __fadd_rn(acc.lo, __fadd_rn(s.lo, e))};
+}
+
+__host__ __device__ inline size_t det_jets_smem_per_warp(int nmax, int N3) {
+  const size_t nn = (size_t)nmax * nmax;
+  const size_t fl = nn * (14 + 4) + (size_t)(N3 + 1) * nmax * 2;  // float arrays
+  const size_t bytes = fl * 4 + 2 * nn * 8 + 32 * 4;
+  return (bytes + 15) / 16 * 16;
+}
+
+__global__ void __launch_bounds__(128)
+    orbital_det_jets_kernel(const float* __restrict__ phi, const float* __restrict__ geo,
+                            const float* __restrict__ params, int64_t Bc, int N, int n_up, int M, int K, int C,
+                            int Wo, int E, int n_ee, int64_t om_up, int64_t om_dn, int64_t ze_up, int64_t ze_dn,
+                            double* __restrict__ det, unsigned long long* __restrict__ n_fp64) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int warps = blockDim.x / 32;
+  const int64_t gw = (int64_t)blockIdx.x * warps + warp;
+  const int n_dn = N - n_up;
+  const int nmax = n_up > n_dn ? n_up : n_dn;
+  const int N3 = 3 * N;
+  const int nn = nmax * nmax;
+  unsigned char* base = smem_raw + warp * det_jets_smem_per_warp(nmax, N3);
+  double* LUd = reinterpret_cast<double*>(base);  // FP64 fallback
+  double* Ainvd = LUd + nn;
+  float* A = reinterpret_cast<float*>(Ainvd + nn);
+  float* LU = A + nn;
+  float* X0 = LU + nn;
+  float* Xhi = X0 + nn;
+  float* Xlo = Xhi + nn;
+  float* tmp = Xlo + nn;
+  float* Th = tmp + nn;   // [2][nn] double-buffered X_t, high part
+  float* Tl = Th + 2 * nn;  // [2][nn] low part
+  float* env = Tl + 2 * nn;
+  float* jenv = env + nn;  // [3][nn]
+  float* lenv = jenv + 3 * nn;
+  float* phi0 = lenv + nn;
+  float* rmax = phi0 + nn;   // [nmax] row maxima of A (nn reserved)
+  float* DG = rmax + nn;     // [N3 + 1][nmax][2] diagonals of X_t
+  int* perm = reinterpret_cast<int*>(DG + (N3 + 1) * nmax * 2);
+
+  if (gw >= Bc * 2 * K) return;
+  const int64_t b = gw / (2 * K);
+  const int s = (int)((gw / K) % 2);
+  const int p = (int)(gw % K);
+  const int n = s == 0 ? n_up : n_dn;
+  const int i0 = s == 0 ? 0 : n_up;
+  double* out = det + gw * (N3 + 3);
+  if (n == 0) {  // empty determinant = 1
+    for (int k = lane; k < N3 + 3; k += 32) out[k] = k == 0 ? 1.0 : 0.0;
+    return;
+  }
+  const float* om = params + (s == 0 ? om_up : om_dn);
+  const float* ze = params + (s == 0 ? ze_up : ze_dn);
+  const float* phib = phi + b * N * C * Wo;
+  const float* gb = geo + b * E * 4;
+  const int nsq = n * n;
+
+  // Envelopes (Eq. 20) with their derivatives in the coordinates of electron i.
+  for (int q = lane; q < nsq; q += 32) {
+    const int ii = q / n, k = q - (q / n) * n, o = p * n + k, i = i0 + ii;
+    float ev = 0, j0 = 0, j1 = 0, j2 = 0, lv = 0;
+    for (int I = 0; I < M; ++I) {
+      const float* g = gb + (n_ee + i * M + I) * 4;
+      const float z = ze[o * M + I];
+      const float w = om[o * M + I] * expf(-z * g[0]);
+      ev += w;
+      j0 -= w * z * g[1];
+      j1 -= w * z * g[2];
+      j2 -= w * z * g[3];
+      lv += w * (z * z - 2.f * z / g[0]);
+    }
+    env[q] = ev;
+    jenv[q] = j0;
+    jenv[nn + q] = j1;
+    jenv[2 * nn + q] = j2;
+    lenv[q] = lv;
+    const float f0 = phib[(int64_t)i * C * Wo + o];
+    phi0[q] = f0;
+    A[q] = f0 * ev;
+    LU[q] = f0 * ev;
+  }
+  __syncwarp();
+  if (lane < n) {
+    float m = 0;
+    for (int k = 0; k < n; ++k) m = fmaxf(m, fabsf(A[lane * n + k]));
+    rmax[lane] = m;
+  }
+  __syncwarp();
+
+  int sign = 0;
+  double logabs = -INFINITY;
+  bool fp64 = !warp_lu<float>(LU, perm, n, lane, &sign, &logabs);
+  if (!fp64) {
+    warp_inverse<float>(LU, perm, n, lane, X0);
+    float imax = 0;
+    for (int q = lane; q < nsq; q += 32) imax = fmaxf(imax, fabsf(X0[q]) * rmax[q - (q / n) * n]);
+    const float kappa = float(n) * warp_max(imax);
+    fp64 = !(kappa <= DQ_KAPPA_FP32_JET);
+  }
+  if (!fp64) {
+    // residual R = I - A X0 into tmp
+    for (int q = lane; q < nsq; q += 32) {
+      const int a = q / n, m = q - (q / n) * n;
+      dfloat acc = {a == m ? -1.f : 0.f, 0.f};
+      for (int l = 0; l < n; ++l) acc = dot2_step(acc, A[a * n + l], X0[l * n + m]);
+      tmp[q] = -(acc.hi + acc.lo);
+    }
+    __syncwarp();
+    // X = X0 + X0 R as a double-float pair
+    for (int q = lane; q < nsq; q += 32) {
+      const int a = q / n, m = q - (q / n) * n;
+      float c = 0.f;
+      for (int l = 0; l < n; ++l) c = fmaf(X0[a * n + l], tmp[l * n + m], c);
+      const dfloat x = two_sum(X0[q], c);
+      Xhi[q] = x.hi;
+      Xlo[q] = x.lo;
+    }
+    __syncwarp();
+    // log|det A| = log|det LU| + tr(X P^T (P A - L U)); entry (r, c) of P A - L U
+    // pairs with X[c][perm[r]].
+    float part = 0.f;
+    for (int q = lane; q < nsq; q += 32) {
+      const int r = q / n, c = q - (q / n) * n;
+      const int mm = r < c ? r : c;
+      dfloat acc = {-A[perm[r] * n + c], 0.f};
+      for (int m = 0; m <= mm; ++m) acc = dot2_step(acc, m == r ? 1.f : LU[r * n + m], LU[m * n + c]);
+      part = fmaf(Xhi[c * n + perm[r]], -(acc.hi + acc.lo), part);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    logabs += (double)part;
+  } else {
+    if (lane == 0) atomicAdd(n_fp64, 1ull);
+    for (int q = lane; q < nsq; q += 32) LUd[q] = (double)A[q];
+    __syncwarp();
+    if (!warp_lu<double>(LUd, perm, n, lane, &sign, &logabs)) {
+      for (int k = lane; k < N3 + 3; k += 32) out[k] = k == 1 ? -INFINITY : 0.0;
+      return;
+    }
+    warp_inverse<double>(LUd, perm, n, lane, Ainvd);
+    for (int q = lane; q < nsq; q += 32) {
+      const double a = Ainvd[q];
+      const float h = (float)a;
+      Xhi[q] = h;
+      Xlo[q] = (float)(a - (double)h);
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    out[0] = (double)sign;
+    out[1] = logabs;
+  }
+
+  // ---- tangents ----
+  // entries owned by this lane: q = lane and lane + 32 (n <= kDetNR)
+  int qa[2], ra[2], ma[2];
+  float ah[2][kDetNR], al[2][kDetNR];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int q = lane + 32 * r;
+    qa[r] = q < nsq ? q : -1;
+    ra[r] = q < nsq ? q / n : 0;
+    ma[r] = q < nsq ? q - (q / n) * n : 0;
+#pragma unroll
+    for (int l = 0; l < kDetNR; ++l) {
+      ah[r][l] = l < n && q < nsq ? Xhi[ra[r] * n + l] : 0.f;
+      al[r][l] = l < n && q < nsq ? Xlo[ra[r] * n + l] : 0.f;
+    }
+  }
+  dfloat s2 = {0.f, 0.f};
+  for (int t = 0; t <= N3; ++t) {
+    const bool is_lap = t == N3;
+    const int c = is_lap ? C - 1 : 1 + t;
+    const int te = t / 3, tx = t - (t / 3) * 3;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      if (qa[r] < 0) continue;
+      const int q = qa[r], ii = ra[r], k = ma[r], i = i0 + ii, o = p * n + k;
+      const float* ph = phib + (int64_t)i * C * Wo + o;
+      float v = ph[(int64_t)c * Wo] * env[q];
+      if (is_lap) {
+        v += phi0[q] * lenv[q];
+        for (int x = 0; x < 3; ++x) v += 2.f * ph[(int64_t)(1 + 3 * i + x) * Wo] * jenv[x * nn + q];
+      } else if (te == i) {
+        v += phi0[q] * jenv[tx * nn + q];
+      }
+      tmp[q] = v;
+    }
+    __syncwarp();
+    float* th = Th + (t & 1) * nn;
+    float* tl = Tl + (t & 1) * nn;
+    dfloat xv[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      xv[r] = {0.f, 0.f};
+      if (qa[r] < 0) continue;
+      const int m = ma[r];
+      dfloat acc = {0.f, 0.f};
+      float cl = 0.f;
+#pragma unroll
+      for (int l = 0; l < kDetNR; ++l) {
+        if (l < n) {
+          const float y = tmp[l * n + m];
+          acc = dot2_step(acc, ah[r][l], y);
+          cl = fmaf(al[r][l], y, cl);
+        }
+      }
+      const dfloat x = quick_two_sum(acc.hi, __fadd_rn(acc.lo, cl));
+      xv[r] = x;
+      if (ra[r] == m) {
+        DG[(t * nmax + m) * 2] = x.hi;
+        DG[(t * nmax + m) * 2 + 1] = x.lo;
+      }
+      if (!is_lap) {
+        th[qa[r]] = x.hi;
+        tl[qa[r]] = x.lo;
+      }
+    }
+    __syncwarp();
+    if (!is_lap) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (qa[r] < 0) continue;
+        const int tq = ma[r] * n + ra[r];  // transposed entry
+        s2 = df_add(s2, df_mul(xv[r], {th[tq], tl[tq]}));
+      }
+    }
+  }
+  const dfloat s2s = warp_sum_df(s2);
+  __syncwarp();
+  for (int t = lane; t <= N3; t += 32) {
+    dfloat tr = {0.f, 0.f};
+    for (int a = 0; a < n; ++a) tr = df_add(tr, {DG[(t * nmax + a) * 2], DG[(t * nmax + a) * 2 + 1]});
+    const double v = (double)tr.hi + (double)tr.lo;
+    if (t < N3) out[2 + t] = v;
+    else out[2 + N3] = v - ((double)s2s.hi + (double)s2s.lo);
+  }
+}
+
 // Sum of embeddings over electrons, the input of the Jastrow factor (Eq. 24).
 template <class T>
 __global__ void jastrow_sum_kernel(const T* __restrict__ F, int64_t Bc, int N, int C, int D, T* __restrict__ js) {
@@ -1061,18 +1356,18 @@ cudaError_t launch_messages_t(const dq_handle_s& h, const FwdDims& d, const T* p
   if (d.D % kMsgLanes) return cudaErrorInvalidConfiguration;
   constexpr int IB = msg_ib<T>(), CB = sizeof(T) == 4 ? 4 : 2;
   auto kern = messages_kernel<T, TO, IB, CB>;
-  bool stage_w1 = true;
-  MsgSmem lay = msg_smem_layout<T>(d.N, IB, stage_w1);
-  if (lay.total_bytes > 200 * 1024) {
-    stage_w1 = false;
-    lay = msg_smem_layout<T>(d.N, IB, stage_w1);
+  bool stage_w12 = true;
+  MsgSmem lay = msg_smem_layout<T>(d.N, IB, stage_w12);
+  if (lay.total_bytes > 112 * 1024) {  // keep two CTAs per SM, else fetch w', w'' from global memory
+    stage_w12 = false;
+    lay = msg_smem_layout<T>(d.N, IB, stage_w12);
   }
   if (lay.total_bytes > 220 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total_bytes);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)d.Bc, d.D / kMsgLanes);
   kern<<<grid, 256, lay.total_bytes, s>>>(b.Z, b.z0, b.ew, b.geo, Y, h.d_pair_of, d.N, d.n_up, d.M, d.C, d.D,
-                                          h.edges.n_all, h.edges.n_ee, z_const ? 1 : 0, stage_w1 ? 1 : 0, out);
+                                          h.edges.n_all, h.edges.n_ee, z_const ? 1 : 0, stage_w12 ? 1 : 0, out);
   return cudaGetLastError();
 }
 }  // namespace
@@ -1113,6 +1408,19 @@ cudaError_t launch_orbital_det(const dq_handle_s& h, const FwdDims& d, const T* 
                                cudaStream_t s) {
   const int nmax = d.n_up > d.n_dn ? d.n_up : d.n_dn;
   const int nn = nmax * nmax;
+  if constexpr (sizeof(T) == 4) {
+    if (d.C > 1 && nmax <= kDetNR) {
+      const size_t smem = det_jets_smem_per_warp(nmax, 3 * d.N) * 4;
+      cudaError_t e = cudaFuncSetAttribute(orbital_det_jets_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return e;
+      const int64_t nmat = d.Bc * 2 * d.K;
+      orbital_det_jets_kernel<<<blocks(nmat, 4), 128, smem, s>>>(
+          b.phi, b.geo, params, d.Bc, d.N, d.n_up, d.M, d.K, d.C, d.K * nmax, h.edges.n_all, h.edges.n_ee,
+          h.off.omega[0], h.off.omega[1], h.off.zeta[0], h.off.zeta[1], b.det, h.d_fp64_count);
+      return cudaGetLastError();
+    }
+  }
   const size_t per_warp = ((size_t)nn * (3 * sizeof(double) + 10 * sizeof(T)) + 32 * sizeof(int) + 15) / 16 * 16;
   const int warps = per_warp * 4 <= 200 * 1024 ? 4 : 1;
   const size_t smem = per_warp * warps;

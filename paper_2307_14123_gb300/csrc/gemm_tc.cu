@@ -59,6 +59,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (clock64() - t0 > kWaitCycles) return false;
   }
 }
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -115,6 +122,31 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 // columns): the MMA warp fills one while the epilogue warps drain the other
 // (acc_full / acc_empty mbarriers), so the epilogue of a tile overlaps the
 // loads and MMAs of the next.
+// Epilogue store of a 32 x 32 FP32 block that a warp holds one row per lane
+// (after tmem_ld32: lane t has row t, columns 0..31), through a padded
+// shared-memory transpose so that every store instruction writes 32
+// consecutive columns of one row (one full 128-byte line).  my_row: this
+// lane's destination row pointer at the block's first column (nullptr: row
+// outside the output); my_bias: that row takes the bias; bn: the bias of this
+// lane's column; col_ok: this lane's column is inside the output.
+__device__ __forceinline__ void store_block_32x32(const uint32_t (&v)[32], float (*st)[33], int lane, float* my_row,
+                                                  bool my_bias, float bn, bool col_ok) {
+#pragma unroll
+  for (int j = 0; j < 32; ++j) st[lane][j] = __uint_as_float(v[j]);
+  __syncwarp();
+  const unsigned long long pr = reinterpret_cast<unsigned long long>(my_row);
+  const uint32_t plo = (uint32_t)pr, phi = (uint32_t)(pr >> 32), fb = my_bias ? 1u : 0u;
+#pragma unroll 4
+  for (int rr = 0; rr < 32; ++rr) {
+    const uint32_t lo = __shfl_sync(0xffffffffu, plo, rr), hi = __shfl_sync(0xffffffffu, phi, rr);
+    const uint32_t b = __shfl_sync(0xffffffffu, fb, rr);
+    float* y = reinterpret_cast<float*>(((unsigned long long)hi << 32) | lo);
+    const float val = st[rr][lane] + (b ? bn : 0.f);
+    if (y != nullptr && col_ok) y[lane] = val;
+  }
+  __syncwarp();
+}
+
 constexpr int TC_THREADS = 192;
 constexpr uint32_t TC_TMEM_ALLOC = 2 * TC_TMEM_COLS;
 
@@ -132,6 +164,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t* acc_empty = acc_full + 2;      // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   __shared__ volatile int s_abort;
+  __shared__ float ep_stage[4][32][33];  // epilogue transpose, one block per epilogue warp
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int nk = K / TC_BK;
@@ -217,6 +250,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else {
     // Epilogue warps 2..5: warp w reads tensor-memory lanes 32 (w % 4) .. + 31.
     const int q = warp % 4;
+    float(*st)[33] = ep_stage[warp - 2];
     int64_t lt = 0;
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
       const int a = (int)(lt & 1);
@@ -230,24 +264,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int n0 = (int)(t % n_tiles_n) * TC_BN;
       const int64_t row = m0 + q * 32 + lane;
       const bool add_bias = bias != nullptr && (row % bias_period) == 0;
+      float* yrow = row < rows ? Y + row * ldy + n0 : nullptr;
       for (int c0 = 0; c0 < TC_BN; c0 += 32) {
         uint32_t vv[32];
         tmem_ld32(tmem + (uint32_t)(a * TC_TMEM_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, vv);
-        if (row < rows) {
-          float* y = Y + row * ldy + n0 + c0;
-          if (n0 + c0 + 32 <= n_out && !add_bias && (reinterpret_cast<uintptr_t>(y) & 15) == 0) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 4)
-              *reinterpret_cast<float4*>(y + j) = make_float4(__uint_as_float(vv[j]), __uint_as_float(vv[j + 1]),
-                                                              __uint_as_float(vv[j + 2]), __uint_as_float(vv[j + 3]));
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int n = n0 + c0 + j;
-              if (n < n_out) y[j] = __uint_as_float(vv[j]) + (add_bias ? bias[n] : 0.f);
-            }
-          }
-        }
+        const int n = n0 + c0 + lane;
+        const bool col_ok = n < n_out;
+        store_block_32x32(vv, st, lane, yrow ? yrow + c0 : nullptr, add_bias, bias != nullptr && col_ok ? bias[n] : 0.f,
+                          col_ok);
       }
       tc_fence_before();
       __syncwarp();
@@ -309,9 +333,9 @@ __device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint6
 
 __global__ void __launch_bounds__(T3_THREADS, 1)
     gemm_tf32x3_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBb,
-                          const __grid_constant__ CUtensorMap tmBs, int64_t rows, int n_out, int K,
-                          const float* __restrict__ bias, int bias_period, float* __restrict__ Y, int64_t ldy,
-                          unsigned int* __restrict__ status) {
+                          const __grid_constant__ CUtensorMap tmBs, int64_t seg_rows, int64_t n_seg, int rb,
+                          int n_out, int K, const float* __restrict__ bias, int bias_period, float* __restrict__ Y,
+                          int64_t ldy, int64_t y_seg_stride, unsigned int* __restrict__ status) {
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;                                  // [stage] X tile, x_big after conversion
@@ -325,11 +349,16 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   uint64_t* acc_empty = acc_full + 2;      // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   __shared__ volatile int s_abort;
+  __shared__ float ep_stage[4][32][33];  // epilogue transpose, one block per epilogue warp
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int nk = K / T3_BK;
   const int n_tiles_n = (n_out + TC_BN - 1) / TC_BN;
-  const int64_t n_tiles = ((rows + TC_BM - 1) / TC_BM) * n_tiles_n;
+  // A tile holds TC_BM rows: rb rows of each of sb = TC_BM / rb segments (rb < TC_BM only if
+  // seg_rows <= rb), or a TC_BM-row block of one segment.
+  const int sb = TC_BM / rb;
+  const int64_t rb_per_seg = (seg_rows + rb - 1) / rb;
+  const int64_t n_tiles = ((n_seg + sb - 1) / sb) * rb_per_seg * n_tiles_n;  // (segment group, row block, column block)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < T3_STAGES; ++s) {
@@ -359,7 +388,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     if (lane == 0) {  // TMA producer
       int64_t g = 0;
       for (int64_t t = blockIdx.x; t < n_tiles && !s_abort; t += gridDim.x) {
-        const int64_t m0 = (t / n_tiles_n) * TC_BM;
+        const int64_t mt = t / n_tiles_n;
+        const int seg = (int)(mt / rb_per_seg) * sb, m0 = (int)(mt % rb_per_seg) * rb;
         const int n0 = (int)(t % n_tiles_n) * TC_BN;
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = (int)(g % T3_STAGES);
@@ -369,7 +399,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             break;
           }
           mbar_expect_tx(&full[s], T3_TILE_A + 2 * T3_TILE_B);
-          tma_load_2d(sA + s * T3_TILE_A, &tmA, kb * T3_BK, (int)m0, &full[s]);
+          tma_load_3d(sA + s * T3_TILE_A, &tmA, kb * T3_BK, m0, seg, &full[s]);
           tma_load_2d(sBb + s * T3_TILE_B, &tmBb, kb * T3_BK, n0, &full[s]);
           tma_load_2d(sBs + s * T3_TILE_B, &tmBs, kb * T3_BK, n0, &full[s]);
         }
@@ -451,6 +481,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   } else {
     // Epilogue warps 2..5
     const int q = warp % 4;
+    float(*st)[33] = ep_stage[warp - 2];
     int64_t lt = 0;
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
       const int a = (int)(lt & 1);
@@ -460,28 +491,20 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         break;
       }
       tc_fence_after();
-      const int64_t m0 = (t / n_tiles_n) * TC_BM;
+      const int64_t mt = t / n_tiles_n;
+      const int tr = q * 32 + lane;  // row of the tile
+      const int64_t seg = (mt / rb_per_seg) * sb + tr / rb;
       const int n0 = (int)(t % n_tiles_n) * TC_BN;
-      const int64_t row = m0 + q * 32 + lane;
+      const int64_t row = (mt % rb_per_seg) * rb + tr % rb;  // row within the segment
       const bool add_bias = bias != nullptr && (row % bias_period) == 0;
+      float* yrow = row < seg_rows && seg < n_seg ? Y + seg * y_seg_stride + row * ldy + n0 : nullptr;
       for (int c0 = 0; c0 < TC_BN; c0 += 32) {
         uint32_t vv[32];
         tmem_ld32(tmem + (uint32_t)(a * TC_TMEM_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, vv);
-        if (row < rows) {
-          float* y = Y + row * ldy + n0 + c0;
-          if (n0 + c0 + 32 <= n_out && !add_bias && (reinterpret_cast<uintptr_t>(y) & 15) == 0) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 4)
-              *reinterpret_cast<float4*>(y + j) = make_float4(__uint_as_float(vv[j]), __uint_as_float(vv[j + 1]),
-                                                              __uint_as_float(vv[j + 2]), __uint_as_float(vv[j + 3]));
-          } else {
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int n = n0 + c0 + j;
-              if (n < n_out) y[j] = __uint_as_float(vv[j]) + (add_bias ? bias[n] : 0.f);
-            }
-          }
-        }
+        const int n = n0 + c0 + lane;
+        const bool col_ok = n < n_out;
+        store_block_32x32(vv, st, lane, yrow ? yrow + c0 : nullptr, add_bias, bias != nullptr && col_ok ? bias[n] : 0.f,
+                          col_ok);
       }
       tc_fence_before();
       __syncwarp();
@@ -525,6 +548,19 @@ bool make_map(CUtensorMap* m, const void* base, int64_t rows, int K, int64_t ld,
             dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+// FP32 rows in segments: dims {K, seg_rows, n_seg}, box {32, 128, 1}
+bool make_map_seg_f32(CUtensorMap* m, const void* base, int64_t seg_rows, int64_t n_seg, int K, int64_t ld,
+                      int64_t seg_stride, int rb) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)seg_rows, (cuuint64_t)n_seg};
+  const cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)seg_stride * 4};
+  const cuuint32_t box[3] = {32, (cuuint32_t)rb, (cuuint32_t)(TC_BM / rb)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 constexpr size_t t3_smem_bytes() {
   return 1024 + T3_STAGES * (2 * T3_TILE_A + 2 * T3_TILE_B) + (3 * T3_STAGES + 4) * 8 + 16;
 }
@@ -558,16 +594,19 @@ cudaError_t split_tf32(const float* W, float* big, float* small, int64_t n, cuda
   return cudaGetLastError();
 }
 
-cudaError_t gemm_tf32x3_tc(const float* X, int64_t rows, int K, int64_t ldx, const float* Wbig, const float* Wsmall,
-                           int n_out, const float* bias, int bias_period, float* Y, int64_t ldy, unsigned int* status,
-                           cudaStream_t s) {
-  if (rows <= 0 || n_out <= 0) return cudaSuccess;
-  if (K % T3_BK || ldx % 4 || (uintptr_t)X % 16 || (uintptr_t)Wbig % 16 || (uintptr_t)Wsmall % 16 ||
-      bias_period <= 0)
+cudaError_t gemm_tf32x3_tc_seg(const float* X, int64_t seg_rows, int64_t n_seg, int64_t x_seg_stride, int K,
+                               int64_t ldx, const float* Wbig, const float* Wsmall, int n_out, const float* bias,
+                               int bias_period, float* Y, int64_t ldy, int64_t y_seg_stride, unsigned int* status,
+                               cudaStream_t s) {
+  if (seg_rows <= 0 || n_seg <= 0 || n_out <= 0) return cudaSuccess;
+  if (K % T3_BK || ldx % 4 || x_seg_stride % 4 || (uintptr_t)X % 16 || (uintptr_t)Wbig % 16 ||
+      (uintptr_t)Wsmall % 16 || bias_period <= 0 || seg_rows > (int64_t)INT32_MAX || n_seg > (int64_t)INT32_MAX)
     return cudaErrorInvalidValue;
+  int rb = TC_BM;  // short segments: several per tile, rb (a power of two >= 8) rows each
+  while (rb > 8 && rb / 2 >= seg_rows) rb /= 2;
   CUtensorMap ma, mbb, mbs;
-  if (!make_map(&ma, X, rows, K, ldx, TC_BM, true) || !make_map(&mbb, Wbig, n_out, K, K, TC_BN, true) ||
-      !make_map(&mbs, Wsmall, n_out, K, K, TC_BN, true))
+  if (!make_map_seg_f32(&ma, X, seg_rows, n_seg, K, ldx, n_seg > 1 ? x_seg_stride : seg_rows * ldx, rb) ||
+      !make_map(&mbb, Wbig, n_out, K, K, TC_BN, true) || !make_map(&mbs, Wsmall, n_out, K, K, TC_BN, true))
     return cudaErrorInvalidValue;
   const size_t smem = t3_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -575,11 +614,18 @@ cudaError_t gemm_tf32x3_tc(const float* X, int64_t rows, int K, int64_t ldx, con
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t tiles = ((rows + TC_BM - 1) / TC_BM) * ((n_out + TC_BN - 1) / TC_BN);
+  const int64_t tiles = ((n_seg + TC_BM / rb - 1) / (TC_BM / rb)) * ((seg_rows + rb - 1) / rb) *
+                        ((n_out + TC_BN - 1) / TC_BN);
   const int64_t grid = tiles < sms ? tiles : sms;
-  gemm_tf32x3_tc_kernel<<<(unsigned)grid, T3_THREADS, smem, s>>>(ma, mbb, mbs, rows, n_out, K, bias, bias_period, Y,
-                                                                ldy, status);
+  gemm_tf32x3_tc_kernel<<<(unsigned)grid, T3_THREADS, smem, s>>>(ma, mbb, mbs, seg_rows, n_seg, rb, n_out, K, bias,
+                                                                bias_period, Y, ldy, y_seg_stride, status);
   return cudaGetLastError();
+}
+
+cudaError_t gemm_tf32x3_tc(const float* X, int64_t rows, int K, int64_t ldx, const float* Wbig, const float* Wsmall,
+                           int n_out, const float* bias, int bias_period, float* Y, int64_t ldy, unsigned int* status,
+                           cudaStream_t s) {
+  return gemm_tf32x3_tc_seg(X, rows, 1, 0, K, ldx, Wbig, Wsmall, n_out, bias, bias_period, Y, ldy, 0, status, s);
 }
 
 }  // namespace dq
