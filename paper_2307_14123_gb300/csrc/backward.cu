@@ -443,15 +443,18 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Column sums S[o] = sum_r X[r][o] (bias-type gradients): one thread per
-// column, consecutive threads on consecutive columns (coalesced), rows of the
-// walker range read in order.  blockIdx.y: walker (per-walker mode) or split.
+// Column sums S[o] = sum_r X[r][o] (bias-type gradients).  A CTA covers 32
+// consecutive columns (one per lane, coalesced rows) with 8 warps that take
+// every 8th row of the walker range; the 8 partial sums are added in a fixed
+// order in shared memory.  blockIdx.y: walker (per-walker mode) or split.
+constexpr int kColRows = 8;
 template <class T>
-__global__ void colsum_kernel(const T* __restrict__ X, RowMap mx, int rpw, int64_t nw, int n_o, T* __restrict__ G,
-                              int64_t P, int64_t off, int ld, int mode, int64_t walkers_per_split,
-                              T* __restrict__ part) {
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= n_o) return;
+__global__ void __launch_bounds__(32 * kColRows)
+    colsum_kernel(const T* __restrict__ X, RowMap mx, int rpw, int64_t nw, int n_o, T* __restrict__ G, int64_t P,
+                  int64_t off, int ld, int mode, int64_t walkers_per_split, T* __restrict__ part) {
+  __shared__ T red[kColRows][32];
+  const int lane = threadIdx.x % 32, rl = threadIdx.x / 32;
+  const int o = blockIdx.x * 32 + lane;
   int64_t wb0, wb1;
   if (mode == 1) {
     wb0 = blockIdx.y;
@@ -461,19 +464,30 @@ __global__ void colsum_kernel(const T* __restrict__ X, RowMap mx, int rpw, int64
     wb1 = min(nw, wb0 + walkers_per_split);
   }
   T acc = 0;
-  const int64_t r_begin = wb0 * rpw, r_end = wb1 * rpw;
-  int64_t seg = r_begin / mx.rows_per_seg, in = r_begin % mx.rows_per_seg;  // one division, then increments
-  for (int64_t r = r_begin; r < r_end; ++r) {
-    acc += X[seg * mx.seg_stride + in * mx.ld + o];
-    if (++in == mx.rows_per_seg) {
-      in = 0;
-      ++seg;
+  const int64_t r_begin = wb0 * rpw + rl, r_end = wb1 * rpw;
+  if (o < n_o && r_begin < r_end) {
+    int64_t seg = r_begin / mx.rows_per_seg, in = r_begin % mx.rows_per_seg;  // one division, then increments
+    const T* xo = X + o;
+    for (int64_t r = r_begin; r < r_end; r += kColRows) {
+      acc += xo[seg * mx.seg_stride + in * mx.ld];
+      in += kColRows;
+      while (in >= mx.rows_per_seg) {
+        in -= mx.rows_per_seg;
+        ++seg;
+      }
     }
   }
-  if (mode == 1)
-    G[wb0 * P + off + (int64_t)o * ld] = acc;
-  else
-    part[(int64_t)blockIdx.y * n_o + o] = acc;
+  red[rl][lane] = acc;
+  __syncthreads();
+  if (rl == 0 && o < n_o) {
+    T sum = 0;
+#pragma unroll
+    for (int k = 0; k < kColRows; ++k) sum += red[k][lane];
+    if (mode == 1)
+      G[wb0 * P + off + (int64_t)o * ld] = sum;
+    else
+      part[(int64_t)blockIdx.y * n_o + o] = sum;
+  }
 }
 
 template <class T>
@@ -664,24 +678,26 @@ cudaError_t param_reduce(const T* X, RowMap mx, const T* Y, RowMap my, int rpw, 
   if (Y != nullptr && n_o >= 16 && n_a >= 16)
     return param_reduce_tiled<T>(X, mx, Y, my, rpw, nw, n_o, n_a, G, P, off, ld, mode, part, part_elems, s);
   if (Y == nullptr && n_a == 1) {
-    const unsigned gx = nblocks(n_o, 128);
+    const unsigned gx = nblocks(n_o, 32);
     if (mode == 1) {
       for (int64_t w0 = 0; w0 < nw; w0 += 65535) {
         const int64_t nws = nw - w0 < 65535 ? nw - w0 : 65535;
         const int64_t r_off = w0 * rpw;
         const T* Xo = X + (r_off / mx.rows_per_seg) * mx.seg_stride + (r_off % mx.rows_per_seg) * mx.ld;
-        colsum_kernel<T><<<dim3(gx, (unsigned)nws), 128, 0, s>>>(Xo, mx, rpw, nws, n_o, G + w0 * P, P, off, ld, 1, 1,
-                                                                 nullptr);
+        colsum_kernel<T><<<dim3(gx, (unsigned)nws), 32 * kColRows, 0, s>>>(Xo, mx, rpw, nws, n_o, G + w0 * P, P, off,
+                                                                          ld, 1, 1, nullptr);
       }
       return cudaGetLastError();
     }
-    int64_t splits = (nw + 15) / 16;  // 16 walkers per thread
+    int64_t splits = (4 * 152 + gx - 1) / gx;  // about four CTAs per SM
+    if (splits > nw) splits = nw;
     if (splits * n_o > part_elems) splits = part_elems / n_o;
     if (splits < 1) return cudaErrorInvalidValue;
     if (splits > 65535) splits = 65535;
     const int64_t wps = (nw + splits - 1) / splits;
     splits = (nw + wps - 1) / wps;
-    colsum_kernel<T><<<dim3(gx, (unsigned)splits), 128, 0, s>>>(X, mx, rpw, nw, n_o, G, P, off, ld, 0, wps, part);
+    colsum_kernel<T><<<dim3(gx, (unsigned)splits), 32 * kColRows, 0, s>>>(X, mx, rpw, nw, n_o, G, P, off, ld, 0, wps,
+                                                                          part);
     reduce_splits_kernel<T><<<nblocks(n_o, 256), 256, 0, s>>>(part, (int)splits, n_o, 1, G, off, ld);
     return cudaGetLastError();
   }
