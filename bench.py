@@ -195,6 +195,12 @@ def peaks():
         "fallback"
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of the jet message kernel (layer >= 1 launch) per walker,
+# from the ncu capture summarised in profiles/messages_kernel_n2_512.md (N2, FP32); None once the kernel
+# has changed since that capture.
+MSG_DRAM_BYTES_PER_WALKER = (276.438016e6 + 428.677120e6) / 512
+
+
 def roofline_for(kind, ms, n, wl, chunk, pk, how):
     """Roofline entry of one kernel kind: algorithmic work per launch / average launch time."""
     s, c = wl.system, wl.cfg
@@ -206,18 +212,30 @@ def roofline_for(kind, ms, n, wl, chunk, pk, how):
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     bf16 = wl.precision == "bf16"
-    if kind in ("jet.gemm_update", "jet.gemm_node"):
-        k = 3 * D if kind == "jet.gemm_update" else D
-        flops = 2.0 * rows * k * D
-        if bf16:
-            peak, bound, src = pk["bf16_tflops_sustained"], "tensor", f"{how} bf16 sustained (cuBLAS loop)"
-        elif wl.precision == "fp64":
+    gemm_k = {"jet.gemm_update": (rows, 3 * D, D), "jet.gemm_node": (rows, D, D),
+              "jet.gemm_edge": (chunk * E * 3, D, D),
+              # per spin s: (n_s * C rows) x (K * n_s outputs), summed over both spins
+              "jet.gemm_orbital": (chunk * C, D, c.n_det * (s.n_up ** 2 + s.n_down ** 2))}
+    if kind in gemm_k:
+        m, k, n_out = gemm_k[kind]
+        flops = 2.0 * m * k * n_out
+        if wl.precision == "fp64":
             peak, bound, src = 1.25, "alu", "nominal FP64"
+        elif bf16 and kind in ("jet.gemm_update", "jet.gemm_node"):
+            peak, bound, src = pk["bf16_tflops_sustained"], "tensor", f"{how} bf16 sustained (cuBLAS loop)"
         else:
-            peak, bound, src = fp32_peak, "alu", f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"
+            # FP32 operands as three TF32 tensor-core products: TF32 peak (measured bf16 x nominal 1.1/2.25) / 3
+            peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25) / 3.0
+            bound, src = "tensor", f"{how} bf16 sustained x 1.1/2.25 (TF32) / 3 (3xTF32 split)"
         ach = flops / t / 1e12
         return {"kernel": kind, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": None, "peak_source": src, "flops_per_launch": flops, "avg_launch_ms": ms / n}
+    if kind == "jet.messages" and wl.name == "n2_fp32" and MSG_DRAM_BYTES_PER_WALKER:
+        # DRAM bytes of one launch from an ncu capture (profiles/messages_kernel_n2_512.md), per walker,
+        # scaled to the launch's walkers
+        traffic = MSG_DRAM_BYTES_PER_WALKER * chunk
+    else:
+        traffic = None
     if kind == "jet.messages":
         el = 8 if wl.precision == "fp64" else 4
         out_el = 2 if bf16 else el
@@ -226,7 +244,7 @@ def roofline_for(kind, ms, n, wl, chunk, pk, how):
         byts = (rows * D * el * (L - 1) / L) + chunk * E * 3 * D * el + rows * 3 * D * out_el
         ach = byts / t / 1e9
         return {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": f"{how} copy bandwidth",
+                "frac": ach / pk["hbm_gbs"], "traffic": traffic, "peak_source": f"{how} copy bandwidth",
                 "bytes_per_launch": byts, "avg_launch_ms": ms / n}
     return None
 
@@ -343,7 +361,7 @@ def main():
     dom = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
     roof = None
     others = []
-    for kind in ("jet.gemm_update", "jet.messages", "jet.gemm_node"):
+    for kind in ("jet.messages", "jet.gemm_update", "jet.gemm_edge", "jet.gemm_node", "jet.gemm_orbital"):
         if kind in prof:
             e = roofline_for(kind, prof[kind][0], prof[kind][1], wl, chunk, pk, how)
             if e:

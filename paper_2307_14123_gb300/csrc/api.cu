@@ -373,7 +373,7 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
 // ---------------------------------------------------------------------------
 struct GradPlan {
   size_t geo, rbf, eh, ew, zl, msg, u, F, phi, det, js, jh, z0;  // saved forward
-  size_t fbar, ubar, mbar, zbar, wbar, hbar, phibar, beta, cbar, jhbar, gt, sbar, envbar, ybar, part, wt3;
+  size_t fbar, ubar, mbar, zbar, wbar, hbar, phibar, beta, cbar, jhbar, gt, sbar, envbar, ybar, part, wt3, wt3t;
   int64_t part_elems;
   size_t total;
 };
@@ -419,6 +419,7 @@ GradPlan plan_grad(const dq_handle_s& h, int64_t Bc, size_t elem) {
   p.part_elems = 64 * blk;
   p.part = take(p.part_elems * elem);
   p.wt3 = take(use_tf32x3(h) ? t3_weight_floats(h) * 4 : 0);
+  p.wt3t = take(use_tf32x3(h) ? (size_t)L * kT3PerLayer * D * D * 4 : 0);  // transposed splits (reverse pass)
   p.total = o;
   return p;
 }
@@ -441,8 +442,18 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
   T* part = buf(pl.part);
   const bool use_t3 = sizeof(T) == 4 && use_tf32x3(h);
   const T3Weights w3 = t3_weights(h, ws + pl.wt3);
+  // transposed splits for the products with W in the reverse pass (same block layout per layer)
+  const T3Weights w3t = t3_weights(h, ws + pl.wt3t);
   if (use_t3) {
-    if constexpr (sizeof(T) == 4) DQ_CU(split_t3_weights(h, params, w3, s));
+    if constexpr (sizeof(T) == 4) {
+      DQ_CU(split_t3_weights(h, params, w3, s));
+      for (int l = 0; l < L; ++l) {
+        const auto& y = off.layer[l];
+        DQ_CU(split_tf32_t(params + y.W_g, D, 3 * D, w3t.wg(l, 0), w3t.wg(l, 1), s));
+        DQ_CU(split_tf32_t(params + y.W_h, D, D, w3t.wh(l, 0), w3t.wh(l, 1), s));
+        for (int t = 0; t < 3; ++t) DQ_CU(split_tf32_t(params + y.W2[t], D, D, w3t.w2(l, t, 0), w3t.w2(l, t, 1), s));
+      }
+    }
   }
   const int ns[2] = {h.n_up, h.n_dn}, i0[2] = {0, h.n_up};
   const int e0[3] = {0, h.edges.n_par, h.edges.n_ee};
@@ -574,19 +585,37 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
       DQ_LAUNCH(h, PK_BWD_UPDATE, launch_tanh_bwd<T>(fbar, U(l), nb * N * D, true, ubar, s));
       DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ubar, rm(D), MS(l), rm(3 * D), N, D, 3 * D, y.W_g, 3 * D));
       DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ubar, rm(D), nullptr, rm(1), N, D, 1, y.b_g, 1));
-      DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(ubar, rm(D), params + y.W_g, mbar, rm(3 * D), nb * N, 3 * D, D, false, s));
+      if (use_t3)
+        DQ_LAUNCH(h, PK_BWD_GEMM,
+                  gemm_tf32x3_tc(reinterpret_cast<const float*>(ubar), nb * N, D, D, w3t.wg(l, 0), w3t.wg(l, 1),
+                                 3 * D, nullptr, 1, reinterpret_cast<float*>(mbar), 3 * D, h.d_status, s));
+      else
+        DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(ubar, rm(D), params + y.W_g, mbar, rm(3 * D), nb * N, 3 * D, D, false, s));
       DQ_LAUNCH(h, PK_BWD_MESSAGES, launch_msg_bwd<T>(h, nb, mbar, ZL(l), v.z0, EW(l), params + y.Y, l == 0, zbar, wbar,
                                                       ybar, s));
       DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ybar, rm((int64_t)M * D), nullptr, rm(1), 1, M * D, 1, y.Y, 1));
       DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(zbar, rm(D), F(l), rm(D), N, D, D, y.W_h, D));
-      DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(zbar, rm(D), params + y.W_h, fbar, rm(D), nb * N, D, D, true, s));
+      if (use_t3)
+        DQ_LAUNCH(h, PK_BWD_GEMM,
+                  gemm_tf32x3_tc_seg(reinterpret_cast<const float*>(zbar), nb * N, 1, 0, D, D, w3t.wh(l, 0),
+                                     w3t.wh(l, 1), D, nullptr, 1, reinterpret_cast<float*>(fbar), D, 0, h.d_status, s,
+                                     true));
+      else
+        DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(zbar, rm(D), params + y.W_h, fbar, rm(D), nb * N, D, D, true, s));
       for (int t = 0; t < 3; ++t) {
         if (ng[t] == 0) continue;
         const RowMap me{(int64_t)ng[t], (int64_t)E * D, D};
         const T* wb = wbar + (int64_t)e0[t] * D;
         DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(wb, me, EH(l) + (int64_t)e0[t] * D, me, ng[t], D, D, y.W2[t], D));
         DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(wb, me, nullptr, rm(1), ng[t], D, 1, y.b2[t], 1));
-        DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(wb, me, params + y.W2[t], hbar + (int64_t)e0[t] * D, me, nb * ng[t], D, D,
+        if (use_t3)
+          DQ_LAUNCH(h, PK_BWD_GEMM,
+                    gemm_tf32x3_tc_seg(reinterpret_cast<const float*>(wb), ng[t], nb, (int64_t)E * D, D, D,
+                                       w3t.w2(l, t, 0), w3t.w2(l, t, 1), D, nullptr, 1,
+                                       reinterpret_cast<float*>(hbar) + (int64_t)e0[t] * D, D, (int64_t)E * D,
+                                       h.d_status, s));
+        else
+          DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(wb, me, params + y.W2[t], hbar + (int64_t)e0[t] * D, me, nb * ng[t], D, D,
                                              false, s));
       }
       DQ_LAUNCH(h, PK_BWD_EDGE, launch_tanh_bwd<T>(hbar, EH(l), nb * E * D, false, hbar, s));

@@ -123,10 +123,13 @@ cudaError_t gemm_tf32x3_tc(const float* X, int64_t rows, int K, int64_t ldx, con
 // Rows in n_seg segments of seg_rows rows (segment g starts at X + g * x_seg_stride
 // and Y + g * y_seg_stride; x_seg_stride % 4 == 0); the bias goes on the rows
 // whose index within the segment is a multiple of bias_period.
+// accumulate: Y += X W^T instead of Y = X W^T (+ bias).
 cudaError_t gemm_tf32x3_tc_seg(const float* X, int64_t seg_rows, int64_t n_seg, int64_t x_seg_stride, int K,
                                int64_t ldx, const float* Wbig, const float* Wsmall, int n_out, const float* bias,
                                int bias_period, float* Y, int64_t ldy, int64_t y_seg_stride, unsigned int* status,
-                               cudaStream_t s);
+                               cudaStream_t s, bool accumulate = false);
+// TF32 high / low parts of the transpose of W [rows][cols] (for products X W).
+cudaError_t split_tf32_t(const float* W, int rows, int cols, float* big, float* small, cudaStream_t s);
 
 // ---- forward kernels (forward.cu) ------------------------------------------
 // Sizes of one chunk of Bc walkers; C = channels (1 value-only, 3N+2 with jets).

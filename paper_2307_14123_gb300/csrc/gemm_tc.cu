@@ -130,7 +130,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 // outside the output); my_bias: that row takes the bias; bn: the bias of this
 // lane's column; col_ok: this lane's column is inside the output.
 __device__ __forceinline__ void store_block_32x32(const uint32_t (&v)[32], float (*st)[33], int lane, float* my_row,
-                                                  bool my_bias, float bn, bool col_ok) {
+                                                  bool my_bias, float bn, bool col_ok, bool accumulate = false) {
 #pragma unroll
   for (int j = 0; j < 32; ++j) st[lane][j] = __uint_as_float(v[j]);
   __syncwarp();
@@ -142,7 +142,7 @@ __device__ __forceinline__ void store_block_32x32(const uint32_t (&v)[32], float
     const uint32_t b = __shfl_sync(0xffffffffu, fb, rr);
     float* y = reinterpret_cast<float*>(((unsigned long long)hi << 32) | lo);
     const float val = st[rr][lane] + (b ? bn : 0.f);
-    if (y != nullptr && col_ok) y[lane] = val;
+    if (y != nullptr && col_ok) y[lane] = accumulate ? y[lane] + val : val;
   }
   __syncwarp();
 }
@@ -318,6 +318,27 @@ __global__ void split_tf32_kernel(const float* __restrict__ W, float* __restrict
   small[e] = tf32_rn(x - b);
 }
 
+// Split of the transpose: W [rows][cols] -> big, small [cols][rows] (the B
+// operand of X W, whose reduction index is W's row index).
+__global__ void split_tf32_t_kernel(const float* __restrict__ W, int rows, int cols, float* __restrict__ big,
+                                    float* __restrict__ small) {
+  __shared__ float tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k, c = c0 + threadIdx.x;
+    tile[k][threadIdx.x] = r < rows && c < cols ? W[(int64_t)r * cols + c] : 0.f;
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int c = c0 + k, r = r0 + threadIdx.x;
+    if (c < cols && r < rows) {
+      const float x = tile[threadIdx.x][k], b = tf32_rn(x);
+      big[(int64_t)c * rows + r] = b;
+      small[(int64_t)c * rows + r] = tf32_rn(x - b);
+    }
+  }
+}
+
 // Instruction descriptor: kind::tf32, A and B TF32 (K-major), D FP32.
 constexpr uint32_t t3_idesc(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -335,7 +356,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     gemm_tf32x3_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBb,
                           const __grid_constant__ CUtensorMap tmBs, int64_t seg_rows, int64_t n_seg, int rb,
                           int n_out, int K, const float* __restrict__ bias, int bias_period, float* __restrict__ Y,
-                          int64_t ldy, int64_t y_seg_stride, unsigned int* __restrict__ status) {
+                          int64_t ldy, int64_t y_seg_stride, int accumulate, unsigned int* __restrict__ status) {
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;                                  // [stage] X tile, x_big after conversion
@@ -504,7 +525,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         const int n = n0 + c0 + lane;
         const bool col_ok = n < n_out;
         store_block_32x32(vv, st, lane, yrow ? yrow + c0 : nullptr, add_bias, bias != nullptr && col_ok ? bias[n] : 0.f,
-                          col_ok);
+                          col_ok, accumulate != 0);
       }
       tc_fence_before();
       __syncwarp();
@@ -594,10 +615,16 @@ cudaError_t split_tf32(const float* W, float* big, float* small, int64_t n, cuda
   return cudaGetLastError();
 }
 
+cudaError_t split_tf32_t(const float* W, int rows, int cols, float* big, float* small, cudaStream_t s) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+  split_tf32_t_kernel<<<grid, dim3(32, 8), 0, s>>>(W, rows, cols, big, small);
+  return cudaGetLastError();
+}
+
 cudaError_t gemm_tf32x3_tc_seg(const float* X, int64_t seg_rows, int64_t n_seg, int64_t x_seg_stride, int K,
                                int64_t ldx, const float* Wbig, const float* Wsmall, int n_out, const float* bias,
                                int bias_period, float* Y, int64_t ldy, int64_t y_seg_stride, unsigned int* status,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool accumulate) {
   if (seg_rows <= 0 || n_seg <= 0 || n_out <= 0) return cudaSuccess;
   if (K % T3_BK || ldx % 4 || x_seg_stride % 4 || (uintptr_t)X % 16 || (uintptr_t)Wbig % 16 ||
       (uintptr_t)Wsmall % 16 || bias_period <= 0 || seg_rows > (int64_t)INT32_MAX || n_seg > (int64_t)INT32_MAX)
@@ -618,14 +645,16 @@ cudaError_t gemm_tf32x3_tc_seg(const float* X, int64_t seg_rows, int64_t n_seg, 
                         ((n_out + TC_BN - 1) / TC_BN);
   const int64_t grid = tiles < sms ? tiles : sms;
   gemm_tf32x3_tc_kernel<<<(unsigned)grid, T3_THREADS, smem, s>>>(ma, mbb, mbs, seg_rows, n_seg, rb, n_out, K, bias,
-                                                                bias_period, Y, ldy, y_seg_stride, status);
+                                                                bias_period, Y, ldy, y_seg_stride,
+                                                                accumulate ? 1 : 0, status);
   return cudaGetLastError();
 }
 
 cudaError_t gemm_tf32x3_tc(const float* X, int64_t rows, int K, int64_t ldx, const float* Wbig, const float* Wsmall,
                            int n_out, const float* bias, int bias_period, float* Y, int64_t ldy, unsigned int* status,
                            cudaStream_t s) {
-  return gemm_tf32x3_tc_seg(X, rows, 1, 0, K, ldx, Wbig, Wsmall, n_out, bias, bias_period, Y, ldy, 0, status, s);
+  return gemm_tf32x3_tc_seg(X, rows, 1, 0, K, ldx, Wbig, Wsmall, n_out, bias, bias_period, Y, ldy, 0, status, s,
+                            false);
 }
 
 }  // namespace dq
