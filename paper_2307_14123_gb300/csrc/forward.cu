@@ -83,55 +83,103 @@ __global__ void geometry_kernel(const T* __restrict__ r, const T* __restrict__ R
 }
 
 // Edge hidden layer a = tanh(W1 e + b1) as a jet in d: (a, a', a'').
-// W1 and b1 of the three edge types are staged in shared memory ([t][q][a],
-// conflict-free across the feature lanes); each CTA streams kEdgesPerCta
-// consecutive (walker, edge) rows, threads over features.
+// W1 and b1 of the three edge types are staged in shared memory once per CTA
+// ([t][q][a]); the persistent CTAs then stream blocks of kEdgesPerCta
+// consecutive (walker, edge) rows.  A thread computes kHiddenVec consecutive
+// features of one edge (vector loads of W1, vector stores), so D / kHiddenVec
+// threads cover an edge and one warp holds one edge type.
 constexpr int kEdgesPerCta = 32;
-constexpr int kHiddenThreads = 128;
+constexpr int kHiddenThreads = 256;
+
+template <class T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int n = 4;
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int n = 2;
+};
 
 template <class T>
 __global__ void __launch_bounds__(kHiddenThreads)
     edge_hidden_kernel(const T* __restrict__ rbf, const T* __restrict__ params, int64_t Bc, int E, int n_par,
                        int n_ee, int D, int Q, int ej, int64_t W1_0, int64_t W1_1, int64_t W1_2, int64_t b1_0,
                        int64_t b1_1, int64_t b1_2, T* __restrict__ eh) {
+  using V = typename Vec16<T>::type;
+  constexpr int VW = Vec16<T>::n;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* Ws = reinterpret_cast<T*>(smem_raw);  // [3][Q][D]
   T* bs = Ws + 3 * Q * D;                  // [3][D]
-  T* fs = bs + 3 * D;                      // [kEdgesPerCta][ej][Q] features of this CTA's rows
+  T* fs = bs + 3 * D;                      // [kEdgesPerCta][ej][Q] features of this block's rows
   const int64_t W1o[3] = {W1_0, W1_1, W1_2}, b1o[3] = {b1_0, b1_1, b1_2};
-  for (int k = threadIdx.x; k < 3 * Q * D; k += kHiddenThreads) {
-    const int t = k / (Q * D), q = (k / D) % Q, a = k % D;
-    Ws[k] = params[W1o[t] + (int64_t)a * Q + q];
-  }
-  for (int k = threadIdx.x; k < 3 * D; k += kHiddenThreads) bs[k] = params[b1o[k / D] + k % D];
-  const int64_t be0 = (int64_t)blockIdx.x * kEdgesPerCta;
+  for (int t = 0; t < 3; ++t)
+    for (int a = threadIdx.x; a < D; a += blockDim.x) {
+      const T* src = params + W1o[t] + (int64_t)a * Q;
+      for (int q = 0; q < Q; ++q) Ws[(t * Q + q) * D + a] = src[q];
+      bs[t * D + a] = params[b1o[t] + a];
+    }
+  const int tpe = D / VW;                        // threads per edge
+  const int epp = blockDim.x / tpe;              // edges in parallel
+  const int er = threadIdx.x / tpe, a0 = (threadIdx.x % tpe) * VW;
   const int64_t nrows = Bc * E;
-  const int nb = (int)min((int64_t)kEdgesPerCta, nrows - be0);
-  for (int k = threadIdx.x; k < nb * ej * Q; k += kHiddenThreads) fs[k] = rbf[be0 * ej * Q + k];
-  __syncthreads();
-  for (int r = 0; r < nb; ++r) {
-    const int64_t be = be0 + r;
-    const int e = (int)(be % E);
-    const int t = e < n_par ? 0 : (e < n_ee ? 1 : 2);
-    const T* W = Ws + t * Q * D;
-    const T* f = fs + r * ej * Q;
-    for (int a = threadIdx.x; a < D; a += kHiddenThreads) {
-      T h = bs[t * D + a], h1 = 0, h2 = 0;
+  for (int64_t be0 = (int64_t)blockIdx.x * kEdgesPerCta; be0 < nrows; be0 += (int64_t)gridDim.x * kEdgesPerCta) {
+    const int nb = (int)min((int64_t)kEdgesPerCta, nrows - be0);
+    __syncthreads();  // previous block's features consumed (and the weights staged)
+    for (int k = threadIdx.x; k < nb * ej * Q; k += blockDim.x) fs[k] = rbf[be0 * ej * Q + k];
+    __syncthreads();
+    if (er >= epp) continue;
+    for (int r = er; r < nb; r += epp) {
+      const int64_t be = be0 + r;
+      const int e = (int)(be % E);
+      const int t = e < n_par ? 0 : (e < n_ee ? 1 : 2);
+      const T* W = Ws + t * Q * D + a0;
+      const T* f = fs + r * ej * Q;
+      T h[VW], h1[VW], h2[VW];
+      const V bv = *reinterpret_cast<const V*>(bs + t * D + a0);
+      const T* bp = reinterpret_cast<const T*>(&bv);
+#pragma unroll
+      for (int v = 0; v < VW; ++v) {
+        h[v] = bp[v];
+        h1[v] = 0;
+        h2[v] = 0;
+      }
+#pragma unroll 4
       for (int q = 0; q < Q; ++q) {
-        const T w = W[q * D + a];
-        h += w * f[q];
+        const V wv = *reinterpret_cast<const V*>(W + q * D);
+        const T* w = reinterpret_cast<const T*>(&wv);
+        const T f0 = f[q];
+#pragma unroll
+        for (int v = 0; v < VW; ++v) h[v] += w[v] * f0;
         if (ej == 3) {
-          h1 += w * f[Q + q];
-          h2 += w * f[2 * Q + q];
+          const T f1 = f[Q + q], f2 = f[2 * Q + q];
+#pragma unroll
+          for (int v = 0; v < VW; ++v) {
+            h1[v] += w[v] * f1;
+            h2[v] += w[v] * f2;
+          }
         }
       }
-      const T av = tanh_t(h);
-      T* o = eh + be * ej * D + a;
-      o[0] = av;
-      if (ej == 3) {
+      V o0, o1, o2;
+      T* p0 = reinterpret_cast<T*>(&o0);
+      T* p1 = reinterpret_cast<T*>(&o1);
+      T* p2 = reinterpret_cast<T*>(&o2);
+#pragma unroll
+      for (int v = 0; v < VW; ++v) {
+        const T av = tanh_t(h[v]);
+        p0[v] = av;
         const T da = T(1) - av * av;
-        o[D] = da * h1;
-        o[2 * D] = da * h2 - T(2) * av * da * h1 * h1;
+        p1[v] = da * h1[v];
+        p2[v] = da * h2[v] - T(2) * av * da * h1[v] * h1[v];
+      }
+      T* o = eh + be * ej * D + a0;
+      *reinterpret_cast<V*>(o) = o0;
+      if (ej == 3) {
+        *reinterpret_cast<V*>(o + D) = o1;
+        *reinterpret_cast<V*>(o + 2 * D) = o2;
       }
     }
   }
@@ -182,21 +230,24 @@ constexpr int kMsgLanes = 32;
 
 // Shared-memory layout of the jet message kernel (element offsets in T).
 struct MsgSmem {
-  int w0, w1, w2, us, invd, z0c, zself, sp, ps, total_bytes;
+  int w0, w1, us, invd, z0c, zself, sp, ring, ps, total_bytes;
 };
+constexpr int kMsgRing = 4;     // senders in flight per warp (asynchronous copies)
+constexpr int kMsgWarps = 8;
 template <class T>
-__host__ __device__ inline MsgSmem msg_smem_layout(int N, int IB, bool stage_w12) {
+__host__ __device__ inline MsgSmem msg_smem_layout(int N, int IB, int CB, bool stage_w1) {
   MsgSmem m{};
   int o = 0;
   const int rows = N * N + IB;  // padded: receivers past the end read zeros
   m.w0 = o; o += rows * kMsgLanes;
-  m.w1 = o; o += stage_w12 ? rows * kMsgLanes : 0;
-  m.w2 = o; o += stage_w12 ? N * N * kMsgLanes : 0;
+  m.w1 = o; o += stage_w1 ? rows * kMsgLanes : 0;
   m.us = o; o += (N + IB) * N * 3;  // u_ij,x (zero diagonal, zero padding)
   m.invd = o; o += N * N;
   m.z0c = o; o += N * kMsgLanes;       // z_j[0]
   m.zself = o; o += 3 * N * kMsgLanes;  // dz_j / dr_j,x
   m.sp = o; o += 13 * N * kMsgLanes;   // (b) [N][3 x][3], (c) [N][3], (d) [N]
+  o = (o + 3) / 4 * 4;                 // 16-byte alignment of the copy ring
+  m.ring = o; o += kMsgWarps * kMsgRing * CB * kMsgLanes;  // [warp][slot][q][lane] z of senders in flight
   m.ps = o * (int)sizeof(T);           // byte offset of the int pair table
   m.total_bytes = m.ps + N * N * (int)sizeof(int);
   return m;
@@ -206,20 +257,20 @@ template <class T, class TO, int IB, int CB>
 __global__ void __launch_bounds__(256, 2)
     messages_kernel(const T* __restrict__ Z, const T* __restrict__ z0, const T* __restrict__ ew,
                     const T* __restrict__ geo, const T* __restrict__ Y, const int* __restrict__ pair_of, int N,
-                    int n_up, int M, int C, int D, int E, int n_ee, int z_const, int stage_w12,
+                    int n_up, int M, int C, int D, int E, int n_ee, int z_const, int stage_w1,
                     TO* __restrict__ msg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int L = kMsgLanes, ej = 3;
-  const MsgSmem lay = msg_smem_layout<T>(N, IB, stage_w12 != 0);
+  const MsgSmem lay = msg_smem_layout<T>(N, IB, CB, stage_w1 != 0);
   T* sm = reinterpret_cast<T*>(smem_raw);
   T* W0 = sm + lay.w0;  // [(j*N + i)][L]  w_ij
   T* W1 = sm + lay.w1;  //                 w'_ij
-  T* W2 = sm + lay.w2;  //                 w''_ij
   T* Us = sm + lay.us;  // [(i*N + j)][3]
   T* Id = sm + lay.invd;
   T* Z0c = sm + lay.z0c;  // [j][L]
   T* Zsf = sm + lay.zself;  // [j][x][L]
   T* SP = sm + lay.sp;
+  T* Ring = sm + lay.ring;
   int* Ps = reinterpret_cast<int*>(smem_raw + lay.ps);
   T* SPb = SP;               // [i][x][3]  (same, opposite, nucleus)
   T* SPc = SP + 9 * N * L;   // [i][3]
@@ -260,22 +311,26 @@ __global__ void __launch_bounds__(256, 2)
     Id[k] = id;
   }
   for (int k = tid; k < IB * N * 3; k += blockDim.x) Us[NN * 3 + k] = T(0);
+  TO* mb = msg + b * N * C * 3 * D + d0 + lane;
+  // electron-nucleus part of every output: zero except in the value, Laplacian and
+  // own-coordinate channels, which are written after phase 1
+  for (int i = grp; i < N; i += ngroups) {
+    TO* o = mb + (int64_t)i * C * 3 * D + 2 * D;
+    for (int c = 0; c < C; ++c, o += 3 * D) *o = to_out(T(0), o);
+  }
+  __syncthreads();  // pair table ready
+  // filter tables; rows are independent, so several loads are in flight per warp
+#pragma unroll 4
   for (int r = grp; r < NN + IB; r += ngroups) {
-    T v0 = 0, v1 = 0, v2 = 0;
-    if (r < NN) {
-      const int j = r / N, i = r - (r / N) * N;
-      if (i != j) {
-        const T* w = EWb + (int64_t)pair_of[r] * ej * D;
-        v0 = w[0];
-        v1 = w[D];
-        v2 = w[2 * D];
-      }
+    T v0 = 0, v1 = 0;
+    const int p = r < NN ? Ps[r] : -1;  // Ps[j * N + i]: the edge (i, j), -1 on the diagonal
+    if (p >= 0) {
+      const T* w = EWb + (int64_t)p * ej * D;
+      v0 = w[0];
+      v1 = w[D];
     }
     W0[r * L + lane] = v0;
-    if (stage_w12) {
-      W1[r * L + lane] = v1;
-      if (r < NN) W2[r * L + lane] = v2;
-    }
+    if (stage_w1) W1[r * L + lane] = v1;
   }
   for (int j = grp; j < N; j += ngroups) {
     const T* zj = Zb + (int64_t)j * C * D;
@@ -286,22 +341,24 @@ __global__ void __launch_bounds__(256, 2)
   __syncthreads();
   // w' and w'' of the edge (i, j) for this lane (zero on the diagonal)
   auto w1_at = [&](int i, int j) -> T {
-    if (stage_w12) return W1[(j * N + i) * L + lane];
+    if (stage_w1) return W1[(j * N + i) * L + lane];
     return i == j ? T(0) : EWb[((int64_t)Ps[i * N + j] * ej + 1) * D];
   };
   auto w2_at = [&](int i, int j) -> T {
-    if (stage_w12) return W2[(j * N + i) * L + lane];
     return i == j ? T(0) : EWb[((int64_t)Ps[i * N + j] * ej + 2) * D];
   };
 
   // ---- phase 1: per-receiver terms (b), (c), (d) ----
+  // items: 3N of kind (b) (receiver, axis), 2N of kind (c) (receiver, sender spin), N of kind (d)
   const int n_dn = N - n_up;
-  for (int it = grp; it < 5 * N; it += ngroups) {
+  for (int it = grp; it < 6 * N; it += ngroups) {
     if (it < 3 * N) {  // (b) receiver i, axis x
       const int i = it / 3, x = it - (it / 3) * 3;
       const bool up = i < n_up;
       T sa = 0, sb = 0, sn = 0;  // spin up senders, spin down senders
+#pragma unroll 4
       for (int j = 0; j < n_up; ++j) sa += w1_at(i, j) * Us[(i * N + j) * 3 + x] * Z0c[j * L + lane];
+#pragma unroll 4
       for (int j = n_up; j < N; ++j) sb += w1_at(i, j) * Us[(i * N + j) * 3 + x] * Z0c[j * L + lane];
       for (int I = 0; I < M; ++I) {
         const int en = i * M + I;
@@ -311,13 +368,14 @@ __global__ void __launch_bounds__(256, 2)
       o[0] = up ? sa : sb;
       o[L] = up ? sb : sa;
       o[2 * L] = sn;
-    } else if (it < 4 * N) {  // (c) Laplacian channel of receiver i
-      const int i = it - 3 * N;
+    } else if (it < 5 * N) {  // (c) Laplacian channel of receiver i, senders of one spin
+      const int i = (it - 3 * N) >> 1, h = (it - 3 * N) & 1;
       const bool up = i < n_up;
+      const int j0 = h == 0 ? 0 : n_up, j1 = h == 0 ? n_up : N;
       const T* zc = Zb + (int64_t)(1 + 3 * i) * D;  // dz_j / dr_i of sender j at zc + j * C * D
-      T sa = 0, sb = 0, sn = 0;
-#pragma unroll 2
-      for (int j = 0; j < N; ++j) {
+      T sv = 0;
+#pragma unroll 4
+      for (int j = j0; j < j1; ++j) {
         const T v1 = w1_at(i, j);
         T t = (T(2) * w2_at(i, j) + T(4) * v1 * Id[i * N + j]) * Z0c[j * L + lane];
         if (!z_const) {
@@ -327,19 +385,20 @@ __global__ void __launch_bounds__(256, 2)
                        u[2] * (zj[2 * D] - Zsf[(j * 3 + 2) * L + lane]);
           t += T(2) * v1 * cr;
         }
-        if (j < n_up) sa += t; else sb += t;
+        sv += t;
       }
-      for (int I = 0; I < M; ++I) {
-        const int en = i * M + I;
-        const T* w = EWb + (int64_t)(n_ee + en) * ej * D;
-        sn += (w[2 * D] + T(2) * w[D] / Gb[(n_ee + en) * 4]) * Yd[(int64_t)I * D];
+      SPc[(i * 3 + (up == (h == 0) ? 0 : 1)) * L + lane] = sv;
+      if (h == 0) {
+        T sn = 0;
+        for (int I = 0; I < M; ++I) {
+          const int en = i * M + I;
+          const T* w = EWb + (int64_t)(n_ee + en) * ej * D;
+          sn += (w[2 * D] + T(2) * w[D] / Gb[(n_ee + en) * 4]) * Yd[(int64_t)I * D];
+        }
+        SPc[(i * 3 + 2) * L + lane] = sn;
       }
-      T* o = SPc + i * 3 * L + lane;
-      o[0] = up ? sa : sb;
-      o[L] = up ? sb : sa;
-      o[2 * L] = sn;
     } else {  // (d) value channel, nuclei
-      const int i = it - 4 * N;
+      const int i = it - 5 * N;
       T sn = 0;
       for (int I = 0; I < M; ++I) sn += EWb[(int64_t)(n_ee + i * M + I) * ej * D] * Yd[(int64_t)I * D];
       SPd[i * L + lane] = sn;
@@ -347,18 +406,15 @@ __global__ void __launch_bounds__(256, 2)
   }
   __syncthreads();
 
-  TO* mb = msg + b * N * C * 3 * D + d0 + lane;
-  // electron-nucleus part of every output (nonzero in the value, Laplacian and own-coordinate channels)
+  // electron-nucleus part of the value, Laplacian and own-coordinate channels
   const T nuM = T(1) / T(M);
-  for (int i = grp; i < N; i += ngroups) {
-    TO* o = mb + (int64_t)i * C * 3 * D + 2 * D;
-    for (int c = 0; c < C; ++c) {
-      T v = 0;
-      if (c == 0) v = SPd[i * L + lane];
-      else if (c == C - 1) v = SPc[(i * 3 + 2) * L + lane];
-      else if ((c - 1) / 3 == i) v = SPb[((i * 3 + (c - 1) % 3) * 3 + 2) * L + lane];
-      o[(int64_t)c * 3 * D] = to_out(v * nuM, o);
-    }
+  for (int k = grp; k < 5 * N; k += ngroups) {
+    const int i = k / 5, kind = k - (k / 5) * 5;
+    const int c = kind == 0 ? 0 : (kind == 1 ? C - 1 : 1 + 3 * i + (kind - 2));
+    const T v = kind == 0 ? SPd[i * L + lane]
+                          : (kind == 1 ? SPc[(i * 3 + 2) * L + lane] : SPb[((i * 3 + kind - 2) * 3 + 2) * L + lane]);
+    TO* o = mb + ((int64_t)i * C + c) * 3 * D + 2 * D;
+    *o = to_out(v * nuM, o);
   }
 
   // ---- phase 2: main contraction ----
@@ -384,7 +440,6 @@ __global__ void __launch_bounds__(256, 2)
       eq[q] = coord ? (c - 1) / 3 : -1;
       xq[q] = coord ? (c - 1) - ((c - 1) / 3) * 3 : 0;
     }
-    const bool zc_live = !z_const || c0 == 0;  // constant z: only the value channel
 #pragma unroll 1
     for (int pass = 0; pass < 2; ++pass) {
       const int j0 = pass == 0 ? sb0 : os0, jn = pass == 0 ? sbn : osn;
@@ -393,31 +448,52 @@ __global__ void __launch_bounds__(256, 2)
       for (int a = 0; a < IB; ++a)
 #pragma unroll
         for (int q = 0; q < CB; ++q) acc[a][q] = T(0);
-      if (zc_live && jn > 0) {
-        const T* zp = Zb + (int64_t)j0 * CD + c0 * D;
+      if (z_const && c0 == 0) {  // constant z: only the value channel, z_j[0] staged
         const T* wp = W0 + (j0 * N + i0) * L + lane;
-        T zn[CB];
-#pragma unroll
-        for (int q = 0; q < CB; ++q) zn[q] = q < nc ? (z_const ? (q == 0 ? Z0c[j0 * L + lane] : T(0)) : zp[q * D]) : T(0);
 #pragma unroll 1
-        for (int jj = 0; jj < jn; ++jj) {
-          T zc[CB];
+        for (int jj = 0; jj < jn; ++jj, wp += N * L) {
+          const T z = Z0c[(j0 + jj) * L + lane];
 #pragma unroll
-          for (int q = 0; q < CB; ++q) zc[q] = zn[q];
-          if (jj + 1 < jn) {
-            zp += CD;
+          for (int a = 0; a < IB; ++a) acc[a][0] += wp[a * L] * z;
+        }
+      } else if (!z_const && jn > 0) {
+        // z_j[c0 .. c0 + CB) of the next kMsgRing senders in flight as asynchronous
+        // copies into this warp's ring; each lane copies and later reads its own feature.
+        const T* zp = Zb + (int64_t)j0 * CD + c0 * D;
+        const uint32_t ring = (uint32_t)__cvta_generic_to_shared(Ring + grp * kMsgRing * CB * L + lane);
+        auto issue = [&](int jj) {
+          if (jj < jn) {
+            const T* src = zp + (int64_t)jj * CD;
+            const uint32_t dst = ring + (uint32_t)((jj % kMsgRing) * CB * L * sizeof(T));
 #pragma unroll
             for (int q = 0; q < CB; ++q)
-              zn[q] = q < nc ? (z_const ? (q == 0 ? Z0c[(j0 + jj + 1) * L + lane] : T(0)) : zp[q * D]) : T(0);
+              if (q < nc)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst + (uint32_t)(q * L * sizeof(T))),
+                             "l"(src + (int64_t)q * D), "n"(sizeof(T))
+                             : "memory");
           }
+          asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+#pragma unroll
+        for (int u = 0; u < kMsgRing; ++u) issue(u);
+        const T* wp = W0 + (j0 * N + i0) * L + lane;
+        const T* rs = Ring + grp * kMsgRing * CB * L + lane;
+#pragma unroll 1
+        for (int jj = 0; jj < jn; ++jj, wp += N * L) {
+          asm volatile("cp.async.wait_group %0;" ::"n"(kMsgRing - 1) : "memory");
+          T zc[CB];
+          const T* slot = rs + (jj % kMsgRing) * CB * L;
+#pragma unroll
+          for (int q = 0; q < CB; ++q) zc[q] = q < nc ? slot[q * L] : T(0);
 #pragma unroll
           for (int a = 0; a < IB; ++a) {
             const T w = wp[a * L];
 #pragma unroll
             for (int q = 0; q < CB; ++q) acc[a][q] += w * zc[q];
           }
-          wp += N * L;
+          issue(jj + kMsgRing);  // refill the slot just consumed
         }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
       }
 #pragma unroll
       for (int q = 0; q < CB; ++q) {
@@ -1326,7 +1402,12 @@ cudaError_t launch_edge_hidden(const dq_handle_s& h, const FwdDims& d, const T* 
   auto kern = edge_hidden_kernel<T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<blocks(rows, kEdgesPerCta), kHiddenThreads, smem, s>>>(b.rbf, params, d.Bc, h.edges.n_all, h.edges.n_par,
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t nblk = (rows + kEdgesPerCta - 1) / kEdgesPerCta;
+  const int64_t grid = nblk < (int64_t)sms * 6 ? nblk : (int64_t)sms * 6;  // persistent, 6 CTAs per SM
+  kern<<<(unsigned)grid, kHiddenThreads, smem, s>>>(b.rbf, params, d.Bc, h.edges.n_all, h.edges.n_par,
                                                                 h.edges.n_ee, d.D, d.Q, ej, y.W1[0], y.W1[1], y.W1[2],
                                                                 y.b1[0], y.b1[1], y.b1[2], b.eh);
   return cudaGetLastError();
@@ -1356,18 +1437,18 @@ cudaError_t launch_messages_t(const dq_handle_s& h, const FwdDims& d, const T* p
   if (d.D % kMsgLanes) return cudaErrorInvalidConfiguration;
   constexpr int IB = msg_ib<T>(), CB = sizeof(T) == 4 ? 4 : 2;
   auto kern = messages_kernel<T, TO, IB, CB>;
-  bool stage_w12 = true;
-  MsgSmem lay = msg_smem_layout<T>(d.N, IB, stage_w12);
-  if (lay.total_bytes > 112 * 1024) {  // keep two CTAs per SM, else fetch w', w'' from global memory
-    stage_w12 = false;
-    lay = msg_smem_layout<T>(d.N, IB, stage_w12);
+  bool stage_w1 = true;
+  MsgSmem lay = msg_smem_layout<T>(d.N, IB, CB, stage_w1);
+  if (lay.total_bytes > 112 * 1024) {  // keep two CTAs per SM, else fetch w' from global memory
+    stage_w1 = false;
+    lay = msg_smem_layout<T>(d.N, IB, CB, stage_w1);
   }
   if (lay.total_bytes > 220 * 1024) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total_bytes);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)d.Bc, d.D / kMsgLanes);
-  kern<<<grid, 256, lay.total_bytes, s>>>(b.Z, b.z0, b.ew, b.geo, Y, h.d_pair_of, d.N, d.n_up, d.M, d.C, d.D,
-                                          h.edges.n_all, h.edges.n_ee, z_const ? 1 : 0, stage_w12 ? 1 : 0, out);
+  kern<<<grid, 32 * kMsgWarps, lay.total_bytes, s>>>(b.Z, b.z0, b.ew, b.geo, Y, h.d_pair_of, d.N, d.n_up, d.M, d.C, d.D,
+                                          h.edges.n_all, h.edges.n_ee, z_const ? 1 : 0, stage_w1 ? 1 : 0, out);
   return cudaGetLastError();
 }
 }  // namespace
