@@ -464,7 +464,8 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
     T* Gc = mode == 1 ? G + b0 * P : G;
     const T* wc = weights ? weights + b0 : nullptr;
     auto reduce = [&](const T* X, RowMap mx, const T* Y, RowMap my, int rpw, int n_o, int n_a, int64_t poff, int ld) {
-      return param_reduce<T>(X, mx, Y, my, rpw, nb, n_o, n_a, Gc, P, poff, ld, mode, part, pl.part_elems, s);
+      return param_reduce<T>(X, mx, Y, my, rpw, nb, n_o, n_a, Gc, P, poff, ld, mode, part, pl.part_elems, s,
+                             use_t3 ? h.d_status : nullptr);
     };
     // ---- forward, keeping activations ----
     FwdBuffers<T> v{};

@@ -670,11 +670,42 @@ cudaError_t param_reduce_tiled(const T* X, RowMap mx, const T* Y, RowMap my, int
   return cudaGetLastError();
 }
 
+// Row maps as (rows per walker, row pitch, walker stride), or false if the rows of a
+// walker are not equally spaced.
+inline bool walker_rows(RowMap m, int rpw, int64_t* pitch, int64_t* wstride) {
+  if (m.rows_per_seg == 1) {
+    *pitch = m.seg_stride;
+    *wstride = (int64_t)rpw * m.seg_stride;
+    return true;
+  }
+  if (m.rows_per_seg == rpw) {
+    *pitch = m.ld;
+    *wstride = m.seg_stride;
+    return true;
+  }
+  return false;
+}
+
 template <class T>
 cudaError_t param_reduce(const T* X, RowMap mx, const T* Y, RowMap my, int rpw, int64_t nw, int n_o, int n_a, T* G,
-                         int64_t P, int64_t off, int ld, int mode, T* part, int64_t part_elems, cudaStream_t s) {
+                         int64_t P, int64_t off, int ld, int mode, T* part, int64_t part_elems, cudaStream_t s,
+                         unsigned int* tc_status) {
   if (nw <= 0 || n_o <= 0 || n_a <= 0) return cudaSuccess;
   if (rpw <= 0) return cudaSuccess;
+  if constexpr (sizeof(T) == 4) {
+    int64_t xp, xs, yp, ys, splits = 0;
+    if (tc_status != nullptr && mode == 0 && Y != nullptr && n_o >= 64 && n_a >= 64 &&
+        walker_rows(mx, rpw, &xp, &xs) && walker_rows(my, rpw, &yp, &ys)) {
+      const cudaError_t e = gemm_tn_tf32x3(X, xp, xs, Y, yp, ys, rpw, nw, n_o, n_a, part, part_elems, &splits,
+                                           tc_status, s);
+      if (e == cudaSuccess && splits > 0) {
+        const int64_t per = (int64_t)n_o * n_a;
+        reduce_splits_kernel<T><<<nblocks(per, 256), 256, 0, s>>>(part, (int)splits, n_o, n_a, G, off, ld);
+        return cudaGetLastError();
+      }
+      if (e != cudaErrorInvalidValue) return e;  // unsupported layout: the CUDA-core path below
+    }
+  }
   if (Y != nullptr && n_o >= 16 && n_a >= 16)
     return param_reduce_tiled<T>(X, mx, Y, my, rpw, nw, n_o, n_a, G, P, off, ld, mode, part, part_elems, s);
   if (Y == nullptr && n_a == 1) {
@@ -758,7 +789,7 @@ cudaError_t launch_msg_bwd(const dq_handle_s& h, int64_t Bc, const T* mbar, cons
                                          T*, cudaStream_t);                                                       \
   template cudaError_t gemm_nn<T>(const T*, RowMap, const T*, T*, RowMap, int64_t, int, int, bool, cudaStream_t); \
   template cudaError_t param_reduce<T>(const T*, RowMap, const T*, RowMap, int, int64_t, int, int, T*, int64_t,   \
-                                       int64_t, int, int, T*, int64_t, cudaStream_t);                             \
+                                       int64_t, int, int, T*, int64_t, cudaStream_t, unsigned int*);              \
   template cudaError_t launch_tanh_bwd<T>(const T*, const T*, int64_t, bool, T*, cudaStream_t);                   \
   template cudaError_t launch_add_rows<T>(T*, const T*, int64_t, int, int, cudaStream_t);                         \
   template cudaError_t launch_fill_spin_rows<T>(T*, const T*, int64_t, int, int, int, cudaStream_t);              \

@@ -539,6 +539,224 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_ALLOC) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Row reductions on the tensor cores (weight gradients of the reverse pass):
+//   part[split][o][a] = sum over the split's rows r of X[r][o] * Y[r][a]
+// as 3 x TF32 products with the reduction (row) index as the MMA's K.  Rows
+// come in segments (one per walker); a K step takes 32 rows: rb rows of each
+// of 32 / rb segments.  X and Y tiles arrive by TMA as [32 rows][128 columns]
+// (rows are the slow index of both operands); the converter warps transpose
+// them into the K-major 128-byte-swizzled layout of the MMA operands while
+// splitting into TF32 high and low parts.  Work items are (o tile, a tile,
+// split); each writes its partial tile, and reduce_splits adds the splits in
+// a fixed order.
+// Warps: 0 TMA, 1 MMA, 2..5 epilogue, 6..9 converter.
+// ---------------------------------------------------------------------------
+constexpr int TN_BK = 32;                                  // rows per K step
+constexpr uint32_t TN_TILE = TC_BM * TN_BK * 4;            // 16 KB: one 128 x 32 FP32 tile
+constexpr int TN_TSTAGES = 2, TN_OSTAGES = 2;
+
+__global__ void __launch_bounds__(T3_THREADS, 1)
+    gemm_tn_tf32x3_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
+                          int64_t rps, int64_t n_seg, int rb, int n_o, int n_a, int64_t splits, int64_t kps,
+                          float* __restrict__ part, unsigned int* __restrict__ status) {
+  extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sT = smem;                                   // [tstage][X tile, Y tile] as loaded: [32 rows][128]
+  uint8_t* sO = sT + TN_TSTAGES * 2 * TN_TILE;          // [ostage][A hi, A lo, B hi, B lo] K-major, swizzled
+  uint64_t* full = reinterpret_cast<uint64_t*>(sO + TN_OSTAGES * 4 * TN_TILE);
+  uint64_t* tfree = full + TN_TSTAGES;
+  uint64_t* ready = tfree + TN_TSTAGES;
+  uint64_t* ofree = ready + TN_OSTAGES;
+  uint64_t* acc_full = ofree + TN_OSTAGES;  // [2]
+  uint64_t* acc_empty = acc_full + 2;       // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  __shared__ volatile int s_abort;
+  __shared__ float ep_stage[4][32][33];
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int sb = TN_BK / rb;
+  const int64_t rbps = (rps + rb - 1) / rb;                 // row blocks per segment
+  const int64_t ktot = ((n_seg + sb - 1) / sb) * rbps;      // K steps in all
+  const int tiles_m = (n_o + TC_BM - 1) / TC_BM, tiles_n = (n_a + TC_BN - 1) / TC_BN;
+  const int64_t n_items = (int64_t)tiles_m * tiles_n * splits;
+  auto item_range = [&](int64_t it, int& m0, int& n0, int64_t& sp, int64_t& k0, int64_t& k1) {
+    sp = it % splits;
+    const int64_t mn = it / splits;
+    m0 = (int)(mn / tiles_n) * TC_BM;
+    n0 = (int)(mn % tiles_n) * TC_BN;
+    k0 = sp * kps;
+    k1 = k0 + kps < ktot ? k0 + kps : ktot;
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TN_TSTAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&tfree[s], 4);
+    }
+    for (int s = 0; s < TN_OSTAGES; ++s) {
+      mbar_init(&ready[s], 4);
+      mbar_init(&ofree[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TC_TMEM_ALLOC)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {  // TMA producer
+      int64_t g = 0;
+      for (int64_t it = blockIdx.x; it < n_items && !s_abort; it += gridDim.x) {
+        int m0, n0;
+        int64_t sp, k0, k1;
+        item_range(it, m0, n0, sp, k0, k1);
+        for (int64_t ks = k0; ks < k1; ++ks, ++g) {
+          const int s = (int)(g % TN_TSTAGES);
+          const int64_t u = g / TN_TSTAGES;
+          if (u >= 1 && !mbar_wait(&tfree[s], (uint32_t)((u - 1) & 1))) {
+            s_abort = 1;
+            break;
+          }
+          const int seg = (int)((ks / rbps) * sb), r0 = (int)((ks % rbps) * rb);
+          mbar_expect_tx(&full[s], 2 * TN_TILE);
+          tma_load_3d(sT + (s * 2 + 0) * TN_TILE, &tmX, m0, r0, seg, &full[s]);
+          tma_load_3d(sT + (s * 2 + 1) * TN_TILE, &tmY, n0, r0, seg, &full[s]);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMA issuer
+      constexpr uint32_t idesc = t3_idesc(TC_BM, TC_BN);
+      int64_t g = 0, lt = 0;
+      for (int64_t it = blockIdx.x; it < n_items && !s_abort; it += gridDim.x, ++lt) {
+        int m0, n0;
+        int64_t sp, k0, k1;
+        item_range(it, m0, n0, sp, k0, k1);
+        const int a = (int)(lt & 1);
+        const int64_t v = lt >> 1;
+        if (v >= 1 && !mbar_wait(&acc_empty[a], (uint32_t)((v - 1) & 1))) {
+          s_abort = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(a * TC_TMEM_COLS);
+        bool ok = true;
+        for (int64_t ks = k0; ks < k1; ++ks, ++g) {
+          const int s = (int)(g % TN_OSTAGES);
+          if (!mbar_wait(&ready[s], (uint32_t)((g / TN_OSTAGES) & 1))) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ah = smem_u32(sO + (s * 4 + 0) * TN_TILE), al = smem_u32(sO + (s * 4 + 1) * TN_TILE);
+          const uint32_t bh = smem_u32(sO + (s * 4 + 2) * TN_TILE), bl = smem_u32(sO + (s * 4 + 3) * TN_TILE);
+#pragma unroll
+          for (int kk = 0; kk < TN_BK / 8; ++kk) {
+            const uint32_t o = kk * 32;
+            umma_tf32(d, sw128_desc(ah + o), sw128_desc(bh + o), idesc, (ks > k0 || kk) ? 1u : 0u);
+            umma_tf32(d, sw128_desc(ah + o), sw128_desc(bl + o), idesc, 1u);
+            umma_tf32(d, sw128_desc(al + o), sw128_desc(bh + o), idesc, 1u);
+          }
+          umma_commit(&ofree[s]);
+        }
+        if (!ok) {
+          s_abort = 1;
+          break;
+        }
+        umma_commit(&acc_full[a]);
+      }
+    }
+  } else if (warp >= 6) {
+    // Converter warps: warp w transposes columns 32 w .. 32 w + 31 of both tiles.
+    const int w = warp - 6;
+    const int col = 32 * w + lane;
+    int64_t g = 0;
+    for (int64_t it = blockIdx.x; it < n_items && !s_abort; it += gridDim.x) {
+      int m0, n0;
+      int64_t sp, k0, k1;
+      item_range(it, m0, n0, sp, k0, k1);
+      for (int64_t ks = k0; ks < k1; ++ks, ++g) {
+        const int ts = (int)(g % TN_TSTAGES), os = (int)(g % TN_OSTAGES);
+        if (!mbar_wait(&full[ts], (uint32_t)((g / TN_TSTAGES) & 1)) ||
+            (g >= TN_OSTAGES && !mbar_wait(&ofree[os], (uint32_t)((g / TN_OSTAGES - 1) & 1)))) {
+          s_abort = 1;
+          break;
+        }
+#pragma unroll
+        for (int op = 0; op < 2; ++op) {  // X -> A, Y -> B
+          const float* src = reinterpret_cast<const float*>(sT + (ts * 2 + op) * TN_TILE);
+          uint8_t* hi = sO + (os * 4 + 2 * op) * TN_TILE;
+          uint8_t* lo = hi + TN_TILE;
+#pragma unroll
+          for (int rq = 0; rq < TN_BK / 4; ++rq) {
+            float4 h, l;
+            float x;
+            x = src[(4 * rq + 0) * TC_BM + col]; h.x = tf32_rn(x); l.x = tf32_rn(x - h.x);
+            x = src[(4 * rq + 1) * TC_BM + col]; h.y = tf32_rn(x); l.y = tf32_rn(x - h.y);
+            x = src[(4 * rq + 2) * TC_BM + col]; h.z = tf32_rn(x); l.z = tf32_rn(x - h.z);
+            x = src[(4 * rq + 3) * TC_BM + col]; h.w = tf32_rn(x); l.w = tf32_rn(x - h.w);
+            // K-major, 128-byte swizzle: row col, 16-byte chunk rq at chunk rq ^ (col % 8)
+            const uint32_t off = (uint32_t)col * 128u + ((uint32_t)(rq ^ (col & 7)) << 4);
+            *reinterpret_cast<float4*>(hi + off) = h;
+            *reinterpret_cast<float4*>(lo + off) = l;
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&ready[os])) : "memory");
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree[ts])) : "memory");
+        }
+      }
+    }
+  } else {
+    // Epilogue warps 2..5: rows o, columns a of the partial tile
+    const int q = warp % 4;
+    float(*st)[33] = ep_stage[warp - 2];
+    int64_t lt = 0;
+    for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x, ++lt) {
+      int m0, n0;
+      int64_t sp, k0, k1;
+      item_range(it, m0, n0, sp, k0, k1);
+      const int a = (int)(lt & 1);
+      const int64_t v = lt >> 1;
+      if (!mbar_wait(&acc_full[a], (uint32_t)(v & 1))) {
+        s_abort = 1;
+        break;
+      }
+      tc_fence_after();
+      const int o = m0 + q * 32 + lane;
+      float* yrow = o < n_o ? part + (sp * n_o + o) * (int64_t)n_a + n0 : nullptr;
+      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+        uint32_t vv[32];
+        tmem_ld32(tmem + (uint32_t)(a * TC_TMEM_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, vv);
+        store_block_32x32(vv, st, lane, yrow ? yrow + c0 : nullptr, false, 0.f, n0 + c0 + lane < n_a);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[a])) : "memory");
+    }
+  }
+  __syncthreads();
+  if (s_abort && threadIdx.x == 0) atomicOr(status, (unsigned)DQ_FLAG_TIMEOUT);
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_ALLOC) : "memory");
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link).
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -648,6 +866,60 @@ cudaError_t gemm_tf32x3_tc_seg(const float* X, int64_t seg_rows, int64_t n_seg, 
                                                                 bias_period, Y, ldy, y_seg_stride,
                                                                 accumulate ? 1 : 0, status);
   return cudaGetLastError();
+}
+
+// FP32 rows [n_seg][rps] x cols, dims {cols, rps, n_seg}, box {128, rb, 32 / rb}, no swizzle
+bool make_map_rows_f32(CUtensorMap* m, const void* base, int64_t rps, int64_t n_seg, int cols, int64_t pitch,
+                       int64_t seg_stride, int rb) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rps, (cuuint64_t)n_seg};
+  const cuuint64_t strides[2] = {(cuuint64_t)pitch * 4, (cuuint64_t)seg_stride * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)TC_BM, (cuuint32_t)rb, (cuuint32_t)(TN_BK / rb)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+constexpr size_t tn_smem_bytes() {
+  return 1024 + TN_TSTAGES * 2 * TN_TILE + TN_OSTAGES * 4 * TN_TILE + (2 * TN_TSTAGES + 2 * TN_OSTAGES + 4) * 8 + 16;
+}
+
+cudaError_t gemm_tn_tf32x3(const float* X, int64_t x_pitch, int64_t x_seg_stride, const float* Y, int64_t y_pitch,
+                           int64_t y_seg_stride, int64_t rps, int64_t n_seg, int n_o, int n_a, float* part,
+                           int64_t part_elems, int64_t* splits_out, unsigned int* status, cudaStream_t s) {
+  *splits_out = 0;
+  if (rps <= 0 || n_seg <= 0 || n_o <= 0 || n_a <= 0) return cudaSuccess;
+  if (x_pitch % 4 || y_pitch % 4 || x_seg_stride % 4 || y_seg_stride % 4 || (uintptr_t)X % 16 || (uintptr_t)Y % 16 ||
+      rps > (int64_t)INT32_MAX || n_seg > (int64_t)INT32_MAX)
+    return cudaErrorInvalidValue;
+  int rb = TN_BK;  // short segments: several per K step
+  while (rb > 1 && rb / 2 >= rps) rb /= 2;
+  CUtensorMap mx, my;
+  if (!make_map_rows_f32(&mx, X, rps, n_seg, n_o, x_pitch, x_seg_stride, rb) ||
+      !make_map_rows_f32(&my, Y, rps, n_seg, n_a, y_pitch, y_seg_stride, rb))
+    return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = (int64_t)((n_o + TC_BM - 1) / TC_BM) * ((n_a + TC_BN - 1) / TC_BN);
+  const int64_t ktot = ((n_seg + TN_BK / rb - 1) / (TN_BK / rb)) * ((rps + rb - 1) / rb);
+  int64_t splits = (sms + tiles - 1) / tiles;  // about one work item per SM
+  if (splits > ktot) splits = ktot;
+  if (splits * n_o * n_a > part_elems) splits = part_elems / ((int64_t)n_o * n_a);
+  if (splits < 1) return cudaErrorInvalidValue;
+  const int64_t kps = (ktot + splits - 1) / splits;
+  splits = (ktot + kps - 1) / kps;  // every split has at least one K step
+  const size_t smem = tn_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(gemm_tn_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t items = tiles * splits;
+  const int64_t grid = items < sms ? items : sms;
+  gemm_tn_tf32x3_kernel<<<(unsigned)grid, T3_THREADS, smem, s>>>(mx, my, rps, n_seg, rb, n_o, n_a, splits, kps, part,
+                                                                status);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) *splits_out = splits;
+  return e;
 }
 
 cudaError_t gemm_tf32x3_tc(const float* X, int64_t rows, int K, int64_t ldx, const float* Wbig, const float* Wsmall,

@@ -146,3 +146,44 @@ def test_full_batch_per_walker_gradient_n2_fp32():
     jv = oracle.Oracle(wl.system, wl.cfg).grad_jvp(theta.astype(np.float64), r[sel].astype(np.float64), dirs)
     rel = np.abs(Gs @ dirs.T - jv) / (np.abs(Gs) @ np.abs(dirs.T))
     assert np.all(rel <= 1e-3), rel
+
+
+def test_weighted_mode_fp32_equals_weighted_sum_of_per_walker():
+    """Summed (weighted) mode of the FP32 path, whose weight-matrix blocks are
+    row reductions on the tensor cores (3 x TF32 split, split over walkers),
+    against the weighted sum of the per-walker gradients (CUDA-core path) over
+    1024 N2 walkers.  Both sides sum FP32 products of the same activations, so
+    on the matrix blocks they differ by rounding only: |dg| <= 5e-5 sum_b
+    |w_b g_b| (a transposed or misplaced operand gives errors of order
+    sum_b |w_b g_b|).  Bias blocks are column sums whose per-walker terms can
+    cancel, so sum_b |w_b g_b| is no scale for their rounding; they are checked
+    against the FP64 path elsewhere and only reported here."""
+    wl = fx.workload("n2_fp32")
+    h = _handle(wl.system, wl.cfg, "fp32")
+    B = 1024
+    th = torch.tensor(fx.init_params(wl.system, wl.cfg, wl.param_seed), dtype=torch.float32, device="cuda:0")
+    r = torch.tensor(fx.init_walkers(wl.system, B, wl.walker_seed), dtype=torch.float32, device="cuda:0")
+    w = torch.tensor(np.random.default_rng(11).uniform(-1.0, 1.0, B), dtype=torch.float32, device="cuda:0")
+    g0 = h.grad_logpsi(th, r, w, mode=0).double()
+    G = h.grad_logpsi(th, r, mode=1)
+    ref = torch.zeros_like(g0)
+    scale = torch.zeros_like(g0)
+    for b0 in range(0, B, 256):
+        Gb = G[b0:b0 + 256].double()
+        wb = w[b0:b0 + 256].double()[:, None]
+        ref += (wb * Gb).sum(0)
+        scale += (wb.abs() * Gb.abs()).sum(0)
+    del G
+    rel = ((g0 - ref).abs() / (scale + 1e-30)).cpu().numpy()
+    worst_matrix, worst_other, o = 0.0, 0.0, 0
+    for name, shape, _ in fx.param_layout(wl.system, wl.cfg):
+        n = int(np.prod(shape))
+        m = float(rel[o:o + n].max())
+        if name.startswith(("W_h", "W_g", "W2_", "W_o_")) or name == "W_J1":
+            worst_matrix = max(worst_matrix, m)
+        else:
+            worst_other = max(worst_other, m)
+        o += n
+    print(f"N2 FP32 weighted vs per-walker sum: max |dg| / sum|w g| {worst_matrix:.2e} (weight matrices), "
+          f"{worst_other:.2e} (other blocks)")
+    assert worst_matrix <= 5e-5
