@@ -198,7 +198,7 @@ def peaks():
 # dram__bytes_read.sum + dram__bytes_write.sum of the jet message kernel (layer >= 1 launch) per walker,
 # from the ncu capture summarised in profiles/messages_kernel_n2_512.md (N2, FP32); None once the kernel
 # has changed since that capture.
-MSG_DRAM_BYTES_PER_WALKER = (276.438016e6 + 428.677120e6) / 512
+MSG_DRAM_BYTES_PER_WALKER = (276.218112e6 + 431.757824e6) / 512
 
 
 def roofline_for(kind, ms, n, wl, chunk, pk, how):

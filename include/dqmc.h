@@ -215,7 +215,9 @@ dq_status dq_last_device_status(dq_handle h, void* stream, uint32_t* flags);
  * (then cleared; synchronises `stream`).  In the FP32 modes every matrix is
  * first factorised in FP32 and near-nodal ones are redone in FP64, which this
  * counts: value-only calls (ansatz_eval, mcmc_step) when the condition
- * estimate of the row-equilibrated matrix exceeds 1000; local_energy, for
+ * estimate of the row-equilibrated matrix exceeds 10000 (below that the FP32
+ * log|det| is corrected by the trace of the factorisation residual against
+ * the FP32 inverse); local_energy, for
  * spin blocks of at most 8 electrons, when it exceeds 2000 (below that the
  * FP32 inverse is refined once in double-float).  local_energy with larger
  * spin blocks takes FP64 for every matrix (not counted).  Always 0 in FP64
@@ -238,7 +240,7 @@ dq_status dq_test_gemm_bf16(const void* X, int64_t rows, int32_t K, int64_t ldx,
  * when r % bias_period == 0), computed as three TF32 tensor-core products of
  * the operands split into TF32 high and low parts (x_hi w_hi + x_hi w_lo +
  * x_lo w_hi; relative error about 2^-21 of sum_k |x_k w_k|).  X FP32 device
- * [rows][ldx], K a multiple of 32, ldx a multiple of 4, X and W 16-byte
+ * [rows][ldx], K a multiple of 4, ldx a multiple of 4, X and W 16-byte
  * aligned; W FP32 device [n_out][K]; wsplit: device FP32 scratch of
  * 2 * n_out * K elements that receives the split W; Y FP32 [rows][ldy];
  * status as for dq_test_gemm_bf16.  Enqueued on `stream`. */

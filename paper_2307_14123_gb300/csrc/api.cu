@@ -419,7 +419,7 @@ GradPlan plan_grad(const dq_handle_s& h, int64_t Bc, size_t elem) {
   p.part_elems = 64 * blk;
   p.part = take(p.part_elems * elem);
   p.wt3 = take(use_tf32x3(h) ? t3_weight_floats(h) * 4 : 0);
-  p.wt3t = take(use_tf32x3(h) ? (size_t)L * kT3PerLayer * D * D * 4 : 0);  // transposed splits (reverse pass)
+  p.wt3t = take(use_tf32x3(h) ? t3_weight_floats(h) * 4 : 0);  // transposed splits (reverse pass)
   p.total = o;
   return p;
 }
@@ -453,6 +453,9 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
         DQ_CU(split_tf32_t(params + y.W_h, D, D, w3t.wh(l, 0), w3t.wh(l, 1), s));
         for (int t = 0; t < 3; ++t) DQ_CU(split_tf32_t(params + y.W2[t], D, D, w3t.w2(l, t, 0), w3t.w2(l, t, 1), s));
       }
+      const int nsp[2] = {h.n_up, h.n_dn};
+      for (int sg = 0; sg < 2; ++sg)
+        if (nsp[sg] > 0) DQ_CU(split_tf32_t(params + off.W_o[sg], K * nsp[sg], D, w3t.wo(sg, 0), w3t.wo(sg, 1), s));
     }
   }
   const int ns[2] = {h.n_up, h.n_dn}, i0[2] = {0, h.n_up};
@@ -577,7 +580,14 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
       const T* pb = phibar + (int64_t)i0[sg] * Wo;
       DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(pb, mp, F(L) + (int64_t)i0[sg] * D, mf, ns[sg], K * ns[sg], D, off.W_o[sg], D));
       DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(pb, mp, nullptr, rm(1), ns[sg], K * ns[sg], 1, off.b_o[sg], 1));
-      DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(pb, mp, params + off.W_o[sg], fbar + (int64_t)i0[sg] * D, mf,
+      if (use_t3)
+        DQ_LAUNCH(h, PK_BWD_GEMM,
+                  gemm_tf32x3_tc_seg(reinterpret_cast<const float*>(pb), ns[sg], nb, (int64_t)N * Wo, K * ns[sg], Wo,
+                                     w3t.wo(sg, 0), w3t.wo(sg, 1), D, nullptr, 1,
+                                     reinterpret_cast<float*>(fbar) + (int64_t)i0[sg] * D, D, (int64_t)N * D,
+                                     h.d_status, s));
+      else
+        DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(pb, mp, params + off.W_o[sg], fbar + (int64_t)i0[sg] * D, mf,
                                            nb * ns[sg], D, K * ns[sg], false, s));
     }
     if (h.use_jastrow) DQ_LAUNCH(h, PK_BWD_UPDATE, launch_add_rows<T>(fbar, sbar, nb, N, D, s));

@@ -115,7 +115,7 @@ cudaError_t gemm_bf16_tc(const void* X, int64_t rows, int K, int64_t ldx, const 
                          int bias_period, float* Y, int64_t ldy, unsigned int* status, cudaStream_t s);
 
 // FP32-accurate tensor-core GEMM (3 x TF32 split, gemm_tc.cu): X FP32 [rows][K]
-// (K % 32 == 0), W pre-split by split_tf32 into TF32 big and small parts.
+// (K % 4 == 0), W pre-split by split_tf32 into TF32 big and small parts.
 cudaError_t split_tf32(const float* W, float* big, float* small, int64_t n, cudaStream_t s);
 cudaError_t gemm_tf32x3_tc(const float* X, int64_t rows, int K, int64_t ldx, const float* Wbig, const float* Wsmall,
                            int n_out, const float* bias, int bias_period, float* Y, int64_t ldy, unsigned int* status,

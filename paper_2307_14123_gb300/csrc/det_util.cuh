@@ -88,5 +88,52 @@ __device__ void warp_inverse(const S* LU, const int* perm, int n, int lane, S* A
   __syncwarp();
 }
 
+// Double-float arithmetic (an FP32 pair hi + lo) from error-free
+// transformations: TwoSum (Knuth) and TwoProd via a fused multiply-add
+// (Ogita, Rump, Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput.
+// 26, 2005).  Explicit round-to-nearest intrinsics keep the compiler from
+// contracting the operations that must stay exact.
+struct dfloat {
+  float hi, lo;
+};
+__device__ __forceinline__ dfloat two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dfloat quick_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+  dfloat s = two_sum(a.hi, b.hi);
+  return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return quick_two_sum(p, e);
+}
+// sum_l a[l] b[l] as a double-float pair (Dot2)
+__device__ __forceinline__ dfloat dot2_step(dfloat acc, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const dfloat s = two_sum(acc.hi, p);
+  return {s.hi, __fadd_rn(acc.lo, __fadd_rn(s.lo, e))};
+}
+
+__device__ __forceinline__ dfloat warp_sum_df(dfloat v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dfloat w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v = df_add(v, w);
+  }
+  return v;
+}
+
 }  // namespace
 }  // namespace dq

@@ -622,7 +622,7 @@ __global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __r
 // FP64 mode every step is FP64.
 // ---------------------------------------------------------------------------
 #ifndef DQ_KAPPA_FP32_VALUE
-#define DQ_KAPPA_FP32_VALUE 1000.0f  // value-only log|det| in FP32 below this
+#define DQ_KAPPA_FP32_VALUE 10000.0f  // value-only log|det| in FP32 (corrected) below this
 #endif
 
 // Determinant derivatives: for every tangent t (3N coordinates, then the
@@ -676,44 +676,6 @@ __device__ double det_tangents(const T* phib, const T* env, const T* jenv, const
   return lap;
 }
 
-// Double-float arithmetic (an FP32 pair hi + lo) from error-free
-// transformations: TwoSum (Knuth) and TwoProd via a fused multiply-add
-// (Ogita, Rump, Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput.
-// 26, 2005).  Explicit round-to-nearest intrinsics keep the compiler from
-// contracting the operations that must stay exact.
-struct dfloat {
-  float hi, lo;
-};
-__device__ __forceinline__ dfloat two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return {s, e};
-}
-__device__ __forceinline__ dfloat quick_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
-  dfloat s = two_sum(a.hi, b.hi);
-  return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
-  return quick_two_sum(p, e);
-}
-__device__ __forceinline__ dfloat warp_sum_df(dfloat v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    dfloat w;
-    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
-    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
-    v = df_add(v, w);
-  }
-  return v;
-}
 
 // Determinant derivatives in double-float: A^-1 = Ahi + Alo (split from the
 // FP64 inverse), d_t A exact in FP32 (it comes from the FP32 network), each
@@ -872,6 +834,23 @@ __global__ void __launch_bounds__(128)
     } else {
       fp64 = true;
     }
+    if constexpr (sizeof(T) == 4) {
+      if (!fp64) {
+        // log|det A| = log|det LU| + tr(A^-1 P^T (P A - L U)) to first order in the backward
+        // error of the FP32 factorisation; entry (r, c) of P A - L U pairs with A^-1[c][perm[r]].
+        float part = 0.f;
+        for (int q = lane; q < n * n; q += 32) {
+          const int r = q / n, c = q - (q / n) * n, mm = r < c ? r : c;
+          const int ar = perm[r] * n + c;
+          dfloat acc = {-(phi0[ar] * env[ar]), 0.f};
+          for (int m = 0; m <= mm; ++m) acc = dot2_step(acc, m == r ? 1.f : LUt[r * n + m], LUt[m * n + c]);
+          part = fmaf(Ainvt[c * n + perm[r]], -(acc.hi + acc.lo), part);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        logabs += (double)part;
+      }
+    }
   }
   if (fp64) {
     if (sizeof(T) == 4 && !jets && lane == 0) atomicAdd(n_fp64, 1ull);
@@ -930,14 +909,6 @@ __global__ void __launch_bounds__(128)
 #define DQ_KAPPA_FP32_JET 2000.0f
 #endif
 constexpr int kDetNR = 8;
-
-// sum_l a[l] b[l] as a double-float pair (Dot2)
-__device__ __forceinline__ dfloat dot2_step(dfloat acc, float a, float b) {
-  const float p = __fmul_rn(a, b);
-  const float e = __fmaf_rn(a, b, -p);
-  const dfloat s = two_sum(acc.hi, p);
-  return {s.hi, __fadd_rn(acc.lo, __fadd_rn(s.lo, e))};
-}
 
 __host__ __device__ inline size_t det_jets_smem_per_warp(int nmax, int N3) {
   const size_t nn = (size_t)nmax * nmax;

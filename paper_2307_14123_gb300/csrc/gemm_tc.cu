@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   __shared__ float ep_stage[4][32][33];  // epilogue transpose, one block per epilogue warp
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int nk = K / T3_BK;
+  const int nk = (K + T3_BK - 1) / T3_BK;  // a ragged last K block reads zeros past K
   const int n_tiles_n = (n_out + TC_BN - 1) / TC_BN;
   // A tile holds TC_BM rows: rb rows of each of sb = TC_BM / rb segments (rb < TC_BM only if
   // seg_rows <= rb), or a TC_BM-row block of one segment.
@@ -844,7 +844,7 @@ cudaError_t gemm_tf32x3_tc_seg(const float* X, int64_t seg_rows, int64_t n_seg, 
                                int bias_period, float* Y, int64_t ldy, int64_t y_seg_stride, unsigned int* status,
                                cudaStream_t s, bool accumulate) {
   if (seg_rows <= 0 || n_seg <= 0 || n_out <= 0) return cudaSuccess;
-  if (K % T3_BK || ldx % 4 || x_seg_stride % 4 || (uintptr_t)X % 16 || (uintptr_t)Wbig % 16 ||
+  if (K % 4 || ldx % 4 || x_seg_stride % 4 || (uintptr_t)X % 16 || (uintptr_t)Wbig % 16 ||
       (uintptr_t)Wsmall % 16 || bias_period <= 0 || seg_rows > (int64_t)INT32_MAX || n_seg > (int64_t)INT32_MAX)
     return cudaErrorInvalidValue;
   int rb = TC_BM;  // short segments: several per tile, rb (a power of two >= 8) rows each
