@@ -155,9 +155,31 @@ __global__ void __launch_bounds__(128)
       warp_inverse<T>(LUt, perm, n, lane, Ainvt);
       T imax = 0;
       for (int q = lane; q < n * n; q += 32) imax = max(imax, (T)fabs(Ainvt[q]) * rmax[q % n]);
-      fp64 = !(T(n) * warp_max(imax) <= T(1000));
+      fp64 = !(T(n) * warp_max(imax) <= T(10000));
     } else {
       fp64 = true;
+    }
+    if constexpr (sizeof(T) == 4) {
+      if (!fp64) {
+        // one refinement step X = X0 + X0 (I - A X0), the residual as a compensated
+        // product (Dot2) into LUt, the refined inverse (error about (kappa u)^2) into Ainvt
+        for (int q = lane; q < n * n; q += 32) {
+          const int a = q / n, m = q % n;
+          dfloat acc = {a == m ? -1.f : 0.f, 0.f};
+          for (int l = 0; l < n; ++l) acc = dot2_step(acc, phi0[a * n + l] * env[a * n + l], Ainvt[l * n + m]);
+          LUt[q] = -(acc.hi + acc.lo);
+        }
+        __syncwarp();
+        for (int q = lane; q < n * n; q += 32) {  // rmax (free now) holds the refined inverse
+          const int a = q / n, m = q % n;
+          float c = 0.f;
+          for (int l = 0; l < n; ++l) c = fmaf(Ainvt[a * n + l], LUt[l * n + m], c);
+          rmax[q] = Ainvt[q] + c;
+        }
+        __syncwarp();
+        for (int q = lane; q < n * n; q += 32) Ainvt[q] = rmax[q];
+        __syncwarp();
+      }
     }
   }
   if (fp64 && bp != 0.0) {
@@ -534,6 +556,12 @@ __global__ void __launch_bounds__(256)
                    const int* __restrict__ pair_of, int N, int n_up,
                    int M, int D, int E, int n_ee, int z_const, T* __restrict__ zbar, T* __restrict__ wbar,
                    T* __restrict__ ybar) {
+  extern __shared__ int msg_bwd_smem[];
+  int* Po = msg_bwd_smem;   // [N][N] pair index
+  int* Pij = Po + N * N;    // [n_ee][2] electrons of a pair
+  for (int k = threadIdx.x; k < N * N; k += blockDim.x) Po[k] = pair_of[k];
+  for (int k = threadIdx.x; k < 2 * n_ee; k += blockDim.x) Pij[k] = pair_ij[k];
+  __syncthreads();
   const int64_t b = blockIdx.x;
   const int d = blockIdx.y * 32 + threadIdx.x % 32;
   const int grp = threadIdx.x / 32, ngrp = blockDim.x / 32;
@@ -548,18 +576,20 @@ __global__ void __launch_bounds__(256)
     const bool same = (i < n_up) == (j < n_up);
     return same ? mb[(int64_t)i * 3 * D + d] * nu_s(i) : mb[(int64_t)i * 3 * D + D + d] * nu_o(i);
   };
-  // zbar_j
+  // zbar_j (independent loads, several in flight)
   for (int j = grp; j < N; j += ngrp) {
     T acc = 0;
+#pragma unroll 4
     for (int i = 0; i < N; ++i) {
       if (i == j) continue;
-      acc += m_in(i, j) * ewb[(int64_t)pair_of[i * N + j] * D + d];
+      acc += m_in(i, j) * ewb[(int64_t)Po[i * N + j] * D + d];
     }
     zbar[(b * N + j) * D + d] = acc;
   }
   // wbar for e-e pairs
+#pragma unroll 4
   for (int e = grp; e < n_ee; e += ngrp) {
-    const int i = pair_ij[2 * e], j = pair_ij[2 * e + 1];
+    const int i = Pij[2 * e], j = Pij[2 * e + 1];
     wbar[(b * E + e) * D + d] = m_in(i, j) * zv(j) + m_in(j, i) * zv(i);
   }
   // electron-nucleus edges and Ybar
@@ -777,7 +807,8 @@ template <class T>
 cudaError_t launch_msg_bwd(const dq_handle_s& h, int64_t Bc, const T* mbar, const T* Z, const T* z0, const T* ew,
                            const T* Y, bool z_const, T* zbar, T* wbar, T* ybar, cudaStream_t s) {
   dim3 grid((unsigned)Bc, nblocks(h.D, 32));
-  msg_bwd_kernel<T><<<grid, 256, 0, s>>>(mbar, Z, z0, ew, Y, h.d_pair_ij, h.d_pair_of, h.N, h.n_up, h.M, h.D, h.edges.n_all,
+  const size_t smem = (size_t)(h.N * h.N + 2 * h.edges.n_ee) * sizeof(int);
+  msg_bwd_kernel<T><<<grid, 256, smem, s>>>(mbar, Z, z0, ew, Y, h.d_pair_ij, h.d_pair_of, h.N, h.n_up, h.M, h.D, h.edges.n_all,
                                           h.edges.n_ee, z_const ? 1 : 0, zbar, wbar, ybar);
   return cudaGetLastError();
 }
