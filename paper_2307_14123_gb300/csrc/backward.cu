@@ -556,26 +556,33 @@ __global__ void __launch_bounds__(256)
                    const int* __restrict__ pair_of, int N, int n_up,
                    int M, int D, int E, int n_ee, int z_const, T* __restrict__ zbar, T* __restrict__ wbar,
                    T* __restrict__ ybar) {
-  extern __shared__ int msg_bwd_smem[];
-  int* Po = msg_bwd_smem;   // [N][N] pair index
-  int* Pij = Po + N * N;    // [n_ee][2] electrons of a pair
-  for (int k = threadIdx.x; k < N * N; k += blockDim.x) Po[k] = pair_of[k];
-  for (int k = threadIdx.x; k < 2 * n_ee; k += blockDim.x) Pij[k] = pair_ij[k];
-  __syncthreads();
+  extern __shared__ __align__(16) unsigned char msg_bwd_raw[];
   const int64_t b = blockIdx.x;
-  const int d = blockIdx.y * 32 + threadIdx.x % 32;
+  const int L = 32;
+  T* Ms = reinterpret_cast<T*>(msg_bwd_raw);  // [N][2][L] normalised same / opposite message adjoints
+  T* Zs = Ms + N * 2 * L;                      // [N][L] z_j
+  int* Po = reinterpret_cast<int*>(Zs + N * L);  // [N][N] pair index
+  int* Pij = Po + N * N;                          // [n_ee][2] electrons of a pair
+  const int dl = threadIdx.x % 32, d = blockIdx.y * 32 + dl;
   const int grp = threadIdx.x / 32, ngrp = blockDim.x / 32;
-  if (d >= D) return;
   const int n_dn = N - n_up;
-  auto nu_s = [&](int i) { const int ns = i < n_up ? n_up : n_dn; return T(1) / T(ns - 1 > 1 ? ns - 1 : 1); };
-  auto nu_o = [&](int i) { const int no = i < n_up ? n_dn : n_up; return T(1) / T(no > 1 ? no : 1); };
   const T* mb = mbar + b * N * 3 * D;
   const T* ewb = ew + b * E * D;
-  auto zv = [&](int j) { return z_const ? z0[(j < n_up ? 0 : 1) * D + d] : Z[(b * N + j) * D + d]; };
+  for (int k = threadIdx.x; k < N * N; k += blockDim.x) Po[k] = pair_of[k];
+  for (int k = threadIdx.x; k < 2 * n_ee; k += blockDim.x) Pij[k] = pair_ij[k];
+  for (int i = grp; i < N; i += ngrp) {
+    const int ns = i < n_up ? n_up : n_dn, no = N - ns;
+    const T nus = T(1) / T(ns - 1 > 1 ? ns - 1 : 1), nuo = T(1) / T(no > 1 ? no : 1);
+    Ms[(i * 2 + 0) * L + dl] = d < D ? mb[(int64_t)i * 3 * D + d] * nus : T(0);
+    Ms[(i * 2 + 1) * L + dl] = d < D ? mb[(int64_t)i * 3 * D + D + d] * nuo : T(0);
+    Zs[i * L + dl] = d >= D ? T(0) : (z_const ? z0[(i < n_up ? 0 : 1) * D + d] : Z[(b * N + i) * D + d]);
+  }
+  __syncthreads();
+  if (d >= D) return;
   auto m_in = [&](int i, int j) {  // mbar_i^t for the edge (i, j), normalised
-    const bool same = (i < n_up) == (j < n_up);
-    return same ? mb[(int64_t)i * 3 * D + d] * nu_s(i) : mb[(int64_t)i * 3 * D + D + d] * nu_o(i);
+    return Ms[(i * 2 + ((i < n_up) == (j < n_up) ? 0 : 1)) * L + dl];
   };
+  auto zv = [&](int j) { return Zs[j * L + dl]; };
   // zbar_j (independent loads, several in flight)
   for (int j = grp; j < N; j += ngrp) {
     T acc = 0;
@@ -724,7 +731,7 @@ cudaError_t param_reduce(const T* X, RowMap mx, const T* Y, RowMap my, int rpw, 
   if (rpw <= 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
     int64_t xp, xs, yp, ys, splits = 0;
-    if (tc_status != nullptr && mode == 0 && Y != nullptr && n_o >= 64 && n_a >= 64 &&
+    if (tc_status != nullptr && mode == 0 && Y != nullptr && n_o >= 64 && n_a >= 16 &&
         walker_rows(mx, rpw, &xp, &xs) && walker_rows(my, rpw, &yp, &ys)) {
       const cudaError_t e = gemm_tn_tf32x3(X, xp, xs, Y, yp, ys, rpw, nw, n_o, n_a, part, part_elems, &splits,
                                            tc_status, s);
@@ -807,7 +814,7 @@ template <class T>
 cudaError_t launch_msg_bwd(const dq_handle_s& h, int64_t Bc, const T* mbar, const T* Z, const T* z0, const T* ew,
                            const T* Y, bool z_const, T* zbar, T* wbar, T* ybar, cudaStream_t s) {
   dim3 grid((unsigned)Bc, nblocks(h.D, 32));
-  const size_t smem = (size_t)(h.N * h.N + 2 * h.edges.n_ee) * sizeof(int);
+  const size_t smem = (size_t)h.N * 3 * 32 * sizeof(T) + (size_t)(h.N * h.N + 2 * h.edges.n_ee) * sizeof(int);
   msg_bwd_kernel<T><<<grid, 256, smem, s>>>(mbar, Z, z0, ew, Y, h.d_pair_ij, h.d_pair_of, h.N, h.n_up, h.M, h.D, h.edges.n_all,
                                           h.edges.n_ee, z_const ? 1 : 0, zbar, wbar, ybar);
   return cudaGetLastError();

@@ -1197,6 +1197,7 @@ __global__ void __launch_bounds__(kCombineThreads)
   double* gsq = wp + K;                              // [K] |grad l_p|^2
   double* td = gsq + K;                              // [3][D] Jastrow: w t, w t', w t''
   double* red = td + 3 * D;                          // [32]
+  double* gJk = red + 32;                            // [3N] Jastrow gradient components
   __shared__ double s_scalar[4];
   const int64_t b = blockIdx.x;
   const int tid = threadIdx.x;
@@ -1278,22 +1279,37 @@ __global__ void __launch_bounds__(kCombineThreads)
     gsq[p] = acc;
   }
   __syncthreads();
-  // gradient components and the Jastrow Laplacian term
-  double g2part = 0.0, lJpart = 0.0;
-  for (int k = tid; k < N3; k += kCombineThreads) {
-    double g = 0.0;
-    for (int p = 0; p < K; ++p) g += wp[p] * (dp(0, p)[2 + k] + dp(1, p)[2 + k]);
-    if (use_jastrow) {
+  // Jastrow gradient components and Laplacian term: one warp per coordinate k, lanes over
+  // features (coalesced rows of the Jastrow-input jets)
+  double lJpart = 0.0;
+  if (use_jastrow) {
+    const int wq = tid / 32, ln = tid % 32;
+    for (int k = wq; k < N3; k += kCombineThreads / 32) {
       const T* row = jb + (int64_t)(1 + k) * D;
       double gj = 0.0, lj = 0.0;
-      for (int a = 0; a < D; ++a) {
+      for (int a = ln; a < D; a += 32) {
         const double h = (double)row[a];
         gj += td[D + a] * h;
         lj += td[2 * D + a] * h * h;
       }
-      g += gj;
-      lJpart += lj;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        gj += __shfl_xor_sync(0xffffffffu, gj, o);
+        lj += __shfl_xor_sync(0xffffffffu, lj, o);
+      }
+      if (ln == 0) {
+        gJk[k] = gj;
+        lJpart += lj;
+      }
     }
+    __syncthreads();
+  }
+  // gradient components
+  double g2part = 0.0;
+  for (int k = tid; k < N3; k += kCombineThreads) {
+    double g = 0.0;
+    for (int p = 0; p < K; ++p) g += wp[p] * (dp(0, p)[2 + k] + dp(1, p)[2 + k]);
+    if (use_jastrow) g += gJk[k];
     if (use_cusp) {
       const int e = k / 3, x = k % 3;
       for (int j = 0; j < N; ++j) {
@@ -1497,7 +1513,7 @@ cudaError_t launch_jastrow_sum(const dq_handle_s& h, const FwdDims& d, FwdBuffer
 template <class T>
 cudaError_t launch_combine(const dq_handle_s& h, const FwdDims& d, const T* params, FwdBuffers<T> b, T* logabs,
                            int8_t* sign, T* e_loc, cudaStream_t s) {
-  const size_t smem = (2 * (size_t)d.K + 3 * (size_t)d.D + 32) * sizeof(double);
+  const size_t smem = (2 * (size_t)d.K + 3 * (size_t)d.D + 32 + 3 * (size_t)d.N) * sizeof(double);
   auto kern = combine_kernel<T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -179,7 +179,7 @@ def test_weighted_mode_fp32_equals_weighted_sum_of_per_walker():
     for name, shape, _ in fx.param_layout(wl.system, wl.cfg):
         n = int(np.prod(shape))
         m = float(rel[o:o + n].max())
-        if name.startswith(("W_h", "W_g", "W2_", "W_o_")) or name == "W_J1":
+        if name.startswith(("W_h", "W_g", "W1_", "W2_", "W_o_")) or name == "W_J1":
             worst_matrix = max(worst_matrix, m)
         else:
             worst_other = max(worst_other, m)
