@@ -298,7 +298,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // Warps: 0 TMA, 1 MMA, 2..5 epilogue, 6..9 converter.
 // ---------------------------------------------------------------------------
 constexpr int T3_BK = 32;                            // FP32 elements per 128-byte row
-constexpr int T3_STAGES = 3;
+constexpr int T3_STAGES = 2;
+constexpr int T3_SUB = 2;                               // 128-row blocks per tile (share the W tile)
+constexpr uint32_t T3_TMEM_ALLOC = 2 * T3_SUB * 128;    // double-buffered, T3_SUB accumulators each
 constexpr uint32_t T3_TILE_A = TC_BM * T3_BK * 4;    // 16 KB
 constexpr uint32_t T3_TILE_B = TC_BN * T3_BK * 4;    // 16 KB
 constexpr int T3_THREADS = 320;
@@ -359,10 +361,11 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
                           int64_t ldy, int64_t y_seg_stride, int accumulate, unsigned int* __restrict__ status) {
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
-  uint8_t* sA = smem;                                  // [stage] X tile, x_big after conversion
-  uint8_t* sAs = sA + T3_STAGES * T3_TILE_A;           // [stage] x_small
-  uint8_t* sBb = sAs + T3_STAGES * T3_TILE_A;          // [stage] w_big
-  uint8_t* sBs = sBb + T3_STAGES * T3_TILE_B;          // [stage] w_small
+  // per stage: [x half 0, x half 1] (x_big after conversion), [x_small half 0, half 1], w_big, w_small
+  uint8_t* sA = smem;
+  uint8_t* sAs = sA + T3_STAGES * T3_SUB * T3_TILE_A;
+  uint8_t* sBb = sAs + T3_STAGES * T3_SUB * T3_TILE_A;
+  uint8_t* sBs = sBb + T3_STAGES * T3_TILE_B;
   uint64_t* full = reinterpret_cast<uint64_t*>(sBs + T3_STAGES * T3_TILE_B);
   uint64_t* conv = full + T3_STAGES;
   uint64_t* empty = conv + T3_STAGES;
@@ -375,11 +378,17 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int nk = (K + T3_BK - 1) / T3_BK;  // a ragged last K block reads zeros past K
   const int n_tiles_n = (n_out + TC_BN - 1) / TC_BN;
-  // A tile holds TC_BM rows: rb rows of each of sb = TC_BM / rb segments (rb < TC_BM only if
-  // seg_rows <= rb), or a TC_BM-row block of one segment.
+  // A 128-row block holds rb rows of each of sb = TC_BM / rb segments (rb < TC_BM only if
+  // seg_rows <= rb), or a TC_BM-row block of one segment.  A tile is T3_SUB such blocks
+  // sharing the W tile; each has its own accumulator.
   const int sb = TC_BM / rb;
   const int64_t rb_per_seg = (seg_rows + rb - 1) / rb;
-  const int64_t n_tiles = ((n_seg + sb - 1) / sb) * rb_per_seg * n_tiles_n;  // (segment group, row block, column block)
+  const int64_t n_mblk = ((n_seg + sb - 1) / sb) * rb_per_seg;
+  const int64_t n_tiles = ((n_mblk + T3_SUB - 1) / T3_SUB) * n_tiles_n;  // (row-block pair, column block)
+  auto mblock = [&](int64_t mb, int& seg, int& m0) {  // first segment and row of 128-row block mb
+    seg = (int)(mb / rb_per_seg) * sb;
+    m0 = (int)(mb % rb_per_seg) * rb;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < T3_STAGES; ++s) {
@@ -396,7 +405,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(TC_TMEM_ALLOC)
+                 "r"(T3_TMEM_ALLOC)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -409,9 +418,11 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     if (lane == 0) {  // TMA producer
       int64_t g = 0;
       for (int64_t t = blockIdx.x; t < n_tiles && !s_abort; t += gridDim.x) {
-        const int64_t mt = t / n_tiles_n;
-        const int seg = (int)(mt / rb_per_seg) * sb, m0 = (int)(mt % rb_per_seg) * rb;
+        const int64_t mp = t / n_tiles_n;
         const int n0 = (int)(t % n_tiles_n) * TC_BN;
+        int seg[T3_SUB], m0[T3_SUB];
+#pragma unroll
+        for (int h = 0; h < T3_SUB; ++h) mblock(mp * T3_SUB + h, seg[h], m0[h]);  // past the end: zero fill
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = (int)(g % T3_STAGES);
           const int64_t u = g / T3_STAGES;
@@ -419,8 +430,10 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             s_abort = 1;
             break;
           }
-          mbar_expect_tx(&full[s], T3_TILE_A + 2 * T3_TILE_B);
-          tma_load_3d(sA + s * T3_TILE_A, &tmA, kb * T3_BK, m0, seg, &full[s]);
+          mbar_expect_tx(&full[s], T3_SUB * T3_TILE_A + 2 * T3_TILE_B);
+#pragma unroll
+          for (int h = 0; h < T3_SUB; ++h)
+            tma_load_3d(sA + (s * T3_SUB + h) * T3_TILE_A, &tmA, kb * T3_BK, m0[h], seg[h], &full[s]);
           tma_load_2d(sBb + s * T3_TILE_B, &tmBb, kb * T3_BK, n0, &full[s]);
           tma_load_2d(sBs + s * T3_TILE_B, &tmBs, kb * T3_BK, n0, &full[s]);
         }
@@ -438,7 +451,6 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(a * TC_TMEM_COLS);
         bool ok = true;
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = (int)(g % T3_STAGES);
@@ -447,14 +459,19 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t ab = smem_u32(sA + s * T3_TILE_A), as_ = smem_u32(sAs + s * T3_TILE_A);
           const uint32_t bb = smem_u32(sBb + s * T3_TILE_B), bs = smem_u32(sBs + s * T3_TILE_B);
 #pragma unroll
-          for (int kk = 0; kk < T3_BK / 8; ++kk) {
-            const uint32_t o = kk * 32;
-            umma_tf32(d, sw128_desc(ab + o), sw128_desc(bb + o), idesc, (kb | kk) ? 1u : 0u);
-            umma_tf32(d, sw128_desc(ab + o), sw128_desc(bs + o), idesc, 1u);
-            umma_tf32(d, sw128_desc(as_ + o), sw128_desc(bb + o), idesc, 1u);
+          for (int h = 0; h < T3_SUB; ++h) {
+            const uint32_t d = tmem + (uint32_t)((a * T3_SUB + h) * TC_TMEM_COLS);
+            const uint32_t ab = smem_u32(sA + (s * T3_SUB + h) * T3_TILE_A);
+            const uint32_t as_ = smem_u32(sAs + (s * T3_SUB + h) * T3_TILE_A);
+#pragma unroll
+            for (int kk = 0; kk < T3_BK / 8; ++kk) {
+              const uint32_t o = kk * 32;
+              umma_tf32(d, sw128_desc(ab + o), sw128_desc(bb + o), idesc, (kb | kk) ? 1u : 0u);
+              umma_tf32(d, sw128_desc(ab + o), sw128_desc(bs + o), idesc, 1u);
+              umma_tf32(d, sw128_desc(as_ + o), sw128_desc(bb + o), idesc, 1u);
+            }
           }
           umma_commit(&empty[s]);
         }
@@ -476,10 +493,10 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
           s_abort = 1;
           break;
         }
-        float4* src = reinterpret_cast<float4*>(sA + s * T3_TILE_A);
-        float4* dst = reinterpret_cast<float4*>(sAs + s * T3_TILE_A);
-#pragma unroll
-        for (int j = 0; j < (int)(T3_TILE_A / 16 / 128); ++j) {
+        float4* src = reinterpret_cast<float4*>(sA + s * T3_SUB * T3_TILE_A);
+        float4* dst = reinterpret_cast<float4*>(sAs + s * T3_SUB * T3_TILE_A);
+#pragma unroll 4
+        for (int j = 0; j < (int)(T3_SUB * T3_TILE_A / 16 / 128); ++j) {
           const int idx = j * 128 + ct;
           const float4 x = src[idx];
           float4 b, sm;
@@ -500,7 +517,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
       }
     }
   } else {
-    // Epilogue warps 2..5
+    // Epilogue warps 2..5: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 of each accumulator.
     const int q = warp % 4;
     float(*st)[33] = ep_stage[warp - 2];
     int64_t lt = 0;
@@ -512,20 +529,25 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         break;
       }
       tc_fence_after();
-      const int64_t mt = t / n_tiles_n;
-      const int tr = q * 32 + lane;  // row of the tile
-      const int64_t seg = (mt / rb_per_seg) * sb + tr / rb;
+      const int64_t mp = t / n_tiles_n;
       const int n0 = (int)(t % n_tiles_n) * TC_BN;
-      const int64_t row = (mt % rb_per_seg) * rb + tr % rb;  // row within the segment
-      const bool add_bias = bias != nullptr && (row % bias_period) == 0;
-      float* yrow = row < seg_rows && seg < n_seg ? Y + seg * y_seg_stride + row * ldy + n0 : nullptr;
-      for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-        uint32_t vv[32];
-        tmem_ld32(tmem + (uint32_t)(a * TC_TMEM_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, vv);
-        const int n = n0 + c0 + lane;
-        const bool col_ok = n < n_out;
-        store_block_32x32(vv, st, lane, yrow ? yrow + c0 : nullptr, add_bias, bias != nullptr && col_ok ? bias[n] : 0.f,
-                          col_ok, accumulate != 0);
+      const int tr = q * 32 + lane;  // row of the 128-row block
+#pragma unroll 1
+      for (int h = 0; h < T3_SUB; ++h) {
+        const int64_t mb = mp * T3_SUB + h;
+        const int64_t seg = (mb / rb_per_seg) * sb + tr / rb;
+        const int64_t row = (mb % rb_per_seg) * rb + tr % rb;  // row within the segment
+        const bool add_bias = bias != nullptr && (row % bias_period) == 0;
+        float* yrow = mb < n_mblk && row < seg_rows && seg < n_seg ? Y + seg * y_seg_stride + row * ldy + n0 : nullptr;
+        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+          uint32_t vv[32];
+          tmem_ld32(tmem + (uint32_t)((a * T3_SUB + h) * TC_TMEM_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0,
+                    vv);
+          const int n = n0 + c0 + lane;
+          const bool col_ok = n < n_out;
+          store_block_32x32(vv, st, lane, yrow ? yrow + c0 : nullptr, add_bias,
+                            bias != nullptr && col_ok ? bias[n] : 0.f, col_ok, accumulate != 0);
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -536,7 +558,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   if (s_abort && threadIdx.x == 0) atomicOr(status, (unsigned)DQ_FLAG_TIMEOUT);
   tc_fence_after();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_ALLOC) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(T3_TMEM_ALLOC) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -801,7 +823,7 @@ bool make_map_seg_f32(CUtensorMap* m, const void* base, int64_t seg_rows, int64_
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 constexpr size_t t3_smem_bytes() {
-  return 1024 + T3_STAGES * (2 * T3_TILE_A + 2 * T3_TILE_B) + (3 * T3_STAGES + 4) * 8 + 16;
+  return 1024 + T3_STAGES * (2 * T3_SUB * T3_TILE_A + 2 * T3_TILE_B) + (3 * T3_STAGES + 4) * 8 + 16;
 }
 
 constexpr size_t tc_smem_bytes() { return 1024 + TC_STAGES * (TC_TILE_A + TC_TILE_B) + (2 * TC_STAGES + 4) * 8 + 16; }
@@ -859,8 +881,8 @@ cudaError_t gemm_tf32x3_tc_seg(const float* X, int64_t seg_rows, int64_t n_seg, 
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t tiles = ((n_seg + TC_BM / rb - 1) / (TC_BM / rb)) * ((seg_rows + rb - 1) / rb) *
-                        ((n_out + TC_BN - 1) / TC_BN);
+  const int64_t mblk = ((n_seg + TC_BM / rb - 1) / (TC_BM / rb)) * ((seg_rows + rb - 1) / rb);
+  const int64_t tiles = ((mblk + T3_SUB - 1) / T3_SUB) * ((n_out + TC_BN - 1) / TC_BN);
   const int64_t grid = tiles < sms ? tiles : sms;
   gemm_tf32x3_tc_kernel<<<(unsigned)grid, T3_THREADS, smem, s>>>(ma, mbb, mbs, seg_rows, n_seg, rb, n_out, K, bias,
                                                                 bias_period, Y, ldy, y_seg_stride,
