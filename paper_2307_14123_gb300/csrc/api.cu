@@ -373,7 +373,7 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
 // ---------------------------------------------------------------------------
 struct GradPlan {
   size_t geo, rbf, eh, ew, zl, msg, u, F, phi, det, js, jh, z0;  // saved forward
-  size_t fbar, ubar, mbar, zbar, wbar, hbar, phibar, beta, cbar, jhbar, gt, sbar, envbar, ybar, part, wt3, wt3t;
+  size_t fbar, ubar, mbar, zbar, wbar, hbar, phibar, beta, cbar, jhbar, gt, sbar, envbar, ybar, part, done, wt3, wt3t;
   int64_t part_elems;
   size_t total;
 };
@@ -418,6 +418,7 @@ GradPlan plan_grad(const dq_handle_s& h, int64_t Bc, size_t elem) {
   const int64_t blk = std::max({3 * D * D, D * D, D * Q, Wo * D, Wo * M, M * D, K, D});
   p.part_elems = 64 * blk;
   p.part = take(p.part_elems * elem);
+  p.done = take(kColsumReduceCounters * sizeof(unsigned int));
   p.wt3 = take(use_tf32x3(h) ? t3_weight_floats(h) * 4 : 0);
   p.wt3t = take(use_tf32x3(h) ? t3_weight_floats(h) * 4 : 0);  // transposed splits (reverse pass)
   p.total = o;
@@ -440,6 +441,8 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
   const size_t el = sizeof(T);
   DQ_CU(cudaMemsetAsync(G, 0, (size_t)(mode == 1 ? B : 1) * P * el, s));
   T* part = buf(pl.part);
+  unsigned int* done = reinterpret_cast<unsigned int*>(ws + pl.done);
+  DQ_CU(cudaMemsetAsync(done, 0, kColsumReduceCounters * sizeof(unsigned int), s));
   const bool use_t3 = sizeof(T) == 4 && use_tf32x3(h);
   const T3Weights w3 = t3_weights(h, ws + pl.wt3);
   // transposed splits for the products with W in the reverse pass (same block layout per layer)
@@ -468,7 +471,7 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
     const T* wc = weights ? weights + b0 : nullptr;
     auto reduce = [&](const T* X, RowMap mx, const T* Y, RowMap my, int rpw, int n_o, int n_a, int64_t poff, int ld) {
       return param_reduce<T>(X, mx, Y, my, rpw, nb, n_o, n_a, Gc, P, poff, ld, mode, part, pl.part_elems, s,
-                             use_t3 ? h.d_status : nullptr);
+                             use_t3 ? h.d_status : nullptr, done);
     };
     // ---- forward, keeping activations ----
     FwdBuffers<T> v{};

@@ -470,10 +470,12 @@ __global__ void __launch_bounds__(256)
 // every 8th row of the walker range; the 8 partial sums are added in a fixed
 // order in shared memory.  blockIdx.y: walker (per-walker mode) or split.
 constexpr int kColRows = 8;
+constexpr int kColsumCounters = kColsumReduceCounters;  // column blocks of one column sum (n_o <= 2048)
 template <class T>
 __global__ void __launch_bounds__(32 * kColRows)
     colsum_kernel(const T* __restrict__ X, RowMap mx, int rpw, int64_t nw, int n_o, T* __restrict__ G, int64_t P,
-                  int64_t off, int ld, int mode, int64_t walkers_per_split, T* __restrict__ part) {
+                  int64_t off, int ld, int mode, int64_t walkers_per_split, T* __restrict__ part,
+                  unsigned int* __restrict__ done) {
   __shared__ T red[kColRows][32];
   const int lane = threadIdx.x % 32, rl = threadIdx.x / 32;
   const int o = blockIdx.x * 32 + lane;
@@ -510,6 +512,21 @@ __global__ void __launch_bounds__(32 * kColRows)
     else
       part[(int64_t)blockIdx.y * n_o + o] = sum;
   }
+  if (mode == 1 || done == nullptr) return;
+  // The last split CTA of this column block adds the splits in order (deterministic).
+  __shared__ int s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&done[blockIdx.x], 1u) == gridDim.y - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (rl == 0 && o < n_o) {
+    T sum = 0;
+    for (unsigned sp = 0; sp < gridDim.y; ++sp) sum += __ldcg(part + (int64_t)sp * n_o + o);
+    G[off + (int64_t)o * ld] += sum;
+  }
+  if (threadIdx.x == 0) done[blockIdx.x] = 0;  // ready for the next use of this counter
 }
 
 template <class T>
@@ -726,7 +743,7 @@ inline bool walker_rows(RowMap m, int rpw, int64_t* pitch, int64_t* wstride) {
 template <class T>
 cudaError_t param_reduce(const T* X, RowMap mx, const T* Y, RowMap my, int rpw, int64_t nw, int n_o, int n_a, T* G,
                          int64_t P, int64_t off, int ld, int mode, T* part, int64_t part_elems, cudaStream_t s,
-                         unsigned int* tc_status) {
+                         unsigned int* tc_status, unsigned int* done) {
   if (nw <= 0 || n_o <= 0 || n_a <= 0) return cudaSuccess;
   if (rpw <= 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
@@ -753,7 +770,7 @@ cudaError_t param_reduce(const T* X, RowMap mx, const T* Y, RowMap my, int rpw, 
         const int64_t r_off = w0 * rpw;
         const T* Xo = X + (r_off / mx.rows_per_seg) * mx.seg_stride + (r_off % mx.rows_per_seg) * mx.ld;
         colsum_kernel<T><<<dim3(gx, (unsigned)nws), 32 * kColRows, 0, s>>>(Xo, mx, rpw, nws, n_o, G + w0 * P, P, off,
-                                                                          ld, 1, 1, nullptr);
+                                                                          ld, 1, 1, nullptr, nullptr);
       }
       return cudaGetLastError();
     }
@@ -764,9 +781,14 @@ cudaError_t param_reduce(const T* X, RowMap mx, const T* Y, RowMap my, int rpw, 
     if (splits > 65535) splits = 65535;
     const int64_t wps = (nw + splits - 1) / splits;
     splits = (nw + wps - 1) / wps;
-    colsum_kernel<T><<<dim3(gx, (unsigned)splits), 32 * kColRows, 0, s>>>(X, mx, rpw, nw, n_o, G, P, off, ld, 0, wps,
-                                                                          part);
-    reduce_splits_kernel<T><<<nblocks(n_o, 256), 256, 0, s>>>(part, (int)splits, n_o, 1, G, off, ld);
+    if (done != nullptr && gx <= kColsumCounters) {
+      colsum_kernel<T><<<dim3(gx, (unsigned)splits), 32 * kColRows, 0, s>>>(X, mx, rpw, nw, n_o, G, P, off, ld, 0,
+                                                                            wps, part, done);
+    } else {
+      colsum_kernel<T><<<dim3(gx, (unsigned)splits), 32 * kColRows, 0, s>>>(X, mx, rpw, nw, n_o, G, P, off, ld, 0,
+                                                                            wps, part, nullptr);
+      reduce_splits_kernel<T><<<nblocks(n_o, 256), 256, 0, s>>>(part, (int)splits, n_o, 1, G, off, ld);
+    }
     return cudaGetLastError();
   }
   const unsigned gx = nblocks(n_o, RT), gy = nblocks(n_a, RT);
@@ -827,7 +849,8 @@ cudaError_t launch_msg_bwd(const dq_handle_s& h, int64_t Bc, const T* mbar, cons
                                          T*, cudaStream_t);                                                       \
   template cudaError_t gemm_nn<T>(const T*, RowMap, const T*, T*, RowMap, int64_t, int, int, bool, cudaStream_t); \
   template cudaError_t param_reduce<T>(const T*, RowMap, const T*, RowMap, int, int64_t, int, int, T*, int64_t,   \
-                                       int64_t, int, int, T*, int64_t, cudaStream_t, unsigned int*);              \
+                                       int64_t, int, int, T*, int64_t, cudaStream_t, unsigned int*,              \
+                                       unsigned int*);                                                            \
   template cudaError_t launch_tanh_bwd<T>(const T*, const T*, int64_t, bool, T*, cudaStream_t);                   \
   template cudaError_t launch_add_rows<T>(T*, const T*, int64_t, int, int, cudaStream_t);                         \
   template cudaError_t launch_fill_spin_rows<T>(T*, const T*, int64_t, int, int, int, cudaStream_t);              \

@@ -18,11 +18,14 @@ cudaError_t gemm_nn(const T* X, RowMap mx, const T* W, T* Y, RowMap my, int64_t 
 // Parameter gradient block from rows: per walker (mode 1) writes G[b][off + o*ld + a],
 // summed over walkers (mode 0) adds to G[off + o*ld + a]; Y == nullptr means ones.
 // tc_status != nullptr allows the tensor-core row reduction (FP32, summed mode, large blocks);
-// it receives DQ_FLAG_TIMEOUT if a bounded wait inside that kernel gave up.
+// it receives DQ_FLAG_TIMEOUT if a bounded wait inside that kernel gave up.  done: nullptr or
+// kColsumReduceCounters zeroed counters (left zeroed) with which summed-mode column sums add their
+// splits in their last CTA instead of a second launch.
+constexpr int kColsumReduceCounters = 64;
 template <class T>
 cudaError_t param_reduce(const T* X, RowMap mx, const T* Y, RowMap my, int rpw, int64_t nw, int n_o, int n_a, T* G,
                          int64_t P, int64_t off, int ld, int mode, T* part, int64_t part_elems, cudaStream_t s,
-                         unsigned int* tc_status = nullptr);
+                         unsigned int* tc_status = nullptr, unsigned int* done = nullptr);
 template <class T>
 cudaError_t launch_tanh_bwd(const T* g, const T* u, int64_t n, bool is_pre, T* out, cudaStream_t s);
 template <class T>
