@@ -536,34 +536,42 @@ __global__ void __launch_bounds__(256, 2)
   }
 }
 
-// Value-only messages (C = 1): one thread per (walker, receiver, feature).
+// Value-only messages (C = 1): one CTA per (walker, 32 features); a warp per
+// receiver, lanes over features; pair table and z of the walker staged in
+// shared memory, sender loops split by spin (no per-edge branch).
 template <class T, class TO>
 __global__ void __launch_bounds__(256)
     messages_value_kernel(const T* __restrict__ Z, const T* __restrict__ z0, const T* __restrict__ ew,
                           const T* __restrict__ Y, const int* __restrict__ pair_of, int64_t Bc, int N, int n_up,
                           int M, int D, int E, int n_ee, int z_const, TO* __restrict__ msg) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= Bc * N * D) return;
-  const int d = (int)(gid % D);
-  const int64_t bi = gid / D;
-  const int i = (int)(bi % N);
-  const int64_t b = bi / N;
-  const bool up = i < n_up;
+  extern __shared__ __align__(16) unsigned char mv_smem[];
+  T* Zs = reinterpret_cast<T*>(mv_smem);           // [N][32]
+  int* Ps = reinterpret_cast<int*>(Zs + N * 32);   // [N][N]
+  const int64_t b = blockIdx.x;
+  const int lane = threadIdx.x % 32, wq = threadIdx.x / 32, nw = blockDim.x / 32;
+  const int d = blockIdx.y * 32 + lane;
+  for (int k = threadIdx.x; k < N * N; k += blockDim.x) Ps[k] = pair_of[k];
+  for (int j = wq; j < N; j += nw)
+    Zs[j * 32 + lane] = d >= D ? T(0) : (z_const ? z0[(j < n_up ? 0 : D) + d] : Z[(b * N + j) * D + d]);
+  __syncthreads();
+  if (d >= D) return;
   const T* ewb = ew + b * E * D + d;
-  const T* zb = Z + b * N * D + d;
-  T ss = 0, so = 0, sn = 0;
-  for (int j = 0; j < N; ++j) {
-    if (j == i) continue;
-    const T w = ewb[(int64_t)pair_of[i * N + j] * D];
-    const T z = z_const ? z0[(j < n_up ? 0 : D) + d] : zb[(int64_t)j * D];
-    if ((j < n_up) == up) ss += w * z; else so += w * z;
+  for (int i = wq; i < N; i += nw) {
+    const bool up = i < n_up;
+    T su = 0, sd = 0, sn = 0;  // spin-up senders, spin-down senders, nuclei
+#pragma unroll 4
+    for (int j = 0; j < n_up; ++j)
+      if (j != i) su += ewb[(int64_t)Ps[i * N + j] * D] * Zs[j * 32 + lane];
+#pragma unroll 4
+    for (int j = n_up; j < N; ++j)
+      if (j != i) sd += ewb[(int64_t)Ps[i * N + j] * D] * Zs[j * 32 + lane];
+    for (int I = 0; I < M; ++I) sn += ewb[(int64_t)(n_ee + i * M + I) * D] * Y[(int64_t)I * D + d];
+    const int n_same = up ? n_up : N - n_up, n_opp = N - n_same;
+    TO* out = msg + (b * N + i) * 3 * D + d;
+    out[0] = to_out((up ? su : sd) / T(n_same - 1 > 1 ? n_same - 1 : 1), out);
+    out[D] = to_out((up ? sd : su) / T(n_opp > 1 ? n_opp : 1), out);
+    out[2 * D] = to_out(sn / T(M), out);
   }
-  for (int I = 0; I < M; ++I) sn += ewb[(int64_t)(n_ee + i * M + I) * D] * Y[(int64_t)I * D + d];
-  const int n_same = up ? n_up : N - n_up, n_opp = N - n_same;
-  TO* out = msg + bi * 3 * D + d;
-  out[0] = to_out(ss / T(n_same - 1 > 1 ? n_same - 1 : 1), out);
-  out[D] = to_out(so / T(n_opp > 1 ? n_opp : 1), out);
-  out[2 * D] = to_out(sn / T(M), out);
 }
 
 // ---------------------------------------------------------------------------
@@ -1415,8 +1423,9 @@ cudaError_t launch_messages_t(const dq_handle_s& h, const FwdDims& d, const T* p
                               FwdBuffers<T> b, TO* out, cudaStream_t s) {
   const T* Y = params + h.off.layer[l].Y;
   if (d.C == 1) {
-    const int64_t n = d.Bc * d.N * d.D;
-    messages_value_kernel<T, TO><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+    const size_t smem = (size_t)d.N * 32 * sizeof(T) + (size_t)d.N * d.N * sizeof(int);
+    dim3 grid((unsigned)d.Bc, (unsigned)((d.D + 31) / 32));
+    messages_value_kernel<T, TO><<<grid, 32 * (d.N < 8 ? d.N : 8), smem, s>>>(
         b.Z, b.z0, b.ew, Y, h.d_pair_of, d.Bc, d.N, d.n_up, d.M, d.D, h.edges.n_all, h.edges.n_ee, z_const ? 1 : 0,
         out);
     return cudaGetLastError();
