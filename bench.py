@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--workload", default="n2_fp32")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay of the step")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--profile-case", type=int, default=0, metavar="B",
                    help="run one call on B walkers of the workload and exit (small case for ncu)")
@@ -418,6 +419,49 @@ def main():
         e2e = {"value": B * world * args.steps / (float(t2.item()) / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    # the same step captured as one CUDA graph (step counter on the device) and replayed
+    graph = None
+    if not args.no_graph:
+        ctr = torch.tensor([counter[0]], dtype=torch.int64, device=dev)
+
+        def gstep(th, rr, la):
+            h.mcmc_step(th, rr, la, 1, step_size, wl.walker_seed, ctr)
+            la2, _, el, e2 = h.local_energy(th, rr, sums=True)
+            w, stats = h.vmc_loss_weights(el, 5.0)
+            g = h.grad_logpsi(th, rr, w, 0) if with_grad else None
+            return el, e2, g
+
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            gstep(theta, r, logabs)
+        torch.cuda.current_stream().wait_stream(side)
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg):
+            gstep(theta, r, logabs)
+        for _ in range(args.warmup):
+            cg.replay()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        gev = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            cg.replay()
+            b.record()
+            gev.append((a, b))
+        torch.cuda.synchronize()
+        t3 = torch.tensor([sum(a.elapsed_time(b) for a, b in gev)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t3, op=dist.ReduceOp.MAX)
+        gms = float(t3.item())
+        graph = {"value": B * world * args.steps / (gms / 1e3), "unit": UNIT, "ms_per_step": gms / args.steps,
+                 "note": "the timed step replayed as one CUDA graph (Metropolis step counter on the device), "
+                         "L2 flushed before every replay"}
+        del cg
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, dtc, cores = oracle_sample(wl, args.cpu_seconds)
@@ -436,6 +480,7 @@ def main():
                 "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16+f32"}[wl.precision],
                 "data": "synthetic (seeded walkers and random-init weights)", "config": cfg,
                 "roofline": roof, "roofline_main_kernels": others, "cpu_baseline": cpu, "e2e": e2e,
+                "cuda_graph": graph,
                 "gpu_launches": launches,
                 "clocks": clk,
                 "local_energy_only": {"value": B * world * args.steps / (jet_ms / 1e3) if jet_ms else None,

@@ -170,6 +170,17 @@ dq_status mcmc_step(dq_handle h, const void* params, void* r, void* logabs, int6
                     double step_size, uint64_t seed, uint64_t step_counter, int64_t* n_accepted, void* ws,
                     size_t ws_bytes, void* stream);
 
+/* mcmc_step_dev: mcmc_step with the step counter in device memory:
+ *   step_counter  device uint64, read by the call's kernels (step t =
+ *                 *step_counter + s) and advanced by n_steps at its end.
+ * Every other argument as for mcmc_step.  With the counter on the device a
+ * captured CUDA graph of a VMC step (this call, local_energy, the loss
+ * weights and grad_logpsi) replays successive Metropolis steps; the draws are
+ * the same as mcmc_step's with step_counter = the counter's value. */
+dq_status mcmc_step_dev(dq_handle h, const void* params, void* r, void* logabs, int64_t B, int32_t n_steps,
+                        double step_size, uint64_t seed, uint64_t* step_counter, int64_t* n_accepted, void* ws,
+                        size_t ws_bytes, void* stream);
+
 /* grad_logpsi: parameter gradient of log|psi| (Sec. 4.1, Eq. 30).
  *   mode 0 (weighted): grad_out[P] = sum_b weights[b] d log|psi_b| / d theta
  *                      (weights [B] required);

@@ -32,7 +32,7 @@ EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_
            "ansatz_eval", "local_energy", "mcmc_step", "grad_logpsi", "vmc_loss_weights", "dq_last_device_status",
            "dq_status_string", "dq_profile_enable", "dq_profile_reset", "dq_profile_read", "dq_profile_kind_name",
            "dq_profile_kind_count", "vmc_loss_weights_noalloc", "dq_fp64_matrix_count", "dq_test_gemm_bf16",
-           "dq_test_gemm_tf32x3"]
+           "dq_test_gemm_tf32x3", "mcmc_step_dev"]
 
 
 class DQError(RuntimeError):
@@ -75,6 +75,7 @@ def load_library(path=None):
         lib.ansatz_eval.argtypes = [P, P, P, i64, P, P, P, sz, P]
         lib.local_energy.argtypes = [P, P, P, i64, P, P, P, P, P, sz, P]
         lib.mcmc_step.argtypes = [P, P, P, P, i64, i32, f64, u64, u64, P, P, sz, P]
+        lib.mcmc_step_dev.argtypes = [P, P, P, P, i64, i32, f64, u64, P, P, P, sz, P]
         lib.grad_logpsi.argtypes = [P, P, P, i64, P, i32, P, P, sz, P]
         lib.vmc_loss_weights.argtypes = [P, P, i64, f64, P, P, P, sz, P]
         lib.vmc_loss_weights_noalloc.argtypes = [P, P, i64, f64, P, P, P]
@@ -221,7 +222,10 @@ class Ansatz:
         return out
 
     def mcmc_step(self, params, r, logabs, n_steps=1, step_size=0.2, seed=0, step_counter=0):
-        """In-place Metropolis update of device tensors r and logabs; returns the accepted count (device int64)."""
+        """In-place Metropolis update of device tensors r and logabs; returns the accepted count (device int64).
+
+        step_counter: an int, or a one-element int64 CUDA tensor holding the counter on the device
+        (read by the kernels and advanced by n_steps: the form a captured CUDA graph can replay)."""
         params = self._dev(params, shape=(self.P,))
         for t in (r, logabs):
             if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous():
@@ -229,9 +233,16 @@ class Ansatz:
         B = r.numel() // (3 * self.N)
         n_acc = torch.empty(1, dtype=torch.int64, device=self.device)
         ws = self.workspace(B, OP_MCMC)
-        _check(self.lib.mcmc_step(self.h, _ptr(params), _ptr(r), _ptr(logabs), B, int(n_steps), float(step_size),
-                                  int(seed) & 0xFFFFFFFFFFFFFFFF, int(step_counter), _ptr(n_acc), _ptr(ws),
-                                  ws.numel(), self._stream()))
+        if isinstance(step_counter, torch.Tensor):
+            if step_counter.device != self.device or step_counter.dtype != torch.int64 or step_counter.numel() != 1:
+                raise DQError("a device step counter is a one-element int64 tensor on the handle's device")
+            _check(self.lib.mcmc_step_dev(self.h, _ptr(params), _ptr(r), _ptr(logabs), B, int(n_steps),
+                                          float(step_size), int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(step_counter),
+                                          _ptr(n_acc), _ptr(ws), ws.numel(), self._stream()))
+        else:
+            _check(self.lib.mcmc_step(self.h, _ptr(params), _ptr(r), _ptr(logabs), B, int(n_steps),
+                                      float(step_size), int(seed) & 0xFFFFFFFFFFFFFFFF, int(step_counter), _ptr(n_acc),
+                                      _ptr(ws), ws.numel(), self._stream()))
         return n_acc
 
     def grad_logpsi(self, params, r, weights=None, mode=0):

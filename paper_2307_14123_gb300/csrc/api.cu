@@ -667,7 +667,8 @@ namespace dq {
 namespace {
 template <class T>
 dq_status run_mcmc(dq_handle h, const T* params, T* r, T* logabs, int64_t B, int32_t n_steps, double step,
-                   uint64_t seed, uint64_t t0, int64_t* n_acc, unsigned char* ws, size_t ws_bytes, cudaStream_t s) {
+                   uint64_t seed, uint64_t t0, uint64_t* t_dev, int64_t* n_acc, unsigned char* ws, size_t ws_bytes,
+                   cudaStream_t s) {
   const McmcPlan plan = plan_mcmc(*h, B, sizeof(T));
   if (ws == nullptr || ws_bytes < plan.total || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
   T* r_prop = reinterpret_cast<T*>(ws + plan.r_prop);
@@ -676,13 +677,14 @@ dq_status run_mcmc(dq_handle h, const T* params, T* r, T* logabs, int64_t B, int
   if (n_acc) DQ_CU(cudaMemsetAsync(n_acc, 0, sizeof(int64_t), s));
   for (int32_t k = 0; k < n_steps; ++k) {
     const uint64_t t = t0 + (uint64_t)k;
-    DQ_LAUNCH(*h, PK_PROPOSE, launch_propose<T>(*h, B, r, r_prop, step, seed, t, s));
+    DQ_LAUNCH(*h, PK_PROPOSE, launch_propose<T>(*h, B, r, r_prop, step, seed, t, t_dev, s));
     dq_status st = run_forward<T>(*h, params, r_prop, B, false, la_prop, sg_prop, nullptr, ws + plan.fwd,
                                   ws_bytes - plan.fwd, s);
     if (st != DQ_OK) return st;
-    DQ_LAUNCH(*h, PK_ACCEPT, launch_accept<T>(*h, B, r, logabs, r_prop, la_prop, sg_prop, seed, t,
+    DQ_LAUNCH(*h, PK_ACCEPT, launch_accept<T>(*h, B, r, logabs, r_prop, la_prop, sg_prop, seed, t, t_dev,
                            reinterpret_cast<unsigned long long*>(n_acc), s));
   }
+  if (t_dev) DQ_CU(launch_advance_counter(t_dev, (uint64_t)n_steps, s));
   return DQ_OK;
 }
 }  // namespace
@@ -885,24 +887,43 @@ dq_status local_energy(dq_handle h, const void* params, const void* r, int64_t B
 }
 
 
-dq_status mcmc_step(dq_handle h, const void* params, void* r, void* logabs, int64_t B, int32_t n_steps,
-                    double step_size, uint64_t seed, uint64_t step_counter, int64_t* n_accepted, void* ws,
-                    size_t ws_bytes, void* stream) {
+namespace {
+dq_status mcmc_impl(dq_handle h, const void* params, void* r, void* logabs, int64_t B, int32_t n_steps,
+                    double step_size, uint64_t seed, uint64_t step_counter, uint64_t* t_dev, int64_t* n_accepted,
+                    void* ws, size_t ws_bytes, void* stream) {
   dq_status st = check_handle(h);
   if (st != DQ_OK) return st;
   if (B < 0 || n_steps < 0 || !(step_size >= 0) || !isfinite(step_size)) return DQ_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (B == 0 || n_steps == 0) {
     if (n_accepted && cudaMemsetAsync(n_accepted, 0, sizeof(int64_t), s) != cudaSuccess) return DQ_ERR_CUDA;
+    if (t_dev && n_steps > 0 && launch_advance_counter(t_dev, (uint64_t)n_steps, s) != cudaSuccess)
+      return DQ_ERR_CUDA;
     return DQ_OK;
   }
   if (!params || !r || !logabs) return DQ_ERR_ARG;
   auto* w = static_cast<unsigned char*>(ws);
   if (h->precision == DQ_FP64)
     return run_mcmc<double>(h, (const double*)params, (double*)r, (double*)logabs, B, n_steps, step_size, seed,
-                            step_counter, n_accepted, w, ws_bytes, s);
+                            step_counter, t_dev, n_accepted, w, ws_bytes, s);
   return run_mcmc<float>(h, (const float*)params, (float*)r, (float*)logabs, B, n_steps, step_size, seed,
-                         step_counter, n_accepted, w, ws_bytes, s);
+                         step_counter, t_dev, n_accepted, w, ws_bytes, s);
+}
+}  // namespace
+
+dq_status mcmc_step(dq_handle h, const void* params, void* r, void* logabs, int64_t B, int32_t n_steps,
+                    double step_size, uint64_t seed, uint64_t step_counter, int64_t* n_accepted, void* ws,
+                    size_t ws_bytes, void* stream) {
+  return mcmc_impl(h, params, r, logabs, B, n_steps, step_size, seed, step_counter, nullptr, n_accepted, ws, ws_bytes,
+                   stream);
+}
+
+dq_status mcmc_step_dev(dq_handle h, const void* params, void* r, void* logabs, int64_t B, int32_t n_steps,
+                        double step_size, uint64_t seed, uint64_t* step_counter, int64_t* n_accepted, void* ws,
+                        size_t ws_bytes, void* stream) {
+  if (step_counter == nullptr) return DQ_ERR_ARG;
+  return mcmc_impl(h, params, r, logabs, B, n_steps, step_size, seed, 0, step_counter, n_accepted, ws, ws_bytes,
+                   stream);
 }
 
 dq_status grad_logpsi(dq_handle h, const void* params, const void* r, int64_t B, const void* weights, int32_t mode,

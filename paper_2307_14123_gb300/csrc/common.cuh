@@ -192,13 +192,16 @@ cudaError_t launch_combine(const dq_handle_s& h, const FwdDims& d, const T* para
                            T* logabs, int8_t* sign, T* e_loc, cudaStream_t s);
 
 // ---- sampler, reductions, loss weights (mcmc.cu) ---------------------------
+// Step t of the Philox counter: t, plus *t_base when t_base (device) is non-null.
 template <class T>
 cudaError_t launch_propose(const dq_handle_s& h, int64_t B, const T* r, T* r_prop, double step, uint64_t seed,
-                           uint64_t t, cudaStream_t s);
+                           uint64_t t, const uint64_t* t_base, cudaStream_t s);
 template <class T>
 cudaError_t launch_accept(const dq_handle_s& h, int64_t B, T* r, T* logabs, const T* r_prop,
                           const T* logabs_prop, const int8_t* sign_prop, uint64_t seed, uint64_t t,
-                          unsigned long long* n_acc, cudaStream_t s);
+                          const uint64_t* t_base, unsigned long long* n_acc, cudaStream_t s);
+// *c += n on the device (advances a device-resident step counter).
+cudaError_t launch_advance_counter(uint64_t* c, uint64_t n, cudaStream_t s);
 template <class T>
 cudaError_t launch_esum(const T* e, int64_t B, double* out2, unsigned int* status, cudaStream_t s);
 template <class T>

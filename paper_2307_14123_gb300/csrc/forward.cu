@@ -1213,10 +1213,10 @@ __global__ void __launch_bounds__(kCombineThreads)
   const double* db = det + b * 2 * K * (N3 + 3);
   auto dp = [&](int s, int p) { return db + ((int64_t)s * K + p) * (N3 + 3); };
 
-  // log-sum-exp over determinant pairs (Eq. 28)
-  if (tid == 0) {
+  // log-sum-exp over determinant pairs (Eq. 28), warp 0 with lanes over pairs
+  if (tid < 32) {
     double lmax = -INFINITY;
-    for (int p = 0; p < K; ++p) {
+    for (int p = tid; p < K; p += 32) {
       const double cp = (double)params[c_off + p];
       const double sp = dp(0, p)[0] * dp(1, p)[0] * (cp > 0 ? 1.0 : cp < 0 ? -1.0 : 0.0);
       const double lp = sp != 0.0 ? dp(0, p)[1] + dp(1, p)[1] + log(fabs(cp)) : -INFINITY;
@@ -1224,13 +1224,24 @@ __global__ void __launch_bounds__(kCombineThreads)
       gsq[p] = sp;
       if (sp != 0.0 && lp > lmax) lmax = lp;
     }
-    double S = 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lmax = fmax(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    double S = 0.0;  // summed in a fixed order below: per lane, then a butterfly
     if (lmax > -INFINITY)
-      for (int p = 0; p < K; ++p)
-        if (gsq[p] != 0.0) S += gsq[p] * exp(wp[p] - lmax);
-    for (int p = 0; p < K; ++p) wp[p] = (gsq[p] != 0.0 && S != 0.0) ? gsq[p] * exp(wp[p] - lmax) / S : 0.0;
-    s_scalar[0] = S > 0 ? 1.0 : (S < 0 ? -1.0 : 0.0);
-    s_scalar[1] = S != 0.0 ? lmax + log(fabs(S)) : -INFINITY;
+      for (int p = tid; p < K; p += 32) {
+        const double e = gsq[p] != 0.0 ? gsq[p] * exp(wp[p] - lmax) : 0.0;
+        wp[p] = e;
+        S += e;
+      }
+    else
+      for (int p = tid; p < K; p += 32) wp[p] = 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+    for (int p = tid; p < K; p += 32) wp[p] = S != 0.0 ? wp[p] / S : 0.0;
+    if (tid == 0) {
+      s_scalar[0] = S > 0 ? 1.0 : (S < 0 ? -1.0 : 0.0);
+      s_scalar[1] = S != 0.0 ? lmax + log(fabs(S)) : -INFINITY;
+    }
   }
   __syncthreads();
   const double sgn = s_scalar[0];

@@ -34,7 +34,8 @@ __device__ __forceinline__ double unit_uniform(uint32_t x) { return ((double)x +
 
 template <class T>
 __global__ void propose_kernel(const T* __restrict__ r, T* __restrict__ r_prop, int64_t B, int N3, double step,
-                               uint64_t seed, uint64_t t) {
+                               uint64_t seed, uint64_t t, const uint64_t* __restrict__ t_base) {
+  if (t_base) t += *t_base;  // step counter kept in device memory
   const int nblk = (N3 + 3) / 4;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= B * nblk) return;
@@ -60,7 +61,9 @@ __global__ void propose_kernel(const T* __restrict__ r, T* __restrict__ r_prop, 
 template <class T>
 __global__ void accept_kernel(T* __restrict__ r, T* __restrict__ logabs, const T* __restrict__ r_prop,
                               const T* __restrict__ la_prop, const int8_t* __restrict__ sign_prop, int64_t B, int N3,
-                              uint64_t seed, uint64_t t, unsigned long long* __restrict__ n_acc) {
+                              uint64_t seed, uint64_t t, const uint64_t* __restrict__ t_base,
+                              unsigned long long* __restrict__ n_acc) {
+  if (t_base) t += *t_base;
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool acc = false;
   if (b < B) {
@@ -175,21 +178,28 @@ __global__ void __launch_bounds__(kRedThreads)
 
 }  // namespace
 
+__global__ void advance_counter_kernel(uint64_t* c, uint64_t n) { *c += n; }
+
 template <class T>
 cudaError_t launch_propose(const dq_handle_s& h, int64_t B, const T* r, T* r_prop, double step, uint64_t seed,
-                           uint64_t t, cudaStream_t s) {
+                           uint64_t t, const uint64_t* t_base, cudaStream_t s) {
   const int N3 = 3 * h.N, nblk = (N3 + 3) / 4;
   const int64_t n = B * nblk;
-  propose_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(r, r_prop, B, N3, step, seed, t);
+  propose_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(r, r_prop, B, N3, step, seed, t, t_base);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_counter(uint64_t* c, uint64_t n, cudaStream_t s) {
+  advance_counter_kernel<<<1, 1, 0, s>>>(c, n);
   return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t launch_accept(const dq_handle_s& h, int64_t B, T* r, T* logabs, const T* r_prop, const T* logabs_prop,
-                          const int8_t* sign_prop, uint64_t seed, uint64_t t, unsigned long long* n_acc,
-                          cudaStream_t s) {
+                          const int8_t* sign_prop, uint64_t seed, uint64_t t, const uint64_t* t_base,
+                          unsigned long long* n_acc, cudaStream_t s) {
   accept_kernel<T><<<(unsigned)((B + 255) / 256), 256, 0, s>>>(r, logabs, r_prop, logabs_prop, sign_prop, B, 3 * h.N,
-                                                               seed, t, n_acc);
+                                                               seed, t, t_base, n_acc);
   return cudaGetLastError();
 }
 
@@ -210,9 +220,9 @@ cudaError_t launch_loss_weights(const T* e, int64_t B, double k, T* w, double* s
 
 #define DQ_INST(T)                                                                                                 \
   template cudaError_t launch_propose<T>(const dq_handle_s&, int64_t, const T*, T*, double, uint64_t, uint64_t,    \
-                                         cudaStream_t);                                                           \
+                                         const uint64_t*, cudaStream_t);                                          \
   template cudaError_t launch_accept<T>(const dq_handle_s&, int64_t, T*, T*, const T*, const T*, const int8_t*,    \
-                                        uint64_t, uint64_t, unsigned long long*, cudaStream_t);                   \
+                                        uint64_t, uint64_t, const uint64_t*, unsigned long long*, cudaStream_t);  \
   template cudaError_t launch_esum<T>(const T*, int64_t, double*, unsigned int*, cudaStream_t);                   \
   template cudaError_t launch_loss_weights<T>(const T*, int64_t, double, T*, double*, double*, cudaStream_t);
 DQ_INST(float)
