@@ -14,6 +14,8 @@ Functions, each following the paper's definitions:
   parameter directions (dual numbers), the ingredient of Eq. (30).
 * :func:`metropolis_step` - one random-walk Metropolis step (Sec. 5) on
   draws passed in.
+* :func:`mala_step` - one Metropolis-adjusted Langevin step (Sec. 5, the
+  Langevin sampler, with per-electron drift limiting) on draws passed in.
 * :func:`clipped_loss_weights` - median/MAD clipping of Sec. 4.4 and the
   per-walker weights of the gradient estimator, Eq. (30).
 * :func:`energy_estimate` - Eq. (33) and the batch-means error bar, Eq. (35).
@@ -79,6 +81,7 @@ def _load(real="fp64"):
         lib.oracle_grad_jvp.argtypes = [P, P, P, ctypes.c_int64, P, ctypes.c_int32, P]
         lib.oracle_grad_index.argtypes = [P, P, P, ctypes.c_int64, P, ctypes.c_int32, P]
         lib.oracle_metropolis_step.argtypes = [P, P, P, P, ctypes.c_int64, P, P, ctypes.c_double, P]
+        lib.oracle_mala_step.argtypes = [P, P, P, P, P, ctypes.c_int64, P, P, ctypes.c_double, P, P]
         lib.oracle_intermediates.argtypes = [P, P, P, P, P]
         _libs[real] = lib
     return _libs[real]
@@ -183,6 +186,23 @@ class Oracle:
         self.lib.oracle_metropolis_step(ctypes.byref(self.spec), _ptr(theta), _ptr(r), _ptr(la), r.shape[0],
                                         _ptr(xi), _ptr(u), float(step), _ptr(acc))
         return r, la, acc
+
+    def mala_step(self, theta, r, logabs, grad, xi, u, tau):
+        """Metropolis-adjusted Langevin step (Sec. 5) on draws passed in; returns
+        (r_new, logabs_new, grad_new, accepted, log_alpha) without modifying inputs.
+        grad is d log|psi| / d r at r ([B][N][3])."""
+        self._fp64_only()
+        theta, r = self._prep(theta, r)
+        r = r.copy()
+        la = np.ascontiguousarray(logabs, dtype=np.float64).copy()
+        g = np.ascontiguousarray(grad, dtype=np.float64).reshape(r.shape).copy()
+        xi = np.ascontiguousarray(xi, dtype=np.float64).reshape(r.shape)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        acc = np.empty(r.shape[0], dtype=np.int8)
+        lal = np.empty(r.shape[0])
+        self.lib.oracle_mala_step(ctypes.byref(self.spec), _ptr(theta), _ptr(r), _ptr(la), _ptr(g), r.shape[0],
+                                  _ptr(xi), _ptr(u), float(tau), _ptr(acc), _ptr(lal))
+        return r, la, g, acc, lal
 
     def intermediates(self, theta, r):
         """Final embeddings f[N][D] and orbital matrices A[2][K][nmax][nmax] of one walker."""

@@ -569,3 +569,93 @@ def test_clipping_rule():
         assert np.all(c >= m - hw - 1e-15) and np.all(c <= m + hw + 1e-15)
         assert np.allclose(w, 2 / B * (c - c.mean()))
         assert abs(w.sum()) < 1e-14
+
+
+# ----------------------------------------------------------------------------
+# Langevin (MALA) sampler, Sec. 5
+# ----------------------------------------------------------------------------
+def _drift_limited(g, tau):
+    """Per-electron drift limiting (Umrigar, Nightingale, Runge 1993, a = 1)."""
+    v2 = np.sum(g * g, axis=-1, keepdims=True)
+    s = tau * v2
+    f = np.where(s > 0, (np.sqrt(1 + 2 * s) - 1) / np.where(s > 0, s, 1), 1.0)
+    return f * g
+
+
+def test_mala_hydrogen_closed_form():
+    """psi = exp(-r): grad log|psi| = -r/|r|, so proposal and acceptance ratio
+    follow in closed form; the oracle gets its gradient from the network
+    (switched off) by hyper-dual numbers."""
+    H = fx.molecule("H")
+    cfg = fx.AnsatzCfg(8, 1, 1, use_cusp=0)
+    o = oracle.Oracle(H, cfg)
+    th = fx.network_off_params(H, cfg, 1.0)
+    B, tau = 64, 0.3
+    r = fx.init_walkers(H, B, 21, sigma=1.5)
+    la = -np.linalg.norm(r[:, 0], axis=1)
+    g = -r / np.linalg.norm(r, axis=-1, keepdims=True)
+    xi, u = fx.metropolis_draws(5, B, 1, 0)
+    rn, lan, gn, acc, lal = o.mala_step(th, r, la, g, xi, u, tau)
+    rp = r + tau * _drift_limited(g, tau) + np.sqrt(tau) * xi
+    rpn = np.linalg.norm(rp[:, 0], axis=1)
+    gp = -rp / rpn[:, None, None]
+    back = r - rp - tau * _drift_limited(gp, tau)
+    want = 2 * (-rpn - la) + 0.5 * np.sum(xi ** 2, axis=(1, 2)) - np.sum(back ** 2, axis=(1, 2)) / (2 * tau)
+    np.testing.assert_allclose(lal, want, rtol=0, atol=1e-11)
+    want_acc = np.log(u) < want
+    assert np.array_equal(acc.astype(bool), want_acc)
+    assert 0 < want_acc.sum() < B
+    np.testing.assert_allclose(rn[want_acc], rp[want_acc], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(rn[~want_acc], r[~want_acc], rtol=0, atol=0)
+    np.testing.assert_allclose(gn[want_acc], gp[want_acc], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(lan[want_acc], -rpn[want_acc], rtol=0, atol=1e-13)
+
+
+def test_mala_detailed_balance():
+    """The acceptance ratio of the move r -> r' and of the reverse move r' -> r
+    multiply to one, log alpha(r -> r') + log alpha(r' -> r) = 0, for the
+    network switched on (checks the asymmetric-proposal correction)."""
+    sys_, cfg = small_system(), fx.AnsatzCfg(8, 2, 2)
+    o = oracle.Oracle(sys_, cfg)
+    th = fx.init_params(sys_, cfg, 4)
+    B, tau = 6, 0.05
+    r = fx.init_walkers(sys_, B, 8)
+    out = o.local_energy(th, r, with_grad=True)
+    g = out["grad"].reshape(r.shape)
+    xi, _ = fx.metropolis_draws(9, B, sys_.n_elec, 0)
+    tiny = np.full(B, 1e-300)
+    r1, la1, g1, acc1, lal1 = o.mala_step(th, r, out["logabs"], g, xi, tiny, tau)
+    assert acc1.all()
+    xi_back = (r - r1 - tau * _drift_limited(g1, tau)) / np.sqrt(tau)
+    r2, la2, g2, acc2, lal2 = o.mala_step(th, r1, la1, g1, xi_back, tiny, tau)
+    assert acc2.all()
+    np.testing.assert_allclose(r2, r, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(lal1 + lal2, 0.0, rtol=0, atol=1e-9)
+    # the gradient carried along is the oracle's own gradient at the new positions
+    np.testing.assert_allclose(g1, o.local_energy(th, r1, with_grad=True)["grad"].reshape(r.shape), rtol=0,
+                               atol=1e-12)
+
+
+def test_mala_stationarity_hydrogen():
+    """MALA samples |psi|^2: psi = exp(-r) gives <r> = 3/2 (within the Eq. 35 error
+    bar) and zero-variance local energies."""
+    H = fx.molecule("H")
+    cfg = fx.AnsatzCfg(4, 1, 1, use_cusp=0)
+    o = oracle.Oracle(H, cfg)
+    th = fx.network_off_params(H, cfg, 1.0)
+    B, tau = 256, 0.4
+    r = fx.init_walkers(H, B, 31)
+    out = o.local_energy(th, r, with_grad=True)
+    la, g = out["logabs"], out["grad"].reshape(r.shape)
+    rs, acc_tot = [], 0
+    for t in range(400):
+        xi, u = fx.metropolis_draws(31, B, 1, t)
+        r, la, g, acc, _ = o.mala_step(th, r, la, g, xi, u, tau)
+        if t >= 100:
+            rs.append(r.copy())
+            acc_tot += acc.sum()
+    rad = np.linalg.norm(np.stack(rs, axis=1)[:, :, 0], axis=-1)
+    mean, err = oracle.energy_estimate(rad)
+    assert 0.5 < acc_tot / (B * 300) < 1.0
+    assert abs(mean - 1.5) < 5 * err, (mean, err)
+    assert np.all(np.abs(o.local_energy(th, r)["e_loc"] + 0.5) < 1e-11)
