@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay of the step")
+    p.add_argument("--no-mala", action="store_true", help="skip the step with the Langevin sampler")
+    p.add_argument("--mala-tau", type=float, default=0.1, help="Langevin time step (bohr^2)")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--profile-case", type=int, default=0, metavar="B",
                    help="run one call on B walkers of the workload and exit (small case for ncu)")
@@ -462,6 +464,49 @@ def main():
                          "L2 flushed before every replay"}
         del cg
 
+    # the VMC step with the Langevin sampler in place of the Metropolis one: the proposal's
+    # forward (value, drift, Laplacian) also gives E_loc at the accepted positions, so the
+    # step is mala_step + vmc_loss_weights + grad_logpsi
+    langevin = None
+    if not args.no_mala:
+        tau = args.mala_tau
+        r_m, la_m = r.clone(), torch.empty_like(logabs)
+        g_m, e_m = torch.empty_like(r), torch.empty_like(logabs)
+        h.mala_step(theta, r_m, la_m, g_m, n_steps=0, tau=tau, grad_valid=False, e_loc=e_m)
+        mctr = torch.zeros(1, dtype=torch.int64, device=dev)
+
+        def mstep():
+            n = h.mala_step(theta, r_m, la_m, g_m, 1, tau, wl.walker_seed + 1, mctr, e_loc=e_m)
+            w, stats = h.vmc_loss_weights(e_m, 5.0)
+            g = h.grad_logpsi(theta, r_m, w, 0) if with_grad else None
+            return n
+
+        for _ in range(args.warmup):
+            mstep()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        mev, n_acc = [], torch.zeros(1, dtype=torch.int64, device=dev)
+        for _ in range(args.steps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            n = mstep()
+            b.record()
+            n_acc += n
+            mev.append((a, b))
+        torch.cuda.synchronize()
+        t4 = torch.tensor([sum(a.elapsed_time(b) for a, b in mev)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t4, op=dist.ReduceOp.MAX)
+        mms = float(t4.item())
+        langevin = {"value": B * world * args.steps / (mms / 1e3), "unit": UNIT, "ms_per_step": mms / args.steps,
+                    "tau": tau, "acceptance": int(n_acc.item()) / (B * args.steps),
+                    "step": "mala_step(1 Langevin sweep, E_loc carried) + vmc_loss_weights"
+                            + (" + grad_logpsi(weighted)" if with_grad else ""),
+                    "note": "same workload, Langevin sampler (Sec. 5) instead of random-walk Metropolis; "
+                            "L2 flushed before every step"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, dtc, cores = oracle_sample(wl, args.cpu_seconds)
@@ -481,6 +526,7 @@ def main():
                 "data": "synthetic (seeded walkers and random-init weights)", "config": cfg,
                 "roofline": roof, "roofline_main_kernels": others, "cpu_baseline": cpu, "e2e": e2e,
                 "cuda_graph": graph,
+                "langevin_sampler": langevin,
                 "gpu_launches": launches,
                 "clocks": clk,
                 "local_energy_only": {"value": B * world * args.steps / (jet_ms / 1e3) if jet_ms else None,

@@ -88,7 +88,8 @@ typedef enum {
   DQ_OP_LOCAL_ENERGY = 1,
   DQ_OP_MCMC = 2,
   DQ_OP_GRAD = 3,
-  DQ_OP_LOSS_WEIGHTS = 4
+  DQ_OP_LOSS_WEIGHTS = 4,
+  DQ_OP_MALA = 5
 } dq_op;
 
 /* Device status flags (dq_last_device_status). */
@@ -180,6 +181,38 @@ dq_status mcmc_step(dq_handle h, const void* params, void* r, void* logabs, int6
 dq_status mcmc_step_dev(dq_handle h, const void* params, void* r, void* logabs, int64_t B, int32_t n_steps,
                         double step_size, uint64_t seed, uint64_t* step_counter, int64_t* n_accepted, void* ws,
                         size_t ws_bytes, void* stream);
+
+/* mala_step: n_steps Metropolis-adjusted Langevin steps (Sec. 5, the Langevin
+ * sampler) on B walkers.  The paper names a correction that shortens electron
+ * steps near the nuclei without giving it; here the drift of electron i,
+ * v_i = d log|psi| / d r_i, is limited as (Umrigar, Nightingale, Runge,
+ * J. Chem. Phys. 99, 2865 (1993), a = 1)
+ *   vbar_i = v_i (sqrt(1 + 2 tau |v_i|^2) - 1) / (tau |v_i|^2).
+ * Step t = step_counter + s proposes r' = r + tau vbar(r) + sqrt(tau) xi with
+ * the normals xi of mcmc_step's step t, evaluates log|psi|, sign and
+ * d log|psi| / d r at r' (value, 3N first derivatives and Laplacian
+ * propagated together, as in local_energy), and accepts iff psi(r') != 0 and
+ *   log u < 2 (log|psi(r')| - log|psi(r)|) + |xi|^2 / 2
+ *           - |r - r' - tau vbar(r')|^2 / (2 tau)
+ * with mcmc_step's uniform u of step t (FP64 arithmetic).
+ *   r        [B][N][3] in/out    positions
+ *   logabs   [B]       in/out    log|psi| of r
+ *   grad     [B][N][3] in/out    d log|psi| / d r at r; grad_valid = 0 makes
+ *                                the call compute it (and logabs) first, so
+ *                                n_steps = 0 with grad_valid = 0 only sets up
+ *                                logabs and grad at r
+ *   e_loc    [B]       in/out    nullable: E_loc at r (as from local_energy),
+ *                                carried with r (the proposal's evaluation
+ *                                gives E_loc at r' at no extra cost);
+ *                                computed with grad when grad_valid = 0
+ *   step_counter_dev   nullable, device uint64: if given, the step counter is
+ *                      read from it (step_counter ignored) and advanced by
+ *                      n_steps, as in mcmc_step_dev
+ *   n_accepted         nullable, device int64: accepted moves of this call
+ * tau > 0.  Workspace: dq_workspace_size(op = DQ_OP_MALA). */
+dq_status mala_step(dq_handle h, const void* params, void* r, void* logabs, void* grad, void* e_loc,
+                    int32_t grad_valid, int64_t B, int32_t n_steps, double tau, uint64_t seed, uint64_t step_counter,
+                    uint64_t* step_counter_dev, int64_t* n_accepted, void* ws, size_t ws_bytes, void* stream);
 
 /* grad_logpsi: parameter gradient of log|psi| (Sec. 4.1, Eq. 30).
  *   mode 0 (weighted): grad_out[P] = sum_b weights[b] d log|psi_b| / d theta

@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdqmc.so")
 
 DQ_FP64, DQ_FP32, DQ_BF16_MIXED = 0, 1, 2
-OP_EVAL, OP_LOCAL_ENERGY, OP_MCMC, OP_GRAD, OP_LOSS_WEIGHTS = 0, 1, 2, 3, 4
+OP_EVAL, OP_LOCAL_ENERGY, OP_MCMC, OP_GRAD, OP_LOSS_WEIGHTS, OP_MALA = 0, 1, 2, 3, 4, 5
 FLAG_SINGULAR, FLAG_NONFINITE = 0x1, 0x2
 PRECISIONS = {"fp64": DQ_FP64, "fp32": DQ_FP32, "bf16": DQ_BF16_MIXED}
 
@@ -32,7 +32,7 @@ EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_
            "ansatz_eval", "local_energy", "mcmc_step", "grad_logpsi", "vmc_loss_weights", "dq_last_device_status",
            "dq_status_string", "dq_profile_enable", "dq_profile_reset", "dq_profile_read", "dq_profile_kind_name",
            "dq_profile_kind_count", "vmc_loss_weights_noalloc", "dq_fp64_matrix_count", "dq_test_gemm_bf16",
-           "dq_test_gemm_tf32x3", "mcmc_step_dev"]
+           "dq_test_gemm_tf32x3", "mcmc_step_dev", "mala_step"]
 
 
 class DQError(RuntimeError):
@@ -76,6 +76,7 @@ def load_library(path=None):
         lib.local_energy.argtypes = [P, P, P, i64, P, P, P, P, P, sz, P]
         lib.mcmc_step.argtypes = [P, P, P, P, i64, i32, f64, u64, u64, P, P, sz, P]
         lib.mcmc_step_dev.argtypes = [P, P, P, P, i64, i32, f64, u64, P, P, P, sz, P]
+        lib.mala_step.argtypes = [P, P, P, P, P, P, i32, i64, i32, f64, u64, u64, P, P, P, sz, P]
         lib.grad_logpsi.argtypes = [P, P, P, i64, P, i32, P, P, sz, P]
         lib.vmc_loss_weights.argtypes = [P, P, i64, f64, P, P, P, sz, P]
         lib.vmc_loss_weights_noalloc.argtypes = [P, P, i64, f64, P, P, P]
@@ -243,6 +244,32 @@ class Ansatz:
             _check(self.lib.mcmc_step(self.h, _ptr(params), _ptr(r), _ptr(logabs), B, int(n_steps),
                                       float(step_size), int(seed) & 0xFFFFFFFFFFFFFFFF, int(step_counter), _ptr(n_acc),
                                       _ptr(ws), ws.numel(), self._stream()))
+        return n_acc
+
+    def mala_step(self, params, r, logabs, grad, n_steps=1, tau=0.05, seed=0, step_counter=0, grad_valid=True,
+                  e_loc=None):
+        """In-place Metropolis-adjusted Langevin update of device tensors r, logabs and grad
+        (d log|psi| / d r at r) and, if given, e_loc (E_loc at r); grad_valid=False computes
+        them first (n_steps=0 then only sets them up).  Returns the accepted count (device
+        int64).  step_counter: an int, or a one-element int64 CUDA tensor (read on the
+        device and advanced by n_steps)."""
+        params = self._dev(params, shape=(self.P,))
+        for t in (r, logabs, grad) + ((e_loc,) if e_loc is not None else ()):
+            if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous():
+                raise DQError("mala_step updates r, logabs, grad and e_loc in place: pass contiguous device tensors")
+        B = r.numel() // (3 * self.N)
+        if grad.numel() != r.numel() or logabs.numel() != B or (e_loc is not None and e_loc.numel() != B):
+            raise DQError("grad has the shape of r; logabs and e_loc one value per walker")
+        n_acc = torch.empty(1, dtype=torch.int64, device=self.device)
+        ws = self.workspace(B, OP_MALA)
+        dev_ctr = None
+        if isinstance(step_counter, torch.Tensor):
+            if step_counter.device != self.device or step_counter.dtype != torch.int64 or step_counter.numel() != 1:
+                raise DQError("a device step counter is a one-element int64 tensor on the handle's device")
+            dev_ctr, step_counter = step_counter, 0
+        _check(self.lib.mala_step(self.h, _ptr(params), _ptr(r), _ptr(logabs), _ptr(grad), _ptr(e_loc),
+                                  1 if grad_valid else 0, B, int(n_steps), float(tau), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                  int(step_counter), _ptr(dev_ctr), _ptr(n_acc), _ptr(ws), ws.numel(), self._stream()))
         return n_acc
 
     def grad_logpsi(self, params, r, weights=None, mode=0):

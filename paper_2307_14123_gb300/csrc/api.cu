@@ -181,6 +181,31 @@ FwdPlan plan_forward(const dq_handle_s& h, int64_t Bc, bool jets, size_t elem) {
 struct McmcPlan {
   size_t r_prop, la_prop, sign_prop, fwd, total;
 };
+// Langevin sampler: proposals, their log|psi|, sign, gradient and normals, the
+// local energies the jet forward also produces, then the jet forward's workspace.
+struct MalaPlan {
+  size_t r_prop, la_prop, sign_prop, g_prop, xi, e_prop, fwd, total;
+};
+MalaPlan plan_mala(const dq_handle_s& h, int64_t B, size_t elem) {
+  MalaPlan p{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += align_up(bytes);
+    return at;
+  };
+  const size_t n3 = (size_t)B * 3 * h.N * elem;
+  p.r_prop = take(n3);
+  p.la_prop = take((size_t)B * elem);
+  p.sign_prop = take((size_t)B);
+  p.g_prop = take(n3);
+  p.xi = take(n3);
+  p.e_prop = take((size_t)B * elem);
+  p.fwd = o;
+  o += plan_forward(h, std::min<int64_t>(B, h.max_chunk), true, elem).total;
+  p.total = o;
+  return p;
+}
 
 McmcPlan plan_mcmc(const dq_handle_s& h, int64_t B, size_t elem) {
   McmcPlan p{};
@@ -225,7 +250,8 @@ inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 template <class T>
 dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t B, bool jets, T* logabs,
-                      int8_t* sign, T* e_loc, unsigned char* ws, size_t ws_bytes, cudaStream_t s) {
+                      int8_t* sign, T* e_loc, unsigned char* ws, size_t ws_bytes, cudaStream_t s,
+                      T* grad = nullptr) {
   const int64_t Bmax = std::min<int64_t>(B, h.max_chunk);
   const FwdPlan plan = plan_forward(h, Bmax, jets, sizeof(T));
   if (ws == nullptr || ws_bytes < plan.total || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
@@ -361,7 +387,9 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
       const RowMap mj{(int64_t)C, (int64_t)C * D, D};
       DQ_LAUNCH(h, kb + PK_GEMM_JASTROW, gemm_nt<T>(bf.js, mj, params + h.off.W_J1, params + h.off.b_J1, C, bf.jh, mj, nb * C, D, D, false, s));
     }
-    DQ_LAUNCH(h, kb + PK_COMBINE, launch_combine<T>(h, d, params, bf, logabs + b0, sign + b0, e_loc ? e_loc + b0 : nullptr, s));
+    DQ_LAUNCH(h, kb + PK_COMBINE, launch_combine<T>(h, d, params, bf, logabs + b0, sign + b0,
+                                                    e_loc ? e_loc + b0 : nullptr, s,
+                                                    grad ? grad + b0 * 3 * N : nullptr));
   }
   return DQ_OK;
 }
@@ -687,6 +715,38 @@ dq_status run_mcmc(dq_handle h, const T* params, T* r, T* logabs, int64_t B, int
   if (t_dev) DQ_CU(launch_advance_counter(t_dev, (uint64_t)n_steps, s));
   return DQ_OK;
 }
+
+template <class T>
+dq_status run_mala(dq_handle h, const T* params, T* r, T* logabs, T* grad, T* e_loc, int grad_valid, int64_t B,
+                   int32_t n_steps, double tau, uint64_t seed, uint64_t t0, uint64_t* t_dev, int64_t* n_acc,
+                   unsigned char* ws, size_t ws_bytes, cudaStream_t s) {
+  const MalaPlan plan = plan_mala(*h, B, sizeof(T));
+  if (ws == nullptr || ws_bytes < plan.total || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
+  T* r_prop = reinterpret_cast<T*>(ws + plan.r_prop);
+  T* la_prop = reinterpret_cast<T*>(ws + plan.la_prop);
+  int8_t* sg_prop = reinterpret_cast<int8_t*>(ws + plan.sign_prop);
+  T* g_prop = reinterpret_cast<T*>(ws + plan.g_prop);
+  T* xi = reinterpret_cast<T*>(ws + plan.xi);
+  T* e_prop = reinterpret_cast<T*>(ws + plan.e_prop);
+  if (n_acc) DQ_CU(cudaMemsetAsync(n_acc, 0, sizeof(int64_t), s));
+  if (!grad_valid) {  // d log|psi| / d r at the starting positions (log|psi| recomputed too)
+    dq_status st = run_forward<T>(*h, params, r, B, true, logabs, sg_prop, e_loc ? e_loc : e_prop, ws + plan.fwd,
+                                  ws_bytes - plan.fwd, s, grad);
+    if (st != DQ_OK) return st;
+  }
+  for (int32_t k = 0; k < n_steps; ++k) {
+    const uint64_t t = t0 + (uint64_t)k;
+    DQ_LAUNCH(*h, PK_PROPOSE, launch_mala_propose<T>(*h, B, r, grad, r_prop, xi, tau, seed, t, t_dev, s));
+    dq_status st = run_forward<T>(*h, params, r_prop, B, true, la_prop, sg_prop, e_prop, ws + plan.fwd,
+                                  ws_bytes - plan.fwd, s, g_prop);
+    if (st != DQ_OK) return st;
+    DQ_LAUNCH(*h, PK_ACCEPT, launch_mala_accept<T>(*h, B, r, logabs, grad, r_prop, la_prop, sg_prop, g_prop, xi, e_loc,
+                                                   e_prop, tau, seed, t, t_dev,
+                                                   reinterpret_cast<unsigned long long*>(n_acc), s));
+  }
+  if (t_dev && n_steps > 0) DQ_CU(launch_advance_counter(t_dev, (uint64_t)n_steps, s));
+  return DQ_OK;
+}
 }  // namespace
 }  // namespace dq
 
@@ -842,6 +902,7 @@ dq_status dq_workspace_size(dq_handle h, int64_t B, int32_t op, size_t* bytes) {
     case DQ_OP_MCMC: *bytes = plan_mcmc(*h, std::max<int64_t>(B, 1), el).total; return DQ_OK;
     case DQ_OP_GRAD: *bytes = plan_grad(*h, Bc, el).total; return DQ_OK;
     case DQ_OP_LOSS_WEIGHTS: *bytes = loss_scratch_bytes(std::max<int64_t>(B, 1)); return DQ_OK;
+    case DQ_OP_MALA: *bytes = plan_mala(*h, std::max<int64_t>(B, 1), el).total; return DQ_OK;
   }
   return DQ_ERR_ARG;
 }
@@ -916,6 +977,29 @@ dq_status mcmc_step(dq_handle h, const void* params, void* r, void* logabs, int6
                     size_t ws_bytes, void* stream) {
   return mcmc_impl(h, params, r, logabs, B, n_steps, step_size, seed, step_counter, nullptr, n_accepted, ws, ws_bytes,
                    stream);
+}
+
+dq_status mala_step(dq_handle h, const void* params, void* r, void* logabs, void* grad, void* e_loc,
+                    int32_t grad_valid, int64_t B, int32_t n_steps, double tau, uint64_t seed, uint64_t step_counter,
+                    uint64_t* step_counter_dev, int64_t* n_accepted, void* ws, size_t ws_bytes, void* stream) {
+  dq_status st = check_handle(h);
+  if (st != DQ_OK) return st;
+  if (B < 0 || n_steps < 0 || !(tau > 0) || !isfinite(tau)) return DQ_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (B == 0 || (n_steps == 0 && grad_valid)) {
+    if (n_accepted && cudaMemsetAsync(n_accepted, 0, sizeof(int64_t), s) != cudaSuccess) return DQ_ERR_CUDA;
+    if (step_counter_dev && n_steps > 0 && launch_advance_counter(step_counter_dev, (uint64_t)n_steps, s) != cudaSuccess)
+      return DQ_ERR_CUDA;
+    return DQ_OK;
+  }
+  if (!params || !r || !logabs || !grad) return DQ_ERR_ARG;
+  auto* w = static_cast<unsigned char*>(ws);
+  if (h->precision == DQ_FP64)
+    return run_mala<double>(h, (const double*)params, (double*)r, (double*)logabs, (double*)grad, (double*)e_loc,
+                            grad_valid, B, n_steps, tau, seed, step_counter, step_counter_dev, n_accepted, w, ws_bytes,
+                            s);
+  return run_mala<float>(h, (const float*)params, (float*)r, (float*)logabs, (float*)grad, (float*)e_loc, grad_valid, B,
+                         n_steps, tau, seed, step_counter, step_counter_dev, n_accepted, w, ws_bytes, s);
 }
 
 dq_status mcmc_step_dev(dq_handle h, const void* params, void* r, void* logabs, int64_t B, int32_t n_steps,

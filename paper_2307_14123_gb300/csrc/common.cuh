@@ -189,7 +189,7 @@ template <class T>
 cudaError_t launch_jastrow_sum(const dq_handle_s& h, const FwdDims& d, FwdBuffers<T> b, cudaStream_t s);
 template <class T>
 cudaError_t launch_combine(const dq_handle_s& h, const FwdDims& d, const T* params, FwdBuffers<T> b,
-                           T* logabs, int8_t* sign, T* e_loc, cudaStream_t s);
+                           T* logabs, int8_t* sign, T* e_loc, cudaStream_t s, T* grad = nullptr);
 
 // ---- sampler, reductions, loss weights (mcmc.cu) ---------------------------
 // Step t of the Philox counter: t, plus *t_base when t_base (device) is non-null.
@@ -202,6 +202,15 @@ cudaError_t launch_accept(const dq_handle_s& h, int64_t B, T* r, T* logabs, cons
                           const uint64_t* t_base, unsigned long long* n_acc, cudaStream_t s);
 // *c += n on the device (advances a device-resident step counter).
 cudaError_t launch_advance_counter(uint64_t* c, uint64_t n, cudaStream_t s);
+// Langevin (MALA) proposal and acceptance; g: d log|psi| / d r at r, g_prop at r_prop.
+template <class T>
+cudaError_t launch_mala_propose(const dq_handle_s& h, int64_t B, const T* r, const T* g, T* r_prop, T* xi,
+                                double tau, uint64_t seed, uint64_t t, const uint64_t* t_base, cudaStream_t s);
+template <class T>
+cudaError_t launch_mala_accept(const dq_handle_s& h, int64_t B, T* r, T* logabs, T* g, const T* r_prop,
+                               const T* la_prop, const int8_t* sign_prop, const T* g_prop, const T* xi, T* e_loc,
+                               const T* e_prop, double tau, uint64_t seed, uint64_t t, const uint64_t* t_base,
+                               unsigned long long* n_acc, cudaStream_t s);
 template <class T>
 cudaError_t launch_esum(const T* e, int64_t B, double* out2, unsigned int* status, cudaStream_t s);
 template <class T>

@@ -1198,7 +1198,8 @@ __global__ void __launch_bounds__(kCombineThreads)
                    const T* __restrict__ params, const double* __restrict__ Zn, const int* __restrict__ pair_ij,
                    const int* __restrict__ pair_of, int64_t Bc, int N, int n_up, int M, int K, int C, int D, int E, int n_ee, int64_t c_off,
                    int64_t wJ2_off, int use_jastrow, int use_cusp, double alpha, double Vnn, T* __restrict__ logabs,
-                   int8_t* __restrict__ sign_out, T* __restrict__ e_loc, unsigned int* __restrict__ status) {
+                   int8_t* __restrict__ sign_out, T* __restrict__ e_loc, T* __restrict__ grad_out,
+                   unsigned int* __restrict__ status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N3 = 3 * N;
   double* wp = reinterpret_cast<double*>(smem_raw);  // [K] determinant weights
@@ -1342,6 +1343,7 @@ __global__ void __launch_bounds__(kCombineThreads)
       }
     }
     g2part += g * g;
+    if (grad_out) grad_out[b * N3 + k] = (T)g;  // d log|psi| / d r_k
   }
   // Laplacian terms
   double lpart = lJpart;
@@ -1532,14 +1534,15 @@ cudaError_t launch_jastrow_sum(const dq_handle_s& h, const FwdDims& d, FwdBuffer
 
 template <class T>
 cudaError_t launch_combine(const dq_handle_s& h, const FwdDims& d, const T* params, FwdBuffers<T> b, T* logabs,
-                           int8_t* sign, T* e_loc, cudaStream_t s) {
+                           int8_t* sign, T* e_loc, cudaStream_t s, T* grad) {
   const size_t smem = (2 * (size_t)d.K + 3 * (size_t)d.D + 32 + 3 * (size_t)d.N) * sizeof(double);
   auto kern = combine_kernel<T>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)d.Bc, kCombineThreads, smem, s>>>(
       b.det, b.jh, b.geo, params, h.d_Z, h.d_pair_ij, h.d_pair_of, d.Bc, d.N, d.n_up, d.M, d.K, d.C, d.D, h.edges.n_all,
-      h.edges.n_ee, h.off.c, h.off.w_J2, h.use_jastrow, h.use_cusp, h.alpha, h.Vnn, logabs, sign, e_loc, h.d_status);
+      h.edges.n_ee, h.off.c, h.off.w_J2, h.use_jastrow, h.use_cusp, h.alpha, h.Vnn, logabs, sign, e_loc, grad,
+      h.d_status);
   return cudaGetLastError();
 }
 
@@ -1560,7 +1563,7 @@ cudaError_t launch_combine(const dq_handle_s& h, const FwdDims& d, const T* para
                                              cudaStream_t);                                                       \
   template cudaError_t launch_jastrow_sum<T>(const dq_handle_s&, const FwdDims&, FwdBuffers<T>, cudaStream_t);    \
   template cudaError_t launch_combine<T>(const dq_handle_s&, const FwdDims&, const T*, FwdBuffers<T>, T*,         \
-                                         int8_t*, T*, cudaStream_t);
+                                         int8_t*, T*, cudaStream_t, T*);
 
 DQ_INSTANTIATE(float)
 DQ_INSTANTIATE(double)

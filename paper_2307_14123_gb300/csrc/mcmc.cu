@@ -80,6 +80,96 @@ __global__ void accept_kernel(T* __restrict__ r, T* __restrict__ logabs, const T
   if ((threadIdx.x % 32) == 0 && m && n_acc) atomicAdd(n_acc, (unsigned long long)__popc(m));
 }
 
+// ---------------------------------------------------------------------------
+// Metropolis-adjusted Langevin step (Sec. 5, the Langevin sampler).  Drift
+// v_i = d log|psi| / d r_i per electron, limited as
+//   vbar_i = v_i (sqrt(1 + 2 tau |v_i|^2) - 1) / (tau |v_i|^2)
+// (Umrigar, Nightingale, Runge 1993, a = 1); proposal r' = r + tau vbar(r) +
+// sqrt(tau) xi with the Metropolis sampler's normals; acceptance of
+//   log alpha = 2 (log|psi'| - log|psi|) + |xi|^2 / 2 - |r - r' - tau vbar(r')|^2 / (2 tau)
+// against the same uniforms (FP64 arithmetic).
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ double drift_factor(const T* g, double tau) {  // vbar_i / v_i for the electron at g
+  const double v2 = (double)g[0] * g[0] + (double)g[1] * g[1] + (double)g[2] * g[2];
+  const double s = tau * v2;
+  return s > 0 ? (sqrt(1.0 + 2.0 * s) - 1.0) / s : 1.0;
+}
+
+template <class T>
+__global__ void mala_propose_kernel(const T* __restrict__ r, const T* __restrict__ g, T* __restrict__ r_prop,
+                                    T* __restrict__ xi_out, int64_t B, int N3, double tau, uint64_t seed, uint64_t t,
+                                    const uint64_t* __restrict__ t_base) {
+  if (t_base) t += *t_base;
+  const int nblk = (N3 + 3) / 4;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= B * nblk) return;
+  const int64_t b = gid / nblk;
+  const int blk = (int)(gid % nblk);
+  const uint4 ctr = make_uint4((uint32_t)b, (uint32_t)t, (kTagPropose << 24) | (uint32_t)blk, (uint32_t)(t >> 32));
+  const uint4 x = philox4x32_10(ctr, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const double ra = sqrt(-2.0 * log(unit_uniform(x.x))), ta = 2.0 * M_PI * unit_uniform(x.y);
+  const double rb = sqrt(-2.0 * log(unit_uniform(x.z))), tb = 2.0 * M_PI * unit_uniform(x.w);
+  double z[4];
+  sincos(ta, &z[1], &z[0]);
+  sincos(tb, &z[3], &z[2]);
+  z[0] *= ra;
+  z[1] *= ra;
+  z[2] *= rb;
+  z[3] *= rb;
+  const double sq = sqrt(tau);
+  for (int m = 0; m < 4; ++m) {
+    const int q = 4 * blk + m;
+    if (q >= N3) break;
+    const T* gi = g + b * N3 + (q / 3) * 3;
+    const double vbar = drift_factor(gi, tau) * (double)g[b * N3 + q];
+    r_prop[b * N3 + q] = (T)((double)r[b * N3 + q] + tau * vbar + sq * z[m]);
+    xi_out[b * N3 + q] = (T)z[m];
+  }
+}
+
+template <class T>
+__global__ void mala_accept_kernel(T* __restrict__ r, T* __restrict__ logabs, T* __restrict__ g,
+                                   const T* __restrict__ r_prop, const T* __restrict__ la_prop,
+                                   const int8_t* __restrict__ sign_prop, const T* __restrict__ g_prop,
+                                   const T* __restrict__ xi, T* __restrict__ e_loc, const T* __restrict__ e_prop,
+                                   int64_t B, int N3, double tau, uint64_t seed, uint64_t t,
+                                   const uint64_t* __restrict__ t_base, unsigned long long* __restrict__ n_acc) {
+  if (t_base) t += *t_base;
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool acc = false;
+  if (b < B) {
+    const T* rb = r + b * N3;
+    const T* rp = r_prop + b * N3;
+    const T* gp = g_prop + b * N3;
+    double fwd = 0.0, bwd = 0.0;
+    for (int q = 0; q < N3; q += 3) {
+      const double f = drift_factor(gp + q, tau);
+      for (int x = 0; x < 3; ++x) {
+        const double z = (double)xi[b * N3 + q + x];
+        fwd += z * z;
+        const double e = (double)rb[q + x] - (double)rp[q + x] - tau * f * (double)gp[q + x];
+        bwd += e * e;
+      }
+    }
+    const uint4 ctr = make_uint4((uint32_t)b, (uint32_t)t, kTagAccept << 24, (uint32_t)(t >> 32));
+    const uint4 x = philox4x32_10(ctr, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const double lu = log(unit_uniform(x.x));
+    const double la = 2.0 * ((double)la_prop[b] - (double)logabs[b]) + 0.5 * fwd - bwd / (2.0 * tau);
+    acc = sign_prop[b] != 0 && lu < la;
+    if (acc) {
+      for (int q = 0; q < N3; ++q) {
+        r[b * N3 + q] = rp[q];
+        g[b * N3 + q] = gp[q];
+      }
+      logabs[b] = la_prop[b];
+      if (e_loc) e_loc[b] = e_prop[b];
+    }
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, acc);
+  if ((threadIdx.x % 32) == 0 && m && n_acc) atomicAdd(n_acc, (unsigned long long)__popc(m));
+}
+
 // Deterministic FP64 sums of the finite local energies: one CTA, fixed order.
 constexpr int kRedThreads = 1024;
 
@@ -189,6 +279,25 @@ cudaError_t launch_propose(const dq_handle_s& h, int64_t B, const T* r, T* r_pro
   return cudaGetLastError();
 }
 
+template <class T>
+cudaError_t launch_mala_propose(const dq_handle_s& h, int64_t B, const T* r, const T* g, T* r_prop, T* xi,
+                                double tau, uint64_t seed, uint64_t t, const uint64_t* t_base, cudaStream_t s) {
+  const int N3 = 3 * h.N, nblk = (N3 + 3) / 4;
+  const int64_t n = B * nblk;
+  mala_propose_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(r, g, r_prop, xi, B, N3, tau, seed, t, t_base);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_mala_accept(const dq_handle_s& h, int64_t B, T* r, T* logabs, T* g, const T* r_prop,
+                               const T* la_prop, const int8_t* sign_prop, const T* g_prop, const T* xi, T* e_loc,
+                               const T* e_prop, double tau, uint64_t seed, uint64_t t, const uint64_t* t_base,
+                               unsigned long long* n_acc, cudaStream_t s) {
+  mala_accept_kernel<T><<<(unsigned)((B + 255) / 256), 256, 0, s>>>(
+      r, logabs, g, r_prop, la_prop, sign_prop, g_prop, xi, e_loc, e_prop, B, 3 * h.N, tau, seed, t, t_base, n_acc);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_advance_counter(uint64_t* c, uint64_t n, cudaStream_t s) {
   advance_counter_kernel<<<1, 1, 0, s>>>(c, n);
   return cudaGetLastError();
@@ -223,6 +332,12 @@ cudaError_t launch_loss_weights(const T* e, int64_t B, double k, T* w, double* s
                                          const uint64_t*, cudaStream_t);                                          \
   template cudaError_t launch_accept<T>(const dq_handle_s&, int64_t, T*, T*, const T*, const T*, const int8_t*,    \
                                         uint64_t, uint64_t, const uint64_t*, unsigned long long*, cudaStream_t);  \
+  template cudaError_t launch_mala_propose<T>(const dq_handle_s&, int64_t, const T*, const T*, T*, T*, double,      \
+                                              uint64_t, uint64_t, const uint64_t*, cudaStream_t);                 \
+  template cudaError_t launch_mala_accept<T>(const dq_handle_s&, int64_t, T*, T*, T*, const T*, const T*,          \
+                                             const int8_t*, const T*, const T*, T*, const T*, double, uint64_t,   \
+                                             uint64_t,                                                            \
+                                             const uint64_t*, unsigned long long*, cudaStream_t);                 \
   template cudaError_t launch_esum<T>(const T*, int64_t, double*, unsigned int*, cudaStream_t);                   \
   template cudaError_t launch_loss_weights<T>(const T*, int64_t, double, T*, double*, double*, cudaStream_t);
 DQ_INST(float)
