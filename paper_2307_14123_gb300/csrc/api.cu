@@ -312,18 +312,20 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
       DQ_LAUNCH(h, kb + PK_EDGE_HIDDEN, launch_edge_hidden<T>(h, d, params, l, bf, s));
       const int e0[3] = {0, h.edges.n_par, h.edges.n_ee};
       const int ng[3] = {h.edges.n_par, h.edges.n_anti, h.edges.n_en};
-      for (int t = 0; t < 3; ++t) {
+      if (use_t3) {  // the three edge types' filters in one launch
+        T3JobDesc jd[3];
+        const int64_t seg = (int64_t)E * ej * D;
+        for (int t = 0; t < 3; ++t)
+          jd[t] = T3JobDesc{reinterpret_cast<const float*>(bf.eh) + (int64_t)e0[t] * ej * D, (int64_t)ng[t] * ej, nb,
+                            seg, D, D, w2_t3(l, t, 0), w2_t3(l, t, 1), D,
+                            reinterpret_cast<const float*>(params + y.b2[t]), ej,
+                            reinterpret_cast<float*>(bf.ew) + (int64_t)e0[t] * ej * D, D, seg, false};
+        DQ_LAUNCH(h, kb + PK_GEMM_EDGE, gemm_tf32x3_tc_jobs(jd, 3, h.d_status, s));
+      }
+      for (int t = 0; t < 3 && !use_t3; ++t) {
         if (ng[t] == 0) continue;
         const RowMap m{(int64_t)ng[t] * ej, (int64_t)E * ej * D, D};
-        if (use_t3) {
-          const int64_t seg = (int64_t)E * ej * D;
-          DQ_LAUNCH(h, kb + PK_GEMM_EDGE,
-                    gemm_tf32x3_tc_seg(reinterpret_cast<const float*>(bf.eh) + (int64_t)e0[t] * ej * D,
-                                       (int64_t)ng[t] * ej, nb, seg, D, D, w2_t3(l, t, 0), w2_t3(l, t, 1), D,
-                                       reinterpret_cast<const float*>(params + y.b2[t]), ej,
-                                       reinterpret_cast<float*>(bf.ew) + (int64_t)e0[t] * ej * D, D, seg,
-                                       h.d_status, s));
-        } else {
+        {
           DQ_LAUNCH(h, kb + PK_GEMM_EDGE, gemm_nt<T>(bf.eh + (int64_t)e0[t] * ej * D, m, params + y.W2[t],
                                                      params + y.b2[t], ej, bf.ew + (int64_t)e0[t] * ej * D, m,
                                                      nb * ng[t] * ej, D, D, false, s));
@@ -364,18 +366,21 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
       DQ_LAUNCH(h, kb + PK_UPDATE, launch_update<T>(h, d, params, l == 0, bf, s));
     }
     const int ns[2] = {h.n_up, h.n_dn}, i0[2] = {0, h.n_up};
-    for (int sg = 0; sg < 2; ++sg) {
+    if (use_t3) {  // both spins' orbitals in one launch
+      T3JobDesc jd[2];
+      for (int sg = 0; sg < 2; ++sg)
+        jd[sg] = T3JobDesc{reinterpret_cast<const float*>(bf.F) + (int64_t)i0[sg] * C * D, (int64_t)ns[sg] * C, nb,
+                           (int64_t)N * C * D, D, D, wo_t3(sg, 0), wo_t3(sg, 1), K * ns[sg],
+                           reinterpret_cast<const float*>(params + h.off.b_o[sg]), C,
+                           reinterpret_cast<float*>(bf.phi) + (int64_t)i0[sg] * C * Wo, Wo, (int64_t)N * C * Wo,
+                           false};
+      DQ_LAUNCH(h, kb + PK_GEMM_ORBITAL, gemm_tf32x3_tc_jobs(jd, 2, h.d_status, s));
+    }
+    for (int sg = 0; sg < 2 && !use_t3; ++sg) {
       if (ns[sg] == 0) continue;
       const RowMap mx{(int64_t)ns[sg] * C, (int64_t)N * C * D, D};
       const RowMap my{(int64_t)ns[sg] * C, (int64_t)N * C * Wo, Wo};
-      if (use_t3) {
-        DQ_LAUNCH(h, kb + PK_GEMM_ORBITAL,
-                  gemm_tf32x3_tc_seg(reinterpret_cast<const float*>(bf.F) + (int64_t)i0[sg] * C * D,
-                                     (int64_t)ns[sg] * C, nb, (int64_t)N * C * D, D, D, wo_t3(sg, 0), wo_t3(sg, 1),
-                                     K * ns[sg], reinterpret_cast<const float*>(params + h.off.b_o[sg]), C,
-                                     reinterpret_cast<float*>(bf.phi) + (int64_t)i0[sg] * C * Wo, Wo,
-                                     (int64_t)N * C * Wo, h.d_status, s));
-      } else {
+      {
         DQ_LAUNCH(h, kb + PK_GEMM_ORBITAL,
                   gemm_nt<T>(bf.F + (int64_t)i0[sg] * C * D, mx, params + h.off.W_o[sg], params + h.off.b_o[sg], C,
                              bf.phi + (int64_t)i0[sg] * C * Wo, my, nb * ns[sg] * C, K * ns[sg], D, false, s));

@@ -128,6 +128,22 @@ cudaError_t gemm_tf32x3_tc_seg(const float* X, int64_t seg_rows, int64_t n_seg, 
                                int64_t ldx, const float* Wbig, const float* Wsmall, int n_out, const float* bias,
                                int bias_period, float* Y, int64_t ldy, int64_t y_seg_stride, unsigned int* status,
                                cudaStream_t s, bool accumulate = false);
+// A list of such GEMMs in one persistent launch (tiles of all jobs share the
+// grid); at most 16 per launch (more are split over launches).
+struct T3JobDesc {
+  const float* X;
+  int64_t seg_rows, n_seg, x_seg_stride;
+  int K;
+  int64_t ldx;
+  const float *Wbig, *Wsmall;
+  int n_out;
+  const float* bias;
+  int bias_period;
+  float* Y;
+  int64_t ldy, y_seg_stride;
+  bool accumulate;
+};
+cudaError_t gemm_tf32x3_tc_jobs(const T3JobDesc* jobs, int n, unsigned int* status, cudaStream_t s);
 // TF32 high / low parts of the transpose of W [rows][cols] (for products X W).
 cudaError_t split_tf32_t(const float* W, int rows, int cols, float* big, float* small, cudaStream_t s);
 // Row reduction part[split][o][a] = sum_r X[r][o] Y[r][a] on the tensor cores (3 x TF32); rows in n_seg

@@ -234,34 +234,36 @@ struct MsgSmem {
 };
 constexpr int kMsgRing = 4;     // senders in flight per warp (asynchronous copies)
 constexpr int kMsgWarps = 8;
+// L: features per CTA (lanes of a group; 32, or 16 for molecules whose pair
+// tables do not fit at 32).
 template <class T>
-__host__ __device__ inline MsgSmem msg_smem_layout(int N, int IB, int CB, bool stage_w1) {
+__host__ __device__ inline MsgSmem msg_smem_layout(int N, int IB, int CB, bool stage_w1, int L) {
   MsgSmem m{};
   int o = 0;
   const int rows = N * N + IB;  // padded: receivers past the end read zeros
-  m.w0 = o; o += rows * kMsgLanes;
-  m.w1 = o; o += stage_w1 ? rows * kMsgLanes : 0;
+  m.w0 = o; o += rows * L;
+  m.w1 = o; o += stage_w1 ? rows * L : 0;
   m.us = o; o += (N + IB) * N * 3;  // u_ij,x (zero diagonal, zero padding)
   m.invd = o; o += N * N;
-  m.z0c = o; o += N * kMsgLanes;       // z_j[0]
-  m.zself = o; o += 3 * N * kMsgLanes;  // dz_j / dr_j,x
-  m.sp = o; o += 13 * N * kMsgLanes;   // (b) [N][3 x][3], (c) [N][3], (d) [N]
-  o = (o + 3) / 4 * 4;                 // 16-byte alignment of the copy ring
-  m.ring = o; o += kMsgWarps * kMsgRing * CB * kMsgLanes;  // [warp][slot][q][lane] z of senders in flight
+  m.z0c = o; o += N * L;       // z_j[0]
+  m.zself = o; o += 3 * N * L;  // dz_j / dr_j,x
+  m.sp = o; o += 13 * N * L;   // (b) [N][3 x][3], (c) [N][3], (d) [N]
+  o = (o + 3) / 4 * 4;         // 16-byte alignment of the copy ring
+  m.ring = o; o += kMsgWarps * 32 * kMsgRing * CB;  // [group][slot][q][lane] z of senders in flight
   m.ps = o * (int)sizeof(T);           // byte offset of the int pair table
   m.total_bytes = m.ps + N * N * (int)sizeof(int);
   return m;
 }
 
-template <class T, class TO, int IB, int CB>
+template <class T, class TO, int IB, int CB, int L>
 __global__ void __launch_bounds__(256, 2)
     messages_kernel(const T* __restrict__ Z, const T* __restrict__ z0, const T* __restrict__ ew,
                     const T* __restrict__ geo, const T* __restrict__ Y, const int* __restrict__ pair_of, int N,
                     int n_up, int M, int C, int D, int E, int n_ee, int z_const, int stage_w1,
                     TO* __restrict__ msg) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int L = kMsgLanes, ej = 3;
-  const MsgSmem lay = msg_smem_layout<T>(N, IB, CB, stage_w1 != 0);
+  constexpr int ej = 3;
+  const MsgSmem lay = msg_smem_layout<T>(N, IB, CB, stage_w1 != 0, L);
   T* sm = reinterpret_cast<T*>(smem_raw);
   T* W0 = sm + lay.w0;  // [(j*N + i)][L]  w_ij
   T* W1 = sm + lay.w1;  //                 w'_ij
@@ -1445,17 +1447,22 @@ cudaError_t launch_messages_t(const dq_handle_s& h, const FwdDims& d, const T* p
   }
   if (d.D % kMsgLanes) return cudaErrorInvalidConfiguration;
   constexpr int IB = msg_ib<T>(), CB = sizeof(T) == 4 ? 4 : 2;
-  auto kern = messages_kernel<T, TO, IB, CB>;
   bool stage_w1 = true;
-  MsgSmem lay = msg_smem_layout<T>(d.N, IB, CB, stage_w1);
+  int L = kMsgLanes;
+  MsgSmem lay = msg_smem_layout<T>(d.N, IB, CB, stage_w1, L);
   if (lay.total_bytes > 112 * 1024) {  // keep two CTAs per SM, else fetch w' from global memory
     stage_w1 = false;
-    lay = msg_smem_layout<T>(d.N, IB, CB, stage_w1);
+    lay = msg_smem_layout<T>(d.N, IB, CB, stage_w1, L);
+  }
+  if (lay.total_bytes > 220 * 1024) {  // large molecules: 16 features per CTA
+    L = 16;
+    lay = msg_smem_layout<T>(d.N, IB, CB, stage_w1, L);
   }
   if (lay.total_bytes > 220 * 1024) return cudaErrorInvalidConfiguration;
+  auto kern = L == 16 ? messages_kernel<T, TO, IB, CB, 16> : messages_kernel<T, TO, IB, CB, kMsgLanes>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total_bytes);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)d.Bc, d.D / kMsgLanes);
+  dim3 grid((unsigned)d.Bc, d.D / L);
   kern<<<grid, 32 * kMsgWarps, lay.total_bytes, s>>>(b.Z, b.z0, b.ew, b.geo, Y, h.d_pair_of, d.N, d.n_up, d.M, d.C, d.D,
                                           h.edges.n_all, h.edges.n_ee, z_const ? 1 : 0, stage_w1 ? 1 : 0, out);
   return cudaGetLastError();

@@ -354,11 +354,35 @@ __device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint6
       : "memory");
 }
 
+// One launch runs a list of GEMMs (jobs): the edge filters of every edge type,
+// the orbitals of both spins, or one step of several molecules.  Tiles of all
+// jobs form one sequence that the persistent CTAs take in turn; a job's tiles
+// are contiguous, so every role finds the job of a tile by its prefix counts.
+// A 128-row block holds rb rows of each of sb = TC_BM / rb segments (rb <
+// TC_BM only if seg_rows <= rb), or a TC_BM-row block of one segment.  A tile is
+// T3_SUB such blocks sharing the W tile; each has its own accumulator.
+struct T3Job {
+  CUtensorMap a, bb, bs;  // X (segmented rows), W big, W small
+  const float* bias;
+  float* Y;
+  int64_t seg_rows, n_seg, ldy, y_seg_stride;
+  int64_t rb_per_seg, n_mblk, tile_end;  // tile_end: tiles of jobs 0 .. this one
+  int rb, sb, n_out, nk, n_tiles_n, bias_period, accumulate;
+};
+constexpr int kT3MaxJobs = 16;
+struct T3Jobs {
+  T3Job j[kT3MaxJobs];
+  int n;
+};
+__device__ __forceinline__ const T3Job& t3_job(const T3Jobs& J, int64_t t, int64_t& tl) {
+  int m = 0;
+  while (m + 1 < J.n && t >= J.j[m].tile_end) ++m;
+  tl = t - (m > 0 ? J.j[m - 1].tile_end : 0);
+  return J.j[m];
+}
+
 __global__ void __launch_bounds__(T3_THREADS, 1)
-    gemm_tf32x3_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmBb,
-                          const __grid_constant__ CUtensorMap tmBs, int64_t seg_rows, int64_t n_seg, int rb,
-                          int n_out, int K, const float* __restrict__ bias, int bias_period, float* __restrict__ Y,
-                          int64_t ldy, int64_t y_seg_stride, int accumulate, unsigned int* __restrict__ status) {
+    gemm_tf32x3_tc_kernel(const __grid_constant__ T3Jobs jobs, unsigned int* __restrict__ status) {
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
   // per stage: [x half 0, x half 1] (x_big after conversion), [x_small half 0, half 1], w_big, w_small
@@ -376,19 +400,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   __shared__ float ep_stage[4][32][33];  // epilogue transpose, one block per epilogue warp
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int nk = (K + T3_BK - 1) / T3_BK;  // a ragged last K block reads zeros past K
-  const int n_tiles_n = (n_out + TC_BN - 1) / TC_BN;
-  // A 128-row block holds rb rows of each of sb = TC_BM / rb segments (rb < TC_BM only if
-  // seg_rows <= rb), or a TC_BM-row block of one segment.  A tile is T3_SUB such blocks
-  // sharing the W tile; each has its own accumulator.
-  const int sb = TC_BM / rb;
-  const int64_t rb_per_seg = (seg_rows + rb - 1) / rb;
-  const int64_t n_mblk = ((n_seg + sb - 1) / sb) * rb_per_seg;
-  const int64_t n_tiles = ((n_mblk + T3_SUB - 1) / T3_SUB) * n_tiles_n;  // (row-block pair, column block)
-  auto mblock = [&](int64_t mb, int& seg, int& m0) {  // first segment and row of 128-row block mb
-    seg = (int)(mb / rb_per_seg) * sb;
-    m0 = (int)(mb % rb_per_seg) * rb;
-  };
+  const int64_t n_tiles = jobs.j[jobs.n - 1].tile_end;  // (job, row-block pair, column block)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < T3_STAGES; ++s) {
@@ -418,12 +430,18 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     if (lane == 0) {  // TMA producer
       int64_t g = 0;
       for (int64_t t = blockIdx.x; t < n_tiles && !s_abort; t += gridDim.x) {
-        const int64_t mp = t / n_tiles_n;
-        const int n0 = (int)(t % n_tiles_n) * TC_BN;
+        int64_t tl;
+        const T3Job& J = t3_job(jobs, t, tl);
+        const int64_t mp = tl / J.n_tiles_n;
+        const int n0 = (int)(tl % J.n_tiles_n) * TC_BN;
         int seg[T3_SUB], m0[T3_SUB];
 #pragma unroll
-        for (int h = 0; h < T3_SUB; ++h) mblock(mp * T3_SUB + h, seg[h], m0[h]);  // past the end: zero fill
-        for (int kb = 0; kb < nk; ++kb, ++g) {
+        for (int h = 0; h < T3_SUB; ++h) {  // first segment and row of each 128-row block (past the end: zero fill)
+          const int64_t mb = mp * T3_SUB + h;
+          seg[h] = (int)(mb / J.rb_per_seg) * J.sb;
+          m0[h] = (int)(mb % J.rb_per_seg) * J.rb;
+        }
+        for (int kb = 0; kb < J.nk; ++kb, ++g) {
           const int s = (int)(g % T3_STAGES);
           const int64_t u = g / T3_STAGES;
           if (u >= 1 && !mbar_wait(&empty[s], (uint32_t)((u - 1) & 1))) {
@@ -433,9 +451,9 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
           mbar_expect_tx(&full[s], T3_SUB * T3_TILE_A + 2 * T3_TILE_B);
 #pragma unroll
           for (int h = 0; h < T3_SUB; ++h)
-            tma_load_3d(sA + (s * T3_SUB + h) * T3_TILE_A, &tmA, kb * T3_BK, m0[h], seg[h], &full[s]);
-          tma_load_2d(sBb + s * T3_TILE_B, &tmBb, kb * T3_BK, n0, &full[s]);
-          tma_load_2d(sBs + s * T3_TILE_B, &tmBs, kb * T3_BK, n0, &full[s]);
+            tma_load_3d(sA + (s * T3_SUB + h) * T3_TILE_A, &J.a, kb * T3_BK, m0[h], seg[h], &full[s]);
+          tma_load_2d(sBb + s * T3_TILE_B, &J.bb, kb * T3_BK, n0, &full[s]);
+          tma_load_2d(sBs + s * T3_TILE_B, &J.bs, kb * T3_BK, n0, &full[s]);
         }
       }
     }
@@ -451,6 +469,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
           break;
         }
         tc_fence_after();
+        int64_t tl;
+        const int nk = t3_job(jobs, t, tl).nk;
         bool ok = true;
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = (int)(g % T3_STAGES);
@@ -487,6 +507,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     const int ct = threadIdx.x - 6 * 32;  // 0..127
     int64_t g = 0;
     for (int64_t t = blockIdx.x; t < n_tiles && !s_abort; t += gridDim.x) {
+      int64_t tl;
+      const int nk = t3_job(jobs, t, tl).nk;
       for (int kb = 0; kb < nk; ++kb, ++g) {
         const int s = (int)(g % T3_STAGES);
         if (!mbar_wait(&full[s], (uint32_t)((g / T3_STAGES) & 1))) {
@@ -529,16 +551,22 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         break;
       }
       tc_fence_after();
-      const int64_t mp = t / n_tiles_n;
-      const int n0 = (int)(t % n_tiles_n) * TC_BN;
+      int64_t tl;
+      const T3Job& J = t3_job(jobs, t, tl);
+      const int64_t mp = tl / J.n_tiles_n;
+      const int n0 = (int)(tl % J.n_tiles_n) * TC_BN;
       const int tr = q * 32 + lane;  // row of the 128-row block
+      const float* bias = J.bias;
+      const int n_out = J.n_out;
 #pragma unroll 1
       for (int h = 0; h < T3_SUB; ++h) {
         const int64_t mb = mp * T3_SUB + h;
-        const int64_t seg = (mb / rb_per_seg) * sb + tr / rb;
-        const int64_t row = (mb % rb_per_seg) * rb + tr % rb;  // row within the segment
-        const bool add_bias = bias != nullptr && (row % bias_period) == 0;
-        float* yrow = mb < n_mblk && row < seg_rows && seg < n_seg ? Y + seg * y_seg_stride + row * ldy + n0 : nullptr;
+        const int64_t seg = (mb / J.rb_per_seg) * J.sb + tr / J.rb;
+        const int64_t row = (mb % J.rb_per_seg) * J.rb + tr % J.rb;  // row within the segment
+        const bool add_bias = bias != nullptr && (row % J.bias_period) == 0;
+        float* yrow = mb < J.n_mblk && row < J.seg_rows && seg < J.n_seg
+                          ? J.Y + seg * J.y_seg_stride + row * J.ldy + n0
+                          : nullptr;
         for (int c0 = 0; c0 < TC_BN; c0 += 32) {
           uint32_t vv[32];
           tmem_ld32(tmem + (uint32_t)((a * T3_SUB + h) * TC_TMEM_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0,
@@ -546,7 +574,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
           const int n = n0 + c0 + lane;
           const bool col_ok = n < n_out;
           store_block_32x32(vv, st, lane, yrow ? yrow + c0 : nullptr, add_bias,
-                            bias != nullptr && col_ok ? bias[n] : 0.f, col_ok, accumulate != 0);
+                            bias != nullptr && col_ok ? bias[n] : 0.f, col_ok, J.accumulate != 0);
         }
       }
       tc_fence_before();
@@ -861,33 +889,71 @@ cudaError_t split_tf32_t(const float* W, int rows, int cols, float* big, float* 
   return cudaGetLastError();
 }
 
+cudaError_t gemm_tf32x3_tc_jobs(const T3JobDesc* d, int n, unsigned int* status, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = t3_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  T3Jobs J;
+  J.n = 0;
+  int64_t tiles = 0;
+  auto flush = [&]() -> cudaError_t {
+    if (J.n == 0) return cudaSuccess;
+    const int64_t grid = tiles < sms ? tiles : sms;
+    gemm_tf32x3_tc_kernel<<<(unsigned)grid, T3_THREADS, smem, s>>>(J, status);
+    J.n = 0;
+    tiles = 0;
+    return cudaGetLastError();
+  };
+  for (int i = 0; i < n; ++i) {
+    const T3JobDesc& q = d[i];
+    if (q.seg_rows <= 0 || q.n_seg <= 0 || q.n_out <= 0) continue;
+    if (q.K % 4 || q.ldx % 4 || q.x_seg_stride % 4 || (uintptr_t)q.X % 16 || (uintptr_t)q.Wbig % 16 ||
+        (uintptr_t)q.Wsmall % 16 || q.bias_period <= 0 || q.seg_rows > (int64_t)INT32_MAX ||
+        q.n_seg > (int64_t)INT32_MAX)
+      return cudaErrorInvalidValue;
+    T3Job& j = J.j[J.n];
+    int rb = TC_BM;  // short segments: several per tile, rb (a power of two >= 8) rows each
+    while (rb > 8 && rb / 2 >= q.seg_rows) rb /= 2;
+    if (!make_map_seg_f32(&j.a, q.X, q.seg_rows, q.n_seg, q.K, q.ldx,
+                          q.n_seg > 1 ? q.x_seg_stride : q.seg_rows * q.ldx, rb) ||
+        !make_map(&j.bb, q.Wbig, q.n_out, q.K, q.K, TC_BN, true) ||
+        !make_map(&j.bs, q.Wsmall, q.n_out, q.K, q.K, TC_BN, true))
+      return cudaErrorInvalidValue;
+    j.bias = q.bias;
+    j.Y = q.Y;
+    j.seg_rows = q.seg_rows;
+    j.n_seg = q.n_seg;
+    j.ldy = q.ldy;
+    j.y_seg_stride = q.y_seg_stride;
+    j.rb = rb;
+    j.sb = TC_BM / rb;
+    j.rb_per_seg = (q.seg_rows + rb - 1) / rb;
+    j.n_mblk = ((q.n_seg + j.sb - 1) / j.sb) * j.rb_per_seg;
+    j.n_out = q.n_out;
+    j.nk = (q.K + T3_BK - 1) / T3_BK;  // a ragged last K block reads zeros past K
+    j.n_tiles_n = (q.n_out + TC_BN - 1) / TC_BN;
+    j.bias_period = q.bias_period;
+    j.accumulate = q.accumulate ? 1 : 0;
+    tiles += ((j.n_mblk + T3_SUB - 1) / T3_SUB) * j.n_tiles_n;
+    j.tile_end = tiles;
+    if (++J.n == kT3MaxJobs) {
+      e = flush();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return flush();
+}
+
 cudaError_t gemm_tf32x3_tc_seg(const float* X, int64_t seg_rows, int64_t n_seg, int64_t x_seg_stride, int K,
                                int64_t ldx, const float* Wbig, const float* Wsmall, int n_out, const float* bias,
                                int bias_period, float* Y, int64_t ldy, int64_t y_seg_stride, unsigned int* status,
                                cudaStream_t s, bool accumulate) {
-  if (seg_rows <= 0 || n_seg <= 0 || n_out <= 0) return cudaSuccess;
-  if (K % 4 || ldx % 4 || x_seg_stride % 4 || (uintptr_t)X % 16 || (uintptr_t)Wbig % 16 ||
-      (uintptr_t)Wsmall % 16 || bias_period <= 0 || seg_rows > (int64_t)INT32_MAX || n_seg > (int64_t)INT32_MAX)
-    return cudaErrorInvalidValue;
-  int rb = TC_BM;  // short segments: several per tile, rb (a power of two >= 8) rows each
-  while (rb > 8 && rb / 2 >= seg_rows) rb /= 2;
-  CUtensorMap ma, mbb, mbs;
-  if (!make_map_seg_f32(&ma, X, seg_rows, n_seg, K, ldx, n_seg > 1 ? x_seg_stride : seg_rows * ldx, rb) ||
-      !make_map(&mbb, Wbig, n_out, K, K, TC_BN, true) || !make_map(&mbs, Wsmall, n_out, K, K, TC_BN, true))
-    return cudaErrorInvalidValue;
-  const size_t smem = t3_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(gemm_tf32x3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t mblk = ((n_seg + TC_BM / rb - 1) / (TC_BM / rb)) * ((seg_rows + rb - 1) / rb);
-  const int64_t tiles = ((mblk + T3_SUB - 1) / T3_SUB) * ((n_out + TC_BN - 1) / TC_BN);
-  const int64_t grid = tiles < sms ? tiles : sms;
-  gemm_tf32x3_tc_kernel<<<(unsigned)grid, T3_THREADS, smem, s>>>(ma, mbb, mbs, seg_rows, n_seg, rb, n_out, K, bias,
-                                                                bias_period, Y, ldy, y_seg_stride,
-                                                                accumulate ? 1 : 0, status);
-  return cudaGetLastError();
+  const T3JobDesc d{X, seg_rows, n_seg, x_seg_stride, K, ldx, Wbig, Wsmall, n_out, bias, bias_period, Y, ldy,
+                    y_seg_stride, accumulate};
+  return gemm_tf32x3_tc_jobs(&d, 1, status, s);
 }
 
 // FP32 rows [n_seg][rps] x cols, dims {cols, rps, n_seg}, box {128, rb, 32 / rb}, no swizzle

@@ -381,3 +381,14 @@ def workload(name):
     if name == "c4h4_bf16":  # C4H4, D=256, L=4, K=32, 8192 walkers
         return Workload(name, molecule("C4H4"), AnsatzCfg(256, 4, 32), 8192, 3, 3, "bf16")
     raise KeyError(name)
+
+
+BATCH_MOLECULES = (("H2O", 8192), ("NH3", 8192), ("C2H4", 4096), ("C6H6", 2048))
+
+
+def batch_workload(name="mixed_fp32"):
+    """Molecules with uneven electron counts (10, 10, 16, 42) that run as one batch:
+    each D=128, L=3, K=8, parameters and walkers from seed 4, its own walker count."""
+    prec = {"mixed_fp32": "fp32", "mixed_bf16": "bf16"}[name]
+    cfg = AnsatzCfg(128, 3, 8)
+    return [Workload(f"{m.lower()}_{prec}", molecule(m), cfg, B, 4, 4, prec) for m, B in BATCH_MOLECULES]

@@ -220,6 +220,18 @@ def test_n2_fp32_full_batch_sampled():
     assert e2[0] == pytest.approx(np.sum(el[fin].astype(np.float64)), rel=1e-9)
 
 
+@pytest.mark.parametrize("k", range(len(fx.BATCH_MOLECULES)))
+def test_batch_molecules_fp32_sample(k):
+    """Each molecule of the uneven batch (H2O, NH3, C2H4, C6H6: D=128, L=3, K=8) on its own
+    handle, FP32, against the oracle on a few walkers (benzene: 42 electrons, 21 x 21 spin blocks)."""
+    wl = fx.batch_workload("mixed_fp32")[k]
+    h = _handle(wl.system, wl.cfg, "fp32")
+    B = 12 if wl.system.n_elec < 40 else 4
+    theta, r, th_t, r_t = _inputs(wl.system, wl.cfg, "fp32", B, wl.param_seed, wl.walker_seed)
+    la, sg, el = _np(*h.local_energy(th_t, r_t))
+    _check_fp32(la, sg, el, oracle.Oracle(wl.system, wl.cfg).local_energy(theta, r, with_grad=True), r, wl.name)
+
+
 # ----------------------------------------------------------------------------
 # Metropolis sampler, teacher-forced against the oracle
 # ----------------------------------------------------------------------------
