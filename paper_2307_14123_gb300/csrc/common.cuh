@@ -71,6 +71,39 @@ struct Profiler {
 };
 }  // namespace dq
 
+namespace dq {
+// Table of a grouped launch: one kernel launch over several molecules (or
+// other independent problems).  Entry m owns blocks end[m-1] .. end[m] - 1 of
+// the 1-D grid, which it sees as an nbx x ny grid (flattened x-major); tag
+// selects a variant of the kernel body for the entry.
+constexpr int kMaxGroup = 8;
+template <class A>
+struct Grp {
+  A a[kMaxGroup];
+  int64_t end[kMaxGroup];
+  int64_t nbx[kMaxGroup];
+  int ny[kMaxGroup];
+  int tag[kMaxGroup];
+  int n;
+  void add(const A& x, int64_t bx, int by = 1, int t = 0) {
+    a[n] = x;
+    nbx[n] = bx;
+    ny[n] = by;
+    tag[n] = t;
+    end[n] = (n > 0 ? end[n - 1] : 0) + bx * by;
+    ++n;
+  }
+  int64_t blocks() const { return n > 0 ? end[n - 1] : 0; }
+};
+template <class A>
+__device__ __forceinline__ int grp_find(const Grp<A>& g, int64_t blk, int64_t& local) {
+  int m = 0;
+  while (m + 1 < g.n && blk >= g.end[m]) ++m;
+  local = blk - (m > 0 ? g.end[m - 1] : 0);
+  return m;
+}
+}  // namespace dq
+
 struct dq_handle_s {
   int device = 0;
   int precision = 0;
@@ -178,6 +211,49 @@ struct FwdBuffers {
   void* msg_bf;  // [Bc][N][C][3D]  messages, BF16 (replaces msg)
   void* F_bf;    // [Bc][N][C][D]   BF16 copy of the embeddings
 };
+
+// Grouped sampler and reduction launches (mcmc.cu), one entry per molecule.
+template <class T>
+cudaError_t launch_propose_group(const dq_handle_s* const* hs, int n, const int64_t* B, const T* const* r,
+                                 T* const* r_prop, double step, uint64_t seed, uint64_t t, const uint64_t* t_base,
+                                 cudaStream_t s);
+template <class T>
+cudaError_t launch_accept_group(const dq_handle_s* const* hs, int n, const int64_t* B, T* const* r, T* const* logabs,
+                                const T* const* r_prop, const T* const* la_prop, const int8_t* const* sign_prop,
+                                uint64_t seed, uint64_t t, const uint64_t* t_base, unsigned long long* const* n_acc,
+                                cudaStream_t s);
+template <class T>
+cudaError_t launch_esum_group(int n, const T* const* e, const int64_t* B, double* const* out2,
+                              unsigned int* const* status, cudaStream_t s);
+template <class T>
+cudaError_t launch_loss_weights_group(int n, const T* const* e, const int64_t* B, double k, T* const* w,
+                                      double* const* stats, double* const* scratch, cudaStream_t s);
+
+// One molecule of a grouped launch: its handle, chunk dimensions, parameters and buffers.
+template <class T>
+struct MolFwd {
+  const dq_handle_s* h;
+  FwdDims d;
+  const T* params;
+  FwdBuffers<T> b;
+};
+template <class T>
+cudaError_t launch_geometry_group(const MolFwd<T>* m, int n, const T* const* r, cudaStream_t s);
+template <class T>
+cudaError_t launch_edge_hidden_group(const MolFwd<T>* m, int n, int layer, cudaStream_t s);
+template <class T>
+cudaError_t launch_layer0_node_group(const MolFwd<T>* m, int n, cudaStream_t s);
+template <class T>
+cudaError_t launch_messages_group(const MolFwd<T>* m, int n, int layer, bool z_const, cudaStream_t s);
+template <class T>
+cudaError_t launch_update_group(const MolFwd<T>* m, int n, bool from_spin, cudaStream_t s);
+template <class T>
+cudaError_t launch_orbital_det_group(const MolFwd<T>* m, int n, cudaStream_t s);
+template <class T>
+cudaError_t launch_jastrow_sum_group(const MolFwd<T>* m, int n, cudaStream_t s);
+template <class T>
+cudaError_t launch_combine_group(const MolFwd<T>* m, int n, T* const* logabs, int8_t* const* sign, T* const* e_loc,
+                                 T* const* grad, cudaStream_t s);
 
 template <class T>
 cudaError_t launch_geometry(const dq_handle_s& h, const FwdDims& d, const T* r, FwdBuffers<T> b, cudaStream_t s);

@@ -25,6 +25,8 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "det_util.cuh"
 
@@ -48,10 +50,27 @@ __device__ __forceinline__ double warp_sum(double v) {
 // Geometry and Gaussian features
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void geometry_kernel(const T* __restrict__ r, const T* __restrict__ R, const int* __restrict__ pair_ij,
+struct geometry_kernel_args {
+  const T* r;
+  const T* R;
+  const int* pair_ij;
+  int64_t Bc;
+  int N;
+  int M;
+  int n_ee;
+  int E;
+  int Q;
+  int ej;
+  double rc;
+  T* geo;
+  T* rbf;
+};
+
+template <class T>
+__device__ __forceinline__ void geometry_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const T* __restrict__ r, const T* __restrict__ R, const int* __restrict__ pair_ij,
                                 int64_t Bc, int N, int M, int n_ee, int E, int Q, int ej, double rc,
                                 T* __restrict__ geo, T* __restrict__ rbf) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gid = (int64_t)bx_ * blockDim.x + threadIdx.x;
   if (gid >= Bc * E) return;
   const int64_t b = gid / E;
   const int e = (int)(gid % E);
@@ -82,6 +101,22 @@ __global__ void geometry_kernel(const T* __restrict__ r, const T* __restrict__ R
   }
 }
 
+template <class T>
+__global__ void geometry_kernel(const T* __restrict__ r, const T* __restrict__ R, const int* __restrict__ pair_ij,
+                                int64_t Bc, int N, int M, int n_ee, int E, int Q, int ej, double rc,
+                                T* __restrict__ geo, T* __restrict__ rbf) {
+  geometry_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, r, R, pair_ij, Bc, N, M, n_ee, E, Q, ej, rc, geo, rbf);
+}
+
+// One launch over several molecules: block b runs entry m of the table.
+template <class T>
+__global__ void geometry_kernel_group(const __grid_constant__ Grp<geometry_kernel_args<T>> g) {
+  int64_t l_;
+  const int m_ = grp_find(g, blockIdx.x, l_);
+  const geometry_kernel_args<T>& a_ = g.a[m_];
+  geometry_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.r, a_.R, a_.pair_ij, a_.Bc, a_.N, a_.M, a_.n_ee, a_.E, a_.Q, a_.ej, a_.rc, a_.geo, a_.rbf);
+}
+
 // Edge hidden layer a = tanh(W1 e + b1) as a jet in d: (a, a', a'').
 // W1 and b1 of the three edge types are staged in shared memory once per CTA
 // ([t][q][a]); the persistent CTAs then stream blocks of kEdgesPerCta
@@ -105,8 +140,27 @@ struct Vec16<double> {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kHiddenThreads)
-    edge_hidden_kernel(const T* __restrict__ rbf, const T* __restrict__ params, int64_t Bc, int E, int n_par,
+struct edge_hidden_kernel_args {
+  const T* rbf;
+  const T* params;
+  int64_t Bc;
+  int E;
+  int n_par;
+  int n_ee;
+  int D;
+  int Q;
+  int ej;
+  int64_t W1_0;
+  int64_t W1_1;
+  int64_t W1_2;
+  int64_t b1_0;
+  int64_t b1_1;
+  int64_t b1_2;
+  T* eh;
+};
+
+template <class T>
+__device__ __forceinline__ void edge_hidden_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const T* __restrict__ rbf, const T* __restrict__ params, int64_t Bc, int E, int n_par,
                        int n_ee, int D, int Q, int ej, int64_t W1_0, int64_t W1_1, int64_t W1_2, int64_t b1_0,
                        int64_t b1_1, int64_t b1_2, T* __restrict__ eh) {
   using V = typename Vec16<T>::type;
@@ -126,7 +180,7 @@ __global__ void __launch_bounds__(kHiddenThreads)
   const int epp = blockDim.x / tpe;              // edges in parallel
   const int er = threadIdx.x / tpe, a0 = (threadIdx.x % tpe) * VW;
   const int64_t nrows = Bc * E;
-  for (int64_t be0 = (int64_t)blockIdx.x * kEdgesPerCta; be0 < nrows; be0 += (int64_t)gridDim.x * kEdgesPerCta) {
+  for (int64_t be0 = (int64_t)bx_ * kEdgesPerCta; be0 < nrows; be0 += (int64_t)nbx_ * kEdgesPerCta) {
     const int nb = (int)min((int64_t)kEdgesPerCta, nrows - be0);
     __syncthreads();  // previous block's features consumed (and the weights staged)
     for (int k = threadIdx.x; k < nb * ej * Q; k += blockDim.x) fs[k] = rbf[be0 * ej * Q + k];
@@ -185,15 +239,54 @@ __global__ void __launch_bounds__(kHiddenThreads)
   }
 }
 
+template <class T>
+__global__ void __launch_bounds__(kHiddenThreads) edge_hidden_kernel(const T* __restrict__ rbf, const T* __restrict__ params, int64_t Bc, int E, int n_par,
+                       int n_ee, int D, int Q, int ej, int64_t W1_0, int64_t W1_1, int64_t W1_2, int64_t b1_0,
+                       int64_t b1_1, int64_t b1_2, T* __restrict__ eh) {
+  edge_hidden_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, rbf, params, Bc, E, n_par, n_ee, D, Q, ej, W1_0, W1_1, W1_2, b1_0, b1_1, b1_2, eh);
+}
+
+// One launch over several molecules: block b runs entry m of the table.
+template <class T>
+__global__ void __launch_bounds__(kHiddenThreads) edge_hidden_kernel_group(const __grid_constant__ Grp<edge_hidden_kernel_args<T>> g) {
+  int64_t l_;
+  const int m_ = grp_find(g, blockIdx.x, l_);
+  const edge_hidden_kernel_args<T>& a_ = g.a[m_];
+  edge_hidden_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.rbf, a_.params, a_.Bc, a_.E, a_.n_par, a_.n_ee, a_.D, a_.Q, a_.ej, a_.W1_0, a_.W1_1, a_.W1_2, a_.b1_0, a_.b1_1, a_.b1_2, a_.eh);
+}
+
 // z0[s][a] = (W_h^0 E_spin[s])[a]: the node map of layer 0 on the spin embeddings.
 template <class T>
-__global__ void layer0_node_kernel(const T* __restrict__ params, int D, int64_t E_spin, int64_t W_h, T* z0) {
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+struct layer0_node_kernel_args {
+  const T* params;
+  int D;
+  int64_t E_spin;
+  int64_t W_h;
+  T* z0;
+};
+
+template <class T>
+__device__ __forceinline__ void layer0_node_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const T* __restrict__ params, int D, int64_t E_spin, int64_t W_h, T* z0) {
+  const int gid = bx_ * blockDim.x + threadIdx.x;
   if (gid >= 2 * D) return;
   const int s = gid / D, a = gid % D;
   T acc = 0;
   for (int c = 0; c < D; ++c) acc += params[W_h + (int64_t)a * D + c] * params[E_spin + s * D + c];
   z0[gid] = acc;
+}
+
+template <class T>
+__global__ void layer0_node_kernel(const T* __restrict__ params, int D, int64_t E_spin, int64_t W_h, T* z0) {
+  layer0_node_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, params, D, E_spin, W_h, z0);
+}
+
+// One launch over several molecules: block b runs entry m of the table.
+template <class T>
+__global__ void layer0_node_kernel_group(const __grid_constant__ Grp<layer0_node_kernel_args<T>> g) {
+  int64_t l_;
+  const int m_ = grp_find(g, blockIdx.x, l_);
+  const layer0_node_kernel_args<T>& a_ = g.a[m_];
+  layer0_node_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.params, a_.D, a_.E_spin, a_.W_h, a_.z0);
 }
 
 // ---------------------------------------------------------------------------
@@ -255,9 +348,28 @@ __host__ __device__ inline MsgSmem msg_smem_layout(int N, int IB, int CB, bool s
   return m;
 }
 
+template <class T, class TO>
+struct messages_kernel_args {
+  const T* Z;
+  const T* z0;
+  const T* ew;
+  const T* geo;
+  const T* Y;
+  const int* pair_of;
+  int N;
+  int n_up;
+  int M;
+  int C;
+  int D;
+  int E;
+  int n_ee;
+  int z_const;
+  int stage_w1;
+  TO* msg;
+};
+
 template <class T, class TO, int IB, int CB, int L>
-__global__ void __launch_bounds__(256, 2)
-    messages_kernel(const T* __restrict__ Z, const T* __restrict__ z0, const T* __restrict__ ew,
+__device__ __forceinline__ void messages_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const T* __restrict__ Z, const T* __restrict__ z0, const T* __restrict__ ew,
                     const T* __restrict__ geo, const T* __restrict__ Y, const int* __restrict__ pair_of, int N,
                     int n_up, int M, int C, int D, int E, int n_ee, int z_const, int stage_w1,
                     TO* __restrict__ msg) {
@@ -278,8 +390,8 @@ __global__ void __launch_bounds__(256, 2)
   T* SPc = SP + 9 * N * L;   // [i][3]
   T* SPd = SP + 12 * N * L;  // [i]
 
-  const int64_t b = blockIdx.x;
-  const int d0 = blockIdx.y * L;
+  const int64_t b = bx_;
+  const int d0 = by_ * L;
   const int tid = threadIdx.x, lane = tid % L, grp = tid / L, ngroups = blockDim.x / L;
   const T* EWb = ew + b * E * ej * D + d0 + lane;  // this lane's feature of every edge filter
   const T* Zb = Z + b * N * C * D + d0 + lane;
@@ -538,20 +650,62 @@ __global__ void __launch_bounds__(256, 2)
   }
 }
 
+template <class T, class TO, int IB, int CB, int L>
+__global__ void __launch_bounds__(256, 2) messages_kernel(const T* __restrict__ Z, const T* __restrict__ z0, const T* __restrict__ ew,
+                    const T* __restrict__ geo, const T* __restrict__ Y, const int* __restrict__ pair_of, int N,
+                    int n_up, int M, int C, int D, int E, int n_ee, int z_const, int stage_w1,
+                    TO* __restrict__ msg) {
+  messages_kernel_body<T, TO, IB, CB, L>(blockIdx.x, blockIdx.y, gridDim.x, Z, z0, ew, geo, Y, pair_of, N, n_up, M, C, D, E, n_ee, z_const, stage_w1, msg);
+}
+
+// One launch over several molecules: block b runs entry m of the table; the
+// entry's tag is its features per CTA (32, or 16 for large molecules).
+template <class T, class TO, int IB, int CB>
+__global__ void __launch_bounds__(256, 2) messages_kernel_group(const __grid_constant__ Grp<messages_kernel_args<T, TO>> g) {
+  int64_t l_;
+  const int m_ = grp_find(g, blockIdx.x, l_);
+  const messages_kernel_args<T, TO>& a_ = g.a[m_];
+  if (g.tag[m_] == 16)
+    messages_kernel_body<T, TO, IB, CB, 16>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.Z, a_.z0, a_.ew, a_.geo,
+                                            a_.Y, a_.pair_of, a_.N, a_.n_up, a_.M, a_.C, a_.D, a_.E, a_.n_ee,
+                                            a_.z_const, a_.stage_w1, a_.msg);
+  else
+    messages_kernel_body<T, TO, IB, CB, kMsgLanes>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.Z, a_.z0, a_.ew,
+                                                   a_.geo, a_.Y, a_.pair_of, a_.N, a_.n_up, a_.M, a_.C, a_.D, a_.E,
+                                                   a_.n_ee, a_.z_const, a_.stage_w1, a_.msg);
+}
+
 // Value-only messages (C = 1): one CTA per (walker, 32 features); a warp per
 // receiver, lanes over features; pair table and z of the walker staged in
 // shared memory, sender loops split by spin (no per-edge branch).
 template <class T, class TO>
-__global__ void __launch_bounds__(256)
-    messages_value_kernel(const T* __restrict__ Z, const T* __restrict__ z0, const T* __restrict__ ew,
+struct messages_value_kernel_args {
+  const T* Z;
+  const T* z0;
+  const T* ew;
+  const T* Y;
+  const int* pair_of;
+  int64_t Bc;
+  int N;
+  int n_up;
+  int M;
+  int D;
+  int E;
+  int n_ee;
+  int z_const;
+  TO* msg;
+};
+
+template <class T, class TO>
+__device__ __forceinline__ void messages_value_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const T* __restrict__ Z, const T* __restrict__ z0, const T* __restrict__ ew,
                           const T* __restrict__ Y, const int* __restrict__ pair_of, int64_t Bc, int N, int n_up,
                           int M, int D, int E, int n_ee, int z_const, TO* __restrict__ msg) {
   extern __shared__ __align__(16) unsigned char mv_smem[];
   T* Zs = reinterpret_cast<T*>(mv_smem);           // [N][32]
   int* Ps = reinterpret_cast<int*>(Zs + N * 32);   // [N][N]
-  const int64_t b = blockIdx.x;
+  const int64_t b = bx_;
   const int lane = threadIdx.x % 32, wq = threadIdx.x / 32, nw = blockDim.x / 32;
-  const int d = blockIdx.y * 32 + lane;
+  const int d = by_ * 32 + lane;
   for (int k = threadIdx.x; k < N * N; k += blockDim.x) Ps[k] = pair_of[k];
   for (int j = wq; j < N; j += nw)
     Zs[j * 32 + lane] = d >= D ? T(0) : (z_const ? z0[(j < n_up ? 0 : D) + d] : Z[(b * N + j) * D + d]);
@@ -576,14 +730,45 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+template <class T, class TO>
+__global__ void __launch_bounds__(256) messages_value_kernel(const T* __restrict__ Z, const T* __restrict__ z0, const T* __restrict__ ew,
+                          const T* __restrict__ Y, const int* __restrict__ pair_of, int64_t Bc, int N, int n_up,
+                          int M, int D, int E, int n_ee, int z_const, TO* __restrict__ msg) {
+  messages_value_kernel_body<T, TO>(blockIdx.x, blockIdx.y, gridDim.x, Z, z0, ew, Y, pair_of, Bc, N, n_up, M, D, E, n_ee, z_const, msg);
+}
+
+// One launch over several molecules: block b runs entry m of the table.
+template <class T, class TO>
+__global__ void __launch_bounds__(256) messages_value_kernel_group(const __grid_constant__ Grp<messages_value_kernel_args<T, TO>> g) {
+  int64_t l_;
+  const int m_ = grp_find(g, blockIdx.x, l_);
+  const messages_value_kernel_args<T, TO>& a_ = g.a[m_];
+  messages_value_kernel_body<T, TO>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.Z, a_.z0, a_.ew, a_.Y, a_.pair_of, a_.Bc, a_.N, a_.n_up, a_.M, a_.D, a_.E, a_.n_ee, a_.z_const, a_.msg);
+}
+
 // ---------------------------------------------------------------------------
 // Residual tanh update, Eq. (18): f <- f + tanh(P) with jets.
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void update_kernel(const T* __restrict__ P, const T* Fin, T* Fout, const T* __restrict__ E_spin,
+struct update_kernel_args {
+  const T* P;
+  const T* Fin;
+  T* Fout;
+  const T* E_spin;
+  int64_t Bc;
+  int N;
+  int n_up;
+  int C;
+  int D;
+  int from_spin;
+  __nv_bfloat16* Fbf;
+};
+
+template <class T>
+__device__ __forceinline__ void update_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const T* __restrict__ P, const T* Fin, T* Fout, const T* __restrict__ E_spin,
                               int64_t Bc, int N, int n_up, int C, int D, int from_spin,
                               __nv_bfloat16* __restrict__ Fbf) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gid = (int64_t)bx_ * blockDim.x + threadIdx.x;
   if (gid >= Bc * N * D) return;
   const int a = (int)(gid % D);
   const int64_t bi = gid / D;
@@ -608,6 +793,22 @@ __global__ void update_kernel(const T* __restrict__ P, const T* Fin, T* Fout, co
     __nv_bfloat16* fb = Fbf + bi * C * D + a;
     for (int c = 0; c < C; ++c) fb[(int64_t)c * D] = __float2bfloat16_rn((float)f[(int64_t)c * D]);
   }
+}
+
+template <class T>
+__global__ void update_kernel(const T* __restrict__ P, const T* Fin, T* Fout, const T* __restrict__ E_spin,
+                              int64_t Bc, int N, int n_up, int C, int D, int from_spin,
+                              __nv_bfloat16* __restrict__ Fbf) {
+  update_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, P, Fin, Fout, E_spin, Bc, N, n_up, C, D, from_spin, Fbf);
+}
+
+// One launch over several molecules: block b runs entry m of the table.
+template <class T>
+__global__ void update_kernel_group(const __grid_constant__ Grp<update_kernel_args<T>> g) {
+  int64_t l_;
+  const int m_ = grp_find(g, blockIdx.x, l_);
+  const update_kernel_args<T>& a_ = g.a[m_];
+  update_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.P, a_.Fin, a_.Fout, a_.E_spin, a_.Bc, a_.N, a_.n_up, a_.C, a_.D, a_.from_spin, a_.Fbf);
 }
 
 __global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int64_t n) {
@@ -750,15 +951,36 @@ __device__ double det_tangents_df(const T* phib, const T* env, const T* jenv, co
 }
 
 template <class T>
-__global__ void __launch_bounds__(128)
-    orbital_det_kernel(const T* __restrict__ phi, const T* __restrict__ geo, const T* __restrict__ params,
+struct orbital_det_kernel_args {
+  const T* phi;
+  const T* geo;
+  const T* params;
+  int64_t Bc;
+  int N;
+  int n_up;
+  int M;
+  int K;
+  int C;
+  int Wo;
+  int E;
+  int n_ee;
+  int64_t om_up;
+  int64_t om_dn;
+  int64_t ze_up;
+  int64_t ze_dn;
+  double* det;
+  unsigned long long* n_fp64;
+};
+
+template <class T>
+__device__ __forceinline__ void orbital_det_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const T* __restrict__ phi, const T* __restrict__ geo, const T* __restrict__ params,
                        int64_t Bc, int N, int n_up, int M, int K, int C, int Wo, int E, int n_ee,
                        int64_t om_up, int64_t om_dn, int64_t ze_up, int64_t ze_dn, double* __restrict__ det,
                        unsigned long long* __restrict__ n_fp64) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int warps = blockDim.x / 32;
-  const int64_t gw = (int64_t)blockIdx.x * warps + warp;
+  const int64_t gw = (int64_t)bx_ * warps + warp;
   const int n_dn = N - n_up;
   const int nmax = n_up > n_dn ? n_up : n_dn;
   const int N3 = 3 * N;
@@ -898,6 +1120,23 @@ __global__ void __launch_bounds__(128)
   if (lane == 0) out[2 + N3] = lap;
 }
 
+template <class T>
+__global__ void __launch_bounds__(128) orbital_det_kernel(const T* __restrict__ phi, const T* __restrict__ geo, const T* __restrict__ params,
+                       int64_t Bc, int N, int n_up, int M, int K, int C, int Wo, int E, int n_ee,
+                       int64_t om_up, int64_t om_dn, int64_t ze_up, int64_t ze_dn, double* __restrict__ det,
+                       unsigned long long* __restrict__ n_fp64) {
+  orbital_det_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, phi, geo, params, Bc, N, n_up, M, K, C, Wo, E, n_ee, om_up, om_dn, ze_up, ze_dn, det, n_fp64);
+}
+
+// One launch over several molecules: block b runs entry m of the table.
+template <class T>
+__global__ void __launch_bounds__(128) orbital_det_kernel_group(const __grid_constant__ Grp<orbital_det_kernel_args<T>> g) {
+  int64_t l_;
+  const int m_ = grp_find(g, blockIdx.x, l_);
+  const orbital_det_kernel_args<T>& a_ = g.a[m_];
+  orbital_det_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.phi, a_.geo, a_.params, a_.Bc, a_.N, a_.n_up, a_.M, a_.K, a_.C, a_.Wo, a_.E, a_.n_ee, a_.om_up, a_.om_dn, a_.ze_up, a_.ze_dn, a_.det, a_.n_fp64);
+}
+
 // ---------------------------------------------------------------------------
 // Determinant jets of the FP32 modes for spin blocks of at most kDetNR
 // electrons, one warp per matrix, on the FP32 pipes:
@@ -927,15 +1166,14 @@ __host__ __device__ inline size_t det_jets_smem_per_warp(int nmax, int N3) {
   return (bytes + 15) / 16 * 16;
 }
 
-__global__ void __launch_bounds__(128)
-    orbital_det_jets_kernel(const float* __restrict__ phi, const float* __restrict__ geo,
+__device__ __forceinline__ void orbital_det_jets_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const float* __restrict__ phi, const float* __restrict__ geo,
                             const float* __restrict__ params, int64_t Bc, int N, int n_up, int M, int K, int C,
                             int Wo, int E, int n_ee, int64_t om_up, int64_t om_dn, int64_t ze_up, int64_t ze_dn,
                             double* __restrict__ det, unsigned long long* __restrict__ n_fp64) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int warps = blockDim.x / 32;
-  const int64_t gw = (int64_t)blockIdx.x * warps + warp;
+  const int64_t gw = (int64_t)bx_ * warps + warp;
   const int n_dn = N - n_up;
   const int nmax = n_up > n_dn ? n_up : n_dn;
   const int N3 = 3 * N;
@@ -1158,16 +1396,64 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+__global__ void __launch_bounds__(128) orbital_det_jets_kernel(const float* __restrict__ phi, const float* __restrict__ geo,
+                            const float* __restrict__ params, int64_t Bc, int N, int n_up, int M, int K, int C,
+                            int Wo, int E, int n_ee, int64_t om_up, int64_t om_dn, int64_t ze_up, int64_t ze_dn,
+                            double* __restrict__ det, unsigned long long* __restrict__ n_fp64) {
+  orbital_det_jets_kernel_body(blockIdx.x, blockIdx.y, gridDim.x, phi, geo, params, Bc, N, n_up, M, K, C, Wo, E, n_ee, om_up, om_dn, ze_up, ze_dn, det, n_fp64);
+}
+
+// Determinants of several molecules in one launch (FP32 modes): tag 1 runs the
+// FP32 jet kernel body (spin blocks of at most kDetNR electrons), tag 0 the
+// general body (value-only calls, larger spin blocks).  Both use four warps per
+// CTA, one matrix per warp.
+__global__ void __launch_bounds__(128) orbital_det_mixed_group(const __grid_constant__ Grp<orbital_det_kernel_args<float>> g) {
+  int64_t l_;
+  const int m_ = grp_find(g, blockIdx.x, l_);
+  const orbital_det_kernel_args<float>& a_ = g.a[m_];
+  if (g.tag[m_])
+    orbital_det_jets_kernel_body(l_, 0, g.nbx[m_], a_.phi, a_.geo, a_.params, a_.Bc, a_.N, a_.n_up, a_.M, a_.K, a_.C,
+                                 a_.Wo, a_.E, a_.n_ee, a_.om_up, a_.om_dn, a_.ze_up, a_.ze_dn, a_.det, a_.n_fp64);
+  else
+    orbital_det_kernel_body<float>(l_, 0, g.nbx[m_], a_.phi, a_.geo, a_.params, a_.Bc, a_.N, a_.n_up, a_.M, a_.K,
+                                   a_.C, a_.Wo, a_.E, a_.n_ee, a_.om_up, a_.om_dn, a_.ze_up, a_.ze_dn, a_.det,
+                                   a_.n_fp64);
+}
+
 // Sum of embeddings over electrons, the input of the Jastrow factor (Eq. 24).
 template <class T>
-__global__ void jastrow_sum_kernel(const T* __restrict__ F, int64_t Bc, int N, int C, int D, T* __restrict__ js) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+struct jastrow_sum_kernel_args {
+  const T* F;
+  int64_t Bc;
+  int N;
+  int C;
+  int D;
+  T* js;
+};
+
+template <class T>
+__device__ __forceinline__ void jastrow_sum_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const T* __restrict__ F, int64_t Bc, int N, int C, int D, T* __restrict__ js) {
+  const int64_t gid = (int64_t)bx_ * blockDim.x + threadIdx.x;
   if (gid >= Bc * C * D) return;
   const int64_t b = gid / (C * D);
   const int64_t cd = gid % (C * D);
   T acc = 0;
   for (int i = 0; i < N; ++i) acc += F[(b * N + i) * C * D + cd];
   js[gid] = acc;
+}
+
+template <class T>
+__global__ void jastrow_sum_kernel(const T* __restrict__ F, int64_t Bc, int N, int C, int D, T* __restrict__ js) {
+  jastrow_sum_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, F, Bc, N, C, D, js);
+}
+
+// One launch over several molecules: block b runs entry m of the table.
+template <class T>
+__global__ void jastrow_sum_kernel_group(const __grid_constant__ Grp<jastrow_sum_kernel_args<T>> g) {
+  int64_t l_;
+  const int m_ = grp_find(g, blockIdx.x, l_);
+  const jastrow_sum_kernel_args<T>& a_ = g.a[m_];
+  jastrow_sum_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.F, a_.Bc, a_.N, a_.C, a_.D, a_.js);
 }
 
 // ---------------------------------------------------------------------------
@@ -1195,8 +1481,38 @@ __device__ double block_sum(double v, double* red) {
 }
 
 template <class T>
-__global__ void __launch_bounds__(kCombineThreads)
-    combine_kernel(const double* __restrict__ det, const T* __restrict__ jh, const T* __restrict__ geo,
+struct combine_kernel_args {
+  const double* det;
+  const T* jh;
+  const T* geo;
+  const T* params;
+  const double* Zn;
+  const int* pair_ij;
+  const int* pair_of;
+  int64_t Bc;
+  int N;
+  int n_up;
+  int M;
+  int K;
+  int C;
+  int D;
+  int E;
+  int n_ee;
+  int64_t c_off;
+  int64_t wJ2_off;
+  int use_jastrow;
+  int use_cusp;
+  double alpha;
+  double Vnn;
+  T* logabs;
+  int8_t* sign_out;
+  T* e_loc;
+  T* grad_out;
+  unsigned int* status;
+};
+
+template <class T>
+__device__ __forceinline__ void combine_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const double* __restrict__ det, const T* __restrict__ jh, const T* __restrict__ geo,
                    const T* __restrict__ params, const double* __restrict__ Zn, const int* __restrict__ pair_ij,
                    const int* __restrict__ pair_of, int64_t Bc, int N, int n_up, int M, int K, int C, int D, int E, int n_ee, int64_t c_off,
                    int64_t wJ2_off, int use_jastrow, int use_cusp, double alpha, double Vnn, T* __restrict__ logabs,
@@ -1210,7 +1526,7 @@ __global__ void __launch_bounds__(kCombineThreads)
   double* red = td + 3 * D;                          // [32]
   double* gJk = red + 32;                            // [3N] Jastrow gradient components
   __shared__ double s_scalar[4];
-  const int64_t b = blockIdx.x;
+  const int64_t b = bx_;
   const int tid = threadIdx.x;
   const bool jets = C > 1;
   const double* db = det + b * 2 * K * (N3 + 3);
@@ -1385,6 +1701,25 @@ __global__ void __launch_bounds__(kCombineThreads)
   }
 }
 
+template <class T>
+__global__ void __launch_bounds__(kCombineThreads) combine_kernel(const double* __restrict__ det, const T* __restrict__ jh, const T* __restrict__ geo,
+                   const T* __restrict__ params, const double* __restrict__ Zn, const int* __restrict__ pair_ij,
+                   const int* __restrict__ pair_of, int64_t Bc, int N, int n_up, int M, int K, int C, int D, int E, int n_ee, int64_t c_off,
+                   int64_t wJ2_off, int use_jastrow, int use_cusp, double alpha, double Vnn, T* __restrict__ logabs,
+                   int8_t* __restrict__ sign_out, T* __restrict__ e_loc, T* __restrict__ grad_out,
+                   unsigned int* __restrict__ status) {
+  combine_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, det, jh, geo, params, Zn, pair_ij, pair_of, Bc, N, n_up, M, K, C, D, E, n_ee, c_off, wJ2_off, use_jastrow, use_cusp, alpha, Vnn, logabs, sign_out, e_loc, grad_out, status);
+}
+
+// One launch over several molecules: block b runs entry m of the table.
+template <class T>
+__global__ void __launch_bounds__(kCombineThreads) combine_kernel_group(const __grid_constant__ Grp<combine_kernel_args<T>> g) {
+  int64_t l_;
+  const int m_ = grp_find(g, blockIdx.x, l_);
+  const combine_kernel_args<T>& a_ = g.a[m_];
+  combine_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.det, a_.jh, a_.geo, a_.params, a_.Zn, a_.pair_ij, a_.pair_of, a_.Bc, a_.N, a_.n_up, a_.M, a_.K, a_.C, a_.D, a_.E, a_.n_ee, a_.c_off, a_.wJ2_off, a_.use_jastrow, a_.use_cusp, a_.alpha, a_.Vnn, a_.logabs, a_.sign_out, a_.e_loc, a_.grad_out, a_.status);
+}
+
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -1552,6 +1887,278 @@ cudaError_t launch_combine(const dq_handle_s& h, const FwdDims& d, const T* para
       h.d_status);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Grouped launches: one launch per step over every molecule of a batch, each
+// molecule with its own dimensions, parameters and buffers (entry m of the
+// launch's table).  Block counts per molecule are those of the single-molecule
+// launchers above; dynamic shared memory is the largest any entry needs.
+// ---------------------------------------------------------------------------
+namespace {
+int device_sms() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+template <class A>
+cudaError_t check_group(const Grp<A>& g) {
+  if (g.blocks() <= 0) return cudaSuccess;
+  return g.blocks() > (int64_t)INT32_MAX ? cudaErrorInvalidConfiguration : cudaSuccess;
+}
+}  // namespace
+
+template <class T>
+cudaError_t launch_geometry_group(const MolFwd<T>* m, int n, const T* const* r, cudaStream_t s) {
+  if (n > kMaxGroup) return cudaErrorInvalidValue;
+  Grp<geometry_kernel_args<T>> g{};
+  for (int k = 0; k < n; ++k) {
+    const dq_handle_s& h = *m[k].h;
+    const FwdDims& d = m[k].d;
+    if (d.Bc <= 0) continue;
+    const T* R = nullptr;
+    if constexpr (sizeof(T) == 8) R = h.d_R; else R = h.d_Rf;
+    g.add({r[k], R, h.d_pair_ij, d.Bc, d.N, d.M, h.edges.n_ee, h.edges.n_all, d.Q, d.C > 1 ? 3 : 1, h.rc, m[k].b.geo,
+           m[k].b.rbf},
+          blocks(d.Bc * h.edges.n_all, 128));
+  }
+  if (g.n == 0) return cudaSuccess;
+  cudaError_t e = check_group(g);
+  if (e != cudaSuccess) return e;
+  geometry_kernel_group<T><<<(unsigned)g.blocks(), 128, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_edge_hidden_group(const MolFwd<T>* m, int n, int l, cudaStream_t s) {
+  if (n > kMaxGroup) return cudaErrorInvalidValue;
+  Grp<edge_hidden_kernel_args<T>> g{};
+  size_t smem = 0;
+  int64_t rows_all = 0;
+  for (int k = 0; k < n; ++k) rows_all += m[k].d.Bc > 0 ? m[k].d.Bc * m[k].h->edges.n_all : 0;
+  const int64_t grid_all = (int64_t)device_sms() * 6;  // persistent, 6 CTAs per SM, shared by row count
+  for (int k = 0; k < n; ++k) {
+    const dq_handle_s& h = *m[k].h;
+    const FwdDims& d = m[k].d;
+    if (d.Bc <= 0) continue;
+    const int ej = d.C > 1 ? 3 : 1;
+    const auto& y = h.off.layer[l];
+    const int64_t rows = d.Bc * h.edges.n_all;
+    smem = std::max(smem, ((size_t)3 * d.Q * d.D + 3 * d.D + (size_t)kEdgesPerCta * ej * d.Q) * sizeof(T));
+    const int64_t nblk = (rows + kEdgesPerCta - 1) / kEdgesPerCta;
+    int64_t share = (grid_all * rows + rows_all - 1) / rows_all;
+    share = std::max<int64_t>(1, std::min(share, nblk));
+    g.add({m[k].b.rbf, m[k].params, d.Bc, h.edges.n_all, h.edges.n_par, h.edges.n_ee, d.D, d.Q, ej, y.W1[0], y.W1[1],
+           y.W1[2], y.b1[0], y.b1[1], y.b1[2], m[k].b.eh},
+          share);
+  }
+  if (g.n == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(edge_hidden_kernel_group<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  edge_hidden_kernel_group<T><<<(unsigned)g.blocks(), kHiddenThreads, smem, s>>>(g);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_layer0_node_group(const MolFwd<T>* m, int n, cudaStream_t s) {
+  if (n > kMaxGroup) return cudaErrorInvalidValue;
+  Grp<layer0_node_kernel_args<T>> g{};
+  for (int k = 0; k < n; ++k) {
+    const dq_handle_s& h = *m[k].h;
+    g.add({m[k].params, m[k].d.D, h.off.E_spin, h.off.layer[0].W_h, m[k].b.z0}, blocks(2 * m[k].d.D, 128));
+  }
+  if (g.n == 0) return cudaSuccess;
+  layer0_node_kernel_group<T><<<(unsigned)g.blocks(), 128, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+namespace {
+template <class T, class TO>
+cudaError_t launch_messages_group_t(const MolFwd<T>* m, int n, int l, bool z_const, bool bf_out, cudaStream_t s) {
+  auto out_of = [&](const MolFwd<T>& q) -> TO* {
+    if constexpr (sizeof(TO) == 2) return static_cast<TO*>(q.b.msg_bf);
+    else return reinterpret_cast<TO*>(q.b.msg);
+  };
+  (void)bf_out;
+  if (m[0].d.C == 1) {
+    Grp<messages_value_kernel_args<T, TO>> g{};
+    size_t smem = 0;
+    int threads = 32;
+    for (int k = 0; k < n; ++k) threads = std::max(threads, 32 * (m[k].d.N < 8 ? m[k].d.N : 8));
+    for (int k = 0; k < n; ++k) {
+      const dq_handle_s& h = *m[k].h;
+      const FwdDims& d = m[k].d;
+      if (d.Bc <= 0) continue;
+      smem = std::max(smem, (size_t)d.N * 32 * sizeof(T) + (size_t)d.N * d.N * sizeof(int));
+      g.add({m[k].b.Z, m[k].b.z0, m[k].b.ew, m[k].params + h.off.layer[l].Y, h.d_pair_of, d.Bc, d.N, d.n_up, d.M, d.D,
+             h.edges.n_all, h.edges.n_ee, z_const ? 1 : 0, out_of(m[k])},
+            d.Bc, (d.D + 31) / 32);
+    }
+    if (g.n == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(messages_value_kernel_group<T, TO>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = check_group(g);
+    if (e != cudaSuccess) return e;
+    messages_value_kernel_group<T, TO><<<(unsigned)g.blocks(), threads, smem, s>>>(g);
+    return cudaGetLastError();
+  }
+  constexpr int IB = msg_ib<T>(), CB = sizeof(T) == 4 ? 4 : 2;
+  Grp<messages_kernel_args<T, TO>> g{};
+  int smem = 0;
+  for (int k = 0; k < n; ++k) {
+    const dq_handle_s& h = *m[k].h;
+    const FwdDims& d = m[k].d;
+    if (d.Bc <= 0) continue;
+    if (d.D % kMsgLanes) return cudaErrorInvalidConfiguration;
+    bool stage_w1 = true;
+    int L = kMsgLanes;
+    MsgSmem lay = msg_smem_layout<T>(d.N, IB, CB, stage_w1, L);
+    if (lay.total_bytes > 112 * 1024) {
+      stage_w1 = false;
+      lay = msg_smem_layout<T>(d.N, IB, CB, stage_w1, L);
+    }
+    if (lay.total_bytes > 220 * 1024) {
+      L = 16;
+      lay = msg_smem_layout<T>(d.N, IB, CB, stage_w1, L);
+    }
+    if (lay.total_bytes > 220 * 1024) return cudaErrorInvalidConfiguration;
+    smem = std::max(smem, lay.total_bytes);
+    g.add({m[k].b.Z, m[k].b.z0, m[k].b.ew, m[k].b.geo, m[k].params + h.off.layer[l].Y, h.d_pair_of, d.N, d.n_up, d.M,
+           d.C, d.D, h.edges.n_all, h.edges.n_ee, z_const ? 1 : 0, stage_w1 ? 1 : 0, out_of(m[k])},
+          d.Bc, d.D / L, L);
+  }
+  if (g.n == 0) return cudaSuccess;
+  auto kern = messages_kernel_group<T, TO, IB, CB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = check_group(g);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)g.blocks(), 32 * kMsgWarps, smem, s>>>(g);
+  return cudaGetLastError();
+}
+}  // namespace
+
+template <class T>
+cudaError_t launch_messages_group(const MolFwd<T>* m, int n, int l, bool z_const, cudaStream_t s) {
+  if (n > kMaxGroup) return cudaErrorInvalidValue;
+  if (n == 0) return cudaSuccess;
+  if constexpr (sizeof(T) == 4) {
+    if (m[0].b.msg_bf) return launch_messages_group_t<T, __nv_bfloat16>(m, n, l, z_const, true, s);
+  }
+  return launch_messages_group_t<T, T>(m, n, l, z_const, false, s);
+}
+
+template <class T>
+cudaError_t launch_update_group(const MolFwd<T>* m, int n, bool from_spin, cudaStream_t s) {
+  if (n > kMaxGroup) return cudaErrorInvalidValue;
+  Grp<update_kernel_args<T>> g{};
+  for (int k = 0; k < n; ++k) {
+    const FwdDims& d = m[k].d;
+    if (d.Bc <= 0) continue;
+    g.add({m[k].b.Z, m[k].b.F, m[k].b.F, m[k].params + m[k].h->off.E_spin, d.Bc, d.N, d.n_up, d.C, d.D,
+           from_spin ? 1 : 0, static_cast<__nv_bfloat16*>(m[k].b.F_bf)},
+          blocks(d.Bc * d.N * d.D, 256));
+  }
+  if (g.n == 0) return cudaSuccess;
+  cudaError_t e = check_group(g);
+  if (e != cudaSuccess) return e;
+  update_kernel_group<T><<<(unsigned)g.blocks(), 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_orbital_det_group(const MolFwd<T>* m, int n, cudaStream_t s) {
+  if (n > kMaxGroup) return cudaErrorInvalidValue;
+  Grp<orbital_det_kernel_args<T>> g{};
+  size_t smem = 0;
+  for (int k = 0; k < n; ++k) {
+    const dq_handle_s& h = *m[k].h;
+    const FwdDims& d = m[k].d;
+    if (d.Bc <= 0) continue;
+    const int nmax = d.n_up > d.n_dn ? d.n_up : d.n_dn;
+    const int nn = nmax * nmax;
+    const int64_t nmat = d.Bc * 2 * d.K;
+    const bool jets = sizeof(T) == 4 && d.C > 1 && nmax <= kDetNR;
+    if (jets) {
+      smem = std::max(smem, det_jets_smem_per_warp(nmax, 3 * d.N) * 4);
+    } else {
+      const size_t per_warp = ((size_t)nn * (3 * sizeof(double) + 10 * sizeof(T)) + 32 * sizeof(int) + 15) / 16 * 16;
+      if (per_warp * 4 > 200 * 1024) return cudaErrorInvalidConfiguration;  // grouped form: four warps per CTA
+      smem = std::max(smem, per_warp * 4);
+    }
+    g.add({m[k].b.phi, m[k].b.geo, m[k].params, d.Bc, d.N, d.n_up, d.M, d.K, d.C, d.K * nmax, h.edges.n_all,
+           h.edges.n_ee, h.off.omega[0], h.off.omega[1], h.off.zeta[0], h.off.zeta[1], m[k].b.det, h.d_fp64_count},
+          blocks(nmat, 4), 1, jets ? 1 : 0);
+  }
+  if (g.n == 0) return cudaSuccess;
+  cudaError_t e = check_group(g);
+  if (e != cudaSuccess) return e;
+  if constexpr (sizeof(T) == 4) {
+    e = cudaFuncSetAttribute(orbital_det_mixed_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    orbital_det_mixed_group<<<(unsigned)g.blocks(), 128, smem, s>>>(g);
+  } else {
+    e = cudaFuncSetAttribute(orbital_det_kernel_group<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    orbital_det_kernel_group<T><<<(unsigned)g.blocks(), 128, smem, s>>>(g);
+  }
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_jastrow_sum_group(const MolFwd<T>* m, int n, cudaStream_t s) {
+  if (n > kMaxGroup) return cudaErrorInvalidValue;
+  Grp<jastrow_sum_kernel_args<T>> g{};
+  for (int k = 0; k < n; ++k) {
+    const FwdDims& d = m[k].d;
+    if (d.Bc <= 0 || !m[k].h->use_jastrow) continue;
+    g.add({m[k].b.F, d.Bc, d.N, d.C, d.D, m[k].b.js}, blocks(d.Bc * d.C * d.D, 256));
+  }
+  if (g.n == 0) return cudaSuccess;
+  cudaError_t e = check_group(g);
+  if (e != cudaSuccess) return e;
+  jastrow_sum_kernel_group<T><<<(unsigned)g.blocks(), 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_combine_group(const MolFwd<T>* m, int n, T* const* logabs, int8_t* const* sign, T* const* e_loc,
+                                 T* const* grad, cudaStream_t s) {
+  if (n > kMaxGroup) return cudaErrorInvalidValue;
+  Grp<combine_kernel_args<T>> g{};
+  size_t smem = 0;
+  for (int k = 0; k < n; ++k) {
+    const dq_handle_s& h = *m[k].h;
+    const FwdDims& d = m[k].d;
+    if (d.Bc <= 0) continue;
+    smem = std::max(smem, (2 * (size_t)d.K + 3 * (size_t)d.D + 32 + 3 * (size_t)d.N) * sizeof(double));
+    g.add({m[k].b.det, m[k].b.jh, m[k].b.geo, m[k].params, h.d_Z, h.d_pair_ij, h.d_pair_of, d.Bc, d.N, d.n_up, d.M,
+           d.K, d.C, d.D, h.edges.n_all, h.edges.n_ee, h.off.c, h.off.w_J2, h.use_jastrow, h.use_cusp, h.alpha, h.Vnn,
+           logabs[k], sign[k], e_loc ? e_loc[k] : nullptr, grad ? grad[k] : nullptr, h.d_status},
+          d.Bc);
+  }
+  if (g.n == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(combine_kernel_group<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  combine_kernel_group<T><<<(unsigned)g.blocks(), kCombineThreads, smem, s>>>(g);
+  return cudaGetLastError();
+}
+
+#define DQ_INSTANTIATE_GROUP(T)                                                                                    \
+  template cudaError_t launch_geometry_group<T>(const MolFwd<T>*, int, const T* const*, cudaStream_t);            \
+  template cudaError_t launch_edge_hidden_group<T>(const MolFwd<T>*, int, int, cudaStream_t);                     \
+  template cudaError_t launch_layer0_node_group<T>(const MolFwd<T>*, int, cudaStream_t);                          \
+  template cudaError_t launch_messages_group<T>(const MolFwd<T>*, int, int, bool, cudaStream_t);                  \
+  template cudaError_t launch_update_group<T>(const MolFwd<T>*, int, bool, cudaStream_t);                         \
+  template cudaError_t launch_orbital_det_group<T>(const MolFwd<T>*, int, cudaStream_t);                          \
+  template cudaError_t launch_jastrow_sum_group<T>(const MolFwd<T>*, int, cudaStream_t);                          \
+  template cudaError_t launch_combine_group<T>(const MolFwd<T>*, int, T* const*, int8_t* const*, T* const*,      \
+                                               T* const*, cudaStream_t);
+DQ_INSTANTIATE_GROUP(float)
+DQ_INSTANTIATE_GROUP(double)
 
 #define DQ_INSTANTIATE(T)                                                                                          \
   template cudaError_t launch_geometry<T>(const dq_handle_s&, const FwdDims&, const T*, FwdBuffers<T>,            \

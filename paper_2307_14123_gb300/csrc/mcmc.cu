@@ -33,11 +33,23 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 __device__ __forceinline__ double unit_uniform(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386963e-10; }
 
 template <class T>
-__global__ void propose_kernel(const T* __restrict__ r, T* __restrict__ r_prop, int64_t B, int N3, double step,
+struct propose_kernel_args {
+  const T* r;
+  T* r_prop;
+  int64_t B;
+  int N3;
+  double step;
+  uint64_t seed;
+  uint64_t t;
+  const uint64_t* t_base;
+};
+
+template <class T>
+__device__ __forceinline__ void propose_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const T* __restrict__ r, T* __restrict__ r_prop, int64_t B, int N3, double step,
                                uint64_t seed, uint64_t t, const uint64_t* __restrict__ t_base) {
   if (t_base) t += *t_base;  // step counter kept in device memory
   const int nblk = (N3 + 3) / 4;
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gid = (int64_t)bx_ * blockDim.x + threadIdx.x;
   if (gid >= B * nblk) return;
   const int64_t b = gid / nblk;
   const int blk = (int)(gid % nblk);
@@ -59,12 +71,42 @@ __global__ void propose_kernel(const T* __restrict__ r, T* __restrict__ r_prop, 
 }
 
 template <class T>
-__global__ void accept_kernel(T* __restrict__ r, T* __restrict__ logabs, const T* __restrict__ r_prop,
+__global__ void propose_kernel(const T* __restrict__ r, T* __restrict__ r_prop, int64_t B, int N3, double step,
+                               uint64_t seed, uint64_t t, const uint64_t* __restrict__ t_base) {
+  propose_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, r, r_prop, B, N3, step, seed, t, t_base);
+}
+
+// One launch over several molecules: block b runs entry m of the table.
+template <class T>
+__global__ void propose_kernel_group(const __grid_constant__ Grp<propose_kernel_args<T>> g) {
+  int64_t l_;
+  const int m_ = grp_find(g, blockIdx.x, l_);
+  const propose_kernel_args<T>& a_ = g.a[m_];
+  propose_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.r, a_.r_prop, a_.B, a_.N3, a_.step, a_.seed, a_.t, a_.t_base);
+}
+
+template <class T>
+struct accept_kernel_args {
+  T* r;
+  T* logabs;
+  const T* r_prop;
+  const T* la_prop;
+  const int8_t* sign_prop;
+  int64_t B;
+  int N3;
+  uint64_t seed;
+  uint64_t t;
+  const uint64_t* t_base;
+  unsigned long long* n_acc;
+};
+
+template <class T>
+__device__ __forceinline__ void accept_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, T* __restrict__ r, T* __restrict__ logabs, const T* __restrict__ r_prop,
                               const T* __restrict__ la_prop, const int8_t* __restrict__ sign_prop, int64_t B, int N3,
                               uint64_t seed, uint64_t t, const uint64_t* __restrict__ t_base,
                               unsigned long long* __restrict__ n_acc) {
   if (t_base) t += *t_base;
-  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t b = (int64_t)bx_ * blockDim.x + threadIdx.x;
   bool acc = false;
   if (b < B) {
     const uint4 ctr = make_uint4((uint32_t)b, (uint32_t)t, kTagAccept << 24, (uint32_t)(t >> 32));
@@ -78,6 +120,23 @@ __global__ void accept_kernel(T* __restrict__ r, T* __restrict__ logabs, const T
   }
   const unsigned m = __ballot_sync(0xffffffffu, acc);
   if ((threadIdx.x % 32) == 0 && m && n_acc) atomicAdd(n_acc, (unsigned long long)__popc(m));
+}
+
+template <class T>
+__global__ void accept_kernel(T* __restrict__ r, T* __restrict__ logabs, const T* __restrict__ r_prop,
+                              const T* __restrict__ la_prop, const int8_t* __restrict__ sign_prop, int64_t B, int N3,
+                              uint64_t seed, uint64_t t, const uint64_t* __restrict__ t_base,
+                              unsigned long long* __restrict__ n_acc) {
+  accept_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, r, logabs, r_prop, la_prop, sign_prop, B, N3, seed, t, t_base, n_acc);
+}
+
+// One launch over several molecules: block b runs entry m of the table.
+template <class T>
+__global__ void accept_kernel_group(const __grid_constant__ Grp<accept_kernel_args<T>> g) {
+  int64_t l_;
+  const int m_ = grp_find(g, blockIdx.x, l_);
+  const accept_kernel_args<T>& a_ = g.a[m_];
+  accept_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.r, a_.logabs, a_.r_prop, a_.la_prop, a_.sign_prop, a_.B, a_.N3, a_.seed, a_.t, a_.t_base, a_.n_acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -174,8 +233,15 @@ __global__ void mala_accept_kernel(T* __restrict__ r, T* __restrict__ logabs, T*
 constexpr int kRedThreads = 1024;
 
 template <class T>
-__global__ void __launch_bounds__(kRedThreads)
-    esum_kernel(const T* __restrict__ e, int64_t B, double* __restrict__ out2, unsigned int* status) {
+struct esum_kernel_args {
+  const T* e;
+  int64_t B;
+  double* out2;
+  unsigned int* status;
+};
+
+template <class T>
+__device__ __forceinline__ void esum_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const T* __restrict__ e, int64_t B, double* __restrict__ out2, unsigned int* status) {
   __shared__ double s1[kRedThreads], s2[kRedThreads];
   double a = 0, q = 0;
   bool bad = false;
@@ -205,6 +271,20 @@ __global__ void __launch_bounds__(kRedThreads)
   }
 }
 
+template <class T>
+__global__ void __launch_bounds__(kRedThreads) esum_kernel(const T* __restrict__ e, int64_t B, double* __restrict__ out2, unsigned int* status) {
+  esum_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, e, B, out2, status);
+}
+
+// One launch over several molecules: block b runs entry m of the table.
+template <class T>
+__global__ void __launch_bounds__(kRedThreads) esum_kernel_group(const __grid_constant__ Grp<esum_kernel_args<T>> g) {
+  int64_t l_;
+  const int m_ = grp_find(g, blockIdx.x, l_);
+  const esum_kernel_args<T>& a_ = g.a[m_];
+  esum_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.e, a_.B, a_.out2, a_.status);
+}
+
 __device__ double block_sum_det(double v, double* sh) {
   sh[threadIdx.x] = v;
   __syncthreads();
@@ -221,8 +301,18 @@ __device__ double block_sum_det(double v, double* sh) {
 // One CTA: bitonic sort of a padded FP64 copy in global scratch, then
 // block reductions in a fixed order.
 template <class T>
-__global__ void __launch_bounds__(kRedThreads)
-    loss_weights_kernel(const T* __restrict__ e, int64_t B, int64_t Bp, double k, T* __restrict__ w,
+struct loss_weights_kernel_args {
+  const T* e;
+  int64_t B;
+  int64_t Bp;
+  double k;
+  T* w;
+  double* stats;
+  double* srt;
+};
+
+template <class T>
+__device__ __forceinline__ void loss_weights_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const T* __restrict__ e, int64_t B, int64_t Bp, double k, T* __restrict__ w,
                         double* __restrict__ stats, double* __restrict__ srt) {
   __shared__ double sh[kRedThreads];
   for (int64_t i = threadIdx.x; i < Bp; i += kRedThreads) srt[i] = i < B ? (double)e[i] : INFINITY;
@@ -264,6 +354,21 @@ __global__ void __launch_bounds__(kRedThreads)
     stats[2] = mean_c;
     stats[3] = mean_raw;
   }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kRedThreads) loss_weights_kernel(const T* __restrict__ e, int64_t B, int64_t Bp, double k, T* __restrict__ w,
+                        double* __restrict__ stats, double* __restrict__ srt) {
+  loss_weights_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, e, B, Bp, k, w, stats, srt);
+}
+
+// One launch over several molecules: block b runs entry m of the table.
+template <class T>
+__global__ void __launch_bounds__(kRedThreads) loss_weights_kernel_group(const __grid_constant__ Grp<loss_weights_kernel_args<T>> g) {
+  int64_t l_;
+  const int m_ = grp_find(g, blockIdx.x, l_);
+  const loss_weights_kernel_args<T>& a_ = g.a[m_];
+  loss_weights_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.e, a_.B, a_.Bp, a_.k, a_.w, a_.stats, a_.srt);
 }
 
 }  // namespace
@@ -326,6 +431,86 @@ cudaError_t launch_loss_weights(const T* e, int64_t B, double k, T* w, double* s
   loss_weights_kernel<T><<<1, kRedThreads, 0, s>>>(e, B, Bp, k, w, stats, scratch);
   return cudaGetLastError();
 }
+
+// Grouped launches: one launch per sampler step over every molecule of a batch
+// (entry m: molecule m's walkers, buffers and accept counter).  Molecule m's
+// draws are those of the single-molecule calls with the same seed and step.
+template <class T>
+cudaError_t launch_propose_group(const dq_handle_s* const* hs, int n, const int64_t* B, const T* const* r,
+                                 T* const* r_prop, double step, uint64_t seed, uint64_t t, const uint64_t* t_base,
+                                 cudaStream_t s) {
+  if (n > kMaxGroup) return cudaErrorInvalidValue;
+  Grp<propose_kernel_args<T>> g{};
+  for (int k = 0; k < n; ++k) {
+    if (B[k] <= 0) continue;
+    const int N3 = 3 * hs[k]->N, nblk = (N3 + 3) / 4;
+    g.add({r[k], r_prop[k], B[k], N3, step, seed, t, t_base}, (B[k] * nblk + 255) / 256);
+  }
+  if (g.n == 0) return cudaSuccess;
+  propose_kernel_group<T><<<(unsigned)g.blocks(), 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_accept_group(const dq_handle_s* const* hs, int n, const int64_t* B, T* const* r, T* const* logabs,
+                                const T* const* r_prop, const T* const* la_prop, const int8_t* const* sign_prop,
+                                uint64_t seed, uint64_t t, const uint64_t* t_base, unsigned long long* const* n_acc,
+                                cudaStream_t s) {
+  if (n > kMaxGroup) return cudaErrorInvalidValue;
+  Grp<accept_kernel_args<T>> g{};
+  for (int k = 0; k < n; ++k) {
+    if (B[k] <= 0) continue;
+    g.add({r[k], logabs[k], r_prop[k], la_prop[k], sign_prop[k], B[k], 3 * hs[k]->N, seed, t, t_base,
+           n_acc ? n_acc[k] : nullptr},
+          (B[k] + 255) / 256);
+  }
+  if (g.n == 0) return cudaSuccess;
+  accept_kernel_group<T><<<(unsigned)g.blocks(), 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_esum_group(int n, const T* const* e, const int64_t* B, double* const* out2,
+                              unsigned int* const* status, cudaStream_t s) {
+  if (n > kMaxGroup) return cudaErrorInvalidValue;
+  Grp<esum_kernel_args<T>> g{};
+  for (int k = 0; k < n; ++k)
+    if (out2[k]) g.add({e[k], B[k], out2[k], status[k]}, 1);
+  if (g.n == 0) return cudaSuccess;
+  esum_kernel_group<T><<<(unsigned)g.blocks(), kRedThreads, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_loss_weights_group(int n, const T* const* e, const int64_t* B, double k, T* const* w,
+                                      double* const* stats, double* const* scratch, cudaStream_t s) {
+  if (n > kMaxGroup) return cudaErrorInvalidValue;
+  Grp<loss_weights_kernel_args<T>> g{};
+  for (int m = 0; m < n; ++m) {
+    if (B[m] <= 0) continue;
+    int64_t Bp = 1;
+    while (Bp < B[m]) Bp <<= 1;
+    g.add({e[m], B[m], Bp, k, w[m], stats ? stats[m] : nullptr, scratch[m]}, 1);
+  }
+  if (g.n == 0) return cudaSuccess;
+  loss_weights_kernel_group<T><<<(unsigned)g.blocks(), kRedThreads, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+#define DQ_INST_GROUP(T)                                                                                           \
+  template cudaError_t launch_propose_group<T>(const dq_handle_s* const*, int, const int64_t*, const T* const*,     \
+                                               T* const*, double, uint64_t, uint64_t, const uint64_t*,            \
+                                               cudaStream_t);                                                     \
+  template cudaError_t launch_accept_group<T>(const dq_handle_s* const*, int, const int64_t*, T* const*, T* const*, \
+                                              const T* const*, const T* const*, const int8_t* const*, uint64_t,   \
+                                              uint64_t, const uint64_t*, unsigned long long* const*,             \
+                                              cudaStream_t);                                                      \
+  template cudaError_t launch_esum_group<T>(int, const T* const*, const int64_t*, double* const*,                  \
+                                            unsigned int* const*, cudaStream_t);                                  \
+  template cudaError_t launch_loss_weights_group<T>(int, const T* const*, const int64_t*, double, T* const*,       \
+                                                    double* const*, double* const*, cudaStream_t);
+DQ_INST_GROUP(float)
+DQ_INST_GROUP(double)
 
 #define DQ_INST(T)                                                                                                 \
   template cudaError_t launch_propose<T>(const dq_handle_s&, int64_t, const T*, T*, double, uint64_t, uint64_t,    \
