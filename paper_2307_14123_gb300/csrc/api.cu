@@ -106,10 +106,11 @@ struct FwdPlan {
 // the BF16 GEMM instead.
 inline bool use_tf32x3(const dq_handle_s& h) { return h.precision != DQ_FP64 && h.D % 32 == 0; }
 constexpr int kT3PerLayer = 14;  // D x D blocks per layer: W_g 2 x 3, W_h 2, W2 2 x 3
-// TF32 splits: the layers' blocks, then W_o of both spins (high, low; K * nmax x D each)
+// TF32 splits: the layers' blocks, then W_o of both spins (high, low; K * nmax x D
+// each), then the Jastrow map W_J1 (high, low; D x D)
 inline int64_t t3_weight_floats(const dq_handle_s& h) {
   const int64_t nmax = std::max(h.n_up, h.n_dn);
-  return (int64_t)h.L * kT3PerLayer * h.D * h.D + 4 * h.K * nmax * h.D;
+  return (int64_t)h.L * kT3PerLayer * h.D * h.D + 4 * h.K * nmax * h.D + 2 * (int64_t)h.D * h.D;
 }
 // Views of the split weights; part 0 = TF32 high, 1 = low.
 struct T3Weights {
@@ -121,6 +122,7 @@ struct T3Weights {
   float* wh(int l, int part) const { return base + (int64_t)l * kT3PerLayer * DD + 6 * DD + part * DD; }
   float* w2(int l, int t, int part) const { return base + (int64_t)l * kT3PerLayer * DD + (8 + 2 * t + part) * DD; }
   float* wo(int sg, int part) const { return base + (int64_t)L * kT3PerLayer * DD + (2 * sg + part) * WoD; }
+  float* wj(int part) const { return base + (int64_t)L * kT3PerLayer * DD + 4 * WoD + part * DD; }
 };
 inline T3Weights t3_weights(const dq_handle_s& h, void* base) {
   return T3Weights{static_cast<float*>(base), (int64_t)h.D * h.D, (int64_t)h.K * std::max(h.n_up, h.n_dn) * h.D,
@@ -141,6 +143,7 @@ cudaError_t split_t3_weights(const dq_handle_s& h, const float* params, const T3
     const cudaError_t e = split_tf32(params + h.off.W_o[sg], w.wo(sg, 0), w.wo(sg, 1), (int64_t)h.K * nsp[sg] * h.D, s);
     if (e != cudaSuccess) return e;
   }
+  if (h.use_jastrow) return split_tf32(params + h.off.W_J1, w.wj(0), w.wj(1), w.DD, s);
   return cudaSuccess;
 }
 
@@ -389,8 +392,16 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
     DQ_LAUNCH(h, kb + PK_ORBITAL_DET, launch_orbital_det<T>(h, d, params, bf, s));
     if (h.use_jastrow) {
       DQ_LAUNCH(h, kb + PK_JASTROW_SUM, launch_jastrow_sum<T>(h, d, bf, s));
-      const RowMap mj{(int64_t)C, (int64_t)C * D, D};
-      DQ_LAUNCH(h, kb + PK_GEMM_JASTROW, gemm_nt<T>(bf.js, mj, params + h.off.W_J1, params + h.off.b_J1, C, bf.jh, mj, nb * C, D, D, false, s));
+      if (use_t3) {
+        DQ_LAUNCH(h, kb + PK_GEMM_JASTROW,
+                  gemm_tf32x3_tc_seg(reinterpret_cast<const float*>(bf.js), nb * C, 1, 0, D, D, w3.wj(0), w3.wj(1), D,
+                                     reinterpret_cast<const float*>(params + h.off.b_J1), C,
+                                     reinterpret_cast<float*>(bf.jh), D, 0, h.d_status, s));
+      } else {
+        const RowMap mj{(int64_t)C, (int64_t)C * D, D};
+        DQ_LAUNCH(h, kb + PK_GEMM_JASTROW, gemm_nt<T>(bf.js, mj, params + h.off.W_J1, params + h.off.b_J1, C, bf.jh,
+                                                      mj, nb * C, D, D, false, s));
+      }
     }
     DQ_LAUNCH(h, kb + PK_COMBINE, launch_combine<T>(h, d, params, bf, logabs + b0, sign + b0,
                                                     e_loc ? e_loc + b0 : nullptr, s,

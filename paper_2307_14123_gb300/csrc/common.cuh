@@ -95,13 +95,47 @@ struct Grp {
   }
   int64_t blocks() const { return n > 0 ? end[n - 1] : 0; }
 };
+// Reads of a kernel's parameter block at run-time offsets are slow, so the
+// table is read at compile-time offsets only: the entry search is unrolled,
+// and GRP_STATIC runs a block of code once per entry index K_ (a constant)
+// through a switch.  The empty asm with the index as an immediate keeps the
+// compiler from merging the cases back into one run-time-indexed read.
 template <class A>
 __device__ __forceinline__ int grp_find(const Grp<A>& g, int64_t blk, int64_t& local) {
   int m = 0;
-  while (m + 1 < g.n && blk >= g.end[m]) ++m;
-  local = blk - (m > 0 ? g.end[m - 1] : 0);
+  int64_t start = 0;
+#pragma unroll
+  for (int k = 0; k + 1 < kMaxGroup; ++k)
+    if (k + 1 < g.n && blk >= g.end[k]) {
+      m = k + 1;
+      start = g.end[k];
+    }
+  local = blk - start;
   return m;
 }
+// Entry m's block l as (x, y) of its nbx x ny grid; l < 2^31 (checked at launch).
+template <class A>
+__device__ __forceinline__ int64_t grp_bx(const Grp<A>& g, int m, int64_t l) {
+  const int ny = g.ny[m];
+  return ny == 1 ? l : (int64_t)((uint32_t)l / (uint32_t)ny);
+}
+template <class A>
+__device__ __forceinline__ int grp_by(const Grp<A>& g, int m, int64_t l) {
+  const int ny = g.ny[m];
+  return ny == 1 ? 0 : (int)((uint32_t)l % (uint32_t)ny);
+}
+#define GRP_CASE(K, ...)            \
+  case K: {                         \
+    asm volatile("" ::"n"(K));      \
+    constexpr int K_ = K;           \
+    __VA_ARGS__                     \
+  } break;
+#define GRP_STATIC(m, ...)                                                                     \
+  switch (m) {                                                                                 \
+    GRP_CASE(0, __VA_ARGS__) GRP_CASE(1, __VA_ARGS__) GRP_CASE(2, __VA_ARGS__)                 \
+    GRP_CASE(3, __VA_ARGS__) GRP_CASE(4, __VA_ARGS__) GRP_CASE(5, __VA_ARGS__)                 \
+    GRP_CASE(6, __VA_ARGS__) GRP_CASE(7, __VA_ARGS__)                                          \
+  }
 }  // namespace dq
 
 struct dq_handle_s {

@@ -101,20 +101,13 @@ __device__ __forceinline__ void geometry_kernel_body(const int64_t bx_, const in
   }
 }
 
-template <class T>
-__global__ void geometry_kernel(const T* __restrict__ r, const T* __restrict__ R, const int* __restrict__ pair_ij,
-                                int64_t Bc, int N, int M, int n_ee, int E, int Q, int ej, double rc,
-                                T* __restrict__ geo, T* __restrict__ rbf) {
-  geometry_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, r, R, pair_ij, Bc, N, M, n_ee, E, Q, ej, rc, geo, rbf);
-}
-
 // One launch over several molecules: block b runs entry m of the table.
 template <class T>
 __global__ void geometry_kernel_group(const __grid_constant__ Grp<geometry_kernel_args<T>> g) {
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
-  const geometry_kernel_args<T>& a_ = g.a[m_];
-  geometry_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.r, a_.R, a_.pair_ij, a_.Bc, a_.N, a_.M, a_.n_ee, a_.E, a_.Q, a_.ej, a_.rc, a_.geo, a_.rbf);
+  GRP_STATIC(m_, const auto& a_ = g.a[K_];
+             geometry_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.r, a_.R, a_.pair_ij, a_.Bc, a_.N, a_.M, a_.n_ee, a_.E, a_.Q, a_.ej, a_.rc, a_.geo, a_.rbf);)
 }
 
 // Edge hidden layer a = tanh(W1 e + b1) as a jet in d: (a, a', a'').
@@ -239,20 +232,13 @@ __device__ __forceinline__ void edge_hidden_kernel_body(const int64_t bx_, const
   }
 }
 
-template <class T>
-__global__ void __launch_bounds__(kHiddenThreads) edge_hidden_kernel(const T* __restrict__ rbf, const T* __restrict__ params, int64_t Bc, int E, int n_par,
-                       int n_ee, int D, int Q, int ej, int64_t W1_0, int64_t W1_1, int64_t W1_2, int64_t b1_0,
-                       int64_t b1_1, int64_t b1_2, T* __restrict__ eh) {
-  edge_hidden_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, rbf, params, Bc, E, n_par, n_ee, D, Q, ej, W1_0, W1_1, W1_2, b1_0, b1_1, b1_2, eh);
-}
-
 // One launch over several molecules: block b runs entry m of the table.
 template <class T>
 __global__ void __launch_bounds__(kHiddenThreads) edge_hidden_kernel_group(const __grid_constant__ Grp<edge_hidden_kernel_args<T>> g) {
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
-  const edge_hidden_kernel_args<T>& a_ = g.a[m_];
-  edge_hidden_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.rbf, a_.params, a_.Bc, a_.E, a_.n_par, a_.n_ee, a_.D, a_.Q, a_.ej, a_.W1_0, a_.W1_1, a_.W1_2, a_.b1_0, a_.b1_1, a_.b1_2, a_.eh);
+  GRP_STATIC(m_, const auto& a_ = g.a[K_];
+             edge_hidden_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.rbf, a_.params, a_.Bc, a_.E, a_.n_par, a_.n_ee, a_.D, a_.Q, a_.ej, a_.W1_0, a_.W1_1, a_.W1_2, a_.b1_0, a_.b1_1, a_.b1_2, a_.eh);)
 }
 
 // z0[s][a] = (W_h^0 E_spin[s])[a]: the node map of layer 0 on the spin embeddings.
@@ -275,18 +261,13 @@ __device__ __forceinline__ void layer0_node_kernel_body(const int64_t bx_, const
   z0[gid] = acc;
 }
 
-template <class T>
-__global__ void layer0_node_kernel(const T* __restrict__ params, int D, int64_t E_spin, int64_t W_h, T* z0) {
-  layer0_node_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, params, D, E_spin, W_h, z0);
-}
-
 // One launch over several molecules: block b runs entry m of the table.
 template <class T>
 __global__ void layer0_node_kernel_group(const __grid_constant__ Grp<layer0_node_kernel_args<T>> g) {
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
-  const layer0_node_kernel_args<T>& a_ = g.a[m_];
-  layer0_node_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.params, a_.D, a_.E_spin, a_.W_h, a_.z0);
+  GRP_STATIC(m_, const auto& a_ = g.a[K_];
+             layer0_node_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.params, a_.D, a_.E_spin, a_.W_h, a_.z0);)
 }
 
 // ---------------------------------------------------------------------------
@@ -650,14 +631,6 @@ __device__ __forceinline__ void messages_kernel_body(const int64_t bx_, const in
   }
 }
 
-template <class T, class TO, int IB, int CB, int L>
-__global__ void __launch_bounds__(256, 2) messages_kernel(const T* __restrict__ Z, const T* __restrict__ z0, const T* __restrict__ ew,
-                    const T* __restrict__ geo, const T* __restrict__ Y, const int* __restrict__ pair_of, int N,
-                    int n_up, int M, int C, int D, int E, int n_ee, int z_const, int stage_w1,
-                    TO* __restrict__ msg) {
-  messages_kernel_body<T, TO, IB, CB, L>(blockIdx.x, blockIdx.y, gridDim.x, Z, z0, ew, geo, Y, pair_of, N, n_up, M, C, D, E, n_ee, z_const, stage_w1, msg);
-}
-
 // One launch over several molecules: block b runs entry m of the table; the
 // entry's tag is its features per CTA (32, or 16 for large molecules).
 template <class T, class TO, int IB, int CB>
@@ -666,11 +639,11 @@ __global__ void __launch_bounds__(256, 2) messages_kernel_group(const __grid_con
   const int m_ = grp_find(g, blockIdx.x, l_);
   const messages_kernel_args<T, TO>& a_ = g.a[m_];
   if (g.tag[m_] == 16)
-    messages_kernel_body<T, TO, IB, CB, 16>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.Z, a_.z0, a_.ew, a_.geo,
+    messages_kernel_body<T, TO, IB, CB, 16>(grp_bx(g, m_, l_), grp_by(g, m_, l_), g.nbx[m_], a_.Z, a_.z0, a_.ew, a_.geo,
                                             a_.Y, a_.pair_of, a_.N, a_.n_up, a_.M, a_.C, a_.D, a_.E, a_.n_ee,
                                             a_.z_const, a_.stage_w1, a_.msg);
   else
-    messages_kernel_body<T, TO, IB, CB, kMsgLanes>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.Z, a_.z0, a_.ew,
+    messages_kernel_body<T, TO, IB, CB, kMsgLanes>(grp_bx(g, m_, l_), grp_by(g, m_, l_), g.nbx[m_], a_.Z, a_.z0, a_.ew,
                                                    a_.geo, a_.Y, a_.pair_of, a_.N, a_.n_up, a_.M, a_.C, a_.D, a_.E,
                                                    a_.n_ee, a_.z_const, a_.stage_w1, a_.msg);
 }
@@ -730,20 +703,13 @@ __device__ __forceinline__ void messages_value_kernel_body(const int64_t bx_, co
   }
 }
 
-template <class T, class TO>
-__global__ void __launch_bounds__(256) messages_value_kernel(const T* __restrict__ Z, const T* __restrict__ z0, const T* __restrict__ ew,
-                          const T* __restrict__ Y, const int* __restrict__ pair_of, int64_t Bc, int N, int n_up,
-                          int M, int D, int E, int n_ee, int z_const, TO* __restrict__ msg) {
-  messages_value_kernel_body<T, TO>(blockIdx.x, blockIdx.y, gridDim.x, Z, z0, ew, Y, pair_of, Bc, N, n_up, M, D, E, n_ee, z_const, msg);
-}
-
 // One launch over several molecules: block b runs entry m of the table.
 template <class T, class TO>
 __global__ void __launch_bounds__(256) messages_value_kernel_group(const __grid_constant__ Grp<messages_value_kernel_args<T, TO>> g) {
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
   const messages_value_kernel_args<T, TO>& a_ = g.a[m_];
-  messages_value_kernel_body<T, TO>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.Z, a_.z0, a_.ew, a_.Y, a_.pair_of, a_.Bc, a_.N, a_.n_up, a_.M, a_.D, a_.E, a_.n_ee, a_.z_const, a_.msg);
+  messages_value_kernel_body<T, TO>(grp_bx(g, m_, l_), grp_by(g, m_, l_), g.nbx[m_], a_.Z, a_.z0, a_.ew, a_.Y, a_.pair_of, a_.Bc, a_.N, a_.n_up, a_.M, a_.D, a_.E, a_.n_ee, a_.z_const, a_.msg);
 }
 
 // ---------------------------------------------------------------------------
@@ -807,8 +773,8 @@ template <class T>
 __global__ void update_kernel_group(const __grid_constant__ Grp<update_kernel_args<T>> g) {
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
-  const update_kernel_args<T>& a_ = g.a[m_];
-  update_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.P, a_.Fin, a_.Fout, a_.E_spin, a_.Bc, a_.N, a_.n_up, a_.C, a_.D, a_.from_spin, a_.Fbf);
+  GRP_STATIC(m_, const auto& a_ = g.a[K_];
+             update_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.P, a_.Fin, a_.Fout, a_.E_spin, a_.Bc, a_.N, a_.n_up, a_.C, a_.D, a_.from_spin, a_.Fbf);)
 }
 
 __global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int64_t n) {
@@ -1134,7 +1100,7 @@ __global__ void __launch_bounds__(128) orbital_det_kernel_group(const __grid_con
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
   const orbital_det_kernel_args<T>& a_ = g.a[m_];
-  orbital_det_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.phi, a_.geo, a_.params, a_.Bc, a_.N, a_.n_up, a_.M, a_.K, a_.C, a_.Wo, a_.E, a_.n_ee, a_.om_up, a_.om_dn, a_.ze_up, a_.ze_dn, a_.det, a_.n_fp64);
+  orbital_det_kernel_body<T>(grp_bx(g, m_, l_), grp_by(g, m_, l_), g.nbx[m_], a_.phi, a_.geo, a_.params, a_.Bc, a_.N, a_.n_up, a_.M, a_.K, a_.C, a_.Wo, a_.E, a_.n_ee, a_.om_up, a_.om_dn, a_.ze_up, a_.ze_dn, a_.det, a_.n_fp64);
 }
 
 // ---------------------------------------------------------------------------
@@ -1396,13 +1362,6 @@ __device__ __forceinline__ void orbital_det_jets_kernel_body(const int64_t bx_, 
   }
 }
 
-__global__ void __launch_bounds__(128) orbital_det_jets_kernel(const float* __restrict__ phi, const float* __restrict__ geo,
-                            const float* __restrict__ params, int64_t Bc, int N, int n_up, int M, int K, int C,
-                            int Wo, int E, int n_ee, int64_t om_up, int64_t om_dn, int64_t ze_up, int64_t ze_dn,
-                            double* __restrict__ det, unsigned long long* __restrict__ n_fp64) {
-  orbital_det_jets_kernel_body(blockIdx.x, blockIdx.y, gridDim.x, phi, geo, params, Bc, N, n_up, M, K, C, Wo, E, n_ee, om_up, om_dn, ze_up, ze_dn, det, n_fp64);
-}
-
 // Determinants of several molecules in one launch (FP32 modes): tag 1 runs the
 // FP32 jet kernel body (spin blocks of at most kDetNR electrons), tag 0 the
 // general body (value-only calls, larger spin blocks).  Both use four warps per
@@ -1442,18 +1401,13 @@ __device__ __forceinline__ void jastrow_sum_kernel_body(const int64_t bx_, const
   js[gid] = acc;
 }
 
-template <class T>
-__global__ void jastrow_sum_kernel(const T* __restrict__ F, int64_t Bc, int N, int C, int D, T* __restrict__ js) {
-  jastrow_sum_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, F, Bc, N, C, D, js);
-}
-
 // One launch over several molecules: block b runs entry m of the table.
 template <class T>
 __global__ void jastrow_sum_kernel_group(const __grid_constant__ Grp<jastrow_sum_kernel_args<T>> g) {
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
-  const jastrow_sum_kernel_args<T>& a_ = g.a[m_];
-  jastrow_sum_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.F, a_.Bc, a_.N, a_.C, a_.D, a_.js);
+  GRP_STATIC(m_, const auto& a_ = g.a[K_];
+             jastrow_sum_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.F, a_.Bc, a_.N, a_.C, a_.D, a_.js);)
 }
 
 // ---------------------------------------------------------------------------
@@ -1701,23 +1655,13 @@ __device__ __forceinline__ void combine_kernel_body(const int64_t bx_, const int
   }
 }
 
-template <class T>
-__global__ void __launch_bounds__(kCombineThreads) combine_kernel(const double* __restrict__ det, const T* __restrict__ jh, const T* __restrict__ geo,
-                   const T* __restrict__ params, const double* __restrict__ Zn, const int* __restrict__ pair_ij,
-                   const int* __restrict__ pair_of, int64_t Bc, int N, int n_up, int M, int K, int C, int D, int E, int n_ee, int64_t c_off,
-                   int64_t wJ2_off, int use_jastrow, int use_cusp, double alpha, double Vnn, T* __restrict__ logabs,
-                   int8_t* __restrict__ sign_out, T* __restrict__ e_loc, T* __restrict__ grad_out,
-                   unsigned int* __restrict__ status) {
-  combine_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, det, jh, geo, params, Zn, pair_ij, pair_of, Bc, N, n_up, M, K, C, D, E, n_ee, c_off, wJ2_off, use_jastrow, use_cusp, alpha, Vnn, logabs, sign_out, e_loc, grad_out, status);
-}
-
 // One launch over several molecules: block b runs entry m of the table.
 template <class T>
 __global__ void __launch_bounds__(kCombineThreads) combine_kernel_group(const __grid_constant__ Grp<combine_kernel_args<T>> g) {
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
-  const combine_kernel_args<T>& a_ = g.a[m_];
-  combine_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.det, a_.jh, a_.geo, a_.params, a_.Zn, a_.pair_ij, a_.pair_of, a_.Bc, a_.N, a_.n_up, a_.M, a_.K, a_.C, a_.D, a_.E, a_.n_ee, a_.c_off, a_.wJ2_off, a_.use_jastrow, a_.use_cusp, a_.alpha, a_.Vnn, a_.logabs, a_.sign_out, a_.e_loc, a_.grad_out, a_.status);
+  GRP_STATIC(m_, const auto& a_ = g.a[K_];
+             combine_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.det, a_.jh, a_.geo, a_.params, a_.Zn, a_.pair_ij, a_.pair_of, a_.Bc, a_.N, a_.n_up, a_.M, a_.K, a_.C, a_.D, a_.E, a_.n_ee, a_.c_off, a_.wJ2_off, a_.use_jastrow, a_.use_cusp, a_.alpha, a_.Vnn, a_.logabs, a_.sign_out, a_.e_loc, a_.grad_out, a_.status);)
 }
 
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -1727,98 +1671,45 @@ inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// Single-molecule launchers: the grouped kernels with a one-entry table, so that
+// a molecule gives the same bits alone and in a batch.
 template <class T>
 cudaError_t launch_geometry(const dq_handle_s& h, const FwdDims& d, const T* r, FwdBuffers<T> b, cudaStream_t s) {
-  const T* R = nullptr;
-  if constexpr (sizeof(T) == 8) R = h.d_R; else R = h.d_Rf;
-  const int ej = d.C > 1 ? 3 : 1;
-  geometry_kernel<T><<<blocks(d.Bc * h.edges.n_all, 128), 128, 0, s>>>(
-      r, R, h.d_pair_ij, d.Bc, d.N, d.M, h.edges.n_ee, h.edges.n_all, d.Q, ej, h.rc, b.geo, b.rbf);
-  return cudaGetLastError();
+  const MolFwd<T> m{&h, d, nullptr, b};
+  return launch_geometry_group<T>(&m, 1, &r, s);
 }
 
 template <class T>
 cudaError_t launch_edge_hidden(const dq_handle_s& h, const FwdDims& d, const T* params, int l, FwdBuffers<T> b,
                                cudaStream_t s) {
-  const int ej = d.C > 1 ? 3 : 1;
-  const auto& y = h.off.layer[l];
-  const int64_t rows = d.Bc * h.edges.n_all;
-  const size_t smem = ((size_t)3 * d.Q * d.D + 3 * d.D + (size_t)kEdgesPerCta * ej * d.Q) * sizeof(T);
-  auto kern = edge_hidden_kernel<T>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t nblk = (rows + kEdgesPerCta - 1) / kEdgesPerCta;
-  const int64_t grid = nblk < (int64_t)sms * 6 ? nblk : (int64_t)sms * 6;  // persistent, 6 CTAs per SM
-  kern<<<(unsigned)grid, kHiddenThreads, smem, s>>>(b.rbf, params, d.Bc, h.edges.n_all, h.edges.n_par,
-                                                                h.edges.n_ee, d.D, d.Q, ej, y.W1[0], y.W1[1], y.W1[2],
-                                                                y.b1[0], y.b1[1], y.b1[2], b.eh);
-  return cudaGetLastError();
+  const MolFwd<T> m{&h, d, params, b};
+  return launch_edge_hidden_group<T>(&m, 1, l, s);
 }
 
 template <class T>
 cudaError_t launch_layer0_node(const dq_handle_s& h, const FwdDims& d, const T* params, FwdBuffers<T> b,
                                cudaStream_t s) {
-  layer0_node_kernel<T><<<blocks(2 * d.D, 128), 128, 0, s>>>(params, d.D, h.off.E_spin, h.off.layer[0].W_h, b.z0);
-  return cudaGetLastError();
+  const MolFwd<T> m{&h, d, params, b};
+  return launch_layer0_node_group<T>(&m, 1, s);
 }
 
 namespace {
 template <class T>
 constexpr int msg_ib() { return sizeof(T) == 4 ? 8 : 4; }
-template <class T, class TO>
-cudaError_t launch_messages_t(const dq_handle_s& h, const FwdDims& d, const T* params, int l, bool z_const,
-                              FwdBuffers<T> b, TO* out, cudaStream_t s) {
-  const T* Y = params + h.off.layer[l].Y;
-  if (d.C == 1) {
-    const size_t smem = (size_t)d.N * 32 * sizeof(T) + (size_t)d.N * d.N * sizeof(int);
-    dim3 grid((unsigned)d.Bc, (unsigned)((d.D + 31) / 32));
-    messages_value_kernel<T, TO><<<grid, 32 * (d.N < 8 ? d.N : 8), smem, s>>>(
-        b.Z, b.z0, b.ew, Y, h.d_pair_of, d.Bc, d.N, d.n_up, d.M, d.D, h.edges.n_all, h.edges.n_ee, z_const ? 1 : 0,
-        out);
-    return cudaGetLastError();
-  }
-  if (d.D % kMsgLanes) return cudaErrorInvalidConfiguration;
-  constexpr int IB = msg_ib<T>(), CB = sizeof(T) == 4 ? 4 : 2;
-  bool stage_w1 = true;
-  int L = kMsgLanes;
-  MsgSmem lay = msg_smem_layout<T>(d.N, IB, CB, stage_w1, L);
-  if (lay.total_bytes > 112 * 1024) {  // keep two CTAs per SM, else fetch w' from global memory
-    stage_w1 = false;
-    lay = msg_smem_layout<T>(d.N, IB, CB, stage_w1, L);
-  }
-  if (lay.total_bytes > 220 * 1024) {  // large molecules: 16 features per CTA
-    L = 16;
-    lay = msg_smem_layout<T>(d.N, IB, CB, stage_w1, L);
-  }
-  if (lay.total_bytes > 220 * 1024) return cudaErrorInvalidConfiguration;
-  auto kern = L == 16 ? messages_kernel<T, TO, IB, CB, 16> : messages_kernel<T, TO, IB, CB, kMsgLanes>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total_bytes);
-  if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)d.Bc, d.D / L);
-  kern<<<grid, 32 * kMsgWarps, lay.total_bytes, s>>>(b.Z, b.z0, b.ew, b.geo, Y, h.d_pair_of, d.N, d.n_up, d.M, d.C, d.D,
-                                          h.edges.n_all, h.edges.n_ee, z_const ? 1 : 0, stage_w1 ? 1 : 0, out);
-  return cudaGetLastError();
-}
 }  // namespace
 
 template <class T>
 cudaError_t launch_messages(const dq_handle_s& h, const FwdDims& d, const T* params, int l, bool z_const,
                             FwdBuffers<T> b, cudaStream_t s) {
-  if constexpr (sizeof(T) == 4) {
-    if (b.msg_bf)
-      return launch_messages_t<T, __nv_bfloat16>(h, d, params, l, z_const, b, static_cast<__nv_bfloat16*>(b.msg_bf),
-                                                 s);
-  }
-  return launch_messages_t<T, T>(h, d, params, l, z_const, b, b.msg, s);
+  const MolFwd<T> m{&h, d, params, b};
+  return launch_messages_group<T>(&m, 1, l, z_const, s);
 }
 
 template <class T>
 cudaError_t launch_update(const dq_handle_s& h, const FwdDims& d, const T* params, bool from_spin, FwdBuffers<T> b,
                           cudaStream_t s) {
-  return launch_update_io<T>(h, d, params, from_spin, b.Z, b.F, b.F, s, b.F_bf);
+  const MolFwd<T> m{&h, d, params, b};
+  return launch_update_group<T>(&m, 1, from_spin, s);
 }
 
 template <class T>
@@ -1840,19 +1731,15 @@ cudaError_t launch_orbital_det(const dq_handle_s& h, const FwdDims& d, const T* 
                                cudaStream_t s) {
   const int nmax = d.n_up > d.n_dn ? d.n_up : d.n_dn;
   const int nn = nmax * nmax;
-  if constexpr (sizeof(T) == 4) {
-    if (d.C > 1 && nmax <= kDetNR) {
-      const size_t smem = det_jets_smem_per_warp(nmax, 3 * d.N) * 4;
-      cudaError_t e = cudaFuncSetAttribute(orbital_det_jets_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
-      if (e != cudaSuccess) return e;
-      const int64_t nmat = d.Bc * 2 * d.K;
-      orbital_det_jets_kernel<<<blocks(nmat, 4), 128, smem, s>>>(
-          b.phi, b.geo, params, d.Bc, d.N, d.n_up, d.M, d.K, d.C, d.K * nmax, h.edges.n_all, h.edges.n_ee,
-          h.off.omega[0], h.off.omega[1], h.off.zeta[0], h.off.zeta[1], b.det, h.d_fp64_count);
-      return cudaGetLastError();
+  {
+    const size_t pw = ((size_t)nn * (3 * sizeof(double) + 10 * sizeof(T)) + 32 * sizeof(int) + 15) / 16 * 16;
+    const bool jets = sizeof(T) == 4 && d.C > 1 && nmax <= kDetNR;
+    if (jets || pw * 4 <= 200 * 1024) {
+      const MolFwd<T> m{&h, d, params, b};
+      return launch_orbital_det_group<T>(&m, 1, s);
     }
   }
+  // spin blocks too large for four warps per CTA: one matrix per CTA
   const size_t per_warp = ((size_t)nn * (3 * sizeof(double) + 10 * sizeof(T)) + 32 * sizeof(int) + 15) / 16 * 16;
   const int warps = per_warp * 4 <= 200 * 1024 ? 4 : 1;
   const size_t smem = per_warp * warps;
@@ -1869,23 +1756,15 @@ cudaError_t launch_orbital_det(const dq_handle_s& h, const FwdDims& d, const T* 
 
 template <class T>
 cudaError_t launch_jastrow_sum(const dq_handle_s& h, const FwdDims& d, FwdBuffers<T> b, cudaStream_t s) {
-  (void)h;
-  jastrow_sum_kernel<T><<<blocks(d.Bc * d.C * d.D, 256), 256, 0, s>>>(b.F, d.Bc, d.N, d.C, d.D, b.js);
-  return cudaGetLastError();
+  const MolFwd<T> m{&h, d, nullptr, b};
+  return launch_jastrow_sum_group<T>(&m, 1, s);
 }
 
 template <class T>
 cudaError_t launch_combine(const dq_handle_s& h, const FwdDims& d, const T* params, FwdBuffers<T> b, T* logabs,
                            int8_t* sign, T* e_loc, cudaStream_t s, T* grad) {
-  const size_t smem = (2 * (size_t)d.K + 3 * (size_t)d.D + 32 + 3 * (size_t)d.N) * sizeof(double);
-  auto kern = combine_kernel<T>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)d.Bc, kCombineThreads, smem, s>>>(
-      b.det, b.jh, b.geo, params, h.d_Z, h.d_pair_ij, h.d_pair_of, d.Bc, d.N, d.n_up, d.M, d.K, d.C, d.D, h.edges.n_all,
-      h.edges.n_ee, h.off.c, h.off.w_J2, h.use_jastrow, h.use_cusp, h.alpha, h.Vnn, logabs, sign, e_loc, grad,
-      h.d_status);
-  return cudaGetLastError();
+  const MolFwd<T> m{&h, d, params, b};
+  return launch_combine_group<T>(&m, 1, &logabs, &sign, &e_loc, &grad, s);
 }
 
 // ---------------------------------------------------------------------------

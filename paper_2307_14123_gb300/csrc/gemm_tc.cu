@@ -361,24 +361,77 @@ __device__ __forceinline__ void umma_tf32(uint32_t tmem_d, uint64_t adesc, uint6
 // A 128-row block holds rb rows of each of sb = TC_BM / rb segments (rb <
 // TC_BM only if seg_rows <= rb), or a TC_BM-row block of one segment.  A tile is
 // T3_SUB such blocks sharing the W tile; each has its own accumulator.
-struct T3Job {
-  CUtensorMap a, bb, bs;  // X (segmented rows), W big, W small
+// Reads of the parameter block at run-time offsets are slow (measured: a job
+// table read that way cost a third of the GEMM's speed at K = 128), so the
+// roles that run per K block or per output element read it at compile-time
+// offsets only: the producer's TMA loads and the epilogue are templates on the
+// job index, reached through a switch.  The job lookup itself reads a copy of
+// the scalar fields that each CTA keeps in shared memory.
+struct T3Fields {
   const float* bias;
   float* Y;
   int64_t seg_rows, n_seg, ldy, y_seg_stride;
   int64_t rb_per_seg, n_mblk, tile_end;  // tile_end: tiles of jobs 0 .. this one
   int rb, sb, n_out, nk, n_tiles_n, bias_period, accumulate;
 };
+struct T3Job {
+  CUtensorMap a, bb, bs;  // X (segmented rows), W big, W small
+  T3Fields f;
+};
 constexpr int kT3MaxJobs = 16;
 struct T3Jobs {
   T3Job j[kT3MaxJobs];
   int n;
 };
-__device__ __forceinline__ const T3Job& t3_job(const T3Jobs& J, int64_t t, int64_t& tl) {
+__device__ __forceinline__ int t3_job(const T3Fields* sj, int n, int64_t t, int64_t& tl) {
   int m = 0;
-  while (m + 1 < J.n && t >= J.j[m].tile_end) ++m;
-  tl = t - (m > 0 ? J.j[m - 1].tile_end : 0);
-  return J.j[m];
+  while (m + 1 < n && t >= sj[m].tile_end) ++m;
+  tl = t - (m > 0 ? sj[m - 1].tile_end : 0);
+  return m;
+}
+// TMA loads of one K block of job M's tile (A blocks of T3_SUB segments, W big and small).
+template <int M>
+__device__ __forceinline__ void t3_issue(const T3Jobs& jobs, uint8_t* a_dst, uint8_t* bb_dst, uint8_t* bs_dst,
+                                         int x, const int* m0, const int* seg, int n0, uint64_t* bar) {
+  asm volatile("// job %0" ::"n"(M));  // keeps the 16 cases of the switch apart
+#pragma unroll
+  for (int h = 0; h < T3_SUB; ++h) tma_load_3d(a_dst + h * T3_TILE_A, &jobs.j[M].a, x, m0[h], seg[h], bar);
+  tma_load_2d(bb_dst, &jobs.j[M].bb, x, n0, bar);
+  tma_load_2d(bs_dst, &jobs.j[M].bs, x, n0, bar);
+}
+
+// Epilogue of one tile of job M (the job's fields read at compile-time offsets
+// of the parameter block): TMEM -> registers -> shared-memory transpose -> Y.
+template <int M>
+__device__ __forceinline__ void t3_epi_tile(const T3Jobs& jobs, int64_t tl, uint32_t acc, int q, int lane,
+                                            float (*st)[33]) {
+  asm volatile("// job %0" ::"n"(M));  // keeps the 16 cases of the switch apart
+  const T3Fields& J = jobs.j[M].f;
+  const int n_tiles_n = J.n_tiles_n, rb = J.rb, sbk = J.sb, bias_period = J.bias_period, n_out = J.n_out;
+  const int accumulate = J.accumulate;
+  const int64_t rb_per_seg = J.rb_per_seg, n_mblk = J.n_mblk, seg_rows = J.seg_rows, n_seg = J.n_seg;
+  const int64_t ldy = J.ldy, y_seg_stride = J.y_seg_stride;
+  float* const Y = J.Y;
+  const float* const bias = J.bias;
+  const int64_t mp = tl / n_tiles_n;
+  const int n0 = (int)(tl % n_tiles_n) * TC_BN;
+  const int tr = q * 32 + lane;  // row of the 128-row block
+#pragma unroll 1
+  for (int h = 0; h < T3_SUB; ++h) {
+    const int64_t mb = mp * T3_SUB + h;
+    const int64_t seg = (mb / rb_per_seg) * sbk + tr / rb;
+    const int64_t row = (mb % rb_per_seg) * rb + tr % rb;  // row within the segment
+    const bool add_bias = bias != nullptr && (row % bias_period) == 0;
+    float* yrow = mb < n_mblk && row < seg_rows && seg < n_seg ? Y + seg * y_seg_stride + row * ldy + n0 : nullptr;
+    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+      uint32_t vv[32];
+      tmem_ld32(acc + (uint32_t)(h * TC_TMEM_COLS) + (uint32_t)c0, vv);
+      const int n = n0 + c0 + lane;
+      const bool col_ok = n < n_out;
+      store_block_32x32(vv, st, lane, yrow ? yrow + c0 : nullptr, add_bias,
+                        bias != nullptr && col_ok ? bias[n] : 0.f, col_ok, accumulate != 0);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(T3_THREADS, 1)
@@ -399,8 +452,14 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   __shared__ volatile int s_abort;
   __shared__ float ep_stage[4][32][33];  // epilogue transpose, one block per epilogue warp
 
+  __shared__ T3Fields sj[kT3MaxJobs];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int64_t n_tiles = jobs.j[jobs.n - 1].tile_end;  // (job, row-block pair, column block)
+  const int n_jobs = jobs.n;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < kT3MaxJobs; ++k)
+      if (k < n_jobs) sj[k] = jobs.j[k].f;
+  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < T3_STAGES; ++s) {
@@ -425,23 +484,27 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const int64_t n_tiles = sj[n_jobs - 1].tile_end;  // (job, row-block pair, column block)
 
   if (warp == 0) {
     if (lane == 0) {  // TMA producer
       int64_t g = 0;
       for (int64_t t = blockIdx.x; t < n_tiles && !s_abort; t += gridDim.x) {
         int64_t tl;
-        const T3Job& J = t3_job(jobs, t, tl);
-        const int64_t mp = tl / J.n_tiles_n;
-        const int n0 = (int)(tl % J.n_tiles_n) * TC_BN;
+        const int jm = t3_job(sj, n_jobs, t, tl);
+        const T3Fields& J = sj[jm];
+        const int n_tiles_n = J.n_tiles_n, nk = J.nk, rb = J.rb, sbk = J.sb;
+        const int64_t rb_per_seg = J.rb_per_seg;
+        const int64_t mp = tl / n_tiles_n;
+        const int n0 = (int)(tl % n_tiles_n) * TC_BN;
         int seg[T3_SUB], m0[T3_SUB];
 #pragma unroll
         for (int h = 0; h < T3_SUB; ++h) {  // first segment and row of each 128-row block (past the end: zero fill)
           const int64_t mb = mp * T3_SUB + h;
-          seg[h] = (int)(mb / J.rb_per_seg) * J.sb;
-          m0[h] = (int)(mb % J.rb_per_seg) * J.rb;
+          seg[h] = (int)(mb / rb_per_seg) * sbk;
+          m0[h] = (int)(mb % rb_per_seg) * rb;
         }
-        for (int kb = 0; kb < J.nk; ++kb, ++g) {
+        for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = (int)(g % T3_STAGES);
           const int64_t u = g / T3_STAGES;
           if (u >= 1 && !mbar_wait(&empty[s], (uint32_t)((u - 1) & 1))) {
@@ -449,11 +512,17 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             break;
           }
           mbar_expect_tx(&full[s], T3_SUB * T3_TILE_A + 2 * T3_TILE_B);
-#pragma unroll
-          for (int h = 0; h < T3_SUB; ++h)
-            tma_load_3d(sA + (s * T3_SUB + h) * T3_TILE_A, &J.a, kb * T3_BK, m0[h], seg[h], &full[s]);
-          tma_load_2d(sBb + s * T3_TILE_B, &J.bb, kb * T3_BK, n0, &full[s]);
-          tma_load_2d(sBs + s * T3_TILE_B, &J.bs, kb * T3_BK, n0, &full[s]);
+          uint8_t* const ad = sA + s * T3_SUB * T3_TILE_A;
+          uint8_t* const bbd = sBb + s * T3_TILE_B;
+          uint8_t* const bsd = sBs + s * T3_TILE_B;
+          const int x = kb * T3_BK;
+          switch (jm) {
+#define T3_CASE(M) \
+  case M: t3_issue<M>(jobs, ad, bbd, bsd, x, m0, seg, n0, &full[s]); break;
+            T3_CASE(0) T3_CASE(1) T3_CASE(2) T3_CASE(3) T3_CASE(4) T3_CASE(5) T3_CASE(6) T3_CASE(7)
+            T3_CASE(8) T3_CASE(9) T3_CASE(10) T3_CASE(11) T3_CASE(12) T3_CASE(13) T3_CASE(14) T3_CASE(15)
+#undef T3_CASE
+          }
         }
       }
     }
@@ -470,7 +539,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         }
         tc_fence_after();
         int64_t tl;
-        const int nk = t3_job(jobs, t, tl).nk;
+        const int nk = sj[t3_job(sj, n_jobs, t, tl)].nk;
         bool ok = true;
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = (int)(g % T3_STAGES);
@@ -508,7 +577,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     int64_t g = 0;
     for (int64_t t = blockIdx.x; t < n_tiles && !s_abort; t += gridDim.x) {
       int64_t tl;
-      const int nk = t3_job(jobs, t, tl).nk;
+      const int nk = sj[t3_job(sj, n_jobs, t, tl)].nk;
       for (int kb = 0; kb < nk; ++kb, ++g) {
         const int s = (int)(g % T3_STAGES);
         if (!mbar_wait(&full[s], (uint32_t)((g / T3_STAGES) & 1))) {
@@ -552,30 +621,14 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
       }
       tc_fence_after();
       int64_t tl;
-      const T3Job& J = t3_job(jobs, t, tl);
-      const int64_t mp = tl / J.n_tiles_n;
-      const int n0 = (int)(tl % J.n_tiles_n) * TC_BN;
-      const int tr = q * 32 + lane;  // row of the 128-row block
-      const float* bias = J.bias;
-      const int n_out = J.n_out;
-#pragma unroll 1
-      for (int h = 0; h < T3_SUB; ++h) {
-        const int64_t mb = mp * T3_SUB + h;
-        const int64_t seg = (mb / J.rb_per_seg) * J.sb + tr / J.rb;
-        const int64_t row = (mb % J.rb_per_seg) * J.rb + tr % J.rb;  // row within the segment
-        const bool add_bias = bias != nullptr && (row % J.bias_period) == 0;
-        float* yrow = mb < J.n_mblk && row < J.seg_rows && seg < J.n_seg
-                          ? J.Y + seg * J.y_seg_stride + row * J.ldy + n0
-                          : nullptr;
-        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-          uint32_t vv[32];
-          tmem_ld32(tmem + (uint32_t)((a * T3_SUB + h) * TC_TMEM_COLS) + ((uint32_t)(q * 32) << 16) + (uint32_t)c0,
-                    vv);
-          const int n = n0 + c0 + lane;
-          const bool col_ok = n < n_out;
-          store_block_32x32(vv, st, lane, yrow ? yrow + c0 : nullptr, add_bias,
-                            bias != nullptr && col_ok ? bias[n] : 0.f, col_ok, J.accumulate != 0);
-        }
+      const int jm = t3_job(sj, n_jobs, t, tl);
+      const uint32_t acc = tmem + (uint32_t)(a * T3_SUB * TC_TMEM_COLS) + ((uint32_t)(q * 32) << 16);
+      switch (jm) {
+#define T3_EPI(M) \
+  case M: t3_epi_tile<M>(jobs, tl, acc, q, lane, st); break;
+        T3_EPI(0) T3_EPI(1) T3_EPI(2) T3_EPI(3) T3_EPI(4) T3_EPI(5) T3_EPI(6) T3_EPI(7)
+        T3_EPI(8) T3_EPI(9) T3_EPI(10) T3_EPI(11) T3_EPI(12) T3_EPI(13) T3_EPI(14) T3_EPI(15)
+#undef T3_EPI
       }
       tc_fence_before();
       __syncwarp();
@@ -922,23 +975,23 @@ cudaError_t gemm_tf32x3_tc_jobs(const T3JobDesc* d, int n, unsigned int* status,
         !make_map(&j.bb, q.Wbig, q.n_out, q.K, q.K, TC_BN, true) ||
         !make_map(&j.bs, q.Wsmall, q.n_out, q.K, q.K, TC_BN, true))
       return cudaErrorInvalidValue;
-    j.bias = q.bias;
-    j.Y = q.Y;
-    j.seg_rows = q.seg_rows;
-    j.n_seg = q.n_seg;
-    j.ldy = q.ldy;
-    j.y_seg_stride = q.y_seg_stride;
-    j.rb = rb;
-    j.sb = TC_BM / rb;
-    j.rb_per_seg = (q.seg_rows + rb - 1) / rb;
-    j.n_mblk = ((q.n_seg + j.sb - 1) / j.sb) * j.rb_per_seg;
-    j.n_out = q.n_out;
-    j.nk = (q.K + T3_BK - 1) / T3_BK;  // a ragged last K block reads zeros past K
-    j.n_tiles_n = (q.n_out + TC_BN - 1) / TC_BN;
-    j.bias_period = q.bias_period;
-    j.accumulate = q.accumulate ? 1 : 0;
-    tiles += ((j.n_mblk + T3_SUB - 1) / T3_SUB) * j.n_tiles_n;
-    j.tile_end = tiles;
+    j.f.bias = q.bias;
+    j.f.Y = q.Y;
+    j.f.seg_rows = q.seg_rows;
+    j.f.n_seg = q.n_seg;
+    j.f.ldy = q.ldy;
+    j.f.y_seg_stride = q.y_seg_stride;
+    j.f.rb = rb;
+    j.f.sb = TC_BM / rb;
+    j.f.rb_per_seg = (q.seg_rows + rb - 1) / rb;
+    j.f.n_mblk = ((q.n_seg + j.f.sb - 1) / j.f.sb) * j.f.rb_per_seg;
+    j.f.n_out = q.n_out;
+    j.f.nk = (q.K + T3_BK - 1) / T3_BK;  // a ragged last K block reads zeros past K
+    j.f.n_tiles_n = (q.n_out + TC_BN - 1) / TC_BN;
+    j.f.bias_period = q.bias_period;
+    j.f.accumulate = q.accumulate ? 1 : 0;
+    tiles += ((j.f.n_mblk + T3_SUB - 1) / T3_SUB) * j.f.n_tiles_n;
+    j.f.tile_end = tiles;
     if (++J.n == kT3MaxJobs) {
       e = flush();
       if (e != cudaSuccess) return e;

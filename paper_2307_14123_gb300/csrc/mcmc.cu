@@ -70,19 +70,13 @@ __device__ __forceinline__ void propose_kernel_body(const int64_t bx_, const int
   }
 }
 
-template <class T>
-__global__ void propose_kernel(const T* __restrict__ r, T* __restrict__ r_prop, int64_t B, int N3, double step,
-                               uint64_t seed, uint64_t t, const uint64_t* __restrict__ t_base) {
-  propose_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, r, r_prop, B, N3, step, seed, t, t_base);
-}
-
 // One launch over several molecules: block b runs entry m of the table.
 template <class T>
 __global__ void propose_kernel_group(const __grid_constant__ Grp<propose_kernel_args<T>> g) {
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
-  const propose_kernel_args<T>& a_ = g.a[m_];
-  propose_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.r, a_.r_prop, a_.B, a_.N3, a_.step, a_.seed, a_.t, a_.t_base);
+  GRP_STATIC(m_, const auto& a_ = g.a[K_];
+             propose_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.r, a_.r_prop, a_.B, a_.N3, a_.step, a_.seed, a_.t, a_.t_base);)
 }
 
 template <class T>
@@ -122,21 +116,13 @@ __device__ __forceinline__ void accept_kernel_body(const int64_t bx_, const int 
   if ((threadIdx.x % 32) == 0 && m && n_acc) atomicAdd(n_acc, (unsigned long long)__popc(m));
 }
 
-template <class T>
-__global__ void accept_kernel(T* __restrict__ r, T* __restrict__ logabs, const T* __restrict__ r_prop,
-                              const T* __restrict__ la_prop, const int8_t* __restrict__ sign_prop, int64_t B, int N3,
-                              uint64_t seed, uint64_t t, const uint64_t* __restrict__ t_base,
-                              unsigned long long* __restrict__ n_acc) {
-  accept_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, r, logabs, r_prop, la_prop, sign_prop, B, N3, seed, t, t_base, n_acc);
-}
-
 // One launch over several molecules: block b runs entry m of the table.
 template <class T>
 __global__ void accept_kernel_group(const __grid_constant__ Grp<accept_kernel_args<T>> g) {
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
-  const accept_kernel_args<T>& a_ = g.a[m_];
-  accept_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.r, a_.logabs, a_.r_prop, a_.la_prop, a_.sign_prop, a_.B, a_.N3, a_.seed, a_.t, a_.t_base, a_.n_acc);
+  GRP_STATIC(m_, const auto& a_ = g.a[K_];
+             accept_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.r, a_.logabs, a_.r_prop, a_.la_prop, a_.sign_prop, a_.B, a_.N3, a_.seed, a_.t, a_.t_base, a_.n_acc);)
 }
 
 // ---------------------------------------------------------------------------
@@ -271,18 +257,13 @@ __device__ __forceinline__ void esum_kernel_body(const int64_t bx_, const int by
   }
 }
 
-template <class T>
-__global__ void __launch_bounds__(kRedThreads) esum_kernel(const T* __restrict__ e, int64_t B, double* __restrict__ out2, unsigned int* status) {
-  esum_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, e, B, out2, status);
-}
-
 // One launch over several molecules: block b runs entry m of the table.
 template <class T>
 __global__ void __launch_bounds__(kRedThreads) esum_kernel_group(const __grid_constant__ Grp<esum_kernel_args<T>> g) {
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
-  const esum_kernel_args<T>& a_ = g.a[m_];
-  esum_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.e, a_.B, a_.out2, a_.status);
+  GRP_STATIC(m_, const auto& a_ = g.a[K_];
+             esum_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.e, a_.B, a_.out2, a_.status);)
 }
 
 __device__ double block_sum_det(double v, double* sh) {
@@ -356,32 +337,25 @@ __device__ __forceinline__ void loss_weights_kernel_body(const int64_t bx_, cons
   }
 }
 
-template <class T>
-__global__ void __launch_bounds__(kRedThreads) loss_weights_kernel(const T* __restrict__ e, int64_t B, int64_t Bp, double k, T* __restrict__ w,
-                        double* __restrict__ stats, double* __restrict__ srt) {
-  loss_weights_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, e, B, Bp, k, w, stats, srt);
-}
-
 // One launch over several molecules: block b runs entry m of the table.
 template <class T>
 __global__ void __launch_bounds__(kRedThreads) loss_weights_kernel_group(const __grid_constant__ Grp<loss_weights_kernel_args<T>> g) {
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
-  const loss_weights_kernel_args<T>& a_ = g.a[m_];
-  loss_weights_kernel_body<T>(l_ / g.ny[m_], (int)(l_ % g.ny[m_]), g.nbx[m_], a_.e, a_.B, a_.Bp, a_.k, a_.w, a_.stats, a_.srt);
+  GRP_STATIC(m_, const auto& a_ = g.a[K_];
+             loss_weights_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.e, a_.B, a_.Bp, a_.k, a_.w, a_.stats, a_.srt);)
 }
 
 }  // namespace
 
 __global__ void advance_counter_kernel(uint64_t* c, uint64_t n) { *c += n; }
 
+// Single-molecule launchers: the grouped kernels with a one-entry table.
 template <class T>
 cudaError_t launch_propose(const dq_handle_s& h, int64_t B, const T* r, T* r_prop, double step, uint64_t seed,
                            uint64_t t, const uint64_t* t_base, cudaStream_t s) {
-  const int N3 = 3 * h.N, nblk = (N3 + 3) / 4;
-  const int64_t n = B * nblk;
-  propose_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(r, r_prop, B, N3, step, seed, t, t_base);
-  return cudaGetLastError();
+  const dq_handle_s* hp = &h;
+  return launch_propose_group<T>(&hp, 1, &B, &r, &r_prop, step, seed, t, t_base, s);
 }
 
 template <class T>
@@ -412,24 +386,20 @@ template <class T>
 cudaError_t launch_accept(const dq_handle_s& h, int64_t B, T* r, T* logabs, const T* r_prop, const T* logabs_prop,
                           const int8_t* sign_prop, uint64_t seed, uint64_t t, const uint64_t* t_base,
                           unsigned long long* n_acc, cudaStream_t s) {
-  accept_kernel<T><<<(unsigned)((B + 255) / 256), 256, 0, s>>>(r, logabs, r_prop, logabs_prop, sign_prop, B, 3 * h.N,
-                                                               seed, t, t_base, n_acc);
-  return cudaGetLastError();
+  const dq_handle_s* hp = &h;
+  return launch_accept_group<T>(&hp, 1, &B, &r, &logabs, &r_prop, &logabs_prop, &sign_prop, seed, t, t_base, &n_acc,
+                                s);
 }
 
 template <class T>
 cudaError_t launch_esum(const T* e, int64_t B, double* out2, unsigned int* status, cudaStream_t s) {
-  esum_kernel<T><<<1, kRedThreads, 0, s>>>(e, B, out2, status);
-  return cudaGetLastError();
+  return launch_esum_group<T>(1, &e, &B, &out2, &status, s);
 }
 
 template <class T>
 cudaError_t launch_loss_weights(const T* e, int64_t B, double k, T* w, double* stats, double* scratch,
                                 cudaStream_t s) {
-  int64_t Bp = 1;
-  while (Bp < B) Bp <<= 1;
-  loss_weights_kernel<T><<<1, kRedThreads, 0, s>>>(e, B, Bp, k, w, stats, scratch);
-  return cudaGetLastError();
+  return launch_loss_weights_group<T>(1, &e, &B, k, &w, stats ? &stats : nullptr, &scratch, s);
 }
 
 // Grouped launches: one launch per sampler step over every molecule of a batch
