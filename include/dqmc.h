@@ -292,6 +292,60 @@ dq_status dq_test_gemm_tf32x3(const float* X, int64_t rows, int32_t K, int64_t l
                               const float* bias, int32_t bias_period, float* Y, int64_t ldy, float* wsplit,
                               uint32_t* status, void* stream);
 
+/* ---- Batches of molecules ------------------------------------------------
+ * A batch holds up to DQ_MAX_BATCH molecules, each with its own system,
+ * ansatz sizes and parameter vector, in one precision (DQ_FP32 or
+ * DQ_BF16_MIXED) and with equal numbers of layers.  The walkers of all
+ * molecules, uneven electron counts included, go through every step of the
+ * forward pass (Sec. 3 and Sec. 4.2), the Metropolis sampler (Sec. 5) and the
+ * loss weights (Sec. 4.4) in one kernel launch per step: each launch carries
+ * a table with every molecule's dimensions, parameters and buffers, and the
+ * tensor-core GEMMs of a step run as one persistent launch whose tiles cover
+ * all molecules.  Walkers are processed in `rounds` chunks (molecule m takes
+ * ceil(B[m] / rounds) walkers per chunk); 0, the default, picks the fewest
+ * chunks of at most dq_max_chunk walkers of each molecule.  Each molecule's
+ * results equal those of the single-molecule calls on its own handle with the
+ * same inputs (the single-molecule calls launch the same kernels with a
+ * one-entry table): log|psi|, sign and E_loc bit for bit, and the Metropolis
+ * draws of molecule m are those of mcmc_step with the same seed and step
+ * counter.  grad_logpsi_multi runs the reverse pass molecule by molecule.
+ * Array arguments (params, r, B, logabs, ...) are HOST arrays of n_mol
+ * entries; entry m is a device pointer (or count) for molecule m, laid out as
+ * in the single-molecule call.  Workspace: dq_multi_workspace_size with the
+ * same B and op (DQ_OP_EVAL, _LOCAL_ENERGY, _MCMC, _GRAD, _LOSS_WEIGHTS). */
+#define DQ_MAX_BATCH 8
+typedef struct dq_multi_s* dq_multi;
+dq_status dq_create_multi(int32_t n_mol, const dq_system* systems, const dq_ansatz_cfg* cfgs, int32_t precision,
+                          dq_multi* out);
+dq_status dq_destroy_multi(dq_multi m);
+/* Borrowed handle of molecule k (parameter count and layout, single-molecule
+ * calls); owned by the batch, valid until dq_destroy_multi. */
+dq_status dq_multi_handle(dq_multi m, int32_t k, dq_handle* h);
+dq_status dq_multi_set_rounds(dq_multi m, int32_t rounds);
+dq_status dq_multi_rounds(dq_multi m, int32_t* rounds);
+dq_status dq_multi_workspace_size(dq_multi m, const int64_t* B, int32_t op, size_t* bytes);
+dq_status ansatz_eval_multi(dq_multi m, const void* const* params, const void* const* r, const int64_t* B,
+                            void* const* logabs, int8_t* const* sign, void* ws, size_t ws_bytes, void* stream);
+/* e_sum2: nullable host array; entry m nullable, device double[2] of molecule m. */
+dq_status local_energy_multi(dq_multi m, const void* const* params, const void* const* r, const int64_t* B,
+                             void* const* logabs, int8_t* const* sign, void* const* e_loc, double* const* e_sum2,
+                             void* ws, size_t ws_bytes, void* stream);
+/* One step counter for the batch: host step_counter, or the device counter
+ * step_counter_dev (nullable) as in mcmc_step_dev.  n_accepted: nullable host
+ * array of nullable device int64 counters, one per molecule. */
+dq_status mcmc_step_multi(dq_multi m, const void* const* params, void* const* r, void* const* logabs,
+                          const int64_t* B, int32_t n_steps, double step_size, uint64_t seed, uint64_t step_counter,
+                          uint64_t* step_counter_dev, int64_t* const* n_accepted, void* ws, size_t ws_bytes,
+                          void* stream);
+/* Weighted gradient (grad_logpsi mode 0) of every molecule. */
+dq_status grad_logpsi_multi(dq_multi m, const void* const* params, const void* const* r, const int64_t* B,
+                            const void* const* weights, void* const* grad_out, void* ws, size_t ws_bytes,
+                            void* stream);
+/* stats: nullable host array; entry m nullable, device double[4] as in vmc_loss_weights. */
+dq_status vmc_loss_weights_multi(dq_multi m, const void* const* e_loc, const int64_t* B, double clip_k,
+                                 void* const* weights, double* const* stats, void* ws, size_t ws_bytes,
+                                 void* stream);
+
 /* Human-readable name of a status code (static string). */
 const char* dq_status_string(dq_status s);
 

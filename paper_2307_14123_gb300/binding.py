@@ -32,7 +32,10 @@ EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_
            "ansatz_eval", "local_energy", "mcmc_step", "grad_logpsi", "vmc_loss_weights", "dq_last_device_status",
            "dq_status_string", "dq_profile_enable", "dq_profile_reset", "dq_profile_read", "dq_profile_kind_name",
            "dq_profile_kind_count", "vmc_loss_weights_noalloc", "dq_fp64_matrix_count", "dq_test_gemm_bf16",
-           "dq_test_gemm_tf32x3", "mcmc_step_dev", "mala_step"]
+           "dq_test_gemm_tf32x3", "mcmc_step_dev", "mala_step", "dq_create_multi", "dq_destroy_multi",
+           "dq_multi_handle", "dq_multi_set_rounds", "dq_multi_rounds", "dq_multi_workspace_size",
+           "ansatz_eval_multi", "local_energy_multi", "mcmc_step_multi", "grad_logpsi_multi",
+           "vmc_loss_weights_multi"]
 
 
 class DQError(RuntimeError):
@@ -90,6 +93,17 @@ def load_library(path=None):
         lib.dq_profile_read.argtypes = [P, i32, P, P]
         lib.dq_profile_kind_name.argtypes = [i32]
         lib.dq_profile_kind_count.argtypes = []
+        lib.dq_create_multi.argtypes = [i32, P, P, i32, P]
+        lib.dq_destroy_multi.argtypes = [P]
+        lib.dq_multi_handle.argtypes = [P, i32, P]
+        lib.dq_multi_set_rounds.argtypes = [P, i32]
+        lib.dq_multi_rounds.argtypes = [P, P]
+        lib.dq_multi_workspace_size.argtypes = [P, P, i32, P]
+        lib.ansatz_eval_multi.argtypes = [P, P, P, P, P, P, P, sz, P]
+        lib.local_energy_multi.argtypes = [P, P, P, P, P, P, P, P, P, sz, P]
+        lib.mcmc_step_multi.argtypes = [P, P, P, P, P, i32, f64, u64, u64, P, P, P, sz, P]
+        lib.grad_logpsi_multi.argtypes = [P, P, P, P, P, P, P, sz, P]
+        lib.vmc_loss_weights_multi.argtypes = [P, P, P, f64, P, P, P, sz, P]
         for name in EXPORTS:
             getattr(lib, name).restype = ctypes.c_int
         lib.dq_status_string.restype = ctypes.c_char_p
@@ -325,6 +339,174 @@ class Ansatz:
         f = ctypes.c_uint32()
         _check(self.lib.dq_last_device_status(self.h, self._stream(), ctypes.byref(f)))
         return f.value
+
+
+def _sys_cfg(system, cfg, keep):
+    Z = (ctypes.c_double * len(system.Z))(*[float(z) for z in system.Z])
+    flatR = [float(x) for x in torch.as_tensor(system.R, dtype=torch.float64).reshape(-1).tolist()]
+    R = (ctypes.c_double * len(flatR))(*flatR)
+    keep += [Z, R]
+    sysc = _System(len(system.Z), ctypes.cast(Z, ctypes.c_void_p), ctypes.cast(R, ctypes.c_void_p),
+                   int(system.n_up), int(system.n_down))
+    cfgc = _Cfg(int(cfg.width), int(cfg.n_layers), int(cfg.n_det), int(cfg.n_rbf), float(cfg.rbf_cutoff),
+                int(cfg.use_jastrow), int(cfg.use_cusp), float(cfg.cusp_alpha))
+    return sysc, cfgc
+
+
+def _ptrs(ts):
+    """Host array of device pointers (None for a missing entry)."""
+    return (ctypes.c_void_p * len(ts))(*[t.data_ptr() if t is not None else None for t in ts])
+
+
+class AnsatzBatch:
+    """A batch of molecules (``dq_multi``): each its own system, ansatz sizes and
+    parameters, all in one precision (fp32 or bf16).  Every step of the forward
+    pass, the Metropolis sampler and the loss weights runs as one kernel launch
+    over all molecules' walkers.  Methods take and return lists with one entry
+    per molecule (device tensors, laid out as for :class:`Ansatz`)."""
+
+    def __init__(self, systems, cfgs, precision="fp32", device=None):
+        self.lib = load_library()
+        if not torch.cuda.is_available():
+            raise DQError("no CUDA device: the library has no CPU path")
+        device = torch.device("cuda") if device is None else torch.device(device)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device.index is None else device.index)
+        self.precision = precision
+        self.dtype = torch.float32
+        self.n = len(systems)
+        self._keep = []
+        pairs = [_sys_cfg(sy, cf, self._keep) for sy, cf in zip(systems, cfgs)]
+        sys_arr = (_System * self.n)(*[p[0] for p in pairs])
+        cfg_arr = (_Cfg * self.n)(*[p[1] for p in pairs])
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.dq_create_multi(self.n, sys_arr, cfg_arr, PRECISIONS[precision], ctypes.byref(h)))
+        self.h = h
+        self.handles, self.P = [], []
+        for k in range(self.n):
+            hk = ctypes.c_void_p()
+            _check(self.lib.dq_multi_handle(self.h, k, ctypes.byref(hk)))
+            P = ctypes.c_int64()
+            _check(self.lib.dq_param_count(hk, ctypes.byref(P)))
+            self.handles.append(hk)
+            self.P.append(P.value)
+        self.N = [int(sy.n_up + sy.n_down) for sy in systems]
+        self._ws = None
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.lib is not None:
+            try:
+                self.lib.dq_destroy_multi(self.h)
+            except Exception:
+                pass
+            self.h = None
+
+    def _stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _B(self, r):
+        return (ctypes.c_int64 * self.n)(*[t.numel() // (3 * N) for t, N in zip(r, self.N)])
+
+    def _check_in(self, ts, what):
+        for t in ts:
+            if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous():
+                raise DQError(f"{what}: contiguous {self.dtype} tensors on {self.device} expected")
+
+    def set_rounds(self, rounds):
+        _check(self.lib.dq_multi_set_rounds(self.h, int(rounds)))
+
+    def rounds(self):
+        v = ctypes.c_int32()
+        _check(self.lib.dq_multi_rounds(self.h, ctypes.byref(v)))
+        return v.value
+
+    def workspace(self, B, op):
+        n = ctypes.c_size_t()
+        _check(self.lib.dq_multi_workspace_size(self.h, B, int(op), ctypes.byref(n)))
+        size = max(n.value, 256)
+        if self._ws is None or self._ws.numel() < size:
+            self._ws = None
+            self._ws = torch.empty(size, dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def ansatz_eval(self, params, r):
+        self._check_in(list(params) + list(r), "ansatz_eval")
+        B = self._B(r)
+        la = [torch.empty(B[k], dtype=self.dtype, device=self.device) for k in range(self.n)]
+        sg = [torch.empty(B[k], dtype=torch.int8, device=self.device) for k in range(self.n)]
+        ws = self.workspace(B, OP_EVAL)
+        _check(self.lib.ansatz_eval_multi(self.h, _ptrs(params), _ptrs(r), B, _ptrs(la), _ptrs(sg), _ptr(ws),
+                                          ws.numel(), self._stream()))
+        return la, sg
+
+    def local_energy(self, params, r, sums=False):
+        """Lists (logabs, sign, e_loc) and, with ``sums``, an FP64 [n][2] tensor of [sum E, sum E^2]."""
+        self._check_in(list(params) + list(r), "local_energy")
+        B = self._B(r)
+        la = [torch.empty(B[k], dtype=self.dtype, device=self.device) for k in range(self.n)]
+        sg = [torch.empty(B[k], dtype=torch.int8, device=self.device) for k in range(self.n)]
+        el = [torch.empty(B[k], dtype=self.dtype, device=self.device) for k in range(self.n)]
+        e2 = torch.empty((self.n, 2), dtype=torch.float64, device=self.device) if sums else None
+        ws = self.workspace(B, OP_LOCAL_ENERGY)
+        _check(self.lib.local_energy_multi(self.h, _ptrs(params), _ptrs(r), B, _ptrs(la), _ptrs(sg), _ptrs(el),
+                                           _ptrs(list(e2)) if sums else None, _ptr(ws), ws.numel(),
+                                           self._stream()))
+        return (la, sg, el) + ((e2,) if sums else ())
+
+    def mcmc_step(self, params, r, logabs, n_steps=1, step_size=0.2, seed=0, step_counter=0):
+        """In-place Metropolis update of every molecule's walkers; returns the accepted counts
+        ([n] device int64).  step_counter: int, or a one-element int64 CUDA tensor."""
+        self._check_in(list(params) + list(r) + list(logabs), "mcmc_step")
+        B = self._B(r)
+        n_acc = torch.zeros(self.n, dtype=torch.int64, device=self.device)
+        ws = self.workspace(B, OP_MCMC)
+        dev_ctr = None
+        if isinstance(step_counter, torch.Tensor):
+            dev_ctr, step_counter = step_counter, 0
+        _check(self.lib.mcmc_step_multi(self.h, _ptrs(params), _ptrs(r), _ptrs(logabs), B, int(n_steps),
+                                        float(step_size), int(seed) & 0xFFFFFFFFFFFFFFFF, int(step_counter),
+                                        _ptr(dev_ctr), _ptrs(list(n_acc.view(self.n, 1))), _ptr(ws), ws.numel(),
+                                        self._stream()))
+        return n_acc
+
+    def vmc_loss_weights(self, e_loc, clip_k=5.0):
+        """Lists of weights and an FP64 [n][4] tensor of stats (see :meth:`Ansatz.vmc_loss_weights`)."""
+        self._check_in(list(e_loc), "vmc_loss_weights")
+        B = (ctypes.c_int64 * self.n)(*[t.numel() for t in e_loc])
+        w = [torch.empty_like(t) for t in e_loc]
+        stats = torch.empty((self.n, 4), dtype=torch.float64, device=self.device)
+        ws = self.workspace(B, OP_LOSS_WEIGHTS)
+        _check(self.lib.vmc_loss_weights_multi(self.h, _ptrs(e_loc), B, float(clip_k), _ptrs(w), _ptrs(list(stats)),
+                                               _ptr(ws), ws.numel(), self._stream()))
+        return w, stats
+
+    def grad_logpsi(self, params, r, weights):
+        """Weighted gradients sum_b w_b d log|psi_b| / d theta, one [P_m] tensor per molecule."""
+        self._check_in(list(params) + list(r) + list(weights), "grad_logpsi")
+        B = self._B(r)
+        out = [torch.empty(P, dtype=self.dtype, device=self.device) for P in self.P]
+        ws = self.workspace(B, OP_GRAD)
+        _check(self.lib.grad_logpsi_multi(self.h, _ptrs(params), _ptrs(r), B, _ptrs(weights), _ptrs(out), _ptr(ws),
+                                          ws.numel(), self._stream()))
+        return out
+
+    # -- measurement: launches of the batch are timed on molecule 0's handle ------------
+    def profile(self, on=True):
+        _check(self.lib.dq_profile_enable(self.handles[0], 1 if on else 0))
+
+    def profile_reset(self):
+        _check(self.lib.dq_profile_reset(self.handles[0]))
+
+    def profile_read(self):
+        out = {}
+        for k in range(self.lib.dq_profile_kind_count()):
+            ms, n = ctypes.c_double(), ctypes.c_int64()
+            st = self.lib.dq_profile_read(self.handles[0], k, ctypes.byref(ms), ctypes.byref(n))
+            if st not in (0, 5):
+                _check(st)
+            if n.value:
+                out[self.lib.dq_profile_kind_name(k).decode()] = (ms.value, n.value)
+        return out
 
 
 def test_gemm_bf16(X, W, bias=None, bias_period=1):

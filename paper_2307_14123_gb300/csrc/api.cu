@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <initializer_list>
 #include <new>
 #include <vector>
 
@@ -763,6 +764,309 @@ dq_status run_mala(dq_handle h, const T* params, T* r, T* logabs, T* grad, T* e_
   if (t_dev && n_steps > 0) DQ_CU(launch_advance_counter(t_dev, (uint64_t)n_steps, s));
   return DQ_OK;
 }
+// ---------------------------------------------------------------------------
+// Batches of molecules (dq_multi): every kernel of the forward pass, the
+// sampler and the loss weights runs as one launch over all molecules of the
+// batch (grouped launches, forward.cu / mcmc.cu; the 3 x TF32 GEMMs as one
+// persistent job-list launch), each molecule with its own electron count,
+// parameters and buffers.  Walkers are processed in `rounds` chunks: molecule m
+// takes ceil(B_m / rounds) walkers per round.
+// ---------------------------------------------------------------------------
+struct MultiFwdPlan {
+  int rounds;
+  int64_t Bc[kMaxGroup];
+  size_t off[kMaxGroup];
+  FwdPlan fp[kMaxGroup];
+  size_t total;
+};
+
+int multi_rounds(const dq_multi_s& g, const int64_t* B) {
+  if (g.rounds > 0) return g.rounds;
+  int r = 1;
+  for (int m = 0; m < g.n; ++m) r = std::max<int>(r, (int)((B[m] + g.h[m]->max_chunk - 1) / g.h[m]->max_chunk));
+  return r;
+}
+
+MultiFwdPlan plan_forward_multi(const dq_multi_s& g, const int64_t* B, bool jets, size_t elem) {
+  MultiFwdPlan p{};
+  p.rounds = multi_rounds(g, B);
+  size_t o = 0;
+  for (int m = 0; m < g.n; ++m) {
+    p.Bc[m] = std::max<int64_t>(1, (std::max<int64_t>(B[m], 0) + p.rounds - 1) / p.rounds);
+    p.fp[m] = plan_forward(*g.h[m], p.Bc[m], jets, elem);
+    p.off[m] = o;
+    o += align_up(p.fp[m].total);
+  }
+  p.total = o;
+  return p;
+}
+
+template <class T>
+FwdBuffers<T> carve_forward(const FwdPlan& plan, unsigned char* ws, bool bf16) {
+  FwdBuffers<T> bf;
+  bf.geo = reinterpret_cast<T*>(ws + plan.geo);
+  bf.rbf = reinterpret_cast<T*>(ws + plan.rbf);
+  bf.eh = reinterpret_cast<T*>(ws + plan.eh);
+  bf.ew = reinterpret_cast<T*>(ws + plan.ew);
+  bf.F = reinterpret_cast<T*>(ws + plan.F);
+  bf.Z = reinterpret_cast<T*>(ws + plan.Z);
+  bf.msg = reinterpret_cast<T*>(ws + plan.msg);
+  bf.phi = reinterpret_cast<T*>(ws + plan.phi);
+  bf.det = reinterpret_cast<double*>(ws + plan.det);
+  bf.js = reinterpret_cast<T*>(ws + plan.js);
+  bf.jh = reinterpret_cast<T*>(ws + plan.jh);
+  bf.z0 = reinterpret_cast<T*>(ws + plan.z0);
+  bf.msg_bf = bf16 ? ws + plan.msg_bf : nullptr;
+  bf.F_bf = bf16 ? ws + plan.F_bf : nullptr;
+  return bf;
+}
+
+// The forward pass of a batch: per walker the same kernels and GEMM tiles as
+// run_forward (which launches the same grouped kernels with one entry), so each
+// molecule's results equal its single-molecule results bit for bit.
+template <class T>
+dq_status run_forward_multi(const dq_multi_s& g, const T* const* params, const T* const* r, const int64_t* B,
+                            bool jets, T* const* logabs, int8_t* const* sign, T* const* e_loc, unsigned char* ws,
+                            size_t ws_bytes, cudaStream_t s, const MultiFwdPlan* given = nullptr) {
+  static_assert(sizeof(T) == 4, "batches run in the FP32 modes");
+  const int n = g.n;
+  const MultiFwdPlan P = given ? *given : plan_forward_multi(g, B, jets, sizeof(T));
+  if (ws == nullptr || ws_bytes < P.total || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
+  const dq_handle_s& H = *g.h[0];  // launch timing of the batch goes to molecule 0's profiler
+  const bool use_tc = g.precision == DQ_BF16_MIXED;
+  MolFwd<T> mf[kMaxGroup];
+  T3Weights w3[kMaxGroup];
+  unsigned char* Wbf[kMaxGroup];
+  for (int m = 0; m < n; ++m) {
+    const dq_handle_s& h = *g.h[m];
+    unsigned char* base = ws + P.off[m];
+    mf[m].h = &h;
+    mf[m].params = params[m];
+    mf[m].b = carve_forward<T>(P.fp[m], base, use_tc);
+    const int C = jets ? 3 * h.N + 2 : 1;
+    mf[m].d = FwdDims{P.Bc[m], h.N, h.n_up, h.n_dn, h.M, h.D, h.K, h.Q, C};
+    w3[m] = t3_weights(h, base + P.fp[m].W_t3);
+    DQ_CU(split_t3_weights(h, params[m], w3[m], s));
+    Wbf[m] = base + P.fp[m].W_bf;
+    if (use_tc)
+      for (int l = 0; l < h.L; ++l) {
+        DQ_CU(launch_to_bf16(params[m] + h.off.layer[l].W_g, Wbf[m] + (size_t)l * 4 * h.D * h.D * 2,
+                             (int64_t)3 * h.D * h.D, s));
+        DQ_CU(launch_to_bf16(params[m] + h.off.layer[l].W_h, Wbf[m] + ((size_t)l * 4 + 3) * h.D * h.D * 2,
+                             (int64_t)h.D * h.D, s));
+      }
+  }
+  const int kb = jets ? 0 : kValueOffset;
+  const int L = g.h[0]->L;
+  DQ_LAUNCH(H, kb + PK_LAYER0, launch_layer0_node_group<T>(mf, n, s));
+  const T* rq[kMaxGroup];
+  T *la[kMaxGroup], *el[kMaxGroup];
+  int8_t* sg[kMaxGroup];
+  T3JobDesc jd[6 * kMaxGroup];
+  for (int q = 0; q < P.rounds; ++q) {
+    bool any = false;
+    for (int m = 0; m < n; ++m) {
+      const dq_handle_s& h = *g.h[m];
+      const int64_t b0 = (int64_t)q * P.Bc[m];
+      const int64_t nb = std::max<int64_t>(0, std::min<int64_t>(P.Bc[m], B[m] - b0));
+      mf[m].d.Bc = nb;
+      any = any || nb > 0;
+      rq[m] = nb > 0 ? r[m] + b0 * h.N * 3 : nullptr;
+      la[m] = nb > 0 ? logabs[m] + b0 : nullptr;
+      sg[m] = nb > 0 ? sign[m] + b0 : nullptr;
+      el[m] = nb > 0 && e_loc ? e_loc[m] + b0 : nullptr;
+    }
+    if (!any) break;
+    DQ_LAUNCH(H, kb + PK_GEOMETRY, launch_geometry_group<T>(mf, n, rq, s));
+    for (int l = 0; l < L; ++l) {
+      DQ_LAUNCH(H, kb + PK_EDGE_HIDDEN, launch_edge_hidden_group<T>(mf, n, l, s));
+      int nj = 0;
+      for (int m = 0; m < n; ++m) {  // edge filters: three edge types of every molecule
+        const dq_handle_s& h = *g.h[m];
+        const FwdDims& d = mf[m].d;
+        if (d.Bc <= 0) continue;
+        const int ej = d.C > 1 ? 3 : 1, E = h.edges.n_all, D = h.D;
+        const int e0[3] = {0, h.edges.n_par, h.edges.n_ee};
+        const int ng[3] = {h.edges.n_par, h.edges.n_anti, h.edges.n_en};
+        const int64_t seg = (int64_t)E * ej * D;
+        for (int t = 0; t < 3; ++t)
+          jd[nj++] = T3JobDesc{reinterpret_cast<const float*>(mf[m].b.eh) + (int64_t)e0[t] * ej * D,
+                               (int64_t)ng[t] * ej, d.Bc, seg, D, D, w3[m].w2(l, t, 0), w3[m].w2(l, t, 1), D,
+                               reinterpret_cast<const float*>(params[m] + h.off.layer[l].b2[t]), ej,
+                               reinterpret_cast<float*>(mf[m].b.ew) + (int64_t)e0[t] * ej * D, D, seg, false};
+      }
+      DQ_LAUNCH(H, kb + PK_GEMM_EDGE, gemm_tf32x3_tc_jobs(jd, nj, H.d_status, s));
+      if (l > 0) {  // node map z = W_h f
+        nj = 0;
+        for (int m = 0; m < n; ++m) {
+          const dq_handle_s& h = *g.h[m];
+          const FwdDims& d = mf[m].d;
+          if (d.Bc <= 0) continue;
+          const int64_t rows = d.Bc * d.N * d.C;
+          if (use_tc) {
+            DQ_LAUNCH(H, kb + PK_GEMM_NODE,
+                      gemm_bf16_tc(mf[m].b.F_bf, rows, h.D, h.D, Wbf[m] + ((size_t)l * 4 + 3) * h.D * h.D * 2, h.D,
+                                   nullptr, 1, reinterpret_cast<float*>(mf[m].b.Z), h.D, H.d_status, s));
+          } else {
+            jd[nj++] = T3JobDesc{reinterpret_cast<const float*>(mf[m].b.F), rows, 1, 0, h.D, h.D, w3[m].wh(l, 0),
+                                 w3[m].wh(l, 1), h.D, nullptr, 1, reinterpret_cast<float*>(mf[m].b.Z), h.D, 0, false};
+          }
+        }
+        if (!use_tc) DQ_LAUNCH(H, kb + PK_GEMM_NODE, gemm_tf32x3_tc_jobs(jd, nj, H.d_status, s));
+      }
+      DQ_LAUNCH(H, kb + PK_MESSAGES, launch_messages_group<T>(mf, n, l, l == 0, s));
+      nj = 0;
+      for (int m = 0; m < n; ++m) {  // update map W_g [m_par; m_anti; m_nuc] + b_g
+        const dq_handle_s& h = *g.h[m];
+        const FwdDims& d = mf[m].d;
+        if (d.Bc <= 0) continue;
+        const int64_t rows = d.Bc * d.N * d.C;
+        const float* bg = reinterpret_cast<const float*>(params[m] + h.off.layer[l].b_g);
+        if (use_tc) {
+          DQ_LAUNCH(H, kb + PK_GEMM_UPDATE,
+                    gemm_bf16_tc(mf[m].b.msg_bf, rows, 3 * h.D, 3 * h.D, Wbf[m] + (size_t)l * 4 * h.D * h.D * 2, h.D,
+                                 bg, d.C, reinterpret_cast<float*>(mf[m].b.Z), h.D, H.d_status, s));
+        } else {
+          jd[nj++] = T3JobDesc{reinterpret_cast<const float*>(mf[m].b.msg), rows, 1, 0, 3 * h.D, 3 * h.D,
+                               w3[m].wg(l, 0), w3[m].wg(l, 1), h.D, bg, d.C, reinterpret_cast<float*>(mf[m].b.Z), h.D,
+                               0, false};
+        }
+      }
+      if (!use_tc) DQ_LAUNCH(H, kb + PK_GEMM_UPDATE, gemm_tf32x3_tc_jobs(jd, nj, H.d_status, s));
+      DQ_LAUNCH(H, kb + PK_UPDATE, launch_update_group<T>(mf, n, l == 0, s));
+    }
+    int nj = 0;
+    for (int m = 0; m < n; ++m) {  // orbitals of both spins of every molecule
+      const dq_handle_s& h = *g.h[m];
+      const FwdDims& d = mf[m].d;
+      if (d.Bc <= 0) continue;
+      const int Wo = h.K * std::max(h.n_up, h.n_dn), C = d.C, D = h.D, N = h.N;
+      const int ns[2] = {h.n_up, h.n_dn}, i0[2] = {0, h.n_up};
+      for (int sp = 0; sp < 2; ++sp)
+        jd[nj++] = T3JobDesc{reinterpret_cast<const float*>(mf[m].b.F) + (int64_t)i0[sp] * C * D,
+                             (int64_t)ns[sp] * C, d.Bc, (int64_t)N * C * D, D, D, w3[m].wo(sp, 0), w3[m].wo(sp, 1),
+                             h.K * ns[sp], reinterpret_cast<const float*>(params[m] + h.off.b_o[sp]), C,
+                             reinterpret_cast<float*>(mf[m].b.phi) + (int64_t)i0[sp] * C * Wo, Wo,
+                             (int64_t)N * C * Wo, false};
+    }
+    DQ_LAUNCH(H, kb + PK_GEMM_ORBITAL, gemm_tf32x3_tc_jobs(jd, nj, H.d_status, s));
+    DQ_LAUNCH(H, kb + PK_ORBITAL_DET, launch_orbital_det_group<T>(mf, n, s));
+    DQ_LAUNCH(H, kb + PK_JASTROW_SUM, launch_jastrow_sum_group<T>(mf, n, s));
+    nj = 0;
+    for (int m = 0; m < n; ++m) {
+      const dq_handle_s& h = *g.h[m];
+      const FwdDims& d = mf[m].d;
+      if (d.Bc <= 0 || !h.use_jastrow) continue;
+      jd[nj++] = T3JobDesc{reinterpret_cast<const float*>(mf[m].b.js), d.Bc * d.C, 1, 0, h.D, h.D, w3[m].wj(0),
+                           w3[m].wj(1), h.D, reinterpret_cast<const float*>(params[m] + h.off.b_J1), d.C,
+                           reinterpret_cast<float*>(mf[m].b.jh), h.D, 0, false};
+    }
+    DQ_LAUNCH(H, kb + PK_GEMM_JASTROW, gemm_tf32x3_tc_jobs(jd, nj, H.d_status, s));
+    DQ_LAUNCH(H, kb + PK_COMBINE, launch_combine_group<T>(mf, n, la, sg, e_loc ? el : nullptr, nullptr, s));
+  }
+  return DQ_OK;
+}
+
+// Metropolis steps of a batch: one grouped proposal, value-only forward and
+// accept launch per step; molecule m's draws equal mcmc_step's on its own handle.
+struct MultiMcmcPlan {
+  size_t r_prop[kMaxGroup], la_prop[kMaxGroup], sign_prop[kMaxGroup], fwd;
+  MultiFwdPlan fp;
+  size_t total;
+};
+MultiMcmcPlan plan_mcmc_multi(const dq_multi_s& g, const int64_t* B, size_t elem) {
+  MultiMcmcPlan p{};
+  size_t o = 0;
+  for (int m = 0; m < g.n; ++m) {
+    const size_t b = (size_t)std::max<int64_t>(B[m], 1);
+    p.r_prop[m] = o;
+    o += align_up(b * 3 * g.h[m]->N * elem);
+    p.la_prop[m] = o;
+    o += align_up(b * elem);
+    p.sign_prop[m] = o;
+    o += align_up(b);
+  }
+  p.fwd = o;
+  p.fp = plan_forward_multi(g, B, false, elem);
+  p.total = o + p.fp.total;
+  return p;
+}
+
+template <class T>
+dq_status run_mcmc_multi(const dq_multi_s& g, const T* const* params, T* const* r, T* const* logabs, const int64_t* B,
+                         int32_t n_steps, double step, uint64_t seed, uint64_t t0, uint64_t* t_dev,
+                         int64_t* const* n_acc, unsigned char* ws, size_t ws_bytes, cudaStream_t s) {
+  const int n = g.n;
+  const MultiMcmcPlan plan = plan_mcmc_multi(g, B, sizeof(T));
+  if (ws == nullptr || ws_bytes < plan.total || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
+  const dq_handle_s& H = *g.h[0];
+  T *rp[kMaxGroup], *lp[kMaxGroup];
+  const T *rpc[kMaxGroup], *lpc[kMaxGroup], *rc[kMaxGroup];
+  int8_t* sp[kMaxGroup];
+  const int8_t* spc[kMaxGroup];
+  unsigned long long* acc[kMaxGroup];
+  const dq_handle_s* hs[kMaxGroup];
+  for (int m = 0; m < n; ++m) {
+    hs[m] = g.h[m];
+    rp[m] = reinterpret_cast<T*>(ws + plan.r_prop[m]);
+    lp[m] = reinterpret_cast<T*>(ws + plan.la_prop[m]);
+    sp[m] = reinterpret_cast<int8_t*>(ws + plan.sign_prop[m]);
+    rpc[m] = rp[m];
+    lpc[m] = lp[m];
+    spc[m] = sp[m];
+    rc[m] = r[m];
+    acc[m] = n_acc ? reinterpret_cast<unsigned long long*>(n_acc[m]) : nullptr;
+    if (acc[m]) DQ_CU(cudaMemsetAsync(acc[m], 0, sizeof(int64_t), s));
+  }
+  for (int32_t k = 0; k < n_steps; ++k) {
+    const uint64_t t = t0 + (uint64_t)k;
+    DQ_LAUNCH(H, PK_PROPOSE, launch_propose_group<T>(hs, n, B, rc, rp, step, seed, t, t_dev, s));
+    dq_status st = run_forward_multi<T>(g, params, rpc, B, false, lp, sp, nullptr, ws + plan.fwd, ws_bytes - plan.fwd,
+                                        s, &plan.fp);
+    if (st != DQ_OK) return st;
+    DQ_LAUNCH(H, PK_ACCEPT, launch_accept_group<T>(hs, n, B, r, logabs, rpc, lpc, spc, seed, t, t_dev,
+                                                   n_acc ? acc : nullptr, s));
+  }
+  if (t_dev && n_steps > 0) DQ_CU(launch_advance_counter(t_dev, (uint64_t)n_steps, s));
+  return DQ_OK;
+}
+
+// Reverse pass of a batch: molecule by molecule (run_grad), each in its own
+// workspace region.
+struct MultiGradPlan {
+  size_t off[kMaxGroup];
+  size_t bytes[kMaxGroup];
+  size_t total;
+};
+MultiGradPlan plan_grad_multi(const dq_multi_s& g, const int64_t* B, size_t elem) {
+  MultiGradPlan p{};
+  size_t o = 0;
+  for (int m = 0; m < g.n; ++m) {
+    const int64_t Bc = std::max<int64_t>(1, std::min<int64_t>(B[m], g.h[m]->max_chunk));
+    p.off[m] = o;
+    p.bytes[m] = plan_grad(*g.h[m], Bc, elem).total;
+    o += align_up(p.bytes[m]);
+  }
+  p.total = o;
+  return p;
+}
+
+size_t loss_scratch_multi(const dq_multi_s& g, const int64_t* B, size_t* off) {
+  size_t o = 0;
+  for (int m = 0; m < g.n; ++m) {
+    if (off) off[m] = o;
+    o += loss_scratch_bytes(std::max<int64_t>(B[m], 1));
+  }
+  return o;
+}
+
+dq_status check_multi(dq_multi g) {
+  if (g == nullptr) return DQ_ERR_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return DQ_ERR_CUDA;
+  if (dev != g->device) return DQ_ERR_ARG;
+  return DQ_OK;
+}
 }  // namespace
 }  // namespace dq
 
@@ -1155,6 +1459,194 @@ dq_status dq_test_gemm_tf32x3(const float* X, int64_t rows, int32_t K, int64_t l
     e = gemm_tf32x3_tc(X, rows, K, ldx, wsplit, wsplit + nw, n_out, bias, bias_period, Y, ldy, status, s);
   if (e == cudaErrorInvalidValue) return DQ_ERR_ARG;
   return e == cudaSuccess ? DQ_OK : DQ_ERR_CUDA;
+}
+
+// ---- batches of molecules ----
+dq_status dq_create_multi(int32_t n_mol, const dq_system* systems, const dq_ansatz_cfg* cfgs, int32_t precision,
+                          dq_multi* out) {
+  if (!out || !systems || !cfgs) return DQ_ERR_ARG;
+  *out = nullptr;
+  if (n_mol < 1 || n_mol > DQ_MAX_BATCH || DQ_MAX_BATCH > kMaxGroup) return DQ_ERR_SHAPE;
+  if (precision == DQ_FP64) return DQ_ERR_UNSUPPORTED;
+  if (precision != DQ_FP32 && precision != DQ_BF16_MIXED) return DQ_ERR_ARG;
+  for (int m = 0; m < n_mol; ++m)
+    if (cfgs[m].n_layers != cfgs[0].n_layers || cfgs[m].width % 32) return DQ_ERR_SHAPE;
+  dq_multi_s* g = new (std::nothrow) dq_multi_s();
+  if (!g) return DQ_ERR_ARG;
+  if (cudaGetDevice(&g->device) != cudaSuccess) {
+    delete g;
+    return DQ_ERR_CUDA;
+  }
+  g->precision = precision;
+  for (int m = 0; m < n_mol; ++m) {
+    dq_handle h = nullptr;
+    const dq_status st = dq_create(&systems[m], &cfgs[m], precision, &h);
+    if (st != DQ_OK) {
+      dq_destroy_multi(g);
+      return st;
+    }
+    g->h[g->n++] = h;
+  }
+  *out = g;
+  return DQ_OK;
+}
+
+dq_status dq_destroy_multi(dq_multi g) {
+  if (!g) return DQ_ERR_ARG;
+  dq_status st = DQ_OK;
+  for (int m = 0; m < g->n; ++m)
+    if (dq_destroy(g->h[m]) != DQ_OK) st = DQ_ERR_CUDA;
+  delete g;
+  return st;
+}
+
+dq_status dq_multi_handle(dq_multi g, int32_t k, dq_handle* h) {
+  if (!g || !h || k < 0 || k >= g->n) return DQ_ERR_ARG;
+  *h = g->h[k];
+  return DQ_OK;
+}
+
+dq_status dq_multi_set_rounds(dq_multi g, int32_t rounds) {
+  if (!g || rounds < 0) return DQ_ERR_ARG;
+  g->rounds = rounds;
+  return DQ_OK;
+}
+
+dq_status dq_multi_rounds(dq_multi g, int32_t* rounds) {
+  if (!g || !rounds) return DQ_ERR_ARG;
+  *rounds = g->rounds;
+  return DQ_OK;
+}
+
+dq_status dq_multi_workspace_size(dq_multi g, const int64_t* B, int32_t op, size_t* bytes) {
+  if (!g || !B || !bytes) return DQ_ERR_ARG;
+  for (int m = 0; m < g->n; ++m)
+    if (B[m] < 0) return DQ_ERR_ARG;
+  const size_t el = 4;
+  switch (op) {
+    case DQ_OP_EVAL: *bytes = plan_forward_multi(*g, B, false, el).total; return DQ_OK;
+    case DQ_OP_LOCAL_ENERGY: *bytes = plan_forward_multi(*g, B, true, el).total; return DQ_OK;
+    case DQ_OP_MCMC: *bytes = plan_mcmc_multi(*g, B, el).total; return DQ_OK;
+    case DQ_OP_GRAD: *bytes = plan_grad_multi(*g, B, el).total; return DQ_OK;
+    case DQ_OP_LOSS_WEIGHTS: *bytes = loss_scratch_multi(*g, B, nullptr); return DQ_OK;
+  }
+  return DQ_ERR_ARG;
+}
+
+namespace {
+dq_status multi_args(dq_multi g, const int64_t* B, std::initializer_list<const void*> arrays) {
+  dq_status st = check_multi(g);
+  if (st != DQ_OK) return st;
+  if (!B) return DQ_ERR_ARG;
+  for (const void* a : arrays)
+    if (!a) return DQ_ERR_ARG;
+  for (int m = 0; m < g->n; ++m)
+    if (B[m] < 0) return DQ_ERR_ARG;
+  return DQ_OK;
+}
+// every molecule with walkers has its pointer in the host array arr
+bool entries_set(const void* arr, const int64_t* B, int n) {
+  const void* const* a = static_cast<const void* const*>(arr);
+  for (int m = 0; m < n; ++m)
+    if (B[m] > 0 && !a[m]) return false;
+  return true;
+}
+}  // namespace
+
+dq_status ansatz_eval_multi(dq_multi g, const void* const* params, const void* const* r, const int64_t* B,
+                            void* const* logabs, int8_t* const* sign, void* ws, size_t ws_bytes, void* stream) {
+  dq_status st = multi_args(g, B, {params, r, logabs, sign});
+  if (st != DQ_OK) return st;
+  if (!entries_set(params, B, g->n) || !entries_set(r, B, g->n) || !entries_set(logabs, B, g->n) ||
+      !entries_set(sign, B, g->n))
+    return DQ_ERR_ARG;
+  return run_forward_multi<float>(*g, reinterpret_cast<const float* const*>(params),
+                                  reinterpret_cast<const float* const*>(r), B, false,
+                                  reinterpret_cast<float* const*>(logabs), sign, nullptr,
+                                  static_cast<unsigned char*>(ws), ws_bytes, (cudaStream_t)stream);
+}
+
+dq_status local_energy_multi(dq_multi g, const void* const* params, const void* const* r, const int64_t* B,
+                             void* const* logabs, int8_t* const* sign, void* const* e_loc, double* const* e_sum2,
+                             void* ws, size_t ws_bytes, void* stream) {
+  dq_status st = multi_args(g, B, {params, r, logabs, sign, e_loc});
+  if (st != DQ_OK) return st;
+  if (!entries_set(params, B, g->n) || !entries_set(r, B, g->n) || !entries_set(logabs, B, g->n) ||
+      !entries_set(sign, B, g->n) || !entries_set(e_loc, B, g->n))
+    return DQ_ERR_ARG;
+  const cudaStream_t s = (cudaStream_t)stream;
+  st = run_forward_multi<float>(*g, reinterpret_cast<const float* const*>(params),
+                                reinterpret_cast<const float* const*>(r), B, true,
+                                reinterpret_cast<float* const*>(logabs), sign, reinterpret_cast<float* const*>(e_loc),
+                                static_cast<unsigned char*>(ws), ws_bytes, s);
+  if (st != DQ_OK || !e_sum2) return st;
+  double* out2[kMaxGroup];
+  unsigned int* status[kMaxGroup];
+  for (int m = 0; m < g->n; ++m) {
+    out2[m] = e_sum2[m];
+    status[m] = g->h[m]->d_status;
+    if (out2[m] && B[m] == 0) DQ_CU(cudaMemsetAsync(out2[m], 0, 2 * sizeof(double), s));
+    if (B[m] == 0) out2[m] = nullptr;
+  }
+  DQ_LAUNCH(*g->h[0], PK_ESUM, launch_esum_group<float>(g->n, reinterpret_cast<const float* const*>(e_loc), B, out2,
+                                                        status, s));
+  return DQ_OK;
+}
+
+dq_status mcmc_step_multi(dq_multi g, const void* const* params, void* const* r, void* const* logabs,
+                          const int64_t* B, int32_t n_steps, double step_size, uint64_t seed, uint64_t step_counter,
+                          uint64_t* step_counter_dev, int64_t* const* n_accepted, void* ws, size_t ws_bytes,
+                          void* stream) {
+  dq_status st = multi_args(g, B, {params, r, logabs});
+  if (st != DQ_OK) return st;
+  if (n_steps < 0 || !(step_size >= 0) || !isfinite(step_size)) return DQ_ERR_ARG;
+  if (!entries_set(params, B, g->n) || !entries_set(r, B, g->n) || !entries_set(logabs, B, g->n)) return DQ_ERR_ARG;
+  const cudaStream_t s = (cudaStream_t)stream;
+  if (n_steps == 0) {
+    for (int m = 0; m < g->n; ++m)
+      if (n_accepted && n_accepted[m]) DQ_CU(cudaMemsetAsync(n_accepted[m], 0, sizeof(int64_t), s));
+    return DQ_OK;
+  }
+  return run_mcmc_multi<float>(*g, reinterpret_cast<const float* const*>(params), reinterpret_cast<float* const*>(r),
+                               reinterpret_cast<float* const*>(logabs), B, n_steps, step_size, seed,
+                               step_counter_dev ? 0 : step_counter, step_counter_dev, n_accepted,
+                               static_cast<unsigned char*>(ws), ws_bytes, s);
+}
+
+dq_status grad_logpsi_multi(dq_multi g, const void* const* params, const void* const* r, const int64_t* B,
+                            const void* const* weights, void* const* grad_out, void* ws, size_t ws_bytes,
+                            void* stream) {
+  dq_status st = multi_args(g, B, {params, r, weights, grad_out});
+  if (st != DQ_OK) return st;
+  const MultiGradPlan plan = plan_grad_multi(*g, B, 4);
+  if (!ws || ws_bytes < plan.total || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
+  auto* w = static_cast<unsigned char*>(ws);
+  for (int m = 0; m < g->n; ++m) {
+    st = grad_logpsi(g->h[m], params[m], r[m], B[m], weights[m], 0, grad_out[m], w + plan.off[m], plan.bytes[m],
+                     stream);
+    if (st != DQ_OK) return st;
+  }
+  return DQ_OK;
+}
+
+dq_status vmc_loss_weights_multi(dq_multi g, const void* const* e_loc, const int64_t* B, double clip_k,
+                                 void* const* weights, double* const* stats, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  dq_status st = multi_args(g, B, {e_loc, weights});
+  if (st != DQ_OK) return st;
+  if (!(clip_k > 0)) return DQ_ERR_ARG;
+  for (int m = 0; m < g->n; ++m)
+    if (B[m] < 1 || B[m] > 65536 || !e_loc[m] || !weights[m]) return DQ_ERR_ARG;
+  size_t off[kMaxGroup];
+  const size_t need = loss_scratch_multi(*g, B, off);
+  if (!ws || ws_bytes < need || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
+  double* scratch[kMaxGroup];
+  for (int m = 0; m < g->n; ++m) scratch[m] = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + off[m]);
+  const cudaStream_t s = (cudaStream_t)stream;
+  DQ_LAUNCH(*g->h[0], PK_LOSS_WEIGHTS,
+            launch_loss_weights_group<float>(g->n, reinterpret_cast<const float* const*>(e_loc), B, clip_k,
+                                             reinterpret_cast<float* const*>(weights), stats, scratch, s));
+  return DQ_OK;
 }
 
 }  // extern "C"

@@ -160,6 +160,15 @@ struct dq_handle_s {
   dq::Profiler* prof = nullptr;
 };
 
+// A batch of molecules: one handle per molecule (owned), launched together.
+struct dq_multi_s {
+  int n = 0;
+  int device = 0;
+  int precision = 0;
+  int rounds = 0;  // walker chunks per call; 0: automatic
+  dq_handle_s* h[dq::kMaxGroup] = {};
+};
+
 namespace dq {
 
 // Row map of a row-major matrix stored in segments:
