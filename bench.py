@@ -45,6 +45,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay of the step")
     p.add_argument("--no-mala", action="store_true", help="skip the step with the Langevin sampler")
+    p.add_argument("--no-batch", action="store_true", help="skip the uneven-molecule batch")
     p.add_argument("--mala-tau", type=float, default=0.1, help="Langevin time step (bohr^2)")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--profile-case", type=int, default=0, metavar="B",
@@ -274,6 +275,99 @@ def profile_case(args):
     torch.cuda.synchronize()
     print("profile case done:", args.profile_op, args.profile_case, "walkers", float(out.double().abs().sum()))
     return 0
+
+
+def batch_leg(args, dev, flush):
+    """The uneven-molecule batch (H2O, NH3, C2H4, C6H6; 8192/8192/4096/2048 walkers): local
+    energies of all molecules in one grouped call per step, after the autotuner picked its
+    tile shapes, against the same molecules run one after another through single-molecule
+    handles (plain FP32 path); then the batch's whole VMC step as one CUDA graph."""
+    import torch
+
+    from paper_2307_14123_gb300 import Ansatz, AnsatzBatch
+    from paper_2307_14123_gb300 import fixtures as fx
+
+    def timed(fn, steps):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / steps
+
+    out = {}
+    steps = max(3, min(args.steps, 10))
+    for prec in ("fp32", "bf16"):
+        wls = fx.batch_workload("mixed_" + prec)
+        batch = AnsatzBatch([w.system for w in wls], [w.cfg for w in wls], prec, device=dev)
+        th = [torch.tensor(fx.init_params(w.system, w.cfg, w.param_seed), dtype=torch.float32, device=dev)
+              for w in wls]
+        r = [torch.tensor(fx.init_walkers(w.system, w.B, w.walker_seed), dtype=torch.float32, device=dev)
+             for w in wls]
+        walkers = sum(w.B for w in wls)
+        tune_ms, rounds, ib = batch.autotune(th, r)
+        res = {}
+        ms_b = timed(lambda: res.__setitem__("el", batch.local_energy(th, r)[2]), steps)
+        entry = {"value": walkers / (ms_b / 1e3), "unit": UNIT, "ms_per_call": ms_b, "walkers": walkers,
+                 "tuning": {"rounds": rounds, "msg_ib": ib, "autotune_ms": tune_ms}}
+        if prec == "fp32":
+            singles = [Ansatz(w.system, w.cfg, "fp32", device=dev) for w in wls]
+            ms_p = timed(lambda: [h.local_energy(th[k], r[k]) for k, h in enumerate(singles)], steps)
+            entry["plain_fp32_one_by_one"] = {"value": walkers / (ms_p / 1e3), "ms_per_call": ms_p}
+            entry["speedup_vs_plain"] = ms_p / ms_b
+            el32 = [e.double() for e in res["el"]]
+            out["fp32"] = entry
+            del singles
+            # the batch's VMC step (Metropolis sweep, local energies, loss weights, gradients) as one graph
+            la, _ = batch.ansatz_eval(th, r)
+            ctr = torch.zeros(1, dtype=torch.int64, device=dev)
+
+            def vstep():
+                batch.mcmc_step(th, r, la, 1, 0.2, 4, ctr)
+                _, _, el = batch.local_energy(th, r)
+                w, _ = batch.vmc_loss_weights(el, 5.0)
+                return batch.grad_logpsi(th, r, w)
+
+            side = torch.cuda.Stream(device=dev)
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                vstep()
+            torch.cuda.current_stream().wait_stream(side)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                vstep()
+            ms_g = timed(g.replay, steps)
+            entry["vmc_step_graph"] = {"value": walkers / (ms_g / 1e3), "unit": UNIT, "ms_per_step": ms_g,
+                                       "step": "mcmc_step_multi + local_energy_multi + vmc_loss_weights_multi + "
+                                               "grad_logpsi_multi, captured once, replayed"}
+            del g
+        else:
+            # BF16 embedding GEMMs against the FP32 batch on the same walkers: change of each
+            # molecule's mean local energy with the standard error of the per-walker differences
+            el16 = [e.double() for e in res["el"]]
+            dev_e = []
+            for k, w in enumerate(wls):
+                d = el16[k] - el32[k]
+                fin = torch.isfinite(d)
+                d = d[fin]
+                dev_e.append({"molecule": w.system.name, "mean_dE": float(d.mean()),
+                              "stderr": float(d.std() / max(1, d.numel()) ** 0.5)})
+            entry["mean_energy_change_vs_fp32"] = dev_e
+            entry["speedup_vs_fp32_batch"] = out["fp32"]["ms_per_call"] / ms_b
+            entry["speedup_vs_plain_fp32"] = out["fp32"]["plain_fp32_one_by_one"]["ms_per_call"] / ms_b
+            out["bf16"] = entry
+        del batch
+        torch.cuda.empty_cache()
+    out["workload"] = ("H2O 10e / NH3 10e / C2H4 16e / C6H6 42e, D=128, L=3, K=8, "
+                       "8192/8192/4096/2048 walkers, local energies of all molecules per call")
+    return out
 
 
 def main():
@@ -507,6 +601,8 @@ def main():
                     "note": "same workload, Langevin sampler (Sec. 5) instead of random-walk Metropolis; "
                             "L2 flushed before every step"}
 
+    batched = batch_leg(args, dev, flush) if (world == 1 and not args.no_batch) else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, dtc, cores = oracle_sample(wl, args.cpu_seconds)
@@ -527,6 +623,7 @@ def main():
                 "roofline": roof, "roofline_main_kernels": others, "cpu_baseline": cpu, "e2e": e2e,
                 "cuda_graph": graph,
                 "langevin_sampler": langevin,
+                "batched_molecules": batched,
                 "gpu_launches": launches,
                 "clocks": clk,
                 "local_energy_only": {"value": B * world * args.steps / (jet_ms / 1e3) if jet_ms else None,

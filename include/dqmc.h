@@ -89,7 +89,8 @@ typedef enum {
   DQ_OP_MCMC = 2,
   DQ_OP_GRAD = 3,
   DQ_OP_LOSS_WEIGHTS = 4,
-  DQ_OP_MALA = 5
+  DQ_OP_MALA = 5,
+  DQ_OP_AUTOTUNE = 6 /* dq_autotune_multi (batches only) */
 } dq_op;
 
 /* Device status flags (dq_last_device_status). */
@@ -345,6 +346,23 @@ dq_status grad_logpsi_multi(dq_multi m, const void* const* params, const void* c
 dq_status vmc_loss_weights_multi(dq_multi m, const void* const* e_loc, const int64_t* B, double clip_k,
                                  void* const* weights, double* const* stats, void* ws, size_t ws_bytes,
                                  void* stream);
+
+/* Autotuner of a batch's tile shapes (no counterpart in the paper; the
+ * batching it serves is the paper's many-molecule use of one program): times
+ * local_energy_multi on the given walkers for every candidate of
+ *   rounds   1, 2, 3, 4   (walkers per launch: the M extent of every GEMM and
+ *                          the grid of every other kernel), and
+ *   msg_ib   8, 4         (receivers per warp task of the jet message kernel:
+ *                          its register tile of msg_ib x 4 channels),
+ * one warm-up and two timed calls each (CUDA events on `stream`, host waits),
+ * and keeps the fastest in the batch (later calls use it; dq_multi_tuning
+ * reports it).  Candidates whose workspace exceeds ws_bytes are skipped.
+ * Workspace: dq_multi_workspace_size(op = DQ_OP_AUTOTUNE) covers all
+ * candidates and the timing outputs.  Synchronises; not for use inside a
+ * stream capture.  best_ms: nullable host double, the winner's time. */
+dq_status dq_autotune_multi(dq_multi m, const void* const* params, const void* const* r, const int64_t* B, void* ws,
+                            size_t ws_bytes, void* stream, double* best_ms);
+dq_status dq_multi_tuning(dq_multi m, int32_t* rounds, int32_t* msg_ib);
 
 /* Human-readable name of a status code (static string). */
 const char* dq_status_string(dq_status s);

@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdqmc.so")
 
 DQ_FP64, DQ_FP32, DQ_BF16_MIXED = 0, 1, 2
-OP_EVAL, OP_LOCAL_ENERGY, OP_MCMC, OP_GRAD, OP_LOSS_WEIGHTS, OP_MALA = 0, 1, 2, 3, 4, 5
+OP_EVAL, OP_LOCAL_ENERGY, OP_MCMC, OP_GRAD, OP_LOSS_WEIGHTS, OP_MALA, OP_AUTOTUNE = 0, 1, 2, 3, 4, 5, 6
 FLAG_SINGULAR, FLAG_NONFINITE = 0x1, 0x2
 PRECISIONS = {"fp64": DQ_FP64, "fp32": DQ_FP32, "bf16": DQ_BF16_MIXED}
 
@@ -35,7 +35,7 @@ EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_
            "dq_test_gemm_tf32x3", "mcmc_step_dev", "mala_step", "dq_create_multi", "dq_destroy_multi",
            "dq_multi_handle", "dq_multi_set_rounds", "dq_multi_rounds", "dq_multi_workspace_size",
            "ansatz_eval_multi", "local_energy_multi", "mcmc_step_multi", "grad_logpsi_multi",
-           "vmc_loss_weights_multi"]
+           "vmc_loss_weights_multi", "dq_autotune_multi", "dq_multi_tuning"]
 
 
 class DQError(RuntimeError):
@@ -104,6 +104,8 @@ def load_library(path=None):
         lib.mcmc_step_multi.argtypes = [P, P, P, P, P, i32, f64, u64, u64, P, P, P, sz, P]
         lib.grad_logpsi_multi.argtypes = [P, P, P, P, P, P, P, sz, P]
         lib.vmc_loss_weights_multi.argtypes = [P, P, P, f64, P, P, P, sz, P]
+        lib.dq_autotune_multi.argtypes = [P, P, P, P, P, sz, P, P]
+        lib.dq_multi_tuning.argtypes = [P, P, P]
         for name in EXPORTS:
             getattr(lib, name).restype = ctypes.c_int
         lib.dq_status_string.restype = ctypes.c_char_p
@@ -428,6 +430,22 @@ class AnsatzBatch:
             self._ws = None
             self._ws = torch.empty(size, dtype=torch.uint8, device=self.device)
         return self._ws
+
+    def autotune(self, params, r):
+        """Times local_energy on these walkers for every candidate tile shape (walkers per
+        launch, message-kernel register tile), keeps the fastest; returns (ms, rounds, msg_ib)."""
+        self._check_in(list(params) + list(r), "autotune")
+        B = self._B(r)
+        ws = self.workspace(B, OP_AUTOTUNE)
+        best = ctypes.c_double()
+        _check(self.lib.dq_autotune_multi(self.h, _ptrs(params), _ptrs(r), B, _ptr(ws), ws.numel(), self._stream(),
+                                          ctypes.byref(best)))
+        return (best.value,) + self.tuning()
+
+    def tuning(self):
+        rounds, ib = ctypes.c_int32(), ctypes.c_int32()
+        _check(self.lib.dq_multi_tuning(self.h, ctypes.byref(rounds), ctypes.byref(ib)))
+        return rounds.value, ib.value
 
     def ansatz_eval(self, params, r):
         self._check_in(list(params) + list(r), "ansatz_eval")

@@ -1060,6 +1060,17 @@ size_t loss_scratch_multi(const dq_multi_s& g, const int64_t* B, size_t* off) {
   return o;
 }
 
+// Autotuner workspace: the largest candidate's forward (one round), then the
+// timing outputs (log|psi|, E_loc, sign of every molecule).
+size_t autotune_bytes(dq_multi_s& g, const int64_t* B) {
+  const int keep = g.rounds;
+  g.rounds = 1;
+  size_t o = plan_forward_multi(g, B, true, 4).total;
+  g.rounds = keep;
+  for (int m = 0; m < g.n; ++m) o += 2 * align_up((size_t)std::max<int64_t>(B[m], 1) * 4) + align_up((size_t)std::max<int64_t>(B[m], 1));
+  return o;
+}
+
 dq_status check_multi(dq_multi g) {
   if (g == nullptr) return DQ_ERR_ARG;
   int dev = -1;
@@ -1529,6 +1540,7 @@ dq_status dq_multi_workspace_size(dq_multi g, const int64_t* B, int32_t op, size
     case DQ_OP_MCMC: *bytes = plan_mcmc_multi(*g, B, el).total; return DQ_OK;
     case DQ_OP_GRAD: *bytes = plan_grad_multi(*g, B, el).total; return DQ_OK;
     case DQ_OP_LOSS_WEIGHTS: *bytes = loss_scratch_multi(*g, B, nullptr); return DQ_OK;
+    case DQ_OP_AUTOTUNE: *bytes = autotune_bytes(*g, B); return DQ_OK;
   }
   return DQ_ERR_ARG;
 }
@@ -1646,6 +1658,82 @@ dq_status vmc_loss_weights_multi(dq_multi g, const void* const* e_loc, const int
   DQ_LAUNCH(*g->h[0], PK_LOSS_WEIGHTS,
             launch_loss_weights_group<float>(g->n, reinterpret_cast<const float* const*>(e_loc), B, clip_k,
                                              reinterpret_cast<float* const*>(weights), stats, scratch, s));
+  return DQ_OK;
+}
+
+dq_status dq_autotune_multi(dq_multi g, const void* const* params, const void* const* r, const int64_t* B, void* ws,
+                            size_t ws_bytes, void* stream, double* best_ms) {
+  dq_status st = multi_args(g, B, {params, r});
+  if (st != DQ_OK) return st;
+  if (!entries_set(params, B, g->n) || !entries_set(r, B, g->n)) return DQ_ERR_ARG;
+  const size_t need = autotune_bytes(*g, B);
+  if (!ws || ws_bytes < need || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
+  const cudaStream_t s = (cudaStream_t)stream;
+  auto* w = static_cast<unsigned char*>(ws);
+  // timing outputs at the end of the workspace
+  size_t o = need;
+  float *la[kMaxGroup], *el[kMaxGroup];
+  int8_t* sg[kMaxGroup];
+  for (int m = g->n - 1; m >= 0; --m) {
+    const size_t b = (size_t)std::max<int64_t>(B[m], 1);
+    o -= align_up(b);
+    sg[m] = reinterpret_cast<int8_t*>(w + o);
+    o -= align_up(b * 4);
+    el[m] = reinterpret_cast<float*>(w + o);
+    o -= align_up(b * 4);
+    la[m] = reinterpret_cast<float*>(w + o);
+  }
+  const size_t fwd_bytes = o;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return DQ_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return DQ_ERR_CUDA;
+  }
+  const int keep_rounds = g->rounds;
+  const int keep_ib = g->h[0]->msg_ib;
+  double best = -1;
+  int best_rounds = keep_rounds, best_ib = keep_ib;
+  st = DQ_OK;
+  for (int rounds = 1; rounds <= 4 && st == DQ_OK; ++rounds) {
+    g->rounds = rounds;
+    if (plan_forward_multi(*g, B, true, 4).total > fwd_bytes) continue;
+    for (int ib : {8, 4}) {
+      for (int m = 0; m < g->n; ++m) g->h[m]->msg_ib = ib;
+      float ms = 0;
+      for (int rep = 0; rep < 3 && st == DQ_OK; ++rep) {
+        if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) st = DQ_ERR_CUDA;
+        if (st == DQ_OK)
+          st = run_forward_multi<float>(*g, reinterpret_cast<const float* const*>(params),
+                                        reinterpret_cast<const float* const*>(r), B, true, la, sg, el, w, fwd_bytes,
+                                        s);
+      }
+      if (st != DQ_OK) break;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        st = DQ_ERR_CUDA;
+        break;
+      }
+      const double t = ms / 2.0;
+      if (best < 0 || t < best) {
+        best = t;
+        best_rounds = rounds;
+        best_ib = ib;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g->rounds = st == DQ_OK ? best_rounds : keep_rounds;
+  for (int m = 0; m < g->n; ++m) g->h[m]->msg_ib = st == DQ_OK ? best_ib : keep_ib;
+  if (best_ms) *best_ms = best;
+  return st;
+}
+
+dq_status dq_multi_tuning(dq_multi g, int32_t* rounds, int32_t* msg_ib) {
+  if (!g || !rounds || !msg_ib) return DQ_ERR_ARG;
+  *rounds = g->rounds;
+  *msg_ib = g->h[0]->msg_ib == 0 ? 8 : g->h[0]->msg_ib;
   return DQ_OK;
 }
 

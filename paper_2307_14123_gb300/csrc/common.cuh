@@ -149,6 +149,7 @@ struct dq_handle_s {
   dq::ParamOffsets off{};
   dq::Edges edges{};
   int64_t max_chunk = 4096;
+  int msg_ib = 0;  // receivers per warp task of the jet message kernel (FP32 modes: 8 or 4; 0: 8)
   // device tables
   double* d_R = nullptr;   // [M][3]
   float* d_Rf = nullptr;   // [M][3]

@@ -1853,7 +1853,7 @@ cudaError_t launch_layer0_node_group(const MolFwd<T>* m, int n, cudaStream_t s) 
 }
 
 namespace {
-template <class T, class TO>
+template <class T, class TO, int IB>
 cudaError_t launch_messages_group_t(const MolFwd<T>* m, int n, int l, bool z_const, bool bf_out, cudaStream_t s) {
   auto out_of = [&](const MolFwd<T>& q) -> TO* {
     if constexpr (sizeof(TO) == 2) return static_cast<TO*>(q.b.msg_bf);
@@ -1883,9 +1883,14 @@ cudaError_t launch_messages_group_t(const MolFwd<T>* m, int n, int l, bool z_con
     messages_value_kernel_group<T, TO><<<(unsigned)g.blocks(), threads, smem, s>>>(g);
     return cudaGetLastError();
   }
-  constexpr int IB = msg_ib<T>(), CB = sizeof(T) == 4 ? 4 : 2;
-  Grp<messages_kernel_args<T, TO>> g{};
-  int smem = 0;
+  constexpr int CB = sizeof(T) == 4 ? 4 : 2;
+  struct Ent {
+    messages_kernel_args<T, TO> a;
+    int64_t bx;
+    int ny, L, smem, occ;
+  };
+  Ent ent[kMaxGroup];
+  int ne = 0, smem = 0;
   for (int k = 0; k < n; ++k) {
     const dq_handle_s& h = *m[k].h;
     const FwdDims& d = m[k].d;
@@ -1904,18 +1909,39 @@ cudaError_t launch_messages_group_t(const MolFwd<T>* m, int n, int l, bool z_con
     }
     if (lay.total_bytes > 220 * 1024) return cudaErrorInvalidConfiguration;
     smem = std::max(smem, lay.total_bytes);
-    g.add({m[k].b.Z, m[k].b.z0, m[k].b.ew, m[k].b.geo, m[k].params + h.off.layer[l].Y, h.d_pair_of, d.N, d.n_up, d.M,
-           d.C, d.D, h.edges.n_all, h.edges.n_ee, z_const ? 1 : 0, stage_w1 ? 1 : 0, out_of(m[k])},
-          d.Bc, d.D / L, L);
+    ent[ne++] = Ent{{m[k].b.Z, m[k].b.z0, m[k].b.ew, m[k].b.geo, m[k].params + h.off.layer[l].Y, h.d_pair_of, d.N,
+                     d.n_up, d.M, d.C, d.D, h.edges.n_all, h.edges.n_ee, z_const ? 1 : 0, stage_w1 ? 1 : 0,
+                     out_of(m[k])},
+                    d.Bc, d.D / L, L, lay.total_bytes, 0};
   }
-  if (g.n == 0) return cudaSuccess;
+  if (ne == 0) return cudaSuccess;
   auto kern = messages_kernel_group<T, TO, IB, CB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  e = check_group(g);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)g.blocks(), 32 * kMsgWarps, smem, s>>>(g);
-  return cudaGetLastError();
+  // One launch per occupancy class: molecules whose CTAs fit the same number per SM share a
+  // launch (the launch's shared memory is its largest entry's, which sets everyone's occupancy).
+  for (int i = 0; i < ne; ++i) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ent[i].occ, kern, 32 * kMsgWarps, ent[i].smem);
+    if (e != cudaSuccess) return e;
+  }
+  bool done[kMaxGroup] = {};
+  for (int i = 0; i < ne; ++i) {
+    if (done[i]) continue;
+    Grp<messages_kernel_args<T, TO>> g{};
+    int sm = 0;
+    for (int j = i; j < ne; ++j)
+      if (!done[j] && ent[j].occ == ent[i].occ) {
+        g.add(ent[j].a, ent[j].bx, ent[j].ny, ent[j].L);
+        sm = std::max(sm, ent[j].smem);
+        done[j] = true;
+      }
+    e = check_group(g);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)g.blocks(), 32 * kMsgWarps, sm, s>>>(g);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 }  // namespace
 
@@ -1923,10 +1949,16 @@ template <class T>
 cudaError_t launch_messages_group(const MolFwd<T>* m, int n, int l, bool z_const, cudaStream_t s) {
   if (n > kMaxGroup) return cudaErrorInvalidValue;
   if (n == 0) return cudaSuccess;
+  // receivers per warp task (the register tile IB x CB): the handle's tuned value, else the default
   if constexpr (sizeof(T) == 4) {
-    if (m[0].b.msg_bf) return launch_messages_group_t<T, __nv_bfloat16>(m, n, l, z_const, true, s);
+    const bool ib4 = m[0].h->msg_ib == 4;
+    if (m[0].b.msg_bf)
+      return ib4 ? launch_messages_group_t<T, __nv_bfloat16, 4>(m, n, l, z_const, true, s)
+                 : launch_messages_group_t<T, __nv_bfloat16, 8>(m, n, l, z_const, true, s);
+    return ib4 ? launch_messages_group_t<T, T, 4>(m, n, l, z_const, false, s)
+               : launch_messages_group_t<T, T, 8>(m, n, l, z_const, false, s);
   }
-  return launch_messages_group_t<T, T>(m, n, l, z_const, false, s);
+  return launch_messages_group_t<T, T, msg_ib<T>()>(m, n, l, z_const, false, s);
 }
 
 template <class T>
@@ -1950,7 +1982,14 @@ cudaError_t launch_update_group(const MolFwd<T>* m, int n, bool from_spin, cudaS
 template <class T>
 cudaError_t launch_orbital_det_group(const MolFwd<T>* m, int n, cudaStream_t s) {
   if (n > kMaxGroup) return cudaErrorInvalidValue;
-  Grp<orbital_det_kernel_args<T>> g{};
+  struct Ent {
+    orbital_det_kernel_args<T> a;
+    int64_t bx;
+    int tag, occ;
+    size_t smem;
+  };
+  Ent ent[kMaxGroup];
+  int ne = 0;
   size_t smem = 0;
   for (int k = 0; k < n; ++k) {
     const dq_handle_s& h = *m[k].h;
@@ -1960,30 +1999,50 @@ cudaError_t launch_orbital_det_group(const MolFwd<T>* m, int n, cudaStream_t s) 
     const int nn = nmax * nmax;
     const int64_t nmat = d.Bc * 2 * d.K;
     const bool jets = sizeof(T) == 4 && d.C > 1 && nmax <= kDetNR;
+    size_t sm = 0;
     if (jets) {
-      smem = std::max(smem, det_jets_smem_per_warp(nmax, 3 * d.N) * 4);
+      sm = det_jets_smem_per_warp(nmax, 3 * d.N) * 4;
     } else {
       const size_t per_warp = ((size_t)nn * (3 * sizeof(double) + 10 * sizeof(T)) + 32 * sizeof(int) + 15) / 16 * 16;
       if (per_warp * 4 > 200 * 1024) return cudaErrorInvalidConfiguration;  // grouped form: four warps per CTA
-      smem = std::max(smem, per_warp * 4);
+      sm = per_warp * 4;
     }
-    g.add({m[k].b.phi, m[k].b.geo, m[k].params, d.Bc, d.N, d.n_up, d.M, d.K, d.C, d.K * nmax, h.edges.n_all,
-           h.edges.n_ee, h.off.omega[0], h.off.omega[1], h.off.zeta[0], h.off.zeta[1], m[k].b.det, h.d_fp64_count},
-          blocks(nmat, 4), 1, jets ? 1 : 0);
+    smem = std::max(smem, sm);
+    ent[ne++] = Ent{{m[k].b.phi, m[k].b.geo, m[k].params, d.Bc, d.N, d.n_up, d.M, d.K, d.C, d.K * nmax,
+                     h.edges.n_all, h.edges.n_ee, h.off.omega[0], h.off.omega[1], h.off.zeta[0], h.off.zeta[1],
+                     m[k].b.det, h.d_fp64_count},
+                    blocks(nmat, 4), jets ? 1 : 0, 0, sm};
   }
-  if (g.n == 0) return cudaSuccess;
-  cudaError_t e = check_group(g);
+  if (ne == 0) return cudaSuccess;
+  const void* kern = nullptr;
+  if constexpr (sizeof(T) == 4) kern = (const void*)orbital_det_mixed_group;
+  else kern = (const void*)orbital_det_kernel_group<T>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if constexpr (sizeof(T) == 4) {
-    e = cudaFuncSetAttribute(orbital_det_mixed_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // one launch per occupancy class (see launch_messages_group)
+  for (int i = 0; i < ne; ++i) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ent[i].occ, kern, 128, ent[i].smem);
     if (e != cudaSuccess) return e;
-    orbital_det_mixed_group<<<(unsigned)g.blocks(), 128, smem, s>>>(g);
-  } else {
-    e = cudaFuncSetAttribute(orbital_det_kernel_group<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    orbital_det_kernel_group<T><<<(unsigned)g.blocks(), 128, smem, s>>>(g);
   }
-  return cudaGetLastError();
+  bool done[kMaxGroup] = {};
+  for (int i = 0; i < ne; ++i) {
+    if (done[i]) continue;
+    Grp<orbital_det_kernel_args<T>> g{};
+    size_t sm = 0;
+    for (int j = i; j < ne; ++j)
+      if (!done[j] && ent[j].occ == ent[i].occ) {
+        g.add(ent[j].a, ent[j].bx, 1, ent[j].tag);
+        sm = std::max(sm, ent[j].smem);
+        done[j] = true;
+      }
+    e = check_group(g);
+    if (e != cudaSuccess) return e;
+    if constexpr (sizeof(T) == 4) orbital_det_mixed_group<<<(unsigned)g.blocks(), 128, sm, s>>>(g);
+    else orbital_det_kernel_group<T><<<(unsigned)g.blocks(), 128, sm, s>>>(g);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <class T>

@@ -54,6 +54,20 @@ def test_batch_local_energy_equals_single(rounds):
         assert torch.isfinite(el[k]).all()
 
 
+def test_batch_autotune_keeps_results():
+    """The autotuner picks a tile shape among its candidates; results stay equal to the
+    single-molecule calls (the message kernel's register tile does not change the order
+    of any sum)."""
+    wls, batch, singles, th, r = _setup()
+    ms, rounds, ib = batch.autotune(th, r)
+    assert ms > 0 and rounds in (1, 2, 3, 4) and ib in (4, 8)
+    assert batch.tuning() == (rounds, ib)
+    la, sg, el = batch.local_energy(th, r)
+    for k, h in enumerate(singles):
+        la1, sg1, el1 = h.local_energy(th[k], r[k])
+        assert torch.equal(la[k], la1) and torch.equal(el[k], el1), (wls[k].name, rounds, ib)
+
+
 def test_batch_eval_and_mcmc_equal_single():
     wls, batch, singles, th, r = _setup()
     la, sg = batch.ansatz_eval(th, r)
