@@ -200,9 +200,9 @@ def peaks():
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of the jet message kernel (layer >= 1 launch) per walker,
-# from the ncu capture summarised in profiles/messages_kernel_n2_512.md (N2, FP32); None once the kernel
-# has changed since that capture.
-MSG_DRAM_BYTES_PER_WALKER = (276.218112e6 + 431.757824e6) / 512
+# from an ncu capture of the layer-1 launch on 512 N2 walkers (FP32; summary under profiles/); None
+# once the kernel has changed since that capture.
+MSG_DRAM_BYTES_PER_WALKER = (263.808768e6 + 431.145728e6) / 512
 
 
 def roofline_for(kind, ms, n, wl, chunk, pk, how):
@@ -235,8 +235,7 @@ def roofline_for(kind, ms, n, wl, chunk, pk, how):
         return {"kernel": kind, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": None, "peak_source": src, "flops_per_launch": flops, "avg_launch_ms": ms / n}
     if kind == "jet.messages" and wl.name == "n2_fp32" and MSG_DRAM_BYTES_PER_WALKER:
-        # DRAM bytes of one launch from an ncu capture (profiles/messages_kernel_n2_512.md), per walker,
-        # scaled to the launch's walkers
+        # DRAM bytes of one launch from the ncu capture above, per walker, scaled to the launch's walkers
         traffic = MSG_DRAM_BYTES_PER_WALKER * chunk
     else:
         traffic = None
