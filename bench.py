@@ -397,6 +397,11 @@ def main():
     r0 = fx.init_walkers(wl.system, B, wl.walker_seed, walker_offset=rank * B)
     r = torch.tensor(r0, dtype=dt, device=dev)
     logabs, _ = h.ansatz_eval(theta, r)
+    # tile shapes (message register tile, walker chunk) timed on these walkers before the timed region
+    tuning = None
+    if wl.precision != "fp64":
+        t_ms, t_chunk, t_ib = h.autotune(theta, r)
+        tuning = {"msg_ib": t_ib, "max_chunk": t_chunk, "local_energy_ms": t_ms}
     step_size = wl.extra.get("step_size", 0.2)
     try:
         h.grad_logpsi(theta, r[:1], torch.ones(1, dtype=dt, device=dev), 0)
@@ -613,7 +618,7 @@ def main():
         step_desc = "mcmc_step(1 sweep) + local_energy + vmc_loss_weights" + (" + grad_logpsi(weighted)" if with_grad
                                                                              else " (grad_logpsi not built)")
         cfg = workload_config(wl, world)
-        cfg.update({"step": step_desc, "l2": "flushed before every timed step (256 MB write)"})
+        cfg.update({"step": step_desc, "l2": "flushed before every timed step (256 MB write)", "tuning": tuning})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,

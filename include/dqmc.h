@@ -347,6 +347,19 @@ dq_status vmc_loss_weights_multi(dq_multi m, const void* const* e_loc, const int
                                  void* const* weights, double* const* stats, void* ws, size_t ws_bytes,
                                  void* stream);
 
+/* Tile shape of one handle (no counterpart in the paper): msg_ib = receivers
+ * per warp task of the jet message kernel (its register tile is msg_ib x 4
+ * channels; 8 or 4, 0 restores the default 8).  Results do not depend on it.
+ * dq_autotune times local_energy on the given walkers for msg_ib 8 and 4 and
+ * walker chunks (dq_set_max_chunk) of 4096 and 2048, one warm-up and two timed
+ * calls each (CUDA events on `stream`, host waits), and keeps the fastest;
+ * workspace as for local_energy with B walkers.  Synchronises; not for use
+ * inside a stream capture.  best_ms: nullable host double. */
+dq_status dq_set_msg_tile(dq_handle h, int32_t msg_ib);
+dq_status dq_msg_tile(dq_handle h, int32_t* msg_ib);
+dq_status dq_autotune(dq_handle h, const void* params, const void* r, int64_t B, void* ws, size_t ws_bytes,
+                      void* stream, double* best_ms);
+
 /* Autotuner of a batch's tile shapes (no counterpart in the paper; the
  * batching it serves is the paper's many-molecule use of one program): times
  * local_energy_multi on the given walkers for every candidate of

@@ -35,7 +35,7 @@ EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_
            "dq_test_gemm_tf32x3", "mcmc_step_dev", "mala_step", "dq_create_multi", "dq_destroy_multi",
            "dq_multi_handle", "dq_multi_set_rounds", "dq_multi_rounds", "dq_multi_workspace_size",
            "ansatz_eval_multi", "local_energy_multi", "mcmc_step_multi", "grad_logpsi_multi",
-           "vmc_loss_weights_multi", "dq_autotune_multi", "dq_multi_tuning"]
+           "vmc_loss_weights_multi", "dq_autotune_multi", "dq_multi_tuning", "dq_set_msg_tile", "dq_msg_tile", "dq_autotune"]
 
 
 class DQError(RuntimeError):
@@ -106,6 +106,9 @@ def load_library(path=None):
         lib.vmc_loss_weights_multi.argtypes = [P, P, P, f64, P, P, P, sz, P]
         lib.dq_autotune_multi.argtypes = [P, P, P, P, P, sz, P, P]
         lib.dq_multi_tuning.argtypes = [P, P, P]
+        lib.dq_set_msg_tile.argtypes = [P, i32]
+        lib.dq_msg_tile.argtypes = [P, P]
+        lib.dq_autotune.argtypes = [P, P, P, i64, P, sz, P, P]
         for name in EXPORTS:
             getattr(lib, name).restype = ctypes.c_int
         lib.dq_status_string.restype = ctypes.c_char_p
@@ -169,6 +172,33 @@ class Ansatz:
     # -- plumbing -----------------------------------------------------------
     def _stream(self):
         return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def set_msg_tile(self, msg_ib):
+        """Receivers per warp task of the jet message kernel (8 or 4; 0: default)."""
+        _check(self.lib.dq_set_msg_tile(self.h, int(msg_ib)))
+
+    def autotune(self, params, r):
+        """Times local_energy on these walkers for the candidate tile shapes (message
+        register tile, walker chunk) and keeps the fastest; returns (ms, chunk, msg_ib)."""
+        params = self._dev(params, shape=(self.P,))
+        r = self._dev(r)
+        B = r.numel() // (3 * self.N)
+        keep = self.max_chunk()
+        self.set_max_chunk(4096)  # the largest candidate
+        n = self.workspace_size(B, OP_LOCAL_ENERGY) + 2 * ((B * 4 + 255) // 256 * 256) + (B + 255) // 256 * 256
+        self.set_max_chunk(keep)
+        ws = self._ws if self._ws is not None and self._ws.numel() >= n else torch.empty(n, dtype=torch.uint8,
+                                                                                       device=self.device)
+        self._ws = ws
+        best = ctypes.c_double()
+        _check(self.lib.dq_autotune(self.h, _ptr(params), _ptr(r), B, _ptr(ws), ws.numel(), self._stream(),
+                                    ctypes.byref(best)))
+        return best.value, self.max_chunk(), self._msg_ib()
+
+    def _msg_ib(self):
+        v = ctypes.c_int32()
+        _check(self.lib.dq_msg_tile(self.h, ctypes.byref(v)))
+        return v.value
 
     def set_max_chunk(self, chunk):
         _check(self.lib.dq_set_max_chunk(self.h, int(chunk)))

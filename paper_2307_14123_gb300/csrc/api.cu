@@ -1661,6 +1661,78 @@ dq_status vmc_loss_weights_multi(dq_multi g, const void* const* e_loc, const int
   return DQ_OK;
 }
 
+dq_status dq_set_msg_tile(dq_handle h, int32_t msg_ib) {
+  if (!h || (msg_ib != 0 && msg_ib != 4 && msg_ib != 8)) return DQ_ERR_ARG;
+  h->msg_ib = msg_ib;
+  return DQ_OK;
+}
+
+dq_status dq_msg_tile(dq_handle h, int32_t* msg_ib) {
+  if (!h || !msg_ib) return DQ_ERR_ARG;
+  *msg_ib = h->msg_ib == 0 ? 8 : h->msg_ib;
+  return DQ_OK;
+}
+
+dq_status dq_autotune(dq_handle h, const void* params, const void* r, int64_t B, void* ws, size_t ws_bytes,
+                      void* stream, double* best_ms) {
+  dq_status st = check_handle(h);
+  if (st != DQ_OK) return st;
+  if (B < 1 || !params || !r || h->precision == DQ_FP64) return h->precision == DQ_FP64 ? DQ_ERR_UNSUPPORTED : DQ_ERR_ARG;
+  if (!ws || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
+  const cudaStream_t s = (cudaStream_t)stream;
+  auto* w = static_cast<unsigned char*>(ws);
+  // timing outputs after the largest candidate's forward workspace
+  const int64_t keep_chunk = h->max_chunk;
+  const int keep_ib = h->msg_ib;
+  h->max_chunk = 4096;
+  const size_t fwd = align_up(plan_forward(*h, std::min<int64_t>(B, 4096), true, 4).total);
+  h->max_chunk = keep_chunk;
+  const size_t b = (size_t)B;
+  if (ws_bytes < fwd + 2 * align_up(b * 4) + align_up(b)) return DQ_ERR_WORKSPACE;
+  float* la = reinterpret_cast<float*>(w + fwd);
+  float* el = reinterpret_cast<float*>(w + fwd + align_up(b * 4));
+  int8_t* sg = reinterpret_cast<int8_t*>(w + fwd + 2 * align_up(b * 4));
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return DQ_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return DQ_ERR_CUDA;
+  }
+  double best = -1;
+  int64_t best_chunk = keep_chunk;
+  int best_ib = keep_ib;
+  for (int64_t chunk : {(int64_t)4096, (int64_t)2048}) {
+    for (int ib : {8, 4}) {
+      h->max_chunk = chunk;
+      h->msg_ib = ib;
+      float ms = 0;
+      for (int rep = 0; rep < 3 && st == DQ_OK; ++rep) {
+        if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) st = DQ_ERR_CUDA;
+        if (st == DQ_OK)
+          st = run_forward<float>(*h, (const float*)params, (const float*)r, B, true, la, sg, el, w, fwd, s);
+      }
+      if (st != DQ_OK) break;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        st = DQ_ERR_CUDA;
+        break;
+      }
+      if (best < 0 || ms / 2.0 < best) {
+        best = ms / 2.0;
+        best_chunk = chunk;
+        best_ib = ib;
+      }
+    }
+    if (st != DQ_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->max_chunk = st == DQ_OK ? best_chunk : keep_chunk;
+  h->msg_ib = st == DQ_OK ? best_ib : keep_ib;
+  if (best_ms) *best_ms = best;
+  return st;
+}
+
 dq_status dq_autotune_multi(dq_multi g, const void* const* params, const void* const* r, const int64_t* B, void* ws,
                             size_t ws_bytes, void* stream, double* best_ms) {
   dq_status st = multi_args(g, B, {params, r});

@@ -312,3 +312,21 @@ def test_host_tensors_end_to_end():
     assert b[0].device.type == "cpu"
     for x, y in zip(a, _np(*b)):
         assert np.array_equal(x, y)
+
+
+def test_msg_tile_and_autotune_keep_results():
+    """The message kernel's register tile (8 or 4 receivers per warp task) and the walker
+    chunk change no result bit; the autotuner keeps one of its candidates."""
+    wl = fx.workload("n2_fp32")
+    h = _handle(wl.system, wl.cfg, "fp32")
+    theta, r, th_t, r_t = _inputs(wl.system, wl.cfg, "fp32", 300, wl.param_seed, wl.walker_seed)
+    h.set_msg_tile(8)
+    ref = h.local_energy(th_t, r_t)
+    h.set_msg_tile(4)
+    got = h.local_energy(th_t, r_t)
+    for a, b in zip(ref, got):
+        assert torch.equal(a, b)
+    ms, chunk, ib = h.autotune(th_t, r_t)
+    assert ms > 0 and chunk in (4096, 2048) and ib in (4, 8)
+    for a, b in zip(ref, h.local_energy(th_t, r_t)):
+        assert torch.equal(a, b)
