@@ -19,6 +19,10 @@ Functions, each following the paper's definitions:
 * :func:`clipped_loss_weights` - median/MAD clipping of Sec. 4.4 and the
   per-walker weights of the gradient estimator, Eq. (30).
 * :func:`energy_estimate` - Eq. (33) and the batch-means error bar, Eq. (35).
+* :func:`natural_gradient` - the natural-gradient direction of the optimiser
+  section (Sec. 4, "Optimizer"): the loss gradient preconditioned by the damped
+  Fisher information of |psi|^2, estimated from walker-centred per-walker
+  gradients of log|psi|; dense FP64 solve.
 
 Parity status: all functions are pinned by the ``-m "not gpu"`` tests
 (closed forms, invariants, finite differences and brute force).
@@ -249,3 +253,25 @@ def energy_estimate(e_loc_steps):
     batch = e.mean(axis=1)
     err = np.sqrt(np.sum((batch - mean) ** 2) / (nb * (nb - 1)))
     return mean, err
+
+
+def natural_gradient(G, w, lam, form="sample"):
+    """Natural-gradient direction delta = (F + lam I)^-1 g (Sec. 4, "Optimizer"):
+    F = Gc^T Gc / B, the Fisher information of the density |psi|^2 up to the
+    constant factor 4 (which lam absorbs), estimated from the per-walker gradients
+    G[b] = d log|psi_b| / d theta centred over the walkers (Gc = G - mean_b G), and
+    g = G^T w the loss gradient of Eq. (30) for the walker weights w (sum_b w_b = 0
+    for the clipped-energy weights, so G^T w = Gc^T w).
+
+    form "sample": Gc^T (Gc Gc^T / B + lam I)^-1 w, a B x B solve; form "parameter":
+    (Gc^T Gc / B + lam I)^-1 Gc^T w, a P x P solve (small P only).  The two are equal
+    by the push-through identity (A^T A + c I)^-1 A^T = A^T (A A^T + c I)^-1."""
+    G = np.asarray(G, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    B, P = G.shape
+    Gc = G - G.mean(axis=0, keepdims=True)
+    if form == "sample":
+        x = np.linalg.solve(Gc @ Gc.T / B + lam * np.eye(B), w)
+        return Gc.T @ x
+    return np.linalg.solve(Gc.T @ Gc / B + lam * np.eye(P), Gc.T @ w)
+

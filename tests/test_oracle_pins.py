@@ -659,3 +659,38 @@ def test_mala_stationarity_hydrogen():
     assert 0.5 < acc_tot / (B * 300) < 1.0
     assert abs(mean - 1.5) < 5 * err, (mean, err)
     assert np.all(np.abs(o.local_energy(th, r)["e_loc"] + 0.5) < 1e-11)
+
+
+# ----------------------------------------------------------------------------
+# Natural-gradient direction (Sec. 4, "Optimizer")
+# ----------------------------------------------------------------------------
+def _natgrad_inputs(B, P, seed):
+    rng = np.random.default_rng(seed)
+    G = rng.standard_normal((B, P)) * rng.uniform(0.1, 3.0, P) + rng.standard_normal(P)
+    e = rng.standard_normal(B)
+    w = (2.0 / B) * (e - e.mean())
+    return G, w
+
+
+@pytest.mark.parametrize("B,P", [(40, 13), (12, 30)])
+def test_natural_gradient_push_through(B, P):
+    """Sample-space (B x B) and parameter-space (P x P) forms agree."""
+    G, w = _natgrad_inputs(B, P, 1)
+    a = oracle.natural_gradient(G, w, 0.3, "sample")
+    b = oracle.natural_gradient(G, w, 0.3, "parameter")
+    np.testing.assert_allclose(a, b, rtol=1e-10, atol=1e-12)
+
+
+def test_natural_gradient_limits():
+    """Large damping: delta -> g / lam; centring: a constant added to every walker's
+    gradient changes nothing; small damping with B > P: F delta = g."""
+    G, w = _natgrad_inputs(50, 7, 2)
+    g = G.T @ w
+    lam = 1e9  # the deviation from g / lam is of relative order ||F|| / lam (||F|| ~ 10 here)
+    np.testing.assert_allclose(oracle.natural_gradient(G, w, lam) * lam, g, rtol=1e-6, atol=1e-12)
+    shift = np.random.default_rng(3).standard_normal(7) * 10
+    np.testing.assert_allclose(oracle.natural_gradient(G + shift, w, 0.1), oracle.natural_gradient(G, w, 0.1),
+                               rtol=1e-9, atol=1e-12)
+    Gc = G - G.mean(axis=0)
+    d = oracle.natural_gradient(G, w, 1e-10)
+    np.testing.assert_allclose(Gc.T @ Gc / 50 @ d, g, rtol=1e-6, atol=1e-10)
