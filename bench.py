@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--no-graph", action="store_true", help="skip the CUDA-graph replay of the step")
     p.add_argument("--no-mala", action="store_true", help="skip the step with the Langevin sampler")
     p.add_argument("--no-batch", action="store_true", help="skip the uneven-molecule batch")
+    p.add_argument("--no-natgrad", action="store_true", help="skip the natural-gradient direction")
     p.add_argument("--mala-tau", type=float, default=0.1, help="Langevin time step (bohr^2)")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--profile-case", type=int, default=0, metavar="B",
@@ -274,6 +275,44 @@ def profile_case(args):
     torch.cuda.synchronize()
     print("profile case done:", args.profile_op, args.profile_case, "walkers", float(out.double().abs().sum()))
     return 0
+
+
+def natgrad_leg(h, theta, r, wl, args, flush):
+    """The natural-gradient direction of one optimisation step on the bench walkers: per-walker
+    gradients (grad_logpsi mode 1), clipped-energy weights, then natural_gradient (Gram matrix of
+    the centred gradients on the tensor cores, conjugate gradients in FP64)."""
+    import torch
+
+    B = r.shape[0]
+    _, _, el = h.local_energy(theta, r)
+    w, _ = h.vmc_loss_weights(el, 5.0)
+    G = h.grad_logpsi(theta, r, mode=1)
+    Gc_sq = float(((G.double() - G.double().mean(dim=0)) ** 2).sum())
+    lam = 1e-1 * Gc_sq / B / B  # 1e-1 of the mean eigenvalue of Gc Gc^T / B
+    h.natural_gradient(G, w, lam, max_iter=500, tol=1e-8)  # warm-up (workspace)
+    torch.cuda.synchronize()
+    times = {"grad_per_walker": 0.0, "natural_gradient": 0.0}
+    reps = 3
+    for _ in range(reps):
+        flush.fill_(1)
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record()
+        G = h.grad_logpsi(theta, r, mode=1)
+        b.record()
+        d, st = h.natural_gradient(G, w, lam, max_iter=500, tol=1e-8)
+        c.record()
+        torch.cuda.synchronize()
+        times["grad_per_walker"] += a.elapsed_time(b) / reps
+        times["natural_gradient"] += b.elapsed_time(c) / reps
+    st = st.cpu().tolist()
+    P = h.P
+    gram_flops = 2.0 * B * B * P
+    return {"walkers": B, "params": P, "ms_grad_per_walker": times["grad_per_walker"],
+            "ms_natural_gradient": times["natural_gradient"], "cg_iterations": st[0], "cg_rel_residual": st[1],
+            "damping": "1e-1 x mean eigenvalue of Gc Gc^T / B",
+            "gram_fp32_tflops_incl_solve": gram_flops / (times["natural_gradient"] / 1e3) / 1e12,
+            "note": "Gram matrix of the centred per-walker gradients (3xTF32 tensor cores, FP32 chunks of 8192 "
+                    "parameters added in FP64), conjugate gradients in FP64, delta = Gc^T x"}
 
 
 def batch_leg(args, dev, flush):
@@ -605,6 +644,7 @@ def main():
                     "note": "same workload, Langevin sampler (Sec. 5) instead of random-walk Metropolis; "
                             "L2 flushed before every step"}
 
+    natgrad = natgrad_leg(h, theta, r, wl, args, flush) if (world == 1 and with_grad and not args.no_natgrad) else None
     batched = batch_leg(args, dev, flush) if (world == 1 and not args.no_batch) else None
 
     cpu = None
@@ -628,6 +668,7 @@ def main():
                 "cuda_graph": graph,
                 "langevin_sampler": langevin,
                 "batched_molecules": batched,
+                "natural_gradient": natgrad,
                 "gpu_launches": launches,
                 "clocks": clk,
                 "local_energy_only": {"value": B * world * args.steps / (jet_ms / 1e3) if jet_ms else None,

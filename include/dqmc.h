@@ -90,7 +90,8 @@ typedef enum {
   DQ_OP_GRAD = 3,
   DQ_OP_LOSS_WEIGHTS = 4,
   DQ_OP_MALA = 5,
-  DQ_OP_AUTOTUNE = 6 /* dq_autotune_multi (batches only) */
+  DQ_OP_AUTOTUNE = 6, /* dq_autotune_multi (batches only) */
+  DQ_OP_NATGRAD = 7   /* natural_gradient */
 } dq_op;
 
 /* Device status flags (dq_last_device_status). */
@@ -223,6 +224,31 @@ dq_status mala_step(dq_handle h, const void* params, void* r, void* logabs, void
  * Walkers with psi = 0 contribute zero.                                    */
 dq_status grad_logpsi(dq_handle h, const void* params, const void* r, int64_t B, const void* weights,
                       int32_t mode, void* grad_out, void* ws, size_t ws_bytes, void* stream);
+
+/* natural_gradient: the natural-gradient direction of the optimiser (Sec. 4,
+ * "Optimizer"): the loss gradient g = G^T w (Eq. 30) preconditioned by the
+ * damped Fisher information of |psi|^2 estimated from the walkers,
+ *   delta = (Gc^T Gc / B + lambda I)^-1 g = Gc^T (Gc Gc^T / B + lambda I)^-1 w,
+ * Gc = G minus its mean over the walkers (equal forms by the push-through
+ * identity; the second, a B x B system, is the one solved).  The paper's
+ * optimiser approximates this preconditioner by Kronecker factors; here it is
+ * formed exactly in the walkers' space.
+ *   G      [B][P] in   per-walker gradients d log|psi_b| / d theta, as from
+ *                      grad_logpsi(mode = 1); not modified
+ *   w      [B]    in   walker weights (vmc_loss_weights), so that G^T w is the
+ *                      loss gradient
+ *   lambda        damping, > 0 (absorbs the factor 4 of the Fisher information)
+ *   max_iter, tol conjugate-gradient iterations (at most max_iter; they stop on
+ *                 the device once ||r|| <= tol ||w||)
+ *   delta  [P]    out
+ *   stats  [4]    nullable, device double out: iterations, final ||r|| / ||w||,
+ *                 ||w||, lambda
+ * Gc Gc^T is formed on the tensor cores (3 x TF32 products); the system is
+ * solved in FP64 with fixed-order reductions (deterministic).  FP32 and BF16
+ * handles (DQ_ERR_UNSUPPORTED in FP64 mode); B >= 2.  Workspace:
+ * dq_workspace_size(op = DQ_OP_NATGRAD, B), about 12 B P bytes. */
+dq_status natural_gradient(dq_handle h, const void* G, const void* w, int64_t B, double lambda, int32_t max_iter,
+                           double tol, void* delta, double* stats, void* ws, size_t ws_bytes, void* stream);
 
 /* vmc_loss_weights: clipped local energies and gradient weights (Sec. 4.4,
  * Eq. 30).  Centre mu = median of e_loc (mean of the two middle values for

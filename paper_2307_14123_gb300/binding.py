@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdqmc.so")
 
 DQ_FP64, DQ_FP32, DQ_BF16_MIXED = 0, 1, 2
-OP_EVAL, OP_LOCAL_ENERGY, OP_MCMC, OP_GRAD, OP_LOSS_WEIGHTS, OP_MALA, OP_AUTOTUNE = 0, 1, 2, 3, 4, 5, 6
+OP_EVAL, OP_LOCAL_ENERGY, OP_MCMC, OP_GRAD, OP_LOSS_WEIGHTS, OP_MALA, OP_AUTOTUNE, OP_NATGRAD = 0, 1, 2, 3, 4, 5, 6, 7
 FLAG_SINGULAR, FLAG_NONFINITE = 0x1, 0x2
 PRECISIONS = {"fp64": DQ_FP64, "fp32": DQ_FP32, "bf16": DQ_BF16_MIXED}
 
@@ -35,7 +35,7 @@ EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_
            "dq_test_gemm_tf32x3", "mcmc_step_dev", "mala_step", "dq_create_multi", "dq_destroy_multi",
            "dq_multi_handle", "dq_multi_set_rounds", "dq_multi_rounds", "dq_multi_workspace_size",
            "ansatz_eval_multi", "local_energy_multi", "mcmc_step_multi", "grad_logpsi_multi",
-           "vmc_loss_weights_multi", "dq_autotune_multi", "dq_multi_tuning", "dq_set_msg_tile", "dq_msg_tile", "dq_autotune"]
+           "vmc_loss_weights_multi", "dq_autotune_multi", "dq_multi_tuning", "dq_set_msg_tile", "dq_msg_tile", "dq_autotune", "natural_gradient"]
 
 
 class DQError(RuntimeError):
@@ -109,6 +109,7 @@ def load_library(path=None):
         lib.dq_set_msg_tile.argtypes = [P, i32]
         lib.dq_msg_tile.argtypes = [P, P]
         lib.dq_autotune.argtypes = [P, P, P, i64, P, sz, P, P]
+        lib.natural_gradient.argtypes = [P, P, P, i64, f64, i32, f64, P, P, P, sz, P]
         for name in EXPORTS:
             getattr(lib, name).restype = ctypes.c_int
         lib.dq_status_string.restype = ctypes.c_char_p
@@ -329,6 +330,20 @@ class Ansatz:
         _check(self.lib.grad_logpsi(self.h, _ptr(params), _ptr(r), B, _ptr(w), int(mode), _ptr(out), _ptr(ws),
                                     ws.numel(), self._stream()))
         return out
+
+    def natural_gradient(self, G, w, lam, max_iter=200, tol=1e-8):
+        """Natural-gradient direction (F + lam I)^-1 G^T w from per-walker gradients G [B][P]
+        (grad_logpsi mode 1) and walker weights w; returns (delta [P], stats [iterations,
+        relative residual, ||w||, lam])."""
+        G = self._dev(G)
+        B = G.numel() // self.P
+        w = self._dev(w, shape=(B,))
+        delta = torch.empty(self.P, dtype=self.dtype, device=self.device)
+        stats = torch.empty(4, dtype=torch.float64, device=self.device)
+        ws = self.workspace(B, OP_NATGRAD)
+        _check(self.lib.natural_gradient(self.h, _ptr(G), _ptr(w), B, float(lam), int(max_iter), float(tol),
+                                         _ptr(delta), _ptr(stats), _ptr(ws), ws.numel(), self._stream()))
+        return delta, stats
 
     def vmc_loss_weights(self, e_loc, clip_k=5.0):
         """Median/MAD-clipped gradient weights; returns (weights, stats[mu, half-width, mean E^, mean E])."""

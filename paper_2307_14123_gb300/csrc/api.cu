@@ -1234,6 +1234,7 @@ dq_status dq_workspace_size(dq_handle h, int64_t B, int32_t op, size_t* bytes) {
     case DQ_OP_GRAD: *bytes = plan_grad(*h, Bc, el).total; return DQ_OK;
     case DQ_OP_LOSS_WEIGHTS: *bytes = loss_scratch_bytes(std::max<int64_t>(B, 1)); return DQ_OK;
     case DQ_OP_MALA: *bytes = plan_mala(*h, std::max<int64_t>(B, 1), el).total; return DQ_OK;
+    case DQ_OP_NATGRAD: *bytes = natgrad_workspace(std::max<int64_t>(B, 2), h->off.total); return DQ_OK;
   }
   return DQ_ERR_ARG;
 }
@@ -1360,6 +1361,22 @@ dq_status grad_logpsi(dq_handle h, const void* params, const void* r, int64_t B,
                             w, ws_bytes, s);
   return run_grad<float>(*h, (const float*)params, (const float*)r, B, (const float*)wt, mode, (float*)grad_out, w,
                          ws_bytes, s);
+}
+
+dq_status natural_gradient(dq_handle h, const void* G, const void* w, int64_t B, double lambda, int32_t max_iter,
+                           double tol, void* delta, double* stats, void* ws, size_t ws_bytes, void* stream) {
+  dq_status st = check_handle(h);
+  if (st != DQ_OK) return st;
+  if (h->precision == DQ_FP64) return DQ_ERR_UNSUPPORTED;
+  if (!G || !w || !delta || B < 2 || !(lambda > 0) || !isfinite(lambda) || max_iter < 0 || !(tol >= 0))
+    return DQ_ERR_ARG;
+  if (B > (int64_t)INT32_MAX || h->off.total > (int64_t)INT32_MAX) return DQ_ERR_SHAPE;
+  if (!ws || ws_bytes < natgrad_workspace(B, h->off.total) || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
+  const cudaError_t e = natgrad_run(static_cast<const float*>(G), static_cast<const float*>(w), B, h->off.total,
+                                    lambda, max_iter, tol, static_cast<float*>(delta), stats,
+                                    static_cast<unsigned char*>(ws), h->d_status, (cudaStream_t)stream);
+  if (e == cudaErrorInvalidValue) return DQ_ERR_ARG;
+  return e == cudaSuccess ? DQ_OK : DQ_ERR_CUDA;
 }
 
 dq_status vmc_loss_weights(dq_handle h, const void* e_loc, int64_t B, double clip_k, void* weights, double* stats,

@@ -205,6 +205,11 @@ cudaError_t gemm_tf32x3_tc_seg(const float* X, int64_t seg_rows, int64_t n_seg, 
                                int64_t ldx, const float* Wbig, const float* Wsmall, int n_out, const float* bias,
                                int bias_period, float* Y, int64_t ldy, int64_t y_seg_stride, unsigned int* status,
                                cudaStream_t s, bool accumulate = false);
+// Natural-gradient direction (natgrad.cu): workspace bytes and the computation for B
+// walkers' gradients G [B][P] and weights w [B].
+size_t natgrad_workspace(int64_t B, int64_t P);
+cudaError_t natgrad_run(const float* G, const float* w, int64_t B, int64_t P, double lam, int max_iter, double tol,
+                        float* delta, double* stats, unsigned char* ws, unsigned int* status, cudaStream_t s);
 // A list of such GEMMs in one persistent launch (tiles of all jobs share the
 // grid); at most 16 per launch (more are split over launches).
 struct T3JobDesc {
@@ -219,6 +224,7 @@ struct T3JobDesc {
   float* Y;
   int64_t ldy, y_seg_stride;
   bool accumulate;
+  int64_t ldw = 0;  // row pitch of Wbig / Wsmall in elements (0: K)
 };
 cudaError_t gemm_tf32x3_tc_jobs(const T3JobDesc* jobs, int n, unsigned int* status, cudaStream_t s);
 // TF32 high / low parts of the transpose of W [rows][cols] (for products X W).

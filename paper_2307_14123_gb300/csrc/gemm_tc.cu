@@ -963,7 +963,7 @@ cudaError_t gemm_tf32x3_tc_jobs(const T3JobDesc* d, int n, unsigned int* status,
   for (int i = 0; i < n; ++i) {
     const T3JobDesc& q = d[i];
     if (q.seg_rows <= 0 || q.n_seg <= 0 || q.n_out <= 0) continue;
-    if (q.K % 4 || q.ldx % 4 || q.x_seg_stride % 4 || (uintptr_t)q.X % 16 || (uintptr_t)q.Wbig % 16 ||
+    if (q.K % 4 || q.ldx % 4 || q.ldw % 4 || q.x_seg_stride % 4 || (uintptr_t)q.X % 16 || (uintptr_t)q.Wbig % 16 ||
         (uintptr_t)q.Wsmall % 16 || q.bias_period <= 0 || q.seg_rows > (int64_t)INT32_MAX ||
         q.n_seg > (int64_t)INT32_MAX)
       return cudaErrorInvalidValue;
@@ -972,8 +972,8 @@ cudaError_t gemm_tf32x3_tc_jobs(const T3JobDesc* d, int n, unsigned int* status,
     while (rb > 8 && rb / 2 >= q.seg_rows) rb /= 2;
     if (!make_map_seg_f32(&j.a, q.X, q.seg_rows, q.n_seg, q.K, q.ldx,
                           q.n_seg > 1 ? q.x_seg_stride : q.seg_rows * q.ldx, rb) ||
-        !make_map(&j.bb, q.Wbig, q.n_out, q.K, q.K, TC_BN, true) ||
-        !make_map(&j.bs, q.Wsmall, q.n_out, q.K, q.K, TC_BN, true))
+        !make_map(&j.bb, q.Wbig, q.n_out, q.K, q.ldw ? q.ldw : q.K, TC_BN, true) ||
+        !make_map(&j.bs, q.Wsmall, q.n_out, q.K, q.ldw ? q.ldw : q.K, TC_BN, true))
       return cudaErrorInvalidValue;
     j.f.bias = q.bias;
     j.f.Y = q.Y;
