@@ -91,7 +91,8 @@ typedef enum {
   DQ_OP_LOSS_WEIGHTS = 4,
   DQ_OP_MALA = 5,
   DQ_OP_AUTOTUNE = 6, /* dq_autotune_multi (batches only) */
-  DQ_OP_NATGRAD = 7   /* natural_gradient */
+  DQ_OP_NATGRAD = 7,  /* natural_gradient */
+  DQ_OP_UPDATE = 8    /* param_update */
 } dq_op;
 
 /* Device status flags (dq_last_device_status). */
@@ -237,18 +238,32 @@ dq_status grad_logpsi(dq_handle h, const void* params, const void* r, int64_t B,
  *                      grad_logpsi(mode = 1); not modified
  *   w      [B]    in   walker weights (vmc_loss_weights), so that G^T w is the
  *                      loss gradient
- *   lambda        damping, > 0 (absorbs the factor 4 of the Fisher information)
+ *   lambda        damping (absorbs the factor 4 of the Fisher information): > 0
+ *                 absolute; < 0 relative, |lambda| times the mean eigenvalue
+ *                 tr(Gc Gc^T) / B^2 of Gc Gc^T / B (taken on the device)
  *   max_iter, tol conjugate-gradient iterations (at most max_iter; they stop on
  *                 the device once ||r|| <= tol ||w||)
  *   delta  [P]    out
  *   stats  [4]    nullable, device double out: iterations, final ||r|| / ||w||,
- *                 ||w||, lambda
+ *                 ||w||, the damping used
  * Gc Gc^T is formed on the tensor cores (3 x TF32 products); the system is
  * solved in FP64 with fixed-order reductions (deterministic).  FP32 and BF16
  * handles (DQ_ERR_UNSUPPORTED in FP64 mode); B >= 2.  Workspace:
  * dq_workspace_size(op = DQ_OP_NATGRAD, B), about 12 B P bytes. */
 dq_status natural_gradient(dq_handle h, const void* G, const void* w, int64_t B, double lambda, int32_t max_iter,
                            double tol, void* delta, double* stats, void* ws, size_t ws_bytes, void* stream);
+
+/* param_update: the parameter step of the optimiser around a direction such
+ * as natural_gradient's, theta <- theta - lr s delta, with the step-length
+ * limit s = min(1, max_norm / (lr ||delta||)) usual for natural-gradient steps
+ * (max_norm <= 0: s = 1).  The paper's optimiser takes its step from a
+ * third-party library; this is the plain form.
+ *   params [P] in/out, delta [P] in (FP32 modes; DQ_ERR_UNSUPPORTED in FP64)
+ *   stats  [2] device double out: ||delta||, s
+ * ||delta|| is a fixed-order FP64 reduction.  Workspace:
+ * dq_workspace_size(op = DQ_OP_UPDATE). */
+dq_status param_update(dq_handle h, void* params, const void* delta, double lr, double max_norm, double* stats,
+                       void* ws, size_t ws_bytes, void* stream);
 
 /* vmc_loss_weights: clipped local energies and gradient weights (Sec. 4.4,
  * Eq. 30).  Centre mu = median of e_loc (mean of the two middle values for

@@ -23,7 +23,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdqmc.so")
 
 DQ_FP64, DQ_FP32, DQ_BF16_MIXED = 0, 1, 2
-OP_EVAL, OP_LOCAL_ENERGY, OP_MCMC, OP_GRAD, OP_LOSS_WEIGHTS, OP_MALA, OP_AUTOTUNE, OP_NATGRAD = 0, 1, 2, 3, 4, 5, 6, 7
+(OP_EVAL, OP_LOCAL_ENERGY, OP_MCMC, OP_GRAD, OP_LOSS_WEIGHTS, OP_MALA, OP_AUTOTUNE, OP_NATGRAD,
+ OP_UPDATE) = 0, 1, 2, 3, 4, 5, 6, 7, 8
 FLAG_SINGULAR, FLAG_NONFINITE = 0x1, 0x2
 PRECISIONS = {"fp64": DQ_FP64, "fp32": DQ_FP32, "bf16": DQ_BF16_MIXED}
 
@@ -35,7 +36,7 @@ EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_
            "dq_test_gemm_tf32x3", "mcmc_step_dev", "mala_step", "dq_create_multi", "dq_destroy_multi",
            "dq_multi_handle", "dq_multi_set_rounds", "dq_multi_rounds", "dq_multi_workspace_size",
            "ansatz_eval_multi", "local_energy_multi", "mcmc_step_multi", "grad_logpsi_multi",
-           "vmc_loss_weights_multi", "dq_autotune_multi", "dq_multi_tuning", "dq_set_msg_tile", "dq_msg_tile", "dq_autotune", "natural_gradient"]
+           "vmc_loss_weights_multi", "dq_autotune_multi", "dq_multi_tuning", "dq_set_msg_tile", "dq_msg_tile", "dq_autotune", "natural_gradient", "param_update"]
 
 
 class DQError(RuntimeError):
@@ -110,6 +111,7 @@ def load_library(path=None):
         lib.dq_msg_tile.argtypes = [P, P]
         lib.dq_autotune.argtypes = [P, P, P, i64, P, sz, P, P]
         lib.natural_gradient.argtypes = [P, P, P, i64, f64, i32, f64, P, P, P, sz, P]
+        lib.param_update.argtypes = [P, P, P, f64, f64, P, P, sz, P]
         for name in EXPORTS:
             getattr(lib, name).restype = ctypes.c_int
         lib.dq_status_string.restype = ctypes.c_char_p
@@ -344,6 +346,18 @@ class Ansatz:
         _check(self.lib.natural_gradient(self.h, _ptr(G), _ptr(w), B, float(lam), int(max_iter), float(tol),
                                          _ptr(delta), _ptr(stats), _ptr(ws), ws.numel(), self._stream()))
         return delta, stats
+
+    def param_update(self, params, delta, lr, max_norm=0.0):
+        """In place: params -= lr * s * delta with s = min(1, max_norm / (lr ||delta||)) (max_norm <= 0:
+        s = 1); returns stats [||delta||, s] (device float64)."""
+        if params.device != self.device or params.dtype != self.dtype or not params.is_contiguous():
+            raise DQError("param_update updates params in place: pass a contiguous device tensor")
+        delta = self._dev(delta, shape=(self.P,))
+        stats = torch.empty(2, dtype=torch.float64, device=self.device)
+        ws = self.workspace(1, OP_UPDATE)
+        _check(self.lib.param_update(self.h, _ptr(params), _ptr(delta), float(lr), float(max_norm), _ptr(stats),
+                                     _ptr(ws), ws.numel(), self._stream()))
+        return stats
 
     def vmc_loss_weights(self, e_loc, clip_k=5.0):
         """Median/MAD-clipped gradient weights; returns (weights, stats[mu, half-width, mean E^, mean E])."""
@@ -650,3 +664,21 @@ def grad_logpsi(h: Ansatz, params, r, weights=None, mode=0):
 
 def vmc_loss_weights(h: Ansatz, e_loc, clip_k=5.0):
     return h.vmc_loss_weights(e_loc, clip_k)
+
+
+def vmc_train_step(h: Ansatz, params, r, logabs, lr, damping=-0.1, max_norm=0.0, step_size=0.2, seed=0,
+                   step_counter=0, clip_k=5.0, cg_iters=200, cg_tol=1e-8):
+    """One step of the VMC training loop with every computation in the library: a Metropolis sweep
+    (positions and log|psi| updated in place), local energies, clipped-energy weights, per-walker
+    gradients, the natural-gradient direction (damping < 0: relative to the Gram matrix's mean
+    eigenvalue) and the parameter update (params in place).  Returns a dict of device tensors:
+    e_sum2 ([sum E, sum E^2] of the unclipped energies before the update), loss-weight stats,
+    natural-gradient stats and update stats."""
+    h.mcmc_step(params, r, logabs, 1, step_size, seed, step_counter)
+    _, _, e_loc, e2 = h.local_energy(params, r, sums=True)
+    w, wstats = h.vmc_loss_weights(e_loc, clip_k)
+    G = h.grad_logpsi(params, r, mode=1)
+    delta, ngstats = h.natural_gradient(G, w, damping, cg_iters, cg_tol)
+    ustats = h.param_update(params, delta, lr, max_norm)
+    return {"e_sum2": e2, "weights": wstats, "natural_gradient": ngstats, "update": ustats}
+

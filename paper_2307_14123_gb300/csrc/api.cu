@@ -628,7 +628,8 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
       const T* pb = phibar + (int64_t)i0[sg] * Wo;
       DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(pb, mp, F(L) + (int64_t)i0[sg] * D, mf, ns[sg], K * ns[sg], D, off.W_o[sg], D));
       DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(pb, mp, nullptr, rm(1), ns[sg], K * ns[sg], 1, off.b_o[sg], 1));
-      if (use_t3)
+      // tensor cores when the rows of phi-bar suit the tensor maps (K * n_s and Wo multiples of 4)
+      if (use_t3 && (K * ns[sg]) % 4 == 0 && Wo % 4 == 0)
         DQ_LAUNCH(h, PK_BWD_GEMM,
                   gemm_tf32x3_tc_seg(reinterpret_cast<const float*>(pb), ns[sg], nb, (int64_t)N * Wo, K * ns[sg], Wo,
                                      w3t.wo(sg, 0), w3t.wo(sg, 1), D, nullptr, 1,
@@ -1235,6 +1236,7 @@ dq_status dq_workspace_size(dq_handle h, int64_t B, int32_t op, size_t* bytes) {
     case DQ_OP_LOSS_WEIGHTS: *bytes = loss_scratch_bytes(std::max<int64_t>(B, 1)); return DQ_OK;
     case DQ_OP_MALA: *bytes = plan_mala(*h, std::max<int64_t>(B, 1), el).total; return DQ_OK;
     case DQ_OP_NATGRAD: *bytes = natgrad_workspace(std::max<int64_t>(B, 2), h->off.total); return DQ_OK;
+    case DQ_OP_UPDATE: *bytes = param_update_workspace(); return DQ_OK;
   }
   return DQ_ERR_ARG;
 }
@@ -1368,7 +1370,7 @@ dq_status natural_gradient(dq_handle h, const void* G, const void* w, int64_t B,
   dq_status st = check_handle(h);
   if (st != DQ_OK) return st;
   if (h->precision == DQ_FP64) return DQ_ERR_UNSUPPORTED;
-  if (!G || !w || !delta || B < 2 || !(lambda > 0) || !isfinite(lambda) || max_iter < 0 || !(tol >= 0))
+  if (!G || !w || !delta || B < 2 || lambda == 0 || !isfinite(lambda) || max_iter < 0 || !(tol >= 0))
     return DQ_ERR_ARG;
   if (B > (int64_t)INT32_MAX || h->off.total > (int64_t)INT32_MAX) return DQ_ERR_SHAPE;
   if (!ws || ws_bytes < natgrad_workspace(B, h->off.total) || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
@@ -1376,6 +1378,19 @@ dq_status natural_gradient(dq_handle h, const void* G, const void* w, int64_t B,
                                     lambda, max_iter, tol, static_cast<float*>(delta), stats,
                                     static_cast<unsigned char*>(ws), h->d_status, (cudaStream_t)stream);
   if (e == cudaErrorInvalidValue) return DQ_ERR_ARG;
+  return e == cudaSuccess ? DQ_OK : DQ_ERR_CUDA;
+}
+
+dq_status param_update(dq_handle h, void* params, const void* delta, double lr, double max_norm, double* stats,
+                       void* ws, size_t ws_bytes, void* stream) {
+  dq_status st = check_handle(h);
+  if (st != DQ_OK) return st;
+  if (h->precision == DQ_FP64) return DQ_ERR_UNSUPPORTED;
+  if (!params || !delta || !stats || !isfinite(lr) || !isfinite(max_norm)) return DQ_ERR_ARG;
+  if (!ws || ws_bytes < param_update_workspace() || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
+  const cudaError_t e = param_update_run<float>(static_cast<float*>(params), static_cast<const float*>(delta),
+                                                h->off.total, lr, max_norm, stats, static_cast<unsigned char*>(ws),
+                                                (cudaStream_t)stream);
   return e == cudaSuccess ? DQ_OK : DQ_ERR_CUDA;
 }
 

@@ -210,6 +210,12 @@ cudaError_t gemm_tf32x3_tc_seg(const float* X, int64_t seg_rows, int64_t n_seg, 
 size_t natgrad_workspace(int64_t B, int64_t P);
 cudaError_t natgrad_run(const float* G, const float* w, int64_t B, int64_t P, double lam, int max_iter, double tol,
                         float* delta, double* stats, unsigned char* ws, unsigned int* status, cudaStream_t s);
+// Parameter update theta -= lr s delta with s = min(1, max_norm / (lr ||delta||)); stats
+// (device double[2]): ||delta||, s.  Workspace: param_update_workspace() bytes.
+size_t param_update_workspace();
+template <class T>
+cudaError_t param_update_run(T* theta, const T* delta, int64_t P, double lr, double max_norm, double* stats,
+                             unsigned char* ws, cudaStream_t s);
 // A list of such GEMMs in one persistent launch (tiles of all jobs share the
 // grid); at most 16 per launch (more are split over launches).
 struct T3JobDesc {

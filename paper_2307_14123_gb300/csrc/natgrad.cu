@@ -88,6 +88,13 @@ __global__ void ng_cg_init_kernel(const float* __restrict__ w, int64_t B, const 
                                   double* r, double* p, double* dinv, CgScalars* sc, double lam, double tol,
                                   int max_iter) {
   __shared__ double sh[kNgThreads];
+  if (lam < 0) {  // relative damping: |lam| x the mean eigenvalue tr(T) / B^2 of T / B
+    double tr = 0;
+    for (int64_t i = threadIdx.x; i < B; i += blockDim.x) tr += T[i * B + i];
+    tr = ng_block_sum(tr, sh);
+    lam = -lam * tr / ((double)B * (double)B);
+    if (!(lam > 0)) lam = 1.0;  // all-zero gradients: any positive damping gives delta = 0
+  }
   double s = 0, sz = 0;
   for (int64_t i = threadIdx.x; i < B; i += blockDim.x) {
     const double v = (double)w[i];
@@ -303,5 +310,59 @@ cudaError_t natgrad_run(const float* G, const float* w, int64_t B, int64_t P, do
   if (stats) ng_stats_kernel<<<1, 1, 0, s>>>(sc, stats);
   return cudaGetLastError();
 }
+
+}  // namespace dq
+
+namespace dq {
+namespace {
+// ||delta||^2 in FP64: per-CTA partials, the last CTA adds them in index order and
+// sets the step scale s = min(1, max_norm / (lr ||delta||)) (no limit when max_norm <= 0)
+__global__ void ng_norm_kernel(const float* __restrict__ d, int64_t P, double lr, double max_norm,
+                               double* partials, unsigned int* counter, double* out) {
+  double part = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = (double)d[i];
+    part += v * v;
+  }
+  __shared__ double sh[kNgThreads];
+  const double cta = ng_block_sum(part, sh);
+  double ss = 0;
+  if (ng_finish(cta, partials, counter, &ss) && threadIdx.x == 0) {
+    const double nrm = sqrt(ss);
+    out[0] = nrm;
+    out[1] = (max_norm > 0 && lr * nrm > max_norm) ? max_norm / (lr * nrm) : 1.0;
+  }
+}
+
+// theta -= lr * s * delta
+template <class T>
+__global__ void ng_update_kernel(T* __restrict__ theta, const T* __restrict__ d, int64_t P, double lr,
+                                 const double* __restrict__ nrm) {
+  const double step = lr * nrm[1];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P; i += (int64_t)gridDim.x * blockDim.x)
+    theta[i] = (T)((double)theta[i] - step * (double)d[i]);
+}
+}  // namespace
+
+size_t param_update_workspace() { return 1024 * 8 + 256; }
+
+template <class T>
+cudaError_t param_update_run(T* theta, const T* delta, int64_t P, double lr, double max_norm, double* stats,
+                             unsigned char* ws, cudaStream_t s) {
+  double* partials = reinterpret_cast<double*>(ws);
+  unsigned int* counter = reinterpret_cast<unsigned int*>(ws + 1024 * 8);
+  const unsigned ctas = ng_blocks(P, kNgThreads) < 1024 ? ng_blocks(P, kNgThreads) : 1024;
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  if constexpr (sizeof(T) == 4) {
+    ng_norm_kernel<<<ctas, kNgThreads, 0, s>>>(delta, P, lr, max_norm, partials, counter, stats);
+  } else {
+    return cudaErrorInvalidValue;  // FP32 modes only
+  }
+  ng_update_kernel<T><<<ctas, kNgThreads, 0, s>>>(theta, delta, P, lr, stats);
+  return cudaGetLastError();
+}
+template cudaError_t param_update_run<float>(float*, const float*, int64_t, double, double, double*, unsigned char*,
+                                             cudaStream_t);
 
 }  // namespace dq

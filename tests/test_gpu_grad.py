@@ -187,3 +187,20 @@ def test_weighted_mode_fp32_equals_weighted_sum_of_per_walker():
     print(f"N2 FP32 weighted vs per-walker sum: max |dg| / sum|w g| {worst_matrix:.2e} (weight matrices), "
           f"{worst_other:.2e} (other blocks)")
     assert worst_matrix <= 5e-5
+
+
+def test_lih_fp32_per_walker_gradient():
+    """LiH in FP32 mode (one determinant pair, two electrons per spin: the orbital adjoint
+    product takes the CUDA-core path, its rows being too short for the tensor maps)."""
+    wl = fx.workload("lih_fp64")
+    h = _handle(wl.system, wl.cfg, "fp32")
+    theta = fx.init_params(wl.system, wl.cfg, wl.param_seed).astype(np.float32).astype(np.float64)
+    r = fx.init_walkers(wl.system, 8, wl.walker_seed).astype(np.float32).astype(np.float64)
+    G = h.grad_logpsi(torch.tensor(theta, dtype=torch.float32, device="cuda:0"),
+                      torch.tensor(r, dtype=torch.float32, device="cuda:0"), mode=1).cpu().numpy().astype(np.float64)
+    o = oracle.Oracle(wl.system, wl.cfg)
+    dirs = np.random.default_rng(4).normal(size=(3, o.P))
+    jv = o.grad_jvp(theta, r, dirs)
+    rel = np.abs(G @ dirs.T - jv) / (np.abs(G) @ np.abs(dirs.T))
+    print("LiH FP32 |g.v - ref| / sum|g v|: max %.2e" % rel.max())
+    assert np.all(rel <= 1e-3)

@@ -92,3 +92,56 @@ def test_natural_gradient_real_gradients_normal_equations():
     rel = float((lhs - g).norm() / g.norm())
     print(f"N2 B={B}: CG iterations {float(st[0]):.0f}, residual {float(st[1]):.2e}, normal-equation residual {rel:.2e}")
     assert rel <= 2e-3
+
+
+def test_relative_damping_matches_absolute():
+    """lambda < 0 means |lambda| x tr(Gc Gc^T) / B^2; against the oracle at that absolute damping."""
+    wl, h = _handle("lih_fp64")
+    G, w = _synthetic(128, h.P, 21)
+    Gc = G - G.mean(axis=0)
+    lam = 0.05 * float(np.sum(Gc * Gc)) / 128 / 128
+    d, st = h.natural_gradient(torch.tensor(G, dtype=torch.float32, device="cuda:0"),
+                               torch.tensor(w, dtype=torch.float32, device="cuda:0"), -0.05, max_iter=400, tol=1e-9)
+    # the Gram diagonal sums positive squares in FP32 over chunks of 8192: at most 8192 x 2^-24 relative
+    assert abs(float(st[3]) - lam) <= 5e-4 * lam
+    ref = oracle.natural_gradient(G, w, lam)
+    assert np.linalg.norm(d.cpu().numpy() - ref) <= 2e-3 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("max_norm", [0.0, 1e-3])
+def test_param_update_definition(max_norm):
+    """theta <- theta - lr s delta, s = min(1, max_norm / (lr ||delta||)) (FP64 reference)."""
+    wl, h = _handle("lih_fp64")
+    rng = np.random.default_rng(7)
+    th = rng.standard_normal(h.P).astype(np.float32)
+    dl = rng.standard_normal(h.P).astype(np.float32)
+    lr = 0.05
+    t = torch.tensor(th, device="cuda:0")
+    st = h.param_update(t, torch.tensor(dl, device="cuda:0"), lr, max_norm).cpu().numpy()
+    nrm = np.linalg.norm(dl.astype(np.float64))
+    s = 1.0 if max_norm <= 0 or lr * nrm <= max_norm else max_norm / (lr * nrm)
+    assert st[0] == pytest.approx(nrm, rel=1e-12) and st[1] == pytest.approx(s, rel=1e-12)
+    ref = th.astype(np.float64) - lr * s * dl.astype(np.float64)
+    np.testing.assert_allclose(t.cpu().numpy(), ref, rtol=0, atol=1e-6 * (1 + np.abs(ref).max()))
+
+
+def test_vmc_train_step_runs_and_is_reproducible():
+    """Three training steps (sampler, local energies, weights, per-walker gradients, natural
+    gradient, update) on LiH: finite statistics, parameters move, and a second run from the
+    same state gives the same bits."""
+    from paper_2307_14123_gb300 import vmc_train_step
+    wl, h = _handle("lih_fp64")
+    th0 = torch.tensor(fx.init_params(wl.system, wl.cfg, wl.param_seed), dtype=torch.float32, device="cuda:0")
+    r0 = torch.tensor(fx.init_walkers(wl.system, 256, wl.walker_seed), dtype=torch.float32, device="cuda:0")
+    runs = []
+    for _ in range(2):
+        th, r = th0.clone(), r0.clone()
+        la, _ = h.ansatz_eval(th, r)
+        for t in range(3):
+            out = vmc_train_step(h, th, r, la, lr=0.02, damping=-0.1, max_norm=0.05, seed=1, step_counter=t)
+            e2 = out["e_sum2"].cpu().numpy()
+            assert np.all(np.isfinite(e2)) and np.all(np.isfinite(out["natural_gradient"].cpu().numpy()))
+            assert float(out["update"][1]) <= 1.0
+        runs.append((th.clone(), r.clone()))
+    assert not torch.equal(runs[0][0], th0)
+    assert torch.equal(runs[0][0], runs[1][0]) and torch.equal(runs[0][1], runs[1][1])
