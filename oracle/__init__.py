@@ -19,6 +19,10 @@ Functions, each following the paper's definitions:
 * :func:`clipped_loss_weights` - median/MAD clipping of Sec. 4.4 and the
   per-walker weights of the gradient estimator, Eq. (30).
 * :func:`energy_estimate` - Eq. (33) and the batch-means error bar, Eq. (35).
+* :func:`pseudopotential` - local and non-local pseudopotential energies of
+  Eqs. (pseudopotential) and (pp_integral): the angular integral by the
+  12-point icosahedral quadrature over a rotated icosahedron, psi ratios from
+  :meth:`Oracle.evaluate`.
 * :func:`natural_gradient` - the natural-gradient direction of the optimiser
   section (Sec. 4, "Optimizer"): the loss gradient preconditioned by the damped
   Fisher information of |psi|^2, estimated from walker-centred per-walker
@@ -274,4 +278,68 @@ def natural_gradient(G, w, lam, form="sample"):
         x = np.linalg.solve(Gc @ Gc.T / B + lam * np.eye(B), w)
         return Gc.T @ x
     return np.linalg.solve(Gc.T @ Gc / B + lam * np.eye(P), Gc.T @ w)
+
+
+_GOLDEN = (1.0 + 5.0 ** 0.5) / 2.0
+
+
+def icosahedron():
+    """The 12 vertices of a regular icosahedron on the unit sphere."""
+    v = []
+    for a in (-1.0, 1.0):
+        for b in (-_GOLDEN, _GOLDEN):
+            v += [(0.0, a, b), (a, b, 0.0), (b, 0.0, a)]
+    v = np.array(v)
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def pp_radial(coef, r):
+    """sum_k beta_k r^(n_k - 2) exp(-alpha_k r^2) for coef [n_terms][3] = (beta, n, alpha)."""
+    coef = np.asarray(coef, dtype=np.float64)
+    return float(np.sum(coef[:, 0] * r ** (coef[:, 1] - 2.0) * np.exp(-coef[:, 2] * r * r)))
+
+
+def legendre(l, x):
+    """P_l(x), l <= 3."""
+    return [1.0, x, 0.5 * (3 * x * x - 1), 0.5 * (5 * x ** 3 - 3 * x)][l]
+
+
+def pseudopotential(orc, theta, r, pps, rot):
+    """Local and non-local pseudopotential energies of every walker (Eqs. pseudopotential and
+    pp_integral).  pps: list of (nucleus index, coef [(l_max + 2)][n_terms][3]) with the local
+    function V first, then W_0 .. W_lmax; rot [B][3][3] rotations of the icosahedron (one per
+    walker).  For electron i and nucleus I the angular integral of Y_lm^* psi-ratio, summed over
+    m with Y_lm(Omega), is (2l + 1) / (4 pi) int P_l(cos) psi'/psi dOmega' by the addition
+    theorem; the quadrature replaces int dOmega' by 4 pi / 12 times the sum over the 12 vertices.
+    Returns (v_loc [B], v_nl [B])."""
+    theta = np.asarray(theta, dtype=np.float64)
+    r = np.asarray(r, dtype=np.float64).reshape(-1, orc.N, 3)
+    B = r.shape[0]
+    R = np.asarray(orc.system.R, dtype=np.float64).reshape(-1, 3)
+    ico = icosahedron()
+    la0, sg0 = orc.evaluate(theta, r)
+    v_loc = np.zeros(B)
+    v_nl = np.zeros(B)
+    for b in range(B):
+        verts = ico @ np.asarray(rot[b], dtype=np.float64).T  # R u_k
+        configs, weights = [], []
+        for I, coef in pps:
+            coef = np.asarray(coef, dtype=np.float64)
+            lmax = coef.shape[0] - 2
+            for i in range(orc.N):
+                d = r[b, i] - R[I]
+                rr = float(np.linalg.norm(d))
+                v_loc[b] += pp_radial(coef[0], rr)
+                u = d / rr
+                for k in range(12):
+                    c = r[b].copy()
+                    c[i] = R[I] + rr * verts[k]
+                    configs.append(c)
+                    cos = float(verts[k] @ u)
+                    weights.append(sum(pp_radial(coef[1 + l], rr) * (2 * l + 1) / 12.0 * legendre(l, cos)
+                                       for l in range(lmax + 1)))
+        la, sg = orc.evaluate(theta, np.array(configs))
+        ratio = sg * sg0[b] * np.exp(la - la0[b])
+        v_nl[b] = float(np.sum(np.array(weights) * ratio))
+    return v_loc, v_nl
 

@@ -695,3 +695,69 @@ def test_natural_gradient_limits():
     Gc = G - G.mean(axis=0)
     d = oracle.natural_gradient(G, w, 1e-3)
     np.testing.assert_allclose(Gc.T @ Gc / 50 @ d + 1e-3 * d, g, rtol=1e-8, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# Pseudopotential quadrature (Eqs. pseudopotential, pp_integral)
+# ----------------------------------------------------------------------------
+def test_icosahedral_rule_and_legendre():
+    """The 12-point rule integrates P_l(u . v) exactly for l = 1..5 (mean 0) and is exact for
+    the constant; the Legendre polynomials and the Gaussian radial form as defined."""
+    from scipy.special import eval_legendre
+    ico = oracle.icosahedron()
+    assert ico.shape == (12, 3) and np.allclose(np.linalg.norm(ico, axis=1), 1.0)
+    rng = np.random.default_rng(0)
+    for _ in range(5):
+        v = rng.standard_normal(3)
+        v /= np.linalg.norm(v)
+        x = ico @ v
+        for l in range(1, 6):
+            assert abs(np.mean(eval_legendre(l, x))) < 1e-12
+        for l in range(4):
+            np.testing.assert_allclose([oracle.legendre(l, t) for t in x], eval_legendre(l, x), atol=1e-14)
+    coef = [(2.0, 2, 0.7), (-1.5, 1, 1.3), (0.5, 3, 0.2)]
+    rr = 0.83
+    direct = 2.0 * np.exp(-0.7 * rr * rr) - 1.5 / rr * np.exp(-1.3 * rr * rr) + 0.5 * rr * np.exp(-0.2 * rr * rr)
+    assert oracle.pp_radial(coef, rr) == pytest.approx(direct, rel=1e-14)
+
+
+def test_pseudopotential_hydrogen_closed_form():
+    """psi = exp(-r) (network off) and the pseudopotential on the nucleus: every rotated point
+    keeps r, so every psi ratio is 1 and the quadrature leaves V_NL = W_0(r) exactly (the
+    l >= 1 channels average P_l over the icosahedron to zero); V_loc = V(r)."""
+    H = fx.molecule("H")
+    cfg = fx.AnsatzCfg(32, 1, 1, use_jastrow=0, use_cusp=0)
+    th = fx.network_off_params(H, cfg, 1.0)
+    o = oracle.Oracle(H, cfg)
+    r = np.random.default_rng(4).normal(size=(6, 1, 3)) * 1.2
+    coef = np.array([[(1.0, 1, 0.5), (0.3, 2, 1.1)],    # V
+                     [(2.0, 2, 0.8), (-0.4, 3, 0.3)],   # W_0
+                     [(1.5, 2, 0.6), (0.2, 2, 2.0)],    # W_1
+                     [(-0.7, 2, 0.4), (0.1, 4, 0.9)]])  # W_2
+    rng = np.random.default_rng(5)
+    rot = [np.linalg.qr(rng.standard_normal((3, 3)))[0] for _ in range(6)]
+    v_loc, v_nl = oracle.pseudopotential(o, th, r, [(0, coef)], rot)
+    for b in range(6):
+        rr = float(np.linalg.norm(r[b, 0]))
+        assert v_loc[b] == pytest.approx(oracle.pp_radial(coef[0], rr), rel=1e-13)
+        assert v_nl[b] == pytest.approx(oracle.pp_radial(coef[1], rr), rel=1e-12, abs=1e-14)
+
+
+def test_pseudopotential_icosahedral_symmetry():
+    """A rotation that maps the icosahedron onto itself (a fivefold turn about a vertex) leaves
+    the quadrature unchanged: LiH with the network on, pseudopotential on Li."""
+    wl = fx.workload("lih_fp64")
+    o = oracle.Oracle(wl.system, wl.cfg)
+    th = fx.init_params(wl.system, wl.cfg, wl.param_seed)
+    r = fx.init_walkers(wl.system, 2, wl.walker_seed)
+    coef = np.array([[(0.5, 2, 0.9)], [(1.0, 2, 0.7)], [(0.6, 2, 0.5)]])
+    ico = oracle.icosahedron()
+    a = ico[0]
+    ang = 2 * np.pi / 5
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    Rsym = np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * K @ K
+    mapped = ico @ Rsym.T
+    assert all(np.min(np.linalg.norm(ico - m, axis=1)) < 1e-12 for m in mapped)
+    _, v1 = oracle.pseudopotential(o, th, r, [(0, coef)], [np.eye(3)] * 2)
+    _, v2 = oracle.pseudopotential(o, th, r, [(0, coef)], [Rsym] * 2)
+    np.testing.assert_allclose(v1, v2, rtol=1e-11, atol=1e-13)
