@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--no-mala", action="store_true", help="skip the step with the Langevin sampler")
     p.add_argument("--no-batch", action="store_true", help="skip the uneven-molecule batch")
     p.add_argument("--no-natgrad", action="store_true", help="skip the natural-gradient direction")
+    p.add_argument("--no-pp", action="store_true", help="skip the pseudopotential energies")
     p.add_argument("--mala-tau", type=float, default=0.1, help="Langevin time step (bohr^2)")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--profile-case", type=int, default=0, metavar="B",
@@ -313,6 +314,35 @@ def natgrad_leg(h, theta, r, wl, args, flush):
             "gram_fp32_tflops_incl_solve": gram_flops / (times["natural_gradient"] / 1e3) / 1e12,
             "note": "Gram matrix of the centred per-walker gradients (3xTF32 tensor cores, FP32 chunks of 8192 "
                     "parameters added in FP64), conjugate gradients in FP64, delta = Gc^T x"}
+
+
+def pp_leg(h, theta, r, wl, flush, B=512):
+    """Local and non-local pseudopotential energies (synthetic coefficients, l_max 2, on both
+    nuclei) for B of the bench walkers: B * N * 2 * 12 value-only psi evaluations per call."""
+    import torch
+
+    from paper_2307_14123_gb300 import fixtures as fx
+
+    rr = r[:B].contiguous()
+    la, sg = h.ansatz_eval(theta, rr)
+    pps = [(0, fx.synthetic_pseudopotential(2, seed=5)), (1, fx.synthetic_pseudopotential(2, seed=6))]
+    rot = torch.tensor(fx.random_rotations(B, 7), dtype=rr.dtype, device=rr.device)
+    h.pseudopotential_energy(theta, rr, pps, rot, la, sg)
+    torch.cuda.synchronize()
+    tot, reps = 0.0, 3
+    for _ in range(reps):
+        flush.fill_(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        h.pseudopotential_energy(theta, rr, pps, rot, la, sg)
+        b.record()
+        torch.cuda.synchronize()
+        tot += a.elapsed_time(b)
+    ms = tot / reps
+    n_eval = B * wl.system.n_elec * len(pps) * 12
+    return {"walkers": B, "psi_evaluations": n_eval, "ms_per_call": ms,
+            "psi_evaluations_per_s": n_eval / (ms / 1e3),
+            "note": "12-point icosahedral quadrature, every electron around both nuclei, synthetic coefficients"}
 
 
 def training_leg(dev, steps=60):
@@ -678,6 +708,7 @@ def main():
     natgrad = natgrad_leg(h, theta, r, wl, args, flush) if (world == 1 and with_grad and not args.no_natgrad) else None
     batched = batch_leg(args, dev, flush) if (world == 1 and not args.no_batch) else None
     training = training_leg(dev) if (world == 1 and not args.no_natgrad) else None
+    pseudo = pp_leg(h, theta, r, wl, flush) if (world == 1 and not args.no_pp) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -702,6 +733,7 @@ def main():
                 "batched_molecules": batched,
                 "natural_gradient": natgrad,
                 "vmc_training": training,
+                "pseudopotential": pseudo,
                 "gpu_launches": launches,
                 "clocks": clk,
                 "local_energy_only": {"value": B * world * args.steps / (jet_ms / 1e3) if jet_ms else None,

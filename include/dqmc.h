@@ -265,6 +265,37 @@ dq_status natural_gradient(dq_handle h, const void* G, const void* w, int64_t B,
 dq_status param_update(dq_handle h, void* params, const void* delta, double lr, double max_norm, double* stats,
                        void* ws, size_t ws_bytes, void* stream);
 
+/* Pseudopotentials (Eqs. pseudopotential and pp_integral): a nucleus with a
+ * pseudopotential carries a local function V and non-local channels
+ * W_0 .. W_lmax, each f(r) = sum_t beta_t r^(n_t - 2) exp(-alpha_t r^2).  The
+ * handle's system then holds the valence electrons and effective charges; the
+ * caller adds v_loc + v_nl to E_loc (and drops the Coulomb attraction of the
+ * pseudopotential nuclei if its V replaces it). */
+typedef struct {
+  int32_t nucleus;     /* index of the nucleus */
+  int32_t l_max;       /* non-local channels l = 0 .. l_max, l_max <= 3 */
+  int32_t n_terms;     /* Gaussian terms of every radial function, 1 .. 4 */
+  const double* coef;  /* host [(l_max + 2)][n_terms][3]: (beta, n, alpha), V first, then W_0 .. W_lmax */
+} dq_pseudopotential;
+
+/* pseudopotential_energy: per walker
+ *   v_loc = sum_{i,I} V_I(r_iI),
+ *   v_nl  = sum_{i,I,l} W_l(r_iI) (2l + 1) / 12 sum_k P_l(cos th_k) psi(r_i -> R_I + r_iI R_b u_k) / psi(r),
+ * the angular integral of Eq. (pp_integral) summed over m by the addition
+ * theorem and replaced by the 12-point icosahedral quadrature (vertices u_k
+ * rotated by the walker's rotation R_b, cos th_k = (R_b u_k) . (r_i - R_I) / r_iI).
+ * Every electron is displaced around every pseudopotential nucleus: B * N *
+ * n_pp * 12 value-only evaluations of psi, in one batch.
+ *   rot     [B][3][3] in   rotations (orthogonal; drawn by the caller, e.g. uniformly)
+ *   logabs, sign [B] in    log|psi| and sign of r (as from ansatz_eval / local_energy)
+ *   v_loc, v_nl  [B] out
+ * 1 <= n_pp <= 8.  Workspace: dq_pp_workspace_size. */
+dq_status dq_pp_workspace_size(dq_handle h, int64_t B, int32_t n_pp, size_t* bytes);
+dq_status pseudopotential_energy(dq_handle h, const void* params, const void* r, int64_t B, int32_t n_pp,
+                                 const dq_pseudopotential* pps, const void* rot, const void* logabs,
+                                 const int8_t* sign, void* v_loc, void* v_nl, void* ws, size_t ws_bytes,
+                                 void* stream);
+
 /* vmc_loss_weights: clipped local energies and gradient weights (Sec. 4.4,
  * Eq. 30).  Centre mu = median of e_loc (mean of the two middle values for
  * even B), half-width = clip_k * mean |e_loc - mu|; E^_b = clamp(e_loc_b);

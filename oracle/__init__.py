@@ -304,14 +304,15 @@ def legendre(l, x):
     return [1.0, x, 0.5 * (3 * x * x - 1), 0.5 * (5 * x ** 3 - 3 * x)][l]
 
 
-def pseudopotential(orc, theta, r, pps, rot):
+def pseudopotential(orc, theta, r, pps, rot, with_abs=False):
     """Local and non-local pseudopotential energies of every walker (Eqs. pseudopotential and
     pp_integral).  pps: list of (nucleus index, coef [(l_max + 2)][n_terms][3]) with the local
     function V first, then W_0 .. W_lmax; rot [B][3][3] rotations of the icosahedron (one per
     walker).  For electron i and nucleus I the angular integral of Y_lm^* psi-ratio, summed over
     m with Y_lm(Omega), is (2l + 1) / (4 pi) int P_l(cos) psi'/psi dOmega' by the addition
     theorem; the quadrature replaces int dOmega' by 4 pi / 12 times the sum over the 12 vertices.
-    Returns (v_loc [B], v_nl [B])."""
+    Returns (v_loc [B], v_nl [B]) and, with ``with_abs``, the sums of |w psi'/psi| (the size
+    of the quadrature sums, for error bounds)."""
     theta = np.asarray(theta, dtype=np.float64)
     r = np.asarray(r, dtype=np.float64).reshape(-1, orc.N, 3)
     B = r.shape[0]
@@ -320,6 +321,7 @@ def pseudopotential(orc, theta, r, pps, rot):
     la0, sg0 = orc.evaluate(theta, r)
     v_loc = np.zeros(B)
     v_nl = np.zeros(B)
+    v_abs = np.zeros(B)
     for b in range(B):
         verts = ico @ np.asarray(rot[b], dtype=np.float64).T  # R u_k
         configs, weights = [], []
@@ -341,5 +343,6 @@ def pseudopotential(orc, theta, r, pps, rot):
         la, sg = orc.evaluate(theta, np.array(configs))
         ratio = sg * sg0[b] * np.exp(la - la0[b])
         v_nl[b] = float(np.sum(np.array(weights) * ratio))
-    return v_loc, v_nl
+        v_abs[b] = float(np.sum(np.abs(np.array(weights) * ratio)))
+    return (v_loc, v_nl, v_abs) if with_abs else (v_loc, v_nl)
 

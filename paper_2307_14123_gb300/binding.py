@@ -36,11 +36,17 @@ EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_
            "dq_test_gemm_tf32x3", "mcmc_step_dev", "mala_step", "dq_create_multi", "dq_destroy_multi",
            "dq_multi_handle", "dq_multi_set_rounds", "dq_multi_rounds", "dq_multi_workspace_size",
            "ansatz_eval_multi", "local_energy_multi", "mcmc_step_multi", "grad_logpsi_multi",
-           "vmc_loss_weights_multi", "dq_autotune_multi", "dq_multi_tuning", "dq_set_msg_tile", "dq_msg_tile", "dq_autotune", "natural_gradient", "param_update"]
+           "vmc_loss_weights_multi", "dq_autotune_multi", "dq_multi_tuning", "dq_set_msg_tile", "dq_msg_tile", "dq_autotune", "natural_gradient", "param_update", "dq_pp_workspace_size",
+           "pseudopotential_energy"]
 
 
 class DQError(RuntimeError):
     pass
+
+
+class _PP(ctypes.Structure):
+    _fields_ = [("nucleus", ctypes.c_int32), ("l_max", ctypes.c_int32), ("n_terms", ctypes.c_int32),
+                ("coef", ctypes.c_void_p)]
 
 
 class _System(ctypes.Structure):
@@ -112,6 +118,8 @@ def load_library(path=None):
         lib.dq_autotune.argtypes = [P, P, P, i64, P, sz, P, P]
         lib.natural_gradient.argtypes = [P, P, P, i64, f64, i32, f64, P, P, P, sz, P]
         lib.param_update.argtypes = [P, P, P, f64, f64, P, P, sz, P]
+        lib.dq_pp_workspace_size.argtypes = [P, i64, i32, P]
+        lib.pseudopotential_energy.argtypes = [P, P, P, i64, i32, P, P, P, P, P, P, P, sz, P]
         for name in EXPORTS:
             getattr(lib, name).restype = ctypes.c_int
         lib.dq_status_string.restype = ctypes.c_char_p
@@ -346,6 +354,32 @@ class Ansatz:
         _check(self.lib.natural_gradient(self.h, _ptr(G), _ptr(w), B, float(lam), int(max_iter), float(tol),
                                          _ptr(delta), _ptr(stats), _ptr(ws), ws.numel(), self._stream()))
         return delta, stats
+
+    def pseudopotential_energy(self, params, r, pps, rot, logabs, sign):
+        """Local and non-local pseudopotential energies per walker by the 12-point icosahedral
+        quadrature.  pps: list of (nucleus index, coef [(l_max + 2)][n_terms][3] = (beta, n,
+        alpha), V first then W_0 .. W_lmax); rot [B][3][3] rotations; logabs, sign of r.
+        Returns (v_loc, v_nl)."""
+        params = self._dev(params, shape=(self.P,))
+        r = self._dev(r)
+        B = r.numel() // (3 * self.N)
+        rot = self._dev(rot, shape=(B, 3, 3))
+        keep, arr = [], (_PP * len(pps))()
+        for q, (nuc, coef) in enumerate(pps):
+            c = torch.as_tensor(coef, dtype=torch.float64).contiguous()
+            keep.append(c)
+            arr[q] = _PP(int(nuc), int(c.shape[0] - 2), int(c.shape[1]), ctypes.c_void_p(c.data_ptr()))
+        n = ctypes.c_size_t()
+        _check(self.lib.dq_pp_workspace_size(self.h, B, len(pps), ctypes.byref(n)))
+        ws = self._ws if self._ws is not None and self._ws.numel() >= n.value else torch.empty(
+            max(n.value, 256), dtype=torch.uint8, device=self.device)
+        self._ws = ws
+        v_loc = torch.empty(B, dtype=self.dtype, device=self.device)
+        v_nl = torch.empty(B, dtype=self.dtype, device=self.device)
+        _check(self.lib.pseudopotential_energy(self.h, _ptr(params), _ptr(r), B, len(pps), arr, _ptr(rot),
+                                               _ptr(logabs), _ptr(sign), _ptr(v_loc), _ptr(v_nl), _ptr(ws),
+                                               ws.numel(), self._stream()))
+        return v_loc, v_nl
 
     def param_update(self, params, delta, lr, max_norm=0.0):
         """In place: params -= lr * s * delta with s = min(1, max_norm / (lr ||delta||)) (max_norm <= 0:

@@ -1079,6 +1079,68 @@ dq_status check_multi(dq_multi g) {
   if (dev != g->device) return DQ_ERR_ARG;
   return DQ_OK;
 }
+// Pseudopotential energies: displaced configurations, their value-only forward, the
+// quadrature sums (pseudo.cu).
+struct PPPlan {
+  int64_t nconf;
+  size_t configs, la, sg, fwd, total;
+};
+PPPlan plan_pp(const dq_handle_s& h, int64_t B, int n_pp, size_t elem) {
+  PPPlan p{};
+  p.nconf = B * h.N * n_pp * 12;
+  size_t o = 0;
+  p.configs = o;
+  o += align_up((size_t)p.nconf * h.N * 3 * elem);
+  p.la = o;
+  o += align_up((size_t)p.nconf * elem);
+  p.sg = o;
+  o += align_up((size_t)p.nconf);
+  p.fwd = o;
+  o += plan_forward(h, std::max<int64_t>(1, std::min<int64_t>(p.nconf, h.max_chunk)), false, elem).total;
+  p.total = o;
+  return p;
+}
+
+template <class T>
+dq_status run_pp(const dq_handle_s& h, const T* params, const T* r, int64_t B, const PPSet& pp, const T* rot,
+                 const T* logabs, const int8_t* sign, T* v_loc, T* v_nl, unsigned char* ws, size_t ws_bytes,
+                 cudaStream_t s) {
+  const PPPlan plan = plan_pp(h, B, pp.n, sizeof(T));
+  if (!ws || ws_bytes < plan.total || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
+  T* configs = reinterpret_cast<T*>(ws + plan.configs);
+  T* la = reinterpret_cast<T*>(ws + plan.la);
+  int8_t* sg = reinterpret_cast<int8_t*>(ws + plan.sg);
+  DQ_CU(pp_displace<T>(r, h.d_R, rot, B, h.N, pp, configs, s));
+  const dq_status st = run_forward<T>(h, params, configs, plan.nconf, false, la, sg, nullptr, ws + plan.fwd,
+                                      ws_bytes - plan.fwd, s);
+  if (st != DQ_OK) return st;
+  DQ_CU(pp_combine<T>(r, h.d_R, rot, logabs, sign, la, sg, B, h.N, pp, v_loc, v_nl, s));
+  return DQ_OK;
+}
+
+dq_status make_ppset(const dq_handle_s& h, int32_t n_pp, const dq_pseudopotential* pps, PPSet* out) {
+  if (n_pp < 1 || n_pp > kMaxPP || !pps) return DQ_ERR_ARG;
+  PPSet& p = *out;
+  p = PPSet{};
+  p.n = n_pp;
+  for (int q = 0; q < n_pp; ++q) {
+    const dq_pseudopotential& d = pps[q];
+    if (d.nucleus < 0 || d.nucleus >= h.M || d.l_max < 0 || d.l_max > kMaxPPChan - 2 || d.n_terms < 1 ||
+        d.n_terms > kMaxPPTerms || !d.coef)
+      return DQ_ERR_ARG;
+    p.nucleus[q] = d.nucleus;
+    p.lmax[q] = d.l_max;
+    p.n_terms[q] = d.n_terms;
+    for (int c = 0; c < d.l_max + 2; ++c)
+      for (int t = 0; t < d.n_terms; ++t)
+        for (int x = 0; x < 3; ++x) {
+          const double v = d.coef[(c * d.n_terms + t) * 3 + x];
+          if (!isfinite(v)) return DQ_ERR_ARG;
+          p.c[(q * kMaxPPChan + c) * kMaxPPTerms + t][x] = v;
+        }
+  }
+  return DQ_OK;
+}
 }  // namespace
 }  // namespace dq
 
@@ -1392,6 +1454,33 @@ dq_status param_update(dq_handle h, void* params, const void* delta, double lr, 
                                                 h->off.total, lr, max_norm, stats, static_cast<unsigned char*>(ws),
                                                 (cudaStream_t)stream);
   return e == cudaSuccess ? DQ_OK : DQ_ERR_CUDA;
+}
+
+dq_status dq_pp_workspace_size(dq_handle h, int64_t B, int32_t n_pp, size_t* bytes) {
+  if (!h || !bytes || B < 0 || n_pp < 1 || n_pp > kMaxPP) return DQ_ERR_ARG;
+  *bytes = plan_pp(*h, std::max<int64_t>(B, 1), n_pp, elem_size(*h)).total;
+  return DQ_OK;
+}
+
+dq_status pseudopotential_energy(dq_handle h, const void* params, const void* r, int64_t B, int32_t n_pp,
+                                 const dq_pseudopotential* pps, const void* rot, const void* logabs,
+                                 const int8_t* sign, void* v_loc, void* v_nl, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  dq_status st = check_handle(h);
+  if (st != DQ_OK) return st;
+  if (B < 0) return DQ_ERR_ARG;
+  if (B == 0) return DQ_OK;
+  if (!params || !r || !rot || !logabs || !sign || !v_loc || !v_nl) return DQ_ERR_ARG;
+  PPSet pp;
+  st = make_ppset(*h, n_pp, pps, &pp);
+  if (st != DQ_OK) return st;
+  auto* w = static_cast<unsigned char*>(ws);
+  const cudaStream_t s = (cudaStream_t)stream;
+  if (h->precision == DQ_FP64)
+    return run_pp<double>(*h, (const double*)params, (const double*)r, B, pp, (const double*)rot,
+                          (const double*)logabs, sign, (double*)v_loc, (double*)v_nl, w, ws_bytes, s);
+  return run_pp<float>(*h, (const float*)params, (const float*)r, B, pp, (const float*)rot, (const float*)logabs,
+                       sign, (float*)v_loc, (float*)v_nl, w, ws_bytes, s);
 }
 
 dq_status vmc_loss_weights(dq_handle h, const void* e_loc, int64_t B, double clip_k, void* weights, double* stats,

@@ -205,6 +205,21 @@ cudaError_t gemm_tf32x3_tc_seg(const float* X, int64_t seg_rows, int64_t n_seg, 
                                int64_t ldx, const float* Wbig, const float* Wsmall, int n_out, const float* bias,
                                int bias_period, float* Y, int64_t ldy, int64_t y_seg_stride, unsigned int* status,
                                cudaStream_t s, bool accumulate = false);
+// Pseudopotentials (pseudo.cu): the coefficient set travels as a kernel parameter.
+constexpr int kMaxPP = 8, kMaxPPChan = 5, kMaxPPTerms = 4;  // nuclei, channels (V, W_0..W_3), Gaussian terms
+struct PPSet {
+  int n;                      // pseudopotentials
+  int nucleus[kMaxPP];
+  int lmax[kMaxPP];
+  int n_terms[kMaxPP];
+  double c[kMaxPP * kMaxPPChan * kMaxPPTerms][3];  // [q][channel][term]: beta, n, alpha
+};
+template <class T>
+cudaError_t pp_displace(const T* r, const double* Rn, const T* rot, int64_t B, int N, const PPSet& pp, T* configs,
+                        cudaStream_t s);
+template <class T>
+cudaError_t pp_combine(const T* r, const double* Rn, const T* rot, const T* logabs, const int8_t* sign, const T* la_c,
+                       const int8_t* sg_c, int64_t B, int N, const PPSet& pp, T* v_loc, T* v_nl, cudaStream_t s);
 // Natural-gradient direction (natgrad.cu): workspace bytes and the computation for B
 // walkers' gradients G [B][P] and weights w [B].
 size_t natgrad_workspace(int64_t B, int64_t P);

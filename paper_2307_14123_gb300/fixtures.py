@@ -392,3 +392,21 @@ def batch_workload(name="mixed_fp32"):
     prec = {"mixed_fp32": "fp32", "mixed_bf16": "bf16"}[name]
     cfg = AnsatzCfg(128, 3, 8)
     return [Workload(f"{m.lower()}_{prec}", molecule(m), cfg, B, 4, 4, prec) for m, B in BATCH_MOLECULES]
+
+
+def synthetic_pseudopotential(l_max=2, seed=0):
+    """Stand-in coefficients of a pseudopotential (no ccECP / BFD tables here): for the local
+    function V and the channels W_0 .. W_lmax, two Gaussian terms (beta, n, alpha) each, of the
+    magnitudes such tables have (a few hartree, exponents 0.5 - 5 bohr^-2)."""
+    rng = np.random.default_rng(seed)
+    coef = np.zeros((l_max + 2, 2, 3))
+    coef[0] = [(-rng.uniform(1, 3), 1, rng.uniform(0.5, 2)), (rng.uniform(0.5, 2), 2, rng.uniform(1, 5))]
+    for l in range(l_max + 1):
+        coef[1 + l] = [(rng.uniform(1, 6), 2, rng.uniform(0.5, 3)), (-rng.uniform(0.2, 1), 2, rng.uniform(2, 5))]
+    return coef
+
+
+def random_rotations(B, seed):
+    """B orthogonal 3 x 3 matrices (QR of Gaussian matrices), the rotations of the quadrature."""
+    rng = np.random.default_rng(seed)
+    return np.array([np.linalg.qr(rng.standard_normal((3, 3)))[0] for _ in range(B)])
