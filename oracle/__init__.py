@@ -16,7 +16,7 @@ Functions, each following the paper's definitions:
   draws passed in.
 * :func:`mala_step` - one Metropolis-adjusted Langevin step (Sec. 5, the
   Langevin sampler, with per-electron drift limiting) on draws passed in.
-* :func:`clipped_loss_weights` - median/MAD clipping of Sec. 4.4 and the
+* :func:`clipped_loss_weights` - median/MAD clipping (hard or logarithmic) of Sec. 4.4 and the
   per-walker weights of the gradient estimator, Eq. (30).
 * :func:`energy_estimate` - Eq. (33) and the batch-means error bar, Eq. (35).
 * :func:`pseudopotential` - local and non-local pseudopotential energies of
@@ -226,14 +226,32 @@ class Oracle:
 # ----------------------------------------------------------------------------
 # Clipping and loss weights (Sec. 4.4, Eq. 30)
 # ----------------------------------------------------------------------------
-def clipped_loss_weights(e_loc, k=5.0):
+def log_clip(e, mu, sigma):
+    """Logarithmically scaling soft clipping (Sec. 4.4, the scheme of Hermann
+    et al.): the identity inside |e - mu| <= sigma; outside, the excess
+    distance is replaced by its logarithm,
+        E^ = mu + sign(e - mu) * sigma * (1 + ln(|e - mu| / sigma)),
+    which is continuous with a continuous first derivative at |e - mu| =
+    sigma and grows without bound, but only logarithmically.  The paper
+    names the scheme without a formula; this is the reading taken."""
+    e = np.asarray(e, dtype=np.float64)
+    u = e - mu
+    a = np.abs(u)
+    out = e.copy()
+    far = a > sigma
+    out[far] = mu + np.sign(u[far]) * sigma * (1.0 + np.log(a[far] / sigma))
+    return out
+
+
+def clipped_loss_weights(e_loc, k=5.0, soft=False):
     """Clip local energies to median +- k * MAD and form gradient weights.
 
     Centre = median (mean of the two middle values for even B); half-width
     = k times the mean absolute deviation from the median (von Glehn et al.,
-    cited in Sec. 4.4).  Weights w_b = (2/B) (E^_b - mean E^), so that
-    sum_b w_b grad log|psi_b| is the estimator of Eq. (30) on clipped energies.
-    Returns (weights, clipped, centre, half_width).
+    cited in Sec. 4.4).  soft=False clamps to the window; soft=True applies
+    :func:`log_clip` (k must be > 0).  Weights w_b = (2/B) (E^_b - mean E^),
+    so that sum_b w_b grad log|psi_b| is the estimator of Eq. (30) on clipped
+    energies.  Returns (weights, clipped, centre, half_width).
     """
     e = np.asarray(e_loc, dtype=np.float64)
     B = e.size
@@ -241,7 +259,12 @@ def clipped_loss_weights(e_loc, k=5.0):
     med = s[B // 2] if B % 2 else 0.5 * (s[B // 2 - 1] + s[B // 2])
     mad = np.mean(np.abs(e - med))
     lo, hi = med - k * mad, med + k * mad
-    clipped = np.minimum(np.maximum(e, lo), hi)
+    if soft:
+        if not k > 0:
+            raise ValueError("soft clipping needs k > 0")
+        clipped = log_clip(e, med, k * mad) if mad > 0 else e.copy()
+    else:
+        clipped = np.minimum(np.maximum(e, lo), hi)
     w = (2.0 / B) * (clipped - clipped.mean())
     return w, clipped, med, k * mad
 

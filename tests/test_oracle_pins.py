@@ -571,6 +571,48 @@ def test_clipping_rule():
         assert abs(w.sum()) < 1e-14
 
 
+def test_log_clipping_properties():
+    """Logarithmic soft clipping (Sec. 4.4): the identity inside the window, value and slope
+    continuous at its edges (slope 1 on both sides), odd about the centre, strictly increasing,
+    between the hard clamp and the raw value, and logarithmic outside: equal ratios of distance
+    beyond the edge give equal steps, sigma * ln(ratio)."""
+    mu, sig = -3.7, 0.8
+    inside = mu + sig * np.linspace(-1, 1, 41)
+    assert np.array_equal(oracle.log_clip(inside, mu, sig), inside)
+    for side in (1, -1):
+        edge = mu + side * sig
+        for h in (1e-4, 1e-6):
+            out = oracle.log_clip(np.array([edge + side * h]), mu, sig)[0]
+            assert abs((out - edge) / (side * h) - 1) < 2 * h / sig
+    u = np.geomspace(1e-3, 1e4, 200) * sig
+    up, dn = oracle.log_clip(mu + u, mu, sig) - mu, oracle.log_clip(mu - u, mu, sig) - mu
+    assert np.allclose(up, -dn, rtol=0, atol=1e-12)
+    assert np.all(np.diff(up) > 0)
+    assert np.all(up <= u + 1e-12) and np.all(up >= np.minimum(u, sig) - 1e-12)
+    for t in (1.0, 2.5, 40.0):
+        for ratio in (np.e, 10.0, 1e3):
+            a, b = oracle.log_clip(np.array([mu + sig * t, mu + sig * t * ratio]), mu, sig)
+            assert abs((b - a) - sig * np.log(ratio)) < 1e-12 * max(1, abs(mu) + sig * np.log(ratio))
+
+
+def test_soft_clipped_weights():
+    """Soft-clipped weights: same centre and half-width as the hard rule, clipped energies between
+    the hard clamp and the raw values, weights summing to zero, and no clipping as k grows."""
+    rng = np.random.default_rng(3)
+    e = rng.standard_cauchy(33) - 5
+    wh, ch, medh, hwh = oracle.clipped_loss_weights(e, k=2.0)
+    ws, cs, meds, hws = oracle.clipped_loss_weights(e, k=2.0, soft=True)
+    assert meds == medh and hws == hwh
+    assert np.all(np.abs(ch - medh) <= np.abs(cs - meds) + 1e-12)
+    assert np.all(np.abs(cs - meds) <= np.abs(e - meds) + 1e-12)
+    assert np.any(np.abs(cs - meds) > hws)
+    assert abs(ws.sum()) < 1e-14
+    w_inf, c_inf, _, _ = oracle.clipped_loss_weights(e, k=1e9, soft=True)
+    assert np.array_equal(c_inf, e)
+    with pytest.raises(ValueError):
+        oracle.clipped_loss_weights(e, k=0.0, soft=True)
+
+
 # ----------------------------------------------------------------------------
 # Langevin (MALA) sampler, Sec. 5
 # ----------------------------------------------------------------------------
