@@ -308,6 +308,20 @@ dq_status pseudopotential_energy(dq_handle h, const void* params, const void* r,
 dq_status vmc_loss_weights(dq_handle h, const void* e_loc, int64_t B, double clip_k, void* weights,
                            double* stats, void* ws, size_t ws_bytes, void* stream);
 
+/* Clipping functions for vmc_loss_weights_clip (Sec. 4.4, "Gradient clipping"). */
+enum { DQ_CLIP_HARD = 0, /* E^ = clamp(e, mu - sigma, mu + sigma) (von Glehn et al.)          */
+       DQ_CLIP_LOG = 1   /* E^ = e inside |e - mu| <= sigma, else                              *
+                          *      mu + sign(e - mu) sigma (1 + ln(|e - mu| / sigma)):           *
+                          * the logarithmically growing soft window (Hermann et al.); value    *
+                          * and slope are continuous at the window's edges                     */ };
+
+/* vmc_loss_weights_clip: vmc_loss_weights with a choice of clipping function
+ * (sigma = the half-width clip_k * MAD, mu = the median).  clip_mode outside
+ * DQ_CLIP_HARD / DQ_CLIP_LOG returns DQ_ERR_ARG.  Other arguments, workspace
+ * and stats as for vmc_loss_weights; DQ_CLIP_HARD gives the same results.   */
+dq_status vmc_loss_weights_clip(dq_handle h, const void* e_loc, int64_t B, double clip_k, int32_t clip_mode,
+                                void* weights, double* stats, void* ws, size_t ws_bytes, void* stream);
+
 /* vmc_loss_weights_noalloc: the same weights and stats as vmc_loss_weights,
  * for callers that cannot allocate device memory and so cannot supply a
  * workspace (for example a plugin whose host framework owns all device

@@ -26,13 +26,14 @@ DQ_FP64, DQ_FP32, DQ_BF16_MIXED = 0, 1, 2
 (OP_EVAL, OP_LOCAL_ENERGY, OP_MCMC, OP_GRAD, OP_LOSS_WEIGHTS, OP_MALA, OP_AUTOTUNE, OP_NATGRAD,
  OP_UPDATE) = 0, 1, 2, 3, 4, 5, 6, 7, 8
 FLAG_SINGULAR, FLAG_NONFINITE = 0x1, 0x2
+CLIP_MODES = {"hard": 0, "log": 1}
 PRECISIONS = {"fp64": DQ_FP64, "fp32": DQ_FP32, "bf16": DQ_BF16_MIXED}
 
 # Every symbol declared in include/dqmc.h.
 EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_max_chunk", "dq_workspace_size",
            "ansatz_eval", "local_energy", "mcmc_step", "grad_logpsi", "vmc_loss_weights", "dq_last_device_status",
            "dq_status_string", "dq_profile_enable", "dq_profile_reset", "dq_profile_read", "dq_profile_kind_name",
-           "dq_profile_kind_count", "vmc_loss_weights_noalloc", "dq_fp64_matrix_count", "dq_test_gemm_bf16",
+           "dq_profile_kind_count", "vmc_loss_weights_noalloc", "vmc_loss_weights_clip", "dq_fp64_matrix_count", "dq_test_gemm_bf16",
            "dq_test_gemm_tf32x3", "mcmc_step_dev", "mala_step", "dq_create_multi", "dq_destroy_multi",
            "dq_multi_handle", "dq_multi_set_rounds", "dq_multi_rounds", "dq_multi_workspace_size",
            "ansatz_eval_multi", "local_energy_multi", "mcmc_step_multi", "grad_logpsi_multi",
@@ -90,6 +91,7 @@ def load_library(path=None):
         lib.grad_logpsi.argtypes = [P, P, P, i64, P, i32, P, P, sz, P]
         lib.vmc_loss_weights.argtypes = [P, P, i64, f64, P, P, P, sz, P]
         lib.vmc_loss_weights_noalloc.argtypes = [P, P, i64, f64, P, P, P]
+        lib.vmc_loss_weights_clip.argtypes = [P, P, i64, f64, ctypes.c_int32, P, P, P, sz, P]
         lib.dq_last_device_status.argtypes = [P, P, P]
         lib.dq_fp64_matrix_count.argtypes = [P, P, P]
         lib.dq_test_gemm_bf16.argtypes = [P, i64, i32, i64, P, i32, P, i32, P, i64, P, P]
@@ -393,15 +395,18 @@ class Ansatz:
                                      _ptr(ws), ws.numel(), self._stream()))
         return stats
 
-    def vmc_loss_weights(self, e_loc, clip_k=5.0):
-        """Median/MAD-clipped gradient weights; returns (weights, stats[mu, half-width, mean E^, mean E])."""
+    def vmc_loss_weights(self, e_loc, clip_k=5.0, clip="hard"):
+        """Median/MAD-clipped gradient weights; returns (weights, stats[mu, half-width, mean E^, mean E]).
+        clip: "hard" (clamp to the window) or "log" (logarithmic soft window)."""
         e_loc = self._dev(e_loc)
         B = e_loc.numel()
         w = torch.empty(B, dtype=self.dtype, device=self.device)
         stats = torch.empty(4, dtype=torch.float64, device=self.device)
         ws = self.workspace(B, OP_LOSS_WEIGHTS)
-        _check(self.lib.vmc_loss_weights(self.h, _ptr(e_loc), B, float(clip_k), _ptr(w), _ptr(stats), _ptr(ws),
-                                         ws.numel(), self._stream()))
+        if clip not in CLIP_MODES:
+            raise DQError(f"clip must be one of {sorted(CLIP_MODES)}")
+        _check(self.lib.vmc_loss_weights_clip(self.h, _ptr(e_loc), B, float(clip_k), CLIP_MODES[clip], _ptr(w),
+                                              _ptr(stats), _ptr(ws), ws.numel(), self._stream()))
         return w, stats
 
     # -- measurement ---------------------------------------------------------
@@ -696,21 +701,21 @@ def grad_logpsi(h: Ansatz, params, r, weights=None, mode=0):
     return h.grad_logpsi(params, r, weights, mode)
 
 
-def vmc_loss_weights(h: Ansatz, e_loc, clip_k=5.0):
-    return h.vmc_loss_weights(e_loc, clip_k)
+def vmc_loss_weights(h: Ansatz, e_loc, clip_k=5.0, clip="hard"):
+    return h.vmc_loss_weights(e_loc, clip_k, clip)
 
 
 def vmc_train_step(h: Ansatz, params, r, logabs, lr, damping=-0.1, max_norm=0.0, step_size=0.2, seed=0,
-                   step_counter=0, clip_k=5.0, cg_iters=200, cg_tol=1e-8):
+                   step_counter=0, clip_k=5.0, cg_iters=200, cg_tol=1e-8, clip="hard"):
     """One step of the VMC training loop with every computation in the library: a Metropolis sweep
     (positions and log|psi| updated in place), local energies, clipped-energy weights, per-walker
-    gradients, the natural-gradient direction (damping < 0: relative to the Gram matrix's mean
+    gradients (clip: "hard" or "log", see :meth:`Ansatz.vmc_loss_weights`), the natural-gradient direction (damping < 0: relative to the Gram matrix's mean
     eigenvalue) and the parameter update (params in place).  Returns a dict of device tensors:
     e_sum2 ([sum E, sum E^2] of the unclipped energies before the update), loss-weight stats,
     natural-gradient stats and update stats."""
     h.mcmc_step(params, r, logabs, 1, step_size, seed, step_counter)
     _, _, e_loc, e2 = h.local_energy(params, r, sums=True)
-    w, wstats = h.vmc_loss_weights(e_loc, clip_k)
+    w, wstats = h.vmc_loss_weights(e_loc, clip_k, clip)
     G = h.grad_logpsi(params, r, mode=1)
     delta, ngstats = h.natural_gradient(G, w, damping, cg_iters, cg_tol)
     ustats = h.param_update(params, delta, lr, max_norm)

@@ -1483,18 +1483,25 @@ dq_status pseudopotential_energy(dq_handle h, const void* params, const void* r,
                        sign, (float*)v_loc, (float*)v_nl, w, ws_bytes, s);
 }
 
-dq_status vmc_loss_weights(dq_handle h, const void* e_loc, int64_t B, double clip_k, void* weights, double* stats,
-                           void* ws, size_t ws_bytes, void* stream) {
+dq_status vmc_loss_weights_clip(dq_handle h, const void* e_loc, int64_t B, double clip_k, int32_t clip_mode,
+                                void* weights, double* stats, void* ws, size_t ws_bytes, void* stream) {
   dq_status st = check_handle(h);
   if (st != DQ_OK) return st;
   if (B < 1 || B > 65536 || !e_loc || !weights || !(clip_k > 0)) return DQ_ERR_ARG;
+  if (clip_mode != DQ_CLIP_HARD && clip_mode != DQ_CLIP_LOG) return DQ_ERR_ARG;
   if (!ws || ws_bytes < loss_scratch_bytes(B) || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
   cudaStream_t s = (cudaStream_t)stream;
+  const int soft = clip_mode == DQ_CLIP_LOG ? 1 : 0;
   if (h->precision == DQ_FP64)
-    DQ_LAUNCH(*h, PK_LOSS_WEIGHTS, launch_loss_weights<double>((const double*)e_loc, B, clip_k, (double*)weights, stats, (double*)ws, s));
+    DQ_LAUNCH(*h, PK_LOSS_WEIGHTS, launch_loss_weights<double>((const double*)e_loc, B, clip_k, (double*)weights, stats, (double*)ws, s, soft));
   else
-    DQ_LAUNCH(*h, PK_LOSS_WEIGHTS, launch_loss_weights<float>((const float*)e_loc, B, clip_k, (float*)weights, stats, (double*)ws, s));
+    DQ_LAUNCH(*h, PK_LOSS_WEIGHTS, launch_loss_weights<float>((const float*)e_loc, B, clip_k, (float*)weights, stats, (double*)ws, s, soft));
   return DQ_OK;
+}
+
+dq_status vmc_loss_weights(dq_handle h, const void* e_loc, int64_t B, double clip_k, void* weights, double* stats,
+                           void* ws, size_t ws_bytes, void* stream) {
+  return vmc_loss_weights_clip(h, e_loc, B, clip_k, DQ_CLIP_HARD, weights, stats, ws, ws_bytes, stream);
 }
 
 dq_status dq_last_device_status(dq_handle h, void* stream, uint32_t* flags) {

@@ -298,7 +298,7 @@ cudaError_t launch_esum_group(int n, const T* const* e, const int64_t* B, double
                               unsigned int* const* status, cudaStream_t s);
 template <class T>
 cudaError_t launch_loss_weights_group(int n, const T* const* e, const int64_t* B, double k, T* const* w,
-                                      double* const* stats, double* const* scratch, cudaStream_t s);
+                                      double* const* stats, double* const* scratch, cudaStream_t s, int soft = 0);
 
 // One molecule of a grouped launch: its handle, chunk dimensions, parameters and buffers.
 template <class T>
@@ -378,6 +378,6 @@ template <class T>
 cudaError_t launch_esum(const T* e, int64_t B, double* out2, unsigned int* status, cudaStream_t s);
 template <class T>
 cudaError_t launch_loss_weights(const T* e, int64_t B, double k, T* w, double* stats, double* scratch,
-                                cudaStream_t s);
+                                cudaStream_t s, int soft = 0);
 
 }  // namespace dq

@@ -287,13 +287,24 @@ struct loss_weights_kernel_args {
   int64_t B;
   int64_t Bp;
   double k;
+  int soft;
   T* w;
   double* stats;
   double* srt;
 };
 
+// Clipped energy: the clamp to [lo, hi], or (soft) the identity inside
+// |v - mu| <= sigma and mu + sign(v - mu) sigma (1 + ln(|v - mu| / sigma))
+// outside, the logarithmically growing window of Sec. 4.4.
+__device__ __forceinline__ double clip_energy(double v, double med, double sig, double lo, double hi, int soft) {
+  if (!soft) return fmin(fmax(v, lo), hi);
+  const double u = v - med, a = fabs(u);
+  if (!(a > sig)) return v;
+  return med + copysign(sig * (1.0 + log(a / sig)), u);
+}
+
 template <class T>
-__device__ __forceinline__ void loss_weights_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const T* __restrict__ e, int64_t B, int64_t Bp, double k, T* __restrict__ w,
+__device__ __forceinline__ void loss_weights_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const T* __restrict__ e, int64_t B, int64_t Bp, double k, int soft, T* __restrict__ w,
                         double* __restrict__ stats, double* __restrict__ srt) {
   __shared__ double sh[kRedThreads];
   for (int64_t i = threadIdx.x; i < Bp; i += kRedThreads) srt[i] = i < B ? (double)e[i] : INFINITY;
@@ -323,12 +334,12 @@ __device__ __forceinline__ void loss_weights_kernel_body(const int64_t bx_, cons
   }
   const double mad = block_sum_det(part, sh) / (double)B;
   const double mean_raw = block_sum_det(raw, sh) / (double)B;
-  const double lo = med - k * mad, hi = med + k * mad;
+  const double sig = k * mad, lo = med - sig, hi = med + sig;
   double cs = 0;
-  for (int64_t i = threadIdx.x; i < B; i += kRedThreads) cs += fmin(fmax((double)e[i], lo), hi);
+  for (int64_t i = threadIdx.x; i < B; i += kRedThreads) cs += clip_energy((double)e[i], med, sig, lo, hi, soft);
   const double mean_c = block_sum_det(cs, sh) / (double)B;
   for (int64_t i = threadIdx.x; i < B; i += kRedThreads)
-    w[i] = (T)((2.0 / (double)B) * (fmin(fmax((double)e[i], lo), hi) - mean_c));
+    w[i] = (T)((2.0 / (double)B) * (clip_energy((double)e[i], med, sig, lo, hi, soft) - mean_c));
   if (threadIdx.x == 0 && stats) {
     stats[0] = med;
     stats[1] = k * mad;
@@ -343,7 +354,7 @@ __global__ void __launch_bounds__(kRedThreads) loss_weights_kernel_group(const _
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
   GRP_STATIC(m_, const auto& a_ = g.a[K_];
-             loss_weights_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.e, a_.B, a_.Bp, a_.k, a_.w, a_.stats, a_.srt);)
+             loss_weights_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.e, a_.B, a_.Bp, a_.k, a_.soft, a_.w, a_.stats, a_.srt);)
 }
 
 }  // namespace
@@ -398,8 +409,8 @@ cudaError_t launch_esum(const T* e, int64_t B, double* out2, unsigned int* statu
 
 template <class T>
 cudaError_t launch_loss_weights(const T* e, int64_t B, double k, T* w, double* stats, double* scratch,
-                                cudaStream_t s) {
-  return launch_loss_weights_group<T>(1, &e, &B, k, &w, stats ? &stats : nullptr, &scratch, s);
+                                cudaStream_t s, int soft) {
+  return launch_loss_weights_group<T>(1, &e, &B, k, &w, stats ? &stats : nullptr, &scratch, s, soft);
 }
 
 // Grouped launches: one launch per sampler step over every molecule of a batch
@@ -453,14 +464,14 @@ cudaError_t launch_esum_group(int n, const T* const* e, const int64_t* B, double
 
 template <class T>
 cudaError_t launch_loss_weights_group(int n, const T* const* e, const int64_t* B, double k, T* const* w,
-                                      double* const* stats, double* const* scratch, cudaStream_t s) {
+                                      double* const* stats, double* const* scratch, cudaStream_t s, int soft) {
   if (n > kMaxGroup) return cudaErrorInvalidValue;
   Grp<loss_weights_kernel_args<T>> g{};
   for (int m = 0; m < n; ++m) {
     if (B[m] <= 0) continue;
     int64_t Bp = 1;
     while (Bp < B[m]) Bp <<= 1;
-    g.add({e[m], B[m], Bp, k, w[m], stats ? stats[m] : nullptr, scratch[m]}, 1);
+    g.add({e[m], B[m], Bp, k, soft, w[m], stats ? stats[m] : nullptr, scratch[m]}, 1);
   }
   if (g.n == 0) return cudaSuccess;
   loss_weights_kernel_group<T><<<(unsigned)g.blocks(), kRedThreads, 0, s>>>(g);
@@ -478,7 +489,7 @@ cudaError_t launch_loss_weights_group(int n, const T* const* e, const int64_t* B
   template cudaError_t launch_esum_group<T>(int, const T* const*, const int64_t*, double* const*,                  \
                                             unsigned int* const*, cudaStream_t);                                  \
   template cudaError_t launch_loss_weights_group<T>(int, const T* const*, const int64_t*, double, T* const*,       \
-                                                    double* const*, double* const*, cudaStream_t);
+                                                    double* const*, double* const*, cudaStream_t, int);
 DQ_INST_GROUP(float)
 DQ_INST_GROUP(double)
 
@@ -494,7 +505,7 @@ DQ_INST_GROUP(double)
                                              uint64_t,                                                            \
                                              const uint64_t*, unsigned long long*, cudaStream_t);                 \
   template cudaError_t launch_esum<T>(const T*, int64_t, double*, unsigned int*, cudaStream_t);                   \
-  template cudaError_t launch_loss_weights<T>(const T*, int64_t, double, T*, double*, double*, cudaStream_t);
+  template cudaError_t launch_loss_weights<T>(const T*, int64_t, double, T*, double*, double*, cudaStream_t, int);
 DQ_INST(float)
 DQ_INST(double)
 

@@ -10,6 +10,7 @@ inputs.  Tolerances (stated per test):
         signs equal.  The bound is derived from the rounding floor of an FP32
         evaluation of the method (tests/test_fp32_floor.py).
 """
+import ctypes
 import math
 import os
 
@@ -291,16 +292,37 @@ def test_mcmc_multi_step_equals_single_steps():
 # ----------------------------------------------------------------------------
 # Clipped loss weights (Sec. 4.4)
 # ----------------------------------------------------------------------------
+@pytest.mark.parametrize("clip", ["hard", "log"])
 @pytest.mark.parametrize("B", [1, 7, 4096, 5000])
-def test_loss_weights_gpu(B):
+def test_loss_weights_gpu(B, clip):
     wl = fx.workload("lih_fp64")
     h = _handle(wl.system, wl.cfg, "fp64")
     e = np.random.default_rng(B).standard_cauchy(B) * 3 - 50
-    w, stats = h.vmc_loss_weights(torch.tensor(e, device="cuda:0"), clip_k=5.0)
-    w_ref, _, med, hw = oracle.clipped_loss_weights(e, 5.0)
+    w, stats = h.vmc_loss_weights(torch.tensor(e, device="cuda:0"), clip_k=5.0, clip=clip)
+    w_ref, c_ref, med, hw = oracle.clipped_loss_weights(e, 5.0, soft=clip == "log")
     np.testing.assert_allclose(w.cpu().numpy(), w_ref, rtol=1e-12, atol=1e-15)
     s = stats.cpu().numpy()
     assert s[0] == med and s[1] == pytest.approx(hw, rel=1e-13)
+    assert s[2] == pytest.approx(c_ref.mean(), rel=1e-13, abs=1e-13)
+
+
+def test_log_clip_weights_fp32():
+    """FP32 energies, FP64 clipping arithmetic: weights equal the oracle's on the FP32 values,
+    rounded once to FP32."""
+    wl = fx.workload("lih_fp64")
+    h = _handle(wl.system, wl.cfg, "fp32")
+    e = (np.random.default_rng(11).standard_cauchy(3000) * 2 - 8).astype(np.float32)
+    w, _ = h.vmc_loss_weights(torch.tensor(e, device="cuda:0"), clip_k=3.0, clip="log")
+    w_ref = oracle.clipped_loss_weights(e.astype(np.float64), 3.0, soft=True)[0].astype(np.float32)
+    np.testing.assert_allclose(w.cpu().numpy(), w_ref, rtol=2 ** -22, atol=1e-12)
+    with pytest.raises(Exception):
+        h.vmc_loss_weights(torch.tensor(e, device="cuda:0"), clip_k=3.0, clip="tanh")
+    ws = h.workspace(len(e), 4)
+    et = torch.tensor(e, device="cuda:0")
+    wt = torch.empty_like(et)
+    st = h.lib.vmc_loss_weights_clip(h.h, ctypes.c_void_p(et.data_ptr()), len(e), 3.0, 2, ctypes.c_void_p(wt.data_ptr()),
+                                     None, ctypes.c_void_p(ws.data_ptr()), ws.numel(), None)
+    assert st == 1  # DQ_ERR_ARG: unknown clipping function
 
 
 def test_host_tensors_end_to_end():
