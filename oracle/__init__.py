@@ -67,7 +67,7 @@ def _spec_class(c_real):
                     ("n_up", ctypes.c_int32), ("n_dn", ctypes.c_int32),
                     ("D", ctypes.c_int32), ("L", ctypes.c_int32), ("K", ctypes.c_int32), ("Q", ctypes.c_int32),
                     ("rc", c_real), ("use_jastrow", ctypes.c_int32), ("use_cusp", ctypes.c_int32),
-                    ("alpha", c_real)]
+                    ("alpha", c_real), ("full_det", ctypes.c_int32)]
     return _Spec
 
 
@@ -110,7 +110,7 @@ class Oracle:
         self._R = np.ascontiguousarray(system.R, dtype=self.dt)
         self.spec = _SPECS[real](len(self._Z), self._Z.ctypes.data, self._R.ctypes.data, system.n_up, system.n_down,
                           cfg.width, cfg.n_layers, cfg.n_det, cfg.n_rbf, cfg.rbf_cutoff,
-                          int(cfg.use_jastrow), int(cfg.use_cusp), cfg.cusp_alpha)
+                          int(cfg.use_jastrow), int(cfg.use_cusp), cfg.cusp_alpha, int(cfg.full_det))
         self.N = system.n_up + system.n_down
         P = ctypes.c_int64()
         self.lib.oracle_param_count(ctypes.byref(self.spec), ctypes.byref(P))
@@ -213,12 +213,14 @@ class Oracle:
         return r, la, g, acc, lal
 
     def intermediates(self, theta, r):
-        """Final embeddings f[N][D] and orbital matrices A[2][K][nmax][nmax] of one walker."""
+        """Final embeddings f[N][D] and orbital matrices A[blocks][K][nmax][nmax] of one walker: blocks
+        = 2 (spin up, spin down; nmax = max(n_up, n_down)), or 1 (the full determinant; nmax = N)."""
         self._fp64_only()
         theta, r = self._prep(theta, r)
-        nmax = max(self.system.n_up, self.system.n_down)
+        full = bool(self.cfg.full_det)
+        nmax = self.N if full else max(self.system.n_up, self.system.n_down)
         f = np.empty((self.N, self.cfg.width))
-        A = np.zeros((2, self.cfg.n_det, nmax, nmax))
+        A = np.zeros((1 if full else 2, self.cfg.n_det, nmax, nmax))
         self.lib.oracle_intermediates(ctypes.byref(self.spec), _ptr(theta), _ptr(r[0]), _ptr(f), _ptr(A))
         return f, A
 

@@ -15,7 +15,9 @@
 //         layer, Eqs. (15)-(16) first case;
 //       - many-body orbitals kappa(f_i^L) (linear), Eq. (19), times isotropic
 //         Slater envelopes (alpha = 1, one exponential per nucleus), Eq. (20);
-//       - spin-factorised determinant pairs, Eq. (21);
+//       - spin-factorised determinant pairs, Eq. (21), or (full_det) one
+//         determinant of all N electrons per p, Eq. (22), whose rows come
+//         from the orbital network of the electron's spin;
 //       - learnable Jastrow factor, Eq. (24), and electron cusp, Eq. (25);
 //       - log-domain evaluation with log-sum-exp over determinants,
 //         Eqs. (27)-(28) (Sec. 3.5);
@@ -129,6 +131,7 @@ struct OracleSpec {
   real rc;           // Gaussian feature cutoff
   int32_t use_jastrow, use_cusp;
   real alpha;        // cusp width
+  int32_t full_det;  // 0: det A^up det A^down per p (Eq. 21); 1: det of the N x N A^p (Eq. 22)
 };
 }
 
@@ -137,8 +140,11 @@ namespace {
 // Offsets of every block of the flat parameter vector.  Order: E_spin[2][D];
 // per layer: W_h[D][D], (W1[D][Q], b1[D], W2[D][D], b2[D]) for the
 // same-spin, opposite-spin and electron-nucleus edge types, Y[M][D],
-// W_g[D][3D], b_g[D]; per spin (up, down): W_o[K n_s][D], b_o[K n_s],
-// omega[K n_s][M], zeta[K n_s][M]; c[K]; W_J1[D][D], b_J1[D], w_J2[D].
+// W_g[D][3D], b_g[D]; per spin (up, down): W_o[K n_c][D], b_o[K n_c],
+// omega[K n_c][M], zeta[K n_c][M]; c[K]; W_J1[D][D], b_J1[D], w_J2[D].
+// n_c, the orbitals per determinant, is n_s (the electrons of that spin)
+// for spin-factorised determinants and N for the full determinant; row
+// p n_c + k of a spin's block is orbital k of determinant p.
 struct Layout {
   int64_t E_spin;
   struct Layer {
@@ -165,12 +171,13 @@ struct Layout {
       y.W_g = o; o += D * 3 * D;
       y.b_g = o; o += D;
     }
-    const int64_t ns[2] = {s.n_up, s.n_dn};
+    const int64_t N = s.n_up + s.n_dn;
+    const int64_t nc[2] = {s.full_det ? N : s.n_up, s.full_det ? N : s.n_dn};
     for (int sg = 0; sg < 2; ++sg) {
-      W_o[sg] = o; o += K * ns[sg] * D;
-      b_o[sg] = o; o += K * ns[sg];
-      omega[sg] = o; o += K * ns[sg] * M;
-      zeta[sg] = o; o += K * ns[sg] * M;
+      W_o[sg] = o; o += K * nc[sg] * D;
+      b_o[sg] = o; o += K * nc[sg];
+      omega[sg] = o; o += K * nc[sg] * M;
+      zeta[sg] = o; o += K * nc[sg] * M;
     }
     c = o; o += K;
     W_J1 = o; o += D * D;
@@ -325,17 +332,22 @@ Walker<T> log_psi(const OracleSpec& s, const Layout& lay, const T* th, const T* 
   if (f_out)
     for (int k = 0; k < N * D; ++k) f_out[k] = val(f[k]);
 
-  // Orbitals x envelopes (Eqs. 8, 19, 20) and determinants (Eq. 21).
-  const int ns[2] = {s.n_up, s.n_dn}, i0[2] = {0, s.n_up};
-  const int nmax = std::max(s.n_up, s.n_dn);
+  // Orbitals x envelopes (Eqs. 8, 19, 20) and determinants: per p, either
+  // det A^{up,p} det A^{down,p} (Eq. 21) or det A^p of all N electrons
+  // (Eq. 22).  A determinant block covers electrons i0 .. i0 + n - 1 and n
+  // orbitals; the row of electron i is filled by the orbital network and
+  // envelopes of i's spin.  A_out is [blocks][K][nmax][nmax].
+  const int n_blk = s.full_det ? 1 : 2;
+  const int ns[2] = {s.full_det ? N : s.n_up, s.n_dn}, i0[2] = {0, s.n_up};
+  const int nmax = s.full_det ? N : std::max(s.n_up, s.n_dn);
   std::vector<int> sgn_p(K, 1);
   std::vector<T> ld_p(K, T(0.0));
-  for (int sg = 0; sg < 2; ++sg) {
-    const int n = ns[sg];
+  for (int blk = 0; blk < n_blk; ++blk) {
+    const int n = ns[blk];
     std::vector<T> phi(K * n);
     std::vector<std::vector<T>> A(K, std::vector<T>(n * n));
     for (int ii = 0; ii < n; ++ii) {
-      const int i = i0[sg] + ii;
+      const int i = i0[blk] + ii, sg = spin(i);
       affine(th + lay.W_o[sg], th + lay.b_o[sg], &f[i * D], K * n, D, phi.data());
       for (int p = 0; p < K; ++p)
         for (int k = 0; k < n; ++k) {
@@ -350,7 +362,7 @@ Walker<T> log_psi(const OracleSpec& s, const Layout& lay, const T* th, const T* 
       if (A_out)
         for (int ii = 0; ii < n; ++ii)
           for (int k = 0; k < n; ++k)
-            A_out[((sg * K + p) * nmax + ii) * nmax + k] = val(A[p][ii * n + k]);
+            A_out[((blk * K + p) * nmax + ii) * nmax + k] = val(A[p][ii * n + k]);
       int sd;
       T ld;
       slogdet(A[p], n, &sd, &ld);

@@ -213,6 +213,7 @@ class AnsatzCfg:
     use_jastrow: int = 1
     use_cusp: int = 1
     cusp_alpha: float = 1.0
+    full_det: int = 0        # 1: one determinant of all N electrons per p (Eq. 22)
 
 
 def param_layout(system: System, cfg: AnsatzCfg):
@@ -221,8 +222,10 @@ def param_layout(system: System, cfg: AnsatzCfg):
     Order: E_spin[2][D]; per layer l: W_h[D][D], then for edge types
     (same-spin, opposite-spin, electron-nucleus) W1[D][n_rbf], b1[D],
     W2[D][D], b2[D]; Y[M][D]; W_g[D][3D], b_g[D]; then per spin (up, down)
-    W_o[K*n_s][D], b_o[K*n_s], omega[K*n_s][M], zeta[K*n_s][M]; then c[K];
-    W_J1[D][D], b_J1[D], w_J2[D].  Matrices are [out][in], row-major.
+    W_o[K*n_c][D], b_o[K*n_c], omega[K*n_c][M], zeta[K*n_c][M]; then c[K];
+    W_J1[D][D], b_J1[D], w_J2[D].  Matrices are [out][in], row-major.  n_c, the
+    orbitals per determinant, is n_s (that spin's electrons) for spin-factorised
+    determinants and N for the full determinant (cfg.full_det).
     """
     D, L, K, Q, M = cfg.width, cfg.n_layers, cfg.n_det, cfg.n_rbf, system.n_nuc
     out = [("E_spin", (2, D), "normal")]
@@ -233,9 +236,12 @@ def param_layout(system: System, cfg: AnsatzCfg):
                     (f"W2_{t}{l}", (D, D), "xavier"), (f"b2_{t}{l}", (D,), "zero")]
         out.append((f"Y{l}", (M, D), "normal"))
         out += [(f"W_g{l}", (D, 3 * D), "xavier"), (f"b_g{l}", (D,), "zero")]
+    N = system.n_up + system.n_down
+    full = bool(getattr(cfg, "full_det", 0))
     for s, ns in (("up", system.n_up), ("dn", system.n_down)):
-        out += [(f"W_o_{s}", (K * ns, D), "xavier"), (f"b_o_{s}", (K * ns,), "zero"),
-                (f"omega_{s}", (K * ns, M), "one"), (f"zeta_{s}", (K * ns, M), "zeta")]
+        nc = N if full else ns
+        out += [(f"W_o_{s}", (K * nc, D), "xavier"), (f"b_o_{s}", (K * nc,), "zero"),
+                (f"omega_{s}", (K * nc, M), "one"), (f"zeta_{s}", (K * nc, M), "zeta")]
     out.append(("c", (K,), "one"))
     out += [("W_J1", (D, D), "xavier"), ("b_J1", (D,), "zero"), ("w_J2", (1, D), "xavier")]
     return out

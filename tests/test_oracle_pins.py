@@ -9,6 +9,7 @@ statement with its batch-means error bar (Eq. 35), a published known-answer
 vector, or a hand-computable special case of the network with one-hot
 weights (which pins every layout and index convention).
 """
+import dataclasses
 import itertools
 import math
 import os
@@ -260,17 +261,19 @@ def test_nuclear_repulsion(name, vnn):
 # Symmetries of the full random-weight ansatz
 # ----------------------------------------------------------------------------
 def _random_case(name):
-    if name == "small":
+    if name.startswith("small"):
         sys_, cfg = small_system(), fx.AnsatzCfg(8, 2, 2)
     else:
         wl = fx.workload("lih_fp64")
         sys_, cfg = wl.system, wl.cfg
+    if name.endswith("_full"):
+        cfg = dataclasses.replace(cfg, full_det=1)
     th = fx.init_params(sys_, cfg, 3)
     r = fx.init_walkers(sys_, 6, 3)
     return sys_, cfg, th, r
 
 
-@pytest.mark.parametrize("name", ["small", "lih"])
+@pytest.mark.parametrize("name", ["small", "lih", "small_full", "lih_full"])
 def test_antisymmetry(name):
     """Exchange of two same-spin electrons flips the sign only (Eqs. 3, 9)."""
     sys_, cfg, th, r = _random_case(name)
@@ -284,9 +287,11 @@ def test_antisymmetry(name):
     np.testing.assert_allclose(b["e_loc"], a["e_loc"], rtol=1e-9, atol=1e-9)
 
 
-def test_opposite_spin_exchange_is_not_a_symmetry():
-    """Spins are fixed (Sec. 2.2): exchanging an up and a down electron changes psi."""
-    sys_, cfg, th, r = _random_case("small")
+@pytest.mark.parametrize("name", ["small", "small_full"])
+def test_opposite_spin_exchange_is_not_a_symmetry(name):
+    """Spins are fixed (Sec. 2.2): exchanging an up and a down electron changes psi; the full
+    determinant (Eq. 22) is not antisymmetric under it either (Sec. 3.3)."""
+    sys_, cfg, th, r = _random_case(name)
     o = oracle.Oracle(sys_, cfg)
     la, _ = o.evaluate(th, r)
     rs = r.copy()
@@ -296,8 +301,9 @@ def test_opposite_spin_exchange_is_not_a_symmetry():
 
 
 @pytest.mark.parametrize("reflect", [False, True])
-def test_rigid_motion_invariance(reflect):
-    sys_, cfg, th, r = _random_case("small")
+@pytest.mark.parametrize("name", ["small", "small_full"])
+def test_rigid_motion_invariance(reflect, name):
+    sys_, cfg, th, r = _random_case(name)
     o = oracle.Oracle(sys_, cfg)
     a = o.local_energy(th, r)
     rng = np.random.default_rng(5)
@@ -326,10 +332,90 @@ def test_orbital_equivariance():
     np.testing.assert_allclose(A2[1], A[1][:, perm_dn], rtol=1e-12, atol=1e-14)
 
 
+def _embed_factorised(sys_, cfg, th):
+    """Full-determinant parameters whose N x N matrices are block diagonal, diag(A^up, A^down):
+    orbital k < n_up of spin up and orbital k >= n_up of spin down copy the factorised orbitals,
+    the others are zero (W_o and b_o rows 0, so phi = 0)."""
+    cfg_f = dataclasses.replace(cfg, full_det=1)
+    off, off_f = fx.param_offsets(sys_, cfg), fx.param_offsets(sys_, cfg_f)
+    th_f = np.zeros(fx.param_count(sys_, cfg_f))
+    for nm in ("omega_up", "zeta_up", "omega_dn", "zeta_dn"):
+        setp(th_f, sys_, cfg_f, nm, 1.0)
+    for name, (o, shape) in off.items():
+        if name in off_f and off_f[name][1] == shape:
+            th_f[off_f[name][0]:off_f[name][0] + int(np.prod(shape))] = th[o:o + int(np.prod(shape))]
+    N, K, nu = sys_.n_elec, cfg.n_det, sys_.n_up
+    for sname, ns, k0 in (("up", nu, 0), ("dn", sys_.n_down, nu)):
+        for blk in ("W_o", "b_o", "omega", "zeta"):
+            o, shape = off[f"{blk}_{sname}"]
+            src = th[o:o + int(np.prod(shape))].reshape(shape[0], -1)
+            of, shape_f = off_f[f"{blk}_{sname}"]
+            dst = th_f[of:of + int(np.prod(shape_f))].reshape(shape_f[0], -1)
+            for p in range(K):
+                dst[p * N + k0:p * N + k0 + ns] = src[p * ns:(p + 1) * ns]
+    return cfg_f, th_f
+
+
+@pytest.mark.parametrize("name", ["small", "lih"])
+def test_full_determinant_block_diagonal_reduces_to_factorised(name):
+    """With block-diagonal matrices the generalised Laplace expansion (Eq. 23) keeps one term, so
+    the full determinant (Eq. 22) equals det A^up det A^down (Eq. 21): log|psi|, sign and E_loc
+    agree with the factorised ansatz."""
+    sys_, cfg, th, r = _random_case(name)
+    cfg_f, th_f = _embed_factorised(sys_, cfg, th)
+    a = oracle.Oracle(sys_, cfg).local_energy(th, r)
+    b = oracle.Oracle(sys_, cfg_f).local_energy(th_f, r)
+    np.testing.assert_allclose(b["logabs"], a["logabs"], rtol=1e-12, atol=1e-12)
+    assert np.array_equal(b["sign"], a["sign"])
+    np.testing.assert_allclose(b["e_loc"], a["e_loc"], rtol=1e-10, atol=1e-10)
+    _, A = oracle.Oracle(sys_, cfg_f).intermediates(th_f, r[:1])
+    assert A.shape == (1, cfg.n_det, sys_.n_elec, sys_.n_elec)
+    nu = sys_.n_up
+    assert np.all(A[0, :, :nu, nu:] == 0) and np.all(A[0, :, nu:, :nu] == 0)
+
+
+def test_full_determinant_laplace_expansion():
+    """Eq. (23) by brute force on the oracle's own full matrices: det A^p = sum over n_up-subsets S of
+    the orbitals of eps_S det A^{up,S} det A^{down,S-bar} (Leibniz determinants); with the Jastrow
+    factor and cusp off, log|psi| = log|sum_p c_p det A^p|.  Each matrix row is the orbital network
+    of that electron's spin, checked against the embeddings."""
+    sys_ = fx.System(Z=np.array([3.0, 1.0]), R=np.array([[0, 0, 0], [0.2, 0.5, 1.9]]), n_up=3, n_down=2)
+    cfg = fx.AnsatzCfg(8, 2, 3, use_jastrow=0, use_cusp=0, full_det=1)
+    o = oracle.Oracle(sys_, cfg)
+    th = fx.init_params(sys_, cfg, 4)
+    setp(th, sys_, cfg, "c", [1.0, -0.6, 0.3])
+    r = fx.init_walkers(sys_, 4, 2)
+    la, sg = o.evaluate(th, r)
+    N, K, nu = 5, 3, 3
+    off = fx.param_offsets(sys_, cfg)
+    get = lambda nm: th[off[nm][0]:off[nm][0] + int(np.prod(off[nm][1]))].reshape(off[nm][1])
+    for b in range(r.shape[0]):
+        f, A = o.intermediates(th, r[b:b + 1])
+        d = np.linalg.norm(r[b][:, None, :] - sys_.R[None], axis=-1)
+        psi = 0.0
+        for p in range(K):
+            for i in range(N):
+                s = "up" if i < nu else "dn"
+                phi = get(f"W_o_{s}") @ f[i] + get(f"b_o_{s}")
+                env = (get(f"omega_{s}") * np.exp(-get(f"zeta_{s}") * d[i][None, :])).sum(axis=1)
+                np.testing.assert_allclose(A[0, p, i], (phi * env)[p * N:(p + 1) * N], rtol=1e-12, atol=1e-14)
+            Ap = A[0, p]
+            lap = 0.0
+            for S in itertools.combinations(range(N), nu):
+                Sb = [k for k in range(N) if k not in S]
+                perm = list(S) + Sb
+                eps = (-1) ** sum(1 for i in range(N) for j in range(i + 1, N) if perm[i] > perm[j])
+                lap += eps * _leibniz(Ap[:nu][:, list(S)]) * _leibniz(Ap[nu:][:, Sb])
+            assert lap == pytest.approx(_leibniz(Ap), rel=1e-12, abs=1e-300)
+            psi += get("c")[p] * lap
+        assert la[b] == pytest.approx(math.log(abs(psi)), rel=1e-12, abs=1e-12)
+        assert sg[b] == np.sign(psi)
+
+
 # ----------------------------------------------------------------------------
 # Derivatives against finite differences
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("name", ["small", "lih"])
+@pytest.mark.parametrize("name", ["small", "lih", "small_full", "lih_full"])
 def test_coordinate_derivatives_finite_differences(name):
     sys_, cfg, th, r = _random_case(name)
     o = oracle.Oracle(sys_, cfg)
@@ -352,7 +438,10 @@ def test_coordinate_derivatives_finite_differences(name):
         assert out["lap"][b] == pytest.approx(lap_fd, rel=1e-5, abs=1e-5)
         V = o.potential(r[b:b + 1])[0]
         e_fd = -0.5 * (lap_fd + np.sum(out["grad"][b] ** 2)) + V
-        assert out["e_loc"][b] == pytest.approx(e_fd, rel=1e-5, abs=1e-5)
+        # E_loc inherits the Laplacian's finite-difference error, which near a node (large |lap|,
+        # cancelled by |grad|^2) is far above 1e-5 |E_loc|.
+        tol = 0.5 * 1e-5 * max(1.0, abs(lap_fd)) + 1e-5 * max(1.0, abs(e_fd))
+        assert abs(out["e_loc"][b] - e_fd) <= tol, (out["e_loc"][b], e_fd, tol)
 
 
 def test_parameter_gradient_finite_differences():
