@@ -35,9 +35,10 @@
  *     for the edge types same-spin, opposite-spin, electron-nucleus:
  *       W1[D][n_rbf], b1[D], W2[D][D], b2[D];
  *     Y[n_nuc][D]; W_g[D][3D], b_g[D];
- *   for spin up then spin down (n_s electrons of that spin):
- *     W_o[K n_s][D], b_o[K n_s], omega[K n_s][n_nuc], zeta[K n_s][n_nuc]
- *     (orbital row p*n_s + k is orbital k of determinant p);
+ *   for spin up then spin down (n_c orbitals per determinant: n_s, the
+ *   electrons of that spin, or N with full_det):
+ *     W_o[K n_c][D], b_o[K n_c], omega[K n_c][n_nuc], zeta[K n_c][n_nuc]
+ *     (orbital row p*n_c + k is orbital k of determinant p);
  *   c[K]; W_J1[D][D], b_J1[D], w_J2[D].
  *
  * Memory and dtypes.  Every array argument of a compute call is DEVICE memory
@@ -119,6 +120,11 @@ typedef struct {
   int32_t use_jastrow;
   int32_t use_cusp;
   double cusp_alpha;  /* alpha of Eq. (25); 1 gives the Kato cusp     */
+  int32_t full_det;   /* 0: psi = sum_p c_p det A^{up,p} det A^{down,p} (Eq. 21);
+                       * 1: psi = sum_p c_p det A^p, one N x N matrix per p
+                       *    whose row i comes from the orbital network and
+                       *    envelopes of electron i's spin (Eq. 22); needs
+                       *    N <= 32.  Other values: DQ_ERR_ARG.           */
 } dq_ansatz_cfg;
 
 typedef struct dq_handle_s* dq_handle;

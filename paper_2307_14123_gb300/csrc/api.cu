@@ -19,7 +19,8 @@
 
 namespace dq {
 
-ParamOffsets make_offsets(int D, int L, int K, int Q, int M, int n_up, int n_dn) {
+// nc_up, nc_dn: orbitals per determinant of the spin-up and spin-down networks.
+ParamOffsets make_offsets(int D, int L, int K, int Q, int M, int nc_up, int nc_dn) {
   ParamOffsets o{};
   int64_t p = 0;
   o.E_spin = p;
@@ -45,7 +46,7 @@ ParamOffsets make_offsets(int D, int L, int K, int Q, int M, int n_up, int n_dn)
     y.b_g = p;
     p += D;
   }
-  const int ns[2] = {n_up, n_dn};
+  const int ns[2] = {nc_up, nc_dn};
   for (int s = 0; s < 2; ++s) {
     o.W_o[s] = p;
     p += (int64_t)K * ns[s] * D;
@@ -110,7 +111,7 @@ constexpr int kT3PerLayer = 14;  // D x D blocks per layer: W_g 2 x 3, W_h 2, W2
 // TF32 splits: the layers' blocks, then W_o of both spins (high, low; K * nmax x D
 // each), then the Jastrow map W_J1 (high, low; D x D)
 inline int64_t t3_weight_floats(const dq_handle_s& h) {
-  const int64_t nmax = std::max(h.n_up, h.n_dn);
+  const int64_t nmax = h.det_n();
   return (int64_t)h.L * kT3PerLayer * h.D * h.D + 4 * h.K * nmax * h.D + 2 * (int64_t)h.D * h.D;
 }
 // Views of the split weights; part 0 = TF32 high, 1 = low.
@@ -126,7 +127,7 @@ struct T3Weights {
   float* wj(int part) const { return base + (int64_t)L * kT3PerLayer * DD + 4 * WoD + part * DD; }
 };
 inline T3Weights t3_weights(const dq_handle_s& h, void* base) {
-  return T3Weights{static_cast<float*>(base), (int64_t)h.D * h.D, (int64_t)h.K * std::max(h.n_up, h.n_dn) * h.D,
+  return T3Weights{static_cast<float*>(base), (int64_t)h.D * h.D, (int64_t)h.K * h.det_n() * h.D,
                    h.L};
 }
 // Splits every weight matrix that runs on the 3 x TF32 GEMM (once per call).
@@ -141,7 +142,7 @@ cudaError_t split_t3_weights(const dq_handle_s& h, const float* params, const T3
   const int nsp[2] = {h.n_up, h.n_dn};
   for (int sg = 0; sg < 2; ++sg) {
     if (nsp[sg] == 0) continue;
-    const cudaError_t e = split_tf32(params + h.off.W_o[sg], w.wo(sg, 0), w.wo(sg, 1), (int64_t)h.K * nsp[sg] * h.D, s);
+    const cudaError_t e = split_tf32(params + h.off.W_o[sg], w.wo(sg, 0), w.wo(sg, 1), (int64_t)h.K * h.ncol(sg) * h.D, s);
     if (e != cudaSuccess) return e;
   }
   if (h.use_jastrow) return split_tf32(params + h.off.W_J1, w.wj(0), w.wj(1), w.DD, s);
@@ -151,7 +152,7 @@ cudaError_t split_t3_weights(const dq_handle_s& h, const float* params, const T3
 FwdPlan plan_forward(const dq_handle_s& h, int64_t Bc, bool jets, size_t elem) {
   const int64_t E = h.edges.n_all, N = h.N, D = h.D, K = h.K;
   const int64_t ej = jets ? 3 : 1, C = jets ? 3 * N + 2 : 1;
-  const int64_t nmax = std::max(h.n_up, h.n_dn);
+  const int64_t nmax = h.det_n();
   FwdPlan p{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -303,8 +304,7 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
   const int C = jets ? 3 * N + 2 : 1;
   const int ej = jets ? 3 : 1;
   const int E = h.edges.n_all;
-  const int nmax = std::max(h.n_up, h.n_dn);
-  const int Wo = K * nmax;
+  const int Wo = K * h.det_n();
   const int kb = jets ? 0 : kValueOffset;
   DQ_LAUNCH(h, kb + PK_LAYER0, launch_layer0_node<T>(h, FwdDims{Bmax, N, h.n_up, h.n_dn, h.M, D, K, h.Q, C}, params, bf, s));
   for (int64_t b0 = 0; b0 < B; b0 += Bmax) {
@@ -374,7 +374,7 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
       T3JobDesc jd[2];
       for (int sg = 0; sg < 2; ++sg)
         jd[sg] = T3JobDesc{reinterpret_cast<const float*>(bf.F) + (int64_t)i0[sg] * C * D, (int64_t)ns[sg] * C, nb,
-                           (int64_t)N * C * D, D, D, wo_t3(sg, 0), wo_t3(sg, 1), K * ns[sg],
+                           (int64_t)N * C * D, D, D, wo_t3(sg, 0), wo_t3(sg, 1), K * h.ncol(sg),
                            reinterpret_cast<const float*>(params + h.off.b_o[sg]), C,
                            reinterpret_cast<float*>(bf.phi) + (int64_t)i0[sg] * C * Wo, Wo, (int64_t)N * C * Wo,
                            false};
@@ -387,7 +387,7 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
       {
         DQ_LAUNCH(h, kb + PK_GEMM_ORBITAL,
                   gemm_nt<T>(bf.F + (int64_t)i0[sg] * C * D, mx, params + h.off.W_o[sg], params + h.off.b_o[sg], C,
-                             bf.phi + (int64_t)i0[sg] * C * Wo, my, nb * ns[sg] * C, K * ns[sg], D, false, s));
+                             bf.phi + (int64_t)i0[sg] * C * Wo, my, nb * ns[sg] * C, K * h.ncol(sg), D, false, s));
       }
     }
     DQ_LAUNCH(h, kb + PK_ORBITAL_DET, launch_orbital_det<T>(h, d, params, bf, s));
@@ -425,7 +425,7 @@ struct GradPlan {
 
 GradPlan plan_grad(const dq_handle_s& h, int64_t Bc, size_t elem) {
   const int64_t E = h.edges.n_all, N = h.N, D = h.D, K = h.K, L = h.L, M = h.M, Q = h.Q;
-  const int64_t nmax = std::max(h.n_up, h.n_dn), Wo = K * nmax;
+  const int64_t nmax = h.det_n(), Wo = K * nmax;
   GradPlan p{};
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -480,7 +480,7 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
   if (ws == nullptr || ws_bytes < pl.total || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
   auto buf = [&](size_t off) { return reinterpret_cast<T*>(ws + off); };
   const int N = h.N, D = h.D, K = h.K, L = h.L, M = h.M, Q = h.Q, E = h.edges.n_all;
-  const int nmax = std::max(h.n_up, h.n_dn), Wo = K * nmax;
+  const int Wo = K * h.det_n();
   const int64_t P = h.off.total;
   const ParamOffsets& off = h.off;
   const size_t el = sizeof(T);
@@ -503,7 +503,7 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
       }
       const int nsp[2] = {h.n_up, h.n_dn};
       for (int sg = 0; sg < 2; ++sg)
-        if (nsp[sg] > 0) DQ_CU(split_tf32_t(params + off.W_o[sg], K * nsp[sg], D, w3t.wo(sg, 0), w3t.wo(sg, 1), s));
+        if (nsp[sg] > 0) DQ_CU(split_tf32_t(params + off.W_o[sg], K * h.ncol(sg), D, w3t.wo(sg, 0), w3t.wo(sg, 1), s));
     }
   }
   const int ns[2] = {h.n_up, h.n_dn}, i0[2] = {0, h.n_up};
@@ -586,13 +586,13 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
       if (use_t3)
         DQ_LAUNCH(h, kValueOffset + PK_GEMM_ORBITAL,
                   gemm_tf32x3_tc_seg(reinterpret_cast<const float*>(F(L)) + (int64_t)i0[sg] * D, ns[sg], nb,
-                                     (int64_t)N * D, D, D, w3.wo(sg, 0), w3.wo(sg, 1), K * ns[sg],
+                                     (int64_t)N * D, D, D, w3.wo(sg, 0), w3.wo(sg, 1), K * h.ncol(sg),
                                      reinterpret_cast<const float*>(params + off.b_o[sg]), 1,
                                      reinterpret_cast<float*>(v.phi) + (int64_t)i0[sg] * Wo, Wo, (int64_t)N * Wo,
                                      h.d_status, s));
       else
         DQ_LAUNCH(h, kValueOffset + PK_GEMM_ORBITAL, gemm_nt<T>(F(L) + (int64_t)i0[sg] * D, mx, params + off.W_o[sg], params + off.b_o[sg],
-                                           1, v.phi + (int64_t)i0[sg] * Wo, my, nb * ns[sg], K * ns[sg], D, false, s));
+                                           1, v.phi + (int64_t)i0[sg] * Wo, my, nb * ns[sg], K * h.ncol(sg), D, false, s));
     }
     DQ_LAUNCH(h, kValueOffset + PK_ORBITAL_DET, launch_orbital_det<T>(h, d, params, v, s));
     if (h.use_jastrow) {
@@ -619,25 +619,26 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
       if (ns[sg] == 0) continue;
       const int64_t blk = (int64_t)Wo * M;
       const RowMap me{1, 4 * blk, 0};
-      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(envbar + (sg * 2 + 0) * blk, me, nullptr, rm(1), 1, K * ns[sg] * M, 1,
+      const int nc = K * h.ncol(sg);  // orbitals of this spin's network
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(envbar + (sg * 2 + 0) * blk, me, nullptr, rm(1), 1, nc * M, 1,
                                          off.omega[sg], 1));
-      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(envbar + (sg * 2 + 1) * blk, me, nullptr, rm(1), 1, K * ns[sg] * M, 1,
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(envbar + (sg * 2 + 1) * blk, me, nullptr, rm(1), 1, nc * M, 1,
                                          off.zeta[sg], 1));
       const RowMap mp{(int64_t)ns[sg], (int64_t)N * Wo, Wo};
       const RowMap mf{(int64_t)ns[sg], (int64_t)N * D, D};
       const T* pb = phibar + (int64_t)i0[sg] * Wo;
-      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(pb, mp, F(L) + (int64_t)i0[sg] * D, mf, ns[sg], K * ns[sg], D, off.W_o[sg], D));
-      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(pb, mp, nullptr, rm(1), ns[sg], K * ns[sg], 1, off.b_o[sg], 1));
-      // tensor cores when the rows of phi-bar suit the tensor maps (K * n_s and Wo multiples of 4)
-      if (use_t3 && (K * ns[sg]) % 4 == 0 && Wo % 4 == 0)
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(pb, mp, F(L) + (int64_t)i0[sg] * D, mf, ns[sg], nc, D, off.W_o[sg], D));
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(pb, mp, nullptr, rm(1), ns[sg], nc, 1, off.b_o[sg], 1));
+      // tensor cores when the rows of phi-bar suit the tensor maps (K * n_c and Wo multiples of 4)
+      if (use_t3 && nc % 4 == 0 && Wo % 4 == 0)
         DQ_LAUNCH(h, PK_BWD_GEMM,
-                  gemm_tf32x3_tc_seg(reinterpret_cast<const float*>(pb), ns[sg], nb, (int64_t)N * Wo, K * ns[sg], Wo,
+                  gemm_tf32x3_tc_seg(reinterpret_cast<const float*>(pb), ns[sg], nb, (int64_t)N * Wo, nc, Wo,
                                      w3t.wo(sg, 0), w3t.wo(sg, 1), D, nullptr, 1,
                                      reinterpret_cast<float*>(fbar) + (int64_t)i0[sg] * D, D, (int64_t)N * D,
                                      h.d_status, s));
       else
         DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(pb, mp, params + off.W_o[sg], fbar + (int64_t)i0[sg] * D, mf,
-                                           nb * ns[sg], D, K * ns[sg], false, s));
+                                           nb * ns[sg], D, nc, false, s));
     }
     if (h.use_jastrow) DQ_LAUNCH(h, PK_BWD_UPDATE, launch_add_rows<T>(fbar, sbar, nb, N, D, s));
     for (int l = L - 1; l >= 0; --l) {
@@ -941,12 +942,12 @@ dq_status run_forward_multi(const dq_multi_s& g, const T* const* params, const T
       const dq_handle_s& h = *g.h[m];
       const FwdDims& d = mf[m].d;
       if (d.Bc <= 0) continue;
-      const int Wo = h.K * std::max(h.n_up, h.n_dn), C = d.C, D = h.D, N = h.N;
+      const int Wo = h.K * h.det_n(), C = d.C, D = h.D, N = h.N;
       const int ns[2] = {h.n_up, h.n_dn}, i0[2] = {0, h.n_up};
       for (int sp = 0; sp < 2; ++sp)
         jd[nj++] = T3JobDesc{reinterpret_cast<const float*>(mf[m].b.F) + (int64_t)i0[sp] * C * D,
                              (int64_t)ns[sp] * C, d.Bc, (int64_t)N * C * D, D, D, w3[m].wo(sp, 0), w3[m].wo(sp, 1),
-                             h.K * ns[sp], reinterpret_cast<const float*>(params[m] + h.off.b_o[sp]), C,
+                             h.K * h.ncol(sp), reinterpret_cast<const float*>(params[m] + h.off.b_o[sp]), C,
                              reinterpret_cast<float*>(mf[m].b.phi) + (int64_t)i0[sp] * C * Wo, Wo,
                              (int64_t)N * C * Wo, false};
     }
@@ -1174,6 +1175,8 @@ dq_status dq_create(const dq_system* sys, const dq_ansatz_cfg* cfg, int32_t prec
       cfg->n_det < 1 || cfg->n_det > 128 || cfg->n_rbf < 8 || cfg->n_rbf % 8 || cfg->n_rbf > 64 ||
       !(cfg->rbf_cutoff > 0) || !(cfg->cusp_alpha > 0))
     return DQ_ERR_SHAPE;
+  if (cfg->full_det != 0 && cfg->full_det != 1) return DQ_ERR_ARG;
+  if (cfg->full_det && N > kMaxSpin) return DQ_ERR_SHAPE;  // the N x N matrix obeys the spin-block limit
   for (int I = 0; I < M; ++I) {
     if (!isfinite(sys->Z[I])) return DQ_ERR_ARG;
     for (int x = 0; x < 3; ++x)
@@ -1198,7 +1201,8 @@ dq_status dq_create(const dq_system* sys, const dq_ansatz_cfg* cfg, int32_t prec
   h->alpha = cfg->cusp_alpha;
   h->use_jastrow = cfg->use_jastrow ? 1 : 0;
   h->use_cusp = cfg->use_cusp ? 1 : 0;
-  h->off = make_offsets(h->D, h->L, h->K, h->Q, M, n_up, n_dn);
+  h->full_det = cfg->full_det;
+  h->off = make_offsets(h->D, h->L, h->K, h->Q, M, h->ncol(0), h->ncol(1));
   double vnn = 0;
   for (int I = 0; I < M; ++I)
     for (int J = I + 1; J < M; ++J) {

@@ -98,13 +98,13 @@ __global__ void __launch_bounds__(128)
     bwd_det_kernel(const T* __restrict__ phi, const T* __restrict__ geo, const T* __restrict__ params,
                    const T* __restrict__ beta, int64_t Bc, int N, int n_up, int M, int K, int Wo, int E, int n_ee,
                    int64_t om_up, int64_t om_dn, int64_t ze_up, int64_t ze_dn, T* __restrict__ phibar,
-                   T* __restrict__ envbar) {
+                   T* __restrict__ envbar, int full) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int warps = blockDim.x / 32;
   const int64_t gw = (int64_t)blockIdx.x * warps + warp;
   const int n_dn = N - n_up;
-  const int nmax = n_up > n_dn ? n_up : n_dn;
+  const int nmax = full ? N : (n_up > n_dn ? n_up : n_dn);
   const int nn = nmax * nmax;
   const size_t per_warp = (size_t)nn * (2 * sizeof(double) + 5 * sizeof(T)) + 32 * sizeof(int);
   unsigned char* base = smem_raw + warp * ((per_warp + 15) / 16 * 16);
@@ -120,19 +120,25 @@ __global__ void __launch_bounds__(128)
   const int64_t b = gw / (2 * K);
   const int s = (int)((gw / K) % 2);
   const int p = (int)(gw % K);
-  const int n = s == 0 ? n_up : n_dn;
-  const int i0 = s == 0 ? 0 : n_up;
+  // Block s: the spin-s matrix of Eq. (21), or (full) the N x N matrix of
+  // Eq. (22) for s = 0 and nothing for s = 1.  Row ii is electron i0 + ii,
+  // with the orbitals and envelopes of its own spin.
+  const int n = full ? (s == 0 ? N : 0) : (s == 0 ? n_up : n_dn);
+  const int i0 = (full || s == 0) ? 0 : n_up;
   if (n == 0) return;
-  const T* om = params + (s == 0 ? om_up : om_dn);
-  const T* ze = params + (s == 0 ? ze_up : ze_dn);
   const T* gb = geo + b * E * 4;
   const T* phib = phi + b * N * Wo;
   const double bp = (double)beta[b * K + p];
-  // envbar staging [Bc][spin][omega|zeta][K*nmax][M]; rows o = p*n + k
-  T* ebo = envbar + ((b * 2 + s) * 2 + 0) * (int64_t)K * nmax * M;
-  T* ebz = envbar + ((b * 2 + s) * 2 + 1) * (int64_t)K * nmax * M;
+  // envbar staging [Bc][spin][omega|zeta][K*nmax][M]; rows o = p*n + k.  The
+  // rows of spin sr of this block are ii in [ra(sr), rb(sr)).
+  const int sr0 = full ? 0 : s, sr1 = full ? 1 : s;
+  auto ra = [&](int sr) { return full ? (sr == 0 ? 0 : n_up) : 0; };
+  auto rb = [&](int sr) { return full ? (sr == 0 ? n_up : N) : n; };
   for (int q = lane; q < n * n; q += 32) {
     const int ii = q / n, k = q % n, o = p * n + k, i = i0 + ii;
+    const bool up = i < n_up;
+    const T* om = params + (up ? om_up : om_dn);
+    const T* ze = params + (up ? ze_up : ze_dn);
     T ev = 0;
     for (int I = 0; I < M; ++I) ev += om[o * M + I] * exp(-ze[o * M + I] * gb[(n_ee + i * M + I) * 4]);
     env[q] = ev;
@@ -194,10 +200,14 @@ __global__ void __launch_bounds__(128)
       const int ii = q / n, k = q % n;
       phibar[(b * N + i0 + ii) * (int64_t)Wo + p * n + k] = T(0);
     }
-    for (int q = lane; q < n * M; q += 32) {
-      const int k = q / M, I = q % M;
-      ebo[(int64_t)(p * n + k) * M + I] = T(0);
-      ebz[(int64_t)(p * n + k) * M + I] = T(0);
+    for (int sr = sr0; sr <= sr1; ++sr) {
+      T* ebo = envbar + ((b * 2 + sr) * 2 + 0) * (int64_t)K * nmax * M;
+      T* ebz = envbar + ((b * 2 + sr) * 2 + 1) * (int64_t)K * nmax * M;
+      for (int q = lane; q < n * M; q += 32) {
+        const int k = q / M, I = q % M;
+        ebo[(int64_t)(p * n + k) * M + I] = T(0);
+        ebz[(int64_t)(p * n + k) * M + I] = T(0);
+      }
     }
     return;
   }
@@ -206,21 +216,28 @@ __global__ void __launch_bounds__(128)
     const int ii = q / n, k = q % n;
     phibar[(b * N + i0 + ii) * (int64_t)Wo + p * n + k] = (T)(bp * ainv(k, ii) * (double)env[q]);
   }
-  // envelope parameters: lanes over (k, I)
-  for (int q = lane; q < n * M; q += 32) {
-    const int k = q / M, I = q % M, o = p * n + k;
-    const T w = om[o * M + I], z = ze[o * M + I];
-    T ob = 0, zb = 0;
-    for (int ii = 0; ii < n; ++ii) {
-      const int i = i0 + ii;
-      const T d = gb[(n_ee + i * M + I) * 4];
-      const T e = exp(-z * d);
-      const T envb = (T)(bp * ainv(k, ii)) * phi0[ii * n + k];
-      ob += envb * e;
-      zb -= envb * w * d * e;
+  // envelope parameters of each spin present in the block: lanes over (k, I)
+  for (int sr = sr0; sr <= sr1; ++sr) {
+    const T* om = params + (sr == 0 ? om_up : om_dn);
+    const T* ze = params + (sr == 0 ? ze_up : ze_dn);
+    T* ebo = envbar + ((b * 2 + sr) * 2 + 0) * (int64_t)K * nmax * M;
+    T* ebz = envbar + ((b * 2 + sr) * 2 + 1) * (int64_t)K * nmax * M;
+    const int iia = ra(sr), iib = rb(sr);
+    for (int q = lane; q < n * M; q += 32) {
+      const int k = q / M, I = q % M, o = p * n + k;
+      const T w = om[o * M + I], z = ze[o * M + I];
+      T ob = 0, zb = 0;
+      for (int ii = iia; ii < iib; ++ii) {
+        const int i = i0 + ii;
+        const T d = gb[(n_ee + i * M + I) * 4];
+        const T e = exp(-z * d);
+        const T envb = (T)(bp * ainv(k, ii)) * phi0[ii * n + k];
+        ob += envb * e;
+        zb -= envb * w * d * e;
+      }
+      ebo[(int64_t)o * M + I] = ob;
+      ebz[(int64_t)o * M + I] = zb;
     }
-    ebo[(int64_t)o * M + I] = ob;
-    ebz[(int64_t)o * M + I] = zb;
   }
 }
 
@@ -661,7 +678,7 @@ cudaError_t launch_bwd_combine(const dq_handle_s& h, int64_t Bc, const double* d
 template <class T>
 cudaError_t launch_bwd_det(const dq_handle_s& h, int64_t Bc, const T* phi, const T* geo, const T* params, const T* beta,
                            T* phibar, T* envbar, cudaStream_t s) {
-  const int nmax = h.n_up > h.n_dn ? h.n_up : h.n_dn;
+  const int nmax = h.det_n();
   const int nn = nmax * nmax;
   const size_t per_warp = ((size_t)nn * (2 * sizeof(double) + 5 * sizeof(T)) + 32 * sizeof(int) + 15) / 16 * 16;
   const int warps = 4;
@@ -671,7 +688,7 @@ cudaError_t launch_bwd_det(const dq_handle_s& h, int64_t Bc, const T* phi, const
   if (e != cudaSuccess) return e;
   kern<<<nblocks(Bc * 2 * h.K, warps), warps * 32, smem, s>>>(
       phi, geo, params, beta, Bc, h.N, h.n_up, h.M, h.K, h.K * nmax, h.edges.n_all, h.edges.n_ee, h.off.omega[0],
-      h.off.omega[1], h.off.zeta[0], h.off.zeta[1], phibar, envbar);
+      h.off.omega[1], h.off.zeta[0], h.off.zeta[1], phibar, envbar, h.full_det);
   return cudaGetLastError();
 }
 

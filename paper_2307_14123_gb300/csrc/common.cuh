@@ -145,7 +145,12 @@ struct dq_handle_s {
   int D = 0, L = 0, K = 0, Q = 0;
   double rc = 10.0, alpha = 1.0;
   int use_jastrow = 1, use_cusp = 1;
+  int full_det = 0;  // 1: one N x N determinant per p (Eq. 22) instead of det A^up det A^down (Eq. 21)
   double Vnn = 0;
+  // Orbitals per determinant of spin sg's orbital network: n_sg, or N for the full determinant.
+  int ncol(int sg) const { return full_det ? N : (sg ? n_dn : n_up); }
+  // Side of the largest determinant matrix; the orbital row pitch is K * det_n().
+  int det_n() const { return full_det ? N : (n_up > n_dn ? n_up : n_dn); }
   dq::ParamOffsets off{};
   dq::Edges edges{};
   int64_t max_chunk = 4096;

@@ -936,19 +936,30 @@ struct orbital_det_kernel_args {
   int64_t ze_dn;
   double* det;
   unsigned long long* n_fp64;
+  int full;  // 1: block 0 is the N x N determinant of Eq. (22), block 1 the empty one
 };
+
+// Determinant blocks.  Every (walker, p) has two: the spin-up and spin-down
+// matrices of Eq. (21), or (full) the N x N matrix of Eq. (22) and an empty
+// block (determinant 1), so that the combination downstream is the same.
+// Row ii of block s is electron i0 + ii; its orbitals and envelopes are those
+// of the electron's own spin.
+__device__ __forceinline__ void det_block(int s, int N, int n_up, int full, int& n, int& i0) {
+  n = full ? (s == 0 ? N : 0) : (s == 0 ? n_up : N - n_up);
+  i0 = (full || s == 0) ? 0 : n_up;
+}
 
 template <class T>
 __device__ __forceinline__ void orbital_det_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const T* __restrict__ phi, const T* __restrict__ geo, const T* __restrict__ params,
                        int64_t Bc, int N, int n_up, int M, int K, int C, int Wo, int E, int n_ee,
                        int64_t om_up, int64_t om_dn, int64_t ze_up, int64_t ze_dn, double* __restrict__ det,
-                       unsigned long long* __restrict__ n_fp64) {
+                       unsigned long long* __restrict__ n_fp64, int full) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int warps = blockDim.x / 32;
   const int64_t gw = (int64_t)bx_ * warps + warp;
   const int n_dn = N - n_up;
-  const int nmax = n_up > n_dn ? n_up : n_dn;
+  const int nmax = full ? N : (n_up > n_dn ? n_up : n_dn);
   const int N3 = 3 * N;
   const bool jets = C > 1;
   const int nn = nmax * nmax;
@@ -971,15 +982,13 @@ __device__ __forceinline__ void orbital_det_kernel_body(const int64_t bx_, const
   const int64_t b = gw / (2 * K);
   const int s = (int)((gw / K) % 2);
   const int p = (int)(gw % K);
-  const int n = s == 0 ? n_up : n_dn;
-  const int i0 = s == 0 ? 0 : n_up;
+  int n, i0;
+  det_block(s, N, n_up, full, n, i0);
   double* out = det + gw * (N3 + 3);
   if (n == 0) {  // empty determinant = 1
     for (int k = lane; k < N3 + 3; k += 32) out[k] = k == 0 ? 1.0 : 0.0;
     return;
   }
-  const T* om = params + (s == 0 ? om_up : om_dn);
-  const T* ze = params + (s == 0 ? ze_up : ze_dn);
   const T* phib = phi + b * N * C * Wo;
   const T* gb = geo + b * E * 4;
 
@@ -987,6 +996,9 @@ __device__ __forceinline__ void orbital_det_kernel_body(const int64_t bx_, const
   T amax = 0;
   for (int q = lane; q < n * n; q += 32) {
     const int ii = q / n, k = q % n, o = p * n + k, i = i0 + ii;
+    const bool up = i < n_up;
+    const T* om = params + (up ? om_up : om_dn);
+    const T* ze = params + (up ? ze_up : ze_dn);
     T ev = 0, j0 = 0, j1 = 0, j2 = 0, lv = 0;
     for (int I = 0; I < M; ++I) {
       const T* g = gb + (n_ee + i * M + I) * 4;
@@ -1090,8 +1102,8 @@ template <class T>
 __global__ void __launch_bounds__(128) orbital_det_kernel(const T* __restrict__ phi, const T* __restrict__ geo, const T* __restrict__ params,
                        int64_t Bc, int N, int n_up, int M, int K, int C, int Wo, int E, int n_ee,
                        int64_t om_up, int64_t om_dn, int64_t ze_up, int64_t ze_dn, double* __restrict__ det,
-                       unsigned long long* __restrict__ n_fp64) {
-  orbital_det_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, phi, geo, params, Bc, N, n_up, M, K, C, Wo, E, n_ee, om_up, om_dn, ze_up, ze_dn, det, n_fp64);
+                       unsigned long long* __restrict__ n_fp64, int full) {
+  orbital_det_kernel_body<T>(blockIdx.x, blockIdx.y, gridDim.x, phi, geo, params, Bc, N, n_up, M, K, C, Wo, E, n_ee, om_up, om_dn, ze_up, ze_dn, det, n_fp64, full);
 }
 
 // One launch over several molecules: block b runs entry m of the table.
@@ -1100,7 +1112,7 @@ __global__ void __launch_bounds__(128) orbital_det_kernel_group(const __grid_con
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
   const orbital_det_kernel_args<T>& a_ = g.a[m_];
-  orbital_det_kernel_body<T>(grp_bx(g, m_, l_), grp_by(g, m_, l_), g.nbx[m_], a_.phi, a_.geo, a_.params, a_.Bc, a_.N, a_.n_up, a_.M, a_.K, a_.C, a_.Wo, a_.E, a_.n_ee, a_.om_up, a_.om_dn, a_.ze_up, a_.ze_dn, a_.det, a_.n_fp64);
+  orbital_det_kernel_body<T>(grp_bx(g, m_, l_), grp_by(g, m_, l_), g.nbx[m_], a_.phi, a_.geo, a_.params, a_.Bc, a_.N, a_.n_up, a_.M, a_.K, a_.C, a_.Wo, a_.E, a_.n_ee, a_.om_up, a_.om_dn, a_.ze_up, a_.ze_dn, a_.det, a_.n_fp64, a_.full);
 }
 
 // ---------------------------------------------------------------------------
@@ -1135,13 +1147,13 @@ __host__ __device__ inline size_t det_jets_smem_per_warp(int nmax, int N3) {
 __device__ __forceinline__ void orbital_det_jets_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const float* __restrict__ phi, const float* __restrict__ geo,
                             const float* __restrict__ params, int64_t Bc, int N, int n_up, int M, int K, int C,
                             int Wo, int E, int n_ee, int64_t om_up, int64_t om_dn, int64_t ze_up, int64_t ze_dn,
-                            double* __restrict__ det, unsigned long long* __restrict__ n_fp64) {
+                            double* __restrict__ det, unsigned long long* __restrict__ n_fp64, int full) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int warps = blockDim.x / 32;
   const int64_t gw = (int64_t)bx_ * warps + warp;
   const int n_dn = N - n_up;
-  const int nmax = n_up > n_dn ? n_up : n_dn;
+  const int nmax = full ? N : (n_up > n_dn ? n_up : n_dn);
   const int N3 = 3 * N;
   const int nn = nmax * nmax;
   unsigned char* base = smem_raw + warp * det_jets_smem_per_warp(nmax, N3);
@@ -1167,15 +1179,13 @@ __device__ __forceinline__ void orbital_det_jets_kernel_body(const int64_t bx_, 
   const int64_t b = gw / (2 * K);
   const int s = (int)((gw / K) % 2);
   const int p = (int)(gw % K);
-  const int n = s == 0 ? n_up : n_dn;
-  const int i0 = s == 0 ? 0 : n_up;
+  int n, i0;
+  det_block(s, N, n_up, full, n, i0);
   double* out = det + gw * (N3 + 3);
   if (n == 0) {  // empty determinant = 1
     for (int k = lane; k < N3 + 3; k += 32) out[k] = k == 0 ? 1.0 : 0.0;
     return;
   }
-  const float* om = params + (s == 0 ? om_up : om_dn);
-  const float* ze = params + (s == 0 ? ze_up : ze_dn);
   const float* phib = phi + b * N * C * Wo;
   const float* gb = geo + b * E * 4;
   const int nsq = n * n;
@@ -1183,6 +1193,9 @@ __device__ __forceinline__ void orbital_det_jets_kernel_body(const int64_t bx_, 
   // Envelopes (Eq. 20) with their derivatives in the coordinates of electron i.
   for (int q = lane; q < nsq; q += 32) {
     const int ii = q / n, k = q - (q / n) * n, o = p * n + k, i = i0 + ii;
+    const bool up = i < n_up;
+    const float* om = params + (up ? om_up : om_dn);
+    const float* ze = params + (up ? ze_up : ze_dn);
     float ev = 0, j0 = 0, j1 = 0, j2 = 0, lv = 0;
     for (int I = 0; I < M; ++I) {
       const float* g = gb + (n_ee + i * M + I) * 4;
@@ -1372,11 +1385,12 @@ __global__ void __launch_bounds__(128) orbital_det_mixed_group(const __grid_cons
   const orbital_det_kernel_args<float>& a_ = g.a[m_];
   if (g.tag[m_])
     orbital_det_jets_kernel_body(l_, 0, g.nbx[m_], a_.phi, a_.geo, a_.params, a_.Bc, a_.N, a_.n_up, a_.M, a_.K, a_.C,
-                                 a_.Wo, a_.E, a_.n_ee, a_.om_up, a_.om_dn, a_.ze_up, a_.ze_dn, a_.det, a_.n_fp64);
+                                 a_.Wo, a_.E, a_.n_ee, a_.om_up, a_.om_dn, a_.ze_up, a_.ze_dn, a_.det, a_.n_fp64,
+                                 a_.full);
   else
     orbital_det_kernel_body<float>(l_, 0, g.nbx[m_], a_.phi, a_.geo, a_.params, a_.Bc, a_.N, a_.n_up, a_.M, a_.K,
                                    a_.C, a_.Wo, a_.E, a_.n_ee, a_.om_up, a_.om_dn, a_.ze_up, a_.ze_dn, a_.det,
-                                   a_.n_fp64);
+                                   a_.n_fp64, a_.full);
 }
 
 // Sum of embeddings over electrons, the input of the Jastrow factor (Eq. 24).
@@ -1729,7 +1743,7 @@ cudaError_t launch_to_bf16(const float* src, void* dst, int64_t n, cudaStream_t 
 template <class T>
 cudaError_t launch_orbital_det(const dq_handle_s& h, const FwdDims& d, const T* params, FwdBuffers<T> b,
                                cudaStream_t s) {
-  const int nmax = d.n_up > d.n_dn ? d.n_up : d.n_dn;
+  const int nmax = h.det_n();
   const int nn = nmax * nmax;
   {
     const size_t pw = ((size_t)nn * (3 * sizeof(double) + 10 * sizeof(T)) + 32 * sizeof(int) + 15) / 16 * 16;
@@ -1750,7 +1764,7 @@ cudaError_t launch_orbital_det(const dq_handle_s& h, const FwdDims& d, const T* 
   kern<<<blocks(nmat, warps), warps * 32, smem, s>>>(b.phi, b.geo, params, d.Bc, d.N, d.n_up, d.M, d.K, d.C,
                                                      d.K * nmax, h.edges.n_all, h.edges.n_ee, h.off.omega[0],
                                                      h.off.omega[1], h.off.zeta[0], h.off.zeta[1], b.det,
-                                                     h.d_fp64_count);
+                                                     h.d_fp64_count, h.full_det);
   return cudaGetLastError();
 }
 
@@ -1995,7 +2009,7 @@ cudaError_t launch_orbital_det_group(const MolFwd<T>* m, int n, cudaStream_t s) 
     const dq_handle_s& h = *m[k].h;
     const FwdDims& d = m[k].d;
     if (d.Bc <= 0) continue;
-    const int nmax = d.n_up > d.n_dn ? d.n_up : d.n_dn;
+    const int nmax = h.det_n();
     const int nn = nmax * nmax;
     const int64_t nmat = d.Bc * 2 * d.K;
     const bool jets = sizeof(T) == 4 && d.C > 1 && nmax <= kDetNR;
@@ -2010,7 +2024,7 @@ cudaError_t launch_orbital_det_group(const MolFwd<T>* m, int n, cudaStream_t s) 
     smem = std::max(smem, sm);
     ent[ne++] = Ent{{m[k].b.phi, m[k].b.geo, m[k].params, d.Bc, d.N, d.n_up, d.M, d.K, d.C, d.K * nmax,
                      h.edges.n_all, h.edges.n_ee, h.off.omega[0], h.off.omega[1], h.off.zeta[0], h.off.zeta[1],
-                     m[k].b.det, h.d_fp64_count},
+                     m[k].b.det, h.d_fp64_count, h.full_det},
                     blocks(nmat, 4), jets ? 1 : 0, 0, sm};
   }
   if (ne == 0) return cudaSuccess;

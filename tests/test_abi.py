@@ -63,3 +63,21 @@ def test_no_cpu_fallback():
     wl = fx.workload("lih_fp64")
     with pytest.raises(DQError):
         Ansatz(wl.system, wl.cfg, "fp64")
+
+
+def test_full_determinant_arguments_are_checked_on_the_host(lib):
+    """full_det must be 0 or 1, and the full determinant needs N <= 32; both are refused before
+    any device call (these run without a GPU)."""
+    import numpy as np
+
+    from paper_2307_14123_gb300 import binding
+    from paper_2307_14123_gb300 import fixtures as fx
+    for mol, full, want in (("C6H6", 1, 2), ("N2", 2, 1)):
+        s = fx.molecule(mol)
+        Z = np.ascontiguousarray(s.Z, dtype=np.float64)
+        R = np.ascontiguousarray(s.R, dtype=np.float64)
+        sysc = binding._System(len(Z), Z.ctypes.data, R.ctypes.data, s.n_up, s.n_down)
+        cfgc = binding._Cfg(32, 1, 1, 16, 10.0, 1, 1, 1.0, full)
+        h = ctypes.c_void_p()
+        assert lib.dq_create(ctypes.byref(sysc), ctypes.byref(cfgc), 1, ctypes.byref(h)) == want
+        assert not h.value
