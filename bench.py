@@ -345,6 +345,43 @@ def pp_leg(h, theta, r, wl, flush, B=512):
             "note": "12-point icosahedral quadrature, every electron around both nuclei, synthetic coefficients"}
 
 
+def full_det_leg(h, theta, r, wl, flush, reps=5):
+    """Local energies of the full-determinant ansatz (Eq. 22: one N x N determinant per p) on the
+    bench walkers, beside the spin-factorised ansatz timed the same way."""
+    import dataclasses
+
+    import torch
+
+    from paper_2307_14123_gb300 import Ansatz
+    from paper_2307_14123_gb300 import fixtures as fx
+
+    cfg = dataclasses.replace(wl.cfg, full_det=1)
+    hf = Ansatz(wl.system, cfg, wl.precision, device=r.device)
+    th_f = torch.tensor(fx.init_params(wl.system, cfg, wl.param_seed), dtype=theta.dtype, device=r.device)
+
+    def timed(hh, th):
+        hh.local_energy(th, r)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(reps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            hh.local_energy(th, r)
+            b.record()
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / reps
+
+    ms_full, ms_fact = timed(hf, th_f), timed(h, theta)
+    B = r.shape[0]
+    return {"value": B / (ms_full / 1e3), "unit": UNIT, "ms_per_call": ms_full, "params": hf.P,
+            "spin_factorised_ms_per_call": ms_fact, "cost_vs_factorised": ms_full / ms_fact,
+            "note": f"{wl.system.name} {wl.precision.upper()}, {B} walkers, one {wl.system.n_elec} x "
+                    f"{wl.system.n_elec} determinant per p instead of two {wl.system.n_up} x {wl.system.n_up} "
+                    "blocks; local_energy calls, L2 flushed before each"}
+
+
 def training_leg(dev, steps=60):
     """VMC training end to end in the library (vmc_train_step: Metropolis sweep, local energies,
     clipped-energy weights, per-walker gradients, natural gradient, parameter update) on LiH in
@@ -709,6 +746,7 @@ def main():
     batched = batch_leg(args, dev, flush) if (world == 1 and not args.no_batch) else None
     training = training_leg(dev) if (world == 1 and not args.no_natgrad) else None
     pseudo = pp_leg(h, theta, r, wl, flush) if (world == 1 and not args.no_pp) else None
+    full_det = full_det_leg(h, theta, r, wl, flush) if (world == 1 and not args.no_pp) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -734,6 +772,7 @@ def main():
                 "natural_gradient": natgrad,
                 "vmc_training": training,
                 "pseudopotential": pseudo,
+                "full_determinant": full_det,
                 "gpu_launches": launches,
                 "clocks": clk,
                 "local_energy_only": {"value": B * world * args.steps / (jet_ms / 1e3) if jet_ms else None,
