@@ -12,7 +12,9 @@
 //         edges, and the concatenating residual update, Eq. (18) (Sec. 3.1);
 //       - spin-only initial electron embedding, Eq. (13) first case;
 //       - edge features: Gaussian expansion of the distance, reused in every
-//         layer, Eqs. (15)-(16) first case;
+//         layer, Eqs. (15)-(16) first case, or (edge_update) updated from
+//         layer to layer, Eq. (16) second case, with the residual map
+//         f^l = f^{l-1} + tanh(U^{l,t} f^{l-1} + c^{l,t}) per edge type;
 //       - many-body orbitals kappa(f_i^L) (linear), Eq. (19), times isotropic
 //         Slater envelopes (alpha = 1, one exponential per nucleus), Eq. (20);
 //       - spin-factorised determinant pairs, Eq. (21), or (full_det) one
@@ -132,13 +134,15 @@ struct OracleSpec {
   int32_t use_jastrow, use_cusp;
   real alpha;        // cusp width
   int32_t full_det;  // 0: det A^up det A^down per p (Eq. 21); 1: det of the N x N A^p (Eq. 22)
+  int32_t edge_update;  // 1: edge embeddings iterated between layers (Eq. 16, second case)
 };
 }
 
 namespace {
 
 // Offsets of every block of the flat parameter vector.  Order: E_spin[2][D];
-// per layer: W_h[D][D], (W1[D][Q], b1[D], W2[D][D], b2[D]) for the
+// per layer: W_h[D][D], ([U[Q][Q], c[Q] when edge embeddings are iterated and
+// l >= 1], W1[D][Q], b1[D], W2[D][D], b2[D]) for the
 // same-spin, opposite-spin and electron-nucleus edge types, Y[M][D],
 // W_g[D][3D], b_g[D]; per spin (up, down): W_o[K n_c][D], b_o[K n_c],
 // omega[K n_c][M], zeta[K n_c][M]; c[K]; W_J1[D][D], b_J1[D], w_J2[D].
@@ -148,7 +152,7 @@ namespace {
 struct Layout {
   int64_t E_spin;
   struct Layer {
-    int64_t W_h, W1[3], b1[3], W2[3], b2[3], Y, W_g, b_g;
+    int64_t W_h, U[3], c[3], W1[3], b1[3], W2[3], b2[3], Y, W_g, b_g;
   };
   std::vector<Layer> layer;
   int64_t W_o[2], b_o[2], omega[2], zeta[2], c, W_J1, b_J1, w_J2, total;
@@ -162,6 +166,11 @@ struct Layout {
       Layer& y = layer[l];
       y.W_h = o; o += D * D;
       for (int t = 0; t < 3; ++t) {
+        y.U[t] = y.c[t] = -1;
+        if (s.edge_update && l > 0) {
+          y.U[t] = o; o += Q * Q;
+          y.c[t] = o; o += Q;
+        }
         y.W1[t] = o; o += D * Q;
         y.b1[t] = o; o += D;
         y.W2[t] = o; o += D * D;
@@ -259,6 +268,20 @@ struct Walker {
 };
 
 // log|psi| and sign psi of one walker.  r: [N][3].  Optional debug outputs:
+// Edge embedding of layer l of an edge of type t at distance d (Eq. 16): the
+// Gaussian features, then, when iterated, l residual updates
+// f <- f + tanh(U^{l',t} f + c^{l',t}) for l' = 1 .. l.
+template <class T>
+void edge_embedding(const OracleSpec& s, const Layout& lay, const T* th, int l, int t, const T& d, T* e) {
+  gaussian_features(d, s.Q, s.rc, e);
+  if (!s.edge_update) return;
+  std::vector<T> a(s.Q);
+  for (int lp = 1; lp <= l; ++lp) {
+    affine(th + lay.layer[lp].U[t], th + lay.layer[lp].c[t], e, s.Q, s.Q, a.data());
+    for (int q = 0; q < s.Q; ++q) e[q] = e[q] + tanh(a[q]);
+  }
+}
+
 // f_out [N][D] final embeddings, A_out [2][K][nmax][nmax] orbital matrices.
 template <class T>
 Walker<T> log_psi(const OracleSpec& s, const Layout& lay, const T* th, const T* r,
@@ -301,8 +324,9 @@ Walker<T> log_psi(const OracleSpec& s, const Layout& lay, const T* th, const T* 
     std::vector<T> wee(N * N * D, T(0.0));
     for (int i = 0; i < N; ++i)
       for (int j = i + 1; j < N; ++j) {
-        gaussian_features(dee[i * N + j], Q, s.rc, e.data());
-        edge_filter(th, y, spin(i) == spin(j) ? 0 : 1, e.data(), D, Q, w.data());
+        const int t = spin(i) == spin(j) ? 0 : 1;
+        edge_embedding(s, lay, th, l, t, dee[i * N + j], e.data());
+        edge_filter(th, y, t, e.data(), D, Q, w.data());
         for (int a = 0; a < D; ++a) wee[(i * N + j) * D + a] = wee[(j * N + i) * D + a] = w[a];
       }
     std::vector<T> fnew(N * D);
@@ -315,7 +339,7 @@ Walker<T> log_psi(const OracleSpec& s, const Layout& lay, const T* th, const T* 
         for (int a = 0; a < D; ++a) m[t * D + a] += wee[(i * N + j) * D + a] * z[j * D + a];
       }
       for (int I = 0; I < M; ++I) {
-        gaussian_features(den[i * M + I], Q, s.rc, e.data());
+        edge_embedding(s, lay, th, l, 2, den[i * M + I], e.data());
         edge_filter(th, y, 2, e.data(), D, Q, w.data());
         for (int a = 0; a < D; ++a) m[2 * D + a] += w[a] * th[y.Y + I * D + a];
       }

@@ -214,13 +214,15 @@ class AnsatzCfg:
     use_cusp: int = 1
     cusp_alpha: float = 1.0
     full_det: int = 0        # 1: one determinant of all N electrons per p (Eq. 22)
+    edge_update: int = 0     # 1: edge embeddings iterated between layers (Eq. 16, second case)
 
 
 def param_layout(system: System, cfg: AnsatzCfg):
     """Flat parameter layout: list of (name, shape, init-kind).
 
     Order: E_spin[2][D]; per layer l: W_h[D][D], then for edge types
-    (same-spin, opposite-spin, electron-nucleus) W1[D][n_rbf], b1[D],
+    (same-spin, opposite-spin, electron-nucleus) [U[n_rbf][n_rbf], c[n_rbf]
+    when cfg.edge_update and l >= 1: the edge-embedding update], W1[D][n_rbf], b1[D],
     W2[D][D], b2[D]; Y[M][D]; W_g[D][3D], b_g[D]; then per spin (up, down)
     W_o[K*n_c][D], b_o[K*n_c], omega[K*n_c][M], zeta[K*n_c][M]; then c[K];
     W_J1[D][D], b_J1[D], w_J2[D].  Matrices are [out][in], row-major.  n_c, the
@@ -232,6 +234,8 @@ def param_layout(system: System, cfg: AnsatzCfg):
     for l in range(L):
         out.append((f"W_h{l}", (D, D), "xavier"))
         for t in ("par", "anti", "nuc"):
+            if getattr(cfg, "edge_update", 0) and l > 0:
+                out += [(f"U_{t}{l}", (Q, Q), "xavier"), (f"c_{t}{l}", (Q,), "zero")]
             out += [(f"W1_{t}{l}", (D, Q), "xavier"), (f"b1_{t}{l}", (D,), "zero"),
                     (f"W2_{t}{l}", (D, D), "xavier"), (f"b2_{t}{l}", (D,), "zero")]
         out.append((f"Y{l}", (M, D), "normal"))

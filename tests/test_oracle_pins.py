@@ -268,12 +268,14 @@ def _random_case(name):
         sys_, cfg = wl.system, wl.cfg
     if name.endswith("_full"):
         cfg = dataclasses.replace(cfg, full_det=1)
+    if name.endswith("_eu"):
+        cfg = dataclasses.replace(cfg, edge_update=1)
     th = fx.init_params(sys_, cfg, 3)
     r = fx.init_walkers(sys_, 6, 3)
     return sys_, cfg, th, r
 
 
-@pytest.mark.parametrize("name", ["small", "lih", "small_full", "lih_full"])
+@pytest.mark.parametrize("name", ["small", "lih", "small_full", "lih_full", "small_eu"])
 def test_antisymmetry(name):
     """Exchange of two same-spin electrons flips the sign only (Eqs. 3, 9)."""
     sys_, cfg, th, r = _random_case(name)
@@ -301,7 +303,7 @@ def test_opposite_spin_exchange_is_not_a_symmetry(name):
 
 
 @pytest.mark.parametrize("reflect", [False, True])
-@pytest.mark.parametrize("name", ["small", "small_full"])
+@pytest.mark.parametrize("name", ["small", "small_full", "small_eu"])
 def test_rigid_motion_invariance(reflect, name):
     sys_, cfg, th, r = _random_case(name)
     o = oracle.Oracle(sys_, cfg)
@@ -415,15 +417,21 @@ def test_full_determinant_laplace_expansion():
 # ----------------------------------------------------------------------------
 # Derivatives against finite differences
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("name", ["small", "lih", "small_full", "lih_full"])
+@pytest.mark.parametrize("name", ["small", "lih", "small_full", "lih_full", "small_eu", "lih_eu"])
 def test_coordinate_derivatives_finite_differences(name):
     sys_, cfg, th, r = _random_case(name)
     o = oracle.Oracle(sys_, cfg)
     r = r[:3]
     out = o.local_energy(th, r, with_grad=True)
     N3 = 3 * sys_.n_elec
-    h1, h2 = 1e-5, 2e-3
     for b in range(r.shape[0]):
+        # steps scaled to the walker's smallest e-e / e-n distance and to its distance from the
+        # nodal surface, about 1 / |grad log|psi|| (the stencil's truncation error grows like
+        # (h / distance)^4 near a coalescence or a node)
+        pts = np.concatenate([r[b], sys_.R])
+        dd = np.linalg.norm(pts[:, None] - pts[None], axis=-1)[:sys_.n_elec]
+        d_min = min(np.min(dd[dd > 0]), 1.0 / np.max(np.abs(out["grad"][b])))
+        h1, h2 = 1e-5, min(2e-3, 0.02 * d_min)
         lap_fd = 0.0
         for x in range(N3):
             def f(dx):
@@ -444,10 +452,11 @@ def test_coordinate_derivatives_finite_differences(name):
         assert abs(out["e_loc"][b] - e_fd) <= tol, (out["e_loc"][b], e_fd, tol)
 
 
-def test_parameter_gradient_finite_differences():
+@pytest.mark.parametrize("edge_update", [0, 1])
+def test_parameter_gradient_finite_differences(edge_update):
     """d log|psi| / d theta by dual numbers vs central differences (h = 1e-4... 1e-5, FP64)."""
     wl = fx.workload("lih_fp64")
-    sys_, cfg = wl.system, wl.cfg
+    sys_, cfg = wl.system, dataclasses.replace(wl.cfg, edge_update=edge_update)
     o = oracle.Oracle(sys_, cfg)
     th = fx.init_params(sys_, cfg, 0)
     r = fx.init_walkers(sys_, 2, 0)
@@ -553,6 +562,70 @@ def test_edge_filter_and_gaussian_features():
     f, _ = oracle.Oracle(sys_, cfg).intermediates(th, r)
     np.testing.assert_allclose(f[0], E[0] + np.tanh(G @ (w * (Hm @ E[1]))), rtol=1e-13)
     np.testing.assert_allclose(f[1], E[1] + np.tanh(G @ (w * (Hm @ E[0]))), rtol=1e-13)
+
+
+def test_iterated_edge_embedding_closed_form():
+    """Eq. (16), second case, on one up and one down electron: layer 0 switched off (W_g = 0,
+    b_g = 0 keep f^1 = E_spin); in layer 1 the opposite-spin edge embedding is
+    e + tanh(U e + c) and W1 one-hot on its components 3 and 5, W2 = I: the messages are
+    tanh of those two components times W_h f of the other electron."""
+    sys_ = fx.System(Z=np.array([1.0]), R=np.array([[0.0, 0.0, 0.0]]), n_up=1, n_down=1)
+    D, Q, rc = 2, 16, 10.0
+    cfg = fx.AnsatzCfg(D, 2, 1, n_rbf=Q, rbf_cutoff=rc, use_cusp=0, edge_update=1)
+    th = fx.init_params(sys_, cfg, 2)
+    rng = np.random.default_rng(7)
+    U, c = rng.normal(size=(Q, Q)) * 0.5, rng.normal(size=Q) * 0.3
+    Hm = np.array([[0.3, -1.2], [0.8, 0.5]])
+    G = np.array([[1.1, 0.2], [-0.4, 0.9]])
+    W1 = np.zeros((D, Q))
+    W1[0, 3] = 1.0
+    W1[1, 5] = 1.0
+    setp(th, sys_, cfg, "W_g0", 0.0)
+    setp(th, sys_, cfg, "b_g0", 0.0)
+    setp(th, sys_, cfg, "U_anti1", U)
+    setp(th, sys_, cfg, "c_anti1", c)
+    setp(th, sys_, cfg, "W_h1", Hm)
+    setp(th, sys_, cfg, "W1_anti1", W1)
+    setp(th, sys_, cfg, "b1_anti1", 0.0)
+    setp(th, sys_, cfg, "W2_anti1", np.eye(D))
+    setp(th, sys_, cfg, "b2_anti1", 0.0)
+    setp(th, sys_, cfg, "W2_nuc1", 0.0)
+    setp(th, sys_, cfg, "b2_nuc1", 0.0)
+    Wg = np.zeros((D, 3 * D))
+    Wg[:, D:2 * D] = G
+    setp(th, sys_, cfg, "W_g1", Wg)
+    setp(th, sys_, cfg, "b_g1", 0.0)
+    E = th[pidx(sys_, cfg, "E_spin"):][:2 * D].reshape(2, D)
+    r = np.array([[[0.4, -0.3, 1.0], [-1.2, 0.9, 2.1]]])
+    d = np.linalg.norm(r[0, 0] - r[0, 1])
+    s = rc / (Q - 1)
+    e = np.exp(-(d - np.arange(Q) * s) ** 2 / (2 * s * s))
+    fe = e + np.tanh(U @ e + c)
+    w = np.tanh(np.array([fe[3], fe[5]]))
+    f, _ = oracle.Oracle(sys_, cfg).intermediates(th, r)
+    np.testing.assert_allclose(f[0], E[0] + np.tanh(G @ (w * (Hm @ E[1]))), rtol=1e-13)
+    np.testing.assert_allclose(f[1], E[1] + np.tanh(G @ (w * (Hm @ E[0]))), rtol=1e-13)
+
+
+@pytest.mark.parametrize("name", ["small", "lih"])
+def test_iterated_edge_embedding_zero_update_reduces(name):
+    """U = 0 and c = 0 make every edge-embedding update the identity (f + tanh 0), so the
+    iterated ansatz equals the one with fixed Gaussian edge features."""
+    sys_, cfg, th, r = _random_case(name)
+    cfg_u = dataclasses.replace(cfg, edge_update=1)
+    off, off_u = fx.param_offsets(sys_, cfg), fx.param_offsets(sys_, cfg_u)
+    th_u = np.zeros(fx.param_count(sys_, cfg_u))
+    for nm, (o, shape) in off.items():
+        th_u[off_u[nm][0]:off_u[nm][0] + int(np.prod(shape))] = th[o:o + int(np.prod(shape))]
+    assert set(off_u) - set(off) == {f"{k}_{t}{l}" for k in "Uc" for t in ("par", "anti", "nuc")
+                                      for l in range(1, cfg.n_layers)}
+    a = oracle.Oracle(sys_, cfg).local_energy(th, r)
+    b = oracle.Oracle(sys_, cfg_u).local_energy(th_u, r)
+    np.testing.assert_allclose(b["logabs"], a["logabs"], rtol=1e-13, atol=1e-13)
+    assert np.array_equal(b["sign"], a["sign"])
+    np.testing.assert_allclose(b["e_loc"], a["e_loc"], rtol=1e-11, atol=1e-11)
+    th_u[pidx(sys_, cfg_u, "U_anti1")] = 0.5  # and a non-zero update changes psi
+    assert np.all(np.abs(oracle.Oracle(sys_, cfg_u).evaluate(th_u, r)[0] - a["logabs"]) > 1e-9)
 
 
 def test_orbital_head_and_jastrow_layout():
