@@ -33,6 +33,7 @@
  *   per layer l < n_layers:
  *     W_h[D][D];
  *     for the edge types same-spin, opposite-spin, electron-nucleus:
+ *       [U[n_rbf][n_rbf], c[n_rbf]: only with edge_update and l >= 1],
  *       W1[D][n_rbf], b1[D], W2[D][D], b2[D];
  *     Y[n_nuc][D]; W_g[D][3D], b_g[D];
  *   for spin up then spin down (n_c orbitals per determinant: n_s, the
@@ -125,6 +126,12 @@ typedef struct {
                        *    whose row i comes from the orbital network and
                        *    envelopes of electron i's spin (Eq. 22); needs
                        *    N <= 32.  Other values: DQ_ERR_ARG.           */
+  int32_t edge_update; /* 0: every layer filters the Gaussian features e(d);
+                        * 1: edge embeddings iterated (Eq. 16, second case):
+                        *    before layer l >= 1's filters,
+                        *    f^l = f^{l-1} + tanh(U^{l,t} f^{l-1} + c^{l,t})
+                        *    per edge type t, f^0 = e(d).  Other values:
+                        *    DQ_ERR_ARG.                                   */
 } dq_ansatz_cfg;
 
 typedef struct dq_handle_s* dq_handle;

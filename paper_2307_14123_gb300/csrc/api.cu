@@ -19,8 +19,9 @@
 
 namespace dq {
 
-// nc_up, nc_dn: orbitals per determinant of the spin-up and spin-down networks.
-ParamOffsets make_offsets(int D, int L, int K, int Q, int M, int nc_up, int nc_dn) {
+// nc_up, nc_dn: orbitals per determinant of the spin-up and spin-down networks;
+// edge_update: the edge-embedding maps U, c of layers l >= 1 precede each type's filter.
+ParamOffsets make_offsets(int D, int L, int K, int Q, int M, int nc_up, int nc_dn, int edge_update) {
   ParamOffsets o{};
   int64_t p = 0;
   o.E_spin = p;
@@ -30,6 +31,13 @@ ParamOffsets make_offsets(int D, int L, int K, int Q, int M, int nc_up, int nc_d
     y.W_h = p;
     p += (int64_t)D * D;
     for (int t = 0; t < 3; ++t) {
+      y.U[t] = y.c[t] = -1;
+      if (edge_update && l > 0) {
+        y.U[t] = p;
+        p += (int64_t)Q * Q;
+        y.c[t] = p;
+        p += Q;
+      }
       y.W1[t] = p;
       p += (int64_t)D * Q;
       y.b1[t] = p;
@@ -313,6 +321,8 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
     DQ_LAUNCH(h, kb + PK_GEOMETRY, launch_geometry<T>(h, d, r + b0 * N * 3, bf, s));
     for (int l = 0; l < h.L; ++l) {
       const auto& y = h.off.layer[l];
+      if (h.edge_update && l > 0)  // edge embeddings of layer l, in place (Eq. 16, second case)
+        DQ_LAUNCH(h, kb + PK_EDGE_HIDDEN, launch_edge_update<T>(h, d, params, l, bf.rbf, bf.rbf, s));
       DQ_LAUNCH(h, kb + PK_EDGE_HIDDEN, launch_edge_hidden<T>(h, d, params, l, bf, s));
       const int e0[3] = {0, h.edges.n_par, h.edges.n_ee};
       const int ng[3] = {h.edges.n_par, h.edges.n_anti, h.edges.n_en};
@@ -419,6 +429,7 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
 struct GradPlan {
   size_t geo, rbf, eh, ew, zl, msg, u, F, phi, det, js, jh, z0;  // saved forward
   size_t fbar, ubar, mbar, zbar, wbar, hbar, phibar, beta, cbar, jhbar, gt, sbar, envbar, ybar, part, done, wt3, wt3t;
+  size_t ebar, abar;  // edge-embedding adjoints (iterated edge embeddings only)
   int64_t part_elems;
   size_t total;
 };
@@ -434,7 +445,7 @@ GradPlan plan_grad(const dq_handle_s& h, int64_t Bc, size_t elem) {
     return at;
   };
   p.geo = take(Bc * E * 4 * elem);
-  p.rbf = take(Bc * E * Q * elem);
+  p.rbf = take((h.edge_update ? L : 1) * Bc * E * Q * elem);  // every layer's edge embeddings when iterated
   p.eh = take(L * Bc * E * D * elem);
   p.ew = take(L * Bc * E * D * elem);
   p.zl = take(L * Bc * N * D * elem);
@@ -460,7 +471,9 @@ GradPlan plan_grad(const dq_handle_s& h, int64_t Bc, size_t elem) {
   p.sbar = take(Bc * D * elem);
   p.envbar = take(Bc * 2 * 2 * Wo * M * elem);
   p.ybar = take(Bc * M * D * elem);
-  const int64_t blk = std::max({3 * D * D, D * D, D * Q, Wo * D, Wo * M, M * D, K, D});
+  p.ebar = take(h.edge_update ? Bc * E * Q * elem : 0);
+  p.abar = take(h.edge_update ? Bc * E * Q * elem : 0);
+  const int64_t blk = std::max({3 * D * D, D * D, D * Q, Wo * D, Wo * M, M * D, K, D, Q * Q});
   p.part_elems = 64 * blk;
   p.part = take(p.part_elems * elem);
   p.done = take(kColsumReduceCounters * sizeof(unsigned int));
@@ -533,6 +546,8 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
     auto MS = [&](int l) { return buf(pl.msg) + (int64_t)l * Bmax * N * 3 * D; };
     auto U = [&](int l) { return buf(pl.u) + (int64_t)l * Bmax * N * D; };
     auto F = [&](int l) { return buf(pl.F) + (int64_t)l * Bmax * N * D; };
+    // edge embeddings of layer l (one shared buffer unless they are iterated)
+    auto RB = [&](int l) { return buf(pl.rbf) + (h.edge_update ? (int64_t)l * Bmax * E * Q : 0); };
     DQ_LAUNCH(h, kValueOffset + PK_LAYER0, launch_layer0_node<T>(h, d, params, v, s));
     DQ_LAUNCH(h, kValueOffset + PK_GEOMETRY, launch_geometry<T>(h, d, r + b0 * N * 3, v, s));
     DQ_LAUNCH(h, kValueOffset + PK_UPDATE, launch_fill_spin_rows<T>(F(0), params + off.E_spin, nb, N, h.n_up, D, s));
@@ -543,6 +558,9 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
       v.F = F(l);
       v.Z = ZL(l);
       v.msg = MS(l);
+      if (h.edge_update && l > 0)
+        DQ_LAUNCH(h, kValueOffset + PK_EDGE_HIDDEN, launch_edge_update<T>(h, d, params, l, RB(l - 1), RB(l), s));
+      v.rbf = RB(l);
       DQ_LAUNCH(h, kValueOffset + PK_EDGE_HIDDEN, launch_edge_hidden<T>(h, d, params, l, v, s));
       for (int t = 0; t < 3; ++t) {
         if (ng[t] == 0) continue;
@@ -605,6 +623,9 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
     T *fbar = buf(pl.fbar), *ubar = buf(pl.ubar), *mbar = buf(pl.mbar), *zbar = buf(pl.zbar);
     T *wbar = buf(pl.wbar), *hbar = buf(pl.hbar), *phibar = buf(pl.phibar), *envbar = buf(pl.envbar);
     T* ybar = buf(pl.ybar);
+    T* ebar = h.edge_update ? buf(pl.ebar) : nullptr;
+    T* abar = h.edge_update ? buf(pl.abar) : nullptr;
+    if (h.edge_update) DQ_CU(cudaMemsetAsync(ebar, 0, (size_t)nb * E * Q * sizeof(T), s));
     DQ_LAUNCH(h, PK_BWD_COMBINE,
               launch_bwd_combine<T>(h, nb, v.det, v.jh, params, wc, beta, cbar, jhbar, gt, s));
     DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(cbar, rm(K), nullptr, rm(1), 1, K, 1, off.c, 1));
@@ -685,8 +706,21 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
         const RowMap me{(int64_t)ng[t], (int64_t)E * D, D};
         const RowMap mq{(int64_t)ng[t], (int64_t)E * Q, Q};
         const T* hb = hbar + (int64_t)e0[t] * D;
-        DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(hb, me, v.rbf + (int64_t)e0[t] * Q, mq, ng[t], D, Q, y.W1[t], Q));
+        DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(hb, me, RB(l) + (int64_t)e0[t] * Q, mq, ng[t], D, Q, y.W1[t], Q));
         DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(hb, me, nullptr, rm(1), ng[t], D, 1, y.b1[t], 1));
+        if (h.edge_update && l > 0)  // adjoint of this layer's edge embeddings: W1^T h-bar
+          DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(hb, me, params + y.W1[t], ebar + (int64_t)e0[t] * Q, mq,
+                                             nb * ng[t], Q, D, true, s));
+      }
+      if (h.edge_update && l > 0) {  // through f^l = f^{l-1} + tanh(U f^{l-1} + c) (Eq. 16)
+        DQ_LAUNCH(h, PK_BWD_EDGE, launch_edge_update_bwd<T>(h, nb, l, params, RB(l - 1), ebar, abar, s));
+        for (int t = 0; t < 3; ++t) {
+          if (ng[t] == 0) continue;
+          const RowMap mq{(int64_t)ng[t], (int64_t)E * Q, Q};
+          const T* ab = abar + (int64_t)e0[t] * Q;
+          DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ab, mq, RB(l - 1) + (int64_t)e0[t] * Q, mq, ng[t], Q, Q, y.U[t], Q));
+          DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ab, mq, nullptr, rm(1), ng[t], Q, 1, y.c[t], 1));
+        }
       }
     }
     for (int sg = 0; sg < 2; ++sg) {
@@ -881,6 +915,16 @@ dq_status run_forward_multi(const dq_multi_s& g, const T* const* params, const T
     if (!any) break;
     DQ_LAUNCH(H, kb + PK_GEOMETRY, launch_geometry_group<T>(mf, n, rq, s));
     for (int l = 0; l < L; ++l) {
+      if (l > 0) {  // iterated edge embeddings of the molecules that have them, in place
+        const T* es[kMaxGroup];
+        T* ed[kMaxGroup];
+        bool anyu = false;
+        for (int m = 0; m < n; ++m) {
+          es[m] = ed[m] = mf[m].b.rbf;
+          anyu = anyu || (g.h[m]->edge_update && mf[m].d.Bc > 0);
+        }
+        if (anyu) DQ_LAUNCH(H, kb + PK_EDGE_HIDDEN, launch_edge_update_group<T>(mf, n, l, es, ed, s));
+      }
       DQ_LAUNCH(H, kb + PK_EDGE_HIDDEN, launch_edge_hidden_group<T>(mf, n, l, s));
       int nj = 0;
       for (int m = 0; m < n; ++m) {  // edge filters: three edge types of every molecule
@@ -1176,6 +1220,7 @@ dq_status dq_create(const dq_system* sys, const dq_ansatz_cfg* cfg, int32_t prec
       !(cfg->rbf_cutoff > 0) || !(cfg->cusp_alpha > 0))
     return DQ_ERR_SHAPE;
   if (cfg->full_det != 0 && cfg->full_det != 1) return DQ_ERR_ARG;
+  if (cfg->edge_update != 0 && cfg->edge_update != 1) return DQ_ERR_ARG;
   if (cfg->full_det && N > kMaxSpin) return DQ_ERR_SHAPE;  // the N x N matrix obeys the spin-block limit
   for (int I = 0; I < M; ++I) {
     if (!isfinite(sys->Z[I])) return DQ_ERR_ARG;
@@ -1202,7 +1247,8 @@ dq_status dq_create(const dq_system* sys, const dq_ansatz_cfg* cfg, int32_t prec
   h->use_jastrow = cfg->use_jastrow ? 1 : 0;
   h->use_cusp = cfg->use_cusp ? 1 : 0;
   h->full_det = cfg->full_det;
-  h->off = make_offsets(h->D, h->L, h->K, h->Q, M, h->ncol(0), h->ncol(1));
+  h->edge_update = cfg->edge_update;
+  h->off = make_offsets(h->D, h->L, h->K, h->Q, M, h->ncol(0), h->ncol(1), h->edge_update);
   double vnn = 0;
   for (int I = 0; I < M; ++I)
     for (int J = I + 1; J < M; ++J) {

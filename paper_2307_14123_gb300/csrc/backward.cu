@@ -13,6 +13,8 @@
 // formed by param_reduce, per walker or summed over walkers.
 #include <math.h>
 
+#include <algorithm>
+
 #include "backward.cuh"
 #include "det_util.cuh"
 
@@ -656,7 +658,85 @@ __global__ void fill_spin_rows_kernel(T* __restrict__ F0, const T* __restrict__ 
   F0[e] = E_spin[(i < n_up ? 0 : 1) * D + e % D];
 }
 
+// ---------------------------------------------------------------------------
+// Reverse of one layer's edge-embedding update f^l = f + tanh(U f + c) (value
+// rows): with th = tanh(U f + c) recomputed from the saved input f = f^{l-1},
+//   abar = ebar (1 - th^2)        (adjoint of U f + c: U-bar = abar f^T, c-bar = abar)
+//   ebar <- ebar + U^T abar       (adjoint of f^{l-1}: the identity path plus the map)
+// ebar is updated in place; one thread per (row, feature), rows staged in
+// shared memory.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256)
+    edge_update_bwd_kernel(const T* __restrict__ fprev, T* __restrict__ ebar, T* __restrict__ abar,
+                           const T* __restrict__ params, int64_t Bc, int E, int n_par, int n_ee, int Q, int64_t U0,
+                           int64_t U1, int64_t U2, int64_t c0, int64_t c1, int64_t c2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Us = reinterpret_cast<T*>(smem_raw);  // [3][Q][Q]
+  T* cs = Us + 3 * Q * Q;                  // [3][Q]
+  const int rpi = blockDim.x / Q;
+  T* fs = cs + 3 * Q;   // [rpi][Q]
+  T* es = fs + rpi * Q;  // [rpi][Q]
+  T* as = es + rpi * Q;  // [rpi][Q]
+  const int64_t Uo[3] = {U0, U1, U2}, co[3] = {c0, c1, c2};
+  for (int t = 0; t < 3; ++t) {
+    for (int k = threadIdx.x; k < Q * Q; k += blockDim.x) Us[t * Q * Q + k] = params[Uo[t] + k];
+    for (int k = threadIdx.x; k < Q; k += blockDim.x) cs[t * Q + k] = params[co[t] + k];
+  }
+  const int rr = threadIdx.x / Q, q = threadIdx.x % Q;
+  const int64_t nrows = Bc * E;
+  for (int64_t be0 = (int64_t)blockIdx.x * rpi; be0 < nrows; be0 += (int64_t)gridDim.x * rpi) {
+    const int nb = (int)min((int64_t)rpi, nrows - be0);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nb * Q; k += blockDim.x) {
+      fs[k] = fprev[be0 * Q + k];
+      es[k] = ebar[be0 * Q + k];
+    }
+    __syncthreads();
+    const bool live = rr < nb;
+    const int64_t be = be0 + rr;
+    const int e = (int)(be % E);
+    const int t = e < n_par ? 0 : (e < n_ee ? 1 : 2);
+    if (live) {
+      const T* f = fs + rr * Q;
+      const T* u = Us + (t * Q + q) * Q;
+      T v = cs[t * Q + q];
+      for (int k = 0; k < Q; ++k) v += u[k] * f[k];
+      const T th = tanh(v);
+      const T ab = es[rr * Q + q] * (T(1) - th * th);
+      as[rr * Q + q] = ab;
+      abar[be * Q + q] = ab;
+    }
+    __syncthreads();
+    if (live) {
+      T acc = es[rr * Q + q];
+      for (int j = 0; j < Q; ++j) acc += Us[(t * Q + j) * Q + q] * as[rr * Q + j];
+      ebar[be * Q + q] = acc;
+    }
+  }
+}
+
 }  // namespace
+
+template <class T>
+cudaError_t launch_edge_update_bwd(const dq_handle_s& h, int64_t Bc, int l, const T* params, const T* fprev, T* ebar,
+                                   T* abar, cudaStream_t s) {
+  const int Q = h.Q, rpi = 256 / Q;
+  const auto& y = h.off.layer[l];
+  const int64_t rows = Bc * h.edges.n_all, nblk = (rows + rpi - 1) / rpi;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = ((size_t)3 * Q * Q + 3 * Q + (size_t)3 * rpi * Q) * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(edge_update_bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)std::max(sms, 1) * 8));
+  edge_update_bwd_kernel<T><<<grid, 256, smem, s>>>(fprev, ebar, abar, params, Bc, h.edges.n_all, h.edges.n_par,
+                                                    h.edges.n_ee, Q, y.U[0], y.U[1], y.U[2], y.c[0], y.c[1],
+                                                    y.c[2]);
+  return cudaGetLastError();
+}
 
 template <class T>
 cudaError_t launch_fill_spin_rows(T* F0, const T* E_spin, int64_t Bc, int N, int n_up, int D, cudaStream_t s) {
@@ -870,6 +950,8 @@ cudaError_t launch_msg_bwd(const dq_handle_s& h, int64_t Bc, const T* mbar, cons
                                        unsigned int*);                                                            \
   template cudaError_t launch_tanh_bwd<T>(const T*, const T*, int64_t, bool, T*, cudaStream_t);                   \
   template cudaError_t launch_add_rows<T>(T*, const T*, int64_t, int, int, cudaStream_t);                         \
+  template cudaError_t launch_edge_update_bwd<T>(const dq_handle_s&, int64_t, int, const T*, const T*, T*, T*,    \
+                                                 cudaStream_t);                                                   \
   template cudaError_t launch_fill_spin_rows<T>(T*, const T*, int64_t, int, int, int, cudaStream_t);              \
   template cudaError_t launch_msg_bwd<T>(const dq_handle_s&, int64_t, const T*, const T*, const T*, const T*,     \
                                          const T*, bool, T*, T*, T*, cudaStream_t);

@@ -30,6 +30,11 @@ template <class T>
 cudaError_t launch_tanh_bwd(const T* g, const T* u, int64_t n, bool is_pre, T* out, cudaStream_t s);
 template <class T>
 cudaError_t launch_add_rows(T* fbar, const T* sbar, int64_t Bc, int N, int D, cudaStream_t s);
+// Reverse of layer l's edge-embedding update: abar = ebar (1 - tanh^2(U f + c)) with f = fprev, then
+// ebar <- ebar + U^T abar in place (rows [Bc * E][Q]).
+template <class T>
+cudaError_t launch_edge_update_bwd(const dq_handle_s& h, int64_t Bc, int l, const T* params, const T* fprev, T* ebar,
+                                   T* abar, cudaStream_t s);
 template <class T>
 cudaError_t launch_fill_spin_rows(T* F0, const T* E_spin, int64_t Bc, int N, int n_up, int D, cudaStream_t s);
 template <class T>

@@ -18,13 +18,13 @@ constexpr int kMaxNuc = 64;
 struct ParamOffsets {
   int64_t E_spin;
   struct Layer {
-    int64_t W_h, W1[3], b1[3], W2[3], b2[3], Y, W_g, b_g;
+    int64_t W_h, U[3], c[3], W1[3], b1[3], W2[3], b2[3], Y, W_g, b_g;  // U, c: -1 without edge updates
   } layer[16];
   int64_t W_o[2], b_o[2], omega[2], zeta[2], c, W_J1, b_J1, w_J2, total;
 };
 constexpr int kMaxLayers = 16;
 
-ParamOffsets make_offsets(int D, int L, int K, int Q, int M, int n_up, int n_dn);
+ParamOffsets make_offsets(int D, int L, int K, int Q, int M, int nc_up, int nc_dn, int edge_update);
 
 // Edge bookkeeping.  Electron-electron pairs (i < j) are ordered by type:
 // up-up pairs, down-down pairs (together: same spin), then up-down pairs
@@ -146,6 +146,7 @@ struct dq_handle_s {
   double rc = 10.0, alpha = 1.0;
   int use_jastrow = 1, use_cusp = 1;
   int full_det = 0;  // 1: one N x N determinant per p (Eq. 22) instead of det A^up det A^down (Eq. 21)
+  int edge_update = 0;  // 1: edge embeddings iterated between layers (Eq. 16, second case)
   double Vnn = 0;
   // Orbitals per determinant of spin sg's orbital network: n_sg, or N for the full determinant.
   int ncol(int sg) const { return full_det ? N : (sg ? n_dn : n_up); }
@@ -317,6 +318,13 @@ template <class T>
 cudaError_t launch_geometry_group(const MolFwd<T>* m, int n, const T* const* r, cudaStream_t s);
 template <class T>
 cudaError_t launch_edge_hidden_group(const MolFwd<T>* m, int n, int layer, cudaStream_t s);
+// Iterated edge embeddings of layer `layer` >= 1 (nothing for handles without them): dst = u(src).
+template <class T>
+cudaError_t launch_edge_update_group(const MolFwd<T>* m, int n, int layer, const T* const* src, T* const* dst,
+                                     cudaStream_t s);
+template <class T>
+cudaError_t launch_edge_update(const dq_handle_s& h, const FwdDims& d, const T* params, int layer, const T* src,
+                               T* dst, cudaStream_t s);
 template <class T>
 cudaError_t launch_layer0_node_group(const MolFwd<T>* m, int n, cudaStream_t s);
 template <class T>

@@ -241,6 +241,81 @@ __global__ void __launch_bounds__(kHiddenThreads) edge_hidden_kernel_group(const
              edge_hidden_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.rbf, a_.params, a_.Bc, a_.E, a_.n_par, a_.n_ee, a_.D, a_.Q, a_.ej, a_.W1_0, a_.W1_1, a_.W1_2, a_.b1_0, a_.b1_1, a_.b1_2, a_.eh);)
 }
 
+// ---------------------------------------------------------------------------
+// Iterated edge embeddings (Eq. 16, second case): before the filters of layer
+// l >= 1, f^l = f^{l-1} + tanh(U^{l,t} f^{l-1} + c^{l,t}) per edge type t, as
+// a univariate jet in the edge's distance (value, d/dd, d2/dd2):
+//   a = U f + c,  a' = U f',  a'' = U f'';  th = tanh a,  g = 1 - th^2;
+//   f^l = f + th,  f^l' = f' + g a',  f^l'' = f'' + g a'' - 2 th g a'^2.
+// One thread per (edge row, feature q); the rows of an iteration are staged
+// in shared memory before any is written, so src may equal dst.
+// ---------------------------------------------------------------------------
+template <class T>
+struct edge_update_kernel_args {
+  const T* src;
+  T* dst;
+  const T* params;
+  int64_t Bc;
+  int E;
+  int n_par;
+  int n_ee;
+  int Q;
+  int ej;
+  int64_t U0, U1, U2, c0, c1, c2;
+};
+
+template <class T>
+__device__ __forceinline__ void edge_update_kernel_body(const int64_t bx_, const int64_t nbx_,
+                                                        const edge_update_kernel_args<T>& a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Q = a.Q, ej = a.ej;
+  T* Us = reinterpret_cast<T*>(smem_raw);  // [3][Q][Q]
+  T* cs = Us + 3 * Q * Q;                  // [3][Q]
+  T* fs = cs + 3 * Q;                      // [rows][ej][Q]
+  const int64_t Uo[3] = {a.U0, a.U1, a.U2}, co[3] = {a.c0, a.c1, a.c2};
+  for (int t = 0; t < 3; ++t) {
+    for (int k = threadIdx.x; k < Q * Q; k += blockDim.x) Us[t * Q * Q + k] = a.params[Uo[t] + k];
+    for (int k = threadIdx.x; k < Q; k += blockDim.x) cs[t * Q + k] = a.params[co[t] + k];
+  }
+  const int rpi = blockDim.x / Q;  // rows per iteration
+  const int rr = threadIdx.x / Q, q = threadIdx.x % Q;
+  const int64_t nrows = a.Bc * a.E;
+  for (int64_t be0 = bx_ * rpi; be0 < nrows; be0 += nbx_ * rpi) {
+    const int nb = (int)min((int64_t)rpi, nrows - be0);
+    __syncthreads();  // weights staged; previous rows consumed
+    for (int k = threadIdx.x; k < nb * ej * Q; k += blockDim.x) fs[k] = a.src[be0 * ej * Q + k];
+    __syncthreads();
+    if (rr >= nb) continue;
+    const int64_t be = be0 + rr;
+    const int e = (int)(be % a.E);
+    const int t = e < a.n_par ? 0 : (e < a.n_ee ? 1 : 2);
+    const T* f = fs + rr * ej * Q;
+    const T* u = Us + (t * Q + q) * Q;
+    T v = cs[t * Q + q], v1 = 0, v2 = 0;
+    for (int k = 0; k < Q; ++k) {
+      v += u[k] * f[k];
+      if (ej == 3) {
+        v1 += u[k] * f[Q + k];
+        v2 += u[k] * f[2 * Q + k];
+      }
+    }
+    const T th = tanh_t(v), g = T(1) - th * th;
+    T* o = a.dst + be * ej * Q;
+    o[q] = f[q] + th;
+    if (ej == 3) {
+      o[Q + q] = f[Q + q] + g * v1;
+      o[2 * Q + q] = f[2 * Q + q] + g * v2 - T(2) * th * g * v1 * v1;
+    }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) edge_update_kernel_group(const __grid_constant__ Grp<edge_update_kernel_args<T>> g) {
+  int64_t l_;
+  const int m_ = grp_find(g, blockIdx.x, l_);
+  GRP_STATIC(m_, edge_update_kernel_body<T>(grp_bx(g, K_, l_), g.nbx[K_], g.a[K_]);)
+}
+
 // z0[s][a] = (W_h^0 E_spin[s])[a]: the node map of layer 0 on the spin embeddings.
 template <class T>
 struct layer0_node_kernel_args {
@@ -1854,6 +1929,42 @@ cudaError_t launch_edge_hidden_group(const MolFwd<T>* m, int n, int l, cudaStrea
 }
 
 template <class T>
+cudaError_t launch_edge_update_group(const MolFwd<T>* m, int n, int l, const T* const* src, T* const* dst,
+                                     cudaStream_t s) {
+  if (n > kMaxGroup) return cudaErrorInvalidValue;
+  Grp<edge_update_kernel_args<T>> g{};
+  size_t smem = 0;
+  for (int k = 0; k < n; ++k) {
+    const dq_handle_s& h = *m[k].h;
+    const FwdDims& d = m[k].d;
+    if (d.Bc <= 0 || !h.edge_update || l < 1) continue;
+    const int ej = d.C > 1 ? 3 : 1, Q = d.Q;
+    const auto& y = h.off.layer[l];
+    const int rpi = 256 / Q;
+    const int64_t rows = d.Bc * h.edges.n_all, nblk = (rows + rpi - 1) / rpi;
+    smem = std::max(smem, ((size_t)3 * Q * Q + 3 * Q + (size_t)rpi * ej * Q) * sizeof(T));
+    g.add({src[k], dst[k], m[k].params, d.Bc, h.edges.n_all, h.edges.n_par, h.edges.n_ee, Q, ej, y.U[0], y.U[1],
+           y.U[2], y.c[0], y.c[1], y.c[2]},
+          std::max<int64_t>(1, std::min<int64_t>(nblk, (int64_t)device_sms() * 8)));
+  }
+  if (g.n == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(edge_update_kernel_group<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  e = check_group(g);
+  if (e != cudaSuccess) return e;
+  edge_update_kernel_group<T><<<(unsigned)g.blocks(), 256, smem, s>>>(g);
+  return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_edge_update(const dq_handle_s& h, const FwdDims& d, const T* params, int l, const T* src, T* dst,
+                               cudaStream_t s) {
+  const MolFwd<T> m{&h, d, params, FwdBuffers<T>{}};
+  return launch_edge_update_group<T>(&m, 1, l, &src, &dst, s);
+}
+
+template <class T>
 cudaError_t launch_layer0_node_group(const MolFwd<T>* m, int n, cudaStream_t s) {
   if (n > kMaxGroup) return cudaErrorInvalidValue;
   Grp<layer0_node_kernel_args<T>> g{};
@@ -2102,6 +2213,10 @@ cudaError_t launch_combine_group(const MolFwd<T>* m, int n, T* const* logabs, in
 #define DQ_INSTANTIATE_GROUP(T)                                                                                    \
   template cudaError_t launch_geometry_group<T>(const MolFwd<T>*, int, const T* const*, cudaStream_t);            \
   template cudaError_t launch_edge_hidden_group<T>(const MolFwd<T>*, int, int, cudaStream_t);                     \
+  template cudaError_t launch_edge_update_group<T>(const MolFwd<T>*, int, int, const T* const*, T* const*,         \
+                                                   cudaStream_t);                                                 \
+  template cudaError_t launch_edge_update<T>(const dq_handle_s&, const FwdDims&, const T*, int, const T*, T*,      \
+                                             cudaStream_t);                                                       \
   template cudaError_t launch_layer0_node_group<T>(const MolFwd<T>*, int, cudaStream_t);                          \
   template cudaError_t launch_messages_group<T>(const MolFwd<T>*, int, int, bool, cudaStream_t);                  \
   template cudaError_t launch_update_group<T>(const MolFwd<T>*, int, bool, cudaStream_t);                         \

@@ -77,7 +77,7 @@ def test_full_determinant_arguments_are_checked_on_the_host(lib):
         Z = np.ascontiguousarray(s.Z, dtype=np.float64)
         R = np.ascontiguousarray(s.R, dtype=np.float64)
         sysc = binding._System(len(Z), Z.ctypes.data, R.ctypes.data, s.n_up, s.n_down)
-        cfgc = binding._Cfg(32, 1, 1, 16, 10.0, 1, 1, 1.0, full)
+        cfgc = binding._Cfg(32, 1, 1, 16, 10.0, 1, 1, 1.0, full, 0)
         h = ctypes.c_void_p()
         assert lib.dq_create(ctypes.byref(sysc), ctypes.byref(cfgc), 1, ctypes.byref(h)) == want
         assert not h.value
