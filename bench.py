@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--no-mala", action="store_true", help="skip the step with the Langevin sampler")
     p.add_argument("--no-batch", action="store_true", help="skip the uneven-molecule batch")
     p.add_argument("--no-natgrad", action="store_true", help="skip the natural-gradient direction")
-    p.add_argument("--no-pp", action="store_true", help="skip the pseudopotential energies")
+    p.add_argument("--no-pp", action="store_true", help="skip the pseudopotential and ansatz-variant legs")
     p.add_argument("--mala-tau", type=float, default=0.1, help="Langevin time step (bohr^2)")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--profile-case", type=int, default=0, metavar="B",
@@ -345,19 +345,16 @@ def pp_leg(h, theta, r, wl, flush, B=512):
             "note": "12-point icosahedral quadrature, every electron around both nuclei, synthetic coefficients"}
 
 
-def full_det_leg(h, theta, r, wl, flush, reps=5):
-    """Local energies of the full-determinant ansatz (Eq. 22: one N x N determinant per p) on the
-    bench walkers, beside the spin-factorised ansatz timed the same way."""
+def ansatz_variants_leg(h, theta, r, wl, flush, reps=5):
+    """Local energies of the ansatz variants on the bench walkers, each timed like the base
+    (spin-factorised determinants, fixed Gaussian edge features): the full determinant (Eq. 22),
+    iterated edge embeddings (Eq. 16, second case), and both (the PauliNet2-style ansatz)."""
     import dataclasses
 
     import torch
 
     from paper_2307_14123_gb300 import Ansatz
     from paper_2307_14123_gb300 import fixtures as fx
-
-    cfg = dataclasses.replace(wl.cfg, full_det=1)
-    hf = Ansatz(wl.system, cfg, wl.precision, device=r.device)
-    th_f = torch.tensor(fx.init_params(wl.system, cfg, wl.param_seed), dtype=theta.dtype, device=r.device)
 
     def timed(hh, th):
         hh.local_energy(th, r)
@@ -373,13 +370,21 @@ def full_det_leg(h, theta, r, wl, flush, reps=5):
             tot += a.elapsed_time(b)
         return tot / reps
 
-    ms_full, ms_fact = timed(hf, th_f), timed(h, theta)
     B = r.shape[0]
-    return {"value": B / (ms_full / 1e3), "unit": UNIT, "ms_per_call": ms_full, "params": hf.P,
-            "spin_factorised_ms_per_call": ms_fact, "cost_vs_factorised": ms_full / ms_fact,
-            "note": f"{wl.system.name} {wl.precision.upper()}, {B} walkers, one {wl.system.n_elec} x "
-                    f"{wl.system.n_elec} determinant per p instead of two {wl.system.n_up} x {wl.system.n_up} "
-                    "blocks; local_energy calls, L2 flushed before each"}
+    ms_base = timed(h, theta)
+    out = {"base": {"value": B / (ms_base / 1e3), "unit": UNIT, "ms_per_call": ms_base, "params": h.P}}
+    for name, kw in (("full_determinant", {"full_det": 1}), ("edge_update", {"edge_update": 1}),
+                     ("full_determinant+edge_update", {"full_det": 1, "edge_update": 1})):
+        cfg = dataclasses.replace(wl.cfg, **kw)
+        hv = Ansatz(wl.system, cfg, wl.precision, device=r.device)
+        th = torch.tensor(fx.init_params(wl.system, cfg, wl.param_seed), dtype=theta.dtype, device=r.device)
+        ms = timed(hv, th)
+        out[name] = {"value": B / (ms / 1e3), "unit": UNIT, "ms_per_call": ms, "params": hv.P,
+                     "cost_vs_base": ms / ms_base}
+        del hv
+    out["note"] = (f"{wl.system.name} {wl.precision.upper()}, {B} walkers, local_energy calls, L2 flushed "
+                   "before each; full determinant: one N x N matrix per p instead of two spin blocks")
+    return out
 
 
 def training_leg(dev, steps=60):
@@ -746,7 +751,7 @@ def main():
     batched = batch_leg(args, dev, flush) if (world == 1 and not args.no_batch) else None
     training = training_leg(dev) if (world == 1 and not args.no_natgrad) else None
     pseudo = pp_leg(h, theta, r, wl, flush) if (world == 1 and not args.no_pp) else None
-    full_det = full_det_leg(h, theta, r, wl, flush) if (world == 1 and not args.no_pp) else None
+    variants = ansatz_variants_leg(h, theta, r, wl, flush) if (world == 1 and not args.no_pp) else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -772,7 +777,7 @@ def main():
                 "natural_gradient": natgrad,
                 "vmc_training": training,
                 "pseudopotential": pseudo,
-                "full_determinant": full_det,
+                "ansatz_variants": variants,
                 "gpu_launches": launches,
                 "clocks": clk,
                 "local_energy_only": {"value": B * world * args.steps / (jet_ms / 1e3) if jet_ms else None,
