@@ -67,7 +67,8 @@ def _spec_class(c_real):
                     ("n_up", ctypes.c_int32), ("n_dn", ctypes.c_int32),
                     ("D", ctypes.c_int32), ("L", ctypes.c_int32), ("K", ctypes.c_int32), ("Q", ctypes.c_int32),
                     ("rc", c_real), ("use_jastrow", ctypes.c_int32), ("use_cusp", ctypes.c_int32),
-                    ("alpha", c_real), ("full_det", ctypes.c_int32), ("edge_update", ctypes.c_int32)]
+                    ("alpha", c_real), ("full_det", ctypes.c_int32), ("edge_update", ctypes.c_int32),
+                    ("el_init", ctypes.c_int32)]
     return _Spec
 
 
@@ -111,7 +112,7 @@ class Oracle:
         self.spec = _SPECS[real](len(self._Z), self._Z.ctypes.data, self._R.ctypes.data, system.n_up, system.n_down,
                           cfg.width, cfg.n_layers, cfg.n_det, cfg.n_rbf, cfg.rbf_cutoff,
                           int(cfg.use_jastrow), int(cfg.use_cusp), cfg.cusp_alpha, int(cfg.full_det),
-                          int(cfg.edge_update))
+                          int(cfg.edge_update), int(cfg.el_init))
         self.N = system.n_up + system.n_down
         P = ctypes.c_int64()
         self.lib.oracle_param_count(ctypes.byref(self.spec), ctypes.byref(P))

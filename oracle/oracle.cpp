@@ -10,7 +10,10 @@
 //     time, straight from the definitions:
 //       - graph convolution messages, Eq. (17), normalised by the number of
 //         edges, and the concatenating residual update, Eq. (18) (Sec. 3.1);
-//       - spin-only initial electron embedding, Eq. (13) first case;
+//       - spin-only initial electron embedding, Eq. (13) first case, or
+//         (el_init) an MLP of the electron-nucleus difference vectors,
+//         Eq. (13) second case: f^0_i = W_e2 tanh(W_e1 x_i + b_e1) + b_e2,
+//         x_i = (r_i - R_1, ..., r_i - R_M);
 //       - edge features: Gaussian expansion of the distance, reused in every
 //         layer, Eqs. (15)-(16) first case, or (edge_update) updated from
 //         layer to layer, Eq. (16) second case, with the residual map
@@ -135,12 +138,14 @@ struct OracleSpec {
   real alpha;        // cusp width
   int32_t full_det;  // 0: det A^up det A^down per p (Eq. 21); 1: det of the N x N A^p (Eq. 22)
   int32_t edge_update;  // 1: edge embeddings iterated between layers (Eq. 16, second case)
+  int32_t el_init;      // 1: initial embeddings from electron-nucleus differences (Eq. 13, second case)
 };
 }
 
 namespace {
 
-// Offsets of every block of the flat parameter vector.  Order: E_spin[2][D];
+// Offsets of every block of the flat parameter vector.  Order: E_spin[2][D]
+// (or, with el_init, W_e1[D][3M], b_e1[D], W_e2[D][D], b_e2[D]);
 // per layer: W_h[D][D], ([U[Q][Q], c[Q] when edge embeddings are iterated and
 // l >= 1], W1[D][Q], b1[D], W2[D][D], b2[D]) for the
 // same-spin, opposite-spin and electron-nucleus edge types, Y[M][D],
@@ -150,7 +155,7 @@ namespace {
 // for spin-factorised determinants and N for the full determinant; row
 // p n_c + k of a spin's block is orbital k of determinant p.
 struct Layout {
-  int64_t E_spin;
+  int64_t E_spin = -1, W_e1 = -1, b_e1 = -1, W_e2 = -1, b_e2 = -1;
   struct Layer {
     int64_t W_h, U[3], c[3], W1[3], b1[3], W2[3], b2[3], Y, W_g, b_g;
   };
@@ -160,7 +165,14 @@ struct Layout {
   explicit Layout(const OracleSpec& s) {
     const int64_t D = s.D, Q = s.Q, M = s.n_nuc, K = s.K;
     int64_t o = 0;
-    E_spin = o; o += 2 * D;
+    if (s.el_init) {
+      W_e1 = o; o += D * 3 * M;
+      b_e1 = o; o += D;
+      W_e2 = o; o += D * D;
+      b_e2 = o; o += D;
+    } else {
+      E_spin = o; o += 2 * D;
+    }
     layer.resize(s.L);
     for (int l = 0; l < s.L; ++l) {
       Layer& y = layer[l];
@@ -310,10 +322,22 @@ Walker<T> log_psi(const OracleSpec& s, const Layout& lay, const T* th, const T* 
       den[i * M + I] = sqrt(acc);
     }
 
-  // Initial embeddings: f_i^0 = E_spin[sigma_i] (Eq. 13, first case).
+  // Initial embeddings: f_i^0 = E_spin[sigma_i] (Eq. 13, first case), or an MLP
+  // of the difference vectors r_i - R_I (Eq. 13, second case).
   std::vector<T> f(N * D);
-  for (int i = 0; i < N; ++i)
-    for (int a = 0; a < D; ++a) f[i * D + a] = th[lay.E_spin + spin(i) * D + a];
+  if (s.el_init) {
+    std::vector<T> x(3 * M), hid(D);
+    for (int i = 0; i < N; ++i) {
+      for (int I = 0; I < M; ++I)
+        for (int c = 0; c < 3; ++c) x[3 * I + c] = r[3 * i + c] - T(s.R[3 * I + c]);
+      affine(th + lay.W_e1, th + lay.b_e1, x.data(), D, 3 * M, hid.data());
+      for (int a = 0; a < D; ++a) hid[a] = tanh(hid[a]);
+      affine(th + lay.W_e2, th + lay.b_e2, hid.data(), D, D, &f[i * D]);
+    }
+  } else {
+    for (int i = 0; i < N; ++i)
+      for (int a = 0; a < D; ++a) f[i * D + a] = th[lay.E_spin + spin(i) * D + a];
+  }
 
   std::vector<T> e(Q), w(D), z(N * D), m(3 * D), u(D);
   const int n_same[2] = {s.n_up, s.n_dn}, n_opp[2] = {s.n_dn, s.n_up};

@@ -215,12 +215,14 @@ class AnsatzCfg:
     cusp_alpha: float = 1.0
     full_det: int = 0        # 1: one determinant of all N electrons per p (Eq. 22)
     edge_update: int = 0     # 1: edge embeddings iterated between layers (Eq. 16, second case)
+    el_init: int = 0         # 1: initial embeddings from electron-nucleus differences (Eq. 13, second case)
 
 
 def param_layout(system: System, cfg: AnsatzCfg):
     """Flat parameter layout: list of (name, shape, init-kind).
 
-    Order: E_spin[2][D]; per layer l: W_h[D][D], then for edge types
+    Order: E_spin[2][D] (or, with cfg.el_init, the initial-embedding MLP
+    W_e1[D][3M], b_e1[D], W_e2[D][D], b_e2[D]); per layer l: W_h[D][D], then for edge types
     (same-spin, opposite-spin, electron-nucleus) [U[n_rbf][n_rbf], c[n_rbf]
     when cfg.edge_update and l >= 1: the edge-embedding update], W1[D][n_rbf], b1[D],
     W2[D][D], b2[D]; Y[M][D]; W_g[D][3D], b_g[D]; then per spin (up, down)
@@ -230,7 +232,11 @@ def param_layout(system: System, cfg: AnsatzCfg):
     determinants and N for the full determinant (cfg.full_det).
     """
     D, L, K, Q, M = cfg.width, cfg.n_layers, cfg.n_det, cfg.n_rbf, system.n_nuc
-    out = [("E_spin", (2, D), "normal")]
+    if getattr(cfg, "el_init", 0):
+        out = [("W_e1", (D, 3 * M), "xavier"), ("b_e1", (D,), "zero"), ("W_e2", (D, D), "xavier"),
+               ("b_e2", (D,), "zero")]
+    else:
+        out = [("E_spin", (2, D), "normal")]
     for l in range(L):
         out.append((f"W_h{l}", (D, D), "xavier"))
         for t in ("par", "anti", "nuc"):

@@ -270,12 +270,14 @@ def _random_case(name):
         cfg = dataclasses.replace(cfg, full_det=1)
     if name.endswith("_eu"):
         cfg = dataclasses.replace(cfg, edge_update=1)
+    if name.endswith("_ei"):
+        cfg = dataclasses.replace(cfg, el_init=1)
     th = fx.init_params(sys_, cfg, 3)
     r = fx.init_walkers(sys_, 6, 3)
     return sys_, cfg, th, r
 
 
-@pytest.mark.parametrize("name", ["small", "lih", "small_full", "lih_full", "small_eu"])
+@pytest.mark.parametrize("name", ["small", "lih", "small_full", "lih_full", "small_eu", "small_ei", "lih_ei"])
 def test_antisymmetry(name):
     """Exchange of two same-spin electrons flips the sign only (Eqs. 3, 9)."""
     sys_, cfg, th, r = _random_case(name)
@@ -289,7 +291,7 @@ def test_antisymmetry(name):
     np.testing.assert_allclose(b["e_loc"], a["e_loc"], rtol=1e-9, atol=1e-9)
 
 
-@pytest.mark.parametrize("name", ["small", "small_full"])
+@pytest.mark.parametrize("name", ["small", "small_full", "small_ei"])
 def test_opposite_spin_exchange_is_not_a_symmetry(name):
     """Spins are fixed (Sec. 2.2): exchanging an up and a down electron changes psi; the full
     determinant (Eq. 22) is not antisymmetric under it either (Sec. 3.3)."""
@@ -417,7 +419,8 @@ def test_full_determinant_laplace_expansion():
 # ----------------------------------------------------------------------------
 # Derivatives against finite differences
 # ----------------------------------------------------------------------------
-@pytest.mark.parametrize("name", ["small", "lih", "small_full", "lih_full", "small_eu", "lih_eu"])
+@pytest.mark.parametrize("name", ["small", "lih", "small_full", "lih_full", "small_eu", "lih_eu", "small_ei",
+                                  "lih_ei"])
 def test_coordinate_derivatives_finite_differences(name):
     sys_, cfg, th, r = _random_case(name)
     o = oracle.Oracle(sys_, cfg)
@@ -452,11 +455,11 @@ def test_coordinate_derivatives_finite_differences(name):
         assert abs(out["e_loc"][b] - e_fd) <= tol, (out["e_loc"][b], e_fd, tol)
 
 
-@pytest.mark.parametrize("edge_update", [0, 1])
-def test_parameter_gradient_finite_differences(edge_update):
+@pytest.mark.parametrize("edge_update,el_init", [(0, 0), (1, 0), (0, 1)])
+def test_parameter_gradient_finite_differences(edge_update, el_init):
     """d log|psi| / d theta by dual numbers vs central differences (h = 1e-4... 1e-5, FP64)."""
     wl = fx.workload("lih_fp64")
-    sys_, cfg = wl.system, dataclasses.replace(wl.cfg, edge_update=edge_update)
+    sys_, cfg = wl.system, dataclasses.replace(wl.cfg, edge_update=edge_update, el_init=el_init)
     o = oracle.Oracle(sys_, cfg)
     th = fx.init_params(sys_, cfg, 0)
     r = fx.init_walkers(sys_, 2, 0)
@@ -626,6 +629,50 @@ def test_iterated_edge_embedding_zero_update_reduces(name):
     np.testing.assert_allclose(b["e_loc"], a["e_loc"], rtol=1e-11, atol=1e-11)
     th_u[pidx(sys_, cfg_u, "U_anti1")] = 0.5  # and a non-zero update changes psi
     assert np.all(np.abs(oracle.Oracle(sys_, cfg_u).evaluate(th_u, r)[0] - a["logabs"]) > 1e-9)
+
+
+def test_electron_nucleus_initial_embedding_closed_form():
+    """Eq. (13), second case, with one-hot weights: W_e1 rows pick single components of the
+    difference vectors r_i - R_I, W_e2 = diag(g); with one layer whose update is switched off
+    (W_g = 0, b_g = 0) the final embeddings are f_i = g * tanh(x_i[k] + beta) + b_e2."""
+    sys_ = small_system()  # 2 up, 1 down, nuclei at R_0, R_1
+    D = 4
+    cfg = fx.AnsatzCfg(D, 1, 1, use_cusp=0, el_init=1)
+    th = fx.init_params(sys_, cfg, 5)
+    picks = [(0, 0), (1, 2), (0, 1), (1, 0)]  # feature a <- (nucleus I, component c)
+    W1 = np.zeros((D, 6))
+    for a, (I, c) in enumerate(picks):
+        W1[a, 3 * I + c] = 1.0
+    beta, g, b2 = np.array([0.3, -0.2, 0.0, 0.5]), np.array([1.5, -0.7, 2.0, 0.4]), np.array([0.1, 0, -0.3, 0.2])
+    setp(th, sys_, cfg, "W_e1", W1)
+    setp(th, sys_, cfg, "b_e1", beta)
+    setp(th, sys_, cfg, "W_e2", np.diag(g))
+    setp(th, sys_, cfg, "b_e2", b2)
+    setp(th, sys_, cfg, "W_g0", 0.0)
+    setp(th, sys_, cfg, "b_g0", 0.0)
+    r = fx.init_walkers(sys_, 1, 4)
+    f, _ = oracle.Oracle(sys_, cfg).intermediates(th, r)
+    for i in range(3):
+        for a, (I, c) in enumerate(picks):
+            x = r[0, i, c] - sys_.R[I, c]
+            assert f[i, a] == pytest.approx(g[a] * math.tanh(x + beta[a]) + b2[a], rel=1e-14, abs=1e-15)
+
+
+def test_electron_nucleus_initial_embedding_frame():
+    """Difference vectors are translation invariant but turn with the molecule: a common shift of
+    electrons and nuclei leaves psi unchanged, a common rotation does not (with the spin-only
+    embedding it does, see the rigid-motion test)."""
+    sys_, cfg, th, r = _random_case("small_ei")
+    a = oracle.Oracle(sys_, cfg).local_energy(th, r)
+    t = np.array([0.7, -1.3, 0.4])
+    sys_t = fx.System(Z=sys_.Z, R=sys_.R + t, n_up=sys_.n_up, n_down=sys_.n_down)
+    b = oracle.Oracle(sys_t, cfg).local_energy(th, r + t)
+    np.testing.assert_allclose(b["logabs"], a["logabs"], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(b["e_loc"], a["e_loc"], rtol=1e-9, atol=1e-9)
+    Q = rand_rotation(np.random.default_rng(8))
+    sys_q = fx.System(Z=sys_.Z, R=sys_.R @ Q.T, n_up=sys_.n_up, n_down=sys_.n_down)
+    lq, _ = oracle.Oracle(sys_q, cfg).evaluate(th, r @ Q.T)
+    assert np.all(np.abs(lq - a["logabs"]) > 1e-8)
 
 
 def test_orbital_head_and_jastrow_layout():
