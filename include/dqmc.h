@@ -29,7 +29,7 @@
  *
  * Flat parameter vector (same dtype as the handle's arithmetic, see below),
  * matrices [out][in] row-major, in this order:
- *   E_spin[2][D];
+ *   E_spin[2][D], or with el_init W_e1[D][3 n_nuc], b_e1[D], W_e2[D][D], b_e2[D];
  *   per layer l < n_layers:
  *     W_h[D][D];
  *     for the edge types same-spin, opposite-spin, electron-nucleus:
@@ -79,7 +79,7 @@ typedef enum {
   DQ_ERR_NONFINITE = 4,  /* reserved: reported via dq_last_device_status */
   DQ_ERR_WORKSPACE = 5,  /* workspace missing, too small or misaligned   */
   DQ_ERR_TIMEOUT = 6,    /* a bounded device wait gave up                */
-  DQ_ERR_UNSUPPORTED = 7 /* operation not available in this precision    */
+  DQ_ERR_UNSUPPORTED = 7 /* not available in this precision or setting */
 } dq_status;
 
 typedef enum { DQ_FP64 = 0, DQ_FP32 = 1, DQ_BF16_MIXED = 2 } dq_precision;
@@ -132,6 +132,12 @@ typedef struct {
                         *    f^l = f^{l-1} + tanh(U^{l,t} f^{l-1} + c^{l,t})
                         *    per edge type t, f^0 = e(d).  Other values:
                         *    DQ_ERR_ARG.                                   */
+  int32_t el_init;     /* 0: f_i^0 = E_spin[spin of i] (Eq. 13, first case);
+                        * 1: f_i^0 = W_e2 tanh(W_e1 x_i + b_e1) + b_e2 with
+                        *    x_i = (r_i - R_1, ..., r_i - R_M) (Eq. 13,
+                        *    second case); not rotation invariant.  Not
+                        *    available in batches (dq_create_multi returns
+                        *    DQ_ERR_UNSUPPORTED).  Other values: DQ_ERR_ARG. */
 } dq_ansatz_cfg;
 
 typedef struct dq_handle_s* dq_handle;

@@ -59,7 +59,7 @@ class _Cfg(ctypes.Structure):
     _fields_ = [("width", ctypes.c_int32), ("n_layers", ctypes.c_int32), ("n_det", ctypes.c_int32),
                 ("n_rbf", ctypes.c_int32), ("rbf_cutoff", ctypes.c_double), ("use_jastrow", ctypes.c_int32),
                 ("use_cusp", ctypes.c_int32), ("cusp_alpha", ctypes.c_double), ("full_det", ctypes.c_int32),
-                ("edge_update", ctypes.c_int32)]
+                ("edge_update", ctypes.c_int32), ("el_init", ctypes.c_int32)]
 
 
 _lib = None
@@ -145,7 +145,7 @@ class Ansatz:
 
     ``system`` needs ``Z``, ``R`` (bohr), ``n_up``, ``n_down``; ``cfg`` needs
     ``width, n_layers, n_det, n_rbf, rbf_cutoff, use_jastrow, use_cusp,
-    cusp_alpha`` and optionally ``full_det``, ``edge_update`` (see :mod:`paper_2307_14123_gb300.fixtures`).
+    cusp_alpha`` and optionally ``full_det``, ``edge_update``, ``el_init`` (see :mod:`paper_2307_14123_gb300.fixtures`).
     """
 
     def __init__(self, system, cfg, precision="fp32", device=None):
@@ -166,7 +166,8 @@ class Ansatz:
                        int(system.n_up), int(system.n_down))
         cfgc = _Cfg(int(cfg.width), int(cfg.n_layers), int(cfg.n_det), int(cfg.n_rbf), float(cfg.rbf_cutoff),
                     int(cfg.use_jastrow), int(cfg.use_cusp), float(cfg.cusp_alpha),
-                    int(getattr(cfg, "full_det", 0)), int(getattr(cfg, "edge_update", 0)))
+                    int(getattr(cfg, "full_det", 0)), int(getattr(cfg, "edge_update", 0)),
+                    int(getattr(cfg, "el_init", 0)))
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(self.lib.dq_create(ctypes.byref(sysc), ctypes.byref(cfgc), PRECISIONS[precision], ctypes.byref(h)))
@@ -452,7 +453,8 @@ def _sys_cfg(system, cfg, keep):
                    int(system.n_up), int(system.n_down))
     cfgc = _Cfg(int(cfg.width), int(cfg.n_layers), int(cfg.n_det), int(cfg.n_rbf), float(cfg.rbf_cutoff),
                 int(cfg.use_jastrow), int(cfg.use_cusp), float(cfg.cusp_alpha),
-                    int(getattr(cfg, "full_det", 0)), int(getattr(cfg, "edge_update", 0)))
+                    int(getattr(cfg, "full_det", 0)), int(getattr(cfg, "edge_update", 0)),
+                    int(getattr(cfg, "el_init", 0)))
     return sysc, cfgc
 
 

@@ -21,11 +21,24 @@ namespace dq {
 
 // nc_up, nc_dn: orbitals per determinant of the spin-up and spin-down networks;
 // edge_update: the edge-embedding maps U, c of layers l >= 1 precede each type's filter.
-ParamOffsets make_offsets(int D, int L, int K, int Q, int M, int nc_up, int nc_dn, int edge_update) {
+// el_init: the initial-embedding MLP W_e1[D][3M], b_e1[D], W_e2[D][D], b_e2[D] in place of E_spin.
+ParamOffsets make_offsets(int D, int L, int K, int Q, int M, int nc_up, int nc_dn, int edge_update, int el_init) {
   ParamOffsets o{};
   int64_t p = 0;
-  o.E_spin = p;
-  p += 2 * (int64_t)D;
+  o.E_spin = o.W_e1 = o.b_e1 = o.W_e2 = o.b_e2 = -1;
+  if (el_init) {
+    o.W_e1 = p;
+    p += (int64_t)D * 3 * M;
+    o.b_e1 = p;
+    p += D;
+    o.W_e2 = p;
+    p += (int64_t)D * D;
+    o.b_e2 = p;
+    p += D;
+  } else {
+    o.E_spin = p;
+    p += 2 * (int64_t)D;
+  }
   for (int l = 0; l < L; ++l) {
     auto& y = o.layer[l];
     y.W_h = p;
@@ -314,11 +327,17 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
   const int E = h.edges.n_all;
   const int Wo = K * h.det_n();
   const int kb = jets ? 0 : kValueOffset;
-  DQ_LAUNCH(h, kb + PK_LAYER0, launch_layer0_node<T>(h, FwdDims{Bmax, N, h.n_up, h.n_dn, h.M, D, K, h.Q, C}, params, bf, s));
+  if (!h.el_init)
+    DQ_LAUNCH(h, kb + PK_LAYER0, launch_layer0_node<T>(h, FwdDims{Bmax, N, h.n_up, h.n_dn, h.M, D, K, h.Q, C}, params, bf, s));
   for (int64_t b0 = 0; b0 < B; b0 += Bmax) {
     const int64_t nb = std::min<int64_t>(Bmax, B - b0);
     const FwdDims d{nb, N, h.n_up, h.n_dn, h.M, D, K, h.Q, C};
     DQ_LAUNCH(h, kb + PK_GEOMETRY, launch_geometry<T>(h, d, r + b0 * N * 3, bf, s));
+    // embeddings of the electron-nucleus difference vectors (Eq. 13, second case): layer 0 then
+    // takes the general path below instead of the spin-embedding shortcut
+    if (h.el_init)
+      DQ_LAUNCH(h, kb + PK_LAYER0, launch_el_init<T>(h, d, params, r + b0 * N * 3, bf.F, use_tc ? bf.F_bf : nullptr,
+                                                    nullptr, nullptr, s));
     for (int l = 0; l < h.L; ++l) {
       const auto& y = h.off.layer[l];
       if (h.edge_update && l > 0)  // edge embeddings of layer l, in place (Eq. 16, second case)
@@ -347,7 +366,7 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
       }
       const RowMap node{(int64_t)N * C, (int64_t)N * C * D, D};
       const int64_t rows = nb * N * C;
-      if (l == 0) {
+      if (l == 0 && !h.el_init) {
         DQ_LAUNCH(h, kb + PK_MESSAGES, launch_messages<T>(h, d, params, l, true, bf, s));
       } else {
         if (use_tc) {
@@ -377,7 +396,7 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
         DQ_LAUNCH(h, kb + PK_GEMM_UPDATE, gemm_nt<T>(bf.msg, mrow, params + y.W_g, params + y.b_g, C, bf.Z, node, rows,
                                                      D, 3 * D, false, s));
       }
-      DQ_LAUNCH(h, kb + PK_UPDATE, launch_update<T>(h, d, params, l == 0, bf, s));
+      DQ_LAUNCH(h, kb + PK_UPDATE, launch_update<T>(h, d, params, l == 0 && !h.el_init, bf, s));
     }
     const int ns[2] = {h.n_up, h.n_dn}, i0[2] = {0, h.n_up};
     if (use_t3) {  // both spins' orbitals in one launch
@@ -430,6 +449,7 @@ struct GradPlan {
   size_t geo, rbf, eh, ew, zl, msg, u, F, phi, det, js, jh, z0;  // saved forward
   size_t fbar, ubar, mbar, zbar, wbar, hbar, phibar, beta, cbar, jhbar, gt, sbar, envbar, ybar, part, done, wt3, wt3t;
   size_t ebar, abar;  // edge-embedding adjoints (iterated edge embeddings only)
+  size_t h0, x0;      // hidden layer and inputs of the electron-nucleus initial embedding
   int64_t part_elems;
   size_t total;
 };
@@ -472,8 +492,10 @@ GradPlan plan_grad(const dq_handle_s& h, int64_t Bc, size_t elem) {
   p.envbar = take(Bc * 2 * 2 * Wo * M * elem);
   p.ybar = take(Bc * M * D * elem);
   p.ebar = take(h.edge_update ? Bc * E * Q * elem : 0);
+  p.h0 = take(h.el_init ? Bc * N * D * elem : 0);
+  p.x0 = take(h.el_init ? Bc * N * 3 * M * elem : 0);
   p.abar = take(h.edge_update ? Bc * E * Q * elem : 0);
-  const int64_t blk = std::max({3 * D * D, D * D, D * Q, Wo * D, Wo * M, M * D, K, D, Q * Q});
+  const int64_t blk = std::max({3 * D * D, D * D, D * Q, Wo * D, Wo * M, M * D, K, D, Q * Q, 3 * M * D});
   p.part_elems = 64 * blk;
   p.part = take(p.part_elems * elem);
   p.done = take(kColsumReduceCounters * sizeof(unsigned int));
@@ -548,9 +570,14 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
     auto F = [&](int l) { return buf(pl.F) + (int64_t)l * Bmax * N * D; };
     // edge embeddings of layer l (one shared buffer unless they are iterated)
     auto RB = [&](int l) { return buf(pl.rbf) + (h.edge_update ? (int64_t)l * Bmax * E * Q : 0); };
-    DQ_LAUNCH(h, kValueOffset + PK_LAYER0, launch_layer0_node<T>(h, d, params, v, s));
+    if (!h.el_init) DQ_LAUNCH(h, kValueOffset + PK_LAYER0, launch_layer0_node<T>(h, d, params, v, s));
     DQ_LAUNCH(h, kValueOffset + PK_GEOMETRY, launch_geometry<T>(h, d, r + b0 * N * 3, v, s));
-    DQ_LAUNCH(h, kValueOffset + PK_UPDATE, launch_fill_spin_rows<T>(F(0), params + off.E_spin, nb, N, h.n_up, D, s));
+    if (h.el_init)
+      DQ_LAUNCH(h, kValueOffset + PK_LAYER0, launch_el_init<T>(h, d, params, r + b0 * N * 3, F(0), nullptr,
+                                                              buf(pl.h0), buf(pl.x0), s));
+    else
+      DQ_LAUNCH(h, kValueOffset + PK_UPDATE, launch_fill_spin_rows<T>(F(0), params + off.E_spin, nb, N, h.n_up, D, s));
+    const bool spin0 = !h.el_init;  // layer 0 on the spin embeddings (constant z, f^0 from E_spin)
     for (int l = 0; l < L; ++l) {
       const auto& y = off.layer[l];
       v.eh = EH(l);
@@ -578,14 +605,14 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
                                v.ew + (int64_t)e0[t] * D, m, nb * ng[t], D, D, false, s));
         }
       }
-      if (l > 0 && use_t3)
+      if ((l > 0 || !spin0) && use_t3)
         DQ_LAUNCH(h, kValueOffset + PK_GEMM_NODE,
                   gemm_tf32x3_tc(reinterpret_cast<const float*>(F(l)), nb * N, D, D, w3.wh(l, 0), w3.wh(l, 1), D,
                                  nullptr, 1, reinterpret_cast<float*>(ZL(l)), D, h.d_status, s));
-      else if (l > 0)
+      else if (l > 0 || !spin0)
         DQ_LAUNCH(h, kValueOffset + PK_GEMM_NODE, gemm_nt<T>(F(l), rm(D), params + y.W_h, nullptr, 1, ZL(l), rm(D), nb * N, D, D,
                                              false, s));
-      DQ_LAUNCH(h, kValueOffset + PK_MESSAGES, launch_messages<T>(h, d, params, l, l == 0, v, s));
+      DQ_LAUNCH(h, kValueOffset + PK_MESSAGES, launch_messages<T>(h, d, params, l, l == 0 && spin0, v, s));
       if (use_t3)
         DQ_LAUNCH(h, kValueOffset + PK_GEMM_UPDATE,
                   gemm_tf32x3_tc(reinterpret_cast<const float*>(MS(l)), nb * N, 3 * D, 3 * D, w3.wg(l, 0),
@@ -594,7 +621,7 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
       else
         DQ_LAUNCH(h, kValueOffset + PK_GEMM_UPDATE, gemm_nt<T>(MS(l), rm(3 * D), params + y.W_g, params + y.b_g, 1, U(l), rm(D), nb * N,
                                            D, 3 * D, false, s));
-      DQ_LAUNCH(h, kValueOffset + PK_UPDATE, launch_update_io<T>(h, d, params, l == 0, U(l), F(l), F(l + 1), s));
+      DQ_LAUNCH(h, kValueOffset + PK_UPDATE, launch_update_io<T>(h, d, params, l == 0 && spin0, U(l), F(l), F(l + 1), s));
     }
     v.F = F(L);
     for (int sg = 0; sg < 2; ++sg) {
@@ -673,8 +700,8 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
                                  3 * D, nullptr, 1, reinterpret_cast<float*>(mbar), 3 * D, h.d_status, s));
       else
         DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(ubar, rm(D), params + y.W_g, mbar, rm(3 * D), nb * N, 3 * D, D, false, s));
-      DQ_LAUNCH(h, PK_BWD_MESSAGES, launch_msg_bwd<T>(h, nb, mbar, ZL(l), v.z0, EW(l), params + y.Y, l == 0, zbar, wbar,
-                                                      ybar, s));
+      DQ_LAUNCH(h, PK_BWD_MESSAGES, launch_msg_bwd<T>(h, nb, mbar, ZL(l), v.z0, EW(l), params + y.Y, l == 0 && spin0,
+                                                      zbar, wbar, ybar, s));
       DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ybar, rm((int64_t)M * D), nullptr, rm(1), 1, M * D, 1, y.Y, 1));
       DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(zbar, rm(D), F(l), rm(D), N, D, D, y.W_h, D));
       if (use_t3)
@@ -723,11 +750,22 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
         }
       }
     }
-    for (int sg = 0; sg < 2; ++sg) {
-      if (ns[sg] == 0) continue;
-      const RowMap mf{(int64_t)ns[sg], (int64_t)N * D, D};
-      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(fbar + (int64_t)i0[sg] * D, mf, nullptr, rm(1), ns[sg], D, 1,
-                                         off.E_spin + (int64_t)sg * D, 1));
+    if (h.el_init) {  // through f^0 = W_e2 tanh(W_e1 x + b_e1) + b_e2 (Eq. 13, second case)
+      const int M3 = 3 * M;
+      T* H0 = buf(pl.h0);
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(fbar, rm(D), H0, rm(D), N, D, D, off.W_e2, D));
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(fbar, rm(D), nullptr, rm(1), N, D, 1, off.b_e2, 1));
+      DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(fbar, rm(D), params + off.W_e2, ubar, rm(D), nb * N, D, D, false, s));
+      DQ_LAUNCH(h, PK_BWD_UPDATE, launch_tanh_bwd<T>(ubar, H0, nb * N * D, false, ubar, s));
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ubar, rm(D), buf(pl.x0), rm(M3), N, D, M3, off.W_e1, M3));
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ubar, rm(D), nullptr, rm(1), N, D, 1, off.b_e1, 1));
+    } else {
+      for (int sg = 0; sg < 2; ++sg) {
+        if (ns[sg] == 0) continue;
+        const RowMap mf{(int64_t)ns[sg], (int64_t)N * D, D};
+        DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(fbar + (int64_t)i0[sg] * D, mf, nullptr, rm(1), ns[sg], D, 1,
+                                           off.E_spin + (int64_t)sg * D, 1));
+      }
     }
   }
   return DQ_OK;
@@ -1221,6 +1259,7 @@ dq_status dq_create(const dq_system* sys, const dq_ansatz_cfg* cfg, int32_t prec
     return DQ_ERR_SHAPE;
   if (cfg->full_det != 0 && cfg->full_det != 1) return DQ_ERR_ARG;
   if (cfg->edge_update != 0 && cfg->edge_update != 1) return DQ_ERR_ARG;
+  if (cfg->el_init != 0 && cfg->el_init != 1) return DQ_ERR_ARG;
   if (cfg->full_det && N > kMaxSpin) return DQ_ERR_SHAPE;  // the N x N matrix obeys the spin-block limit
   for (int I = 0; I < M; ++I) {
     if (!isfinite(sys->Z[I])) return DQ_ERR_ARG;
@@ -1248,7 +1287,8 @@ dq_status dq_create(const dq_system* sys, const dq_ansatz_cfg* cfg, int32_t prec
   h->use_cusp = cfg->use_cusp ? 1 : 0;
   h->full_det = cfg->full_det;
   h->edge_update = cfg->edge_update;
-  h->off = make_offsets(h->D, h->L, h->K, h->Q, M, h->ncol(0), h->ncol(1), h->edge_update);
+  h->el_init = cfg->el_init;
+  h->off = make_offsets(h->D, h->L, h->K, h->Q, M, h->ncol(0), h->ncol(1), h->edge_update, h->el_init);
   double vnn = 0;
   for (int I = 0; I < M; ++I)
     for (int J = I + 1; J < M; ++J) {
@@ -1660,6 +1700,8 @@ dq_status dq_create_multi(int32_t n_mol, const dq_system* systems, const dq_ansa
   if (precision != DQ_FP32 && precision != DQ_BF16_MIXED) return DQ_ERR_ARG;
   for (int m = 0; m < n_mol; ++m)
     if (cfgs[m].n_layers != cfgs[0].n_layers || cfgs[m].width % 32) return DQ_ERR_SHAPE;
+  for (int m = 0; m < n_mol; ++m)  // batches run layer 0 on the spin embeddings
+    if (cfgs[m].el_init) return DQ_ERR_UNSUPPORTED;
   dq_multi_s* g = new (std::nothrow) dq_multi_s();
   if (!g) return DQ_ERR_ARG;
   if (cudaGetDevice(&g->device) != cudaSuccess) {

@@ -16,7 +16,8 @@ constexpr int kMaxNuc = 64;
 
 // Element offsets of the blocks of the flat parameter vector (layout in dqmc.h).
 struct ParamOffsets {
-  int64_t E_spin;
+  int64_t E_spin;                    // -1 with the electron-nucleus initial embedding
+  int64_t W_e1, b_e1, W_e2, b_e2;    // that embedding's MLP (-1 without it)
   struct Layer {
     int64_t W_h, U[3], c[3], W1[3], b1[3], W2[3], b2[3], Y, W_g, b_g;  // U, c: -1 without edge updates
   } layer[16];
@@ -24,7 +25,7 @@ struct ParamOffsets {
 };
 constexpr int kMaxLayers = 16;
 
-ParamOffsets make_offsets(int D, int L, int K, int Q, int M, int nc_up, int nc_dn, int edge_update);
+ParamOffsets make_offsets(int D, int L, int K, int Q, int M, int nc_up, int nc_dn, int edge_update, int el_init);
 
 // Edge bookkeeping.  Electron-electron pairs (i < j) are ordered by type:
 // up-up pairs, down-down pairs (together: same spin), then up-down pairs
@@ -147,6 +148,7 @@ struct dq_handle_s {
   int use_jastrow = 1, use_cusp = 1;
   int full_det = 0;  // 1: one N x N determinant per p (Eq. 22) instead of det A^up det A^down (Eq. 21)
   int edge_update = 0;  // 1: edge embeddings iterated between layers (Eq. 16, second case)
+  int el_init = 0;      // 1: initial embeddings from electron-nucleus differences (Eq. 13, second case)
   double Vnn = 0;
   // Orbitals per determinant of spin sg's orbital network: n_sg, or N for the full determinant.
   int ncol(int sg) const { return full_det ? N : (sg ? n_dn : n_up); }
@@ -325,6 +327,13 @@ cudaError_t launch_edge_update_group(const MolFwd<T>* m, int n, int layer, const
 template <class T>
 cudaError_t launch_edge_update(const dq_handle_s& h, const FwdDims& d, const T* params, int layer, const T* src,
                                T* dst, cudaStream_t s);
+// Initial embeddings from the electron-nucleus difference vectors (Eq. 13, second case) for a
+// chunk of d.Bc walkers at r: F[Bc][N][C][D] with its jets (C > 1) or values (C = 1); Fbf
+// (nullable) a BF16 copy; H0 [Bc N][D] and X0 [Bc N][3M] (nullable) keep the hidden layer
+// and the difference vectors for the reverse pass.
+template <class T>
+cudaError_t launch_el_init(const dq_handle_s& h, const FwdDims& d, const T* params, const T* r, T* F, void* Fbf, T* H0,
+                           T* X0, cudaStream_t s);
 template <class T>
 cudaError_t launch_layer0_node_group(const MolFwd<T>* m, int n, cudaStream_t s);
 template <class T>

@@ -316,6 +316,98 @@ __global__ void __launch_bounds__(256) edge_update_kernel_group(const __grid_con
   GRP_STATIC(m_, edge_update_kernel_body<T>(grp_bx(g, K_, l_), g.nbx[K_], g.a[K_]);)
 }
 
+// ---------------------------------------------------------------------------
+// Initial electron embeddings from the electron-nucleus difference vectors
+// (Eq. 13, second case): x_i = (r_i - R_1, ..., r_i - R_M) and
+// f^0_i = W_e2 tanh(W_e1 x_i + b_e1) + b_e2, with its jets in the coordinates.
+// Only r_i moves x_i, and d x_i / d r_{i,c} = (e_c, ..., e_c); a = W_e1 x_i + b_e1
+// is linear in r_i, so with h = tanh a, g = 1 - h^2 and u_c = sum_I W_e1[:, 3I + c]:
+//   d h / d r_{i,c} = g u_c,   lap_i h = -2 h g sum_c u_c^2,
+// and f^0 = W_e2 h + b_e2 channel by channel (value, the three channels of
+// r_i, the Laplacian; every other channel is zero).  One thread per feature
+// (blockDim = D), `per` electrons per CTA sharing each W_e2 load.
+// ---------------------------------------------------------------------------
+constexpr int kElInitMax = 8;
+template <class T>
+__global__ void __launch_bounds__(512)
+    el_init_kernel(const T* __restrict__ r, const T* __restrict__ R, const T* __restrict__ params, int64_t W_e1,
+                   int64_t b_e1, int64_t W_e2, int64_t b_e2, int64_t Bc, int N, int M, int D, int C, int per,
+                   T* __restrict__ F, __nv_bfloat16* __restrict__ Fbf, T* __restrict__ H0, T* __restrict__ X0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M3 = 3 * M, nch = C > 1 ? 5 : 1;
+  T* xs = reinterpret_cast<T*>(smem_raw);  // [per][3M]
+  T* Hs = xs + per * M3;                   // [per][nch][D]
+  const int a = threadIdx.x;
+  const int64_t n_el = Bc * N, e0 = (int64_t)blockIdx.x * per;
+  const int ne = (int)min((int64_t)per, n_el - e0);
+  for (int k = a; k < ne * M3; k += blockDim.x) {
+    const int e = k / M3, kk = k - e * M3, I = kk / 3, c = kk - I * 3;
+    const T x = r[(e0 + e) * 3 + c] - R[I * 3 + c];
+    xs[k] = x;
+    if (X0) X0[(e0 + e) * M3 + kk] = x;
+  }
+  __syncthreads();
+  const T* w1 = params + W_e1 + (int64_t)a * M3;
+  T u0 = 0, u1 = 0, u2 = 0;
+  for (int I = 0; I < M; ++I) {
+    u0 += w1[3 * I];
+    u1 += w1[3 * I + 1];
+    u2 += w1[3 * I + 2];
+  }
+  const T usq = u0 * u0 + u1 * u1 + u2 * u2;
+  for (int e = 0; e < ne; ++e) {
+    T v = params[b_e1 + a];
+    for (int k = 0; k < M3; ++k) v += w1[k] * xs[e * M3 + k];
+    const T h = tanh_t(v), g = T(1) - h * h;
+    T* hs = Hs + (e * nch) * D + a;
+    hs[0] = h;
+    if (nch == 5) {
+      hs[D] = g * u0;
+      hs[2 * D] = g * u1;
+      hs[3 * D] = g * u2;
+      hs[4 * D] = T(-2) * h * g * usq;
+    }
+    if (H0) H0[(e0 + e) * D + a] = h;
+  }
+  __syncthreads();
+  T acc[kElInitMax][5];
+#pragma unroll
+  for (int e = 0; e < kElInitMax; ++e)
+#pragma unroll
+    for (int c = 0; c < 5; ++c) acc[e][c] = 0;
+  const T* w2 = params + W_e2 + (int64_t)a * D;
+  for (int k = 0; k < D; ++k) {
+    const T w = w2[k];
+#pragma unroll
+    for (int e = 0; e < kElInitMax; ++e) {
+      if (e >= ne) break;
+      const T* hs = Hs + (e * nch) * D + k;
+      acc[e][0] += w * hs[0];
+      if (nch == 5) {
+#pragma unroll
+        for (int c = 1; c < 5; ++c) acc[e][c] += w * hs[c * D];
+      }
+    }
+  }
+  const T bias = params[b_e2 + a];
+#pragma unroll
+  for (int e = 0; e < kElInitMax; ++e) {
+    if (e >= ne) break;
+    const int64_t el = e0 + e;
+    const int i = (int)(el % N);
+    T* o = F + el * C * D + a;
+    __nv_bfloat16* ob = Fbf ? Fbf + el * C * D + a : nullptr;
+    for (int ch = 0; ch < C; ++ch) {
+      T v = 0;
+      if (ch == 0) v = acc[e][0] + bias;
+      else if (ch == C - 1) v = acc[e][4];
+      else if (ch >= 1 + 3 * i && ch < 4 + 3 * i) v = acc[e][ch - 3 * i];
+      o[(int64_t)ch * D] = v;
+      if (ob) ob[(int64_t)ch * D] = __float2bfloat16_rn((float)v);
+    }
+  }
+}
+
 // z0[s][a] = (W_h^0 E_spin[s])[a]: the node map of layer 0 on the spin embeddings.
 template <class T>
 struct layer0_node_kernel_args {
@@ -1804,7 +1896,7 @@ cudaError_t launch_update(const dq_handle_s& h, const FwdDims& d, const T* param
 template <class T>
 cudaError_t launch_update_io(const dq_handle_s& h, const FwdDims& d, const T* params, bool from_spin, const T* P,
                              const T* Fin, T* Fout, cudaStream_t s, void* Fbf) {
-  update_kernel<T><<<blocks(d.Bc * d.N * d.D, 256), 256, 0, s>>>(P, Fin, Fout, params + h.off.E_spin, d.Bc, d.N,
+  update_kernel<T><<<blocks(d.Bc * d.N * d.D, 256), 256, 0, s>>>(P, Fin, Fout, params + std::max<int64_t>(h.off.E_spin, 0), d.Bc, d.N,
                                                                  d.n_up, d.C, d.D, from_spin ? 1 : 0,
                                                                  static_cast<__nv_bfloat16*>(Fbf));
   return cudaGetLastError();
@@ -1958,6 +2050,24 @@ cudaError_t launch_edge_update_group(const MolFwd<T>* m, int n, int l, const T* 
 }
 
 template <class T>
+cudaError_t launch_el_init(const dq_handle_s& h, const FwdDims& d, const T* params, const T* r, T* F, void* Fbf, T* H0,
+                           T* X0, cudaStream_t s) {
+  if (d.Bc <= 0) return cudaSuccess;
+  const int D = h.D, M3 = 3 * h.M, nch = d.C > 1 ? 5 : 1;
+  int per = (int)std::min<size_t>(kElInitMax, (96 * 1024) / ((size_t)nch * D * sizeof(T) + M3 * sizeof(T)));
+  per = std::max(per, 1);
+  const size_t smem = (size_t)per * (M3 + nch * D) * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(el_init_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const T* R = sizeof(T) == 8 ? reinterpret_cast<const T*>(h.d_R) : reinterpret_cast<const T*>(h.d_Rf);
+  const int64_t n_el = d.Bc * h.N;
+  el_init_kernel<T><<<(unsigned)((n_el + per - 1) / per), D, smem, s>>>(
+      r, R, params, h.off.W_e1, h.off.b_e1, h.off.W_e2, h.off.b_e2, d.Bc, h.N, h.M, D, d.C, per, F,
+      static_cast<__nv_bfloat16*>(Fbf), H0, X0);
+  return cudaGetLastError();
+}
+
+template <class T>
 cudaError_t launch_edge_update(const dq_handle_s& h, const FwdDims& d, const T* params, int l, const T* src, T* dst,
                                cudaStream_t s) {
   const MolFwd<T> m{&h, d, params, FwdBuffers<T>{}};
@@ -2093,7 +2203,7 @@ cudaError_t launch_update_group(const MolFwd<T>* m, int n, bool from_spin, cudaS
   for (int k = 0; k < n; ++k) {
     const FwdDims& d = m[k].d;
     if (d.Bc <= 0) continue;
-    g.add({m[k].b.Z, m[k].b.F, m[k].b.F, m[k].params + m[k].h->off.E_spin, d.Bc, d.N, d.n_up, d.C, d.D,
+    g.add({m[k].b.Z, m[k].b.F, m[k].b.F, m[k].params + std::max<int64_t>(m[k].h->off.E_spin, 0), d.Bc, d.N, d.n_up, d.C, d.D,
            from_spin ? 1 : 0, static_cast<__nv_bfloat16*>(m[k].b.F_bf)},
           blocks(d.Bc * d.N * d.D, 256));
   }
@@ -2217,6 +2327,8 @@ cudaError_t launch_combine_group(const MolFwd<T>* m, int n, T* const* logabs, in
                                                    cudaStream_t);                                                 \
   template cudaError_t launch_edge_update<T>(const dq_handle_s&, const FwdDims&, const T*, int, const T*, T*,      \
                                              cudaStream_t);                                                       \
+  template cudaError_t launch_el_init<T>(const dq_handle_s&, const FwdDims&, const T*, const T*, T*, void*, T*, T*, \
+                                         cudaStream_t);                                                           \
   template cudaError_t launch_layer0_node_group<T>(const MolFwd<T>*, int, cudaStream_t);                          \
   template cudaError_t launch_messages_group<T>(const MolFwd<T>*, int, int, bool, cudaStream_t);                  \
   template cudaError_t launch_update_group<T>(const MolFwd<T>*, int, bool, cudaStream_t);                         \
