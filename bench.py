@@ -347,8 +347,10 @@ def pp_leg(h, theta, r, wl, flush, B=512):
 
 def ansatz_variants_leg(h, theta, r, wl, flush, reps=5):
     """Local energies of the ansatz variants on the bench walkers, each timed like the base
-    (spin-factorised determinants, fixed Gaussian edge features): the full determinant (Eq. 22),
-    iterated edge embeddings (Eq. 16, second case), and both (the PauliNet2-style ansatz)."""
+    (spin-factorised determinants, fixed Gaussian edge features, spin initial embeddings): the
+    full determinant (Eq. 22), iterated edge embeddings (Eq. 16, second case), both (the
+    PauliNet2-style ansatz), and initial embeddings from the electron-nucleus difference vectors
+    (Eq. 13, second case)."""
     import dataclasses
 
     import torch
@@ -374,7 +376,8 @@ def ansatz_variants_leg(h, theta, r, wl, flush, reps=5):
     ms_base = timed(h, theta)
     out = {"base": {"value": B / (ms_base / 1e3), "unit": UNIT, "ms_per_call": ms_base, "params": h.P}}
     for name, kw in (("full_determinant", {"full_det": 1}), ("edge_update", {"edge_update": 1}),
-                     ("full_determinant+edge_update", {"full_det": 1, "edge_update": 1})):
+                     ("full_determinant+edge_update", {"full_det": 1, "edge_update": 1}),
+                     ("electron_nucleus_init", {"el_init": 1})):
         cfg = dataclasses.replace(wl.cfg, **kw)
         hv = Ansatz(wl.system, cfg, wl.precision, device=r.device)
         th = torch.tensor(fx.init_params(wl.system, cfg, wl.param_seed), dtype=theta.dtype, device=r.device)
