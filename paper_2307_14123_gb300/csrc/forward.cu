@@ -606,9 +606,6 @@ __device__ __forceinline__ void messages_kernel_body(const int64_t bx_, const in
     if (stage_w1) return W1[(j * N + i) * L + lane];
     return i == j ? T(0) : EWb[((int64_t)Ps[i * N + j] * ej + 1) * D];
   };
-  auto w2_at = [&](int i, int j) -> T {
-    return i == j ? T(0) : EWb[((int64_t)Ps[i * N + j] * ej + 2) * D];
-  };
 
   // ---- phase 1: per-receiver terms (b), (c), (d) ----
   // items: 3N of kind (b) (receiver, axis), 2N of kind (c) (receiver, sender spin), N of kind (d)
@@ -636,18 +633,35 @@ __device__ __forceinline__ void messages_kernel_body(const int64_t bx_, const in
       const int j0 = h == 0 ? 0 : n_up, j1 = h == 0 ? n_up : N;
       const T* zc = Zb + (int64_t)(1 + 3 * i) * D;  // dz_j / dr_i of sender j at zc + j * C * D
       T sv = 0;
-#pragma unroll 4
-      for (int j = j0; j < j1; ++j) {
-        const T v1 = w1_at(i, j);
-        T t = (T(2) * w2_at(i, j) + T(4) * v1 * Id[i * N + j]) * Z0c[j * L + lane];
-        if (!z_const) {
-          const T* u = Us + (i * N + j) * 3;
-          const T* zj = zc + (int64_t)j * C * D;
-          const T cr = u[0] * (zj[0] - Zsf[(j * 3) * L + lane]) + u[1] * (zj[D] - Zsf[(j * 3 + 1) * L + lane]) +
-                       u[2] * (zj[2 * D] - Zsf[(j * 3 + 2) * L + lane]);
-          t += T(2) * v1 * cr;
+      // senders in batches of kCJ: every global load of a batch (w'' and the three channels
+      // dz_j / dr_i) is issued before any is used, so their latencies overlap
+      constexpr int kCJ = 8;
+      for (int jb = j0; jb < j1; jb += kCJ) {
+        T w2v[kCJ], zx[kCJ], zy[kCJ], zz[kCJ];
+#pragma unroll
+        for (int u = 0; u < kCJ; ++u) {
+          const int j = jb + u;
+          const bool ok = j < j1 && j != i;
+          w2v[u] = ok ? EWb[((int64_t)Ps[i * N + j] * ej + 2) * D] : T(0);
+          const T* zj = zc + (int64_t)(ok ? j : i) * C * D;
+          zx[u] = ok && !z_const ? zj[0] : T(0);
+          zy[u] = ok && !z_const ? zj[D] : T(0);
+          zz[u] = ok && !z_const ? zj[2 * D] : T(0);
         }
-        sv += t;
+#pragma unroll
+        for (int u = 0; u < kCJ; ++u) {
+          const int j = jb + u;
+          if (j >= j1) break;
+          const T v1 = w1_at(i, j);
+          T t = (T(2) * w2v[u] + T(4) * v1 * Id[i * N + j]) * Z0c[j * L + lane];
+          if (!z_const) {
+            const T* uu = Us + (i * N + j) * 3;
+            const T cr = uu[0] * (zx[u] - Zsf[(j * 3) * L + lane]) + uu[1] * (zy[u] - Zsf[(j * 3 + 1) * L + lane]) +
+                         uu[2] * (zz[u] - Zsf[(j * 3 + 2) * L + lane]);
+            t += T(2) * v1 * cr;
+          }
+          sv += t;
+        }
       }
       SPc[(i * 3 + (up == (h == 0) ? 0 : 1)) * L + lane] = sv;
       if (h == 0) {
