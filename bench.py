@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--profile-case", type=int, default=0, metavar="B",
                    help="run one call on B walkers of the workload and exit (small case for ncu)")
     p.add_argument("--profile-op", default="local_energy", choices=["local_energy", "grad", "mcmc"])
+    p.add_argument("--msg-ib", type=int, default=0, choices=[0, 4, 8],
+                   help="profile case: receivers per warp task of the jet message kernel (0: library default)")
     return p.parse_args()
 
 
@@ -202,9 +204,9 @@ def peaks():
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of the jet message kernel (layer >= 1 launch) per walker,
-# from an ncu capture of the layer-1 launch on 512 N2 walkers (FP32; summary under profiles/); None
+# from an ncu capture of the layer-1 launch on 512 N2 walkers (FP32, the tuned 4-receiver tile; summary under profiles/); None
 # once the kernel has changed since that capture.
-MSG_DRAM_BYTES_PER_WALKER = (263.808768e6 + 431.145728e6) / 512
+MSG_DRAM_BYTES_PER_WALKER = (263.570432e6 + 432.803840e6) / 512
 
 
 def roofline_for(kind, ms, n, wl, chunk, pk, how):
@@ -265,6 +267,8 @@ def profile_case(args):
     h = Ansatz(wl.system, wl.cfg, wl.precision, device="cuda:0")
     theta = torch.tensor(fx.init_params(wl.system, wl.cfg, wl.param_seed), dtype=dt, device="cuda:0")
     r = torch.tensor(fx.init_walkers(wl.system, args.profile_case, wl.walker_seed), dtype=dt, device="cuda:0")
+    if args.msg_ib:
+        h.set_msg_tile(args.msg_ib)
     if args.profile_op == "grad":
         w = torch.full((args.profile_case,), 1.0 / args.profile_case, dtype=dt, device="cuda:0")
         out = h.grad_logpsi(theta, r, w, 0)
@@ -343,6 +347,33 @@ def pp_leg(h, theta, r, wl, flush, B=512):
     return {"walkers": B, "psi_evaluations": n_eval, "ms_per_call": ms,
             "psi_evaluations_per_s": n_eval / (ms / 1e3),
             "note": "12-point icosahedral quadrature, every electron around both nuclei, synthetic coefficients"}
+
+
+def graph_kernel_count(fn):
+    """Kernel launches of one call of fn: the kernel nodes of a CUDA graph captured from it (the
+    capture enqueues nothing; memset and copy nodes are not counted)."""
+    import ctypes
+
+    import torch
+
+    g = torch.cuda.CUDAGraph(keep_graph=True)
+    with torch.cuda.graph(g):
+        fn()
+    cu = ctypes.CDLL("libcuda.so.1")
+    handle = ctypes.c_void_p(g.raw_cuda_graph())
+    n = ctypes.c_size_t(0)
+    if cu.cuGraphGetNodes(handle, None, ctypes.byref(n)) != 0:
+        raise RuntimeError("cuGraphGetNodes failed")
+    nodes = (ctypes.c_void_p * max(n.value, 1))()
+    if cu.cuGraphGetNodes(handle, nodes, ctypes.byref(n)) != 0:
+        raise RuntimeError("cuGraphGetNodes failed")
+    kind, kernels = ctypes.c_int(), 0
+    for i in range(n.value):
+        if cu.cuGraphNodeGetType(ctypes.c_void_p(nodes[i]), ctypes.byref(kind)) != 0:
+            raise RuntimeError("cuGraphNodeGetType failed")
+        kernels += kind.value == 0  # CU_GRAPH_NODE_TYPE_KERNEL
+    del g
+    return kernels
 
 
 def ansatz_variants_leg(h, theta, r, wl, flush, reps=5):
@@ -598,7 +629,11 @@ def main():
 
     # local_energy alone (same timed-kernel view, from the profile)
     jet_ms = sum(ms for k, (ms, n) in prof.items() if k.startswith("jet.") or k == "esum")
-    launches = sum(n for _, (ms, n) in prof.items())
+    launch_sites = sum(n for _, (ms, n) in prof.items())
+    # kernels of one step: the kernel nodes of a CUDA-graph capture of the same step (a launch
+    # site of the library may launch several kernels, e.g. a split reduction and its sum)
+    kernels_per_step = graph_kernel_count(lambda: step(theta, r, logabs))
+    launches = kernels_per_step * args.steps
     gpu_time_ms = sum(ms for _, (ms, n) in prof.items())
 
     # roofline of the dominant kernel (and of the other main kernels)
@@ -782,6 +817,8 @@ def main():
                 "pseudopotential": pseudo,
                 "ansatz_variants": variants,
                 "gpu_launches": launches,
+                "gpu_kernels_per_step": kernels_per_step,
+                "gpu_launch_sites": launch_sites,
                 "clocks": clk,
                 "local_energy_only": {"value": B * world * args.steps / (jet_ms / 1e3) if jet_ms else None,
                                       "unit": UNIT, "note": "sum of the local_energy kernels' device time"},
