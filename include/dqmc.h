@@ -113,7 +113,8 @@ typedef struct {
 
 /* Ansatz hyper-parameters (Sec. 3). */
 typedef struct {
-  int32_t width;      /* D: embedding width, multiple of 32, <= 512  */
+  int32_t width;      /* D: embedding width, multiple of 32, <= 512;
+                       * a multiple of 64 in DQ_BF16_MIXED          */
   int32_t n_layers;   /* L >= 1 message-passing layers                */
   int32_t n_det;      /* K >= 1 determinant pairs                     */
   int32_t n_rbf;      /* Gaussian distance features, multiple of 8    */
@@ -135,9 +136,8 @@ typedef struct {
   int32_t el_init;     /* 0: f_i^0 = E_spin[spin of i] (Eq. 13, first case);
                         * 1: f_i^0 = W_e2 tanh(W_e1 x_i + b_e1) + b_e2 with
                         *    x_i = (r_i - R_1, ..., r_i - R_M) (Eq. 13,
-                        *    second case); not rotation invariant.  Not
-                        *    available in batches (dq_create_multi returns
-                        *    DQ_ERR_UNSUPPORTED).  Other values: DQ_ERR_ARG. */
+                        *    second case); not rotation invariant.  Other
+                        *    values: DQ_ERR_ARG.                            */
 } dq_ansatz_cfg;
 
 typedef struct dq_handle_s* dq_handle;

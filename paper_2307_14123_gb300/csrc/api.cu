@@ -952,6 +952,10 @@ dq_status run_forward_multi(const dq_multi_s& g, const T* const* params, const T
     }
     if (!any) break;
     DQ_LAUNCH(H, kb + PK_GEOMETRY, launch_geometry_group<T>(mf, n, rq, s));
+    for (int m = 0; m < n; ++m)  // electron-nucleus initial embeddings (Eq. 13, second case)
+      if (g.h[m]->el_init && mf[m].d.Bc > 0)
+        DQ_LAUNCH(H, kb + PK_LAYER0, launch_el_init<T>(*g.h[m], mf[m].d, params[m], rq[m], mf[m].b.F,
+                                                      use_tc ? mf[m].b.F_bf : nullptr, nullptr, nullptr, s));
     for (int l = 0; l < L; ++l) {
       if (l > 0) {  // iterated edge embeddings of the molecules that have them, in place
         const T* es[kMaxGroup];
@@ -980,12 +984,12 @@ dq_status run_forward_multi(const dq_multi_s& g, const T* const* params, const T
                                reinterpret_cast<float*>(mf[m].b.ew) + (int64_t)e0[t] * ej * D, D, seg, false};
       }
       DQ_LAUNCH(H, kb + PK_GEMM_EDGE, gemm_tf32x3_tc_jobs(jd, nj, H.d_status, s));
-      if (l > 0) {  // node map z = W_h f
+      {  // node map z = W_h f (layer 0 only for the molecules without spin embeddings)
         nj = 0;
         for (int m = 0; m < n; ++m) {
           const dq_handle_s& h = *g.h[m];
           const FwdDims& d = mf[m].d;
-          if (d.Bc <= 0) continue;
+          if (d.Bc <= 0 || (l == 0 && !h.el_init)) continue;
           const int64_t rows = d.Bc * d.N * d.C;
           if (use_tc) {
             DQ_LAUNCH(H, kb + PK_GEMM_NODE,
@@ -996,7 +1000,7 @@ dq_status run_forward_multi(const dq_multi_s& g, const T* const* params, const T
                                  w3[m].wh(l, 1), h.D, nullptr, 1, reinterpret_cast<float*>(mf[m].b.Z), h.D, 0, false};
           }
         }
-        if (!use_tc) DQ_LAUNCH(H, kb + PK_GEMM_NODE, gemm_tf32x3_tc_jobs(jd, nj, H.d_status, s));
+        if (!use_tc && nj > 0) DQ_LAUNCH(H, kb + PK_GEMM_NODE, gemm_tf32x3_tc_jobs(jd, nj, H.d_status, s));
       }
       DQ_LAUNCH(H, kb + PK_MESSAGES, launch_messages_group<T>(mf, n, l, l == 0, s));
       nj = 0;
@@ -1257,6 +1261,8 @@ dq_status dq_create(const dq_system* sys, const dq_ansatz_cfg* cfg, int32_t prec
       cfg->n_det < 1 || cfg->n_det > 128 || cfg->n_rbf < 8 || cfg->n_rbf % 8 || cfg->n_rbf > 64 ||
       !(cfg->rbf_cutoff > 0) || !(cfg->cusp_alpha > 0))
     return DQ_ERR_SHAPE;
+  // the BF16 tensor-core GEMMs take K = D and 3D in 64-wide tiles
+  if (precision == DQ_BF16_MIXED && cfg->width % 64) return DQ_ERR_SHAPE;
   if (cfg->full_det != 0 && cfg->full_det != 1) return DQ_ERR_ARG;
   if (cfg->edge_update != 0 && cfg->edge_update != 1) return DQ_ERR_ARG;
   if (cfg->el_init != 0 && cfg->el_init != 1) return DQ_ERR_ARG;
@@ -1700,8 +1706,6 @@ dq_status dq_create_multi(int32_t n_mol, const dq_system* systems, const dq_ansa
   if (precision != DQ_FP32 && precision != DQ_BF16_MIXED) return DQ_ERR_ARG;
   for (int m = 0; m < n_mol; ++m)
     if (cfgs[m].n_layers != cfgs[0].n_layers || cfgs[m].width % 32) return DQ_ERR_SHAPE;
-  for (int m = 0; m < n_mol; ++m)  // batches run layer 0 on the spin embeddings
-    if (cfgs[m].el_init) return DQ_ERR_UNSUPPORTED;
   dq_multi_s* g = new (std::nothrow) dq_multi_s();
   if (!g) return DQ_ERR_ARG;
   if (cudaGetDevice(&g->device) != cudaSuccess) {

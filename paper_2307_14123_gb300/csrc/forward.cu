@@ -2094,6 +2094,7 @@ cudaError_t launch_layer0_node_group(const MolFwd<T>* m, int n, cudaStream_t s) 
   Grp<layer0_node_kernel_args<T>> g{};
   for (int k = 0; k < n; ++k) {
     const dq_handle_s& h = *m[k].h;
+    if (h.el_init) continue;  // no spin embeddings: layer 0 takes the general path
     g.add({m[k].params, m[k].d.D, h.off.E_spin, h.off.layer[0].W_h, m[k].b.z0}, blocks(2 * m[k].d.D, 128));
   }
   if (g.n == 0) return cudaSuccess;
@@ -2120,7 +2121,7 @@ cudaError_t launch_messages_group_t(const MolFwd<T>* m, int n, int l, bool z_con
       if (d.Bc <= 0) continue;
       smem = std::max(smem, (size_t)d.N * 32 * sizeof(T) + (size_t)d.N * d.N * sizeof(int));
       g.add({m[k].b.Z, m[k].b.z0, m[k].b.ew, m[k].params + h.off.layer[l].Y, h.d_pair_of, d.Bc, d.N, d.n_up, d.M, d.D,
-             h.edges.n_all, h.edges.n_ee, z_const ? 1 : 0, out_of(m[k])},
+             h.edges.n_all, h.edges.n_ee, z_const && !h.el_init ? 1 : 0, out_of(m[k])},
             d.Bc, (d.D + 31) / 32);
     }
     if (g.n == 0) return cudaSuccess;
@@ -2159,7 +2160,7 @@ cudaError_t launch_messages_group_t(const MolFwd<T>* m, int n, int l, bool z_con
     if (lay.total_bytes > 220 * 1024) return cudaErrorInvalidConfiguration;
     smem = std::max(smem, lay.total_bytes);
     ent[ne++] = Ent{{m[k].b.Z, m[k].b.z0, m[k].b.ew, m[k].b.geo, m[k].params + h.off.layer[l].Y, h.d_pair_of, d.N,
-                     d.n_up, d.M, d.C, d.D, h.edges.n_all, h.edges.n_ee, z_const ? 1 : 0, stage_w1 ? 1 : 0,
+                     d.n_up, d.M, d.C, d.D, h.edges.n_all, h.edges.n_ee, z_const && !h.el_init ? 1 : 0, stage_w1 ? 1 : 0,
                      out_of(m[k])},
                     d.Bc, d.D / L, L, lay.total_bytes, 0};
   }
@@ -2218,7 +2219,7 @@ cudaError_t launch_update_group(const MolFwd<T>* m, int n, bool from_spin, cudaS
     const FwdDims& d = m[k].d;
     if (d.Bc <= 0) continue;
     g.add({m[k].b.Z, m[k].b.F, m[k].b.F, m[k].params + std::max<int64_t>(m[k].h->off.E_spin, 0), d.Bc, d.N, d.n_up, d.C, d.D,
-           from_spin ? 1 : 0, static_cast<__nv_bfloat16*>(m[k].b.F_bf)},
+           from_spin && !m[k].h->el_init ? 1 : 0, static_cast<__nv_bfloat16*>(m[k].b.F_bf)},
           blocks(d.Bc * d.N * d.D, 256));
   }
   if (g.n == 0) return cudaSuccess;

@@ -83,9 +83,8 @@ def test_full_determinant_arguments_are_checked_on_the_host(lib):
         assert not h.value
 
 
-def test_electron_nucleus_embedding_is_refused_in_batches(lib):
-    """Batches run layer 0 on the spin embeddings: dq_create_multi refuses el_init with
-    DQ_ERR_UNSUPPORTED before any device call, and el_init outside {0, 1} is an argument error."""
+def test_electron_nucleus_embedding_flag_is_checked_on_the_host(lib):
+    """el_init outside {0, 1} is an argument error, returned before any device call."""
     import numpy as np
 
     from paper_2307_14123_gb300 import binding
@@ -93,10 +92,23 @@ def test_electron_nucleus_embedding_is_refused_in_batches(lib):
     s = fx.molecule("LiH")
     Z = np.ascontiguousarray(s.Z, dtype=np.float64)
     R = np.ascontiguousarray(s.R, dtype=np.float64)
-    sysc = (binding._System * 1)(binding._System(len(Z), Z.ctypes.data, R.ctypes.data, s.n_up, s.n_down))
-    cfgc = (binding._Cfg * 1)(binding._Cfg(32, 2, 1, 16, 10.0, 1, 1, 1.0, 0, 0, 1))
-    out = ctypes.c_void_p()
-    assert lib.dq_create_multi(1, sysc, cfgc, 1, ctypes.byref(out)) == 7 and not out.value
-    cfgc[0].el_init = 2
+    sysc = binding._System(len(Z), Z.ctypes.data, R.ctypes.data, s.n_up, s.n_down)
+    cfgc = binding._Cfg(32, 2, 1, 16, 10.0, 1, 1, 1.0, 0, 0, 2)
     h = ctypes.c_void_p()
-    assert lib.dq_create(sysc, cfgc, 1, ctypes.byref(h)) == 1 and not h.value
+    assert lib.dq_create(ctypes.byref(sysc), ctypes.byref(cfgc), 1, ctypes.byref(h)) == 1 and not h.value
+
+
+def test_bf16_mode_needs_width_multiple_of_64(lib):
+    """The BF16 embedding GEMMs take K = D and 3D in 64-wide tiles: dq_create refuses other widths
+    in that mode (DQ_ERR_SHAPE) before any device call."""
+    import numpy as np
+
+    from paper_2307_14123_gb300 import binding
+    from paper_2307_14123_gb300 import fixtures as fx
+    s = fx.molecule("LiH")
+    Z = np.ascontiguousarray(s.Z, dtype=np.float64)
+    R = np.ascontiguousarray(s.R, dtype=np.float64)
+    sysc = binding._System(len(Z), Z.ctypes.data, R.ctypes.data, s.n_up, s.n_down)
+    cfgc = binding._Cfg(96, 2, 1, 16, 10.0, 1, 1, 1.0, 0, 0, 0)
+    h = ctypes.c_void_p()
+    assert lib.dq_create(ctypes.byref(sysc), ctypes.byref(cfgc), 2, ctypes.byref(h)) == 2 and not h.value

@@ -158,3 +158,34 @@ def test_el_init_metropolis_and_langevin_consistent():
     h.mala_step(th_t, r_t, la_t, g, n_steps=2, tau=0.05, seed=5, step_counter=0, grad_valid=False)
     ref, _ = oracle.Oracle(sys_, cfg).evaluate(theta, r_t.cpu().numpy())
     assert np.all(np.abs(la_t.cpu().numpy() - ref) <= 1e-10 * np.maximum(1, np.abs(ref)))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_el_init_in_a_batch_equals_single(prec):
+    """A batch mixing an electron-nucleus-embedding molecule with a spin-embedding one (layer 0
+    on the general path for the first only, in the same grouped launches) gives each molecule's
+    single-handle results bit for bit; the FP32 results match the oracle."""
+    from paper_2307_14123_gb300 import Ansatz, AnsatzBatch
+    small = _case("small")
+    lih = _case("lih")
+    mols = [lih, (small[0], dataclasses.replace(small[1], el_init=0), small[2]),
+            (small[0], small[1], small[2])]
+    if prec == "bf16":  # the BF16 GEMMs need D % 64 == 0
+        mols = [(m[0], dataclasses.replace(m[1], width=64), m[2]) for m in mols]
+    batch = AnsatzBatch([m[0] for m in mols], [m[1] for m in mols], prec, device="cuda:0")
+    th, r, ths, rs = [], [], [], []
+    for k, (sys_, cfg, seed) in enumerate(mols):
+        a, b, c, d = _inputs(sys_, cfg, "fp32", 24 + 8 * k, seed, 5 + k)
+        th.append(c), r.append(d), ths.append(a), rs.append(b)
+    la, sg, el = batch.local_energy(th, r)
+    for k, (sys_, cfg, _) in enumerate(mols):
+        la1, sg1, el1 = Ansatz(sys_, cfg, prec, device="cuda:0").local_energy(th[k], r[k])
+        assert torch.equal(la[k], la1) and torch.equal(sg[k], sg1) and torch.equal(el[k], el1)
+        if prec != "fp32":
+            continue
+        ref = oracle.Oracle(sys_, cfg).local_energy(ths[k], rs[k], with_grad=True)
+        lan, sgn, eln = _np(la[k], sg[k], el[k])
+        assert np.array_equal(sgn, ref["sign"])
+        assert np.all(np.abs(lan - ref["logabs"]) <= 1e-4 * np.maximum(1, np.abs(ref["logabs"])))
+        S = 0.5 * (np.abs(ref["lap"]) + np.sum(ref["grad"] ** 2, axis=1))
+        assert np.all(np.abs(eln - ref["e_loc"]) <= np.maximum(1e-4, 3e-5 * S))
