@@ -509,14 +509,38 @@ __global__ void __launch_bounds__(32 * kColRows)
   T acc = 0;
   const int64_t r_begin = wb0 * rpw + rl, r_end = wb1 * rpw;
   if (o < n_o && r_begin < r_end) {
-    int64_t seg = r_begin / mx.rows_per_seg, in = r_begin % mx.rows_per_seg;  // one division, then increments
     const T* xo = X + o;
-    for (int64_t r = r_begin; r < r_end; r += kColRows) {
-      acc += xo[seg * mx.seg_stride + in * mx.ld];
-      in += kColRows;
-      while (in >= mx.rows_per_seg) {
-        in -= mx.rows_per_seg;
-        ++seg;
+    if (r_end <= (int64_t)UINT32_MAX && mx.rows_per_seg <= (int64_t)UINT32_MAX) {
+      // kColU rows per iteration, each addressed on its own (32-bit division) and summed into
+      // its own accumulator, so that kColU loads are in flight; the accumulators are added in
+      // a fixed order
+      constexpr int kColU = 8;
+      const uint32_t rps = (uint32_t)mx.rows_per_seg;
+      T a[kColU];
+#pragma unroll
+      for (int u = 0; u < kColU; ++u) a[u] = 0;
+      for (int64_t r0 = r_begin; r0 < r_end; r0 += (int64_t)kColU * kColRows) {
+        T v[kColU];
+#pragma unroll
+        for (int u = 0; u < kColU; ++u) {
+          const int64_t r = r0 + (int64_t)u * kColRows;
+          const uint32_t seg = (uint32_t)r / rps, in = (uint32_t)r - seg * rps;
+          v[u] = r < r_end ? xo[(int64_t)seg * mx.seg_stride + (int64_t)in * mx.ld] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kColU; ++u) a[u] += v[u];
+      }
+#pragma unroll
+      for (int u = 0; u < kColU; ++u) acc += a[u];
+    } else {
+      int64_t seg = r_begin / mx.rows_per_seg, in = r_begin % mx.rows_per_seg;  // one division, then increments
+      for (int64_t r = r_begin; r < r_end; r += kColRows) {
+        acc += xo[seg * mx.seg_stride + in * mx.ld];
+        in += kColRows;
+        while (in >= mx.rows_per_seg) {
+          in -= mx.rows_per_seg;
+          ++seg;
+        }
       }
     }
   }
