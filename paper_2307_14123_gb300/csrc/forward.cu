@@ -27,6 +27,8 @@
 
 #include <algorithm>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "det_util.cuh"
 
@@ -179,54 +181,74 @@ __device__ __forceinline__ void edge_hidden_kernel_body(const int64_t bx_, const
     for (int k = threadIdx.x; k < nb * ej * Q; k += blockDim.x) fs[k] = rbf[be0 * ej * Q + k];
     __syncthreads();
     if (er >= epp) continue;
-    for (int r = er; r < nb; r += epp) {
-      const int64_t be = be0 + r;
-      const int e = (int)(be % E);
-      const int t = e < n_par ? 0 : (e < n_ee ? 1 : 2);
+    auto type_of = [&](int r) {
+      const int e = (int)((be0 + r) % E);
+      return e < n_par ? 0 : (e < n_ee ? 1 : 2);
+    };
+    // NE consecutive edges of one type: every W1 load from shared memory serves NE edges
+    auto rows = [&](auto ne, int r) {
+      constexpr int NE = decltype(ne)::value;
+      const int t = type_of(r);
       const T* W = Ws + t * Q * D + a0;
-      const T* f = fs + r * ej * Q;
-      T h[VW], h1[VW], h2[VW];
+      T h[NE][VW], h1[NE][VW], h2[NE][VW];
       const V bv = *reinterpret_cast<const V*>(bs + t * D + a0);
       const T* bp = reinterpret_cast<const T*>(&bv);
 #pragma unroll
-      for (int v = 0; v < VW; ++v) {
-        h[v] = bp[v];
-        h1[v] = 0;
-        h2[v] = 0;
-      }
+      for (int n = 0; n < NE; ++n)
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+          h[n][v] = bp[v];
+          h1[n][v] = 0;
+          h2[n][v] = 0;
+        }
 #pragma unroll 4
       for (int q = 0; q < Q; ++q) {
         const V wv = *reinterpret_cast<const V*>(W + q * D);
         const T* w = reinterpret_cast<const T*>(&wv);
-        const T f0 = f[q];
 #pragma unroll
-        for (int v = 0; v < VW; ++v) h[v] += w[v] * f0;
-        if (ej == 3) {
-          const T f1 = f[Q + q], f2 = f[2 * Q + q];
+        for (int n = 0; n < NE; ++n) {
+          const T* f = fs + (r + n) * ej * Q;
+          const T f0 = f[q];
 #pragma unroll
-          for (int v = 0; v < VW; ++v) {
-            h1[v] += w[v] * f1;
-            h2[v] += w[v] * f2;
+          for (int v = 0; v < VW; ++v) h[n][v] += w[v] * f0;
+          if (ej == 3) {
+            const T f1 = f[Q + q], f2 = f[2 * Q + q];
+#pragma unroll
+            for (int v = 0; v < VW; ++v) {
+              h1[n][v] += w[v] * f1;
+              h2[n][v] += w[v] * f2;
+            }
           }
         }
       }
-      V o0, o1, o2;
-      T* p0 = reinterpret_cast<T*>(&o0);
-      T* p1 = reinterpret_cast<T*>(&o1);
-      T* p2 = reinterpret_cast<T*>(&o2);
 #pragma unroll
-      for (int v = 0; v < VW; ++v) {
-        const T av = tanh_t(h[v]);
-        p0[v] = av;
-        const T da = T(1) - av * av;
-        p1[v] = da * h1[v];
-        p2[v] = da * h2[v] - T(2) * av * da * h1[v] * h1[v];
+      for (int n = 0; n < NE; ++n) {
+        V o0, o1, o2;
+        T* p0 = reinterpret_cast<T*>(&o0);
+        T* p1 = reinterpret_cast<T*>(&o1);
+        T* p2 = reinterpret_cast<T*>(&o2);
+#pragma unroll
+        for (int v = 0; v < VW; ++v) {
+          const T av = tanh_t(h[n][v]);
+          p0[v] = av;
+          const T da = T(1) - av * av;
+          p1[v] = da * h1[n][v];
+          p2[v] = da * h2[n][v] - T(2) * av * da * h1[n][v] * h1[n][v];
+        }
+        T* o = eh + (be0 + r + n) * ej * D + a0;
+        *reinterpret_cast<V*>(o) = o0;
+        if (ej == 3) {
+          *reinterpret_cast<V*>(o + D) = o1;
+          *reinterpret_cast<V*>(o + 2 * D) = o2;
+        }
       }
-      T* o = eh + be * ej * D + a0;
-      *reinterpret_cast<V*>(o) = o0;
-      if (ej == 3) {
-        *reinterpret_cast<V*>(o + D) = o1;
-        *reinterpret_cast<V*>(o + 2 * D) = o2;
+    };
+    for (int r = 2 * er; r < nb; r += 2 * epp) {
+      if (r + 1 < nb && type_of(r) == type_of(r + 1)) {
+        rows(std::integral_constant<int, 2>{}, r);
+      } else {
+        rows(std::integral_constant<int, 1>{}, r);
+        if (r + 1 < nb) rows(std::integral_constant<int, 1>{}, r + 1);
       }
     }
   }
