@@ -243,13 +243,26 @@ __device__ __forceinline__ void edge_hidden_kernel_body(const int64_t bx_, const
         }
       }
     };
-    for (int r = 2 * er; r < nb; r += 2 * epp) {
+    auto pair = [&](int r) {  // edges r, r + 1 (if present)
       if (r + 1 < nb && type_of(r) == type_of(r + 1)) {
         rows(std::integral_constant<int, 2>{}, r);
       } else {
         rows(std::integral_constant<int, 1>{}, r);
         if (r + 1 < nb) rows(std::integral_constant<int, 1>{}, r + 1);
       }
+    };
+    if (ej == 1) {  // value rows: four edges per W1 load (registers allow it)
+      for (int r = 4 * er; r < nb; r += 4 * epp) {
+        const int t = type_of(r);
+        if (r + 3 < nb && type_of(r + 1) == t && type_of(r + 2) == t && type_of(r + 3) == t) {
+          rows(std::integral_constant<int, 4>{}, r);
+        } else {
+          pair(r);
+          if (r + 2 < nb) pair(r + 2);
+        }
+      }
+    } else {
+      for (int r = 2 * er; r < nb; r += 2 * epp) pair(r);
     }
   }
 }
