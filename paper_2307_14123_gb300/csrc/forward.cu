@@ -2187,6 +2187,15 @@ cudaError_t launch_messages_group_t(const MolFwd<T>* m, int n, int l, bool z_con
     if (lay.total_bytes > 112 * 1024) {
       stage_w1 = false;
       lay = msg_smem_layout<T>(d.N, IB, CB, stage_w1, L);
+      // 16 features per CTA with both filter tables staged, when that keeps as many CTAs per
+      // SM as 32 features without the w' table (which then comes from global memory)
+      const MsgSmem l16 = msg_smem_layout<T>(d.N, IB, CB, true, 16);
+      auto per_sm = [](int bytes) { return (228 * 1024) / (bytes + 1024); };
+      if (l16.total_bytes <= 220 * 1024 && per_sm(l16.total_bytes) >= per_sm(lay.total_bytes)) {
+        stage_w1 = true;
+        L = 16;
+        lay = l16;
+      }
     }
     if (lay.total_bytes > 220 * 1024) {
       L = 16;
