@@ -284,7 +284,7 @@ dq_status natural_gradient(dq_handle h, const void* G, const void* w, int64_t B,
 dq_status param_update(dq_handle h, void* params, const void* delta, double lr, double max_norm, double* stats,
                        void* ws, size_t ws_bytes, void* stream);
 
-/* Pseudopotentials (Eqs. pseudopotential and pp_integral): a nucleus with a
+/* Pseudopotentials (Eqs. 11 and 12): a nucleus with a
  * pseudopotential carries a local function V and non-local channels
  * W_0 .. W_lmax, each f(r) = sum_t beta_t r^(n_t - 2) exp(-alpha_t r^2).  The
  * handle's system then holds the valence electrons and effective charges; the
@@ -300,7 +300,7 @@ typedef struct {
 /* pseudopotential_energy: per walker
  *   v_loc = sum_{i,I} V_I(r_iI),
  *   v_nl  = sum_{i,I,l} W_l(r_iI) (2l + 1) / 12 sum_k P_l(cos th_k) psi(r_i -> R_I + r_iI R_b u_k) / psi(r),
- * the angular integral of Eq. (pp_integral) summed over m by the addition
+ * the angular integral of Eq. 12 summed over m by the addition
  * theorem and replaced by the 12-point icosahedral quadrature (vertices u_k
  * rotated by the walker's rotation R_b, cos th_k = (R_b u_k) . (r_i - R_I) / r_iI).
  * Every electron is displaced around every pseudopotential nucleus: B * N *

@@ -20,7 +20,7 @@ Functions, each following the paper's definitions:
   per-walker weights of the gradient estimator, Eq. (30).
 * :func:`energy_estimate` - Eq. (33) and the batch-means error bar, Eq. (35).
 * :func:`pseudopotential` - local and non-local pseudopotential energies of
-  Eqs. (pseudopotential) and (pp_integral): the angular integral by the
+  Eqs. 11 and 12: the angular integral by the
   12-point icosahedral quadrature over a rotated icosahedron, psi ratios from
   :meth:`Oracle.evaluate`.
 * :func:`natural_gradient` - the natural-gradient direction of the optimiser
@@ -332,8 +332,8 @@ def legendre(l, x):
 
 
 def pseudopotential(orc, theta, r, pps, rot, with_abs=False):
-    """Local and non-local pseudopotential energies of every walker (Eqs. pseudopotential and
-    pp_integral).  pps: list of (nucleus index, coef [(l_max + 2)][n_terms][3]) with the local
+    """Local and non-local pseudopotential energies of every walker (Eqs. 11 and 12).
+    pps: list of (nucleus index, coef [(l_max + 2)][n_terms][3]) with the local
     function V first, then W_0 .. W_lmax; rot [B][3][3] rotations of the icosahedron (one per
     walker).  For electron i and nucleus I the angular integral of Y_lm^* psi-ratio, summed over
     m with Y_lm(Omega), is (2l + 1) / (4 pi) int P_l(cos) psi'/psi dOmega' by the addition

@@ -1,5 +1,5 @@
-// Local and non-local pseudopotential energies (Eqs. pseudopotential and
-// pp_integral).  For walker b, electron i and a nucleus I that carries a
+// Local and non-local pseudopotential energies (Eqs. 11 and 12).
+// For walker b, electron i and a nucleus I that carries a
 // pseudopotential, the non-local term is
 //   sum_l W_l(r_iI) (2l + 1) / 12 sum_k P_l(cos th_k) psi(r_i -> R_I + r_iI R_b u_k) / psi(r),
 // the addition theorem turning the sum over m of Y_lm(Omega) Y_lm^*(Omega')

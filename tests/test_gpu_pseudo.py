@@ -1,4 +1,4 @@
-"""Pseudopotential energies (Eqs. pseudopotential and pp_integral) on the GPU against
+"""Pseudopotential energies (Eqs. 11 and 12) on the GPU against
 the oracle's quadrature on the same walkers, rotations and (synthetic) coefficients.
 
 Bounds: FP64 mode 1e-10 relative (of sum |w psi'/psi|, the size of the quadrature

@@ -949,7 +949,7 @@ def test_natural_gradient_limits():
 
 
 # ----------------------------------------------------------------------------
-# Pseudopotential quadrature (Eqs. pseudopotential, pp_integral)
+# Pseudopotential quadrature (Eqs. 11, 12)
 # ----------------------------------------------------------------------------
 def test_icosahedral_rule_and_legendre():
     """The 12-point rule integrates P_l(u . v) exactly for l = 1..5 (mean 0) and is exact for
