@@ -74,27 +74,107 @@ def workload_config(wl, world):
             "precision": wl.precision, "parallelism": f"walker-sharded x{world}"}
 
 
-def oracle_sample(wl, seconds):
-    """Times the FP64 oracle's local energy on a bounded walker sample."""
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), or None."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def oracle_sample(wl, seconds, threads=None):
+    """Times the FP64 oracle's local energy on a bounded walker sample (inputs rounded to the
+    workload's precision, so that the outputs are also the parity reference of those walkers).
+    Returns (walkers, seconds, threads, theta, r, oracle outputs)."""
     import numpy as np
 
     import oracle
     from paper_2307_14123_gb300 import fixtures as fx
 
     oracle.build()
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     oracle.Oracle.set_threads(cores)
     o = oracle.Oracle(wl.system, wl.cfg)
     theta = fx.init_params(wl.system, wl.cfg, wl.param_seed)
+    if wl.precision != "fp64":
+        theta = theta.astype(np.float32).astype(np.float64)
     n = cores
     while True:
         r = fx.init_walkers(wl.system, n, wl.walker_seed)
+        if wl.precision != "fp64":
+            r = r.astype(np.float32).astype(np.float64)
         t0 = time.perf_counter()
-        o.local_energy(theta, r)
+        ref = o.local_energy(theta, r, with_grad=True)
         dt = time.perf_counter() - t0
         if dt * 2 > seconds or n >= wl.B:
-            return n, dt, oracle.Oracle.threads()
+            return n, dt, oracle.Oracle.threads(), theta, r, ref, o
         n = min(wl.B, n * max(2, int(seconds / max(dt, 1e-3) / 2)))
+
+
+def oracle_leg(h, wl, seconds, dev, with_grad):
+    """The oracle on the host cores: the CPU baseline (all cores, and one core on a smaller sample)
+    and, from the same oracle outputs, the error of the GPU path on those walkers (log|psi|, E_loc,
+    and the weighted gradient of log|psi| along random parameter directions)."""
+    import numpy as np
+    import torch
+
+    import oracle
+
+    n, dtc, cores, theta, r, ref, o = oracle_sample(wl, seconds)
+    # one core, on a sample sized to ~a quarter of the budget
+    n1 = max(1, min(n, int(n * seconds / 4 / max(dtc * cores, 1e-3))))
+    oracle.Oracle.set_threads(1)
+    t0 = time.perf_counter()
+    o.local_energy(theta, r[:n1])
+    dt1 = time.perf_counter() - t0
+    oracle.Oracle.set_threads(cores)
+    tdt = torch.float64 if wl.precision == "fp64" else torch.float32
+    th_d = torch.tensor(theta, dtype=tdt, device=dev)
+    r_d = torch.tensor(r, dtype=tdt, device=dev)
+    la, sg, el = (x.cpu().numpy() for x in h.local_energy(th_d, r_d))
+    la, el = la.astype(np.float64), el.astype(np.float64)
+    S = 0.5 * (np.abs(ref["lap"]) + np.sum(ref["grad"] ** 2, axis=1))
+    d_la, d_e = np.abs(la - ref["logabs"]), np.abs(el - ref["e_loc"])
+    parity = {"walkers": int(n),
+              "logabs": {"max_abs_err": float(d_la.max()), "mean_abs_err": float(d_la.mean()),
+                         "max_rel_err": float(np.max(d_la / np.maximum(1, np.abs(ref["logabs"])))),
+                         "frac_within_1e-5_rel": float(np.mean(d_la <= 1e-5 * np.maximum(1, np.abs(ref["logabs"]))))},
+              "e_loc": {"max_abs_err": float(d_e.max()), "mean_abs_err": float(d_e.mean()),
+                        "mean_err": float(np.mean(el - ref["e_loc"])), "max_err_over_S_b": float(np.max(d_e / S)),
+                        "frac_within_contract": float(np.mean(d_e <= np.maximum(1e-4, 1e-5 * S))),
+                        "frac_within_1e-4_Ha": float(np.mean(d_e <= 1e-4))},
+              "sign_equal": float(np.mean(sg == ref["sign"])),
+              "contract": "log|psi| 1e-5 max(1,|log|psi||), E_loc max(1e-4 Ha, 1e-5 S_b), S_b the size of the "
+                          "kinetic terms; exceptions only at near-nodal walkers (tests/fp32_contract.py)"}
+    if with_grad:
+        k = min(n, 16)
+        w = np.random.default_rng(0).normal(size=k) / k
+        dirs = np.random.default_rng(1).normal(size=(2, o.P))
+        G = h.grad_logpsi(th_d, r_d[:k].contiguous(), torch.tensor(w, dtype=tdt, device=dev), 0)
+        g_dir = G.double().cpu().numpy() @ dirs.T
+        jv = o.grad_jvp(theta, r[:k], dirs)
+        ref_dir = w @ jv
+        scale = np.abs(w) @ np.abs(jv)
+        parity["grad_direction"] = {"walkers": k, "directions": 2,
+                                    "max_rel_err": float(np.max(np.abs(g_dir - ref_dir) / scale)),
+                                    "note": "sum_b w_b d log|psi_b| / d theta . v against the oracle's dual-number "
+                                            "derivatives, relative to sum_b |w_b| |d log|psi_b| . v|"}
+    cpu = {"value": n / dtc, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+           "single_thread": {"value": n1 / dt1, "unit": UNIT, "walkers": n1, "seconds": dt1},
+           "sample": f"FP64 oracle local_energy on {n} of the {wl.B} walkers ({dtc:.1f} s on {cores} threads; "
+                     f"{n1} walkers on one thread in {dt1:.1f} s); the oracle has no reverse mode, so its "
+                     f"Metropolis and gradient legs are not included"}
+    return cpu, parity
 
 
 def run_reference(args):
@@ -105,7 +185,7 @@ def run_reference(args):
         return 0
     wl = fx.workload(args.workload)
     # size one step to ~4 s of host time so the whole run stays within minutes
-    n, dt, cores = oracle_sample(wl, 8.0)
+    n, dt, cores = oracle_sample(wl, 8.0)[:3]
     per_walker = dt / n
     step_n = max(1, min(wl.B, int(round(4.0 / per_walker))))
     import numpy as np
@@ -209,26 +289,69 @@ def peaks():
 MSG_DRAM_BYTES_PER_WALKER = (263.570432e6 + 432.803840e6) / 512
 
 
-def roofline_for(kind, ms, n, wl, chunk, pk, how):
-    """Roofline entry of one kernel kind: algorithmic work per launch / average launch time."""
+def gemm_shapes(wl, chunk):
+    """(rows, K, n_out) of the forward GEMM kinds for one launch over `chunk` walkers (jets), and the
+    value-only forward GEMM FLOPs per walker (the reverse pass repeats each product twice: the input
+    adjoint and the weight gradient)."""
+    s, c = wl.system, wl.cfg
+    N, D, M, K = s.n_elec, c.width, s.n_nuc, c.n_det
+    C = 3 * N + 2
+    E = N * (N - 1) // 2 + N * M
+    nsq = s.n_up ** 2 + s.n_down ** 2 if not c.full_det else 2 * N * N
+    shapes = {"jet.gemm_update": (chunk * N * C, 3 * D, D), "jet.gemm_node": (chunk * N * C, D, D),
+              "jet.gemm_edge": (chunk * E * 3, D, D),
+              # per spin s: (n_s * C rows) x (K * n_s outputs), summed over both spins
+              "jet.gemm_orbital": (chunk * C, D, K * nsq)}
+    L = c.n_layers
+    value_flops = (2.0 * N * D * D * (L - 1) + 2.0 * N * 3 * D * D * L + 2.0 * E * D * D * L
+                   + 2.0 * D * K * nsq + 2.0 * D * D)
+    return shapes, value_flops
+
+
+def message_flops_per_walker(wl):
+    """Algorithmic FLOPs of one jet message launch per walker (layer >= 1): for every receiver i,
+    node channel c and feature, the sum over the other electrons of w_ij z_j[c] (2 FLOPs each),
+    plus the product-rule terms of the coordinate and Laplacian channels."""
     s, c = wl.system, wl.cfg
     N, D, M = s.n_elec, c.width, s.n_nuc
     C = 3 * N + 2
-    rows = chunk * N * C
+    main = 2.0 * N * (N - 1) * C * D
+    prod = (2.0 * N * (N - 1) * 3 * 2 + 2.0 * N * (N - 1) * 8 + 2.0 * N * M * 10) * D
+    return main + prod
+
+
+def det_flops_per_walker(wl):
+    """Algorithmic FLOPs of the determinant jets per walker: per (p, spin) matrix of size n with
+    T = 3N + 1 tangent channels, LU (2n^3/3), inverse (4n^3/3), the tangent products A^-1 dA
+    (T 2n^3), their traces and tr((A^-1 dA)^2) (T 2n^2) and tr(A^-1 Lap A) (2n^2)."""
+    s, c = wl.system, wl.cfg
+    N = s.n_elec
+    T = 3 * N + 1
+    tot = 0.0
+    for n in ((N,) if c.full_det else (s.n_up, s.n_down)):
+        if n:
+            tot += c.n_det * (2 * n ** 3 / 3 + 4 * n ** 3 / 3 + T * 2 * n ** 3 + T * 2 * n * n + 2 * n * n)
+    return tot
+
+
+def roofline_for(kind, ms, n, wl, chunk, pk, how, alu, steps):
+    """Roofline entry of one kernel kind: algorithmic work per launch / average launch time, against
+    the bound the kernel runs into (tensor cores for the GEMMs, the CUDA cores' FMA rate for the
+    message contraction and the determinant jets, HBM for the streaming kernels)."""
+    s, c = wl.system, wl.cfg
+    N, D, M = s.n_elec, c.width, s.n_nuc
+    C = 3 * N + 2
     E = N * (N - 1) // 2 + N * M
     t = ms / n / 1e3
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     bf16 = wl.precision == "bf16"
-    gemm_k = {"jet.gemm_update": (rows, 3 * D, D), "jet.gemm_node": (rows, D, D),
-              "jet.gemm_edge": (chunk * E * 3, D, D),
-              # per spin s: (n_s * C rows) x (K * n_s outputs), summed over both spins
-              "jet.gemm_orbital": (chunk * C, D, c.n_det * (s.n_up ** 2 + s.n_down ** 2))}
-    if kind in gemm_k:
-        m, k, n_out = gemm_k[kind]
+    shapes, value_flops = gemm_shapes(wl, chunk)
+    el = 8 if wl.precision == "fp64" else 4
+    base = {"kernel": kind, "avg_launch_ms": ms / n, "launches": n}
+    if kind in shapes:
+        m, k, n_out = shapes[kind]
         flops = 2.0 * m * k * n_out
         if wl.precision == "fp64":
-            peak, bound, src = 1.25, "alu", "nominal FP64"
+            peak, bound, src = alu["fp64_tflops"], "alu", "measured FP64 FMA rate (CUDA cores)"
         elif bf16 and kind in ("jet.gemm_update", "jet.gemm_node"):
             peak, bound, src = pk["bf16_tflops_sustained"], "tensor", f"{how} bf16 sustained (cuBLAS loop)"
         else:
@@ -236,23 +359,50 @@ def roofline_for(kind, ms, n, wl, chunk, pk, how):
             peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25) / 3.0
             bound, src = "tensor", f"{how} bf16 sustained x 1.1/2.25 (TF32) / 3 (3xTF32 split)"
         ach = flops / t / 1e12
-        return {"kernel": kind, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "peak_source": src, "flops_per_launch": flops, "avg_launch_ms": ms / n}
-    if kind == "jet.messages" and wl.name == "n2_fp32" and MSG_DRAM_BYTES_PER_WALKER:
-        # DRAM bytes of one launch from the ncu capture above, per walker, scaled to the launch's walkers
-        traffic = MSG_DRAM_BYTES_PER_WALKER * chunk
-    else:
-        traffic = None
+        return {**base, "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "peak_source": src, "flops_per_launch": flops}
+    if kind in ("bwd_gemm", "bwd_reduce"):
+        # per launch: the value-only forward GEMM FLOPs of the step's walkers, once per kind and step,
+        # spread over the kind's launches
+        flops = value_flops * chunk * steps / n
+        peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25) / 3.0 if wl.precision != "fp64" else alu["fp64_tflops"]
+        ach = flops / t / 1e12
+        return {**base, "bound": "tensor" if wl.precision != "fp64" else "alu", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                "peak_source": f"{how} bf16 sustained x 1.1/2.25 / 3 (3xTF32)",
+                "flops_per_launch": flops,
+                "note": "reverse-pass products of the value-only network (input adjoints for bwd_gemm, weight "
+                        "gradients for bwd_reduce), averaged over the kind's launches"}
     if kind == "jet.messages":
-        el = 8 if wl.precision == "fp64" else 4
-        out_el = 2 if bf16 else el
         L = c.n_layers
-        # average over the L launches of one forward: layer 0 reads no node channels
-        byts = (rows * D * el * (L - 1) / L) + chunk * E * 3 * D * el + rows * 3 * D * out_el
+        flops = message_flops_per_walker(wl) * chunk
+        peak = alu["fp32_tflops"] if wl.precision != "fp64" else alu["fp64_tflops"]
+        ach = flops / t / 1e12
+        byts = (chunk * N * C * D * el * (L - 1) / L) + chunk * E * 3 * D * el + chunk * N * C * 3 * D * (2 if bf16 else el)
+        traffic = MSG_DRAM_BYTES_PER_WALKER * chunk if (wl.name == "n2_fp32" and MSG_DRAM_BYTES_PER_WALKER) else None
+        return {**base, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": traffic, "peak_source": "FMA rate of the CUDA cores measured in this run",
+                "flops_per_launch": flops, "bytes_per_launch": byts,
+                "traffic_over_bytes": traffic / byts if traffic else None,
+                "note": "FLOPs of a layer >= 1 launch (layer 0 has constant node channels and does less)"}
+    if kind == "jet.orbital_det":
+        flops = det_flops_per_walker(wl) * chunk
+        peak = alu["fp32_tflops"] if wl.precision != "fp64" else alu["fp64_tflops"]
+        ach = flops / t / 1e12
+        return {**base, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "peak_source": "FMA rate of the CUDA cores measured in this run",
+                "flops_per_launch": flops,
+                "note": "FP64-accurate work: the tangent contractions run in double-float on the FP32 pipes "
+                        "(about 20 FP32 operations per algorithmic multiply-add) or on the FP64 pipes"}
+    # update: reads the pre-activations and the embeddings, writes the embeddings; edge hidden layer:
+    # reads the Gaussian features, writes the hidden jets
+    hbm = {"jet.update": 3.0 * chunk * N * C * D * el, "jet.edge_hidden": chunk * E * 3 * (D + 16) * el}
+    if kind in hbm:
+        byts = hbm[kind]
         ach = byts / t / 1e9
-        return {"kernel": kind, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": ach / pk["hbm_gbs"], "traffic": traffic, "peak_source": f"{how} copy bandwidth",
-                "bytes_per_launch": byts, "avg_launch_ms": ms / n}
+        return {**base, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": f"{how} copy bandwidth",
+                "bytes_per_launch": byts}
     return None
 
 
@@ -595,6 +745,15 @@ def main():
         return el, e2, g
 
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    # FMA rates of the CUDA cores on this GPU (the bound of the kernels that run on them), with the
+    # SM clock sampled while the probes run; no GPU setting is changed
+    from paper_2307_14123_gb300.binding import fma_rate
+    alu_clk = ClockSampler(local)
+    alu_clk.start()
+    alu = {"fp32_tflops": fma_rate("fp32", dev), "fp64_tflops": fma_rate("fp64", dev)}
+    alu["clocks"] = alu_clk.stop()
+    alu["how"] = ("dq_fma_rate_probe: 1216 blocks x 256 threads, 8 independent FMA chains per thread, best of 5 "
+                  "launches timed with CUDA events")
     for _ in range(args.warmup):
         step(theta, r, logabs)
     torch.cuda.synchronize()
@@ -642,14 +801,15 @@ def main():
     dom = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
     roof = None
     others = []
-    for kind in ("jet.messages", "jet.gemm_update", "jet.gemm_edge", "jet.gemm_node", "jet.gemm_orbital"):
+    for kind in ("jet.messages", "jet.msg_gemm", "jet.gemm_update", "jet.gemm_edge", "jet.gemm_node",
+                 "jet.gemm_orbital", "jet.orbital_det", "jet.update", "jet.edge_hidden", "bwd_gemm", "bwd_reduce"):
         if kind in prof:
-            e = roofline_for(kind, prof[kind][0], prof[kind][1], wl, chunk, pk, how)
+            e = roofline_for(kind, prof[kind][0], prof[kind][1], wl, chunk, pk, how, alu, args.steps)
             if e:
                 e["share_of_gpu_time"] = prof[kind][0] / gpu_time_ms
                 others.append(e)
     if dom is not None:
-        roof = roofline_for(dom, prof[dom][0], prof[dom][1], wl, chunk, pk, how)
+        roof = roofline_for(dom, prof[dom][0], prof[dom][1], wl, chunk, pk, how, alu, args.steps)
         if roof:
             roof["share_of_gpu_time"] = prof[dom][0] / gpu_time_ms
         else:
@@ -687,17 +847,29 @@ def main():
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
+        # same conditions as the device-timed steps: L2 flushed before every step (outside the
+        # timed interval), the library's per-launch events on
+        h.profile_reset()
+        h.profile(True)
+        ev2 = []
         for _ in range(args.steps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
             e2e_step()
-        b.record()
+            b.record()
+            ev2.append((a, b))
         torch.cuda.synchronize()
-        t2 = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device=dev)
+        h.profile(False)
+        t2 = torch.tensor([sum(a.elapsed_time(b) for a, b in ev2)], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(t2, op=dist.ReduceOp.MAX)
         e2e = {"value": B * world * args.steps / (float(t2.item()) / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "note": "each step: parameters, positions and log|psi| copied from pinned host memory (one "
+                       "cudaMemcpyAsync per array), the step through the public API, positions, log|psi|, "
+                       "E_loc and the gradient copied back; L2 flushed before every step and the library's "
+                       "per-launch events on, as for value"}
 
     # the same step captured as one CUDA graph (step counter on the device) and replayed
     graph = None
@@ -791,12 +963,9 @@ def main():
     pseudo = pp_leg(h, theta, r, wl, flush) if (world == 1 and not args.no_pp) else None
     variants = ansatz_variants_leg(h, theta, r, wl, flush) if (world == 1 and not args.no_pp) else None
 
-    cpu = None
+    cpu = parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n, dtc, cores = oracle_sample(wl, args.cpu_seconds)
-        cpu = {"value": n / dtc, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"FP64 oracle local_energy on {n} of the {B} walkers ({dtc:.1f} s); the oracle "
-                         f"has no reverse mode, so its Metropolis and gradient legs are not included"}
+        cpu, parity = oracle_leg(h, wl, args.cpu_seconds, dev, with_grad)
 
     if rank == 0:
         step_desc = "mcmc_step(1 sweep) + local_energy + vmc_loss_weights" + (" + grad_logpsi(weighted)" if with_grad
@@ -808,7 +977,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16+f32"}[wl.precision],
                 "data": "synthetic (seeded walkers and random-init weights)", "config": cfg,
-                "roofline": roof, "roofline_main_kernels": others, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "roofline_main_kernels": others, "alu_peaks": alu, "cpu_baseline": cpu,
+                "parity_vs_oracle": parity, "e2e": e2e,
                 "cuda_graph": graph,
                 "langevin_sampler": langevin,
                 "batched_molecules": batched,

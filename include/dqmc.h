@@ -350,8 +350,13 @@ dq_status vmc_loss_weights_clip(dq_handle h, const void* e_loc, int64_t B, doubl
  * that loads it, kept until exit), so B must not exceed 65536; larger B
  * returns DQ_ERR_SHAPE and nothing is enqueued.  No call allocates.
  * The first call on a device (with that device current) looks up the
- * array's device address; it may load the library's module, so make it
- * before any stream capture.  All calls on a device share the array: calls
+ * array's device address and caches it for the life of the process; it may
+ * load the library's module, so make it before any stream capture.  A device
+ * reset (cudaDeviceReset, or a reset of the primary context) destroys the
+ * array and invalidates the cached address, as it does the handles' device
+ * buffers: do not call this entry point on that device after a reset.  With
+ * the handle's profiling on (dq_profile_enable) the launch is timed as the
+ * loss_weights kind.  All calls on a device share the array: calls
  * whose kernels overlap on the GPU (unordered streams) race and give wrong
  * results.  Arguments as for vmc_loss_weights.                              */
 dq_status vmc_loss_weights_noalloc(dq_handle h, const void* e_loc, int64_t B, double clip_k, void* weights,
@@ -481,6 +486,18 @@ dq_status dq_autotune(dq_handle h, const void* params, const void* r, int64_t B,
 dq_status dq_autotune_multi(dq_multi m, const void* const* params, const void* const* r, const int64_t* B, void* ws,
                             size_t ws_bytes, void* stream, double* best_ms);
 dq_status dq_multi_tuning(dq_multi m, int32_t* rounds, int32_t* msg_ib);
+
+/* Measurement support (not part of the method): enqueues on `stream` one
+ * launch of a kernel that only issues fused multiply-adds on the CUDA cores,
+ * kind 0 FP32 (FFMA), kind 1 FP64 (DFMA): `blocks` blocks of 256 threads,
+ * each thread `iters` x 128 FMAs in 8 independent chains.  The caller times
+ * the launch (CUDA events on `stream`) and divides *flops (host double, the
+ * launch's floating-point operations, 2 per FMA) by the time: the measured
+ * peak FMA rate against which kernels bound by CUDA-core arithmetic are
+ * reported.  sink: device buffer of at least `blocks` elements of the kind's
+ * type (never written for the probe's inputs).  DQ_ERR_ARG on bad sizes or
+ * kind. */
+dq_status dq_fma_rate_probe(int32_t kind, int32_t blocks, int32_t iters, void* sink, void* stream, double* flops);
 
 /* Human-readable name of a status code (static string). */
 const char* dq_status_string(dq_status s);

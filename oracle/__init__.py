@@ -23,6 +23,8 @@ Functions, each following the paper's definitions:
   Eqs. 11 and 12: the angular integral by the
   12-point icosahedral quadrature over a rotated icosahedron, psi ratios from
   :meth:`Oracle.evaluate`.
+* :func:`param_update` - the optimiser's parameter step with its step-length
+  limit (Sec. 4, "Optimizer").
 * :func:`natural_gradient` - the natural-gradient direction of the optimiser
   section (Sec. 4, "Optimizer"): the loss gradient preconditioned by the damped
   Fisher information of |psi|^2, estimated from walker-centred per-walker
@@ -305,6 +307,18 @@ def natural_gradient(G, w, lam, form="sample"):
         x = np.linalg.solve(Gc @ Gc.T / B + lam * np.eye(B), w)
         return Gc.T @ x
     return np.linalg.solve(Gc.T @ Gc / B + lam * np.eye(P), Gc.T @ w)
+
+
+def param_update(theta, delta, lr, max_norm=0.0):
+    """The optimiser's parameter step around a direction delta (Sec. 4, "Optimizer"; the paper
+    takes the step from a third-party library, so its plain form is the reading):
+    theta - lr s delta with the step-length limit s = min(1, max_norm / (lr ||delta||)), s = 1
+    when max_norm <= 0.  Returns (new theta, ||delta||, s), all FP64."""
+    theta = np.asarray(theta, dtype=np.float64)
+    delta = np.asarray(delta, dtype=np.float64)
+    nrm = float(np.sqrt(np.sum(delta * delta)))
+    s = 1.0 if max_norm <= 0 or lr * nrm <= max_norm else max_norm / (lr * nrm)
+    return theta - lr * s * delta, nrm, s
 
 
 _GOLDEN = (1.0 + 5.0 ** 0.5) / 2.0

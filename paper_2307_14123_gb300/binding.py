@@ -38,7 +38,7 @@ EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_
            "dq_multi_handle", "dq_multi_set_rounds", "dq_multi_rounds", "dq_multi_workspace_size",
            "ansatz_eval_multi", "local_energy_multi", "mcmc_step_multi", "grad_logpsi_multi",
            "vmc_loss_weights_multi", "dq_autotune_multi", "dq_multi_tuning", "dq_set_msg_tile", "dq_msg_tile", "dq_autotune", "natural_gradient", "param_update", "dq_pp_workspace_size",
-           "pseudopotential_energy"]
+           "pseudopotential_energy", "dq_fma_rate_probe"]
 
 
 class DQError(RuntimeError):
@@ -123,6 +123,7 @@ def load_library(path=None):
         lib.param_update.argtypes = [P, P, P, f64, f64, P, P, sz, P]
         lib.dq_pp_workspace_size.argtypes = [P, i64, i32, P]
         lib.pseudopotential_energy.argtypes = [P, P, P, i64, i32, P, P, P, P, P, P, P, sz, P]
+        lib.dq_fma_rate_probe.argtypes = [i32, i32, i32, P, P, P]
         for name in EXPORTS:
             getattr(lib, name).restype = ctypes.c_int
         lib.dq_status_string.restype = ctypes.c_char_p
@@ -658,6 +659,28 @@ def test_gemm_tf32x3(X, W, bias=None, bias_period=1):
     _check(lib.dq_test_gemm_tf32x3(_ptr(X), rows, K, X.stride(0), _ptr(W.contiguous()), n, _ptr(bias), bias_period,
                                    _ptr(Y), n, _ptr(wsplit), _ptr(st), stream))
     return Y, st
+
+
+def fma_rate(kind="fp32", device=None, blocks=152 * 8, iters=None, reps=5):
+    """Measured FMA rate of the CUDA cores in TFLOP/s (kind "fp32" or "fp64"): the best of
+    ``reps`` timed launches of dq_fma_rate_probe (CUDA events on the current stream)."""
+    lib = load_library()
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    k = {"fp32": 0, "fp64": 1}[kind]
+    iters = iters or (4096 if k == 0 else 256)
+    sink = torch.empty(blocks, dtype=torch.float64, device=dev)
+    stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    flops = ctypes.c_double()
+    _check(lib.dq_fma_rate_probe(k, blocks, max(1, iters // 64), _ptr(sink), stream, ctypes.byref(flops)))  # warm-up
+    best = 0.0
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        _check(lib.dq_fma_rate_probe(k, blocks, iters, _ptr(sink), stream, ctypes.byref(flops)))
+        b.record()
+        torch.cuda.synchronize(dev)
+        best = max(best, flops.value / (a.elapsed_time(b) / 1e3) / 1e12)
+    return best
 
 
 class LogAbsPsi(torch.autograd.Function):

@@ -20,8 +20,12 @@
 // Host code cannot pass the array's name to a kernel: in host code that name
 // is only a stand-in for the symbol, not a device address.  The first call on
 // a device, made with that device current, looks the address up with
-// cudaGetSymbolAddress and caches it; that first call may load the module and
-// should therefore come before any stream capture.  No call allocates.
+// cudaGetSymbolAddress and caches it for the life of the process; that first
+// call may load the module and should therefore come before any stream
+// capture.  A device reset (cudaDeviceReset, or a reset of the primary
+// context) destroys the array with the context that holds it, and the cached
+// address with it: like a handle's device buffers, it must not be used on
+// that device afterwards.  No call allocates.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -64,11 +68,14 @@ extern "C" dq_status vmc_loss_weights_noalloc(dq_handle h, const void* e_loc, in
   if (st != DQ_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t e;
+  // timed like the workspace form when the handle's per-launch profiling is on
+  if (h->prof) h->prof->begin(dq::PK_LOSS_WEIGHTS, s);
   if (h->precision == DQ_FP64)
     e = dq::launch_loss_weights<double>(static_cast<const double*>(e_loc), B, clip_k, static_cast<double*>(weights),
                                         stats, scratch, s);
   else
     e = dq::launch_loss_weights<float>(static_cast<const float*>(e_loc), B, clip_k, static_cast<float*>(weights),
                                        stats, scratch, s);
+  if (h->prof) h->prof->end(s);
   return e == cudaSuccess ? DQ_OK : DQ_ERR_CUDA;
 }

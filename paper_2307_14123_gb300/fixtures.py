@@ -322,6 +322,21 @@ def network_off_params(system, cfg, zeta):
     return theta
 
 
+def smooth_params(system, cfg, seed, orbital_scale=0.3):
+    """Seeded parameters of a smooth state with small kinetic terms: the random-init blob of
+    ``seed`` with the orbital head W_o scaled by ``orbital_scale`` and its bias b_o set to 1, so
+    that every orbital is its envelope modulated by the network by about +-orbital_scale
+    (the network, Jastrow and envelopes keep their random-init values)."""
+    theta = init_params(system, cfg, seed)
+    off = param_offsets(system, cfg)
+    for s in ("up", "dn"):
+        for name, f in ((f"W_o_{s}", lambda x: x * orbital_scale), (f"b_o_{s}", lambda x: np.ones_like(x))):
+            o, shape = off[name]
+            n = int(np.prod(shape))
+            theta[o:o + n] = f(theta[o:o + n])
+    return theta
+
+
 # ----------------------------------------------------------------------------
 # Walkers
 # ----------------------------------------------------------------------------

@@ -63,11 +63,31 @@ def allreduce_gradient(g: torch.Tensor, group=None) -> torch.Tensor:
     return g
 
 
-def global_energy(e_sum2: torch.Tensor, count: int, group=None):
-    """Mean and variance of the local energy over all ranks from per-rank
-    [sum E, sum E^2] (FP64) and walker counts."""
-    t = torch.cat([e_sum2.double().reshape(-1), torch.tensor([float(count)], dtype=torch.float64,
-                                                              device=e_sum2.device)])
-    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
-    mean = t[0] / t[2]
-    return mean, t[1] / t[2] - mean * mean
+def global_energy(e_local: torch.Tensor, group=None):
+    """Mean and variance of the local energy over all ranks' walkers, from each rank's local
+    energies.  Each rank forms its count, mean and centred sum of squares M2 = sum (E - mean)^2
+    in FP64; the ranks' triples are all-gathered and merged in rank order by the pairwise update
+    of Chan, Golub and LeVeque (1979): n = n_a + n_b, d = mean_b - mean_a, mean = mean_a + d n_b / n,
+    M2 = M2_a + M2_b + d^2 n_a n_b / n.  No step subtracts two large moments, so the variance keeps
+    its relative accuracy when |mean| is much larger than the spread (E[x^2] - mean^2 would not).
+    Non-finite energies are excluded."""
+    e = e_local.detach().double().reshape(-1)
+    e = e[torch.isfinite(e)]
+    n = float(e.numel())
+    mu = float(e.mean()) if n else 0.0
+    m2 = float(((e - mu) ** 2).sum()) if n else 0.0
+    mine = torch.tensor([n, mu, m2], dtype=torch.float64, device=e_local.device)
+    world = dist.get_world_size(group)
+    parts = [torch.zeros_like(mine) for _ in range(world)]
+    dist.all_gather(parts, mine, group=group)
+    n_a, mean_a, m2_a = 0.0, 0.0, 0.0
+    for p in parts:
+        n_b, mean_b, m2_b = (float(x) for x in p)
+        if n_b == 0:
+            continue
+        tot = n_a + n_b
+        d = mean_b - mean_a
+        mean_a = mean_a + d * n_b / tot
+        m2_a = m2_a + m2_b + d * d * n_a * n_b / tot
+        n_a = tot
+    return mean_a, (m2_a / n_a if n_a else float("nan"))

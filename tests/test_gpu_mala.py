@@ -12,6 +12,7 @@ import pytest
 import torch
 
 import oracle
+from fp32_contract import near_nodal
 from paper_2307_14123_gb300 import fixtures as fx
 
 pytestmark = pytest.mark.gpu
@@ -54,8 +55,10 @@ def _teacher_forced(name, precision, B, steps, tau, pos_tol, la_tol, g_tol, band
     n = h.mala_step(th_t, r_t, la_t, g_t, n_steps=0, tau=tau, grad_valid=False, e_loc=e_t)
     assert int(n.item()) == 0 and torch.equal(r_t, torch.tensor(r, dtype=th_t.dtype, device="cuda:0"))
     ref0 = o.local_energy(theta, r, with_grad=True)
-    _check_state(_np(la_t), _np(g_t), ref0["logabs"], ref0["grad"].reshape(r.shape), np.ones(B, bool), la_tol, g_tol)
-    _check_eloc(_np(e_t), ref0, np.ones(B, bool), precision)
+    loose0 = near_nodal(o, theta, r, ref0["logabs"]) if precision != "fp64" else np.zeros(B, bool)
+    _check_state(_np(la_t), _np(g_t), ref0["logabs"], ref0["grad"].reshape(r.shape), np.ones(B, bool), la_tol, g_tol,
+                 loose0)
+    _check_eloc(_np(e_t), ref0, np.ones(B, bool), precision, loose0)
     flips = rejected = 0
     for t in range(steps):
         r_prev, la_prev, g_prev, e_prev = _np(r_t), _np(la_t), _np(g_t), _np(e_t)
@@ -72,35 +75,40 @@ def _teacher_forced(name, precision, B, steps, tau, pos_tol, la_tol, g_tol, band
             flips += int(diff.sum())
         same = ~diff
         np.testing.assert_allclose(r_new[same], ro[same], rtol=0, atol=pos_tol)
-        _check_state(la_new, g_new, lo, go, same & gpu_acc, la_tol, g_tol)
+        ref_new = o.local_energy(theta, r_new, with_grad=True)
+        loose = near_nodal(o, theta, r_new, ref_new["logabs"]) if precision != "fp64" else np.zeros(B, bool)
+        _check_state(la_new, g_new, lo, go, same & gpu_acc, la_tol, g_tol, loose)
         assert np.array_equal(la_new[~gpu_acc], la_prev[~gpu_acc]) and np.array_equal(g_new[~gpu_acc], g_prev[~gpu_acc])
         assert np.array_equal(e_new[~gpu_acc], e_prev[~gpu_acc])
         # the carried E_loc of moved walkers is the local energy at their new positions
-        _check_eloc(e_new, o.local_energy(theta, r_new, with_grad=True), gpu_acc, precision)
+        _check_eloc(e_new, ref_new, gpu_acc, precision, loose)
         assert gpu_acc.sum() > 0
         rejected += int(B - gpu_acc.sum())
     print(f"{name} MALA: {flips} near-threshold flips, {rejected} rejections over {steps} steps of {B} walkers")
     return rejected
 
 
-def _check_eloc(e, ref, mask, precision):
-    """FP64: 1e-10 max(1, |E_loc|); FP32: max(1e-4 Ha, 3e-5 S_b), S_b the size of the kinetic terms
-    (the local-energy parity bound)."""
+def _check_eloc(e, ref, mask, precision, loose):
+    """FP64: 1e-10 max(1, |E_loc|); FP32: the contract's max(1e-4 Ha, 1e-5 S_b), S_b the size of the
+    kinetic terms, ten times looser at near-nodal walkers (tests/fp32_contract.py)."""
     er = ref["e_loc"][mask]
     err = np.abs(e[mask] - er)
     if precision == "fp64":
         assert np.all(err <= 1e-10 * np.maximum(1, np.abs(er))), float(err.max())
     else:
         S = 0.5 * (np.abs(ref["lap"][mask]) + np.sum(ref["grad"][mask] ** 2, axis=1))
-        assert np.all(err <= np.maximum(1e-4, 3e-5 * S)), float((err / S).max())
+        tol = np.maximum(1e-4, 1e-5 * S) * np.where(loose[mask], 10, 1)
+        assert np.all(err <= tol), float((err / S).max())
 
 
-def _check_state(la, g, la_ref, g_ref, mask, la_tol, g_tol):
-    """log|psi| within la_tol max(1, |log|psi||); each walker's drift within g_tol of its largest component."""
-    assert np.all(np.abs(la[mask] - la_ref[mask]) <= la_tol * np.maximum(1, np.abs(la_ref[mask])))
+def _check_state(la, g, la_ref, g_ref, mask, la_tol, g_tol, loose):
+    """log|psi| within la_tol max(1, |log|psi||) and each walker's drift within g_tol of its largest
+    component; both ten times looser at near-nodal walkers."""
+    f = np.where(loose[mask], 10, 1)
+    assert np.all(np.abs(la[mask] - la_ref[mask]) <= la_tol * np.maximum(1, np.abs(la_ref[mask])) * f)
     scale = np.abs(g_ref[mask]).max(axis=(1, 2), keepdims=True)
     gerr = np.abs(g[mask] - g_ref[mask]) / np.maximum(scale, 1.0)
-    assert np.all(gerr <= g_tol), float(gerr.max())
+    assert np.all(gerr <= g_tol * f[:, None, None]), float(gerr.max())
 
 
 def test_mala_lih_fp64_teacher_forced():
@@ -110,9 +118,10 @@ def test_mala_lih_fp64_teacher_forced():
 
 def test_mala_n2_fp32_teacher_forced():
     # FP32 state: the position is stored in FP32 (|r| <= ~10 bohr: 1e-6 rounding) after a
-    # drift step of tau * vbar with vbar computed from the FP32 drift; log|psi| and drift
-    # to the FP32 rounding floor of the jets; flips within 1e-3 of the threshold
-    _teacher_forced("n2_fp32", "fp32", 32, 2, 0.02, 2e-5, 1e-4, 1e-3, 1e-3)
+    # drift step of tau * vbar with vbar computed from the FP32 drift; log|psi| to the FP32
+    # contract's 1e-5 relative, the drift to the FP32 rounding floor of the jets; flips within
+    # 1e-3 of the threshold
+    _teacher_forced("n2_fp32", "fp32", 32, 2, 0.02, 2e-5, 1e-5, 1e-3, 1e-3)
 
 
 def test_mala_multi_step_and_device_counter():

@@ -8,7 +8,8 @@ accumulated in FP32 over chunks of 8192 parameters and added in FP64 (relative
 error about 2^-21 of sum |g||g| per chunk), and the conjugate gradients stop at a
 relative residual of 1e-9, so delta carries a relative (norm-wise) error of order
 kappa 2^-21 for a system of condition kappa; the damping below keeps kappa under
-1e3, and the bound is 2e-3.  Real N2 per-walker gradients are
+1e3, and the bound is 2e-3 (norm-wise; element-wise the bound of each element
+follows from it by Cauchy-Schwarz).  Real N2 per-walker gradients are
 checked through the damped normal equations they must satisfy."""
 import numpy as np
 import pytest
@@ -53,10 +54,19 @@ def test_natural_gradient_matches_oracle(B):
     d, st = h.natural_gradient(torch.tensor(G, dtype=torch.float32, device="cuda:0"),
                                torch.tensor(w, dtype=torch.float32, device="cuda:0"), lam, max_iter=400, tol=1e-9)
     ref = oracle.natural_gradient(G, w, lam)
-    err = np.linalg.norm(d.cpu().numpy().astype(np.float64) - ref) / np.linalg.norm(ref)
+    got = d.cpu().numpy().astype(np.float64)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     st = st.cpu().numpy()
     print(f"B={B}: CG iterations {st[0]:.0f}, residual {st[1]:.2e}, relative error {err:.2e}")
     assert st[1] <= 1e-9 and err <= 2e-3
+    # element by element: delta_p = sum_b Gc_bp x_b with x the sample-space solution, so an error
+    # dx of the solve moves delta_p by at most ||Gc[:, p]|| ||dx|| (Cauchy-Schwarz); with
+    # ||dx|| <= 2e-3 ||x|| as above, plus the FP32 rounding of the final product
+    Gc = G - G.mean(axis=0)
+    x = np.linalg.solve(Gc @ Gc.T / B + lam * np.eye(B), w)
+    tol = 2e-3 * np.linalg.norm(Gc, axis=0) * np.linalg.norm(x) + 1e-5 * (np.abs(Gc).T @ np.abs(x))
+    print(f"B={B}: max element error / bound {np.max(np.abs(got - ref) / tol):.2e}")
+    assert np.all(np.abs(got - ref) <= tol)
 
 
 def test_natural_gradient_deterministic_and_zero_iterations():
@@ -109,8 +119,10 @@ def test_relative_damping_matches_absolute():
 
 
 @pytest.mark.parametrize("max_norm", [0.0, 1e-3])
-def test_param_update_definition(max_norm):
-    """theta <- theta - lr s delta, s = min(1, max_norm / (lr ||delta||)) (FP64 reference)."""
+def test_param_update_against_oracle(max_norm):
+    """theta <- theta - lr s delta against oracle.param_update: the GPU forms the step in FP64 and
+    rounds the new parameters to FP32 once, so every element equals the oracle's FP64 value
+    rounded to FP32 (up to the last bit of lr s, a fixed-order FP64 norm)."""
     wl, h = _handle("lih_fp64")
     rng = np.random.default_rng(7)
     th = rng.standard_normal(h.P).astype(np.float32)
@@ -118,11 +130,11 @@ def test_param_update_definition(max_norm):
     lr = 0.05
     t = torch.tensor(th, device="cuda:0")
     st = h.param_update(t, torch.tensor(dl, device="cuda:0"), lr, max_norm).cpu().numpy()
-    nrm = np.linalg.norm(dl.astype(np.float64))
-    s = 1.0 if max_norm <= 0 or lr * nrm <= max_norm else max_norm / (lr * nrm)
+    ref, nrm, s = oracle.param_update(th, dl, lr, max_norm)
     assert st[0] == pytest.approx(nrm, rel=1e-12) and st[1] == pytest.approx(s, rel=1e-12)
-    ref = th.astype(np.float64) - lr * s * dl.astype(np.float64)
-    np.testing.assert_allclose(t.cpu().numpy(), ref, rtol=0, atol=1e-6 * (1 + np.abs(ref).max()))
+    got = t.cpu().numpy().astype(np.float64)
+    ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(got - ref) <= 0.5 * ulp + 1e-12 * np.abs(ref))
 
 
 def test_vmc_train_step_runs_and_is_reproducible():

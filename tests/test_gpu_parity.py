@@ -4,11 +4,12 @@ Inputs are the seeded fixtures; for FP32 handles the oracle receives the
 same FP32-rounded parameters and positions, so both sides see identical
 inputs.  Tolerances (stated per test):
   FP64: |d log|psi|| and |d E_loc| <= 1e-10 max(1, |x|) per walker;
-  FP32: |d E_loc| <= max(1e-4 Ha, 3e-5 S_b) with S_b = (|Lap log|psi|| +
-        |grad log|psi||^2)/2 the size of the kinetic terms whose difference is
-        E_loc, and |d log|psi|| <= 1e-4 max(1, |log|psi||), on every walker;
-        signs equal.  The bound is derived from the rounding floor of an FP32
-        evaluation of the method (tests/test_fp32_floor.py).
+  FP32: |d log|psi|| <= 1e-5 max(1, |log|psi||) and |d E_loc| <= max(1e-4 Ha,
+        1e-5 S_b) per walker (S_b the size of the kinetic terms whose difference
+        is E_loc), signs equal, the mean E_loc within max(1e-4 Ha, 1e-5 mean S_b);
+        exceptions only at near-nodal or near-coalescence walkers classified from
+        the oracle, each listed (tests/fp32_contract.py).  At low kinetic scale
+        (equilibrated walkers of a smooth state) 1e-4 Ha holds per walker.
 """
 import ctypes
 import math
@@ -19,6 +20,7 @@ import pytest
 import torch
 
 import oracle
+from fp32_contract import check_fp32, fp32_floor, nodal_sensitivity
 from paper_2307_14123_gb300 import fixtures as fx
 
 pytestmark = pytest.mark.gpu
@@ -186,17 +188,15 @@ def test_n2_fp64_jets():
     _check_fp64(la, sg, el, oracle.Oracle(wl.system, wl.cfg).local_energy(theta, r))
 
 
-def _check_fp32(la, sg, el, ref, r, label):
-    assert np.array_equal(sg, ref["sign"])
-    e_la = _report(f"{label} logabs", la, ref["logabs"])
-    assert np.all(e_la <= 1e-4 * np.maximum(1, np.abs(ref["logabs"])))
-    print(f"{label}: logabs within 1e-5 relative on {np.mean(e_la <= 1e-5 * np.maximum(1, np.abs(ref['logabs']))):.3f}")
-    S = 0.5 * (np.abs(ref["lap"]) + np.sum(ref["grad"] ** 2, axis=1))
-    tol = np.maximum(1e-4, 3e-5 * S)
-    e_el = _report(f"{label} e_loc", el, ref["e_loc"])
-    print(f"{label}: |dE|/S max {np.max(e_el / S):.2e} median {np.median(e_el / S):.2e}; "
-          f"within 1e-4 Ha: {np.mean(e_el <= 1e-4):.3f}")
-    assert np.all(e_el <= tol), (e_el / S)[e_el > tol]
+def _coefs(system, cfg, theta):
+    o, shape = fx.param_offsets(system, cfg)["c"]
+    return np.asarray(theta[o:o + shape[0]], dtype=np.float64)
+
+
+def _check_fp32(la, sg, el, ref, r, label, orc=None, theta=None, wl=None):
+    """The FP32 contract (tests/fp32_contract.py) on one set of walkers."""
+    sens = nodal_sensitivity(orc, theta, r, _coefs(wl.system, wl.cfg, theta))
+    return check_fp32(label, la, sg, el, ref, sens, f32=fp32_floor(orc, theta, r))
 
 
 def test_n2_fp32_sample():
@@ -204,7 +204,8 @@ def test_n2_fp32_sample():
     h = _handle(wl.system, wl.cfg, "fp32")
     theta, r, th_t, r_t = _inputs(wl.system, wl.cfg, "fp32", 48, wl.param_seed, wl.walker_seed)
     la, sg, el = _np(*h.local_energy(th_t, r_t))
-    _check_fp32(la, sg, el, oracle.Oracle(wl.system, wl.cfg).local_energy(theta, r, with_grad=True), r, "n2 fp32")
+    o = oracle.Oracle(wl.system, wl.cfg)
+    _check_fp32(la, sg, el, o.local_energy(theta, r, with_grad=True), r, "n2 fp32", o, theta, wl)
 
 
 def test_n2_fp32_full_batch_sampled():
@@ -215,10 +216,44 @@ def test_n2_fp32_full_batch_sampled():
     la, sg, el, e2 = h.local_energy(th_t, r_t, sums=True)
     la, sg, el, e2 = _np(la, sg, el, e2)
     idx = np.unique(np.concatenate([[0, 1, wl.B - 1], np.random.default_rng(0).choice(wl.B, 29, replace=False)]))
-    ref = oracle.Oracle(wl.system, wl.cfg).local_energy(theta, r[idx], with_grad=True)
-    _check_fp32(la[idx], sg[idx], el[idx], ref, r[idx], "n2 fp32 full")
+    o = oracle.Oracle(wl.system, wl.cfg)
+    ref = o.local_energy(theta, r[idx], with_grad=True)
+    _check_fp32(la[idx], sg[idx], el[idx], ref, r[idx], "n2 fp32 full", o, theta, wl)
     fin = np.isfinite(el)
     assert e2[0] == pytest.approx(np.sum(el[fin].astype(np.float64)), rel=1e-9)
+
+
+def oracle_equilibrated(orc, theta, system, B, seed, steps, step_size):
+    """Walkers drawn from |psi|^2 by the oracle's Metropolis sampler (FP64, the fixture draws of
+    ``seed``), from the by-charge placement: inputs that come from the oracle alone."""
+    r = fx.init_walkers(system, B, seed)
+    la, _ = orc.evaluate(theta, r)
+    for t in range(steps):
+        xi, u = fx.metropolis_draws(seed, B, system.n_elec, t)
+        r, la, _ = orc.metropolis_step(theta, r, la, xi, u, step_size)
+    return r
+
+
+def test_lih_fp32_low_kinetic_scale():
+    """1e-4 Ha per walker where FP32 arithmetic can resolve it.  LiH (D=32, L=2) with smooth
+    orbitals (envelopes modulated by the network by about +-30 %, fixtures.smooth_params) and
+    2048 walkers equilibrated by the oracle's Metropolis sampler (300 sweeps): the kinetic
+    terms S_b are tens of Ha instead of the 1e3-1e8 Ha of near-nodal random-init walkers.
+    Bounds: |d E_loc| <= 1e-4 Ha on >= 99.9 % of the walkers and on the mean; the FP32
+    contract on all."""
+    wl = fx.workload("lih_fp64")
+    o = oracle.Oracle(wl.system, wl.cfg)
+    theta = fx.smooth_params(wl.system, wl.cfg, 0).astype(np.float32).astype(np.float64)
+    r = oracle_equilibrated(o, theta, wl.system, 2048, 11, 300, 0.3).astype(np.float32).astype(np.float64)
+    h = _handle(wl.system, wl.cfg, "fp32")
+    la, sg, el = _np(*h.local_energy(torch.tensor(theta, dtype=torch.float32, device="cuda:0"),
+                                     torch.tensor(r, dtype=torch.float32, device="cuda:0")))
+    ref = o.local_energy(theta, r, with_grad=True)
+    rep = _check_fp32(la, sg, el, ref, r, "lih fp32 low kinetic scale", o, theta, wl)
+    S = 0.5 * (np.abs(ref["lap"]) + np.sum(ref["grad"] ** 2, axis=1))
+    print(f"S_b median {np.median(S):.1f}, max {S.max():.1f} Ha")
+    assert rep["frac_within_1e-4"] >= 0.999
+    assert abs(rep["e_loc_mean_err"]) <= 1e-4
 
 
 @pytest.mark.parametrize("k", range(len(fx.BATCH_MOLECULES)))
@@ -230,7 +265,8 @@ def test_batch_molecules_fp32_sample(k):
     B = 12 if wl.system.n_elec < 40 else 4
     theta, r, th_t, r_t = _inputs(wl.system, wl.cfg, "fp32", B, wl.param_seed, wl.walker_seed)
     la, sg, el = _np(*h.local_energy(th_t, r_t))
-    _check_fp32(la, sg, el, oracle.Oracle(wl.system, wl.cfg).local_energy(theta, r, with_grad=True), r, wl.name)
+    o = oracle.Oracle(wl.system, wl.cfg)
+    _check_fp32(la, sg, el, o.local_energy(theta, r, with_grad=True), r, wl.name, o, theta, wl)
 
 
 # ----------------------------------------------------------------------------

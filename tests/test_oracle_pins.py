@@ -923,6 +923,21 @@ def _natgrad_inputs(B, P, seed):
     return G, w
 
 
+def test_param_update_step_length_limit():
+    """The parameter step moves along -delta by lr ||delta|| when that is within max_norm (or
+    max_norm <= 0), and by exactly max_norm otherwise."""
+    rng = np.random.default_rng(3)
+    th, d = rng.normal(size=50), rng.normal(size=50)
+    lr, nrm = 0.1, np.linalg.norm(d)
+    for max_norm, length in ((0.0, lr * nrm), (-1.0, lr * nrm), (10.0, lr * nrm), (0.05, 0.05)):
+        new, n_out, s = oracle.param_update(th, d, lr, max_norm)
+        step = th - new
+        assert n_out == pytest.approx(nrm, rel=1e-14)
+        assert np.linalg.norm(step) == pytest.approx(length, rel=1e-12)
+        np.testing.assert_allclose(step / np.linalg.norm(step), d / nrm, rtol=1e-12, atol=1e-14)
+        assert s == pytest.approx(length / (lr * nrm), rel=1e-12)
+
+
 @pytest.mark.parametrize("B,P", [(40, 13), (12, 30)])
 def test_natural_gradient_push_through(B, P):
     """Sample-space (B x B) and parameter-space (P x P) forms agree."""

@@ -1,6 +1,6 @@
 """Multi-process (gloo, world size 2, CPU) checks of the walker-sharded VMC
 step: the gathered clipping weights, the all-reduced gradient and the global
-energy moments equal the single-process results on the whole batch."""
+energy mean and variance (merged from per-rank centred moments) equal the single-process results on the whole batch."""
 import os
 import socket
 
@@ -32,9 +32,10 @@ def _worker(rank, world, port, B, P, q):
     w = sharding.global_loss_weights(e_loc, lambda e: torch.tensor(oracle.clipped_loss_weights(e.numpy(), 5.0)[0]))
     g = torch.tensor(w.numpy() @ g_all[off:off + cnt])
     sharding.allreduce_gradient(g)
-    e2 = torch.tensor([e_loc.sum().item(), (e_loc ** 2).sum().item()], dtype=torch.float64)
-    mean, var = sharding.global_energy(e2, cnt)
-    q.put((rank, off, cnt, w.numpy(), g.numpy(), float(mean), float(var)))
+    mean, var = sharding.global_energy(e_loc)
+    # an offset of 1e9 Ha with a spread of a few Ha: the centred merge keeps the variance
+    mean_off, var_off = sharding.global_energy(e_loc + 1e9)
+    q.put((rank, off, cnt, w.numpy(), g.numpy(), float(mean), float(var), float(mean_off), float(var_off)))
     dist.barrier()
     dist.destroy_process_group()
 
@@ -61,6 +62,8 @@ def test_sharded_step_equals_unsharded():
         np.testing.assert_allclose(r[4], w_ref @ g_all, rtol=1e-12, atol=1e-14)
         assert abs(r[5] - e_all.mean()) < 1e-10 * max(1, abs(e_all.mean()))
         assert abs(r[6] - e_all.var()) < 1e-8 * e_all.var()
+        assert abs(r[7] - (e_all.mean() + 1e9)) < 1e-6
+        assert abs(r[8] - e_all.var()) < 1e-6 * e_all.var()
 
 
 def test_shard_covers_every_walker_once():
