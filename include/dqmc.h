@@ -459,14 +459,38 @@ dq_status vmc_loss_weights_multi(dq_multi m, const void* const* e_loc, const int
 
 /* Tile shape of one handle (no counterpart in the paper): msg_ib = receivers
  * per warp task of the jet message kernel (its register tile is msg_ib x 4
- * channels; 8 or 4, 0 restores the default 8).  Results do not depend on it.
- * dq_autotune times local_energy on the given walkers for msg_ib 8 and 4 and
- * walker chunks (dq_set_max_chunk) of 4096 and 2048, one warm-up and two timed
- * calls each (CUDA events on `stream`, host waits), and keeps the fastest;
- * workspace as for local_energy with B walkers.  Synchronises; not for use
- * inside a stream capture.  best_ms: nullable host double. */
+ * channels; 8 or 4, 0 restores the default 8).  Results do not depend on it. */
 dq_status dq_set_msg_tile(dq_handle h, int32_t msg_ib);
 dq_status dq_msg_tile(dq_handle h, int32_t* msg_ib);
+
+/* Kernels of the jet layers (Eqs. 17-18) of local_energy and mala_step (no
+ * counterpart in the paper): mode 1 runs each layer's messages, update map W_g
+ * and residual tanh update as one kernel whose messages are the tensor-core
+ * A operand and never reach memory; mode 2 runs them as the message kernel,
+ * the W_g GEMM and the update kernel, with the messages in the workspace;
+ * mode 0 (the default) is mode 1 where the handle supports it and mode 2
+ * elsewhere.  Mode 1 needs DQ_FP32, width 128, at most 16 electrons (8 per
+ * spin) and 8 nuclei: DQ_ERR_UNSUPPORTED otherwise.  Both modes compute the
+ * same quantities within the FP32 mode's rounding (the sums run in different
+ * orders).  The workspace size depends on the mode (mode 2 adds the message
+ * buffer): query dq_workspace_size after setting it.  dq_layer_kernel reports
+ * 1 if the jet layers currently run fused, else 0. */
+dq_status dq_set_layer_kernel(dq_handle h, int32_t mode);
+dq_status dq_layer_kernel(dq_handle h, int32_t* fused);
+
+/* dq_autotune times local_energy on the given walkers for every candidate of
+ *   layer kernels  fused, separate   (dq_set_layer_kernel 1 or 2; the fused
+ *                                      one only where supported, the separate
+ *                                      one only if ws_bytes holds its message
+ *                                      buffer),
+ *   walker chunk   4096, 2048        (dq_set_max_chunk: the M extent of every
+ *                                      GEMM, the grid of every other kernel),
+ *   msg_ib         8, 4              (separate message kernel only),
+ * one warm-up and two timed calls each (CUDA events on `stream`, host waits),
+ * and keeps the fastest; workspace: at least dq_workspace_size(op =
+ * DQ_OP_LOCAL_ENERGY) for a chunk of min(B, 4096) walkers plus 9 B per
+ * walker.  Synchronises; not for use inside a stream capture.  best_ms:
+ * nullable host double. */
 dq_status dq_autotune(dq_handle h, const void* params, const void* r, int64_t B, void* ws, size_t ws_bytes,
                       void* stream, double* best_ms);
 

@@ -38,7 +38,7 @@ EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_
            "dq_multi_handle", "dq_multi_set_rounds", "dq_multi_rounds", "dq_multi_workspace_size",
            "ansatz_eval_multi", "local_energy_multi", "mcmc_step_multi", "grad_logpsi_multi",
            "vmc_loss_weights_multi", "dq_autotune_multi", "dq_multi_tuning", "dq_set_msg_tile", "dq_msg_tile", "dq_autotune", "natural_gradient", "param_update", "dq_pp_workspace_size",
-           "pseudopotential_energy", "dq_fma_rate_probe"]
+           "pseudopotential_energy", "dq_fma_rate_probe", "dq_set_layer_kernel", "dq_layer_kernel"]
 
 
 class DQError(RuntimeError):
@@ -124,6 +124,8 @@ def load_library(path=None):
         lib.dq_pp_workspace_size.argtypes = [P, i64, i32, P]
         lib.pseudopotential_energy.argtypes = [P, P, P, i64, i32, P, P, P, P, P, P, P, sz, P]
         lib.dq_fma_rate_probe.argtypes = [i32, i32, i32, P, P, P]
+        lib.dq_set_layer_kernel.argtypes = [P, i32]
+        lib.dq_layer_kernel.argtypes = [P, P]
         for name in EXPORTS:
             getattr(lib, name).restype = ctypes.c_int
         lib.dq_status_string.restype = ctypes.c_char_p
@@ -195,14 +197,21 @@ class Ansatz:
         _check(self.lib.dq_set_msg_tile(self.h, int(msg_ib)))
 
     def autotune(self, params, r):
-        """Times local_energy on these walkers for the candidate tile shapes (message
-        register tile, walker chunk) and keeps the fastest; returns (ms, chunk, msg_ib)."""
+        """Times local_energy on these walkers for the candidate layer kernels (fused or separate),
+        walker chunks and message register tiles, and keeps the fastest; returns (ms, chunk,
+        msg_ib)."""
         params = self._dev(params, shape=(self.P,))
         r = self._dev(r)
         B = r.numel() // (3 * self.N)
         keep = self.max_chunk()
+        keep_lk = self.layer_kernel_fused()
         self.set_max_chunk(4096)  # the largest candidate
-        n = self.workspace_size(B, OP_LOCAL_ENERGY) + 2 * ((B * 4 + 255) // 256 * 256) + (B + 255) // 256 * 256
+        n = self.workspace_size(B, OP_LOCAL_ENERGY)
+        if self.precision == "fp32":
+            _check(self.lib.dq_set_layer_kernel(self.h, 2))  # the separate kernels' message buffer
+            n = max(n, self.workspace_size(B, OP_LOCAL_ENERGY))
+            _check(self.lib.dq_set_layer_kernel(self.h, 1 if keep_lk else 2))
+        n += 2 * ((B * 4 + 255) // 256 * 256) + (B + 255) // 256 * 256
         self.set_max_chunk(keep)
         ws = self._ws if self._ws is not None and self._ws.numel() >= n else torch.empty(n, dtype=torch.uint8,
                                                                                        device=self.device)
@@ -211,6 +220,16 @@ class Ansatz:
         _check(self.lib.dq_autotune(self.h, _ptr(params), _ptr(r), B, _ptr(ws), ws.numel(), self._stream(),
                                     ctypes.byref(best)))
         return best.value, self.max_chunk(), self._msg_ib()
+
+    def set_layer_kernel(self, mode):
+        """Jet layers: 1 fused kernel (messages as the tensor-core operand), 2 separate kernels, 0 the
+        default (fused where supported)."""
+        _check(self.lib.dq_set_layer_kernel(self.h, int(mode)))
+
+    def layer_kernel_fused(self):
+        v = ctypes.c_int32()
+        _check(self.lib.dq_layer_kernel(self.h, ctypes.byref(v)))
+        return bool(v.value)
 
     def _msg_ib(self):
         v = ctypes.c_int32()

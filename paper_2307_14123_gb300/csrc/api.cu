@@ -93,7 +93,7 @@ ParamOffsets make_offsets(int D, int L, int K, int Q, int M, int nc_up, int nc_d
 const char* prof_kind_name(int k) {
   static const char* fwd[PK_FWD_KINDS] = {"geometry", "edge_hidden", "gemm_edge", "messages", "gemm_node",
                                           "gemm_update", "update", "gemm_orbital", "orbital_det", "jastrow_sum",
-                                          "gemm_jastrow", "combine", "layer0_node"};
+                                          "gemm_jastrow", "combine", "layer0_node", "layer_fused"};
   static const char* fwd_jet[PK_FWD_KINDS];
   static const char* other[PK_COUNT - 2 * PK_FWD_KINDS] = {"esum", "propose", "accept", "loss_weights",
                                                            "bwd_combine", "bwd_det", "bwd_gemm", "bwd_update",
@@ -128,6 +128,10 @@ struct FwdPlan {
 // 128-byte TMA rows (D % 32 == 0); in BF16 mode the node and update maps take
 // the BF16 GEMM instead.
 inline bool use_tf32x3(const dq_handle_s& h) { return h.precision != DQ_FP64 && h.D % 32 == 0; }
+// Jet layers through the fused message / update-map / update kernel (layer_fused.cu).
+inline bool use_fused(const dq_handle_s& h, bool jets) {
+  return jets && h.layer_kernel != 2 && use_tf32x3(h) && layer_fused_supported(h);
+}
 constexpr int kT3PerLayer = 14;  // D x D blocks per layer: W_g 2 x 3, W_h 2, W2 2 x 3
 // TF32 splits: the layers' blocks, then W_o of both spins (high, low; K * nmax x D
 // each), then the Jastrow map W_J1 (high, low; D x D)
@@ -188,7 +192,9 @@ FwdPlan plan_forward(const dq_handle_s& h, int64_t Bc, bool jets, size_t elem) {
   const bool bf = h.precision == DQ_BF16_MIXED;
   p.F = take(Bc * N * C * D * elem);
   p.Z = take(Bc * N * C * D * elem);
-  p.msg = take(bf ? 0 : Bc * N * C * 3 * D * elem);
+  // messages; with the fused layer kernel only the electron-nucleus messages of five channels and
+  // their update-map products
+  p.msg = take(bf ? 0 : use_fused(h, jets) ? Bc * N * 11 * D * elem : Bc * N * C * 3 * D * elem);
   p.phi = take(Bc * N * C * K * nmax * elem);
   p.det = take(Bc * 2 * K * (3 * N + 3) * sizeof(double));
   p.js = take(Bc * C * D * elem);
@@ -366,6 +372,20 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
       }
       const RowMap node{(int64_t)N * C, (int64_t)N * C * D, D};
       const int64_t rows = nb * N * C;
+      if (use_fused(h, jets)) {  // messages, update map and update in one kernel
+        const bool z_const = l == 0 && !h.el_init;
+        if (!z_const)
+          DQ_LAUNCH(h, kb + PK_GEMM_NODE, gemm_tf32x3_tc(reinterpret_cast<const float*>(bf.F), rows, D, D, wh_t3(l, 0),
+                                                         wh_t3(l, 1), D, nullptr, 1, reinterpret_cast<float*>(bf.Z), D,
+                                                         h.d_status, s));
+        if constexpr (sizeof(T) == 4)
+          DQ_LAUNCH(h, kb + PK_LAYER_FUSED,
+                    launch_layer_fused(h, d, params, l, z_const, bf.Z, bf.z0, bf.ew, bf.geo, bf.msg, wg_t3(l, 0),
+                                       wg_t3(l, 1), s));
+        // the electron-nucleus part u_n (with b_g) sits after m_n in the message buffer
+        DQ_LAUNCH(h, kb + PK_UPDATE, launch_update<T>(h, d, params, z_const, bf, s, bf.msg + nb * N * 5 * D));
+        continue;
+      }
       if (l == 0 && !h.el_init) {
         DQ_LAUNCH(h, kb + PK_MESSAGES, launch_messages<T>(h, d, params, l, true, bf, s));
       } else {
@@ -1002,11 +1022,20 @@ dq_status run_forward_multi(const dq_multi_s& g, const T* const* params, const T
         }
         if (!use_tc && nj > 0) DQ_LAUNCH(H, kb + PK_GEMM_NODE, gemm_tf32x3_tc_jobs(jd, nj, H.d_status, s));
       }
-      DQ_LAUNCH(H, kb + PK_MESSAGES, launch_messages_group<T>(mf, n, l, l == 0, s));
+      // molecules on the fused layer kernel (as in their single-molecule calls) leave the
+      // grouped message, update-map and update launches
+      MolFwd<T> rest[kMaxGroup];
+      bool fused[kMaxGroup];
+      for (int m = 0; m < n; ++m) {
+        rest[m] = mf[m];
+        fused[m] = !use_tc && use_fused(*g.h[m], jets) && mf[m].d.Bc > 0;
+        if (fused[m]) rest[m].d.Bc = 0;
+      }
+      DQ_LAUNCH(H, kb + PK_MESSAGES, launch_messages_group<T>(rest, n, l, l == 0, s));
       nj = 0;
       for (int m = 0; m < n; ++m) {  // update map W_g [m_par; m_anti; m_nuc] + b_g
         const dq_handle_s& h = *g.h[m];
-        const FwdDims& d = mf[m].d;
+        const FwdDims& d = rest[m].d;
         if (d.Bc <= 0) continue;
         const int64_t rows = d.Bc * d.N * d.C;
         const float* bg = reinterpret_cast<const float*>(params[m] + h.off.layer[l].b_g);
@@ -1021,7 +1050,17 @@ dq_status run_forward_multi(const dq_multi_s& g, const T* const* params, const T
         }
       }
       if (!use_tc) DQ_LAUNCH(H, kb + PK_GEMM_UPDATE, gemm_tf32x3_tc_jobs(jd, nj, H.d_status, s));
-      DQ_LAUNCH(H, kb + PK_UPDATE, launch_update_group<T>(mf, n, l == 0, s));
+      DQ_LAUNCH(H, kb + PK_UPDATE, launch_update_group<T>(rest, n, l == 0, s));
+      for (int m = 0; m < n; ++m)
+        if (fused[m]) {
+          const dq_handle_s& h = *g.h[m];
+          const bool z_const = l == 0 && !h.el_init;
+          DQ_LAUNCH(H, kb + PK_LAYER_FUSED,
+                    launch_layer_fused(h, mf[m].d, params[m], l, z_const, mf[m].b.Z, mf[m].b.z0, mf[m].b.ew,
+                                       mf[m].b.geo, mf[m].b.msg, w3[m].wg(l, 0), w3[m].wg(l, 1), s));
+          DQ_LAUNCH(H, kb + PK_UPDATE, launch_update<T>(h, mf[m].d, params[m], z_const, mf[m].b, s,
+                                                        mf[m].b.msg + mf[m].d.Bc * h.N * 5 * h.D));
+        }
     }
     int nj = 0;
     for (int m = 0; m < n; ++m) {  // orbitals of both spins of every molecule
@@ -1897,6 +1936,19 @@ dq_status dq_msg_tile(dq_handle h, int32_t* msg_ib) {
   return DQ_OK;
 }
 
+dq_status dq_set_layer_kernel(dq_handle h, int32_t mode) {
+  if (!h || mode < 0 || mode > 2) return DQ_ERR_ARG;
+  if (mode == 1 && !(use_tf32x3(*h) && layer_fused_supported(*h))) return DQ_ERR_UNSUPPORTED;
+  h->layer_kernel = mode;
+  return DQ_OK;
+}
+
+dq_status dq_layer_kernel(dq_handle h, int32_t* fused) {
+  if (!h || !fused) return DQ_ERR_ARG;
+  *fused = use_fused(*h, true) ? 1 : 0;
+  return DQ_OK;
+}
+
 dq_status dq_autotune(dq_handle h, const void* params, const void* r, int64_t B, void* ws, size_t ws_bytes,
                       void* stream, double* best_ms) {
   dq_status st = check_handle(h);
@@ -1908,11 +1960,22 @@ dq_status dq_autotune(dq_handle h, const void* params, const void* r, int64_t B,
   // timing outputs after the largest candidate's forward workspace
   const int64_t keep_chunk = h->max_chunk;
   const int keep_ib = h->msg_ib;
+  const int keep_lk = h->layer_kernel;
+  // layer paths: the fused kernel where supported, and the separate kernels when the workspace
+  // holds their message buffer
+  const bool can_fuse = use_tf32x3(*h) && layer_fused_supported(*h);
   h->max_chunk = 4096;
-  const size_t fwd = align_up(plan_forward(*h, std::min<int64_t>(B, 4096), true, 4).total);
+  h->layer_kernel = can_fuse ? 1 : 2;
+  const size_t fwd_f = align_up(plan_forward(*h, std::min<int64_t>(B, 4096), true, 4).total);
+  h->layer_kernel = 2;
+  const size_t fwd_s = align_up(plan_forward(*h, std::min<int64_t>(B, 4096), true, 4).total);
   h->max_chunk = keep_chunk;
+  h->layer_kernel = keep_lk;
   const size_t b = (size_t)B;
-  if (ws_bytes < fwd + 2 * align_up(b * 4) + align_up(b)) return DQ_ERR_WORKSPACE;
+  const size_t outs = 2 * align_up(b * 4) + align_up(b);
+  const bool try_sep = !can_fuse || ws_bytes >= fwd_s + outs;
+  const size_t fwd = try_sep ? std::max(fwd_f, fwd_s) : fwd_f;
+  if (ws_bytes < fwd + outs) return DQ_ERR_WORKSPACE;
   float* la = reinterpret_cast<float*>(w + fwd);
   float* el = reinterpret_cast<float*>(w + fwd + align_up(b * 4));
   int8_t* sg = reinterpret_cast<int8_t*>(w + fwd + 2 * align_up(b * 4));
@@ -1924,28 +1987,36 @@ dq_status dq_autotune(dq_handle h, const void* params, const void* r, int64_t B,
   }
   double best = -1;
   int64_t best_chunk = keep_chunk;
-  int best_ib = keep_ib;
-  for (int64_t chunk : {(int64_t)4096, (int64_t)2048}) {
-    for (int ib : {8, 4}) {
-      h->max_chunk = chunk;
-      h->msg_ib = ib;
-      float ms = 0;
-      for (int rep = 0; rep < 3 && st == DQ_OK; ++rep) {
-        if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) st = DQ_ERR_CUDA;
-        if (st == DQ_OK)
-          st = run_forward<float>(*h, (const float*)params, (const float*)r, B, true, la, sg, el, w, fwd, s);
+  int best_ib = keep_ib, best_lk = keep_lk;
+  for (int lk : {1, 2}) {
+    if ((lk == 1 && !can_fuse) || (lk == 2 && !try_sep)) continue;
+    for (int64_t chunk : {(int64_t)4096, (int64_t)2048}) {
+      // the message register tile matters only to the separate message kernel
+      for (int ib : {8, 4}) {
+        if (lk == 1 && ib == 4) continue;
+        h->layer_kernel = lk;
+        h->max_chunk = chunk;
+        h->msg_ib = ib;
+        float ms = 0;
+        for (int rep = 0; rep < 3 && st == DQ_OK; ++rep) {
+          if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) st = DQ_ERR_CUDA;
+          if (st == DQ_OK)
+            st = run_forward<float>(*h, (const float*)params, (const float*)r, B, true, la, sg, el, w, fwd, s);
+        }
+        if (st != DQ_OK) break;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          st = DQ_ERR_CUDA;
+          break;
+        }
+        if (best < 0 || ms / 2.0 < best) {
+          best = ms / 2.0;
+          best_chunk = chunk;
+          best_ib = ib;
+          best_lk = lk;
+        }
       }
       if (st != DQ_OK) break;
-      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-        st = DQ_ERR_CUDA;
-        break;
-      }
-      if (best < 0 || ms / 2.0 < best) {
-        best = ms / 2.0;
-        best_chunk = chunk;
-        best_ib = ib;
-      }
     }
     if (st != DQ_OK) break;
   }
@@ -1953,6 +2024,7 @@ dq_status dq_autotune(dq_handle h, const void* params, const void* r, int64_t B,
   cudaEventDestroy(e1);
   h->max_chunk = st == DQ_OK ? best_chunk : keep_chunk;
   h->msg_ib = st == DQ_OK ? best_ib : keep_ib;
+  h->layer_kernel = st == DQ_OK ? best_lk : keep_lk;
   if (best_ms) *best_ms = best;
   return st;
 }

@@ -41,7 +41,8 @@ namespace dq {
 // value-only forward (ansatz_eval, Metropolis) uses kind + kValueOffset.
 enum ProfKind {
   PK_GEOMETRY = 0, PK_EDGE_HIDDEN, PK_GEMM_EDGE, PK_MESSAGES, PK_GEMM_NODE, PK_GEMM_UPDATE, PK_UPDATE,
-  PK_GEMM_ORBITAL, PK_ORBITAL_DET, PK_JASTROW_SUM, PK_GEMM_JASTROW, PK_COMBINE, PK_LAYER0, PK_FWD_KINDS,
+  PK_GEMM_ORBITAL, PK_ORBITAL_DET, PK_JASTROW_SUM, PK_GEMM_JASTROW, PK_COMBINE, PK_LAYER0, PK_LAYER_FUSED,
+  PK_FWD_KINDS,
   PK_ESUM = 2 * PK_FWD_KINDS, PK_PROPOSE, PK_ACCEPT, PK_LOSS_WEIGHTS, PK_BWD_COMBINE, PK_BWD_DET, PK_BWD_GEMM,
   PK_BWD_UPDATE, PK_BWD_MESSAGES, PK_BWD_EDGE, PK_BWD_REDUCE, PK_COUNT
 };
@@ -158,6 +159,7 @@ struct dq_handle_s {
   dq::Edges edges{};
   int64_t max_chunk = 4096;
   int msg_ib = 0;  // receivers per warp task of the jet message kernel (FP32 modes: 8 or 4; 0: 8)
+  int layer_kernel = 0;  // jet layers: 0 fused kernel where supported, 1 the same, 2 separate kernels
   // device tables
   double* d_R = nullptr;   // [M][3]
   float* d_Rf = nullptr;   // [M][3]
@@ -315,6 +317,7 @@ struct MolFwd {
   FwdDims d;
   const T* params;
   FwdBuffers<T> b;
+  const T* un = nullptr;  // fused jet layers: the electron-nucleus part of the pre-activations
 };
 template <class T>
 cudaError_t launch_geometry_group(const MolFwd<T>* m, int n, const T* const* r, cudaStream_t s);
@@ -340,6 +343,18 @@ template <class T>
 cudaError_t launch_messages_group(const MolFwd<T>* m, int n, int layer, bool z_const, cudaStream_t s);
 template <class T>
 cudaError_t launch_update_group(const MolFwd<T>* m, int n, bool from_spin, cudaStream_t s);
+
+// The message and update-map part of one jets layer (layer_fused.cu): the electron-electron
+// messages (Eq. 17) as the A operand of the update map W_g on the tensor cores (three TF32
+// products), so that they never reach memory; the electron-nucleus messages, non-zero on five
+// channels per electron, go through W_g's third block beforehand.  Writes the pre-activations
+// u = W_g m + b_g into Z in place (the tanh update of Eq. 18 follows as in the separate path).
+// mn: workspace of Bc N 11 D floats.  FP32 mode, D = 128, N <= 16 with at most 8 electrons per
+// spin and 8 nuclei.
+bool layer_fused_supported(const dq_handle_s& h);
+cudaError_t launch_layer_fused(const dq_handle_s& h, const FwdDims& d, const float* params, int l, bool z_const,
+                               float* Z, const float* z0, const float* ew, const float* geo, float* mn,
+                               const float* wg_hi, const float* wg_lo, cudaStream_t s);
 template <class T>
 cudaError_t launch_orbital_det_group(const MolFwd<T>* m, int n, cudaStream_t s);
 template <class T>
@@ -361,7 +376,7 @@ cudaError_t launch_messages(const dq_handle_s& h, const FwdDims& d, const T* par
                             FwdBuffers<T> b, cudaStream_t s);
 template <class T>
 cudaError_t launch_update(const dq_handle_s& h, const FwdDims& d, const T* params, bool from_spin,
-                          FwdBuffers<T> b, cudaStream_t s);
+                          FwdBuffers<T> b, cudaStream_t s, const T* un = nullptr);
 template <class T>
 cudaError_t launch_update_io(const dq_handle_s& h, const FwdDims& d, const T* params, bool from_spin, const T* P,
                              const T* Fin, T* Fout, cudaStream_t s, void* Fbf = nullptr);

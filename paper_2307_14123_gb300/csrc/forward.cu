@@ -944,12 +944,13 @@ struct update_kernel_args {
   int D;
   int from_spin;
   __nv_bfloat16* Fbf;
+  const T* un;  // nullable [Bc][N][5][D]: added to the value, own-coordinate and Laplacian channels
 };
 
 template <class T>
 __device__ __forceinline__ void update_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const T* __restrict__ P, const T* Fin, T* Fout, const T* __restrict__ E_spin,
                               int64_t Bc, int N, int n_up, int C, int D, int from_spin,
-                              __nv_bfloat16* __restrict__ Fbf) {
+                              __nv_bfloat16* __restrict__ Fbf, const T* __restrict__ un = nullptr) {
   const int64_t gid = (int64_t)bx_ * blockDim.x + threadIdx.x;
   if (gid >= Bc * N * D) return;
   const int a = (int)(gid % D);
@@ -958,7 +959,11 @@ __device__ __forceinline__ void update_kernel_body(const int64_t bx_, const int 
   const T* p = P + bi * C * D + a;
   const T* fi = Fin + bi * C * D + a;
   T* f = Fout + bi * C * D + a;
-  const T t = tanh_t(p[0]);
+  // the electron-nucleus part of the pre-activation where it was computed apart (value, the
+  // receiver's own coordinates, Laplacian)
+  const T* ub = un ? un + bi * 5 * D + a : nullptr;
+  const T p0 = p[0] + (ub ? ub[0] : T(0));
+  const T t = tanh_t(p0);
   const T dt = T(1) - t * t;
   f[0] = (from_spin ? E_spin[(i < n_up ? 0 : 1) * D + a] : fi[0]) + t;
   if (C > 1) {
@@ -968,8 +973,16 @@ __device__ __forceinline__ void update_kernel_body(const int64_t bx_, const int 
       ss += pc * pc;
       f[(int64_t)c * D] = (from_spin ? T(0) : fi[(int64_t)c * D]) + dt * pc;
     }
+    if (ub)  // the receiver's own coordinates take the electron-nucleus part as well
+      for (int x = 0; x < 3; ++x) {
+        const int64_t c = 1 + 3 * i + x;
+        const T pc = p[c * D], ad = ub[(int64_t)(1 + x) * D];
+        ss += (pc + ad) * (pc + ad) - pc * pc;
+        f[c * D] += dt * ad;
+      }
     const int64_t cl = (int64_t)(C - 1) * D;
-    f[cl] = (from_spin ? T(0) : fi[cl]) + dt * p[cl] - T(2) * t * dt * ss;
+    const T pl = p[cl] + (ub ? ub[4 * D] : T(0));
+    f[cl] = (from_spin ? T(0) : fi[cl]) + dt * pl - T(2) * t * dt * ss;
   }
   if (Fbf) {  // BF16 copy of the embeddings: the input of the next node-map GEMM
     __nv_bfloat16* fb = Fbf + bi * C * D + a;
@@ -990,7 +1003,7 @@ __global__ void update_kernel_group(const __grid_constant__ Grp<update_kernel_ar
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
   GRP_STATIC(m_, const auto& a_ = g.a[K_];
-             update_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.P, a_.Fin, a_.Fout, a_.E_spin, a_.Bc, a_.N, a_.n_up, a_.C, a_.D, a_.from_spin, a_.Fbf);)
+             update_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.P, a_.Fin, a_.Fout, a_.E_spin, a_.Bc, a_.N, a_.n_up, a_.C, a_.D, a_.from_spin, a_.Fbf, a_.un);)
 }
 
 __global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int64_t n) {
@@ -1937,8 +1950,8 @@ cudaError_t launch_messages(const dq_handle_s& h, const FwdDims& d, const T* par
 
 template <class T>
 cudaError_t launch_update(const dq_handle_s& h, const FwdDims& d, const T* params, bool from_spin, FwdBuffers<T> b,
-                          cudaStream_t s) {
-  const MolFwd<T> m{&h, d, params, b};
+                          cudaStream_t s, const T* un) {
+  const MolFwd<T> m{&h, d, params, b, un};
   return launch_update_group<T>(&m, 1, from_spin, s);
 }
 
@@ -2263,7 +2276,7 @@ cudaError_t launch_update_group(const MolFwd<T>* m, int n, bool from_spin, cudaS
     const FwdDims& d = m[k].d;
     if (d.Bc <= 0) continue;
     g.add({m[k].b.Z, m[k].b.F, m[k].b.F, m[k].params + std::max<int64_t>(m[k].h->off.E_spin, 0), d.Bc, d.N, d.n_up, d.C, d.D,
-           from_spin && !m[k].h->el_init ? 1 : 0, static_cast<__nv_bfloat16*>(m[k].b.F_bf)},
+           from_spin && !m[k].h->el_init ? 1 : 0, static_cast<__nv_bfloat16*>(m[k].b.F_bf), m[k].un},
           blocks(d.Bc * d.N * d.D, 256));
   }
   if (g.n == 0) return cudaSuccess;
@@ -2408,7 +2421,7 @@ DQ_INSTANTIATE_GROUP(double)
   template cudaError_t launch_messages<T>(const dq_handle_s&, const FwdDims&, const T*, int, bool, FwdBuffers<T>, \
                                           cudaStream_t);                                                          \
   template cudaError_t launch_update<T>(const dq_handle_s&, const FwdDims&, const T*, bool, FwdBuffers<T>,        \
-                                        cudaStream_t);                                                            \
+                                        cudaStream_t, const T*);                                                  \
   template cudaError_t launch_update_io<T>(const dq_handle_s&, const FwdDims&, const T*, bool, const T*, const T*, \
                                            T*, cudaStream_t, void*);                                              \
   template cudaError_t launch_orbital_det<T>(const dq_handle_s&, const FwdDims&, const T*, FwdBuffers<T>,         \
