@@ -287,6 +287,8 @@ def peaks():
 # from an ncu capture of the layer-1 launch on 512 N2 walkers (FP32, the tuned 4-receiver tile; summary under profiles/); None
 # once the kernel has changed since that capture.
 MSG_DRAM_BYTES_PER_WALKER = (263.570432e6 + 432.803840e6) / 512
+# the same for one launch of the fused layer kernel (layer >= 1); None until captured
+LAYER_FUSED_DRAM_BYTES_PER_WALKER = None
 
 
 def gemm_shapes(wl, chunk):
@@ -373,6 +375,20 @@ def roofline_for(kind, ms, n, wl, chunk, pk, how, alu, steps):
                 "flops_per_launch": flops,
                 "note": "reverse-pass products of the value-only network (input adjoints for bwd_gemm, weight "
                         "gradients for bwd_reduce), averaged over the kind's launches"}
+    if kind == "jet.layer_fused":
+        # the update map W_g over every node channel (the S5 GEMM, 2 N C 3D D per walker) as produced on
+        # the tensor cores; the electron-electron message contraction (CUDA cores) runs inside the same
+        # kernel and is reported beside it
+        flops = 2.0 * chunk * N * C * 3 * D * D
+        peak = pk["bf16_tflops_sustained"] * (1.1 / 2.25) / 3.0
+        ach = flops / t / 1e12
+        return {**base, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": LAYER_FUSED_DRAM_BYTES_PER_WALKER * chunk if LAYER_FUSED_DRAM_BYTES_PER_WALKER else None,
+                "peak_source": f"{how} bf16 sustained x 1.1/2.25 (TF32) / 3 (3xTF32 split)",
+                "flops_per_launch": flops, "message_flops_per_launch": message_flops_per_walker(wl) * chunk,
+                "message_tflops": message_flops_per_walker(wl) * chunk / t / 1e12,
+                "note": "messages, update map and the electron-nucleus part of one layer; FLOPs of the update "
+                        "map (the kernel's tensor-core work), averaged over the layer launches"}
     if kind == "jet.messages":
         L = c.n_layers
         flops = message_flops_per_walker(wl) * chunk
@@ -801,7 +817,7 @@ def main():
     dom = max(prof.items(), key=lambda kv: kv[1][0])[0] if prof else None
     roof = None
     others = []
-    for kind in ("jet.messages", "jet.msg_gemm", "jet.gemm_update", "jet.gemm_edge", "jet.gemm_node",
+    for kind in ("jet.layer_fused", "jet.messages", "jet.gemm_update", "jet.gemm_edge", "jet.gemm_node",
                  "jet.gemm_orbital", "jet.orbital_det", "jet.update", "jet.edge_hidden", "bwd_gemm", "bwd_reduce"):
         if kind in prof:
             e = roofline_for(kind, prof[kind][0], prof[kind][1], wl, chunk, pk, how, alu, args.steps)

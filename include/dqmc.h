@@ -372,11 +372,13 @@ dq_status dq_last_device_status(dq_handle h, void* stream, uint32_t* flags);
  * counts: value-only calls (ansatz_eval, mcmc_step) when the condition
  * estimate of the row-equilibrated matrix exceeds 10000 (below that the FP32
  * log|det| is corrected by the trace of the factorisation residual against
- * the FP32 inverse); local_energy, for
- * spin blocks of at most 8 electrons, when it exceeds 2000 (below that the
- * FP32 inverse is refined once in double-float).  local_energy with larger
- * spin blocks takes FP64 for every matrix (not counted).  Always 0 in FP64
- * mode, where every matrix is FP64. */
+ * the FP32 inverse); local_energy, for determinant blocks of at most 28
+ * electrons, when it exceeds 1e5 or when the iterative refinement of the FP32
+ * inverse (double-float, at most four steps) does not bring the largest
+ * residual entry below 1e-4 (otherwise the tangent products run in
+ * double-float on the FP32 pipes).
+ * local_energy with larger blocks takes FP64 for every matrix (not counted).
+ * Always 0 in FP64 mode, where every matrix is FP64. */
 dq_status dq_fp64_matrix_count(dq_handle h, void* stream, int64_t* count);
 
 /* Test support: the BF16 tensor-core GEMM used by the embedding layers in

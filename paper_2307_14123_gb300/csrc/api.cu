@@ -382,8 +382,7 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
           DQ_LAUNCH(h, kb + PK_LAYER_FUSED,
                     launch_layer_fused(h, d, params, l, z_const, bf.Z, bf.z0, bf.ew, bf.geo, bf.msg, wg_t3(l, 0),
                                        wg_t3(l, 1), s));
-        // the electron-nucleus part u_n (with b_g) sits after m_n in the message buffer
-        DQ_LAUNCH(h, kb + PK_UPDATE, launch_update<T>(h, d, params, z_const, bf, s, bf.msg + nb * N * 5 * D));
+        DQ_LAUNCH(h, kb + PK_UPDATE, launch_update<T>(h, d, params, z_const, bf, s));
         continue;
       }
       if (l == 0 && !h.el_init) {
@@ -1058,8 +1057,7 @@ dq_status run_forward_multi(const dq_multi_s& g, const T* const* params, const T
           DQ_LAUNCH(H, kb + PK_LAYER_FUSED,
                     launch_layer_fused(h, mf[m].d, params[m], l, z_const, mf[m].b.Z, mf[m].b.z0, mf[m].b.ew,
                                        mf[m].b.geo, mf[m].b.msg, w3[m].wg(l, 0), w3[m].wg(l, 1), s));
-          DQ_LAUNCH(H, kb + PK_UPDATE, launch_update<T>(h, mf[m].d, params[m], z_const, mf[m].b, s,
-                                                        mf[m].b.msg + mf[m].d.Bc * h.N * 5 * h.D));
+          DQ_LAUNCH(H, kb + PK_UPDATE, launch_update<T>(h, mf[m].d, params[m], z_const, mf[m].b, s));
         }
     }
     int nj = 0;

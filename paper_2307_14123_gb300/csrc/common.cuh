@@ -317,7 +317,6 @@ struct MolFwd {
   FwdDims d;
   const T* params;
   FwdBuffers<T> b;
-  const T* un = nullptr;  // fused jet layers: the electron-nucleus part of the pre-activations
 };
 template <class T>
 cudaError_t launch_geometry_group(const MolFwd<T>* m, int n, const T* const* r, cudaStream_t s);
@@ -347,7 +346,7 @@ cudaError_t launch_update_group(const MolFwd<T>* m, int n, bool from_spin, cudaS
 // The message and update-map part of one jets layer (layer_fused.cu): the electron-electron
 // messages (Eq. 17) as the A operand of the update map W_g on the tensor cores (three TF32
 // products), so that they never reach memory; the electron-nucleus messages, non-zero on five
-// channels per electron, go through W_g's third block beforehand.  Writes the pre-activations
+// channels per electron, go through W_g's third block apart and are added after.  Writes the pre-activations
 // u = W_g m + b_g into Z in place (the tanh update of Eq. 18 follows as in the separate path).
 // mn: workspace of Bc N 11 D floats.  FP32 mode, D = 128, N <= 16 with at most 8 electrons per
 // spin and 8 nuclei.
@@ -376,7 +375,7 @@ cudaError_t launch_messages(const dq_handle_s& h, const FwdDims& d, const T* par
                             FwdBuffers<T> b, cudaStream_t s);
 template <class T>
 cudaError_t launch_update(const dq_handle_s& h, const FwdDims& d, const T* params, bool from_spin,
-                          FwdBuffers<T> b, cudaStream_t s, const T* un = nullptr);
+                          FwdBuffers<T> b, cudaStream_t s);
 template <class T>
 cudaError_t launch_update_io(const dq_handle_s& h, const FwdDims& d, const T* params, bool from_spin, const T* P,
                              const T* Fin, T* Fout, cudaStream_t s, void* Fbf = nullptr);

@@ -944,13 +944,12 @@ struct update_kernel_args {
   int D;
   int from_spin;
   __nv_bfloat16* Fbf;
-  const T* un;  // nullable [Bc][N][5][D]: added to the value, own-coordinate and Laplacian channels
 };
 
 template <class T>
 __device__ __forceinline__ void update_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, const T* __restrict__ P, const T* Fin, T* Fout, const T* __restrict__ E_spin,
                               int64_t Bc, int N, int n_up, int C, int D, int from_spin,
-                              __nv_bfloat16* __restrict__ Fbf, const T* __restrict__ un = nullptr) {
+                              __nv_bfloat16* __restrict__ Fbf) {
   const int64_t gid = (int64_t)bx_ * blockDim.x + threadIdx.x;
   if (gid >= Bc * N * D) return;
   const int a = (int)(gid % D);
@@ -959,11 +958,7 @@ __device__ __forceinline__ void update_kernel_body(const int64_t bx_, const int 
   const T* p = P + bi * C * D + a;
   const T* fi = Fin + bi * C * D + a;
   T* f = Fout + bi * C * D + a;
-  // the electron-nucleus part of the pre-activation where it was computed apart (value, the
-  // receiver's own coordinates, Laplacian)
-  const T* ub = un ? un + bi * 5 * D + a : nullptr;
-  const T p0 = p[0] + (ub ? ub[0] : T(0));
-  const T t = tanh_t(p0);
+  const T t = tanh_t(p[0]);
   const T dt = T(1) - t * t;
   f[0] = (from_spin ? E_spin[(i < n_up ? 0 : 1) * D + a] : fi[0]) + t;
   if (C > 1) {
@@ -973,16 +968,8 @@ __device__ __forceinline__ void update_kernel_body(const int64_t bx_, const int 
       ss += pc * pc;
       f[(int64_t)c * D] = (from_spin ? T(0) : fi[(int64_t)c * D]) + dt * pc;
     }
-    if (ub)  // the receiver's own coordinates take the electron-nucleus part as well
-      for (int x = 0; x < 3; ++x) {
-        const int64_t c = 1 + 3 * i + x;
-        const T pc = p[c * D], ad = ub[(int64_t)(1 + x) * D];
-        ss += (pc + ad) * (pc + ad) - pc * pc;
-        f[c * D] += dt * ad;
-      }
     const int64_t cl = (int64_t)(C - 1) * D;
-    const T pl = p[cl] + (ub ? ub[4 * D] : T(0));
-    f[cl] = (from_spin ? T(0) : fi[cl]) + dt * pl - T(2) * t * dt * ss;
+    f[cl] = (from_spin ? T(0) : fi[cl]) + dt * p[cl] - T(2) * t * dt * ss;
   }
   if (Fbf) {  // BF16 copy of the embeddings: the input of the next node-map GEMM
     __nv_bfloat16* fb = Fbf + bi * C * D + a;
@@ -1003,7 +990,7 @@ __global__ void update_kernel_group(const __grid_constant__ Grp<update_kernel_ar
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
   GRP_STATIC(m_, const auto& a_ = g.a[K_];
-             update_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.P, a_.Fin, a_.Fout, a_.E_spin, a_.Bc, a_.N, a_.n_up, a_.C, a_.D, a_.from_spin, a_.Fbf, a_.un);)
+             update_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.P, a_.Fin, a_.Fout, a_.E_spin, a_.Bc, a_.N, a_.n_up, a_.C, a_.D, a_.from_spin, a_.Fbf);)
 }
 
 __global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __restrict__ dst, int64_t n) {
@@ -1347,23 +1334,133 @@ __global__ void __launch_bounds__(128) orbital_det_kernel_group(const __grid_con
 // ---------------------------------------------------------------------------
 // Determinant jets of the FP32 modes for spin blocks of at most kDetNR
 // electrons, one warp per matrix, on the FP32 pipes:
-//  * LU of A (FP32 entries, exact) with partial pivoting in FP32 and the
-//    inverse X0 from it;
-//  * one step of inverse refinement, X = X0 + X0 (I - A X0), with the
-//    residual as a compensated dot product (Ogita-Rump-Oishi Dot2), kept as a
-//    double-float pair Xhi + Xlo (error about (kappa u)^2 |A^-1|);
-//  * log|det A| = log|det LU| + tr(X P^T (P A - L U)), the first-order
-//    correction for the backward error of the FP32 factorisation;
+//  * the factorisation of det_factor_jets below (FP32 LU, refined
+//    double-float inverse Xhi + Xlo, log|det A| corrected for the backward
+//    error of the FP32 LU; FP64 for ill-conditioned matrices, counted in n_fp64);
 //  * the 3N + 1 tangents X_t = A^-1 d_t A as compensated dot products with
 //    the rows of Xhi / Xlo in registers; tr X_t from the diagonal in
 //    double-float, sum_t tr(X_t^2) accumulated per lane and reduced once.
-// Matrices whose row-equilibrated condition estimate exceeds
-// DQ_KAPPA_FP32_JET (or whose FP32 LU meets a zero pivot) take the FP64 LU
-// and inverse instead and are counted in n_fp64.
 // ---------------------------------------------------------------------------
-#ifndef DQ_KAPPA_FP32_JET
-#define DQ_KAPPA_FP32_JET 2000.0f
+
+// The factorisation step of the FP32 determinant jets (one warp, n <= 32):
+//  * FP32 LU of A with partial pivoting and the inverse X0 from it; the
+//    row-equilibrated condition estimate kappa = n max_ij |X0_ij| max_k |A_jk|;
+//  * iterative refinement of the inverse as a double-float pair X = Xhi + Xlo,
+//    X <- X + X (I - A X), with the residual as a compensated dot product
+//    (Ogita-Rump-Oishi Dot2) over both parts of X; each step squares the
+//    residual (of the order kappa u at the start), and the steps stop once the
+//    largest residual entry before a step is at most 1e-4 (X then accurate to
+//    about 1e-8 relative), at most four of them;
+//  * log|det A| = log|det LU| - log det(I - E) with E = X (A - P^T L U) (exact
+//    when X = A^-1), kept to second order: tr E + tr(E^2) / 2, with E of the
+//    order kappa u (the third-order term is below 1e-5 up to DQ_KAPPA_FP32_JET_MAX);
+//  * above DQ_KAPPA_FP32_JET_MAX, at a zero FP32 pivot, or when the refinement
+//    does not converge, the FP64 LU and inverse instead, counted in n_fp64.
+// rmax holds the row maxima of A; R and T are n x n scratch (not aliasing A, LU,
+// X0, Xhi, Xlo or each other), LUd / Ainvd n x n doubles (may alias R and T).
+// Returns false if A is singular in FP64.
+#ifndef DQ_KAPPA_FP32_JET_MAX
+#define DQ_KAPPA_FP32_JET_MAX 1.0e5f
 #endif
+__device__ __forceinline__ bool det_factor_jets(const float* A, float* LU, float* X0, float* R, float* T,
+                                                float* Xhi, float* Xlo, double* LUd, double* Ainvd,
+                                                const float* rmax, int* perm, int n, int lane,
+                                                unsigned long long* n_fp64, int* sign, double* logabs) {
+  const int nsq = n * n;
+  bool fp64 = !warp_lu<float>(LU, perm, n, lane, sign, logabs);
+  if (!fp64) {
+    warp_inverse<float>(LU, perm, n, lane, X0);
+    float imax = 0;
+    for (int q = lane; q < nsq; q += 32) imax = fmaxf(imax, fabsf(X0[q]) * rmax[q - (q / n) * n]);
+    const float kappa = float(n) * warp_max(imax);
+    fp64 = !(kappa <= DQ_KAPPA_FP32_JET_MAX);
+  }
+  if (!fp64) {
+    for (int q = lane; q < nsq; q += 32) {
+      Xhi[q] = X0[q];
+      Xlo[q] = 0.f;
+    }
+    __syncwarp();
+    fp64 = true;  // until the residual has converged
+    for (int it = 0; it < 4; ++it) {
+      // residual R = I - A X
+      float rm = 0.f;
+      for (int q = lane; q < nsq; q += 32) {
+        const int a = q / n, m = q - (q / n) * n;
+        dfloat acc = {a == m ? -1.f : 0.f, 0.f};
+        for (int l = 0; l < n; ++l) acc = dot2_step(acc, A[a * n + l], Xhi[l * n + m]);
+        if (it > 0)
+          for (int l = 0; l < n; ++l) acc = dot2_step(acc, A[a * n + l], Xlo[l * n + m]);
+        R[q] = -(acc.hi + acc.lo);
+        rm = fmaxf(rm, fabsf(acc.hi));
+      }
+      rm = warp_max(rm);
+      if (!(rm <= 0.25f)) break;  // not contracting
+      __syncwarp();
+      // T = Xhi R, then X += T (the step squares the residual)
+      for (int q = lane; q < nsq; q += 32) {
+        const int a = q / n, m = q - (q / n) * n;
+        float c = 0.f;
+        for (int l = 0; l < n; ++l) c = fmaf(Xhi[a * n + l], R[l * n + m], c);
+        T[q] = c;
+      }
+      __syncwarp();
+      for (int q = lane; q < nsq; q += 32) {
+        const dfloat x = two_sum(Xhi[q], T[q]);
+        const dfloat y = quick_two_sum(x.hi, __fadd_rn(x.lo, Xlo[q]));
+        Xhi[q] = y.hi;
+        Xlo[q] = y.lo;
+      }
+      __syncwarp();
+      if (rm <= 1e-4f) {  // X now accurate to about rm^2 <= 1e-8 relative
+        fp64 = false;
+        break;
+      }
+    }
+  }
+  if (!fp64) {
+    // R = P A - L U (row r of P A is row perm[r] of A), then T = E = X P^T R:
+    // E[a][c] = sum_r X[a][perm[r]] R[r][c]
+    for (int q = lane; q < nsq; q += 32) {
+      const int r = q / n, c = q - (q / n) * n;
+      const int mm = r < c ? r : c;
+      dfloat acc = {-A[perm[r] * n + c], 0.f};
+      for (int m = 0; m <= mm; ++m) acc = dot2_step(acc, m == r ? 1.f : LU[r * n + m], LU[m * n + c]);
+      R[q] = -(acc.hi + acc.lo);
+    }
+    __syncwarp();
+    for (int q = lane; q < nsq; q += 32) {
+      const int a = q / n, c = q - (q / n) * n;
+      float e = 0.f;
+      for (int r = 0; r < n; ++r) e = fmaf(Xhi[a * n + perm[r]], R[r * n + c], e);
+      T[q] = e;
+    }
+    __syncwarp();
+    float part = 0.f;
+    for (int q = lane; q < nsq; q += 32) {
+      const int a = q / n, c = q - (q / n) * n;
+      part += (a == c ? T[q] : 0.f) + 0.5f * T[q] * T[c * n + a];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    *logabs += (double)part;
+  } else {
+    __syncwarp();
+    if (lane == 0) atomicAdd(n_fp64, 1ull);
+    for (int q = lane; q < nsq; q += 32) LUd[q] = (double)A[q];
+    __syncwarp();
+    if (!warp_lu<double>(LUd, perm, n, lane, sign, logabs)) return false;
+    warp_inverse<double>(LUd, perm, n, lane, Ainvd);
+    for (int q = lane; q < nsq; q += 32) {
+      const double a = Ainvd[q];
+      const float h = (float)a;
+      Xhi[q] = h;
+      Xlo[q] = (float)(a - (double)h);
+    }
+  }
+  __syncwarp();
+  return true;
+}
 constexpr int kDetNR = 8;
 
 __host__ __device__ inline size_t det_jets_smem_per_warp(int nmax, int N3) {
@@ -1456,62 +1553,9 @@ __device__ __forceinline__ void orbital_det_jets_kernel_body(const int64_t bx_, 
 
   int sign = 0;
   double logabs = -INFINITY;
-  bool fp64 = !warp_lu<float>(LU, perm, n, lane, &sign, &logabs);
-  if (!fp64) {
-    warp_inverse<float>(LU, perm, n, lane, X0);
-    float imax = 0;
-    for (int q = lane; q < nsq; q += 32) imax = fmaxf(imax, fabsf(X0[q]) * rmax[q - (q / n) * n]);
-    const float kappa = float(n) * warp_max(imax);
-    fp64 = !(kappa <= DQ_KAPPA_FP32_JET);
-  }
-  if (!fp64) {
-    // residual R = I - A X0 into tmp
-    for (int q = lane; q < nsq; q += 32) {
-      const int a = q / n, m = q - (q / n) * n;
-      dfloat acc = {a == m ? -1.f : 0.f, 0.f};
-      for (int l = 0; l < n; ++l) acc = dot2_step(acc, A[a * n + l], X0[l * n + m]);
-      tmp[q] = -(acc.hi + acc.lo);
-    }
-    __syncwarp();
-    // X = X0 + X0 R as a double-float pair
-    for (int q = lane; q < nsq; q += 32) {
-      const int a = q / n, m = q - (q / n) * n;
-      float c = 0.f;
-      for (int l = 0; l < n; ++l) c = fmaf(X0[a * n + l], tmp[l * n + m], c);
-      const dfloat x = two_sum(X0[q], c);
-      Xhi[q] = x.hi;
-      Xlo[q] = x.lo;
-    }
-    __syncwarp();
-    // log|det A| = log|det LU| + tr(X P^T (P A - L U)); entry (r, c) of P A - L U
-    // pairs with X[c][perm[r]].
-    float part = 0.f;
-    for (int q = lane; q < nsq; q += 32) {
-      const int r = q / n, c = q - (q / n) * n;
-      const int mm = r < c ? r : c;
-      dfloat acc = {-A[perm[r] * n + c], 0.f};
-      for (int m = 0; m <= mm; ++m) acc = dot2_step(acc, m == r ? 1.f : LU[r * n + m], LU[m * n + c]);
-      part = fmaf(Xhi[c * n + perm[r]], -(acc.hi + acc.lo), part);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    logabs += (double)part;
-  } else {
-    if (lane == 0) atomicAdd(n_fp64, 1ull);
-    for (int q = lane; q < nsq; q += 32) LUd[q] = (double)A[q];
-    __syncwarp();
-    if (!warp_lu<double>(LUd, perm, n, lane, &sign, &logabs)) {
-      for (int k = lane; k < N3 + 3; k += 32) out[k] = k == 1 ? -INFINITY : 0.0;
-      return;
-    }
-    warp_inverse<double>(LUd, perm, n, lane, Ainvd);
-    for (int q = lane; q < nsq; q += 32) {
-      const double a = Ainvd[q];
-      const float h = (float)a;
-      Xhi[q] = h;
-      Xlo[q] = (float)(a - (double)h);
-    }
-    __syncwarp();
+  if (!det_factor_jets(A, LU, X0, tmp, Th, Xhi, Xlo, LUd, Ainvd, rmax, perm, n, lane, n_fp64, &sign, &logabs)) {
+    for (int k = lane; k < N3 + 3; k += 32) out[k] = k == 1 ? -INFINITY : 0.0;
+    return;
   }
   if (lane == 0) {
     out[0] = (double)sign;
@@ -1604,15 +1648,291 @@ __device__ __forceinline__ void orbital_det_jets_kernel_body(const int64_t bx_, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Determinant jets of the FP32 modes for spin blocks of 9 to kDetNRL electrons:
+// the factorisation of the small-block body (det_factor_jets), with a layout of
+// the 3N + 1 tangent products X_t = A^-1 d_t A for larger blocks.  The warp's
+// lanes form G = 32 / n column groups; lane (g, a) keeps row a of Xhi / Xlo in
+// registers, forms the entries (a, k) of d_t A for the columns k of group g and
+// computes X_t[a][k] for the same columns as compensated dot products whose
+// second operand (column k of d_t A) is a shared-memory broadcast.  The Jacobian
+// traces go through an 8-slot ring of per-row diagonals, summed once per 8
+// tangents; sum_t tr(X_t^2) pairs each owned entry with its transpose.
+// ---------------------------------------------------------------------------
+constexpr int kDetNRL = 32;
+
+__host__ __device__ inline size_t det_jets_large_smem_per_warp(int nmax) {
+  const size_t nn = (size_t)nmax * nmax;
+  const size_t bytes = (15 * nn + 17 * (size_t)nmax) * 4 + (size_t)nmax * 4;
+  return (bytes + 15) / 16 * 16;
+}
+
+// Column-chunk width of the tangent products for an n x n block (3 to 8).
+__host__ __device__ inline int det_large_cw(int n) {
+  if (n <= 16) {
+    const int G = 32 / n;
+    return (n + G - 1) / G;
+  }
+  const int nch = (n + 7) / 8;
+  return (n + nch - 1) / nch;
+}
+
+template <int NR, int CW>
+__device__ __forceinline__ void det_tangents_large(const float* __restrict__ phr, const float* env,
+                                                   const float* jenv, const float* lenv, const float* phi0,
+                                                   const float* xh, const float* xl, float* tmp, float* Th,
+                                                   float* Tl, float* DG, int n, int nn, int nmax, int i, int a,
+                                                   int cb, int ce, bool active, int C, int Wo, int N3, int lane,
+                                                   double* out) {
+  dfloat s2 = {0.f, 0.f};
+  float lap_tr = 0.f, lap_lo = 0.f;
+  for (int t = 0; t <= N3; ++t) {
+    const bool is_lap = t == N3;
+    const int c = is_lap ? C - 1 : 1 + t;
+    const int te = t / 3, tx = t - (t / 3) * 3;
+    float* dA = tmp + (t & 1) * nn;
+    for (int k0 = cb; k0 < ce; k0 += CW) {
+#pragma unroll
+      for (int j = 0; j < CW; ++j) {
+        const int k = k0 + j;
+        if (k < ce) {
+          const int q = a * n + k;
+          float v = phr[(int64_t)c * Wo + k] * env[q];
+          if (is_lap) {
+            v += phi0[q] * lenv[q];
+            for (int x = 0; x < 3; ++x) v += 2.f * phr[(int64_t)(1 + 3 * i + x) * Wo + k] * jenv[x * nn + q];
+          } else if (te == i) {
+            v += phi0[q] * jenv[tx * nn + q];
+          }
+          dA[q] = v;
+        }
+      }
+    }
+    __syncwarp();
+    float* th = Th + (t & 1) * nn;
+    float* tl = Tl + (t & 1) * nn;
+    for (int c0 = cb; c0 < ce; c0 += CW) {
+      dfloat acc[CW];
+      float cl[CW];
+#pragma unroll
+      for (int j = 0; j < CW; ++j) {
+        acc[j] = {0.f, 0.f};
+        cl[j] = 0.f;
+      }
+      // columns c0 .. c0 + CW - 1 of d_t A; those past ce (at most the next
+      // row's first entries, inside the warp's buffers) are computed and dropped
+#pragma unroll
+      for (int l = 0; l < NR; ++l) {
+        if (l >= n) break;
+        const float* yr = dA + l * n + c0;
+#pragma unroll
+        for (int j = 0; j < CW; ++j) {
+          const float y = yr[j];
+          acc[j] = dot2_step(acc[j], xh[l], y);
+          cl[j] = fmaf(xl[l], y, cl[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < CW; ++j) {
+        const int m = c0 + j;
+        if (m < ce) {
+          const dfloat x = quick_two_sum(acc[j].hi, __fadd_rn(acc[j].lo, cl[j]));
+          if (m == a) {
+            DG[((t & 7) * nmax + a) * 2] = x.hi;
+            DG[((t & 7) * nmax + a) * 2 + 1] = x.lo;
+          }
+          if (!is_lap) {
+            th[a * n + m] = x.hi;
+            tl[a * n + m] = x.lo;
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (!is_lap && active) {
+      for (int m = cb; m < ce; ++m)
+        s2 = df_add(s2, df_mul({th[a * n + m], tl[a * n + m]}, {th[m * n + a], tl[m * n + a]}));
+    }
+    if ((t & 7) == 7 || is_lap) {
+      // traces of the last (t & 7) + 1 tangents: lane j sums slot j over the rows
+      const int t0 = t - (t & 7);
+      if (lane <= (t & 7)) {
+        dfloat tr = {0.f, 0.f};
+        for (int r = 0; r < n; ++r) tr = df_add(tr, {DG[(lane * nmax + r) * 2], DG[(lane * nmax + r) * 2 + 1]});
+        if (t0 + lane < N3) {
+          out[2 + t0 + lane] = (double)tr.hi + (double)tr.lo;
+        } else {
+          lap_tr = tr.hi;
+          lap_lo = tr.lo;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  const dfloat s2s = warp_sum_df(s2);
+  if (lane == (N3 & 7)) out[2 + N3] = ((double)lap_tr + (double)lap_lo) - ((double)s2s.hi + (double)s2s.lo);
+}
+
+template <int NR>
+__device__ __forceinline__ void orbital_det_jets_large_body(const int64_t bx_, const int64_t nbx_, const float* __restrict__ phi,
+                            const float* __restrict__ geo, const float* __restrict__ params, int64_t Bc, int N,
+                            int n_up, int M, int K, int C, int Wo, int E, int n_ee, int64_t om_up, int64_t om_dn,
+                            int64_t ze_up, int64_t ze_dn, double* __restrict__ det,
+                            unsigned long long* __restrict__ n_fp64, int full) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int warps = blockDim.x / 32;
+  const int64_t gw = (int64_t)bx_ * warps + warp;
+  const int n_dn = N - n_up;
+  const int nmax = full ? N : (n_up > n_dn ? n_up : n_dn);
+  const int N3 = 3 * N;
+  const int nn = nmax * nmax;
+  unsigned char* base = smem_raw + warp * det_jets_large_smem_per_warp(nmax);
+  // persistent: envelope jets and phi values of the block
+  float* env = reinterpret_cast<float*>(base);
+  float* jenv = env + nn;  // [3][nn]
+  float* lenv = jenv + 3 * nn;
+  float* phi0 = lenv + nn;
+  // factorisation (9 nn floats); the tangent buffers tmp[2], Th[2], Tl[2] reuse
+  // the first 6 nn of it once Xhi / Xlo are in registers
+  float* W = phi0 + nn;
+  double* LUd = reinterpret_cast<double*>(W);
+  double* Ainvd = LUd + nn;
+  float* A = W + 4 * nn;
+  float* LU = A + nn;
+  float* X0 = LU + nn;
+  float* Xhi = X0 + nn;
+  float* Xlo = Xhi + nn;
+  float* tmp = W;
+  float* Th = W + 2 * nn;
+  float* Tl = W + 4 * nn;
+  float* DG = W + 9 * nn;  // [8][nmax][2]
+  float* rmax = DG + 16 * nmax;
+  int* perm = reinterpret_cast<int*>(rmax + nmax);
+
+  if (gw >= Bc * 2 * K) return;
+  const int64_t b = gw / (2 * K);
+  const int s = (int)((gw / K) % 2);
+  const int p = (int)(gw % K);
+  int n, i0;
+  det_block(s, N, n_up, full, n, i0);
+  double* out = det + gw * (N3 + 3);
+  if (n == 0) {  // empty determinant = 1
+    for (int k = lane; k < N3 + 3; k += 32) out[k] = k == 0 ? 1.0 : 0.0;
+    return;
+  }
+  const float* phib = phi + b * N * C * Wo;
+  const float* gb = geo + b * E * 4;
+  const int nsq = n * n;
+
+  // Envelopes (Eq. 20) with their derivatives in the coordinates of electron i
+  // (block-local row stride n).
+  for (int q = lane; q < nsq; q += 32) {
+    const int ii = q / n, k = q - (q / n) * n, o = p * n + k, i = i0 + ii;
+    const bool up = i < n_up;
+    const float* om = params + (up ? om_up : om_dn);
+    const float* ze = params + (up ? ze_up : ze_dn);
+    float ev = 0, j0 = 0, j1 = 0, j2 = 0, lv = 0;
+    for (int I = 0; I < M; ++I) {
+      const float* g = gb + (n_ee + i * M + I) * 4;
+      const float z = ze[o * M + I];
+      const float w = om[o * M + I] * expf(-z * g[0]);
+      ev += w;
+      j0 -= w * z * g[1];
+      j1 -= w * z * g[2];
+      j2 -= w * z * g[3];
+      lv += w * (z * z - 2.f * z / g[0]);
+    }
+    env[q] = ev;
+    jenv[q] = j0;
+    jenv[nn + q] = j1;
+    jenv[2 * nn + q] = j2;
+    lenv[q] = lv;
+    const float f0 = phib[(int64_t)i * C * Wo + o];
+    phi0[q] = f0;
+    A[q] = f0 * ev;
+    LU[q] = f0 * ev;
+  }
+  __syncwarp();
+  if (lane < n) {
+    float m = 0;
+    for (int k = 0; k < n; ++k) m = fmaxf(m, fabsf(A[lane * n + k]));
+    rmax[lane] = m;
+  }
+  __syncwarp();
+
+  int sign = 0;
+  double logabs = -INFINITY;
+  // R, T = W[0, 2 nn): the LUd area, used only on the other branch
+  if (!det_factor_jets(A, LU, X0, W, W + nn, Xhi, Xlo, LUd, Ainvd, rmax, perm, n, lane, n_fp64, &sign, &logabs)) {
+    for (int k = lane; k < N3 + 3; k += 32) out[k] = k == 1 ? -INFINITY : 0.0;
+    return;
+  }
+  if (lane == 0) {
+    out[0] = (double)sign;
+    out[1] = logabs;
+  }
+
+  const int G = n <= 16 ? 32 / n : 1;
+  const int g = lane / n, a = lane - (lane / n) * n;
+  const bool active = g < G;
+  const int cw = (n + G - 1) / G;
+  const int cb = active ? g * cw : 0;
+  const int ce = active ? min(n, cb + cw) : 0;
+  float xh[NR], xl[NR];
+#pragma unroll
+  for (int l = 0; l < NR; ++l) {
+    xh[l] = active && l < n ? Xhi[a * n + l] : 0.f;
+    xl[l] = active && l < n ? Xlo[a * n + l] : 0.f;
+  }
+  __syncwarp();  // A, LU and the FP64 area become the tangent buffers
+  const int i = i0 + (active ? a : 0);
+  const float* phr = phib + (int64_t)i * C * Wo + p * n;
+  switch (det_large_cw(n)) {
+    case 3:
+    case 4:
+      det_tangents_large<NR, 4>(phr, env, jenv, lenv, phi0, xh, xl, tmp, Th, Tl, DG, n, nn, nmax, i, a, cb, ce,
+                                active, C, Wo, N3, lane, out);
+      break;
+    case 5:
+    case 6:
+      det_tangents_large<NR, 6>(phr, env, jenv, lenv, phi0, xh, xl, tmp, Th, Tl, DG, n, nn, nmax, i, a, cb, ce,
+                                active, C, Wo, N3, lane, out);
+      break;
+    case 7:
+      det_tangents_large<NR, 7>(phr, env, jenv, lenv, phi0, xh, xl, tmp, Th, Tl, DG, n, nn, nmax, i, a, cb, ce,
+                                active, C, Wo, N3, lane, out);
+      break;
+    default:
+      det_tangents_large<NR, 8>(phr, env, jenv, lenv, phi0, xh, xl, tmp, Th, Tl, DG, n, nn, nmax, i, a, cb, ce,
+                                active, C, Wo, N3, lane, out);
+      break;
+  }
+}
+
+// The large-block jet body over several molecules, NR = 16 (tag 2) or kDetNRL
+// (tag 3); a kernel of its own so that its registers do not lower the occupancy
+// of the small-block body.
+template <int NR>
+__global__ void __launch_bounds__(128) orbital_det_large_group(const __grid_constant__ Grp<orbital_det_kernel_args<float>> g) {
+  int64_t l_;
+  const int m_ = grp_find(g, blockIdx.x, l_);
+  const orbital_det_kernel_args<float>& a_ = g.a[m_];
+  orbital_det_jets_large_body<NR>(l_, g.nbx[m_], a_.phi, a_.geo, a_.params, a_.Bc, a_.N, a_.n_up, a_.M, a_.K, a_.C,
+                                  a_.Wo, a_.E, a_.n_ee, a_.om_up, a_.om_dn, a_.ze_up, a_.ze_dn, a_.det, a_.n_fp64,
+                                  a_.full);
+}
+
 // Determinants of several molecules in one launch (FP32 modes): tag 1 runs the
 // FP32 jet kernel body (spin blocks of at most kDetNR electrons), tag 0 the
-// general body (value-only calls, larger spin blocks).  Both use four warps per
-// CTA, one matrix per warp.
+// general body (value-only calls, blocks too large for the jet bodies).  Both
+// use four warps per CTA, one matrix per warp.
 __global__ void __launch_bounds__(128) orbital_det_mixed_group(const __grid_constant__ Grp<orbital_det_kernel_args<float>> g) {
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
   const orbital_det_kernel_args<float>& a_ = g.a[m_];
-  if (g.tag[m_])
+  const int tag = g.tag[m_];
+  if (tag == 1)
     orbital_det_jets_kernel_body(l_, 0, g.nbx[m_], a_.phi, a_.geo, a_.params, a_.Bc, a_.N, a_.n_up, a_.M, a_.K, a_.C,
                                  a_.Wo, a_.E, a_.n_ee, a_.om_up, a_.om_dn, a_.ze_up, a_.ze_dn, a_.det, a_.n_fp64,
                                  a_.full);
@@ -1950,8 +2270,8 @@ cudaError_t launch_messages(const dq_handle_s& h, const FwdDims& d, const T* par
 
 template <class T>
 cudaError_t launch_update(const dq_handle_s& h, const FwdDims& d, const T* params, bool from_spin, FwdBuffers<T> b,
-                          cudaStream_t s, const T* un) {
-  const MolFwd<T> m{&h, d, params, b, un};
+                          cudaStream_t s) {
+  const MolFwd<T> m{&h, d, params, b};
   return launch_update_group<T>(&m, 1, from_spin, s);
 }
 
@@ -1969,15 +2289,35 @@ cudaError_t launch_to_bf16(const float* src, void* dst, int64_t n, cudaStream_t 
   return cudaGetLastError();
 }
 
+// Which determinant body runs a molecule's matrices (the group kernel's tag) and
+// its dynamic shared memory for four warps: 1 the small-block FP32 jet body,
+// 2 / 3 the large-block FP32 jet body, 0 the general body.
+template <class T>
+int det_body_tag(int nmax, int N, int C, size_t* smem4) {
+  const int nn = nmax * nmax;
+  if (sizeof(T) == 4 && C > 1) {
+    if (nmax <= kDetNR) {
+      *smem4 = det_jets_smem_per_warp(nmax, 3 * N) * 4;
+      return 1;
+    }
+    if (nmax <= kDetNRL && det_jets_large_smem_per_warp(nmax) * 4 <= 200 * 1024) {
+      *smem4 = det_jets_large_smem_per_warp(nmax) * 4;
+      return nmax <= 16 ? 2 : 3;
+    }
+  }
+  *smem4 = ((size_t)nn * (3 * sizeof(double) + 10 * sizeof(T)) + 32 * sizeof(int) + 15) / 16 * 16 * 4;
+  return 0;
+}
+
 template <class T>
 cudaError_t launch_orbital_det(const dq_handle_s& h, const FwdDims& d, const T* params, FwdBuffers<T> b,
                                cudaStream_t s) {
   const int nmax = h.det_n();
   const int nn = nmax * nmax;
   {
-    const size_t pw = ((size_t)nn * (3 * sizeof(double) + 10 * sizeof(T)) + 32 * sizeof(int) + 15) / 16 * 16;
-    const bool jets = sizeof(T) == 4 && d.C > 1 && nmax <= kDetNR;
-    if (jets || pw * 4 <= 200 * 1024) {
+    size_t sm4 = 0;
+    const int tag = det_body_tag<T>(nmax, d.N, d.C, &sm4);
+    if (tag != 0 || sm4 <= 200 * 1024) {
       const MolFwd<T> m{&h, d, params, b};
       return launch_orbital_det_group<T>(&m, 1, s);
     }
@@ -2276,7 +2616,7 @@ cudaError_t launch_update_group(const MolFwd<T>* m, int n, bool from_spin, cudaS
     const FwdDims& d = m[k].d;
     if (d.Bc <= 0) continue;
     g.add({m[k].b.Z, m[k].b.F, m[k].b.F, m[k].params + std::max<int64_t>(m[k].h->off.E_spin, 0), d.Bc, d.N, d.n_up, d.C, d.D,
-           from_spin && !m[k].h->el_init ? 1 : 0, static_cast<__nv_bfloat16*>(m[k].b.F_bf), m[k].un},
+           from_spin && !m[k].h->el_init ? 1 : 0, static_cast<__nv_bfloat16*>(m[k].b.F_bf)},
           blocks(d.Bc * d.N * d.D, 256));
   }
   if (g.n == 0) return cudaSuccess;
@@ -2303,32 +2643,35 @@ cudaError_t launch_orbital_det_group(const MolFwd<T>* m, int n, cudaStream_t s) 
     const FwdDims& d = m[k].d;
     if (d.Bc <= 0) continue;
     const int nmax = h.det_n();
-    const int nn = nmax * nmax;
     const int64_t nmat = d.Bc * 2 * d.K;
-    const bool jets = sizeof(T) == 4 && d.C > 1 && nmax <= kDetNR;
     size_t sm = 0;
-    if (jets) {
-      sm = det_jets_smem_per_warp(nmax, 3 * d.N) * 4;
-    } else {
-      const size_t per_warp = ((size_t)nn * (3 * sizeof(double) + 10 * sizeof(T)) + 32 * sizeof(int) + 15) / 16 * 16;
-      if (per_warp * 4 > 200 * 1024) return cudaErrorInvalidConfiguration;  // grouped form: four warps per CTA
-      sm = per_warp * 4;
-    }
+    const int tag = det_body_tag<T>(nmax, d.N, d.C, &sm);
+    if (tag == 0 && sm > 200 * 1024) return cudaErrorInvalidConfiguration;  // grouped form: four warps per CTA
     smem = std::max(smem, sm);
     ent[ne++] = Ent{{m[k].b.phi, m[k].b.geo, m[k].params, d.Bc, d.N, d.n_up, d.M, d.K, d.C, d.K * nmax,
                      h.edges.n_all, h.edges.n_ee, h.off.omega[0], h.off.omega[1], h.off.zeta[0], h.off.zeta[1],
                      m[k].b.det, h.d_fp64_count, h.full_det},
-                    blocks(nmat, 4), jets ? 1 : 0, 0, sm};
+                    blocks(nmat, 4), tag, 0, sm};
   }
   if (ne == 0) return cudaSuccess;
-  const void* kern = nullptr;
-  if constexpr (sizeof(T) == 4) kern = (const void*)orbital_det_mixed_group;
-  else kern = (const void*)orbital_det_kernel_group<T>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  // one launch per occupancy class (see launch_messages_group)
+  // kernel of each body: 0 the mixed / general group kernel, 1 and 2 the large-block ones
+  auto kind = [](int tag) { return tag == 2 ? 1 : tag == 3 ? 2 : 0; };
+  const void* kerns[3] = {nullptr, nullptr, nullptr};
+  if constexpr (sizeof(T) == 4) {
+    kerns[0] = (const void*)orbital_det_mixed_group;
+    kerns[1] = (const void*)orbital_det_large_group<16>;
+    kerns[2] = (const void*)orbital_det_large_group<kDetNRL>;
+  } else {
+    kerns[0] = (const void*)orbital_det_kernel_group<T>;
+  }
+  cudaError_t e = cudaSuccess;
   for (int i = 0; i < ne; ++i) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ent[i].occ, kern, 128, ent[i].smem);
+    e = cudaFuncSetAttribute(kerns[kind(ent[i].tag)], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  // one launch per kernel and occupancy class (see launch_messages_group)
+  for (int i = 0; i < ne; ++i) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ent[i].occ, kerns[kind(ent[i].tag)], 128, ent[i].smem);
     if (e != cudaSuccess) return e;
   }
   bool done[kMaxGroup] = {};
@@ -2336,16 +2679,22 @@ cudaError_t launch_orbital_det_group(const MolFwd<T>* m, int n, cudaStream_t s) 
     if (done[i]) continue;
     Grp<orbital_det_kernel_args<T>> g{};
     size_t sm = 0;
+    const int k = kind(ent[i].tag);
     for (int j = i; j < ne; ++j)
-      if (!done[j] && ent[j].occ == ent[i].occ) {
+      if (!done[j] && ent[j].occ == ent[i].occ && kind(ent[j].tag) == k) {
         g.add(ent[j].a, ent[j].bx, 1, ent[j].tag);
         sm = std::max(sm, ent[j].smem);
         done[j] = true;
       }
     e = check_group(g);
     if (e != cudaSuccess) return e;
-    if constexpr (sizeof(T) == 4) orbital_det_mixed_group<<<(unsigned)g.blocks(), 128, sm, s>>>(g);
-    else orbital_det_kernel_group<T><<<(unsigned)g.blocks(), 128, sm, s>>>(g);
+    if constexpr (sizeof(T) == 4) {
+      if (k == 1) orbital_det_large_group<16><<<(unsigned)g.blocks(), 128, sm, s>>>(g);
+      else if (k == 2) orbital_det_large_group<kDetNRL><<<(unsigned)g.blocks(), 128, sm, s>>>(g);
+      else orbital_det_mixed_group<<<(unsigned)g.blocks(), 128, sm, s>>>(g);
+    } else {
+      orbital_det_kernel_group<T><<<(unsigned)g.blocks(), 128, sm, s>>>(g);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -2421,7 +2770,7 @@ DQ_INSTANTIATE_GROUP(double)
   template cudaError_t launch_messages<T>(const dq_handle_s&, const FwdDims&, const T*, int, bool, FwdBuffers<T>, \
                                           cudaStream_t);                                                          \
   template cudaError_t launch_update<T>(const dq_handle_s&, const FwdDims&, const T*, bool, FwdBuffers<T>,        \
-                                        cudaStream_t, const T*);                                                  \
+                                        cudaStream_t);                                                            \
   template cudaError_t launch_update_io<T>(const dq_handle_s&, const FwdDims&, const T*, bool, const T*, const T*, \
                                            T*, cudaStream_t, void*);                                              \
   template cudaError_t launch_orbital_det<T>(const dq_handle_s&, const FwdDims&, const T*, FwdBuffers<T>,         \

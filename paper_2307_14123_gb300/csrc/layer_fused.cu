@@ -541,6 +541,19 @@ __global__ void value_channel_kernel(const float* __restrict__ Z, int64_t BN, in
   zv[e] = Z[(e / LF_D) * C * LF_D + (e % LF_D)];
 }
 
+// U[b][i][c][:] += un[b][i][slot][:] on the channels where the electron-nucleus messages are
+// non-zero: slot 0 the value channel (b_g included), 1..3 the receiver's own coordinates, 4 the
+// Laplacian.  One block per (walker, receiver), a thread per feature.
+__global__ void add_nucleus_part_kernel(const float* __restrict__ un, int N, int C, float* __restrict__ U) {
+  const int64_t bi = blockIdx.x;
+  const int i = (int)(bi % N), d = threadIdx.x;
+  const float* src = un + bi * 5 * LF_D + d;
+  float* dst = U + bi * C * LF_D + d;
+  const int ch[5] = {0, 1 + 3 * i, 2 + 3 * i, 3 + 3 * i, C - 1};
+#pragma unroll
+  for (int k = 0; k < 5; ++k) dst[(int64_t)ch[k] * LF_D] += src[(int64_t)k * LF_D];
+}
+
 bool map_w(CUtensorMap* m, const float* W, int D) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
@@ -630,6 +643,9 @@ cudaError_t launch_layer_fused(const dq_handle_s& h, const FwdDims& d, const flo
   const int64_t grid = d.Bc < sms ? d.Bc : sms;
   kern<<<(unsigned)grid, lf_threads(nb <= 2 ? 2 : nb <= 4 ? 4 : nb <= 5 ? 5 : nb <= 7 ? 7 : 8), LF_SMEM, s>>>(
       a, mhi, mlo, mz, h.d_status);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  add_nucleus_part_kernel<<<(unsigned)(d.Bc * d.N), LF_D, 0, s>>>(un, d.N, d.C, Z);
   return cudaGetLastError();
 }
 
