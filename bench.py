@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--profile-case", type=int, default=0, metavar="B",
                    help="run one call on B walkers of the workload and exit (small case for ncu)")
     p.add_argument("--profile-op", default="local_energy", choices=["local_energy", "grad", "mcmc"])
+    p.add_argument("--profile-precision", default=None, choices=["fp64", "fp32", "bf16"],
+                   help="precision of the profile case (default: the workload's)")
     p.add_argument("--msg-ib", type=int, default=0, choices=[0, 4, 8],
                    help="profile case: receivers per warp task of the jet message kernel (0: library default)")
     return p.parse_args()
@@ -429,8 +431,9 @@ def profile_case(args):
     from paper_2307_14123_gb300 import fixtures as fx
 
     wl = fx.workload(args.workload)
-    dt = torch.float64 if wl.precision == "fp64" else torch.float32
-    h = Ansatz(wl.system, wl.cfg, wl.precision, device="cuda:0")
+    prec = args.profile_precision or wl.precision
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    h = Ansatz(wl.system, wl.cfg, prec, device="cuda:0")
     theta = torch.tensor(fx.init_params(wl.system, wl.cfg, wl.param_seed), dtype=dt, device="cuda:0")
     r = torch.tensor(fx.init_walkers(wl.system, args.profile_case, wl.walker_seed), dtype=dt, device="cuda:0")
     if args.msg_ib:
@@ -584,6 +587,71 @@ def ansatz_variants_leg(h, theta, r, wl, flush, reps=5):
         del hv
     out["note"] = (f"{wl.system.name} {wl.precision.upper()}, {B} walkers, local_energy calls, L2 flushed "
                    "before each; full determinant: one N x N matrix per p instead of two spin blocks")
+    return out
+
+
+def bf16_leg(h, theta, r, wl, flush, reps=5):
+    """BF16 mode against FP32: local_energy on the bench walkers in both modes (same timing as the
+    base), with the paired change of the mean local energy; and the paired BF16 - FP32 mean shift on
+    a trained low-variance state (LiH, width 64, two layers, one determinant: 200 natural-gradient
+    steps in FP32 from random initialisation, 65,536 walkers after 200 Metropolis sweeps)."""
+    import numpy as np
+    import torch
+
+    from paper_2307_14123_gb300 import Ansatz, vmc_train_step
+    from paper_2307_14123_gb300 import fixtures as fx
+
+    dev = r.device
+    out = {}
+
+    def timed(hh):
+        res = hh.local_energy(theta, r)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(reps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            hh.local_energy(theta, r)
+            b.record()
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / reps, res[2].double()
+
+    h32 = Ansatz(wl.system, wl.cfg, "fp32", device=dev)
+    h16 = Ansatz(wl.system, wl.cfg, "bf16", device=dev)
+    ms32, e32 = timed(h32)
+    ms16, e16 = timed(h16)
+    d = (e16 - e32)[torch.isfinite(e16 - e32)]
+    B = r.shape[0]
+    out["bench_walkers"] = {"fp32_ms_per_call": ms32, "bf16_ms_per_call": ms16, "bf16_speedup": ms32 / ms16,
+                            "fp32_value": B / (ms32 / 1e3), "bf16_value": B / (ms16 / 1e3), "unit": UNIT,
+                            "mean_dE_bf16_minus_fp32": float(d.mean()),
+                            "stderr": float(d.std() / max(1, d.numel()) ** 0.5),
+                            "note": "random-initialised ansatz; FP32 runs the fused layer kernel, BF16 the "
+                                    "message kernel and BF16 update / node GEMMs"}
+    del h32, h16
+    system = fx.molecule("LiH")
+    cfg = fx.AnsatzCfg(64, 2, 1)
+    t32 = Ansatz(system, cfg, "fp32", device=dev)
+    t16 = Ansatz(system, cfg, "bf16", device=dev)
+    th = torch.tensor(fx.init_params(system, cfg, 3), dtype=torch.float32, device=dev)
+    rt = torch.tensor(fx.init_walkers(system, 1024, 3), dtype=torch.float32, device=dev)
+    la, _ = t32.ansatz_eval(th, rt)
+    t32.mcmc_step(th, rt, la, 50, 0.2, 9, 0)
+    for t in range(200):
+        vmc_train_step(t32, th, rt, la, lr=0.2, damping=-0.1, max_norm=0.3, seed=1, step_counter=50 + t)
+    Bt = 65536
+    rr = torch.tensor(fx.init_walkers(system, Bt, 21), dtype=torch.float32, device=dev)
+    la2, _ = t32.ansatz_eval(th, rr)
+    t32.mcmc_step(th, rr, la2, 200, 0.2, 21, 0)
+    a32 = t32.local_energy(th, rr)[2].double().cpu().numpy()
+    a16 = t16.local_energy(th, rr)[2].double().cpu().numpy()
+    dd = a16 - a32
+    out["trained_lih"] = {"walkers": Bt, "mean_e_loc_fp32": float(a32.mean()), "variance_fp32": float(a32.var()),
+                          "mean_dE_bf16_minus_fp32": float(dd.mean()), "stderr": float(dd.std() / np.sqrt(Bt)),
+                          "variance_change_rel": float(a16.var() / a32.var() - 1),
+                          "median_abs_dE": float(np.median(np.abs(dd)))}
     return out
 
 
@@ -773,6 +841,7 @@ def main():
     for _ in range(args.warmup):
         step(theta, r, logabs)
     torch.cuda.synchronize()
+    h.fp64_matrix_count()  # cleared: the timed steps' count is read after them
 
     h.profile(True)
     h.profile_reset()
@@ -794,6 +863,12 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     h.profile(False)
+    n_fp64 = h.fp64_matrix_count()
+    n_mat_step = 2 * B * wl.cfg.n_det * 2  # the sampler's value-only forward and the jets forward
+    fp64_dets = {"per_step": n_fp64 / args.steps, "matrices_per_step": n_mat_step,
+                 "fraction": n_fp64 / args.steps / n_mat_step,
+                 "note": "determinant matrices factorised in FP64 (ill-conditioned ones) by the timed steps, "
+                         "both forwards of a step"}
     total_ms = sum(a.elapsed_time(b) for a, b in evs)
     prof = h.profile_read()
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
@@ -978,6 +1053,7 @@ def main():
     training = training_leg(dev) if (world == 1 and not args.no_natgrad) else None
     pseudo = pp_leg(h, theta, r, wl, flush) if (world == 1 and not args.no_pp) else None
     variants = ansatz_variants_leg(h, theta, r, wl, flush) if (world == 1 and not args.no_pp) else None
+    bf16 = bf16_leg(h, theta, r, wl, flush) if (world == 1 and not args.no_pp and wl.precision == "fp32") else None
 
     cpu = parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1002,6 +1078,8 @@ def main():
                 "vmc_training": training,
                 "pseudopotential": pseudo,
                 "ansatz_variants": variants,
+                "bf16_mode": bf16,
+                "fp64_determinants": fp64_dets,
                 "gpu_launches": launches,
                 "gpu_kernels_per_step": kernels_per_step,
                 "gpu_launch_sites": launch_sites,

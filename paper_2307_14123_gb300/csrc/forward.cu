@@ -1579,21 +1579,39 @@ __device__ __forceinline__ void orbital_det_jets_kernel_body(const int64_t bx_, 
     }
   }
   dfloat s2 = {0.f, 0.f};
+  // the lane's entries of d_t A read one tangent ahead (the load of t + 1 overlaps the products
+  // of t); the derivatives in the row's own electron are kept for the Laplacian
+  const float* phq[2];
+  float pre[2], dself[2][3];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    phq[r] = phib + (int64_t)(i0 + ra[r]) * C * Wo + p * n + ma[r];
+    pre[r] = qa[r] >= 0 ? phq[r][(int64_t)1 * Wo] : 0.f;
+    dself[r][0] = dself[r][1] = dself[r][2] = 0.f;
+  }
   for (int t = 0; t <= N3; ++t) {
     const bool is_lap = t == N3;
-    const int c = is_lap ? C - 1 : 1 + t;
     const int te = t / 3, tx = t - (t / 3) * 3;
+    float cur[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      cur[r] = pre[r];
+      if (qa[r] >= 0 && t < N3) pre[r] = phq[r][(int64_t)(t + 1 == N3 ? C - 1 : 2 + t) * Wo];
+    }
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       if (qa[r] < 0) continue;
-      const int q = qa[r], ii = ra[r], k = ma[r], i = i0 + ii, o = p * n + k;
-      const float* ph = phib + (int64_t)i * C * Wo + o;
-      float v = ph[(int64_t)c * Wo] * env[q];
+      const int q = qa[r], i = i0 + ra[r];
+      float v = cur[r] * env[q];
       if (is_lap) {
         v += phi0[q] * lenv[q];
-        for (int x = 0; x < 3; ++x) v += 2.f * ph[(int64_t)(1 + 3 * i + x) * Wo] * jenv[x * nn + q];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) v += 2.f * dself[r][x] * jenv[x * nn + q];
       } else if (te == i) {
         v += phi0[q] * jenv[tx * nn + q];
+        dself[r][0] = tx == 0 ? cur[r] : dself[r][0];
+        dself[r][1] = tx == 1 ? cur[r] : dself[r][1];
+        dself[r][2] = tx == 2 ? cur[r] : dself[r][2];
       }
       tmp[q] = v;
     }
@@ -1686,18 +1704,30 @@ __device__ __forceinline__ void det_tangents_large(const float* __restrict__ phr
                                                    double* out) {
   dfloat s2 = {0.f, 0.f};
   float lap_tr = 0.f, lap_lo = 0.f;
+  // blocks of at most 16 (one column chunk per lane): the lane's entries of d_t A are read one
+  // tangent ahead, so that the loads of t + 1 overlap the products of t
+  constexpr bool kAhead = NR <= 16;
+  float pre[CW];
+#pragma unroll
+  for (int j = 0; j < CW; ++j) pre[j] = kAhead && cb + j < ce ? phr[(int64_t)1 * Wo + cb + j] : 0.f;
   for (int t = 0; t <= N3; ++t) {
     const bool is_lap = t == N3;
     const int c = is_lap ? C - 1 : 1 + t;
     const int te = t / 3, tx = t - (t / 3) * 3;
     float* dA = tmp + (t & 1) * nn;
+    float cur[CW];
+#pragma unroll
+    for (int j = 0; j < CW; ++j) {
+      cur[j] = pre[j];
+      if (kAhead && t < N3 && cb + j < ce) pre[j] = phr[(int64_t)(t + 1 == N3 ? C - 1 : 2 + t) * Wo + cb + j];
+    }
     for (int k0 = cb; k0 < ce; k0 += CW) {
 #pragma unroll
       for (int j = 0; j < CW; ++j) {
         const int k = k0 + j;
         if (k < ce) {
           const int q = a * n + k;
-          float v = phr[(int64_t)c * Wo + k] * env[q];
+          float v = (kAhead ? cur[j] : phr[(int64_t)c * Wo + k]) * env[q];
           if (is_lap) {
             v += phi0[q] * lenv[q];
             for (int x = 0; x < 3; ++x) v += 2.f * phr[(int64_t)(1 + 3 * i + x) * Wo + k] * jenv[x * nn + q];

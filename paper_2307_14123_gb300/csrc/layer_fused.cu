@@ -17,14 +17,16 @@
 // and 32-feature block, A[row][32] = m_i^t[c][32 features] as three TF32
 // products with the W_g block (hi hi + hi lo + lo hi).
 //
-// Warp roles (704 threads, one CTA per SM, persistent over walkers):
+// Warp roles (16 warps, one CTA per SM, persistent over walkers):
 //   warp 0      TMA: W_g hi/lo blocks and the z slab z_j[c0 .. c0 + G)[32]
 //               of all senders into a 2-stage ring;
 //   warp 1      MMA issue (tcgen05.mma kind::tf32, 128 x 128 x 8) into one
 //               of two tensor-memory accumulators;
-//   warps 2-5   epilogue: tensor memory -> tanh jet update of f;
-//   warps 6-21  message producers: warp 6 + i owns receiver i and writes its
-//               rows of the A block (TF32 high and low parts, 128-byte
+//   warps 2-3   idle;
+//   warps 4-7   epilogue: tensor memory -> the pre-activations U in global memory;
+//   warps 8-15  message producers: warp 8 + w owns two receivers of one spin
+//               block (a half-warp each, two features per lane) and writes
+//               their rows of the A block (TF32 high and low parts, 128-byte
 //               swizzle) from the z slab and the filter jets, prefetching the
 //               next K step's filter lines into L2.
 // Every mbarrier wait is bounded (about one second); a timeout sets
@@ -47,9 +49,13 @@ constexpr int LF_D = 128;                  // embedding width (the MMA's N)
 constexpr int LF_NFB = LF_D / LF_BK;       // feature blocks per edge type
 constexpr int LF_KSTEPS = 2 * LF_NFB;      // K = 2 D: the electron-electron blocks of W_g
 constexpr int LF_STAGES = 2;
+constexpr int LF_UG = 2;                   // node channels per producer group
 constexpr int LF_PROD = 16;                // producer warps at most (one per receiver)
 // threads of the kernel for NB sender slots per spin block: 2 NB producer warps
-constexpr int lf_threads(int nb) { return 32 * (6 + 2 * nb); }
+// 16 warps in four warpgroups: TMA and MMA issue (and two idle warps), epilogue, and two
+// warpgroups of producers (one warp per receiver pair).
+constexpr int LF_THREADS = 512;
+constexpr int LF_PROD_WARPS = 8;
 constexpr int LF_MAX_N = 16;               // electrons (receivers per tile >= 8)
 constexpr int LF_MAX_BLK = 8;              // electrons per spin block
 constexpr int LF_MAX_M = 8;                // nuclei
@@ -62,10 +68,11 @@ constexpr uint32_t LF_TMEM_ALLOC = 256;        // two 128-column accumulators
 constexpr uint32_t LF_OFF_Z = LF_STAGES * LF_STAGE;                                // [2][N][G][32] z slabs
 constexpr uint32_t LF_OFF_ACCL = LF_OFF_Z + LF_ZBUF * LF_TILE;                      // [N][2][D] Laplacian cross terms
 constexpr uint32_t LF_OFF_ST = LF_OFF_ACCL + LF_MAX_N * 2 * LF_D * 4;              // [4][32][33] transposes
-constexpr uint32_t LF_OFF_GEO = LF_OFF_ST + 4 * 32 * 33 * 4;                       // per producer warp tables
+constexpr uint32_t LF_OFF_GEO = LF_OFF_ST + 4 * 32 * 33 * 4;                       // per receiver tables
 constexpr uint32_t LF_GEO_WARP = (LF_MAX_BLK * 2 + LF_MAX_M) * 8 * 4;              // rows x 8 floats
 constexpr uint32_t LF_OFF_BAR = LF_OFF_GEO + LF_PROD * LF_GEO_WARP;
 constexpr uint32_t LF_SMEM = 1024 + LF_OFF_BAR + 20 * 8 + 16;
+static_assert(LF_SMEM <= 232448, "dynamic shared memory above the per-block limit");
 
 struct LayerFusedArgs {
   const float* Z;       // [Bc][N][C][D] node map z_j (not read when z_const)
@@ -79,6 +86,7 @@ struct LayerFusedArgs {
   int64_t Bc;
   int N, n_up, M, C, E, n_ee, G, n_tiles;
   int z_const;
+  int n_prod;  // producer warps (receiver pairs), at most LF_PROD_WARPS
 };
 
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
@@ -96,21 +104,9 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
   }
 }
 
-// Byte offset of element (row, k) of a 128 x 32 FP32 block in the 128-byte swizzle layout.
-__device__ __forceinline__ uint32_t sw_off(int row, int k) {
-  return (uint32_t)(row * 128 + ((((k >> 2) ^ (row & 7))) << 4) + ((k & 3) << 2));
-}
-
-__device__ __forceinline__ void put_a(uint8_t* a_hi, uint8_t* a_lo, int row, int k, float m) {
-  const float h = tf32_rn(m);
-  const uint32_t o = sw_off(row, k);
-  *reinterpret_cast<float*>(a_hi + o) = h;
-  *reinterpret_cast<float*>(a_lo + o) = tf32_rn(m - h);
-}
-
 // NB: sender slots per spin block (at least the larger block's electron count).
-template <int NB>
-__global__ void __launch_bounds__(lf_threads(NB), 1)
+template <int NB, bool ZC>
+__global__ void __launch_bounds__(LF_THREADS, 1)
     layer_fused_kernel(const __grid_constant__ LayerFusedArgs a, const __grid_constant__ CUtensorMap map_whi,
                        const __grid_constant__ CUtensorMap map_wlo, const __grid_constant__ CUtensorMap map_z,
                        unsigned int* __restrict__ status) {
@@ -131,11 +127,12 @@ __global__ void __launch_bounds__(lf_threads(NB), 1)
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int N = a.N, C = a.C, G = a.G, n_tiles = a.n_tiles;
   const uint32_t zbytes = (uint32_t)(LF_BK * G * N * 4);
+  const int n_prod = a.n_prod;  // producer warps: one per receiver pair
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < LF_STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&conv[s], 2 * NB);  // one arrival per producer warp
+      mbar_init(&conv[s], n_prod);  // one arrival per producer warp
       mbar_init(&empty[s], 1);
     }
     for (int q = 0; q < 2; ++q) {
@@ -144,7 +141,7 @@ __global__ void __launch_bounds__(lf_threads(NB), 1)
     }
     for (int q = 0; q < LF_ZBUF; ++q) {
       mbar_init(&zfull[q], 1);
-      mbar_init(&zempty[q], 2 * NB);  // released by every producer warp after its last use
+      mbar_init(&zempty[q], n_prod);  // released by every producer warp after its last use
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
@@ -237,77 +234,67 @@ __global__ void __launch_bounds__(lf_threads(NB), 1)
       }
       if (!ok) s_abort = 1;
     }
-  } else if (warp >= 6) {
-    // ---- message producers: warp 6 + i owns receiver i ----
-    const int i = warp - 6;
+  } else if (warp >= 8) {
+    if (warp - 8 >= n_prod) goto done;  // no receiver pair for this warp
+    // ---- message producers: warp 8 + w owns receiver pair w (two receivers of one spin block);
+    // lane (h, fp) = (lane / 16, lane % 16) computes features f0 + 2 fp and f0 + 2 fp + 1 of
+    // receiver i_h.  The last pair of an odd block repeats its receiver in the second half,
+    // which computes but never writes. ----
+    const int w = warp - 8;
+    const int h = lane >> 4, fp = lane & 15;
     const int n_up = a.n_up, M = a.M, E = a.E, n_ee = a.n_ee;
-    // geometry of the receiver, once per walker: per sender slot k of the same spin block (k < 8),
+    const int pairs_up = (n_up + 1) >> 1;
+    int i = w < pairs_up ? 2 * w + h : n_up + 2 * (w - pairs_up) + h;
+    const bool writer = w < pairs_up ? i < n_up : i < N;
+    if (!writer) i -= 1;
+    const bool up = i < n_up;
+    // geometry of receiver i, once per walker: per sender slot k of the same spin block (k < 8),
     // of the other block (8 <= k < 16) and per nucleus (16 <= k): the edge index (as float bits),
     // the unit vector u_ij and 1 / d_ij
-    float* gt = reinterpret_cast<float*>(smem + LF_OFF_GEO + (i < LF_PROD ? i : 0) * LF_GEO_WARP);
+    float* gt = reinterpret_cast<float*>(smem + LF_OFF_GEO + i * LF_GEO_WARP);
     constexpr int kRows = LF_MAX_BLK * 2 + LF_MAX_M;
-    const bool up = i < n_up;
     int64_t g_ks = 0, zi = 0;
     bool ok = true;
-    // the filter-jet lines of K step (t, f0): lane k < 8 sender slot k's value, lane 8 + k its
-    // first derivative, lane 16 + k its second derivative (nucleus type: slot = nucleus)
+    // the filter-jet lines of K step (t, f0) into L2: lane fp < 8 sender slot fp's value,
+    // 8 <= fp its first derivative
     auto prefetch_filters = [&](const float* ew_b, int t, int f0) {
-      if (i >= N) return;
-      const int k = lane % 8, jet = lane / 8;
-      if (jet > 2) return;
-      const int row = t == 2 ? 2 * LF_MAX_BLK + k : (t == 0 ? 0 : LF_MAX_BLK) + k;
+      const int k = fp & 7, jet = fp >> 3;
+      const int row = (t == 0 ? 0 : LF_MAX_BLK) + k;
       const int edge = __float_as_int(gt[row * 8]);
       if (edge >= 0)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(ew_b + ((int64_t)edge * 3 + jet) * LF_D + f0));
     };
-    float nw[NB], nw1[NB], nz0[NB];  // the electron-electron step's loads
     for (int64_t b = blockIdx.x; b < a.Bc && ok; b += gridDim.x) {
       const float* geo_b = a.geo + b * E * 4;
       const float* ew_b = a.ew + b * (int64_t)E * 3 * LF_D;
       const float* zv_b = a.zv + b * (int64_t)N * LF_D;
-      // loads of the electron-electron step (t, f0) of a tile starting at channel c0: the filter
-      // jets w, w' of every sender slot (invalid slots read slot 0's edge; masked when used) and,
-      // past tile 0, the senders' z_j[0]
-      auto issue_ee = [&](int t, int f0, int c0) {
-        const bool same = t == 0;
-        const int j0 = (up == same) ? 0 : n_up;
-        const float* gs = gt + (same ? 0 : LF_MAX_BLK) * 8;
-#pragma unroll
-        for (int k = 0; k < NB; ++k) {
-          const int edge = __float_as_int(gs[k * 8]);
-          const float* w = ew_b + (int64_t)(edge >= 0 ? edge : 0) * 3 * LF_D + f0 + lane;
-          nw[k] = __ldg(w);
-          nw1[k] = __ldg(w + LF_D);
-          const int j = min(j0 + k, N - 1);
-          nz0[k] = (a.z_const || c0 == 0) ? 0.f : __ldg(zv_b + (int64_t)j * LF_D + f0 + lane);
-        }
-      };
-      if (lane < kRows && i < N) {
-        const int k = lane;
-        float* row = gt + k * 8;
-        int edge = -1;
-        float sg = 1.f;
-        if (k < 2 * LF_MAX_BLK) {
-          const bool same = k < LF_MAX_BLK;
-          const int j0 = (up == same) ? 0 : n_up, j1 = (up == same) ? n_up : N;
-          const int j = j0 + (k % LF_MAX_BLK);
-          if (j < j1 && j != i) {
-            edge = a.pair_of[i * N + j];
-            sg = i < j ? 1.f : -1.f;
+      if (writer) {
+        for (int k = fp; k < kRows; k += 16) {
+          float* row = gt + k * 8;
+          int edge = -1;
+          float sg = 1.f;
+          if (k < 2 * LF_MAX_BLK) {
+            const bool same = k < LF_MAX_BLK;
+            const int j0 = (up == same) ? 0 : n_up, j1 = (up == same) ? n_up : N;
+            const int j = j0 + (k % LF_MAX_BLK);
+            if (j < j1 && j != i) {
+              edge = a.pair_of[i * N + j];
+              sg = i < j ? 1.f : -1.f;
+            }
+          } else if (k - 2 * LF_MAX_BLK < M) {
+            edge = n_ee + i * M + (k - 2 * LF_MAX_BLK);
           }
-        } else if (k - 2 * LF_MAX_BLK < M) {
-          edge = n_ee + i * M + (k - 2 * LF_MAX_BLK);
-        }
-        if (edge >= 0) {
-          const float* gg = geo_b + (int64_t)edge * 4;
-          row[0] = __int_as_float(edge);
-          row[1] = sg * gg[1];
-          row[2] = sg * gg[2];
-          row[3] = sg * gg[3];
-          row[4] = 1.f / gg[0];
-        } else {
-          row[0] = __int_as_float(-1);
-          row[1] = row[2] = row[3] = row[4] = 0.f;
+          if (edge >= 0) {
+            const float* gg = geo_b + (int64_t)edge * 4;
+            row[0] = __int_as_float(edge);
+            row[1] = sg * gg[1];
+            row[2] = sg * gg[2];
+            row[3] = sg * gg[3];
+            row[4] = 1.f / gg[0];
+          } else {
+            row[0] = __int_as_float(-1);
+            row[1] = row[2] = row[3] = row[4] = 0.f;
+          }
         }
       }
       __syncwarp();
@@ -315,135 +302,224 @@ __global__ void __launch_bounds__(lf_threads(NB), 1)
       for (int g = 0; g < n_tiles && ok; ++g) {
         const int c0 = g * G;
         const int c1 = min(C, c0 + G);
-        const bool last = c1 == C;
         for (int ks = 0; ks < LF_KSTEPS; ++ks, ++g_ks) {
           const int s = (int)(g_ks % LF_STAGES);
+          const int fb = ks / 2, t = ks % 2;
+          const int f0 = fb * LF_BK;
+          const int fl = f0 + 2 * fp;  // this lane's first feature
+          // electron-electron messages of type t: senders j = j0 + k, k < NB
+          const bool same = t == 0;
+          const int j0 = (up == same) ? 0 : n_up, j1 = (up == same) ? n_up : N;
+          const float* gs = gt + (same ? 0 : LF_MAX_BLK) * 8;
+          // the step's filter jets and, past tile 0, the senders' z_j[0] (global loads issued
+          // before the waits, so that their latency overlaps them); slots without an edge read
+          // edge 0 and are masked below
+          float2 wv[NB], w1[NB], z0v[NB];
+#pragma unroll
+          for (int k = 0; k < NB; ++k) {
+            const int edge = __float_as_int(gs[k * 8]);
+            const float* wp = ew_b + (int64_t)(edge >= 0 ? edge : 0) * 3 * LF_D + fl;
+            wv[k] = __ldg(reinterpret_cast<const float2*>(wp));
+            w1[k] = __ldg(reinterpret_cast<const float2*>(wp + LF_D));
+            const int j = min(j0 + k, N - 1);
+            if (ZC)
+              z0v[k] = __ldg(reinterpret_cast<const float2*>(a.z0 + (j < n_up ? 0 : LF_D) + fl));
+            else if (c0 > 0)
+              z0v[k] = __ldg(reinterpret_cast<const float2*>(zv_b + (int64_t)j * LF_D + fl));
+          }
+          // the Laplacian channel's w'' lines into L2 ahead of their use at the end of the step
+          if (c1 == C && fp < NB) {
+            const int edge = __float_as_int(gs[fp * 8]);
+            if (edge >= 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(ew_b + ((int64_t)edge * 3 + 2) * LF_D + f0));
+          }
           if (!wait_or_abort(&full[s], (uint32_t)((g_ks / LF_STAGES) & 1), &s_abort)) {
             ok = false;
             break;
           }
-          uint8_t* st = smem + s * LF_STAGE;
-          uint8_t* a_hi = st;
-          uint8_t* a_lo = st + LF_TILE;
-          const int fb = ks / 2, t = ks % 2;
-          const int f0 = fb * LF_BK;
+          uint8_t* a_hi = smem + s * LF_STAGE;
+          uint8_t* a_lo = a_hi + LF_TILE;
           const int zb = (int)(zi % LF_ZBUF);
           const float* zs = reinterpret_cast<const float*>(smem + LF_OFF_Z + zb * LF_TILE);  // [c - c0][j][32]
-          if (t < 2 && !a.z_const && !wait_or_abort(&zfull[zb], (uint32_t)((zi / LF_ZBUF) & 1), &s_abort)) {
+          if (!ZC && !wait_or_abort(&zfull[zb], (uint32_t)((zi / LF_ZBUF) & 1), &s_abort)) {
             ok = false;
             break;
           }
+          const int n_send = same ? (j1 - j0) - 1 : (j1 - j0);
+          const float nu = 1.f / (float)(n_send > 1 ? n_send : 1);
           // the next K step's filter lines into L2 while this one is produced
           if (ks + 1 < LF_KSTEPS) prefetch_filters(ew_b, (ks + 1) % 2, ((ks + 1) / 2) * LF_BK);
           else if (g + 1 < n_tiles) prefetch_filters(ew_b, 0, 0);
-          if (i < N) {
-            // electron-electron messages of type t: senders j = j0 + k, k < NB (the z slab is
-            // [channel][sender][32]; slots past the block read finite data and carry weight 0)
-            const bool same = t == 0;
-            const int j0 = (up == same) ? 0 : n_up, j1 = (up == same) ? n_up : N;
-            const int n_send = same ? (j1 - j0) - 1 : (j1 - j0);
-            const float nu = 1.f / (float)(n_send > 1 ? n_send : 1);
-            const float* gs = gt + (same ? 0 : LF_MAX_BLK) * 8;
-            // the step's filter jets and, past tile 0, the senders' z_j[0]
-            issue_ee(t, f0, c0);
-            float wv[NB], w1[NB], z0v[NB];
 #pragma unroll
-            for (int k = 0; k < NB; ++k) {
-              const bool v = __float_as_int(gs[k * 8]) >= 0;
-              const int j = min(j0 + k, N - 1);
-              const float z0 = a.z_const ? __ldg(a.z0 + (j < n_up ? 0 : LF_D) + f0 + lane)
-                                         : (c0 == 0 ? zs[j * LF_BK + lane] : nz0[k]);
-              wv[k] = v ? nw[k] : 0.f;
-              w1[k] = v ? nw1[k] : 0.f;
-              z0v[k] = v ? z0 : 0.f;
-            }
-            float* acl = accL + (i * 2 + t) * LF_D + f0 + lane;
-            float accv = g == 0 ? 0.f : *acl;
-            const float* zrow = zs + j0 * LF_BK + lane;       // channel c0's senders
-            int row = i;                                      // A row of (c0, i)
-            int e = c0 >= 1 ? (c0 - 1) / 3 : -1, x = c0 >= 1 ? (c0 - 1) - 3 * e : 2;  // electron, axis of c0
-            const int lchunk = lane >> 2, lsub = (lane & 3) << 2;
-            // channels in groups of three: the loads and multiply-add chains of a group overlap
-            for (int cg = c0; cg < c1; cg += 3, zrow += 3 * N * LF_BK) {
-              float zc[3][NB], mm[3];
+          for (int k = 0; k < NB; ++k) {
+            const bool v = __float_as_int(gs[k * 8]) >= 0;
+            const int j = min(j0 + k, N - 1);
+            if (!ZC && c0 == 0) z0v[k] = *reinterpret_cast<const float2*>(zs + j * LF_BK + 2 * fp);
+            wv[k] = v ? wv[k] : make_float2(0.f, 0.f);
+            w1[k] = v ? w1[k] : make_float2(0.f, 0.f);
+            z0v[k] = v ? z0v[k] : make_float2(0.f, 0.f);
+          }
+          float* acl = accL + (i * 2 + t) * LF_D + fl;
+          float2 accv = g == 0 ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2*>(acl);
+          {
+            // the receiver's own coordinates, for both halves at once (no divergence on i):
+            // m_i[c] = sum_j w_ij z_j[c] + sum_j w'_ij u_ij,x z_j[0], c = 1 + 3 i + x, and the Laplacian
+            // cross term 2 sum_j w'_ij u_ij,x dz_j/dr_i,x (before the channel loop, whose Laplacian
+            // channel reads the cross terms)
+            const int cb = 1 + 3 * i;
+            const bool any_own = cb + 2 >= c0 && cb < c1;
+            if (__any_sync(0xffffffffu, any_own)) {
 #pragma unroll
-              for (int u = 0; u < 3; ++u) {
-                const bool in = cg + u < c1;
+              for (int x = 0; x < 3; ++x) {
+                const int c = cb + x;
+                const bool act = c >= c0 && c < c1;
+                const float* zr = zs + ((act ? c - c0 : 0) * N + j0) * LF_BK + 2 * fp;
+                float2 m = make_float2(0.f, 0.f), cr = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int k = 0; k < NB; ++k)
-                  zc[u][k] = a.z_const ? (cg + u == 0 ? z0v[k] : 0.f) : (in ? zrow[(u * N + k) * LF_BK] : 0.f);
+                for (int k = 0; k < NB; ++k) {
+                  const float ux = gs[k * 8 + 1 + x];
+                  const float2 ak = make_float2(w1[k].x * ux, w1[k].y * ux);
+                  m.x = fmaf(ak.x, z0v[k].x, m.x);
+                  m.y = fmaf(ak.y, z0v[k].y, m.y);
+                  if (!ZC) {
+                    const float2 z = *reinterpret_cast<const float2*>(zr + k * LF_BK);
+                    m.x = fmaf(wv[k].x, z.x, m.x);
+                    m.y = fmaf(wv[k].y, z.y, m.y);
+                    cr.x = fmaf(ak.x, z.x, cr.x);
+                    cr.y = fmaf(ak.y, z.y, cr.y);
+                  }
+                }
+                if (act) {
+                  accv.x = fmaf(2.f, cr.x, accv.x);
+                  accv.y = fmaf(2.f, cr.y, accv.y);
+                  if (writer) {
+                    m.x *= nu;
+                    m.y *= nu;
+                    const int orow = (c - c0) * N + i;
+                    float2 hi, lo;
+                    float tt = __fmul_rn(m.x, 8193.f);
+                    hi.x = __fsub_rn(tt, __fsub_rn(tt, m.x));
+                    tt = __fmul_rn(m.y, 8193.f);
+                    hi.y = __fsub_rn(tt, __fsub_rn(tt, m.y));
+                    lo.x = __fsub_rn(m.x, hi.x);
+                    lo.y = __fsub_rn(m.y, hi.y);
+                    const uint32_t o = (uint32_t)orow * 128u + ((((uint32_t)fp >> 1) ^ (uint32_t)(orow & 7)) << 4) +
+                                       ((uint32_t)(fp & 1) << 3);
+                    *reinterpret_cast<float2*>(a_hi + o) = hi;
+                    *reinterpret_cast<float2*>(a_lo + o) = lo;
+                  }
+                }
               }
+            }
+          }
+          const float* zrow = zs + j0 * LF_BK + 2 * fp;  // channel c0's senders
+          int row = i;                                    // A row of (c0, i)
+          int e = c0 >= 1 ? (c0 - 1) / 3 : -1, x = c0 >= 1 ? (c0 - 1) - 3 * e : 2;  // electron, axis of c0
+          int ke_c = -1;                                  // the sender slot whose w' and z_j[0] are cached
+          float2 w1e = make_float2(0.f, 0.f), z0e = make_float2(0.f, 0.f);
+          const uint32_t lchunk = (uint32_t)(fp >> 1), lsub = (uint32_t)(fp & 1) << 3;
+          // channels in groups of LF_UG: the loads and multiply-add chains of a group overlap
+          for (int cg = c0; cg < c1; cg += LF_UG, zrow += LF_UG * N * LF_BK) {
+            float2 zc[LF_UG][NB], mm[LF_UG];
 #pragma unroll
-              for (int u = 0; u < 3; ++u) {
-                float m0 = 0.f, m1 = 0.f;
+            for (int u = 0; u < LF_UG; ++u) {
+              // rows past c1 stay inside the z buffers (finite data) and their sums are dropped
+#pragma unroll
+              for (int k = 0; k < NB; ++k)
+                zc[u][k] = ZC ? make_float2(0.f, 0.f) : *reinterpret_cast<const float2*>(zrow + (u * N + k) * LF_BK);
+            }
+#pragma unroll
+            for (int u = 0; u < LF_UG; ++u) {
+              float2 m0 = make_float2(0.f, 0.f), m1 = make_float2(0.f, 0.f);
+              if (!ZC || (cg + u == 0)) {
 #pragma unroll
                 for (int k = 0; k < NB; k += 2) {
-                  m0 += wv[k] * zc[u][k];
-                  if (k + 1 < NB) m1 += wv[k + 1] * zc[u][k + 1];
+                  const float2 z = ZC ? z0v[k] : zc[u][k];
+                  m0.x = fmaf(wv[k].x, z.x, m0.x);
+                  m0.y = fmaf(wv[k].y, z.y, m0.y);
+                  if (k + 1 < NB) {
+                    const float2 z1 = ZC ? z0v[k + 1] : zc[u][k + 1];
+                    m1.x = fmaf(wv[k + 1].x, z1.x, m1.x);
+                    m1.y = fmaf(wv[k + 1].y, z1.y, m1.y);
+                  }
                 }
-                mm[u] = m0 + m1;
               }
+              mm[u] = make_float2(m0.x + m1.x, m0.y + m1.y);
+            }
 #pragma unroll
-              for (int u = 0; u < 3; ++u) {
-                const int c = cg + u;
-                if (c >= c1) break;
-                float m = mm[u];
-                if (c >= 1 && c < C - 1) {
-                  if (e == i) {
-                    // receiver's own coordinate: sum_j w'_ij u_ij,x z_j[0]; Laplacian cross term
-                    // 2 sum_j w'_ij u_ij,x dz_j/dr_i,x
-                    float own = 0.f, cr = 0.f;
+            for (int u = 0; u < LF_UG; ++u) {
+              const int c = cg + u;
+              if (c >= c1) break;
+              float2 m = mm[u];
+              if (c >= 1 && c < C - 1) {
+                if (e >= j0 && e < j1) {
+                  // a sender's coordinate: -w'_ie u_ie,x z_e[0]; Laplacian cross term
+                  // -2 w'_ie u_ie,x dz_e/dr_e,x (zero for the receiver's own slot, whose weights
+                  // are masked); the slot's registers are picked once per electron
+                  const int ke = e - j0;
+                  if (ke != ke_c) {
+                    ke_c = ke;
+                    w1e = w1[0];
+                    z0e = z0v[0];
 #pragma unroll
-                    for (int k = 0; k < NB; ++k) {
-                      const float ak = w1[k] * gs[k * 8 + 1 + x];
-                      own += ak * z0v[k];
-                      cr += ak * zc[u][k];
-                    }
-                    m += own;
-                    accv += 2.f * cr;
-                  } else if (e >= j0 && e < j1) {
-                    // a sender's coordinate: -w'_ie u_ie,x z_e[0]; cross term -2 w'_ie u_ie,x dz_e/dr_e,x
-                    // (slot ke = e - j0 picked from the registers by selects)
-                    const int ke = e - j0;
-                    float w1e = w1[0], z0e = z0v[0], zce = zc[u][0];
-#pragma unroll
-                    for (int k = 1; k < NB; ++k) {
-                      w1e = ke == k ? w1[k] : w1e;
-                      z0e = ke == k ? z0v[k] : z0e;
-                      zce = ke == k ? zc[u][k] : zce;
-                    }
-                    const float ak = w1e * gs[ke * 8 + 1 + x];
-                    m -= ak * z0e;
-                    accv -= 2.f * ak * zce;
+                    for (int k = 1; k < NB; ++k)
+                      if (ke == k) {
+                        w1e = w1[k];
+                        z0e = z0v[k];
+                      }
                   }
-                } else if (c == C - 1) {
-                  // sum_j (2 w''_ij + 4 w'_ij / d_ij) z_j[0] + the accumulated cross terms
-#pragma unroll
-                  for (int k = 0; k < NB; ++k) {
-                    const int edge = __float_as_int(gs[k * 8]);
-                    const float w2 = edge >= 0 ? __ldg(ew_b + ((int64_t)edge * 3 + 2) * LF_D + f0 + lane) : 0.f;
-                    m += (2.f * w2 + 4.f * w1[k] * gs[k * 8 + 4]) * z0v[k];
+                  const float ux = gs[ke * 8 + 1 + x];
+                  const float2 ak = make_float2(w1e.x * ux, w1e.y * ux);
+                  m.x = fmaf(-ak.x, z0e.x, m.x);
+                  m.y = fmaf(-ak.y, z0e.y, m.y);
+                  if (!ZC) {
+                    const float2 zce = *reinterpret_cast<const float2*>(zrow + (u * N + ke) * LF_BK);
+                    accv.x = fmaf(-2.f * ak.x, zce.x, accv.x);
+                    accv.y = fmaf(-2.f * ak.y, zce.y, accv.y);
                   }
-                  m += accv;
                 }
-                m *= nu;
-                const float hi = tf32_rn(m);
-                const uint32_t o = (uint32_t)(row * 128 + ((lchunk ^ (row & 7)) << 4) + lsub);
-                *reinterpret_cast<float*>(a_hi + o) = hi;
-                *reinterpret_cast<float*>(a_lo + o) = tf32_rn(m - hi);
-                row += N;
-                if (++x == 3) {
-                  x = 0;
-                  ++e;
+              } else if (c == C - 1) {
+                // sum_j (2 w''_ij + 4 w'_ij / d_ij) z_j[0] + the accumulated cross terms
+#pragma unroll
+                for (int k = 0; k < NB; ++k) {
+                  const int edge = __float_as_int(gs[k * 8]);
+                  const float2 w2 = edge >= 0
+                                        ? __ldg(reinterpret_cast<const float2*>(ew_b + ((int64_t)edge * 3 + 2) * LF_D + fl))
+                                        : make_float2(0.f, 0.f);
+                  const float id = 4.f * gs[k * 8 + 4];
+                  m.x = fmaf(fmaf(2.f, w2.x, id * w1[k].x), z0v[k].x, m.x);
+                  m.y = fmaf(fmaf(2.f, w2.y, id * w1[k].y), z0v[k].y, m.y);
                 }
+                m.x += accv.x;
+                m.y += accv.y;
+              }
+              m.x *= nu;
+              m.y *= nu;
+              if (writer && e != i) {  // (the receiver's own channels were formed above)
+                // TF32 high part by Veltkamp splitting (round to nearest at 11 significant
+                // bits), low part the exact remainder
+                float2 hi, lo;
+                float tt = __fmul_rn(m.x, 8193.f);
+                hi.x = __fsub_rn(tt, __fsub_rn(tt, m.x));
+                tt = __fmul_rn(m.y, 8193.f);
+                hi.y = __fsub_rn(tt, __fsub_rn(tt, m.y));
+                lo.x = __fsub_rn(m.x, hi.x);
+                lo.y = __fsub_rn(m.y, hi.y);
+                const uint32_t o = (uint32_t)row * 128u + ((lchunk ^ (uint32_t)(row & 7)) << 4) + lsub;
+                *reinterpret_cast<float2*>(a_hi + o) = hi;
+                *reinterpret_cast<float2*>(a_lo + o) = lo;
+              }
+              row += N;
+              if (++x == 3) {
+                x = 0;
+                ++e;
               }
             }
-            *acl = accv;
           }
+          if (writer) *reinterpret_cast<float2*>(acl) = accv;
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A block visible to the tensor cores
           __syncwarp();
           if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&conv[s])) : "memory");
-          if (t == 1 && !a.z_const) {  // the z slab's last use: release it to the TMA thread
+          if (t == 1 && !ZC) {  // the z slab's last use: release it to the TMA thread
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&zempty[zb])) : "memory");
             ++zi;
           }
@@ -451,11 +527,11 @@ __global__ void __launch_bounds__(lf_threads(NB), 1)
       }
     }
     if (!ok) s_abort = 1;
-  } else {
-    // ---- epilogue warps 2..5: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 ----
+  } else if (warp >= 4) {
+    // ---- epilogue warps 4..7: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 ----
     // Per 32-feature chunk: the warp's 32 rows of the accumulator through a shared-memory
     // transpose, stored as full 128-byte lines of U (the electron-nucleus part, un, is added by
-    // the update kernel that follows).
+    // the kernel that follows).
     const int q = warp % 4;
     float(*stw)[33] = reinterpret_cast<float(*)[33]>(stg + q * 32 * 33);
     int64_t lt = 0;
@@ -495,6 +571,7 @@ __global__ void __launch_bounds__(lf_threads(NB), 1)
       }
     }
   }
+done:
   __syncthreads();
   if (s_abort && threadIdx.x == 0) atomicOr(status, (unsigned)DQ_FLAG_TIMEOUT);
   tc_fence_after();
@@ -630,19 +707,28 @@ cudaError_t launch_layer_fused(const dq_handle_s& h, const FwdDims& d, const flo
   a.z_const = z_const ? 1 : 0;
   CUtensorMap mhi, mlo, mz;
   if (!map_w(&mhi, wg_hi, LF_D) || !map_w(&mlo, wg_lo, LF_D)) return cudaErrorInvalidValue;
-  // with constant node channels the z slab is never loaded; the map is built on W (any valid map)
+  // with constant node channels the z slabs are never loaded; their maps are built on W (any valid map)
   if (!(z_const ? map_w(&mz, wg_hi, LF_D) : map_z(&mz, Z, d.Bc, d.N, d.C, LF_D, a.G))) return cudaErrorInvalidValue;
   const int nb = std::max(h.n_up, h.n_dn);
-  auto kern = nb <= 2 ? layer_fused_kernel<2> : nb <= 4 ? layer_fused_kernel<4> : nb <= 5 ? layer_fused_kernel<5>
-              : nb <= 7 ? layer_fused_kernel<7> : layer_fused_kernel<8>;
+  using KernT = void (*)(LayerFusedArgs, CUtensorMap, CUtensorMap, CUtensorMap, unsigned int*);
+  KernT kern;
+  if (z_const)
+    kern = nb <= 2 ? layer_fused_kernel<2, true> : nb <= 4 ? layer_fused_kernel<4, true>
+           : nb <= 5 ? layer_fused_kernel<5, true> : nb <= 7 ? layer_fused_kernel<7, true>
+                     : layer_fused_kernel<8, true>;
+  else
+    kern = nb <= 2 ? layer_fused_kernel<2, false> : nb <= 4 ? layer_fused_kernel<4, false>
+           : nb <= 5 ? layer_fused_kernel<5, false> : nb <= 7 ? layer_fused_kernel<7, false>
+                     : layer_fused_kernel<8, false>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LF_SMEM);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t grid = d.Bc < sms ? d.Bc : sms;
-  kern<<<(unsigned)grid, lf_threads(nb <= 2 ? 2 : nb <= 4 ? 4 : nb <= 5 ? 5 : nb <= 7 ? 7 : 8), LF_SMEM, s>>>(
-      a, mhi, mlo, mz, h.d_status);
+  a.n_prod = (h.n_up + 1) / 2 + (h.n_dn + 1) / 2;  // receiver pairs of the two spin blocks
+  if (a.n_prod > LF_PROD_WARPS) return cudaErrorInvalidValue;
+  kern<<<(unsigned)grid, LF_THREADS, LF_SMEM, s>>>(a, mhi, mlo, mz, h.d_status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   add_nucleus_part_kernel<<<(unsigned)(d.Bc * d.N), LF_D, 0, s>>>(un, d.N, d.C, Z);
