@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--no-mala", action="store_true", help="skip the step with the Langevin sampler")
     p.add_argument("--no-batch", action="store_true", help="skip the uneven-molecule batch")
     p.add_argument("--no-natgrad", action="store_true", help="skip the natural-gradient direction")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the default tile set (for runs under a profiler, which distorts the autotuner's timings)")
     p.add_argument("--no-pp", action="store_true", help="skip the pseudopotential and ansatz-variant legs")
     p.add_argument("--mala-tau", type=float, default=0.1, help="Langevin time step (bohr^2)")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
@@ -289,8 +291,10 @@ def peaks():
 # from an ncu capture of the layer-1 launch on 512 N2 walkers (FP32, the tuned 4-receiver tile; summary under profiles/); None
 # once the kernel has changed since that capture.
 MSG_DRAM_BYTES_PER_WALKER = (263.570432e6 + 432.803840e6) / 512
-# the same for one launch of the fused layer kernel (layer >= 1); None until captured
-LAYER_FUSED_DRAM_BYTES_PER_WALKER = None
+# the same for one launch of the fused layer kernel (layer 1 of N2, 512 walkers, the receiver-pair
+# producer design; summary under profiles/); None once the kernel has changed since that capture.
+# Layer 0 (constant node channels) reads no z slabs and moves less.
+LAYER_FUSED_DRAM_BYTES_PER_WALKER = (238.052864e6 + 108.800256e6) / 512
 
 
 def gemm_shapes(wl, chunk):
@@ -322,6 +326,12 @@ def message_flops_per_walker(wl):
     main = 2.0 * N * (N - 1) * C * D
     prod = (2.0 * N * (N - 1) * 3 * 2 + 2.0 * N * (N - 1) * 8 + 2.0 * N * M * 10) * D
     return main + prod
+
+
+def wl_edges(wl):
+    """Edges per walker: electron pairs (i < j) and electron-nucleus pairs."""
+    N, M = wl.system.n_elec, wl.system.n_nuc
+    return N * (N - 1) // 2 + N * M
 
 
 def det_flops_per_walker(wl):
@@ -386,6 +396,8 @@ def roofline_for(kind, ms, n, wl, chunk, pk, how, alu, steps):
         ach = flops / t / 1e12
         return {**base, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": LAYER_FUSED_DRAM_BYTES_PER_WALKER * chunk if LAYER_FUSED_DRAM_BYTES_PER_WALKER else None,
+                # z read once, the filter jets (w, w', w'') read, the pre-activations written
+                "algorithmic_bytes_per_launch": chunk * 4.0 * (2 * N * C * D + wl_edges(wl) * 3 * D),
                 "peak_source": f"{how} bf16 sustained x 1.1/2.25 (TF32) / 3 (3xTF32 split)",
                 "flops_per_launch": flops, "message_flops_per_launch": message_flops_per_walker(wl) * chunk,
                 "message_tflops": message_flops_per_walker(wl) * chunk / t / 1e12,
@@ -725,7 +737,7 @@ def batch_leg(args, dev, flush):
         res = {}
         ms_b = timed(lambda: res.__setitem__("el", batch.local_energy(th, r)[2]), steps)
         entry = {"value": walkers / (ms_b / 1e3), "unit": UNIT, "ms_per_call": ms_b, "walkers": walkers,
-                 "tuning": {"rounds": rounds, "msg_ib": ib, "autotune_ms": tune_ms}}
+                 "tuning": dict(batch.tile_set(), autotune_ms=tune_ms)}
         if prec == "fp32":
             singles = [Ansatz(w.system, w.cfg, "fp32", device=dev) for w in wls]
             ms_p = timed(lambda: [h.local_energy(th[k], r[k]) for k, h in enumerate(singles)], steps)
@@ -809,9 +821,11 @@ def main():
     logabs, _ = h.ansatz_eval(theta, r)
     # tile shapes (message register tile, walker chunk) timed on these walkers before the timed region
     tuning = None
-    if wl.precision != "fp64":
+    if wl.precision != "fp64" and not args.no_autotune:
         t_ms, t_chunk, t_ib = h.autotune(theta, r)
-        tuning = {"msg_ib": t_ib, "max_chunk": t_chunk, "local_energy_ms": t_ms}
+        tuning = dict(h.tile_set(), local_energy_ms=t_ms)
+    elif wl.precision != "fp64":
+        tuning = dict(h.tile_set(), autotuned=False)
     step_size = wl.extra.get("step_size", 0.2)
     try:
         h.grad_logpsi(theta, r[:1], torch.ones(1, dtype=dt, device=dev), 0)

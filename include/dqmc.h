@@ -480,6 +480,14 @@ dq_status dq_msg_tile(dq_handle h, int32_t* msg_ib);
 dq_status dq_set_layer_kernel(dq_handle h, int32_t mode);
 dq_status dq_layer_kernel(dq_handle h, int32_t* fused);
 
+/* Warps per CTA of the grouped determinant kernels (no counterpart in the
+ * paper; the matrices of Eqs. 21-22, one per warp): 4 (the default) or 2,
+ * DQ_ERR_ARG otherwise.  Results do not depend on it.  dq_tile_set reports the
+ * handle's current tile set: walker chunk, msg_ib, layer kernels (1 fused,
+ * 2 separate) and determinant warps per CTA (host outputs, non-null). */
+dq_status dq_set_det_warps(dq_handle h, int32_t warps);
+dq_status dq_tile_set(dq_handle h, int64_t* max_chunk, int32_t* msg_ib, int32_t* layer_kernel, int32_t* det_warps);
+
 /* dq_autotune times local_energy on the given walkers for every candidate of
  *   layer kernels  fused, separate   (dq_set_layer_kernel 1 or 2; the fused
  *                                      one only where supported, the separate
@@ -488,11 +496,16 @@ dq_status dq_layer_kernel(dq_handle h, int32_t* fused);
  *   walker chunk   4096, 2048        (dq_set_max_chunk: the M extent of every
  *                                      GEMM, the grid of every other kernel),
  *   msg_ib         8, 4              (separate message kernel only),
+ *   det warps      4, 2              (dq_set_det_warps; with the 4096 chunk),
  * one warm-up and two timed calls each (CUDA events on `stream`, host waits),
  * and keeps the fastest; workspace: at least dq_workspace_size(op =
  * DQ_OP_LOCAL_ENERGY) for a chunk of min(B, 4096) walkers plus 9 B per
- * walker.  Synchronises; not for use inside a stream capture.  best_ms:
- * nullable host double. */
+ * walker.  The chosen set is cached in the process per molecule size
+ * (electrons, spin-up electrons, nuclei), ansatz shape (width, layers,
+ * determinants, radial features, variant flags), precision and B: a later
+ * call with the same key applies the cached set without timing (best_ms then
+ * reports the cached time).  Synchronises; not for use inside a stream
+ * capture.  best_ms: nullable host double. */
 dq_status dq_autotune(dq_handle h, const void* params, const void* r, int64_t B, void* ws, size_t ws_bytes,
                       void* stream, double* best_ms);
 
@@ -504,14 +517,21 @@ dq_status dq_autotune(dq_handle h, const void* params, const void* r, int64_t B,
  *   msg_ib   8, 4         (receivers per warp task of the jet message kernel:
  *                          its register tile of msg_ib x 4 channels),
  * one warm-up and two timed calls each (CUDA events on `stream`, host waits),
+ * then, at the winning pair, the determinant kernels' warps per CTA (4, 2),
  * and keeps the fastest in the batch (later calls use it; dq_multi_tuning
- * reports it).  Candidates whose workspace exceeds ws_bytes are skipped.
+ * and dq_multi_tile_set report it).  Candidates whose workspace exceeds
+ * ws_bytes are skipped.
  * Workspace: dq_multi_workspace_size(op = DQ_OP_AUTOTUNE) covers all
  * candidates and the timing outputs.  Synchronises; not for use inside a
  * stream capture.  best_ms: nullable host double, the winner's time. */
 dq_status dq_autotune_multi(dq_multi m, const void* const* params, const void* const* r, const int64_t* B, void* ws,
                             size_t ws_bytes, void* stream, double* best_ms);
 dq_status dq_multi_tuning(dq_multi m, int32_t* rounds, int32_t* msg_ib);
+/* The batch's tile set: rounds, msg_ib, the number of molecules whose jet
+ * layers run fused (dq_set_layer_kernel mode 1) and the determinant warps per
+ * CTA (host outputs, non-null). */
+dq_status dq_multi_tile_set(dq_multi m, int32_t* rounds, int32_t* msg_ib, int32_t* fused_layers,
+                            int32_t* det_warps);
 
 /* Measurement support (not part of the method): enqueues on `stream` one
  * launch of a kernel that only issues fused multiply-adds on the CUDA cores,

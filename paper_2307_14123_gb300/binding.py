@@ -38,7 +38,8 @@ EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_
            "dq_multi_handle", "dq_multi_set_rounds", "dq_multi_rounds", "dq_multi_workspace_size",
            "ansatz_eval_multi", "local_energy_multi", "mcmc_step_multi", "grad_logpsi_multi",
            "vmc_loss_weights_multi", "dq_autotune_multi", "dq_multi_tuning", "dq_set_msg_tile", "dq_msg_tile", "dq_autotune", "natural_gradient", "param_update", "dq_pp_workspace_size",
-           "pseudopotential_energy", "dq_fma_rate_probe", "dq_set_layer_kernel", "dq_layer_kernel"]
+           "pseudopotential_energy", "dq_fma_rate_probe", "dq_set_layer_kernel", "dq_layer_kernel",
+           "dq_set_det_warps", "dq_tile_set", "dq_multi_tile_set"]
 
 
 class DQError(RuntimeError):
@@ -126,6 +127,9 @@ def load_library(path=None):
         lib.dq_fma_rate_probe.argtypes = [i32, i32, i32, P, P, P]
         lib.dq_set_layer_kernel.argtypes = [P, i32]
         lib.dq_layer_kernel.argtypes = [P, P]
+        lib.dq_set_det_warps.argtypes = [P, i32]
+        lib.dq_tile_set.argtypes = [P, P, P, P, P]
+        lib.dq_multi_tile_set.argtypes = [P, P, P, P, P]
         for name in EXPORTS:
             getattr(lib, name).restype = ctypes.c_int
         lib.dq_status_string.restype = ctypes.c_char_p
@@ -225,6 +229,16 @@ class Ansatz:
         """Jet layers: 1 fused kernel (messages as the tensor-core operand), 2 separate kernels, 0 the
         default (fused where supported)."""
         _check(self.lib.dq_set_layer_kernel(self.h, int(mode)))
+
+    def set_det_warps(self, warps):
+        """Warps (matrices) per CTA of the determinant kernels: 4 or 2."""
+        _check(self.lib.dq_set_det_warps(self.h, int(warps)))
+
+    def tile_set(self):
+        """The current tile set: {max_chunk, msg_ib, layer_kernel (1 fused, 2 separate), det_warps}."""
+        c, ib, lk, dw = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(self.lib.dq_tile_set(self.h, ctypes.byref(c), ctypes.byref(ib), ctypes.byref(lk), ctypes.byref(dw)))
+        return {"max_chunk": c.value, "msg_ib": ib.value, "layer_kernel": lk.value, "det_warps": dw.value}
 
     def layer_kernel_fused(self):
         v = ctypes.c_int32()
@@ -569,6 +583,12 @@ class AnsatzBatch:
         rounds, ib = ctypes.c_int32(), ctypes.c_int32()
         _check(self.lib.dq_multi_tuning(self.h, ctypes.byref(rounds), ctypes.byref(ib)))
         return rounds.value, ib.value
+
+    def tile_set(self):
+        """The batch's tile set: {rounds, msg_ib, fused_layers (molecules), det_warps}."""
+        r, ib, f, dw = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(self.lib.dq_multi_tile_set(self.h, ctypes.byref(r), ctypes.byref(ib), ctypes.byref(f), ctypes.byref(dw)))
+        return {"rounds": r.value, "msg_ib": ib.value, "fused_layers": f.value, "det_warps": dw.value}
 
     def ansatz_eval(self, params, r):
         self._check_in(list(params) + list(r), "ansatz_eval")

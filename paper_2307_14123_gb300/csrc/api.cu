@@ -11,7 +11,10 @@
 
 #include <algorithm>
 #include <initializer_list>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "backward.cuh"
@@ -1947,12 +1950,62 @@ dq_status dq_layer_kernel(dq_handle h, int32_t* fused) {
   return DQ_OK;
 }
 
+dq_status dq_set_det_warps(dq_handle h, int32_t warps) {
+  if (!h || (warps != 2 && warps != 4)) return DQ_ERR_ARG;
+  h->det_warps = warps;
+  return DQ_OK;
+}
+
+dq_status dq_tile_set(dq_handle h, int64_t* max_chunk, int32_t* msg_ib, int32_t* layer_kernel, int32_t* det_warps) {
+  if (!h || !max_chunk || !msg_ib || !layer_kernel || !det_warps) return DQ_ERR_ARG;
+  *max_chunk = h->max_chunk;
+  *msg_ib = h->msg_ib == 0 ? 8 : h->msg_ib;
+  *layer_kernel = use_fused(*h, true) ? 1 : 2;
+  *det_warps = h->det_warps;
+  return DQ_OK;
+}
+
+namespace {
+// Tile sets chosen by dq_autotune, per molecule size, ansatz shape, precision and walker count:
+// a later handle of the same configuration takes the cached set instead of timing again.
+struct TuneKey {
+  int N, n_up, M, D, L, K, Q, precision, full_det, edge_update, el_init;
+  int64_t B;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(N, n_up, M, D, L, K, Q, precision, full_det, edge_update, el_init, B) <
+           std::tie(o.N, o.n_up, o.M, o.D, o.L, o.K, o.Q, o.precision, o.full_det, o.edge_update, o.el_init, o.B);
+  }
+};
+struct TuneVal {
+  int64_t chunk;
+  int ib, lk, dw;
+  double ms;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+TuneKey tune_key(const dq_handle_s& h, int64_t B) {
+  return TuneKey{h.N, h.n_up, h.M, h.D, h.L, h.K, h.Q, (int)h.precision, h.full_det, h.edge_update, h.el_init, B};
+}
+}  // namespace
+
 dq_status dq_autotune(dq_handle h, const void* params, const void* r, int64_t B, void* ws, size_t ws_bytes,
                       void* stream, double* best_ms) {
   dq_status st = check_handle(h);
   if (st != DQ_OK) return st;
   if (B < 1 || !params || !r || h->precision == DQ_FP64) return h->precision == DQ_FP64 ? DQ_ERR_UNSUPPORTED : DQ_ERR_ARG;
   if (!ws || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const auto it = g_tune_cache.find(tune_key(*h, B));
+    if (it != g_tune_cache.end()) {
+      h->max_chunk = it->second.chunk;
+      h->msg_ib = it->second.ib;
+      h->layer_kernel = it->second.lk;
+      h->det_warps = it->second.dw;
+      if (best_ms) *best_ms = it->second.ms;
+      return DQ_OK;
+    }
+  }
   const cudaStream_t s = (cudaStream_t)stream;
   auto* w = static_cast<unsigned char*>(ws);
   // timing outputs after the largest candidate's forward workspace
@@ -1985,16 +2038,20 @@ dq_status dq_autotune(dq_handle h, const void* params, const void* r, int64_t B,
   }
   double best = -1;
   int64_t best_chunk = keep_chunk;
-  int best_ib = keep_ib, best_lk = keep_lk;
+  const int keep_dw = h->det_warps;
+  int best_ib = keep_ib, best_lk = keep_lk, best_dw = keep_dw;
   for (int lk : {1, 2}) {
     if ((lk == 1 && !can_fuse) || (lk == 2 && !try_sep)) continue;
     for (int64_t chunk : {(int64_t)4096, (int64_t)2048}) {
-      // the message register tile matters only to the separate message kernel
-      for (int ib : {8, 4}) {
-        if (lk == 1 && ib == 4) continue;
+      // the message register tile matters only to the separate message kernel; the determinant
+      // kernels' CTA size is tried with the largest chunk only
+      for (int cand = 0; cand < 3; ++cand) {
+        const int ib = cand == 1 ? 4 : 8, dw = cand == 2 ? 2 : 4;
+        if ((lk == 1 && cand == 1) || (cand == 2 && chunk != 4096)) continue;
         h->layer_kernel = lk;
         h->max_chunk = chunk;
         h->msg_ib = ib;
+        h->det_warps = dw;
         float ms = 0;
         for (int rep = 0; rep < 3 && st == DQ_OK; ++rep) {
           if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) st = DQ_ERR_CUDA;
@@ -2012,6 +2069,7 @@ dq_status dq_autotune(dq_handle h, const void* params, const void* r, int64_t B,
           best_chunk = chunk;
           best_ib = ib;
           best_lk = lk;
+          best_dw = dw;
         }
       }
       if (st != DQ_OK) break;
@@ -2023,6 +2081,11 @@ dq_status dq_autotune(dq_handle h, const void* params, const void* r, int64_t B,
   h->max_chunk = st == DQ_OK ? best_chunk : keep_chunk;
   h->msg_ib = st == DQ_OK ? best_ib : keep_ib;
   h->layer_kernel = st == DQ_OK ? best_lk : keep_lk;
+  h->det_warps = st == DQ_OK ? best_dw : keep_dw;
+  if (st == DQ_OK) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[tune_key(*h, B)] = TuneVal{best_chunk, best_ib, best_lk, best_dw, best};
+  }
   if (best_ms) *best_ms = best;
   return st;
 }
@@ -2088,12 +2151,59 @@ dq_status dq_autotune_multi(dq_multi g, const void* const* params, const void* c
       }
     }
   }
+  // the determinant kernels' CTA size, at the best rounds and message tile
+  const int keep_dw = g->h[0]->det_warps;
+  int best_dw = keep_dw;
+  if (st == DQ_OK && best >= 0) {
+    g->rounds = best_rounds;
+    for (int dw : {4, 2}) {
+      for (int m = 0; m < g->n; ++m) {
+        g->h[m]->msg_ib = best_ib;
+        g->h[m]->det_warps = dw;
+      }
+      float ms = 0;
+      for (int rep = 0; rep < 3 && st == DQ_OK; ++rep) {
+        if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) st = DQ_ERR_CUDA;
+        if (st == DQ_OK)
+          st = run_forward_multi<float>(*g, reinterpret_cast<const float* const*>(params),
+                                        reinterpret_cast<const float* const*>(r), B, true, la, sg, el, w, fwd_bytes,
+                                        s);
+      }
+      if (st != DQ_OK) break;
+      if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        st = DQ_ERR_CUDA;
+        break;
+      }
+      if (dw == 2 && ms / 2.0 < best) {
+        best = ms / 2.0;
+        best_dw = 2;
+      } else if (dw == 4) {
+        best = std::min(best, ms / 2.0);  // the same candidate, timed again
+      }
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   g->rounds = st == DQ_OK ? best_rounds : keep_rounds;
-  for (int m = 0; m < g->n; ++m) g->h[m]->msg_ib = st == DQ_OK ? best_ib : keep_ib;
+  for (int m = 0; m < g->n; ++m) {
+    g->h[m]->msg_ib = st == DQ_OK ? best_ib : keep_ib;
+    g->h[m]->det_warps = st == DQ_OK ? best_dw : keep_dw;
+  }
   if (best_ms) *best_ms = best;
   return st;
+}
+
+dq_status dq_multi_tile_set(dq_multi g, int32_t* rounds, int32_t* msg_ib, int32_t* fused_layers,
+                            int32_t* det_warps) {
+  if (!g || !rounds || !msg_ib || !fused_layers || !det_warps) return DQ_ERR_ARG;
+  *rounds = g->rounds;
+  *msg_ib = g->h[0]->msg_ib == 0 ? 8 : g->h[0]->msg_ib;
+  int f = 0;
+  for (int m = 0; m < g->n; ++m) f += use_fused(*g->h[m], true) ? 1 : 0;
+  *fused_layers = f;
+  *det_warps = g->h[0]->det_warps;
+  return DQ_OK;
 }
 
 dq_status dq_multi_tuning(dq_multi g, int32_t* rounds, int32_t* msg_ib) {

@@ -160,6 +160,7 @@ struct dq_handle_s {
   int64_t max_chunk = 4096;
   int msg_ib = 0;  // receivers per warp task of the jet message kernel (FP32 modes: 8 or 4; 0: 8)
   int layer_kernel = 0;  // jet layers: 0 fused kernel where supported, 1 the same, 2 separate kernels
+  int det_warps = 4;     // warps (matrices) per CTA of the grouped determinant kernels: 4 or 2
   // device tables
   double* d_R = nullptr;   // [M][3]
   float* d_Rf = nullptr;   // [M][3]

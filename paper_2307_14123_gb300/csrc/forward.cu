@@ -2668,20 +2668,23 @@ cudaError_t launch_orbital_det_group(const MolFwd<T>* m, int n, cudaStream_t s) 
   Ent ent[kMaxGroup];
   int ne = 0;
   size_t smem = 0;
+  // warps (one matrix each) per CTA, one choice for the launch: the first handle's
+  const int W = (n > 0 && m[0].h->det_warps == 2) ? 2 : 4;
   for (int k = 0; k < n; ++k) {
     const dq_handle_s& h = *m[k].h;
     const FwdDims& d = m[k].d;
     if (d.Bc <= 0) continue;
     const int nmax = h.det_n();
     const int64_t nmat = d.Bc * 2 * d.K;
-    size_t sm = 0;
-    const int tag = det_body_tag<T>(nmax, d.N, d.C, &sm);
-    if (tag == 0 && sm > 200 * 1024) return cudaErrorInvalidConfiguration;  // grouped form: four warps per CTA
+    size_t sm4 = 0;
+    const int tag = det_body_tag<T>(nmax, d.N, d.C, &sm4);
+    if (tag == 0 && sm4 > 200 * 1024) return cudaErrorInvalidConfiguration;  // grouped form: four warps per CTA
+    const size_t sm = sm4 / 4 * W;
     smem = std::max(smem, sm);
     ent[ne++] = Ent{{m[k].b.phi, m[k].b.geo, m[k].params, d.Bc, d.N, d.n_up, d.M, d.K, d.C, d.K * nmax,
                      h.edges.n_all, h.edges.n_ee, h.off.omega[0], h.off.omega[1], h.off.zeta[0], h.off.zeta[1],
                      m[k].b.det, h.d_fp64_count, h.full_det},
-                    blocks(nmat, 4), tag, 0, sm};
+                    blocks(nmat, W), tag, 0, sm};
   }
   if (ne == 0) return cudaSuccess;
   // kernel of each body: 0 the mixed / general group kernel, 1 and 2 the large-block ones
@@ -2701,7 +2704,7 @@ cudaError_t launch_orbital_det_group(const MolFwd<T>* m, int n, cudaStream_t s) 
   }
   // one launch per kernel and occupancy class (see launch_messages_group)
   for (int i = 0; i < ne; ++i) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ent[i].occ, kerns[kind(ent[i].tag)], 128, ent[i].smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ent[i].occ, kerns[kind(ent[i].tag)], 32 * W, ent[i].smem);
     if (e != cudaSuccess) return e;
   }
   bool done[kMaxGroup] = {};
@@ -2719,11 +2722,11 @@ cudaError_t launch_orbital_det_group(const MolFwd<T>* m, int n, cudaStream_t s) 
     e = check_group(g);
     if (e != cudaSuccess) return e;
     if constexpr (sizeof(T) == 4) {
-      if (k == 1) orbital_det_large_group<16><<<(unsigned)g.blocks(), 128, sm, s>>>(g);
-      else if (k == 2) orbital_det_large_group<kDetNRL><<<(unsigned)g.blocks(), 128, sm, s>>>(g);
-      else orbital_det_mixed_group<<<(unsigned)g.blocks(), 128, sm, s>>>(g);
+      if (k == 1) orbital_det_large_group<16><<<(unsigned)g.blocks(), 32 * W, sm, s>>>(g);
+      else if (k == 2) orbital_det_large_group<kDetNRL><<<(unsigned)g.blocks(), 32 * W, sm, s>>>(g);
+      else orbital_det_mixed_group<<<(unsigned)g.blocks(), 32 * W, sm, s>>>(g);
     } else {
-      orbital_det_kernel_group<T><<<(unsigned)g.blocks(), 128, sm, s>>>(g);
+      orbital_det_kernel_group<T><<<(unsigned)g.blocks(), 32 * W, sm, s>>>(g);
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

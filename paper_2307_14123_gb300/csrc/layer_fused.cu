@@ -104,6 +104,14 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, vo
   }
 }
 
+// x rounded to the nearest TF32 value (11 significant bits) by Veltkamp splitting: three FP32
+// operations, ties to even; the low part of a TF32 pair is rounded the same way, so that the
+// tensor cores (which read the top 19 bits of an operand) see it in full.
+__device__ __forceinline__ float tf32_split_hi(float x) {
+  const float t = __fmul_rn(x, 8193.f);
+  return __fsub_rn(t, __fsub_rn(t, x));
+}
+
 // NB: sender slots per spin block (at least the larger block's electron count).
 template <int NB, bool ZC>
 __global__ void __launch_bounds__(LF_THREADS, 1)
@@ -396,12 +404,10 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
                     m.y *= nu;
                     const int orow = (c - c0) * N + i;
                     float2 hi, lo;
-                    float tt = __fmul_rn(m.x, 8193.f);
-                    hi.x = __fsub_rn(tt, __fsub_rn(tt, m.x));
-                    tt = __fmul_rn(m.y, 8193.f);
-                    hi.y = __fsub_rn(tt, __fsub_rn(tt, m.y));
-                    lo.x = __fsub_rn(m.x, hi.x);
-                    lo.y = __fsub_rn(m.y, hi.y);
+                    hi.x = tf32_split_hi(m.x);
+                    hi.y = tf32_split_hi(m.y);
+                    lo.x = tf32_split_hi(__fsub_rn(m.x, hi.x));
+                    lo.y = tf32_split_hi(__fsub_rn(m.y, hi.y));
                     const uint32_t o = (uint32_t)orow * 128u + ((((uint32_t)fp >> 1) ^ (uint32_t)(orow & 7)) << 4) +
                                        ((uint32_t)(fp & 1) << 3);
                     *reinterpret_cast<float2*>(a_hi + o) = hi;
@@ -495,15 +501,12 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
               m.x *= nu;
               m.y *= nu;
               if (writer && e != i) {  // (the receiver's own channels were formed above)
-                // TF32 high part by Veltkamp splitting (round to nearest at 11 significant
-                // bits), low part the exact remainder
+                // TF32 high and low parts, each rounded to 11 significant bits
                 float2 hi, lo;
-                float tt = __fmul_rn(m.x, 8193.f);
-                hi.x = __fsub_rn(tt, __fsub_rn(tt, m.x));
-                tt = __fmul_rn(m.y, 8193.f);
-                hi.y = __fsub_rn(tt, __fsub_rn(tt, m.y));
-                lo.x = __fsub_rn(m.x, hi.x);
-                lo.y = __fsub_rn(m.y, hi.y);
+                hi.x = tf32_split_hi(m.x);
+                hi.y = tf32_split_hi(m.y);
+                lo.x = tf32_split_hi(__fsub_rn(m.x, hi.x));
+                lo.y = tf32_split_hi(__fsub_rn(m.y, hi.y));
                 const uint32_t o = (uint32_t)row * 128u + ((lchunk ^ (uint32_t)(row & 7)) << 4) + lsub;
                 *reinterpret_cast<float2*>(a_hi + o) = hi;
                 *reinterpret_cast<float2*>(a_lo + o) = lo;

@@ -29,8 +29,10 @@ ones, classified from the FP64 oracle before comparing:
   near a node; this class names such walkers by measurement, not by a model.
 
 Such walkers (each listed with sigma_b, rho_b and its smallest distance) must
-still meet bounds ten times looser, and at most 5 % of the walkers (at least one)
-may use the exception.
+still meet bounds ten times looser, or, where the FP32-compiled oracle is given, no
+more than twice that plain FP32 evaluation's own error on the walker when that is
+larger (a walker at the FP32 floor can miss ten times the tolerance in plain FP32
+arithmetic too); at most 5 % of the walkers (at least one) may use the exception.
 """
 from __future__ import annotations
 
@@ -95,10 +97,13 @@ def check_fp32(label, la, sg, el, ref, sens, la_rtol=1e-5, e_atol=1e-4, e_rtol=1
     d_e = np.abs(el - e_ref)
     special = (EPS_ENTRY * sigma > tol_la) | (rho < 1e-6) | (dmin < 1e-3)
     floor = np.zeros(len(la), bool)
+    exc_la, exc_e = 10 * tol_la, 10 * tol_e
     if f32 is not None:
-        floor = (np.abs(np.asarray(f32["logabs"], np.float64) - la_ref) > 0.25 * tol_la) | \
-                (np.abs(np.asarray(f32["e_loc"], np.float64) - e_ref) > 0.25 * tol_e)
+        f_la = np.abs(np.asarray(f32["logabs"], np.float64) - la_ref)
+        f_e = np.abs(np.asarray(f32["e_loc"], np.float64) - e_ref)
+        floor = (f_la > 0.25 * tol_la) | (f_e > 0.25 * tol_e)
         special = special | floor
+        exc_la, exc_e = np.maximum(exc_la, 2 * f_la), np.maximum(exc_e, 2 * f_e)
     miss = (d_la > tol_la) | (d_e > tol_e) | (sg != ref["sign"])
     exc = np.where(miss)[0]
     print(f"{label}: log|psi| max err {d_la.max():.3e} (rel {np.max(d_la / np.maximum(1, np.abs(la_ref))):.2e}), "
@@ -108,10 +113,11 @@ def check_fp32(label, la, sg, el, ref, sens, la_rtol=1e-5, e_atol=1e-4, e_rtol=1
     for b in exc:
         print(f"  exception walker {b}: d log|psi| {d_la[b]:.2e} (tol {tol_la[b]:.2e}), dE {d_e[b]:.2e} "
               f"(tol {tol_e[b]:.2e}), S_b {S[b]:.3g}, sigma_b {sigma[b]:.3g}, rho_b {rho[b]:.3g}, "
-              f"d_min {dmin[b]:.3g}, FP32 floor {bool(floor[b])}, exception class {bool(special[b])}")
+              f"d_min {dmin[b]:.3g}, FP32 floor {bool(floor[b])}, exception class {bool(special[b])}, "
+              f"exception bounds {exc_la[b]:.2e} / {exc_e[b]:.2e}")
     assert np.all(special[exc]), f"{label}: walkers {exc[~special[exc]]} miss the bounds without being near-nodal"
     assert len(exc) <= max(1, max_exception_frac * len(la)), f"{label}: {len(exc)} exceptions"
-    assert np.all(d_la[exc] <= 10 * tol_la[exc]) and np.all(d_e[exc] <= 10 * tol_e[exc])
+    assert np.all(d_la[exc] <= exc_la[exc]) and np.all(d_e[exc] <= exc_e[exc])
     assert np.array_equal(sg[~special], ref["sign"][~special])
     mean_de = abs(float(np.mean(el - e_ref)))
     assert mean_de <= max(e_atol, e_rtol * float(np.mean(S))), (mean_de, float(np.mean(S)))
