@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // 128-byte-swizzled layout carries over) and release it to the MMA warp after a
 // proxy fence.  Three tcgen05.mma.kind::tf32 (K = 8 per instruction) per
 // 8-element slice accumulate into one FP32 accumulator in tensor memory.
-// Warps: 0 TMA, 1 MMA, 2..5 epilogue, 6..9 converter.
+// Warps: 0 TMA, 1 MMA, 2..5 and 10..13 epilogue (column halves), 6..9 converter.
 // ---------------------------------------------------------------------------
 constexpr int T3_BK = 32;                            // FP32 elements per 128-byte row
 constexpr int T3_STAGES = 2;
@@ -225,7 +225,8 @@ constexpr int T3_SUB = 2;                               // 128-row blocks per ti
 constexpr uint32_t T3_TMEM_ALLOC = 2 * T3_SUB * 128;    // double-buffered, T3_SUB accumulators each
 constexpr uint32_t T3_TILE_A = TC_BM * T3_BK * 4;    // 16 KB
 constexpr uint32_t T3_TILE_B = TC_BN * T3_BK * 4;    // 16 KB
-constexpr int T3_THREADS = 320;
+constexpr int T3_THREADS = 320;     // the row-reduction kernel: TMA, MMA, 4 epilogue, 4 converter warps
+constexpr int T3J_THREADS = 448;    // the job-list GEMM: 4 more epilogue warps (10..13)
 
 __global__ void split_tf32_kernel(const float* __restrict__ W, float* __restrict__ big, float* __restrict__ small,
                                   int64_t n) {
@@ -307,7 +308,7 @@ __device__ __forceinline__ void t3_issue(const T3Jobs& jobs, uint8_t* a_dst, uin
 // of the parameter block): TMEM -> registers -> shared-memory transpose -> Y.
 template <int M>
 __device__ __forceinline__ void t3_epi_tile(const T3Jobs& jobs, int64_t tl, uint32_t acc, int q, int lane,
-                                            float (*st)[33]) {
+                                            float (*st)[17], int c_lo, int c_hi, uint64_t* rows_tab) {
   asm volatile("// job %0" ::"n"(M));  // keeps the 16 cases of the switch apart
   const T3Fields& J = jobs.j[M].f;
   const int n_tiles_n = J.n_tiles_n, rb = J.rb, sbk = J.sb, bias_period = J.bias_period, n_out = J.n_out;
@@ -319,6 +320,7 @@ __device__ __forceinline__ void t3_epi_tile(const T3Jobs& jobs, int64_t tl, uint
   const int64_t mp = tl / n_tiles_n;
   const int n0 = (int)(tl % n_tiles_n) * TC_BN;
   const int tr = q * 32 + lane;  // row of the 128-row block
+  const int half = lane >> 4, col = lane & 15;  // store phase: two rows of 16 columns per instruction
 #pragma unroll 1
   for (int h = 0; h < T3_SUB; ++h) {
     const int64_t mb = mp * T3_SUB + h;
@@ -326,18 +328,32 @@ __device__ __forceinline__ void t3_epi_tile(const T3Jobs& jobs, int64_t tl, uint
     const int64_t row = (mb % rb_per_seg) * rb + tr % rb;  // row within the segment
     const bool add_bias = bias != nullptr && (row % bias_period) == 0;
     float* yrow = mb < n_mblk && row < seg_rows && seg < n_seg ? Y + seg * y_seg_stride + row * ldy + n0 : nullptr;
-    for (int c0 = 0; c0 < TC_BN; c0 += 32) {
-      uint32_t vv[32];
-      tmem_ld32(acc + (uint32_t)(h * TC_TMEM_COLS) + (uint32_t)c0, vv);
-      const int n = n0 + c0 + lane;
+    // the warp's 32 row pointers (bit 0: add the bias), read back as shared-memory broadcasts
+    __syncwarp();
+    rows_tab[lane] = reinterpret_cast<uint64_t>(yrow) | (add_bias ? 1ull : 0ull);
+    __syncwarp();
+    for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
+      uint32_t vv[16];
+      tmem_ld16(acc + (uint32_t)(h * TC_TMEM_COLS) + (uint32_t)c0, vv);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) st[lane][j] = __uint_as_float(vv[j]);
+      __syncwarp();
+      const int n = n0 + c0 + col;
       const bool col_ok = n < n_out;
-      store_block_32x32(vv, st, lane, yrow ? yrow + c0 : nullptr, add_bias,
-                        bias != nullptr && col_ok ? bias[n] : 0.f, col_ok, accumulate != 0);
+      const float bn = bias != nullptr && col_ok ? bias[n] : 0.f;
+#pragma unroll 8
+      for (int rr = 0; rr < 32; rr += 2) {
+        const uint64_t e = rows_tab[rr + half];
+        float* y = reinterpret_cast<float*>(e & ~1ull);
+        const float val = st[rr + half][col] + ((e & 1ull) ? bn : 0.f);
+        if (y != nullptr && col_ok) y[c0 + col] = accumulate ? y[c0 + col] + val : val;
+      }
+      __syncwarp();
     }
   }
 }
 
-__global__ void __launch_bounds__(T3_THREADS, 1)
+__global__ void __launch_bounds__(T3J_THREADS, 1)
     gemm_tf32x3_tc_kernel(const __grid_constant__ T3Jobs jobs, unsigned int* __restrict__ status) {
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -353,7 +369,8 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
   uint64_t* acc_empty = acc_full + 2;      // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   __shared__ volatile int s_abort;
-  __shared__ float ep_stage[4][32][33];  // epilogue transpose, one block per epilogue warp
+  __shared__ float ep_stage[8][32][17];  // epilogue transposes, one block per epilogue warp
+  __shared__ uint64_t ep_rows[8][32];     // epilogue row pointers
 
   __shared__ T3Fields sj[kT3MaxJobs];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -372,7 +389,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&acc_full[a], 1);
-      mbar_init(&acc_empty[a], 4);
+      mbar_init(&acc_empty[a], 8);  // one arrival per epilogue warp
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
@@ -474,7 +491,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
         umma_commit(&acc_full[a]);
       }
     }
-  } else if (warp >= 6) {
+  } else if (warp >= 6 && warp < 10) {
     // Converter warps 6..9: split each FP32 X tile into TF32 big (in place) and small.
     const int ct = threadIdx.x - 6 * 32;  // 0..127
     int64_t g = 0;
@@ -511,9 +528,11 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
       }
     }
   } else {
-    // Epilogue warps 2..5: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 of each accumulator.
+    // Epilogue warps 2..5 and 10..13: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 of each
+    // accumulator, columns 0..63 (warps 2..5) or 64..127 (warps 10..13).
     const int q = warp % 4;
-    float(*st)[33] = ep_stage[warp - 2];
+    const int eg = warp >= 10 ? 1 : 0, ei = eg * 4 + (warp - (eg ? 10 : 2));
+    float(*st)[17] = ep_stage[ei];
     int64_t lt = 0;
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x, ++lt) {
       const int a = (int)(lt & 1);
@@ -528,7 +547,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
       const uint32_t acc = tmem + (uint32_t)(a * T3_SUB * TC_TMEM_COLS) + ((uint32_t)(q * 32) << 16);
       switch (jm) {
 #define T3_EPI(M) \
-  case M: t3_epi_tile<M>(jobs, tl, acc, q, lane, st); break;
+  case M: t3_epi_tile<M>(jobs, tl, acc, q, lane, st, 64 * eg, 64 * eg + 64, ep_rows[ei]); break;
         T3_EPI(0) T3_EPI(1) T3_EPI(2) T3_EPI(3) T3_EPI(4) T3_EPI(5) T3_EPI(6) T3_EPI(7)
         T3_EPI(8) T3_EPI(9) T3_EPI(10) T3_EPI(11) T3_EPI(12) T3_EPI(13) T3_EPI(14) T3_EPI(15)
 #undef T3_EPI
@@ -840,7 +859,7 @@ cudaError_t gemm_tf32x3_tc_jobs(const T3JobDesc* d, int n, unsigned int* status,
   auto flush = [&]() -> cudaError_t {
     if (J.n == 0) return cudaSuccess;
     const int64_t grid = tiles < sms ? tiles : sms;
-    gemm_tf32x3_tc_kernel<<<(unsigned)grid, T3_THREADS, smem, s>>>(J, status);
+    gemm_tf32x3_tc_kernel<<<(unsigned)grid, T3J_THREADS, smem, s>>>(J, status);
     J.n = 0;
     tiles = 0;
     return cudaGetLastError();
