@@ -575,6 +575,16 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
       return param_reduce<T>(X, mx, Y, my, rpw, nb, n_o, n_a, Gc, P, poff, ld, mode, part, pl.part_elems, s,
                              use_t3 ? h.d_status : nullptr, done);
     };
+    // a weight gradient X^T Y and the bias gradient sum_r X[r] of the same adjoint X: one pass over X
+    // where the tensor-core reduction runs, else a column-sum launch for the bias
+    auto reduce_wb = [&](const T* X, RowMap mx, const T* Y, RowMap my, int rpw, int n_o, int n_a, int64_t woff,
+                         int ld, int64_t boff) {
+      bool bias_done = false;
+      cudaError_t e = param_reduce<T>(X, mx, Y, my, rpw, nb, n_o, n_a, Gc, P, woff, ld, mode, part, pl.part_elems, s,
+                                      use_t3 ? h.d_status : nullptr, done, boff, &bias_done);
+      if (e == cudaSuccess && !bias_done) e = reduce(X, mx, nullptr, rm(1), rpw, n_o, 1, boff, 1);
+      return e;
+    };
     // ---- forward, keeping activations ----
     FwdBuffers<T> v{};
     v.geo = buf(pl.geo);
@@ -697,8 +707,8 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
       const RowMap mp{(int64_t)ns[sg], (int64_t)N * Wo, Wo};
       const RowMap mf{(int64_t)ns[sg], (int64_t)N * D, D};
       const T* pb = phibar + (int64_t)i0[sg] * Wo;
-      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(pb, mp, F(L) + (int64_t)i0[sg] * D, mf, ns[sg], nc, D, off.W_o[sg], D));
-      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(pb, mp, nullptr, rm(1), ns[sg], nc, 1, off.b_o[sg], 1));
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce_wb(pb, mp, F(L) + (int64_t)i0[sg] * D, mf, ns[sg], nc, D, off.W_o[sg], D,
+                                            off.b_o[sg]));
       // tensor cores when the rows of phi-bar suit the tensor maps (K * n_c and Wo multiples of 4)
       if (use_t3 && nc % 4 == 0 && Wo % 4 == 0)
         DQ_LAUNCH(h, PK_BWD_GEMM,
@@ -714,8 +724,7 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
     for (int l = L - 1; l >= 0; --l) {
       const auto& y = off.layer[l];
       DQ_LAUNCH(h, PK_BWD_UPDATE, launch_tanh_bwd<T>(fbar, U(l), nb * N * D, true, ubar, s));
-      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ubar, rm(D), MS(l), rm(3 * D), N, D, 3 * D, y.W_g, 3 * D));
-      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ubar, rm(D), nullptr, rm(1), N, D, 1, y.b_g, 1));
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce_wb(ubar, rm(D), MS(l), rm(3 * D), N, D, 3 * D, y.W_g, 3 * D, y.b_g));
       if (use_t3)
         DQ_LAUNCH(h, PK_BWD_GEMM,
                   gemm_tf32x3_tc(reinterpret_cast<const float*>(ubar), nb * N, D, D, w3t.wg(l, 0), w3t.wg(l, 1),
@@ -737,8 +746,8 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
         if (ng[t] == 0) continue;
         const RowMap me{(int64_t)ng[t], (int64_t)E * D, D};
         const T* wb = wbar + (int64_t)e0[t] * D;
-        DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(wb, me, EH(l) + (int64_t)e0[t] * D, me, ng[t], D, D, y.W2[t], D));
-        DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(wb, me, nullptr, rm(1), ng[t], D, 1, y.b2[t], 1));
+        DQ_LAUNCH(h, PK_BWD_REDUCE, reduce_wb(wb, me, EH(l) + (int64_t)e0[t] * D, me, ng[t], D, D, y.W2[t], D,
+                                              y.b2[t]));
         if (use_t3)
           DQ_LAUNCH(h, PK_BWD_GEMM,
                     gemm_tf32x3_tc_seg(reinterpret_cast<const float*>(wb), ng[t], nb, (int64_t)E * D, D, D,
@@ -755,8 +764,8 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
         const RowMap me{(int64_t)ng[t], (int64_t)E * D, D};
         const RowMap mq{(int64_t)ng[t], (int64_t)E * Q, Q};
         const T* hb = hbar + (int64_t)e0[t] * D;
-        DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(hb, me, RB(l) + (int64_t)e0[t] * Q, mq, ng[t], D, Q, y.W1[t], Q));
-        DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(hb, me, nullptr, rm(1), ng[t], D, 1, y.b1[t], 1));
+        DQ_LAUNCH(h, PK_BWD_REDUCE, reduce_wb(hb, me, RB(l) + (int64_t)e0[t] * Q, mq, ng[t], D, Q, y.W1[t], Q,
+                                              y.b1[t]));
         if (h.edge_update && l > 0)  // adjoint of this layer's edge embeddings: W1^T h-bar
           DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(hb, me, params + y.W1[t], ebar + (int64_t)e0[t] * Q, mq,
                                              nb * ng[t], Q, D, true, s));
@@ -767,20 +776,18 @@ dq_status run_grad(const dq_handle_s& h, const T* params, const T* r, int64_t B,
           if (ng[t] == 0) continue;
           const RowMap mq{(int64_t)ng[t], (int64_t)E * Q, Q};
           const T* ab = abar + (int64_t)e0[t] * Q;
-          DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ab, mq, RB(l - 1) + (int64_t)e0[t] * Q, mq, ng[t], Q, Q, y.U[t], Q));
-          DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ab, mq, nullptr, rm(1), ng[t], Q, 1, y.c[t], 1));
+          DQ_LAUNCH(h, PK_BWD_REDUCE, reduce_wb(ab, mq, RB(l - 1) + (int64_t)e0[t] * Q, mq, ng[t], Q, Q, y.U[t], Q,
+                                                y.c[t]));
         }
       }
     }
     if (h.el_init) {  // through f^0 = W_e2 tanh(W_e1 x + b_e1) + b_e2 (Eq. 13, second case)
       const int M3 = 3 * M;
       T* H0 = buf(pl.h0);
-      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(fbar, rm(D), H0, rm(D), N, D, D, off.W_e2, D));
-      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(fbar, rm(D), nullptr, rm(1), N, D, 1, off.b_e2, 1));
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce_wb(fbar, rm(D), H0, rm(D), N, D, D, off.W_e2, D, off.b_e2));
       DQ_LAUNCH(h, PK_BWD_GEMM, gemm_nn<T>(fbar, rm(D), params + off.W_e2, ubar, rm(D), nb * N, D, D, false, s));
       DQ_LAUNCH(h, PK_BWD_UPDATE, launch_tanh_bwd<T>(ubar, H0, nb * N * D, false, ubar, s));
-      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ubar, rm(D), buf(pl.x0), rm(M3), N, D, M3, off.W_e1, M3));
-      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce(ubar, rm(D), nullptr, rm(1), N, D, 1, off.b_e1, 1));
+      DQ_LAUNCH(h, PK_BWD_REDUCE, reduce_wb(ubar, rm(D), buf(pl.x0), rm(M3), N, D, M3, off.W_e1, M3, off.b_e1));
     } else {
       for (int sg = 0; sg < 2; ++sg) {
         if (ns[sg] == 0) continue;

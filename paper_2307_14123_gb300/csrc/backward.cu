@@ -864,18 +864,24 @@ inline bool walker_rows(RowMap m, int rpw, int64_t* pitch, int64_t* wstride) {
 template <class T>
 cudaError_t param_reduce(const T* X, RowMap mx, const T* Y, RowMap my, int rpw, int64_t nw, int n_o, int n_a, T* G,
                          int64_t P, int64_t off, int ld, int mode, T* part, int64_t part_elems, cudaStream_t s,
-                         unsigned int* tc_status, unsigned int* done) {
+                         unsigned int* tc_status, unsigned int* done, int64_t boff, bool* bias_done) {
+  if (bias_done) *bias_done = false;
   if (nw <= 0 || n_o <= 0 || n_a <= 0) return cudaSuccess;
   if (rpw <= 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
     int64_t xp, xs, yp, ys, splits = 0;
     if (tc_status != nullptr && mode == 0 && Y != nullptr && n_o >= 64 && n_a >= 16 &&
         walker_rows(mx, rpw, &xp, &xs) && walker_rows(my, rpw, &yp, &ys)) {
+      float* colpart = nullptr;
       const cudaError_t e = gemm_tn_tf32x3(X, xp, xs, Y, yp, ys, rpw, nw, n_o, n_a, part, part_elems, &splits,
-                                           tc_status, s);
+                                           tc_status, s, boff >= 0 && bias_done ? &colpart : nullptr);
       if (e == cudaSuccess && splits > 0) {
         const int64_t per = (int64_t)n_o * n_a;
         reduce_splits_kernel<T><<<nblocks(per, 256), 256, 0, s>>>(part, (int)splits, n_o, n_a, G, off, ld);
+        if (colpart != nullptr) {
+          reduce_splits_kernel<T><<<nblocks(n_o, 256), 256, 0, s>>>(colpart, (int)splits, n_o, 1, G, boff, 1);
+          *bias_done = true;
+        }
         return cudaGetLastError();
       }
       if (e != cudaErrorInvalidValue) return e;  // unsupported layout: the CUDA-core path below
@@ -971,7 +977,7 @@ cudaError_t launch_msg_bwd(const dq_handle_s& h, int64_t Bc, const T* mbar, cons
   template cudaError_t gemm_nn<T>(const T*, RowMap, const T*, T*, RowMap, int64_t, int, int, bool, cudaStream_t); \
   template cudaError_t param_reduce<T>(const T*, RowMap, const T*, RowMap, int, int64_t, int, int, T*, int64_t,   \
                                        int64_t, int, int, T*, int64_t, cudaStream_t, unsigned int*,              \
-                                       unsigned int*);                                                            \
+                                       unsigned int*, int64_t, bool*);                                            \
   template cudaError_t launch_tanh_bwd<T>(const T*, const T*, int64_t, bool, T*, cudaStream_t);                   \
   template cudaError_t launch_add_rows<T>(T*, const T*, int64_t, int, int, cudaStream_t);                         \
   template cudaError_t launch_edge_update_bwd<T>(const dq_handle_s&, int64_t, int, const T*, const T*, T*, T*,    \

@@ -22,10 +22,13 @@ cudaError_t gemm_nn(const T* X, RowMap mx, const T* W, T* Y, RowMap my, int64_t 
 // kColsumReduceCounters zeroed counters (left zeroed) with which summed-mode column sums add their
 // splits in their last CTA instead of a second launch.
 constexpr int kColsumReduceCounters = 64;
+// boff >= 0: also the bias-type gradient G[boff + o] = sum_r X[r][o] where the tensor-core path runs
+// (its column sums ride on the same pass over X); *bias_done tells whether it was formed.
 template <class T>
 cudaError_t param_reduce(const T* X, RowMap mx, const T* Y, RowMap my, int rpw, int64_t nw, int n_o, int n_a, T* G,
                          int64_t P, int64_t off, int ld, int mode, T* part, int64_t part_elems, cudaStream_t s,
-                         unsigned int* tc_status = nullptr, unsigned int* done = nullptr);
+                         unsigned int* tc_status = nullptr, unsigned int* done = nullptr, int64_t boff = -1,
+                         bool* bias_done = nullptr);
 template <class T>
 cudaError_t launch_tanh_bwd(const T* g, const T* u, int64_t n, bool is_pre, T* out, cudaStream_t s);
 template <class T>

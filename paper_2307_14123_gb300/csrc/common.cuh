@@ -264,9 +264,12 @@ cudaError_t split_tf32_t(const float* W, int rows, int cols, float* big, float* 
 // Row reduction part[split][o][a] = sum_r X[r][o] Y[r][a] on the tensor cores (3 x TF32); rows in n_seg
 // segments of rps rows (row pitch, segment stride in elements; multiples of 4, 16-byte aligned bases).
 // The split count (every split non-empty, splits * n_o * n_a <= part_elems) is returned in splits_out.
+// colpart_out non-null: the column sums of X per split as well (colpart[split][o], placed after the
+// partial tiles in part, counted in part_elems), their address returned in *colpart_out.
 cudaError_t gemm_tn_tf32x3(const float* X, int64_t x_pitch, int64_t x_seg_stride, const float* Y, int64_t y_pitch,
                            int64_t y_seg_stride, int64_t rps, int64_t n_seg, int n_o, int n_a, float* part,
-                           int64_t part_elems, int64_t* splits_out, unsigned int* status, cudaStream_t s);
+                           int64_t part_elems, int64_t* splits_out, unsigned int* status, cudaStream_t s,
+                           float** colpart_out = nullptr);
 
 // ---- forward kernels (forward.cu) ------------------------------------------
 // Sizes of one chunk of Bc walkers; C = channels (1 value-only, 3N+2 with jets).

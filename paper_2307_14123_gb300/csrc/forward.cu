@@ -1008,11 +1008,12 @@ __global__ void to_bf16_kernel(const float* __restrict__ src, __nv_bfloat16* __r
 // pivoted LU), decides whether that is accurate enough: near-nodal matrices
 // (kappa above the threshold) are redone in FP64.  The local-energy path
 // needs the determinant derivatives (tangent contractions with A^-1), whose
-// plain FP32 rounding doubles the error of E_loc at near-nodal walkers: it
-// factorises every matrix in FP64 and, in the FP32 modes, contracts the
-// tangents in double-float arithmetic on the FP32 pipes, because FP64
-// instructions issue at a small fraction of the FP32 rate on this GPU.  In
-// FP64 mode every step is FP64.
+// plain FP32 rounding doubles the error of E_loc at near-nodal walkers: the
+// FP32 jet bodies below (blocks of up to 28 electrons) refine the FP32
+// inverse to a double-float pair and contract the tangents in double-float
+// arithmetic on the FP32 pipes, because FP64 instructions issue at a small
+// fraction of the FP32 rate on this GPU; the general body here takes FP64 for
+// larger blocks.  In FP64 mode every step is FP64.
 // ---------------------------------------------------------------------------
 #ifndef DQ_KAPPA_FP32_VALUE
 #define DQ_KAPPA_FP32_VALUE 10000.0f  // value-only log|det| in FP32 (corrected) below this

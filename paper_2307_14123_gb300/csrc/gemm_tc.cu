@@ -574,7 +574,10 @@ __global__ void __launch_bounds__(T3J_THREADS, 1)
 // them into the K-major 128-byte-swizzled layout of the MMA operands while
 // splitting into TF32 high and low parts.  Work items are (o tile, a tile,
 // split); each writes its partial tile, and reduce_splits adds the splits in
-// a fixed order.
+// a fixed order.  With colpart, the converter threads also sum the X columns
+// they transpose (FP32, rows in order) and the a-tile-0 items write
+// colpart[split][o] = sum over the split's rows of X[r][o]: the bias-type
+// gradient of the same adjoint, without a second pass over X.
 // Warps: 0 TMA, 1 MMA, 2..5 epilogue, 6..9 converter.
 // ---------------------------------------------------------------------------
 constexpr int TN_BK = 32;                                  // rows per K step
@@ -584,7 +587,7 @@ constexpr int TN_TSTAGES = 2, TN_OSTAGES = 2;
 __global__ void __launch_bounds__(T3_THREADS, 1)
     gemm_tn_tf32x3_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmY,
                           int64_t rps, int64_t n_seg, int rb, int n_o, int n_a, int64_t splits, int64_t kps,
-                          float* __restrict__ part, unsigned int* __restrict__ status) {
+                          float* __restrict__ part, float* __restrict__ colpart, unsigned int* __restrict__ status) {
   extern __shared__ __align__(1024) uint8_t tc_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* sT = smem;                                   // [tstage][X tile, Y tile] as loaded: [32 rows][128]
@@ -713,6 +716,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
       int m0, n0;
       int64_t sp, k0, k1;
       item_range(it, m0, n0, sp, k0, k1);
+      float csum = 0.f;  // sum of this thread's X column over the item's rows
       for (int64_t ks = k0; ks < k1; ++ks, ++g) {
         const int ts = (int)(g % TN_TSTAGES), os = (int)(g % TN_OSTAGES);
         if (!mbar_wait(&full[ts], (uint32_t)((g / TN_TSTAGES) & 1)) ||
@@ -730,9 +734,13 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
             float4 h, l;
             float x;
             x = src[(4 * rq + 0) * TC_BM + col]; h.x = tf32_rn(x); l.x = tf32_rn(x - h.x);
+            if (op == 0) csum += x;
             x = src[(4 * rq + 1) * TC_BM + col]; h.y = tf32_rn(x); l.y = tf32_rn(x - h.y);
+            if (op == 0) csum += x;
             x = src[(4 * rq + 2) * TC_BM + col]; h.z = tf32_rn(x); l.z = tf32_rn(x - h.z);
+            if (op == 0) csum += x;
             x = src[(4 * rq + 3) * TC_BM + col]; h.w = tf32_rn(x); l.w = tf32_rn(x - h.w);
+            if (op == 0) csum += x;
             // K-major, 128-byte swizzle: row col, 16-byte chunk rq at chunk rq ^ (col % 8)
             const uint32_t off = (uint32_t)col * 128u + ((uint32_t)(rq ^ (col & 7)) << 4);
             *reinterpret_cast<float4*>(hi + off) = h;
@@ -746,6 +754,7 @@ __global__ void __launch_bounds__(T3_THREADS, 1)
           asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tfree[ts])) : "memory");
         }
       }
+      if (colpart != nullptr && n0 == 0 && m0 + col < n_o && !s_abort) colpart[sp * n_o + m0 + col] = csum;
     }
   } else {
     // Epilogue warps 2..5: rows o, columns a of the partial tile
@@ -932,7 +941,8 @@ constexpr size_t tn_smem_bytes() {
 
 cudaError_t gemm_tn_tf32x3(const float* X, int64_t x_pitch, int64_t x_seg_stride, const float* Y, int64_t y_pitch,
                            int64_t y_seg_stride, int64_t rps, int64_t n_seg, int n_o, int n_a, float* part,
-                           int64_t part_elems, int64_t* splits_out, unsigned int* status, cudaStream_t s) {
+                           int64_t part_elems, int64_t* splits_out, unsigned int* status, cudaStream_t s,
+                           float** colpart_out) {
   *splits_out = 0;
   if (rps <= 0 || n_seg <= 0 || n_o <= 0 || n_a <= 0) return cudaSuccess;
   if (x_pitch % 4 || y_pitch % 4 || x_seg_stride % 4 || y_seg_stride % 4 || (uintptr_t)X % 16 || (uintptr_t)Y % 16 ||
@@ -951,19 +961,25 @@ cudaError_t gemm_tn_tf32x3(const float* X, int64_t x_pitch, int64_t x_seg_stride
   const int64_t ktot = ((n_seg + TN_BK / rb - 1) / (TN_BK / rb)) * ((rps + rb - 1) / rb);
   int64_t splits = (sms + tiles - 1) / tiles;  // about one work item per SM
   if (splits > ktot) splits = ktot;
-  if (splits * n_o * n_a > part_elems) splits = part_elems / ((int64_t)n_o * n_a);
+  // per split: the partial tile, and with column sums one partial row of n_o
+  const int64_t per_split = (int64_t)n_o * n_a + (colpart_out ? n_o : 0);
+  if (splits * per_split > part_elems) splits = part_elems / per_split;
   if (splits < 1) return cudaErrorInvalidValue;
   const int64_t kps = (ktot + splits - 1) / splits;
   splits = (ktot + kps - 1) / kps;  // every split has at least one K step
+  float* colpart = colpart_out ? part + splits * (int64_t)n_o * n_a : nullptr;
   const size_t smem = tn_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(gemm_tn_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t items = tiles * splits;
   const int64_t grid = items < sms ? items : sms;
   gemm_tn_tf32x3_kernel<<<(unsigned)grid, T3_THREADS, smem, s>>>(mx, my, rps, n_seg, rb, n_o, n_a, splits, kps, part,
-                                                                status);
+                                                                colpart, status);
   e = cudaGetLastError();
-  if (e == cudaSuccess) *splits_out = splits;
+  if (e == cudaSuccess) {
+    *splits_out = splits;
+    if (colpart_out) *colpart_out = colpart;
+  }
   return e;
 }
 
