@@ -1062,6 +1062,46 @@ def main():
                     "note": "same workload, Langevin sampler (Sec. 5) instead of random-walk Metropolis; "
                             "L2 flushed before every step"}
 
+    # the same Metropolis chain with E_loc carried: proposals evaluated by the jets forward
+    # (mcmc_step_eloc), one forward per step instead of the value-only forward + local_energy
+    metro_eloc = None
+    if not args.no_mala:
+        r_e = r.clone()
+        la_e, _, e_e = h.local_energy(theta, r_e)
+        ectr = torch.zeros(1, dtype=torch.int64, device=dev)
+
+        def estep():
+            n = h.mcmc_step_eloc(theta, r_e, la_e, e_e, 1, step_size, wl.walker_seed, ectr)
+            w, stats = h.vmc_loss_weights(e_e, 5.0)
+            g = h.grad_logpsi(theta, r_e, w, 0) if with_grad else None
+            return n
+
+        for _ in range(args.warmup):
+            estep()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        eev, e_acc = [], torch.zeros(1, dtype=torch.int64, device=dev)
+        for _ in range(args.steps):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            n = estep()
+            b.record()
+            e_acc += n
+            eev.append((a, b))
+        torch.cuda.synchronize()
+        t5 = torch.tensor([sum(a.elapsed_time(b) for a, b in eev)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t5, op=dist.ReduceOp.MAX)
+        ems = float(t5.item())
+        metro_eloc = {"value": B * world * args.steps / (ems / 1e3), "unit": UNIT, "ms_per_step": ems / args.steps,
+                      "acceptance": int(e_acc.item()) / (B * args.steps),
+                      "step": "mcmc_step_eloc(1 Metropolis sweep, proposals through the jets forward, E_loc "
+                              "carried) + vmc_loss_weights" + (" + grad_logpsi(weighted)" if with_grad else ""),
+                      "note": "the headline step's Metropolis chain and outputs with one forward per walker; "
+                              "L2 flushed before every step"}
+
     natgrad = natgrad_leg(h, theta, r, wl, args, flush) if (world == 1 and with_grad and not args.no_natgrad) else None
     batched = batch_leg(args, dev, flush) if (world == 1 and not args.no_batch) else None
     training = training_leg(dev) if (world == 1 and not args.no_natgrad) else None
@@ -1087,6 +1127,7 @@ def main():
                 "parity_vs_oracle": parity, "e2e": e2e,
                 "cuda_graph": graph,
                 "langevin_sampler": langevin,
+                "metropolis_eloc_carried": metro_eloc,
                 "batched_molecules": batched,
                 "natural_gradient": natgrad,
                 "vmc_training": training,

@@ -204,6 +204,27 @@ dq_status mcmc_step_dev(dq_handle h, const void* params, void* r, void* logabs, 
                         double step_size, uint64_t seed, uint64_t* step_counter, int64_t* n_accepted, void* ws,
                         size_t ws_bytes, void* stream);
 
+/* mcmc_step_eloc: mcmc_step (the same Gaussian proposals of step_size, the
+ * same uniforms and acceptance rule of step t = step_counter + s) whose
+ * proposals are evaluated with value, 3N first derivatives and Laplacian
+ * propagated together, as in local_energy, so that the local energy is carried
+ * with every walker: after the call e_loc holds E_loc at the final positions,
+ * and a VMC step needs one forward per walker instead of mcmc_step's value-only
+ * forward followed by local_energy (no counterpart in the paper, which
+ * evaluates the local energy after sampling; the sampled chain is the same).
+ *   r        [B][N][3] in/out    positions
+ *   logabs   [B]       in/out    log|psi| of r as local_energy gives it (the
+ *                                acceptance compares it with the proposals'
+ *                                log|psi| from the same forward)
+ *   e_loc    [B]       in/out    E_loc at r, carried with r
+ *   step_counter_dev   nullable, device uint64: read (step_counter ignored)
+ *                      and advanced by n_steps, as in mcmc_step_dev
+ *   n_accepted         nullable, device int64: accepted moves of this call
+ * Workspace: dq_workspace_size(op = DQ_OP_MALA).  Asynchronous on `stream`. */
+dq_status mcmc_step_eloc(dq_handle h, const void* params, void* r, void* logabs, void* e_loc, int64_t B,
+                         int32_t n_steps, double step_size, uint64_t seed, uint64_t step_counter,
+                         uint64_t* step_counter_dev, int64_t* n_accepted, void* ws, size_t ws_bytes, void* stream);
+
 /* mala_step: n_steps Metropolis-adjusted Langevin steps (Sec. 5, the Langevin
  * sampler) on B walkers.  The paper names a correction that shortens electron
  * steps near the nuclei without giving it; here the drift of electron i,

@@ -39,7 +39,7 @@ EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_
            "ansatz_eval_multi", "local_energy_multi", "mcmc_step_multi", "grad_logpsi_multi",
            "vmc_loss_weights_multi", "dq_autotune_multi", "dq_multi_tuning", "dq_set_msg_tile", "dq_msg_tile", "dq_autotune", "natural_gradient", "param_update", "dq_pp_workspace_size",
            "pseudopotential_energy", "dq_fma_rate_probe", "dq_set_layer_kernel", "dq_layer_kernel",
-           "dq_set_det_warps", "dq_tile_set", "dq_multi_tile_set"]
+           "dq_set_det_warps", "dq_tile_set", "dq_multi_tile_set", "mcmc_step_eloc"]
 
 
 class DQError(RuntimeError):
@@ -90,6 +90,7 @@ def load_library(path=None):
         lib.mcmc_step.argtypes = [P, P, P, P, i64, i32, f64, u64, u64, P, P, sz, P]
         lib.mcmc_step_dev.argtypes = [P, P, P, P, i64, i32, f64, u64, P, P, P, sz, P]
         lib.mala_step.argtypes = [P, P, P, P, P, P, i32, i64, i32, f64, u64, u64, P, P, P, sz, P]
+        lib.mcmc_step_eloc.argtypes = [P, P, P, P, P, i64, i32, f64, u64, u64, P, P, P, sz, P]
         lib.grad_logpsi.argtypes = [P, P, P, i64, P, i32, P, P, sz, P]
         lib.vmc_loss_weights.argtypes = [P, P, i64, f64, P, P, P, sz, P]
         lib.vmc_loss_weights_noalloc.argtypes = [P, P, i64, f64, P, P, P]
@@ -366,6 +367,31 @@ class Ansatz:
         _check(self.lib.mala_step(self.h, _ptr(params), _ptr(r), _ptr(logabs), _ptr(grad), _ptr(e_loc),
                                   1 if grad_valid else 0, B, int(n_steps), float(tau), int(seed) & 0xFFFFFFFFFFFFFFFF,
                                   int(step_counter), _ptr(dev_ctr), _ptr(n_acc), _ptr(ws), ws.numel(), self._stream()))
+        return n_acc
+
+    def mcmc_step_eloc(self, params, r, logabs, e_loc, n_steps=1, step_size=0.2, seed=0, step_counter=0):
+        """In-place Metropolis update of device tensors r, logabs and e_loc whose proposals are
+        evaluated with the jets forward (mcmc_step's proposals, uniforms and acceptance, E_loc
+        carried with the positions).  logabs and e_loc must be local_energy's values at r.
+        Returns the accepted count (device int64).  step_counter: an int, or a one-element int64
+        CUDA tensor (read on the device and advanced by n_steps)."""
+        params = self._dev(params, shape=(self.P,))
+        for t in (r, logabs, e_loc):
+            if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous():
+                raise DQError("mcmc_step_eloc updates r, logabs and e_loc in place: pass contiguous device tensors")
+        B = r.numel() // (3 * self.N)
+        if logabs.numel() != B or e_loc.numel() != B:
+            raise DQError("logabs and e_loc hold one value per walker")
+        n_acc = torch.empty(1, dtype=torch.int64, device=self.device)
+        ws = self.workspace(B, OP_MALA)
+        dev_ctr = None
+        if isinstance(step_counter, torch.Tensor):
+            if step_counter.device != self.device or step_counter.dtype != torch.int64 or step_counter.numel() != 1:
+                raise DQError("a device step counter is a one-element int64 tensor on the handle's device")
+            dev_ctr, step_counter = step_counter, 0
+        _check(self.lib.mcmc_step_eloc(self.h, _ptr(params), _ptr(r), _ptr(logabs), _ptr(e_loc), B, int(n_steps),
+                                       float(step_size), int(seed) & 0xFFFFFFFFFFFFFFFF, int(step_counter),
+                                       _ptr(dev_ctr), _ptr(n_acc), _ptr(ws), ws.numel(), self._stream()))
         return n_acc
 
     def grad_logpsi(self, params, r, weights=None, mode=0):

@@ -836,6 +836,32 @@ dq_status run_mcmc(dq_handle h, const T* params, T* r, T* logabs, int64_t B, int
   return DQ_OK;
 }
 
+// Metropolis steps whose proposals are evaluated by the jets forward: the same proposals, uniforms
+// and acceptance as run_mcmc, with the proposal's local energy carried to accepted walkers.
+template <class T>
+dq_status run_mcmc_eloc(dq_handle h, const T* params, T* r, T* logabs, T* e_loc, int64_t B, int32_t n_steps,
+                        double step, uint64_t seed, uint64_t t0, uint64_t* t_dev, int64_t* n_acc, unsigned char* ws,
+                        size_t ws_bytes, cudaStream_t s) {
+  const MalaPlan plan = plan_mala(*h, B, sizeof(T));
+  if (ws == nullptr || ws_bytes < plan.total || !aligned(ws, kAlign)) return DQ_ERR_WORKSPACE;
+  T* r_prop = reinterpret_cast<T*>(ws + plan.r_prop);
+  T* la_prop = reinterpret_cast<T*>(ws + plan.la_prop);
+  int8_t* sg_prop = reinterpret_cast<int8_t*>(ws + plan.sign_prop);
+  T* e_prop = reinterpret_cast<T*>(ws + plan.e_prop);
+  if (n_acc) DQ_CU(cudaMemsetAsync(n_acc, 0, sizeof(int64_t), s));
+  for (int32_t k = 0; k < n_steps; ++k) {
+    const uint64_t t = t0 + (uint64_t)k;
+    DQ_LAUNCH(*h, PK_PROPOSE, launch_propose<T>(*h, B, r, r_prop, step, seed, t, t_dev, s));
+    dq_status st = run_forward<T>(*h, params, r_prop, B, true, la_prop, sg_prop, e_prop, ws + plan.fwd,
+                                  ws_bytes - plan.fwd, s);
+    if (st != DQ_OK) return st;
+    DQ_LAUNCH(*h, PK_ACCEPT, launch_accept<T>(*h, B, r, logabs, r_prop, la_prop, sg_prop, seed, t, t_dev,
+                                              reinterpret_cast<unsigned long long*>(n_acc), s, e_loc, e_prop));
+  }
+  if (t_dev && n_steps > 0) DQ_CU(launch_advance_counter(t_dev, (uint64_t)n_steps, s));
+  return DQ_OK;
+}
+
 template <class T>
 dq_status run_mala(dq_handle h, const T* params, T* r, T* logabs, T* grad, T* e_loc, int grad_valid, int64_t B,
                    int32_t n_steps, double tau, uint64_t seed, uint64_t t0, uint64_t* t_dev, int64_t* n_acc,
@@ -1539,6 +1565,28 @@ dq_status mala_step(dq_handle h, const void* params, void* r, void* logabs, void
                             s);
   return run_mala<float>(h, (const float*)params, (float*)r, (float*)logabs, (float*)grad, (float*)e_loc, grad_valid, B,
                          n_steps, tau, seed, step_counter, step_counter_dev, n_accepted, w, ws_bytes, s);
+}
+
+dq_status mcmc_step_eloc(dq_handle h, const void* params, void* r, void* logabs, void* e_loc, int64_t B,
+                         int32_t n_steps, double step_size, uint64_t seed, uint64_t step_counter,
+                         uint64_t* step_counter_dev, int64_t* n_accepted, void* ws, size_t ws_bytes, void* stream) {
+  dq_status st = check_handle(h);
+  if (st != DQ_OK) return st;
+  if (B < 0 || n_steps < 0 || !(step_size >= 0) || !isfinite(step_size)) return DQ_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (B == 0 || n_steps == 0) {
+    if (n_accepted && cudaMemsetAsync(n_accepted, 0, sizeof(int64_t), s) != cudaSuccess) return DQ_ERR_CUDA;
+    if (step_counter_dev && n_steps > 0 && launch_advance_counter(step_counter_dev, (uint64_t)n_steps, s) != cudaSuccess)
+      return DQ_ERR_CUDA;
+    return DQ_OK;
+  }
+  if (!params || !r || !logabs || !e_loc) return DQ_ERR_ARG;
+  auto* w = static_cast<unsigned char*>(ws);
+  if (h->precision == DQ_FP64)
+    return run_mcmc_eloc<double>(h, (const double*)params, (double*)r, (double*)logabs, (double*)e_loc, B, n_steps,
+                                 step_size, seed, step_counter, step_counter_dev, n_accepted, w, ws_bytes, s);
+  return run_mcmc_eloc<float>(h, (const float*)params, (float*)r, (float*)logabs, (float*)e_loc, B, n_steps,
+                              step_size, seed, step_counter, step_counter_dev, n_accepted, w, ws_bytes, s);
 }
 
 dq_status mcmc_step_dev(dq_handle h, const void* params, void* r, void* logabs, int64_t B, int32_t n_steps,

@@ -306,7 +306,7 @@ template <class T>
 cudaError_t launch_accept_group(const dq_handle_s* const* hs, int n, const int64_t* B, T* const* r, T* const* logabs,
                                 const T* const* r_prop, const T* const* la_prop, const int8_t* const* sign_prop,
                                 uint64_t seed, uint64_t t, const uint64_t* t_base, unsigned long long* const* n_acc,
-                                cudaStream_t s);
+                                cudaStream_t s, T* e_loc = nullptr, const T* e_prop = nullptr);
 template <class T>
 cudaError_t launch_esum_group(int n, const T* const* e, const int64_t* B, double* const* out2,
                               unsigned int* const* status, cudaStream_t s);
@@ -402,7 +402,8 @@ cudaError_t launch_propose(const dq_handle_s& h, int64_t B, const T* r, T* r_pro
 template <class T>
 cudaError_t launch_accept(const dq_handle_s& h, int64_t B, T* r, T* logabs, const T* r_prop,
                           const T* logabs_prop, const int8_t* sign_prop, uint64_t seed, uint64_t t,
-                          const uint64_t* t_base, unsigned long long* n_acc, cudaStream_t s);
+                          const uint64_t* t_base, unsigned long long* n_acc, cudaStream_t s, T* e_loc = nullptr,
+                          const T* e_prop = nullptr);
 // *c += n on the device (advances a device-resident step counter).
 cudaError_t launch_advance_counter(uint64_t* c, uint64_t n, cudaStream_t s);
 // Langevin (MALA) proposal and acceptance; g: d log|psi| / d r at r, g_prop at r_prop.

@@ -92,13 +92,16 @@ struct accept_kernel_args {
   uint64_t t;
   const uint64_t* t_base;
   unsigned long long* n_acc;
+  T* e_loc;            // nullable: local energies carried with the positions
+  const T* e_prop;     // the proposals' local energies (with e_loc)
 };
 
 template <class T>
 __device__ __forceinline__ void accept_kernel_body(const int64_t bx_, const int by_, const int64_t nbx_, T* __restrict__ r, T* __restrict__ logabs, const T* __restrict__ r_prop,
                               const T* __restrict__ la_prop, const int8_t* __restrict__ sign_prop, int64_t B, int N3,
                               uint64_t seed, uint64_t t, const uint64_t* __restrict__ t_base,
-                              unsigned long long* __restrict__ n_acc) {
+                              unsigned long long* __restrict__ n_acc, T* __restrict__ e_loc,
+                              const T* __restrict__ e_prop) {
   if (t_base) t += *t_base;
   const int64_t b = (int64_t)bx_ * blockDim.x + threadIdx.x;
   bool acc = false;
@@ -110,6 +113,7 @@ __device__ __forceinline__ void accept_kernel_body(const int64_t bx_, const int 
     if (acc) {
       for (int q = 0; q < N3; ++q) r[b * N3 + q] = r_prop[b * N3 + q];
       logabs[b] = la_prop[b];
+      if (e_loc) e_loc[b] = e_prop[b];
     }
   }
   const unsigned m = __ballot_sync(0xffffffffu, acc);
@@ -122,7 +126,7 @@ __global__ void accept_kernel_group(const __grid_constant__ Grp<accept_kernel_ar
   int64_t l_;
   const int m_ = grp_find(g, blockIdx.x, l_);
   GRP_STATIC(m_, const auto& a_ = g.a[K_];
-             accept_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.r, a_.logabs, a_.r_prop, a_.la_prop, a_.sign_prop, a_.B, a_.N3, a_.seed, a_.t, a_.t_base, a_.n_acc);)
+             accept_kernel_body<T>(grp_bx(g, K_, l_), grp_by(g, K_, l_), g.nbx[K_], a_.r, a_.logabs, a_.r_prop, a_.la_prop, a_.sign_prop, a_.B, a_.N3, a_.seed, a_.t, a_.t_base, a_.n_acc, a_.e_loc, a_.e_prop);)
 }
 
 // ---------------------------------------------------------------------------
@@ -396,10 +400,10 @@ cudaError_t launch_advance_counter(uint64_t* c, uint64_t n, cudaStream_t s) {
 template <class T>
 cudaError_t launch_accept(const dq_handle_s& h, int64_t B, T* r, T* logabs, const T* r_prop, const T* logabs_prop,
                           const int8_t* sign_prop, uint64_t seed, uint64_t t, const uint64_t* t_base,
-                          unsigned long long* n_acc, cudaStream_t s) {
+                          unsigned long long* n_acc, cudaStream_t s, T* e_loc, const T* e_prop) {
   const dq_handle_s* hp = &h;
   return launch_accept_group<T>(&hp, 1, &B, &r, &logabs, &r_prop, &logabs_prop, &sign_prop, seed, t, t_base, &n_acc,
-                                s);
+                                s, e_loc, e_prop);
 }
 
 template <class T>
@@ -436,13 +440,13 @@ template <class T>
 cudaError_t launch_accept_group(const dq_handle_s* const* hs, int n, const int64_t* B, T* const* r, T* const* logabs,
                                 const T* const* r_prop, const T* const* la_prop, const int8_t* const* sign_prop,
                                 uint64_t seed, uint64_t t, const uint64_t* t_base, unsigned long long* const* n_acc,
-                                cudaStream_t s) {
+                                cudaStream_t s, T* e_loc, const T* e_prop) {
   if (n > kMaxGroup) return cudaErrorInvalidValue;
   Grp<accept_kernel_args<T>> g{};
   for (int k = 0; k < n; ++k) {
     if (B[k] <= 0) continue;
     g.add({r[k], logabs[k], r_prop[k], la_prop[k], sign_prop[k], B[k], 3 * hs[k]->N, seed, t, t_base,
-           n_acc ? n_acc[k] : nullptr},
+           n_acc ? n_acc[k] : nullptr, n == 1 ? e_loc : nullptr, n == 1 ? e_prop : nullptr},
           (B[k] + 255) / 256);
   }
   if (g.n == 0) return cudaSuccess;
@@ -485,7 +489,7 @@ cudaError_t launch_loss_weights_group(int n, const T* const* e, const int64_t* B
   template cudaError_t launch_accept_group<T>(const dq_handle_s* const*, int, const int64_t*, T* const*, T* const*, \
                                               const T* const*, const T* const*, const int8_t* const*, uint64_t,   \
                                               uint64_t, const uint64_t*, unsigned long long* const*,             \
-                                              cudaStream_t);                                                      \
+                                              cudaStream_t, T*, const T*);                                        \
   template cudaError_t launch_esum_group<T>(int, const T* const*, const int64_t*, double* const*,                  \
                                             unsigned int* const*, cudaStream_t);                                  \
   template cudaError_t launch_loss_weights_group<T>(int, const T* const*, const int64_t*, double, T* const*,       \
@@ -497,7 +501,8 @@ DQ_INST_GROUP(double)
   template cudaError_t launch_propose<T>(const dq_handle_s&, int64_t, const T*, T*, double, uint64_t, uint64_t,    \
                                          const uint64_t*, cudaStream_t);                                          \
   template cudaError_t launch_accept<T>(const dq_handle_s&, int64_t, T*, T*, const T*, const T*, const int8_t*,    \
-                                        uint64_t, uint64_t, const uint64_t*, unsigned long long*, cudaStream_t);  \
+                                        uint64_t, uint64_t, const uint64_t*, unsigned long long*, cudaStream_t,   \
+                                        T*, const T*);                                                            \
   template cudaError_t launch_mala_propose<T>(const dq_handle_s&, int64_t, const T*, const T*, T*, T*, double,      \
                                               uint64_t, uint64_t, const uint64_t*, cudaStream_t);                 \
   template cudaError_t launch_mala_accept<T>(const dq_handle_s&, int64_t, T*, T*, T*, const T*, const T*,          \
