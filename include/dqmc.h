@@ -216,7 +216,9 @@ dq_status mcmc_step_dev(dq_handle h, const void* params, void* r, void* logabs, 
  *   logabs   [B]       in/out    log|psi| of r as local_energy gives it (the
  *                                acceptance compares it with the proposals'
  *                                log|psi| from the same forward)
- *   e_loc    [B]       in/out    E_loc at r, carried with r
+ *   e_loc    [B]       in/out    E_loc at r, carried with r; valid only while
+ *                                params do not change (after a parameter update,
+ *                                recompute logabs and e_loc with local_energy)
  *   step_counter_dev   nullable, device uint64: read (step_counter ignored)
  *                      and advanced by n_steps, as in mcmc_step_dev
  *   n_accepted         nullable, device int64: accepted moves of this call
@@ -246,7 +248,8 @@ dq_status mcmc_step_eloc(dq_handle h, const void* params, void* r, void* logabs,
  *                                logabs and grad at r
  *   e_loc    [B]       in/out    nullable: E_loc at r (as from local_energy),
  *                                carried with r (the proposal's evaluation
- *                                gives E_loc at r' at no extra cost);
+ *                                gives E_loc at r' at no extra cost; valid
+ *                                while params do not change);
  *                                computed with grad when grad_valid = 0
  *   step_counter_dev   nullable, device uint64: if given, the step counter is
  *                      read from it (step_counter ignored) and advanced by
