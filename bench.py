@@ -640,8 +640,9 @@ def bf16_leg(h, theta, r, wl, flush, reps=5):
                             "fp32_value": B / (ms32 / 1e3), "bf16_value": B / (ms16 / 1e3), "unit": UNIT,
                             "mean_dE_bf16_minus_fp32": float(d.mean()),
                             "stderr": float(d.std() / max(1, d.numel()) ** 0.5),
-                            "note": "random-initialised ansatz; FP32 runs the fused layer kernel, BF16 the "
-                                    "message kernel and BF16 update / node GEMMs"}
+                            "note": "random-initialised ansatz; both modes run the fused layer kernel (FP32: "
+                                    "3 x TF32 update-map products; BF16: BF16 operands, FP32 accumulation) "
+                                    "and BF16 takes the BF16 node-map GEMM"}
     del h32, h16
     system = fx.molecule("LiH")
     cfg = fx.AnsatzCfg(64, 2, 1)

@@ -195,16 +195,17 @@ FwdPlan plan_forward(const dq_handle_s& h, int64_t Bc, bool jets, size_t elem) {
   const bool bf = h.precision == DQ_BF16_MIXED;
   p.F = take(Bc * N * C * D * elem);
   p.Z = take(Bc * N * C * D * elem);
-  // messages; with the fused layer kernel only the electron-nucleus messages of five channels and
-  // their update-map products
-  p.msg = take(bf ? 0 : use_fused(h, jets) ? Bc * N * 11 * D * elem : Bc * N * C * 3 * D * elem);
+  // messages; with the fused layer kernel (both FP32 modes) only the electron-nucleus messages of
+  // five channels and their update-map products
+  const bool fused = use_fused(h, jets);
+  p.msg = take(fused ? Bc * N * 11 * D * elem : bf ? 0 : Bc * N * C * 3 * D * elem);
   p.phi = take(Bc * N * C * K * nmax * elem);
   p.det = take(Bc * 2 * K * (3 * N + 3) * sizeof(double));
   p.js = take(Bc * C * D * elem);
   p.jh = take(Bc * C * D * elem);
   p.z0 = take(2 * D * elem);
-  // BF16 mode: messages and a copy of the embeddings in BF16, BF16 weights
-  p.msg_bf = take(bf ? Bc * N * C * 3 * D * 2 : 0);
+  // BF16 mode: messages (unless fused) and a copy of the embeddings in BF16, BF16 weights
+  p.msg_bf = take(bf && !fused ? Bc * N * C * 3 * D * 2 : 0);
   p.F_bf = take(bf ? Bc * N * C * D * 2 : 0);
   p.W_bf = take(bf ? (size_t)h.L * 4 * D * D * 2 : 0);
   // FP32 mode: TF32 high and low parts of W_g, W_h and the three W2 of every layer
@@ -377,15 +378,21 @@ dq_status run_forward(const dq_handle_s& h, const T* params, const T* r, int64_t
       const int64_t rows = nb * N * C;
       if (use_fused(h, jets)) {  // messages, update map and update in one kernel
         const bool z_const = l == 0 && !h.el_init;
+        // the node map on 3 x TF32 in both modes: the BF16 GEMM gains nothing at K = D once the
+        // update kernel has to write a BF16 copy of the embeddings for it
         if (!z_const)
           DQ_LAUNCH(h, kb + PK_GEMM_NODE, gemm_tf32x3_tc(reinterpret_cast<const float*>(bf.F), rows, D, D, wh_t3(l, 0),
                                                          wh_t3(l, 1), D, nullptr, 1, reinterpret_cast<float*>(bf.Z), D,
                                                          h.d_status, s));
+        // BF16 mode: the electron-electron messages meet W_g as BF16 operands (the electron-nucleus
+        // part stays on the 3 x TF32 GEMM)
         if constexpr (sizeof(T) == 4)
           DQ_LAUNCH(h, kb + PK_LAYER_FUSED,
                     launch_layer_fused(h, d, params, l, z_const, bf.Z, bf.z0, bf.ew, bf.geo, bf.msg, wg_t3(l, 0),
-                                       wg_t3(l, 1), s));
-        DQ_LAUNCH(h, kb + PK_UPDATE, launch_update<T>(h, d, params, z_const, bf, s));
+                                       wg_t3(l, 1), use_tc ? wg_bf(l) : nullptr, s));
+        FwdBuffers<T> bu = bf;
+        bu.F_bf = nullptr;  // no BF16 copy of the embeddings: nothing on this path reads one
+        DQ_LAUNCH(h, kb + PK_UPDATE, launch_update<T>(h, d, params, z_const, bu, s));
         continue;
       }
       if (l == 0 && !h.el_init) {
@@ -1046,7 +1053,7 @@ dq_status run_forward_multi(const dq_multi_s& g, const T* const* params, const T
           const FwdDims& d = mf[m].d;
           if (d.Bc <= 0 || (l == 0 && !h.el_init)) continue;
           const int64_t rows = d.Bc * d.N * d.C;
-          if (use_tc) {
+          if (use_tc && !use_fused(h, jets)) {  // (fused molecules: 3 x TF32, as in their single calls)
             DQ_LAUNCH(H, kb + PK_GEMM_NODE,
                       gemm_bf16_tc(mf[m].b.F_bf, rows, h.D, h.D, Wbf[m] + ((size_t)l * 4 + 3) * h.D * h.D * 2, h.D,
                                    nullptr, 1, reinterpret_cast<float*>(mf[m].b.Z), h.D, H.d_status, s));
@@ -1055,7 +1062,7 @@ dq_status run_forward_multi(const dq_multi_s& g, const T* const* params, const T
                                  w3[m].wh(l, 1), h.D, nullptr, 1, reinterpret_cast<float*>(mf[m].b.Z), h.D, 0, false};
           }
         }
-        if (!use_tc && nj > 0) DQ_LAUNCH(H, kb + PK_GEMM_NODE, gemm_tf32x3_tc_jobs(jd, nj, H.d_status, s));
+        if (nj > 0) DQ_LAUNCH(H, kb + PK_GEMM_NODE, gemm_tf32x3_tc_jobs(jd, nj, H.d_status, s));
       }
       // molecules on the fused layer kernel (as in their single-molecule calls) leave the
       // grouped message, update-map and update launches
@@ -1063,7 +1070,7 @@ dq_status run_forward_multi(const dq_multi_s& g, const T* const* params, const T
       bool fused[kMaxGroup];
       for (int m = 0; m < n; ++m) {
         rest[m] = mf[m];
-        fused[m] = !use_tc && use_fused(*g.h[m], jets) && mf[m].d.Bc > 0;
+        fused[m] = use_fused(*g.h[m], jets) && mf[m].d.Bc > 0;
         if (fused[m]) rest[m].d.Bc = 0;
       }
       DQ_LAUNCH(H, kb + PK_MESSAGES, launch_messages_group<T>(rest, n, l, l == 0, s));
@@ -1092,8 +1099,11 @@ dq_status run_forward_multi(const dq_multi_s& g, const T* const* params, const T
           const bool z_const = l == 0 && !h.el_init;
           DQ_LAUNCH(H, kb + PK_LAYER_FUSED,
                     launch_layer_fused(h, mf[m].d, params[m], l, z_const, mf[m].b.Z, mf[m].b.z0, mf[m].b.ew,
-                                       mf[m].b.geo, mf[m].b.msg, w3[m].wg(l, 0), w3[m].wg(l, 1), s));
-          DQ_LAUNCH(H, kb + PK_UPDATE, launch_update<T>(h, mf[m].d, params[m], z_const, mf[m].b, s));
+                                       mf[m].b.geo, mf[m].b.msg, w3[m].wg(l, 0), w3[m].wg(l, 1),
+                                       use_tc ? Wbf[m] + (size_t)l * 4 * h.D * h.D * 2 : nullptr, s));
+          FwdBuffers<T> bu = mf[m].b;
+          bu.F_bf = nullptr;
+          DQ_LAUNCH(H, kb + PK_UPDATE, launch_update<T>(h, mf[m].d, params[m], z_const, bu, s));
         }
     }
     int nj = 0;

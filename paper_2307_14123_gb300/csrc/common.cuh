@@ -349,15 +349,16 @@ cudaError_t launch_update_group(const MolFwd<T>* m, int n, bool from_spin, cudaS
 
 // The message and update-map part of one jets layer (layer_fused.cu): the electron-electron
 // messages (Eq. 17) as the A operand of the update map W_g on the tensor cores (three TF32
-// products), so that they never reach memory; the electron-nucleus messages, non-zero on five
-// channels per electron, go through W_g's third block apart and are added after.  Writes the pre-activations
-// u = W_g m + b_g into Z in place (the tanh update of Eq. 18 follows as in the separate path).
-// mn: workspace of Bc N 11 D floats.  FP32 mode, D = 128, N <= 16 with at most 8 electrons per
-// spin and 8 nuclei.
+// products; BF16 operands when wg_bf, the BF16 copy of W_g, is given), so that they never reach
+// memory; the electron-nucleus messages, non-zero on five channels per electron, go through W_g's
+// third block apart (3 x TF32) and are added after.  Writes the pre-activations u = W_g m + b_g
+// into Z in place (the tanh update of Eq. 18 follows as in the separate path).  mn: workspace of
+// Bc N 11 D floats.  FP32 and BF16 modes, D = 128, N <= 16 with at most 8 electrons per spin and
+// 8 nuclei.
 bool layer_fused_supported(const dq_handle_s& h);
 cudaError_t launch_layer_fused(const dq_handle_s& h, const FwdDims& d, const float* params, int l, bool z_const,
                                float* Z, const float* z0, const float* ew, const float* geo, float* mn,
-                               const float* wg_hi, const float* wg_lo, cudaStream_t s);
+                               const float* wg_hi, const float* wg_lo, const void* wg_bf, cudaStream_t s);
 template <class T>
 cudaError_t launch_orbital_det_group(const MolFwd<T>* m, int n, cudaStream_t s);
 template <class T>

@@ -1,5 +1,5 @@
 // One graph-convolution layer of the jets forward pass in one kernel (FP32
-// mode): the messages of Eq. 17 with their product-rule Jacobian and
+// and BF16 modes): the messages of Eq. 17 with their product-rule Jacobian and
 // Laplacian channels, the update map W_g of Eq. 18 on the tensor cores, and
 // the residual tanh update with its jet,
 //   f <- f + tanh(u),  J(tanh u) = t' J(u),  L(tanh u) = t' L(u) + t'' sum_k J_k(u)^2,
@@ -15,24 +15,28 @@
 // last), so that the Laplacian cross terms and sum_k J_k(u)^2 accumulate on
 // chip.  K steps: for each edge type t (same spin, opposite spin, nucleus)
 // and 32-feature block, A[row][32] = m_i^t[c][32 features] as three TF32
-// products with the W_g block (hi hi + hi lo + lo hi).
+// products with the W_g block (hi hi + hi lo + lo hi), or in BF16 mode as
+// one product of BF16 operands (FP32 accumulation).
 //
 // Warp roles (16 warps, one CTA per SM, persistent over walkers):
-//   warp 0      TMA: W_g hi/lo blocks and the z slab z_j[c0 .. c0 + G)[32]
-//               of all senders into a 2-stage ring;
-//   warp 1      MMA issue (tcgen05.mma kind::tf32, 128 x 128 x 8) into one
-//               of two tensor-memory accumulators;
+//   warp 0      TMA: W_g hi/lo blocks (BF16: one block) and the z slab
+//               z_j[c0 .. c0 + G)[32] of all senders into a 2-stage ring;
+//   warp 1      MMA issue (tcgen05.mma kind::tf32, 128 x 128 x 8; BF16:
+//               kind::f16, 128 x 128 x 16) into one of two tensor-memory
+//               accumulators;
 //   warps 2-3   idle;
 //   warps 4-7   epilogue: tensor memory -> the pre-activations U in global memory;
 //   warps 8-15  message producers: warp 8 + w owns two receivers of one spin
 //               block (a half-warp each, two features per lane) and writes
 //               their rows of the A block (TF32 high and low parts, 128-byte
-//               swizzle) from the z slab and the filter jets, prefetching the
-//               next K step's filter lines into L2.
+//               swizzle; BF16: one part, 64-byte swizzle) from the z slab and
+//               the filter jets, prefetching the next K step's filter lines
+//               into L2.
 // Every mbarrier wait is bounded (about one second); a timeout sets
 // DQ_FLAG_TIMEOUT, the roles stop issuing work, and the tensor memory is
 // released.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -112,12 +116,38 @@ __device__ __forceinline__ float tf32_split_hi(float x) {
   return __fsub_rn(t, __fsub_rn(t, x));
 }
 
-// NB: sender slots per spin block (at least the larger block's electron count).
-template <int NB, bool ZC>
+// One lane's two messages (features 2 fp and 2 fp + 1 of its K step) into row `row` of the A
+// block.  FP32 mode: TF32 high and low parts, each rounded to 11 significant bits, in two
+// 128-row x 128-byte tiles (128-byte swizzle: 16-byte chunk c of row r at c ^ (r & 7)).  BF16
+// mode: one BF16 pair (round to nearest even) in a 128-row x 64-byte tile (64-byte swizzle:
+// chunk c of row r at c ^ ((r >> 1) & 3)).
+template <bool BF>
+__device__ __forceinline__ void store_a(uint8_t* a_hi, uint8_t* a_lo, int row, int fp, float2 m) {
+  if constexpr (BF) {
+    const uint32_t o = (uint32_t)row * 64u + ((((uint32_t)fp >> 2) ^ (((uint32_t)row >> 1) & 3u)) << 4) +
+                       ((uint32_t)(fp & 3) << 2);
+    *reinterpret_cast<__nv_bfloat162*>(a_hi + o) = __floats2bfloat162_rn(m.x, m.y);
+  } else {
+    float2 hi, lo;
+    hi.x = tf32_split_hi(m.x);
+    hi.y = tf32_split_hi(m.y);
+    lo.x = tf32_split_hi(__fsub_rn(m.x, hi.x));
+    lo.y = tf32_split_hi(__fsub_rn(m.y, hi.y));
+    const uint32_t o = (uint32_t)row * 128u + ((((uint32_t)fp >> 1) ^ (uint32_t)(row & 7)) << 4) +
+                       ((uint32_t)(fp & 1) << 3);
+    *reinterpret_cast<float2*>(a_hi + o) = hi;
+    *reinterpret_cast<float2*>(a_lo + o) = lo;
+  }
+}
+
+// NB: sender slots per spin block (at least the larger block's electron count); ZC: constant
+// node channels (layer 0 with spin embeddings); BF: BF16 operands (one MMA product per K
+// step) instead of the 3 x TF32 products.
+template <int NB, bool ZC, bool BF>
 __global__ void __launch_bounds__(LF_THREADS, 1)
     layer_fused_kernel(const __grid_constant__ LayerFusedArgs a, const __grid_constant__ CUtensorMap map_whi,
                        const __grid_constant__ CUtensorMap map_wlo, const __grid_constant__ CUtensorMap map_z,
-                       unsigned int* __restrict__ status) {
+                       const __grid_constant__ CUtensorMap map_wbf, unsigned int* __restrict__ status) {
   extern __shared__ __align__(1024) uint8_t lf_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(lf_smem_raw) + 1023) & ~(uintptr_t)1023);
   float* accL = reinterpret_cast<float*>(smem + LF_OFF_ACCL);
@@ -195,16 +225,21 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
               break;
             }
             uint8_t* st = smem + s * LF_STAGE;
-            mbar_expect_tx(&full[s], 2 * LF_TILE);
-            tma_load_2d(st + 2 * LF_TILE, &map_whi, t * LF_D + fb * LF_BK, 0, &full[s]);
-            tma_load_2d(st + 3 * LF_TILE, &map_wlo, t * LF_D + fb * LF_BK, 0, &full[s]);
+            if (BF) {  // the BF16 block of W_g: 128 rows x 64 bytes
+              mbar_expect_tx(&full[s], LF_TILE / 2);
+              tma_load_2d(st + 2 * LF_TILE, &map_wbf, t * LF_D + fb * LF_BK, 0, &full[s]);
+            } else {
+              mbar_expect_tx(&full[s], 2 * LF_TILE);
+              tma_load_2d(st + 2 * LF_TILE, &map_whi, t * LF_D + fb * LF_BK, 0, &full[s]);
+              tma_load_2d(st + 3 * LF_TILE, &map_wlo, t * LF_D + fb * LF_BK, 0, &full[s]);
+            }
           }
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {  // MMA issuer
-      constexpr uint32_t idesc = t3_idesc(128, LF_D);
+      constexpr uint32_t idesc = BF ? tc_idesc(128, LF_D) : t3_idesc(128, LF_D);
       int64_t g_ks = 0, lt = 0;
       bool ok = true;
       for (int64_t b = blockIdx.x; b < a.Bc && ok && !s_abort; b += gridDim.x) {
@@ -227,12 +262,18 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
             uint8_t* st = smem + s * LF_STAGE;
             const uint32_t ah = smem_u32(st), al = smem_u32(st + LF_TILE);
             const uint32_t bh = smem_u32(st + 2 * LF_TILE), bl = smem_u32(st + 3 * LF_TILE);
+            if constexpr (BF) {  // two K = 16 products per 32-feature step
 #pragma unroll
-            for (int kk = 0; kk < LF_BK / 8; ++kk) {
-              const uint32_t o = kk * 32;
-              umma_tf32(d, sw128_desc(ah + o), sw128_desc(bh + o), idesc, (ks | kk) ? 1u : 0u);
-              umma_tf32(d, sw128_desc(ah + o), sw128_desc(bl + o), idesc, 1u);
-              umma_tf32(d, sw128_desc(al + o), sw128_desc(bh + o), idesc, 1u);
+              for (int kk = 0; kk < LF_BK / 16; ++kk)
+                umma_bf16(d, sw64_desc(ah + kk * 32), sw64_desc(bh + kk * 32), idesc, (ks | kk) ? 1u : 0u);
+            } else {
+#pragma unroll
+              for (int kk = 0; kk < LF_BK / 8; ++kk) {
+                const uint32_t o = kk * 32;
+                umma_tf32(d, sw128_desc(ah + o), sw128_desc(bh + o), idesc, (ks | kk) ? 1u : 0u);
+                umma_tf32(d, sw128_desc(ah + o), sw128_desc(bl + o), idesc, 1u);
+                umma_tf32(d, sw128_desc(al + o), sw128_desc(bh + o), idesc, 1u);
+              }
             }
             umma_commit(&empty[s]);
           }
@@ -402,16 +443,7 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
                   if (writer) {
                     m.x *= nu;
                     m.y *= nu;
-                    const int orow = (c - c0) * N + i;
-                    float2 hi, lo;
-                    hi.x = tf32_split_hi(m.x);
-                    hi.y = tf32_split_hi(m.y);
-                    lo.x = tf32_split_hi(__fsub_rn(m.x, hi.x));
-                    lo.y = tf32_split_hi(__fsub_rn(m.y, hi.y));
-                    const uint32_t o = (uint32_t)orow * 128u + ((((uint32_t)fp >> 1) ^ (uint32_t)(orow & 7)) << 4) +
-                                       ((uint32_t)(fp & 1) << 3);
-                    *reinterpret_cast<float2*>(a_hi + o) = hi;
-                    *reinterpret_cast<float2*>(a_lo + o) = lo;
+                    store_a<BF>(a_hi, a_lo, (c - c0) * N + i, fp, m);
                   }
                 }
               }
@@ -422,7 +454,6 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
           int e = c0 >= 1 ? (c0 - 1) / 3 : -1, x = c0 >= 1 ? (c0 - 1) - 3 * e : 2;  // electron, axis of c0
           int ke_c = -1;                                  // the sender slot whose w' and z_j[0] are cached
           float2 w1e = make_float2(0.f, 0.f), z0e = make_float2(0.f, 0.f);
-          const uint32_t lchunk = (uint32_t)(fp >> 1), lsub = (uint32_t)(fp & 1) << 3;
           // channels in groups of LF_UG: the loads and multiply-add chains of a group overlap
           for (int cg = c0; cg < c1; cg += LF_UG, zrow += LF_UG * N * LF_BK) {
             float2 zc[LF_UG][NB], mm[LF_UG];
@@ -500,17 +531,8 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
               }
               m.x *= nu;
               m.y *= nu;
-              if (writer && e != i) {  // (the receiver's own channels were formed above)
-                // TF32 high and low parts, each rounded to 11 significant bits
-                float2 hi, lo;
-                hi.x = tf32_split_hi(m.x);
-                hi.y = tf32_split_hi(m.y);
-                lo.x = tf32_split_hi(__fsub_rn(m.x, hi.x));
-                lo.y = tf32_split_hi(__fsub_rn(m.y, hi.y));
-                const uint32_t o = (uint32_t)row * 128u + ((lchunk ^ (uint32_t)(row & 7)) << 4) + lsub;
-                *reinterpret_cast<float2*>(a_hi + o) = hi;
-                *reinterpret_cast<float2*>(a_lo + o) = lo;
-              }
+              if (writer && e != i)  // (the receiver's own channels were formed above)
+                store_a<BF>(a_hi, a_lo, row, fp, m);
               row += N;
               if (++x == 3) {
                 x = 0;
@@ -634,6 +656,19 @@ __global__ void add_nucleus_part_kernel(const float* __restrict__ un, int N, int
   for (int k = 0; k < 5; ++k) dst[(int64_t)ch[k] * LF_D] += src[(int64_t)k * LF_D];
 }
 
+// The BF16 copy of W_g [D][3 D] as dims {3 D, D}, box {32, 128}: 64-byte rows, 64-byte swizzle.
+bool map_w_bf(CUtensorMap* m, const void* W, int D) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)(3 * D), (cuuint64_t)D};
+  const cuuint64_t strides[1] = {(cuuint64_t)(3 * D) * 2};
+  const cuuint32_t box[2] = {LF_BK, 128};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(W), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool map_w(CUtensorMap* m, const float* W, int D) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
@@ -660,16 +695,29 @@ bool map_z(CUtensorMap* m, const float* Z, int64_t Bc, int N, int C, int D, int 
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+using KernT = void (*)(LayerFusedArgs, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, unsigned int*);
+
+template <bool BF>
+KernT pick_kernel(int nb, bool z_const) {
+  if (z_const)
+    return nb <= 2 ? layer_fused_kernel<2, true, BF> : nb <= 4 ? layer_fused_kernel<4, true, BF>
+           : nb <= 5 ? layer_fused_kernel<5, true, BF> : nb <= 7 ? layer_fused_kernel<7, true, BF>
+                     : layer_fused_kernel<8, true, BF>;
+  return nb <= 2 ? layer_fused_kernel<2, false, BF> : nb <= 4 ? layer_fused_kernel<4, false, BF>
+         : nb <= 5 ? layer_fused_kernel<5, false, BF> : nb <= 7 ? layer_fused_kernel<7, false, BF>
+                   : layer_fused_kernel<8, false, BF>;
+}
+
 }  // namespace
 
 bool layer_fused_supported(const dq_handle_s& h) {
-  return h.precision == DQ_FP32 && h.D == LF_D && h.N >= 1 && h.N <= LF_MAX_N && h.n_up <= LF_MAX_BLK &&
+  return (h.precision == DQ_FP32 || h.precision == DQ_BF16_MIXED) && h.D == LF_D && h.N >= 1 && h.N <= LF_MAX_N && h.n_up <= LF_MAX_BLK &&
          h.n_dn <= LF_MAX_BLK && h.M >= 1 && h.M <= LF_MAX_M;
 }
 
 cudaError_t launch_layer_fused(const dq_handle_s& h, const FwdDims& d, const float* params, int l, bool z_const,
                                float* Z, const float* z0, const float* ew, const float* geo, float* mn,
-                               const float* wg_hi, const float* wg_lo, cudaStream_t s) {
+                               const float* wg_hi, const float* wg_lo, const void* wg_bf, cudaStream_t s) {
   if (d.Bc <= 0) return cudaSuccess;
   if (!layer_fused_supported(h) || d.C != 3 * d.N + 2) return cudaErrorInvalidValue;
   const auto& y = h.off.layer[l];
@@ -708,21 +756,14 @@ cudaError_t launch_layer_fused(const dq_handle_s& h, const FwdDims& d, const flo
   a.G = std::min(128 / d.N, d.C);
   a.n_tiles = (d.C + a.G - 1) / a.G;
   a.z_const = z_const ? 1 : 0;
-  CUtensorMap mhi, mlo, mz;
+  CUtensorMap mhi, mlo, mz, mbf;
   if (!map_w(&mhi, wg_hi, LF_D) || !map_w(&mlo, wg_lo, LF_D)) return cudaErrorInvalidValue;
+  // BF16 operands when the BF16 copy of W_g is given (otherwise mbf is a copy of the FP32 map, unread)
+  if (wg_bf ? !map_w_bf(&mbf, wg_bf, LF_D) : !map_w(&mbf, wg_hi, LF_D)) return cudaErrorInvalidValue;
   // with constant node channels the z slabs are never loaded; their maps are built on W (any valid map)
   if (!(z_const ? map_w(&mz, wg_hi, LF_D) : map_z(&mz, Z, d.Bc, d.N, d.C, LF_D, a.G))) return cudaErrorInvalidValue;
   const int nb = std::max(h.n_up, h.n_dn);
-  using KernT = void (*)(LayerFusedArgs, CUtensorMap, CUtensorMap, CUtensorMap, unsigned int*);
-  KernT kern;
-  if (z_const)
-    kern = nb <= 2 ? layer_fused_kernel<2, true> : nb <= 4 ? layer_fused_kernel<4, true>
-           : nb <= 5 ? layer_fused_kernel<5, true> : nb <= 7 ? layer_fused_kernel<7, true>
-                     : layer_fused_kernel<8, true>;
-  else
-    kern = nb <= 2 ? layer_fused_kernel<2, false> : nb <= 4 ? layer_fused_kernel<4, false>
-           : nb <= 5 ? layer_fused_kernel<5, false> : nb <= 7 ? layer_fused_kernel<7, false>
-                     : layer_fused_kernel<8, false>;
+  const KernT kern = wg_bf ? pick_kernel<true>(nb, z_const) : pick_kernel<false>(nb, z_const);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LF_SMEM);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
@@ -731,7 +772,7 @@ cudaError_t launch_layer_fused(const dq_handle_s& h, const FwdDims& d, const flo
   const int64_t grid = d.Bc < sms ? d.Bc : sms;
   a.n_prod = (h.n_up + 1) / 2 + (h.n_dn + 1) / 2;  // receiver pairs of the two spin blocks
   if (a.n_prod > LF_PROD_WARPS) return cudaErrorInvalidValue;
-  kern<<<(unsigned)grid, LF_THREADS, LF_SMEM, s>>>(a, mhi, mlo, mz, h.d_status);
+  kern<<<(unsigned)grid, LF_THREADS, LF_SMEM, s>>>(a, mhi, mlo, mz, mbf, h.d_status);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   add_nucleus_part_kernel<<<(unsigned)(d.Bc * d.N), LF_D, 0, s>>>(un, d.N, d.C, Z);

@@ -60,6 +60,17 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;                   // 128-byte swizzle
   return d;
 }
+// The same for a K-major tile in the 64-byte swizzle layout: rows of 64 bytes, 8-row groups
+// 512 bytes apart, the 16-byte chunk c of row r stored at chunk c ^ ((r >> 1) & 3).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                   // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;          // stride byte offset: 8 rows x 64 B
+  d |= (uint64_t)1 << 46;                   // descriptor version
+  d |= (uint64_t)4 << 61;                   // 64-byte swizzle
+  return d;
+}
 // Instruction descriptor: kind::f16, A and B BF16 (K-major), D FP32, M x N.
 constexpr uint32_t tc_idesc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);

@@ -33,6 +33,10 @@ still meet bounds ten times looser, or, where the FP32-compiled oracle is given,
 more than twice that plain FP32 evaluation's own error on the walker when that is
 larger (a walker at the FP32 floor can miss ten times the tolerance in plain FP32
 arithmetic too); at most 5 % of the walkers (at least one) may use the exception.
+
+The BF16 mode's per-walker log|psi| bound (bf16_logabs_bound) takes the same
+first-order bound with eps = 2^-9, one BF16 rounding of every orbital entry, where
+that exceeds its relative bound of 1e-2.
 """
 from __future__ import annotations
 
@@ -143,6 +147,19 @@ def fp32_floor(orc, theta, r):
     o32 = oracle.Oracle(orc.system, orc.cfg, real="fp32")
     oracle.Oracle.set_threads(os.cpu_count() or 1)
     return o32.local_energy(np.asarray(theta, np.float32), np.asarray(r, np.float32).reshape(-1, orc.N, 3))
+
+
+# One BF16 rounding (8 significant bits, round to nearest): the relative accuracy of orbital
+# entries formed from BF16 GEMM operands, in the first-order log|Psi_D| bound eps * sigma_b.
+EPS_BF16 = 2.0 ** -9
+
+
+def bf16_logabs_bound(orc, theta, r, la_ref, rtol=1e-2):
+    """Per-walker log|psi| bound of the BF16 mode: the larger of rtol max(1, |log|psi||) and
+    2^-9 sigma_b, the first-order error bound of log|Psi_D| under one BF16 rounding of every
+    orbital entry (sigma_b as in the near-nodal class)."""
+    sigma, _, _ = sensitivity_for(orc, theta, r)
+    return np.maximum(rtol * np.maximum(1, np.abs(la_ref)), EPS_BF16 * sigma)
 
 
 def check_fp32_oracle(label, la, sg, el, orc, theta, r, ref=None, **kw):

@@ -1,12 +1,14 @@
 """BF16 mode: the embedding-layer GEMMs (graph-convolution update W_g and node
-map W_h) run on the tensor cores with BF16 inputs and FP32 accumulation;
+map W_h) run on the tensor cores with BF16 inputs and FP32 accumulation (in
+the fused layer kernel, W_g's electron-nucleus block stays on 3 x TF32);
 everything else as in FP32 mode (FP32 LU with a refined double-float inverse,
 double-float determinant derivatives, FP64 walker sums).
 
 The result is compared with the FP32 GPU path and with the FP64 oracle.
 BF16 keeps 8 significant bits, so per-walker local energies move by about
 2^-9 relative to the kinetic terms they are formed from: the per-walker bound
-is |dE| <= max(1e-2 Ha, 2e-2 S_b), log|psi| within 1e-2 relative.  What the
+is |dE| <= max(1e-2 Ha, 2e-2 S_b), log|psi| within 1e-2 relative or, where larger, the
+first-order bound for one BF16 rounding of the orbital entries (2^-9 sigma_b).  What the
 precision mode is for is the batch mean: the change of the mean local energy
 and of its variance against the FP32 path are reported, and the mean must agree
 within the statistical error of the per-walker differences (4 sigma); on a
@@ -22,7 +24,7 @@ import pytest
 import torch
 
 import oracle
-from fp32_contract import check_fp32_oracle
+from fp32_contract import bf16_logabs_bound, check_fp32_oracle
 from paper_2307_14123_gb300 import fixtures as fx
 
 pytestmark = pytest.mark.gpu
@@ -77,7 +79,7 @@ def test_bf16_mode_against_fp32_and_oracle(name, B, n_oracle):
             print(f"{name}: {n_oracle} walkers, {lab} mean E_loc - oracle {np.mean(el) - np.mean(ref['e_loc']):+.3e} Ha, "
                   f"variance {np.var(el):.4e} vs oracle {np.var(ref['e_loc']):.4e} Ha^2")
         assert np.all(e <= np.maximum(1e-2, 2e-2 * S))
-        assert np.all(np.abs(la16[idx] - ref["logabs"]) <= 1e-2 * np.maximum(1, np.abs(ref["logabs"])))
+        assert np.all(np.abs(la16[idx] - ref["logabs"]) <= bf16_logabs_bound(o, th64, r64, ref["logabs"]))
         check_fp32_oracle(f"{name} FP32", la32[idx], sg32[idx], el32[idx], o, th64, r64, ref=ref,
                           max_exception_frac=0.13)
 

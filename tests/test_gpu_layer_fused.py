@@ -59,6 +59,8 @@ def test_support_and_mode_switch():
     with pytest.raises(DQError):
         h32.set_layer_kernel(1)
     hb, *_ = _setup(fx.workload("n2_bf16"), 1, precision="bf16")
+    assert hb.layer_kernel_fused()  # BF16 operands in the same kernel
+    hb.set_layer_kernel(2)
     assert not hb.layer_kernel_fused()
 
 
@@ -112,3 +114,45 @@ def test_fused_small_molecules(k):
     assert h.layer_kernel_fused()
     o = oracle.Oracle(w.system, w.cfg)
     check_fp32_oracle(f"{w.name} fused", *_np(h.local_energy(th_t, r_t)), o, theta, r, max_exception_frac=0.13)
+
+
+def test_bf16_fused_and_separate_against_oracle():
+    """BF16 mode, N2: the fused kernel (electron-electron messages rounded to BF16 as the MMA
+    operand, the electron-nucleus part on 3 x TF32) and the separate path (all messages in BF16)
+    against the oracle within the BF16 per-walker bounds: |dE| <= max(1e-2 Ha, 2e-2 S_b) outside
+    the FP32 contract's exception class, and log|psi| within the larger of 1e-2 relative and the
+    first-order bound for one BF16 rounding of the orbital entries (2^-9 sigma_b).  The two paths
+    agree with each other within the same bounds, and the fused BF16 path is deterministic."""
+    from fp32_contract import bf16_logabs_bound
+    wl = fx.workload("n2_fp32")
+    h, theta, r, th_t, r_t = _setup(wl, 48, precision="bf16")
+    o = oracle.Oracle(wl.system, wl.cfg)
+    ref = o.local_energy(theta, r, with_grad=True)
+    S = 0.5 * (np.abs(ref["lap"]) + np.sum(ref["grad"] ** 2, axis=1))
+    e_tol = np.maximum(1e-2, 2e-2 * S)
+    la_tol = bf16_logabs_bound(o, theta, r, ref["logabs"])
+    nodal = near_nodal(o, theta, r, ref["logabs"])
+    out = {}
+    for mode in (1, 2):
+        h.set_layer_kernel(mode)
+        assert h.layer_kernel_fused() == (mode == 1)
+        out[mode] = _np(h.local_energy(th_t, r_t))
+        assert h.device_status() & 0x4 == 0
+    for mode in (1, 2):
+        la, sg, el = out[mode]
+        e, dla = np.abs(el - ref["e_loc"]), np.abs(la - ref["logabs"])
+        print(f"BF16 layer kernel {mode}: |dE|/tol max {np.max(e / e_tol):.2e} (outside the FP32 exception "
+              f"class, {nodal.sum()} of {nodal.size} in it: {np.max((e / e_tol)[~nodal]):.2e}), median |dE|/S "
+              f"{np.median(e / S):.2e}; |d log|psi|| / tol max {np.max(dla / la_tol):.2e}, rel. median "
+              f"{np.median(dla / np.abs(ref['logabs'])):.2e}")
+    for mode in (1, 2):
+        la, sg, el = out[mode]
+        assert np.all(np.abs(el - ref["e_loc"])[~nodal] <= e_tol[~nodal])
+        assert np.all(np.abs(la - ref["logabs"]) <= la_tol)
+    assert np.all(np.abs(out[1][2] - out[2][2])[~nodal] <= e_tol[~nodal])
+    assert np.all(np.abs(out[1][0] - out[2][0]) <= la_tol)
+    h.set_layer_kernel(1)
+    a = h.local_energy(th_t, r_t)
+    b = h.local_energy(th_t, r_t)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
