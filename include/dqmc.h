@@ -489,14 +489,32 @@ dq_status vmc_loss_weights_multi(dq_multi m, const void* const* e_loc, const int
 dq_status dq_set_msg_tile(dq_handle h, int32_t msg_ib);
 dq_status dq_msg_tile(dq_handle h, int32_t* msg_ib);
 
+/* Jet message kernel of the separate layer path (Eq. 17 with the product rule;
+ * no counterpart in the paper): mode 1 the general kernel (a warp task holds
+ * msg_ib receivers x 4 channels, the senders' node channels streamed through
+ * shared memory, the filter tables of all pairs resident); mode 2 the
+ * sender-tiled kernel (one spin block of senders at a time: a warp task holds
+ * their node channels for up to 11 channels in registers and runs over every
+ * receiver; FP32 and BF16 modes, width a multiple of 32, at most 48
+ * electrons, 24 per spin); mode 0 (the default) is mode 2 above 16 electrons
+ * where supported and mode 1 elsewhere.  Layers whose node channels are the
+ * spin-embedding constants always take the general kernel.  Mode 2 on a DQ_FP64
+ * handle: DQ_ERR_UNSUPPORTED; other modes: DQ_ERR_ARG.  Both kernels compute
+ * the same messages within FP32 rounding (different summation orders).
+ * dq_msg_kernel reports the kernel the handle's jet layers take on the
+ * separate path (1 or 2). */
+dq_status dq_set_msg_kernel(dq_handle h, int32_t mode);
+dq_status dq_msg_kernel(dq_handle h, int32_t* mode);
+
 /* Kernels of the jet layers (Eqs. 17-18) of local_energy and mala_step (no
  * counterpart in the paper): mode 1 runs each layer's messages, update map W_g
  * and residual tanh update as one kernel whose messages are the tensor-core
  * A operand and never reach memory; mode 2 runs them as the message kernel,
  * the W_g GEMM and the update kernel, with the messages in the workspace;
  * mode 0 (the default) is mode 1 where the handle supports it and mode 2
- * elsewhere.  Mode 1 needs DQ_FP32, width 128, at most 16 electrons (8 per
- * spin) and 8 nuclei: DQ_ERR_UNSUPPORTED otherwise.  Both modes compute the
+ * elsewhere.  Mode 1 needs DQ_FP32 or DQ_BF16_MIXED (whose fused kernel takes
+ * the electron-electron messages and W_g as BF16 operands), width 128, at
+ * most 16 electrons (8 per spin) and 8 nuclei: DQ_ERR_UNSUPPORTED otherwise.  Both modes compute the
  * same quantities within the FP32 mode's rounding (the sums run in different
  * orders).  The workspace size depends on the mode (mode 2 adds the message
  * buffer): query dq_workspace_size after setting it.  dq_layer_kernel reports

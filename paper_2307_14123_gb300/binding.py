@@ -37,7 +37,7 @@ EXPORTS = ["dq_create", "dq_destroy", "dq_param_count", "dq_max_chunk", "dq_set_
            "dq_test_gemm_tf32x3", "mcmc_step_dev", "mala_step", "dq_create_multi", "dq_destroy_multi",
            "dq_multi_handle", "dq_multi_set_rounds", "dq_multi_rounds", "dq_multi_workspace_size",
            "ansatz_eval_multi", "local_energy_multi", "mcmc_step_multi", "grad_logpsi_multi",
-           "vmc_loss_weights_multi", "dq_autotune_multi", "dq_multi_tuning", "dq_set_msg_tile", "dq_msg_tile", "dq_autotune", "natural_gradient", "param_update", "dq_pp_workspace_size",
+           "vmc_loss_weights_multi", "dq_autotune_multi", "dq_multi_tuning", "dq_set_msg_tile", "dq_msg_tile", "dq_set_msg_kernel", "dq_msg_kernel", "dq_autotune", "natural_gradient", "param_update", "dq_pp_workspace_size",
            "pseudopotential_energy", "dq_fma_rate_probe", "dq_set_layer_kernel", "dq_layer_kernel",
            "dq_set_det_warps", "dq_tile_set", "dq_multi_tile_set", "mcmc_step_eloc"]
 
@@ -119,6 +119,8 @@ def load_library(path=None):
         lib.dq_autotune_multi.argtypes = [P, P, P, P, P, sz, P, P]
         lib.dq_multi_tuning.argtypes = [P, P, P]
         lib.dq_set_msg_tile.argtypes = [P, i32]
+        lib.dq_set_msg_kernel.argtypes = [P, i32]
+        lib.dq_msg_kernel.argtypes = [P, ctypes.POINTER(i32)]
         lib.dq_msg_tile.argtypes = [P, P]
         lib.dq_autotune.argtypes = [P, P, P, i64, P, sz, P, P]
         lib.natural_gradient.argtypes = [P, P, P, i64, f64, i32, f64, P, P, P, sz, P]
@@ -200,6 +202,16 @@ class Ansatz:
     def set_msg_tile(self, msg_ib):
         """Receivers per warp task of the jet message kernel (8 or 4; 0: default)."""
         _check(self.lib.dq_set_msg_tile(self.h, int(msg_ib)))
+
+    def set_msg_kernel(self, mode):
+        """Jet message kernel of the separate layer path: 1 general, 2 sender-tiled, 0 by size."""
+        _check(self.lib.dq_set_msg_kernel(self.h, int(mode)))
+
+    def msg_kernel(self):
+        """The jet message kernel the separate layer path takes (1 general, 2 sender-tiled)."""
+        v = ctypes.c_int32()
+        _check(self.lib.dq_msg_kernel(self.h, ctypes.byref(v)))
+        return v.value
 
     def autotune(self, params, r):
         """Times local_energy on these walkers for the candidate layer kernels (fused or separate),

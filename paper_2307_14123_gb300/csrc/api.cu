@@ -2002,6 +2002,21 @@ dq_status dq_msg_tile(dq_handle h, int32_t* msg_ib) {
   return DQ_OK;
 }
 
+dq_status dq_set_msg_kernel(dq_handle h, int32_t mode) {
+  if (!h || mode < 0 || mode > 2) return DQ_ERR_ARG;
+  if (mode == 2 && h->precision == DQ_FP64) return DQ_ERR_UNSUPPORTED;
+  h->msg_kernel = mode;
+  return DQ_OK;
+}
+
+dq_status dq_msg_kernel(dq_handle h, int32_t* mode) {
+  if (!h || !mode) return DQ_ERR_ARG;
+  const FwdDims d{1, h->N, h->n_up, h->n_dn, h->M, h->D, h->K, h->Q, 3 * h->N + 2};
+  const bool tiled = h->msg_kernel == 2 || (h->msg_kernel == 0 && h->N > 16);
+  *mode = tiled && messages_large_supported(*h, d) ? 2 : 1;
+  return DQ_OK;
+}
+
 dq_status dq_set_layer_kernel(dq_handle h, int32_t mode) {
   if (!h || mode < 0 || mode > 2) return DQ_ERR_ARG;
   if (mode == 1 && !(use_tf32x3(*h) && layer_fused_supported(*h))) return DQ_ERR_UNSUPPORTED;

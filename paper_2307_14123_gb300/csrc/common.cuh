@@ -159,6 +159,7 @@ struct dq_handle_s {
   dq::Edges edges{};
   int64_t max_chunk = 4096;
   int msg_ib = 0;  // receivers per warp task of the jet message kernel (FP32 modes: 8 or 4; 0: 8)
+  int msg_kernel = 0;  // jet message kernel of the separate path: 1 general, 2 sender-tiled, 0 by size
   int layer_kernel = 0;  // jet layers: 0 fused kernel where supported, 1 the same, 2 separate kernels
   int det_warps = 4;     // warps (matrices) per CTA of the grouped determinant kernels: 4 or 2
   // device tables
@@ -356,6 +357,14 @@ cudaError_t launch_update_group(const MolFwd<T>* m, int n, bool from_spin, cudaS
 // Bc N 11 D floats.  FP32 and BF16 modes, D = 128, N <= 16 with at most 8 electrons per spin and
 // 8 nuclei.
 bool layer_fused_supported(const dq_handle_s& h);
+// Jet messages of molecules past the fused layer kernel (messages_large.cu): FP32 modes, node
+// channels from the node map (not the spin-embedding constants), 3 N + 2 channels, D a multiple
+// of 32, N <= 48 with at most 24 electrons per spin.  Writes all three message slots of msg
+// ([Bc][N][C][3D], FP32, or BF16 when bf16_out).
+bool messages_large_supported(const dq_handle_s& h, const FwdDims& d);
+cudaError_t launch_messages_large(const dq_handle_s& h, const FwdDims& d, const float* params, int l,
+                                  const float* Z, const float* ew, const float* geo, void* msg, bool bf16_out,
+                                  cudaStream_t s);
 cudaError_t launch_layer_fused(const dq_handle_s& h, const FwdDims& d, const float* params, int l, bool z_const,
                                float* Z, const float* z0, const float* ew, const float* geo, float* mn,
                                const float* wg_hi, const float* wg_lo, const void* wg_bf, cudaStream_t s);

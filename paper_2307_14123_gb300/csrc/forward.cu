@@ -2565,6 +2565,20 @@ cudaError_t launch_messages_group_t(const MolFwd<T>* m, int n, int l, bool z_con
     const FwdDims& d = m[k].d;
     if (d.Bc <= 0) continue;
     if (d.D % kMsgLanes) return cudaErrorInvalidConfiguration;
+    if constexpr (sizeof(T) == 4) {
+      // node channels from the node map: the sender-tiled kernel of messages_large.cu for the
+      // molecules past the fused kernel's size (or when the handle asks for it)
+      const bool tiled = h.msg_kernel == 2 || (h.msg_kernel == 0 && d.N > 16);
+      if (tiled && !(z_const && !h.el_init) && messages_large_supported(h, d)) {
+        cudaError_t e = launch_messages_large(h, d, reinterpret_cast<const float*>(m[k].params), l,
+                                              reinterpret_cast<const float*>(m[k].b.Z),
+                                              reinterpret_cast<const float*>(m[k].b.ew),
+                                              reinterpret_cast<const float*>(m[k].b.geo), out_of(m[k]),
+                                              sizeof(TO) == 2, s);
+        if (e != cudaSuccess) return e;
+        continue;
+      }
+    }
     bool stage_w1 = true;
     int L = kMsgLanes;
     MsgSmem lay = msg_smem_layout<T>(d.N, IB, CB, stage_w1, L);

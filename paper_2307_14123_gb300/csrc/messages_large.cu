@@ -1,0 +1,348 @@
+// Jet messages of Eq. 17 for molecules beyond the fused layer kernel (FP32 modes, node
+// channels from the node map): for every receiver i, channel c and feature,
+//   m_i^t[c] = nu_t ( sum_{j in block t} w_ij z_j[c] + product-rule terms ),
+// the product-rule terms being those listed with the general message kernel in forward.cu:
+//  (a) a sender's coordinate channel c = 1 + 3e + x:  -w'_ie u_ie,x z_e[0];
+//  (b) the receiver's own coordinate channel:         sum_j w'_ij u_ij,x z_j[0];
+//  (c) the Laplacian channel: sum_j (2 w''_ij + 4 w'_ij / d_ij) z_j[0] + 2 w'_ij u_ij.(dz_j/dr_i - dz_j/dr_j);
+//  and the electron-nucleus messages, non-zero on the value, Laplacian and own-coordinate
+//  channels only.
+//
+// One CTA per (walker, 32 features), a lane per feature, 16 warps.  The senders are taken one
+// spin block at a time: pass p holds the senders of block p, which give a receiver of block p its
+// same-spin message and every other receiver its opposite-spin one.  Per pass, w_ij and w'_ij
+// of the block's senders and all receivers are copied into shared memory as [j][i][32]
+// (16-byte asynchronous copies; rows past the block and the diagonal are zero).  A warp task
+// owns CB consecutive channels: it loads z_j[c] of the block's NBS sender slots for them into
+// registers (each value of z is read by exactly one task, coalesced over the features) and runs
+// over all receivers, NBS x CB multiply-adds per receiver against NBS conflict-free
+// shared-memory loads of w, then adds the product-rule terms and stores the CB messages.
+//
+// The general kernel (forward.cu) stages z in flight four senders at a time through 4-byte
+// copies per lane and keeps the w tables of all N^2 pairs, which at 28 electrons leaves it
+// bound by the copy latency with 16 features per CTA; here z lives in registers and only one
+// spin block's tables are resident.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace dq {
+namespace {
+
+constexpr int kMLLanes = 32;   // features per CTA
+constexpr int kMLMaxN = 48;    // electrons
+
+struct MLArgs {
+  const float* Z;      // [Bc][N][C][D] node map z_j
+  const float* ew;     // [Bc][E][3][D] filter jets w, dw/dd, d2w/dd2
+  const float* geo;    // [Bc][E][4] distance and unit vector of every edge
+  const float* Y;      // [M][D] nucleus embeddings of the layer
+  const int* pair_of;  // [N][N] edge of (i, j), -1 on the diagonal
+  void* msg;           // [Bc][N][C][3D] messages [same spin | opposite spin | nuclei]
+  int N, n_up, M, C, D, E, n_ee;
+  int stage_w1;        // w' tables in shared memory (else read from global memory)
+};
+
+// Shared-memory layout in floats (the pair table in ints at the same scale).
+struct MLSmem {
+  int ps, us, id, z0c, zsf, spb, spc, w0, w1, total_bytes;
+};
+__host__ __device__ inline MLSmem ml_layout(int N, int NBS, bool stage_w1) {
+  MLSmem m{};
+  int o = 0;
+  m.ps = o; o += N * N;
+  m.us = o; o += N * N * 3;
+  m.id = o; o += N * N;
+  m.z0c = o; o += N * kMLLanes;
+  m.zsf = o; o += 3 * N * kMLLanes;
+  m.spb = o; o += 3 * N * kMLLanes;
+  m.spc = o; o += N * kMLLanes;
+  o = (o + 3) / 4 * 4;  // 16-byte alignment of the copied tables
+  m.w0 = o; o += NBS * N * kMLLanes;
+  m.w1 = o; o += stage_w1 ? NBS * N * kMLLanes : 0;
+  m.total_bytes = o * 4;
+  return m;
+}
+
+__device__ __forceinline__ void store_out(float* p, float v) { *p = v; }
+__device__ __forceinline__ void store_out(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src, bool valid) {
+  // a zero-sized source fills the 16 bytes with zeros
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+
+// NBS: sender slots per spin block (at least the larger block); CB: channels per warp task;
+// NW: warps per CTA (the register tile NBS x CB sets how many fit on an SM); SW1: the w' tables
+// in shared memory (else read from global memory where used).
+template <int NBS, int CB, int NW, bool SW1, class TO>
+__global__ void __launch_bounds__(NW * 32, 1) messages_large_kernel(const __grid_constant__ MLArgs a) {
+  extern __shared__ __align__(16) float ml_smem[];
+  const int N = a.N, C = a.C, D = a.D, M = a.M, n_up = a.n_up, n_ee = a.n_ee;
+  const MLSmem lay = ml_layout(N, NBS, SW1);
+  int* Ps = reinterpret_cast<int*>(ml_smem + lay.ps);  // [i][j] edge
+  float* Us = ml_smem + lay.us;                        // [i][j][3] u_ij (zero diagonal)
+  float* Id = ml_smem + lay.id;                        // [i][j] 1 / d_ij
+  float* Z0c = ml_smem + lay.z0c;                      // [j][32] z_j[0]
+  float* Zsf = ml_smem + lay.zsf;                      // [j][x][32] dz_j / dr_j,x
+  float* SPb = ml_smem + lay.spb;                      // [i][x][32] (b) of the pass
+  float* SPc = ml_smem + lay.spc;                      // [i][32] (c) of the pass
+  float* W0 = ml_smem + lay.w0;                        // [jj][i][32] w of the pass's senders
+  float* W1 = ml_smem + lay.w1;                        // [jj][i][32] w'
+  constexpr bool stage_w1 = SW1;
+
+  const int64_t b = blockIdx.x;
+  const int f0 = blockIdx.y * kMLLanes;
+  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
+  const float* EWb = a.ew + b * (int64_t)a.E * 3 * D + f0 + lane;
+  const float* Zb = a.Z + b * (int64_t)N * C * D + f0 + lane;
+  const float* Yd = a.Y + f0 + lane;
+  const float* Gb = a.geo + b * (int64_t)a.E * 4;
+  TO* mb = static_cast<TO*>(a.msg) + b * (int64_t)N * C * 3 * D + f0 + lane;
+  const int NN = N * N;
+
+  // this CTA's slices of the node channels and filters into L2
+  for (int r = tid; r < N * C; r += blockDim.x)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.Z + (b * N * C + r) * (int64_t)D + f0));
+  for (int r = tid; r < a.E * 3; r += blockDim.x)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a.ew + (b * a.E * 3 + r) * (int64_t)D + f0));
+
+  // ---- per-walker tables ----
+  for (int k = tid; k < NN; k += blockDim.x) {
+    const int i = k / N, j = k - (k / N) * N;
+    const int p = a.pair_of[k];
+    Ps[k] = p;
+    float u0 = 0.f, u1 = 0.f, u2 = 0.f, id = 0.f;
+    if (i != j) {
+      const float sg = i < j ? 1.f : -1.f;
+      const float4 g = *reinterpret_cast<const float4*>(Gb + p * 4);
+      u0 = sg * g.y;
+      u1 = sg * g.z;
+      u2 = sg * g.w;
+      id = 1.f / g.x;
+    }
+    Us[k * 3] = u0;
+    Us[k * 3 + 1] = u1;
+    Us[k * 3 + 2] = u2;
+    Id[k] = id;
+  }
+  for (int j = warp; j < N; j += NW) {
+    const float* zj = Zb + (int64_t)j * C * D;
+    Z0c[j * 32 + lane] = zj[0];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) Zsf[(j * 3 + x) * 32 + lane] = zj[(int64_t)(1 + 3 * j + x) * D];
+  }
+  // electron-nucleus slot of receiver i (a warp item): (1/M) sum_I of w_iI Y_I (value channel),
+  // w'_iI u_iI,x Y_I (own coordinates), (w''_iI + 2 w'_iI / d_iI) Y_I (Laplacian), zero on the
+  // other channels; the loads of eight nuclei are issued before any is used
+  const float nuM = 1.f / (float)M;
+  for (int i = warp; i < N; i += NW) {
+    float sv = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, sl = 0.f;
+    for (int I0 = 0; I0 < M; I0 += 8) {
+      float w0v[8], w1v[8], w2v[8], yv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const bool ok = I0 + u < M;
+        const int en = n_ee + i * M + (ok ? I0 + u : 0);
+        const float* w = EWb + (int64_t)en * 3 * D;
+        w0v[u] = ok ? w[0] : 0.f;
+        w1v[u] = ok ? w[D] : 0.f;
+        w2v[u] = ok ? w[2 * D] : 0.f;
+        yv[u] = ok ? Yd[(int64_t)(I0 + u) * D] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (I0 + u >= M) break;
+        const float* g = Gb + (n_ee + i * M + I0 + u) * 4;
+        sv = fmaf(w0v[u], yv[u], sv);
+        sx = fmaf(w1v[u] * g[1], yv[u], sx);
+        sy = fmaf(w1v[u] * g[2], yv[u], sy);
+        sz = fmaf(w1v[u] * g[3], yv[u], sz);
+        sl = fmaf(w2v[u] + 2.f * w1v[u] / g[0], yv[u], sl);
+      }
+    }
+    TO* o = mb + (int64_t)i * C * 3 * D + 2 * D;
+    for (int c = 0; c < C; ++c) {
+      const float v = c == 0 ? sv : c == C - 1 ? sl : c == 1 + 3 * i ? sx : c == 2 + 3 * i ? sy : c == 3 + 3 * i ? sz : 0.f;
+      store_out(o + (int64_t)c * 3 * D, v * nuM);
+    }
+  }
+  __syncthreads();  // pair table, unit vectors, z_j[0]
+
+  const uint32_t w0s = (uint32_t)__cvta_generic_to_shared(W0), w1s = (uint32_t)__cvta_generic_to_shared(W1);
+  const float* ew_row = a.ew + b * (int64_t)a.E * 3 * D + f0;  // lane-independent row base
+  for (int pass = 0; pass < 2; ++pass) {
+    const int j0 = pass == 0 ? 0 : n_up, jn = pass == 0 ? n_up : N - n_up;
+    // ---- the pass's filter tables: row (jj, i) holds w_{i, j0 + jj} for the 32 features, as
+    // eight 16-byte copies (lane / 8 picks one of four rows, lane % 8 the chunk) ----
+    {
+      const int rows = NBS * N;
+      const int sub = lane >> 3, ch = (lane & 7) * 4;
+      for (int r0 = warp * 4; r0 < rows; r0 += NW * 4) {
+        const int r = r0 + sub;
+        if (r < rows) {
+          const int jj = r / N, i = r - (r / N) * N;
+          const int j = j0 + jj;
+          const int p = (jj < jn && i != j) ? Ps[i * N + j] : -1;
+          const float* src = ew_row + (int64_t)(p >= 0 ? p : 0) * 3 * D + ch;
+          cp16(w0s + (uint32_t)((r * 32 + ch) * 4), src, p >= 0);
+          if (stage_w1) cp16(w1s + (uint32_t)((r * 32 + ch) * 4), src + D, p >= 0);
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    auto w1_at = [&](int i, int jj) -> float {  // w'_{i, j0 + jj} of this lane's feature
+      if (stage_w1) return W1[(jj * N + i) * 32 + lane];
+      const int j = j0 + jj;
+      return i == j ? 0.f : EWb[((int64_t)Ps[i * N + j] * 3 + 1) * D];
+    };
+    // ---- per-receiver terms of the pass: (c) (global loads; items 0 .. N - 1, spread over the
+    // warps first), then (b) for the three axes ----
+    for (int it = warp; it < 4 * N; it += NW) {
+      const int i = it < N ? it : (it - N) / 3, kind = it < N ? 3 : (it - N) - 3 * ((it - N) / 3);
+      if (kind < 3) {
+        float sacc = 0.f;
+        for (int jj = 0; jj < jn; ++jj) {
+          const int j = j0 + jj;
+          sacc = fmaf(w1_at(i, jj) * Us[(i * N + j) * 3 + kind], Z0c[j * 32 + lane], sacc);
+        }
+        SPb[(i * 3 + kind) * 32 + lane] = sacc;
+      } else {
+        const float* zc = Zb + (int64_t)(1 + 3 * i) * D;  // dz_j / dr_i of sender j at zc + j C D
+        float sv = 0.f;
+        constexpr int kCJ = 8;  // senders whose global loads are in flight together
+        for (int jb = 0; jb < jn; jb += kCJ) {
+          float w2v[kCJ], zx[kCJ], zy[kCJ], zz[kCJ];
+#pragma unroll
+          for (int u = 0; u < kCJ; ++u) {
+            const int j = j0 + jb + u;
+            const bool ok = jb + u < jn && j != i;
+            w2v[u] = ok ? EWb[((int64_t)Ps[i * N + j] * 3 + 2) * D] : 0.f;
+            const float* zj = zc + (int64_t)(ok ? j : i) * C * D;
+            zx[u] = ok ? zj[0] : 0.f;
+            zy[u] = ok ? zj[D] : 0.f;
+            zz[u] = ok ? zj[2 * D] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < kCJ; ++u) {
+            const int jj = jb + u, j = j0 + jj;
+            if (jj >= jn || j == i) continue;
+            const float v1 = w1_at(i, jj);
+            const float* uu = Us + (i * N + j) * 3;
+            const float cr = uu[0] * (zx[u] - Zsf[(j * 3) * 32 + lane]) + uu[1] * (zy[u] - Zsf[(j * 3 + 1) * 32 + lane]) +
+                             uu[2] * (zz[u] - Zsf[(j * 3 + 2) * 32 + lane]);
+            sv += (2.f * w2v[u] + 4.f * v1 * Id[i * N + j]) * Z0c[j * 32 + lane] + 2.f * v1 * cr;
+          }
+        }
+        SPc[i * 32 + lane] = sv;
+      }
+    }
+    __syncthreads();
+    // ---- the contraction: warp tasks of CB channels over all receivers ----
+    const int ntasks = (C + CB - 1) / CB;
+    const float nu_same = 1.f / (float)(jn - 1 > 1 ? jn - 1 : 1), nu_opp = 1.f / (float)(jn > 1 ? jn : 1);
+    for (int task = warp; task < ntasks; task += NW) {
+      const int c0 = task * CB;
+      float zr[CB][NBS];
+#pragma unroll
+      for (int q = 0; q < CB; ++q)
+#pragma unroll
+        for (int jj = 0; jj < NBS; ++jj)
+          zr[q][jj] = (jj < jn && c0 + q < C) ? Zb[((int64_t)(j0 + jj) * C + c0 + q) * D] : 0.f;
+      // (a) per channel q: the offset of its electron's row in the w' table (-1 when the channel is
+      // not a coordinate of a sender of this pass) and that sender's z_e[0]
+      int ea[CB];
+      float za[CB];
+#pragma unroll
+      for (int q = 0; q < CB; ++q) {
+        const int c = c0 + q, e = (c - 1) / 3;
+        const bool snd = c >= 1 && c < C - 1 && e >= j0 && e < j0 + jn;
+        ea[q] = snd ? (e - j0) * N * 32 : -1;
+        za[q] = snd ? Z0c[e * 32 + lane] : 0.f;
+      }
+      const int qlap = C - 1 - c0, nq = C - c0;  // the Laplacian channel's slot, channels of the task
+      for (int i = 0; i < N; ++i) {
+        float acc[CB];
+#pragma unroll
+        for (int q = 0; q < CB; ++q) acc[q] = 0.f;
+        const float* wr = W0 + i * 32 + lane;
+#pragma unroll
+        for (int jj = 0; jj < NBS; ++jj) {
+          const float w = wr[jj * N * 32];
+#pragma unroll
+          for (int q = 0; q < CB; ++q) acc[q] = fmaf(w, zr[q][jj], acc[q]);
+        }
+        // channel c = c0 + q is a coordinate of electron e, axis x, when c - 1 = 3 e + x: u_{i,e,x}
+        // sits at Us[3 N i + c - 1], and (b)'s own-coordinate sum of receiver i at SPb[c - 1]
+        const int ur = i * 3 * N + c0 - 1;  // (indexed only for coordinate channels, c0 + q >= 1)
+        const int own = c0 - 1 - 3 * i;  // channel q is receiver i's own coordinate iff own + q in [0, 3)
+#pragma unroll
+        for (int q = 0; q < CB; ++q) {
+          if ((unsigned)(own + q) < 3u) {
+            acc[q] += SPb[(c0 + q - 1) * 32 + lane];  // (b)
+          } else if (ea[q] >= 0) {                    // (a)
+            const float w1v = SW1 ? W1[ea[q] + i * 32 + lane] : w1_at(i, ea[q] / (N * 32));
+            acc[q] -= w1v * Us[ur + q] * za[q];
+          }
+          if (q == qlap) acc[q] += SPc[i * 32 + lane];  // (c)
+        }
+        const bool same = (i < n_up) == (pass == 0);
+        const float nu = same ? nu_same : nu_opp;
+        TO* o = mb + ((int64_t)i * C + c0) * 3 * D + (same ? 0 : D);
+#pragma unroll
+        for (int q = 0; q < CB; ++q)
+          if (q < nq) store_out(o + (int64_t)q * 3 * D, acc[q] * nu);
+      }
+    }
+    __syncthreads();  // the tables are rewritten by the next pass
+  }
+}
+
+template <int NBS, int CB, int NW, class TO>
+cudaError_t launch_ml(const MLArgs& a, int64_t Bc, cudaStream_t s) {
+  const MLSmem lay = ml_layout(a.N, NBS, a.stage_w1 != 0);
+  auto kern = a.stage_w1 ? messages_large_kernel<NBS, CB, NW, true, TO> : messages_large_kernel<NBS, CB, NW, false, TO>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total_bytes);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3((unsigned)Bc, (unsigned)(a.D / kMLLanes)), NW * 32, lay.total_bytes, s>>>(a);
+  return cudaGetLastError();
+}
+
+int ml_nbs(int nb) { return nb <= 8 ? 8 : nb <= 14 ? 14 : nb <= 16 ? 16 : 24; }
+
+}  // namespace
+
+bool messages_large_supported(const dq_handle_s& h, const FwdDims& d) {
+  if (h.precision == DQ_FP64 || d.C != 3 * d.N + 2 || d.D % kMLLanes || d.N > kMLMaxN || d.N < 2) return false;
+  const int nb = std::max(d.n_up, d.N - d.n_up);
+  if (nb > 24) return false;
+  const MLSmem l = ml_layout(d.N, ml_nbs(nb), false);
+  return l.total_bytes <= 220 * 1024;
+}
+
+cudaError_t launch_messages_large(const dq_handle_s& h, const FwdDims& d, const float* params, int l,
+                                  const float* Z, const float* ew, const float* geo, void* msg, bool bf16_out,
+                                  cudaStream_t s) {
+  if (d.Bc <= 0) return cudaSuccess;
+  if (!messages_large_supported(h, d)) return cudaErrorInvalidValue;
+  const int nb = std::max(d.n_up, d.N - d.n_up);
+  const int nbs = ml_nbs(nb);
+  MLArgs a{Z, ew, geo, params + h.off.layer[l].Y, h.d_pair_of, msg, d.N, d.n_up, d.M, d.C, d.D,
+           h.edges.n_all, h.edges.n_ee, 1};
+  if (ml_layout(d.N, nbs, true).total_bytes > 220 * 1024) a.stage_w1 = 0;
+  // register tiles of sender slots x channels (64 to 84 values) in 16 warps of 128 registers
+  if (nbs == 8)
+    return bf16_out ? launch_ml<8, 8, 16, __nv_bfloat16>(a, d.Bc, s) : launch_ml<8, 8, 16, float>(a, d.Bc, s);
+  if (nbs == 14)
+    return bf16_out ? launch_ml<14, 6, 16, __nv_bfloat16>(a, d.Bc, s) : launch_ml<14, 6, 16, float>(a, d.Bc, s);
+  if (nbs == 16)
+    return bf16_out ? launch_ml<16, 5, 16, __nv_bfloat16>(a, d.Bc, s) : launch_ml<16, 5, 16, float>(a, d.Bc, s);
+  return bf16_out ? launch_ml<24, 3, 16, __nv_bfloat16>(a, d.Bc, s) : launch_ml<24, 3, 16, float>(a, d.Bc, s);
+}
+
+}  // namespace dq
