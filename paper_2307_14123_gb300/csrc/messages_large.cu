@@ -13,10 +13,12 @@
 // same-spin message and every other receiver its opposite-spin one.  Per pass, w_ij and w'_ij
 // of the block's senders and all receivers are copied into shared memory as [j][i][32]
 // (16-byte asynchronous copies; rows past the block and the diagonal are zero).  A warp task
-// owns CB consecutive channels: it loads z_j[c] of the block's NBS sender slots for them into
-// registers (each value of z is read by exactly one task, coalesced over the features) and runs
-// over all receivers, NBS x CB multiply-adds per receiver against NBS conflict-free
-// shared-memory loads of w, then adds the product-rule terms and stores the CB messages.
+// owns the 3 EPT coordinate channels of EPT consecutive electrons (one more task the value and
+// Laplacian channels): it loads z_j[c] of the block's NBS sender slots for them into registers
+// (each value of z is read by exactly one task, coalesced over the features) and runs over all
+// receivers, NBS x 3 EPT multiply-adds per receiver against NBS conflict-free shared-memory
+// loads of w; with the channels aligned to electrons, the product-rule terms of a register slot
+// have a fixed electron and axis and are added without branches before the store.
 //
 // The general kernel (forward.cu) stages z in flight four senders at a time through 4-byte
 // copies per lane and keeps the w tables of all N^2 pairs, which at 28 electrons leaves it
@@ -75,11 +77,12 @@ __device__ __forceinline__ void cp16(uint32_t dst, const void* src, bool valid) 
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0) : "memory");
 }
 
-// NBS: sender slots per spin block (at least the larger block); CB: channels per warp task;
-// NW: warps per CTA (the register tile NBS x CB sets how many fit on an SM); SW1: the w' tables
-// in shared memory (else read from global memory where used).
-template <int NBS, int CB, int NW, bool SW1, class TO>
+// NBS: sender slots per spin block (at least the larger block); EPT: electrons per warp task (its
+// register tile is NBS x 3 EPT); NW: warps per CTA; SW1: the w' tables in shared memory (else read
+// from global memory where used).
+template <int NBS, int EPT, int NW, bool SW1, class TO>
 __global__ void __launch_bounds__(NW * 32, 1) messages_large_kernel(const __grid_constant__ MLArgs a) {
+  constexpr int CB = 3 * EPT;
   extern __shared__ __align__(16) float ml_smem[];
   const int N = a.N, C = a.C, D = a.D, M = a.M, n_up = a.n_up, n_ee = a.n_ee;
   const MLSmem lay = ml_layout(N, NBS, SW1);
@@ -243,70 +246,97 @@ __global__ void __launch_bounds__(NW * 32, 1) messages_large_kernel(const __grid
       }
     }
     __syncthreads();
-    // ---- the contraction: warp tasks of CB channels over all receivers ----
-    const int ntasks = (C + CB - 1) / CB;
+    // ---- the contraction: a warp task holds the 3 EPT coordinate channels of EPT consecutive
+    // electrons (channel c = 1 + 3 e + x: electron e, axis x known per register slot), and one
+    // more task the value and Laplacian channels; each runs over all receivers ----
     const float nu_same = 1.f / (float)(jn - 1 > 1 ? jn - 1 : 1), nu_opp = 1.f / (float)(jn > 1 ? jn : 1);
-    for (int task = warp; task < ntasks; task += NW) {
-      const int c0 = task * CB;
-      float zr[CB][NBS];
-#pragma unroll
-      for (int q = 0; q < CB; ++q)
-#pragma unroll
-        for (int jj = 0; jj < NBS; ++jj)
-          zr[q][jj] = (jj < jn && c0 + q < C) ? Zb[((int64_t)(j0 + jj) * C + c0 + q) * D] : 0.f;
-      // (a) per channel q: the offset of its electron's row in the w' table (-1 when the channel is
-      // not a coordinate of a sender of this pass) and that sender's z_e[0]
-      int ea[CB];
-      float za[CB];
-#pragma unroll
-      for (int q = 0; q < CB; ++q) {
-        const int c = c0 + q, e = (c - 1) / 3;
-        const bool snd = c >= 1 && c < C - 1 && e >= j0 && e < j0 + jn;
-        ea[q] = snd ? (e - j0) * N * 32 : -1;
-        za[q] = snd ? Z0c[e * 32 + lane] : 0.f;
-      }
-      const int qlap = C - 1 - c0, nq = C - c0;  // the Laplacian channel's slot, channels of the task
-      for (int i = 0; i < N; ++i) {
-        float acc[CB];
-#pragma unroll
-        for (int q = 0; q < CB; ++q) acc[q] = 0.f;
-        const float* wr = W0 + i * 32 + lane;
-#pragma unroll
-        for (int jj = 0; jj < NBS; ++jj) {
-          const float w = wr[jj * N * 32];
-#pragma unroll
-          for (int q = 0; q < CB; ++q) acc[q] = fmaf(w, zr[q][jj], acc[q]);
-        }
-        // channel c = c0 + q is a coordinate of electron e, axis x, when c - 1 = 3 e + x: u_{i,e,x}
-        // sits at Us[3 N i + c - 1], and (b)'s own-coordinate sum of receiver i at SPb[c - 1]
-        const int ur = i * 3 * N + c0 - 1;  // (indexed only for coordinate channels, c0 + q >= 1)
-        const int own = c0 - 1 - 3 * i;  // channel q is receiver i's own coordinate iff own + q in [0, 3)
-#pragma unroll
-        for (int q = 0; q < CB; ++q) {
-          if ((unsigned)(own + q) < 3u) {
-            acc[q] += SPb[(c0 + q - 1) * 32 + lane];  // (b)
-          } else if (ea[q] >= 0) {                    // (a)
-            const float w1v = SW1 ? W1[ea[q] + i * 32 + lane] : w1_at(i, ea[q] / (N * 32));
-            acc[q] -= w1v * Us[ur + q] * za[q];
-          }
-          if (q == qlap) acc[q] += SPc[i * 32 + lane];  // (c)
-        }
-        const bool same = (i < n_up) == (pass == 0);
-        const float nu = same ? nu_same : nu_opp;
-        TO* o = mb + ((int64_t)i * C + c0) * 3 * D + (same ? 0 : D);
+    const int ncoord = (N + EPT - 1) / EPT;
+    for (int task = warp; task <= ncoord; task += NW) {
+      if (task < ncoord) {
+        const int e0 = task * EPT, c0 = 1 + 3 * e0;
+        float zr[CB][NBS];
 #pragma unroll
         for (int q = 0; q < CB; ++q)
-          if (q < nq) store_out(o + (int64_t)q * 3 * D, acc[q] * nu);
+#pragma unroll
+          for (int jj = 0; jj < NBS; ++jj)
+            zr[q][jj] = (jj < jn && e0 + q / 3 < N) ? Zb[((int64_t)(j0 + jj) * C + c0 + q) * D] : 0.f;
+        // (a) per electron slot s: the sender slot of e0 + s and its z_e[0] (zero when e0 + s is not
+        // a sender of this pass, which zeroes the term)
+        int ja[EPT];
+        float za[EPT];
+#pragma unroll
+        for (int s = 0; s < EPT; ++s) {
+          const int e = e0 + s;
+          const bool snd = e < N && e >= j0 && e < j0 + jn;
+          ja[s] = snd ? e - j0 : 0;
+          za[s] = snd ? Z0c[e * 32 + lane] : 0.f;
+        }
+        for (int i = 0; i < N; ++i) {
+          float acc[CB];
+#pragma unroll
+          for (int q = 0; q < CB; ++q) acc[q] = 0.f;
+          const float* wr = W0 + i * 32 + lane;
+#pragma unroll
+          for (int jj = 0; jj < NBS; ++jj) {
+            const float w = wr[jj * N * 32];
+#pragma unroll
+            for (int q = 0; q < CB; ++q) acc[q] = fmaf(w, zr[q][jj], acc[q]);
+          }
+#pragma unroll
+          for (int s = 0; s < EPT; ++s) {
+            const int e = e0 + s;
+            if (e >= N) break;
+            // (a): -w'_ie z_e[0] u_ie,x (w'_ii = 0: nothing on the receiver's own channels)
+            const float pa = (SW1 ? W1[(ja[s] * N + i) * 32 + lane] : w1_at(i, ja[s])) * za[s];
+            const float* ue = Us + (i * N + e) * 3;
+#pragma unroll
+            for (int x = 0; x < 3; ++x) acc[3 * s + x] = fmaf(-pa, ue[x], acc[3 * s + x]);
+            if (e == i) {  // (b): the receiver's own coordinates
+#pragma unroll
+              for (int x = 0; x < 3; ++x) acc[3 * s + x] += SPb[(i * 3 + x) * 32 + lane];
+            }
+          }
+          const bool same = (i < n_up) == (pass == 0);
+          const float nu = same ? nu_same : nu_opp;
+          TO* o = mb + ((int64_t)i * C + c0) * 3 * D + (same ? 0 : D);
+#pragma unroll
+          for (int q = 0; q < CB; ++q)
+            if (e0 + q / 3 < N) store_out(o + (int64_t)q * 3 * D, acc[q] * nu);
+        }
+      } else {
+        // the value channel (z_j[0] from shared memory) and the Laplacian channel, with (c)
+        float zv[NBS], zl[NBS];
+#pragma unroll
+        for (int jj = 0; jj < NBS; ++jj) {
+          zv[jj] = jj < jn ? Z0c[(j0 + jj) * 32 + lane] : 0.f;
+          zl[jj] = jj < jn ? Zb[((int64_t)(j0 + jj) * C + C - 1) * D] : 0.f;
+        }
+        for (int i = 0; i < N; ++i) {
+          float av = 0.f, al = 0.f;
+          const float* wr = W0 + i * 32 + lane;
+#pragma unroll
+          for (int jj = 0; jj < NBS; ++jj) {
+            const float w = wr[jj * N * 32];
+            av = fmaf(w, zv[jj], av);
+            al = fmaf(w, zl[jj], al);
+          }
+          al += SPc[i * 32 + lane];
+          const bool same = (i < n_up) == (pass == 0);
+          const float nu = same ? nu_same : nu_opp;
+          TO* o = mb + (int64_t)i * C * 3 * D + (same ? 0 : D);
+          store_out(o, av * nu);
+          store_out(o + (int64_t)(C - 1) * 3 * D, al * nu);
+        }
       }
     }
     __syncthreads();  // the tables are rewritten by the next pass
   }
 }
 
-template <int NBS, int CB, int NW, class TO>
+template <int NBS, int EPT, int NW, class TO>
 cudaError_t launch_ml(const MLArgs& a, int64_t Bc, cudaStream_t s) {
   const MLSmem lay = ml_layout(a.N, NBS, a.stage_w1 != 0);
-  auto kern = a.stage_w1 ? messages_large_kernel<NBS, CB, NW, true, TO> : messages_large_kernel<NBS, CB, NW, false, TO>;
+  auto kern = a.stage_w1 ? messages_large_kernel<NBS, EPT, NW, true, TO> : messages_large_kernel<NBS, EPT, NW, false, TO>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lay.total_bytes);
   if (e != cudaSuccess) return e;
   kern<<<dim3((unsigned)Bc, (unsigned)(a.D / kMLLanes)), NW * 32, lay.total_bytes, s>>>(a);
@@ -335,14 +365,14 @@ cudaError_t launch_messages_large(const dq_handle_s& h, const FwdDims& d, const 
   MLArgs a{Z, ew, geo, params + h.off.layer[l].Y, h.d_pair_of, msg, d.N, d.n_up, d.M, d.C, d.D,
            h.edges.n_all, h.edges.n_ee, 1};
   if (ml_layout(d.N, nbs, true).total_bytes > 220 * 1024) a.stage_w1 = 0;
-  // register tiles of sender slots x channels (64 to 84 values) in 16 warps of 128 registers
+  // register tiles of sender slots x 3 EPT channels (72 to 84 values) in 16 warps of 128 registers
   if (nbs == 8)
-    return bf16_out ? launch_ml<8, 8, 16, __nv_bfloat16>(a, d.Bc, s) : launch_ml<8, 8, 16, float>(a, d.Bc, s);
+    return bf16_out ? launch_ml<8, 3, 16, __nv_bfloat16>(a, d.Bc, s) : launch_ml<8, 3, 16, float>(a, d.Bc, s);
   if (nbs == 14)
-    return bf16_out ? launch_ml<14, 6, 16, __nv_bfloat16>(a, d.Bc, s) : launch_ml<14, 6, 16, float>(a, d.Bc, s);
+    return bf16_out ? launch_ml<14, 2, 16, __nv_bfloat16>(a, d.Bc, s) : launch_ml<14, 2, 16, float>(a, d.Bc, s);
   if (nbs == 16)
-    return bf16_out ? launch_ml<16, 5, 16, __nv_bfloat16>(a, d.Bc, s) : launch_ml<16, 5, 16, float>(a, d.Bc, s);
-  return bf16_out ? launch_ml<24, 3, 16, __nv_bfloat16>(a, d.Bc, s) : launch_ml<24, 3, 16, float>(a, d.Bc, s);
+    return bf16_out ? launch_ml<16, 1, 16, __nv_bfloat16>(a, d.Bc, s) : launch_ml<16, 1, 16, float>(a, d.Bc, s);
+  return bf16_out ? launch_ml<24, 1, 16, __nv_bfloat16>(a, d.Bc, s) : launch_ml<24, 1, 16, float>(a, d.Bc, s);
 }
 
 }  // namespace dq
