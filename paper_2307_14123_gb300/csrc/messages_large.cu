@@ -10,15 +10,17 @@
 //
 // One CTA per (walker, 32 features), a lane per feature, 16 warps.  The senders are taken one
 // spin block at a time: pass p holds the senders of block p, which give a receiver of block p its
-// same-spin message and every other receiver its opposite-spin one.  Per pass, w_ij and w'_ij
-// of the block's senders and all receivers are copied into shared memory as [j][i][32]
+// same-spin message and every other receiver its opposite-spin one.  Per pass, w_ij, w'_ij and
+// w''_ij of the block's senders and all receivers are copied into shared memory as [j][i][32]
 // (16-byte asynchronous copies; rows past the block and the diagonal are zero).  A warp task
 // owns the 3 EPT coordinate channels of EPT consecutive electrons (one more task the value and
 // Laplacian channels): it loads z_j[c] of the block's NBS sender slots for them into registers
 // (each value of z is read by exactly one task, coalesced over the features) and runs over all
 // receivers, NBS x 3 EPT multiply-adds per receiver against NBS conflict-free shared-memory
 // loads of w; with the channels aligned to electrons, the product-rule terms of a register slot
-// have a fixed electron and axis and are added without branches before the store.
+// have a fixed electron and axis and are added without branches before the store.  The task
+// also forms the pass's sums (b) and (c) for its electrons as receivers, the cross term of (c)
+// from the dz_j / dr_e it holds; the Laplacian channel is completed after all tasks.
 //
 // The general kernel (forward.cu) stages z in flight four senders at a time through 4-byte
 // copies per lane and keeps the w tables of all N^2 pairs, which at 28 electrons leaves it
@@ -45,12 +47,12 @@ struct MLArgs {
   const int* pair_of;  // [N][N] edge of (i, j), -1 on the diagonal
   void* msg;           // [Bc][N][C][3D] messages [same spin | opposite spin | nuclei]
   int N, n_up, M, C, D, E, n_ee;
-  int stage_w1;        // w' tables in shared memory (else read from global memory)
+  int stage_w1;        // w' and w'' tables in shared memory (else read from global memory)
 };
 
 // Shared-memory layout in floats (the pair table in ints at the same scale).
 struct MLSmem {
-  int ps, us, id, z0c, zsf, spb, spc, w0, w1, total_bytes;
+  int ps, us, id, z0c, zsf, spb, spc, lap, w0, w1, w2, total_bytes;
 };
 __host__ __device__ inline MLSmem ml_layout(int N, int NBS, bool stage_w1) {
   MLSmem m{};
@@ -62,9 +64,11 @@ __host__ __device__ inline MLSmem ml_layout(int N, int NBS, bool stage_w1) {
   m.zsf = o; o += 3 * N * kMLLanes;
   m.spb = o; o += 3 * N * kMLLanes;
   m.spc = o; o += N * kMLLanes;
+  m.lap = o; o += N * kMLLanes;
   o = (o + 3) / 4 * 4;  // 16-byte alignment of the copied tables
   m.w0 = o; o += NBS * N * kMLLanes;
   m.w1 = o; o += stage_w1 ? NBS * N * kMLLanes : 0;
+  m.w2 = o; o += stage_w1 ? NBS * N * kMLLanes : 0;
   m.total_bytes = o * 4;
   return m;
 }
@@ -93,8 +97,10 @@ __global__ void __launch_bounds__(NW * 32, 1) messages_large_kernel(const __grid
   float* Zsf = ml_smem + lay.zsf;                      // [j][x][32] dz_j / dr_j,x
   float* SPb = ml_smem + lay.spb;                      // [i][x][32] (b) of the pass
   float* SPc = ml_smem + lay.spc;                      // [i][32] (c) of the pass
+  float* LAP = ml_smem + lay.lap;                      // [i][32] Laplacian-channel contraction
   float* W0 = ml_smem + lay.w0;                        // [jj][i][32] w of the pass's senders
   float* W1 = ml_smem + lay.w1;                        // [jj][i][32] w'
+  float* W2 = ml_smem + lay.w2;                        // [jj][i][32] w''
   constexpr bool stage_w1 = SW1;
 
   const int64_t b = blockIdx.x;
@@ -176,6 +182,7 @@ __global__ void __launch_bounds__(NW * 32, 1) messages_large_kernel(const __grid
   __syncthreads();  // pair table, unit vectors, z_j[0]
 
   const uint32_t w0s = (uint32_t)__cvta_generic_to_shared(W0), w1s = (uint32_t)__cvta_generic_to_shared(W1);
+  const uint32_t w2s = (uint32_t)__cvta_generic_to_shared(W2);
   const float* ew_row = a.ew + b * (int64_t)a.E * 3 * D + f0;  // lane-independent row base
   for (int pass = 0; pass < 2; ++pass) {
     const int j0 = pass == 0 ? 0 : n_up, jn = pass == 0 ? n_up : N - n_up;
@@ -192,7 +199,10 @@ __global__ void __launch_bounds__(NW * 32, 1) messages_large_kernel(const __grid
           const int p = (jj < jn && i != j) ? Ps[i * N + j] : -1;
           const float* src = ew_row + (int64_t)(p >= 0 ? p : 0) * 3 * D + ch;
           cp16(w0s + (uint32_t)((r * 32 + ch) * 4), src, p >= 0);
-          if (stage_w1) cp16(w1s + (uint32_t)((r * 32 + ch) * 4), src + D, p >= 0);
+          if (stage_w1) {
+            cp16(w1s + (uint32_t)((r * 32 + ch) * 4), src + D, p >= 0);
+            cp16(w2s + (uint32_t)((r * 32 + ch) * 4), src + 2 * D, p >= 0);
+          }
         }
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
@@ -204,48 +214,6 @@ __global__ void __launch_bounds__(NW * 32, 1) messages_large_kernel(const __grid
       const int j = j0 + jj;
       return i == j ? 0.f : EWb[((int64_t)Ps[i * N + j] * 3 + 1) * D];
     };
-    // ---- per-receiver terms of the pass: (c) (global loads; items 0 .. N - 1, spread over the
-    // warps first), then (b) for the three axes ----
-    for (int it = warp; it < 4 * N; it += NW) {
-      const int i = it < N ? it : (it - N) / 3, kind = it < N ? 3 : (it - N) - 3 * ((it - N) / 3);
-      if (kind < 3) {
-        float sacc = 0.f;
-        for (int jj = 0; jj < jn; ++jj) {
-          const int j = j0 + jj;
-          sacc = fmaf(w1_at(i, jj) * Us[(i * N + j) * 3 + kind], Z0c[j * 32 + lane], sacc);
-        }
-        SPb[(i * 3 + kind) * 32 + lane] = sacc;
-      } else {
-        const float* zc = Zb + (int64_t)(1 + 3 * i) * D;  // dz_j / dr_i of sender j at zc + j C D
-        float sv = 0.f;
-        constexpr int kCJ = 8;  // senders whose global loads are in flight together
-        for (int jb = 0; jb < jn; jb += kCJ) {
-          float w2v[kCJ], zx[kCJ], zy[kCJ], zz[kCJ];
-#pragma unroll
-          for (int u = 0; u < kCJ; ++u) {
-            const int j = j0 + jb + u;
-            const bool ok = jb + u < jn && j != i;
-            w2v[u] = ok ? EWb[((int64_t)Ps[i * N + j] * 3 + 2) * D] : 0.f;
-            const float* zj = zc + (int64_t)(ok ? j : i) * C * D;
-            zx[u] = ok ? zj[0] : 0.f;
-            zy[u] = ok ? zj[D] : 0.f;
-            zz[u] = ok ? zj[2 * D] : 0.f;
-          }
-#pragma unroll
-          for (int u = 0; u < kCJ; ++u) {
-            const int jj = jb + u, j = j0 + jj;
-            if (jj >= jn || j == i) continue;
-            const float v1 = w1_at(i, jj);
-            const float* uu = Us + (i * N + j) * 3;
-            const float cr = uu[0] * (zx[u] - Zsf[(j * 3) * 32 + lane]) + uu[1] * (zy[u] - Zsf[(j * 3 + 1) * 32 + lane]) +
-                             uu[2] * (zz[u] - Zsf[(j * 3 + 2) * 32 + lane]);
-            sv += (2.f * w2v[u] + 4.f * v1 * Id[i * N + j]) * Z0c[j * 32 + lane] + 2.f * v1 * cr;
-          }
-        }
-        SPc[i * 32 + lane] = sv;
-      }
-    }
-    __syncthreads();
     // ---- the contraction: a warp task holds the 3 EPT coordinate channels of EPT consecutive
     // electrons (channel c = 1 + 3 e + x: electron e, axis x known per register slot), and one
     // more task the value and Laplacian channels; each runs over all receivers ----
@@ -271,6 +239,45 @@ __global__ void __launch_bounds__(NW * 32, 1) messages_large_kernel(const __grid
           ja[s] = snd ? e - j0 : 0;
           za[s] = snd ? Z0c[e * 32 + lane] : 0.f;
         }
+        // the pass's sums over senders for the task's electrons as receivers: (b) into SPb (read
+        // back by this warp only) and (c) into SPc (read by the Laplacian epilogue); the cross term
+        // of (c) takes dz_j / dr_e,x from the register tile
+#pragma unroll
+        for (int s = 0; s < EPT; ++s) {
+          const int e = e0 + s;
+          if (e >= N) break;
+          float b0 = 0.f, b1 = 0.f, b2 = 0.f, sv = 0.f;
+          float w2v[SW1 ? 1 : NBS];  // w'' from global memory when the tables are not staged
+          if (!SW1) {
+#pragma unroll
+            for (int jj = 0; jj < NBS; ++jj) {
+              const int j = j0 + jj;
+              w2v[SW1 ? 0 : jj] = (jj < jn && j != e) ? EWb[((int64_t)Ps[e * N + j] * 3 + 2) * D] : 0.f;
+            }
+          }
+#pragma unroll
+          for (int jj = 0; jj < NBS; ++jj) {
+            if (jj >= jn) break;
+            const int j = j0 + jj;
+            const float v1 = w1_at(e, jj);
+            const float* uu = Us + (e * N + j) * 3;
+            const float z0 = Z0c[j * 32 + lane];
+            b0 = fmaf(v1 * uu[0], z0, b0);
+            b1 = fmaf(v1 * uu[1], z0, b1);
+            b2 = fmaf(v1 * uu[2], z0, b2);
+            if (j == e) continue;
+            const float* zs = Zsf + (j * 3) * 32 + lane;
+            const float cr = uu[0] * (zr[3 * s][jj] - zs[0]) + uu[1] * (zr[3 * s + 1][jj] - zs[32]) +
+                             uu[2] * (zr[3 * s + 2][jj] - zs[64]);
+            const float w2 = SW1 ? W2[(jj * N + e) * 32 + lane] : w2v[SW1 ? 0 : jj];
+            sv += (2.f * w2 + 4.f * v1 * Id[e * N + j]) * z0 + 2.f * v1 * cr;
+          }
+          SPb[(e * 3) * 32 + lane] = b0;
+          SPb[(e * 3 + 1) * 32 + lane] = b1;
+          SPb[(e * 3 + 2) * 32 + lane] = b2;
+          SPc[e * 32 + lane] = sv;
+        }
+        __syncwarp();
         for (int i = 0; i < N; ++i) {
           float acc[CB];
 #pragma unroll
@@ -320,14 +327,20 @@ __global__ void __launch_bounds__(NW * 32, 1) messages_large_kernel(const __grid
             av = fmaf(w, zv[jj], av);
             al = fmaf(w, zl[jj], al);
           }
-          al += SPc[i * 32 + lane];
           const bool same = (i < n_up) == (pass == 0);
           const float nu = same ? nu_same : nu_opp;
-          TO* o = mb + (int64_t)i * C * 3 * D + (same ? 0 : D);
-          store_out(o, av * nu);
-          store_out(o + (int64_t)(C - 1) * 3 * D, al * nu);
+          store_out(mb + (int64_t)i * C * 3 * D + (same ? 0 : D), av * nu);
+          LAP[i * 32 + lane] = al;  // completed with (c) after every task has written SPc
         }
       }
+    }
+    __syncthreads();
+    // the Laplacian channel: contraction + (c)
+    for (int i = warp; i < N; i += NW) {
+      const bool same = (i < n_up) == (pass == 0);
+      const float nu = same ? nu_same : nu_opp;
+      const float al = LAP[i * 32 + lane] + SPc[i * 32 + lane];
+      store_out(mb + ((int64_t)i * C + C - 1) * 3 * D + (same ? 0 : D), al * nu);
     }
     __syncthreads();  // the tables are rewritten by the next pass
   }
