@@ -641,8 +641,8 @@ def bf16_leg(h, theta, r, wl, flush, reps=5):
                             "mean_dE_bf16_minus_fp32": float(d.mean()),
                             "stderr": float(d.std() / max(1, d.numel()) ** 0.5),
                             "note": "random-initialised ansatz; both modes run the fused layer kernel (FP32: "
-                                    "3 x TF32 update-map products; BF16: BF16 operands, FP32 accumulation) "
-                                    "and BF16 takes the BF16 node-map GEMM"}
+                                    "3 x TF32 update-map products; BF16: BF16 operands of W_g's "
+                                    "electron-electron blocks, FP32 accumulation); node maps on 3 x TF32"}
     del h32, h16
     system = fx.molecule("LiH")
     cfg = fx.AnsatzCfg(64, 2, 1)
