@@ -295,6 +295,9 @@ MSG_DRAM_BYTES_PER_WALKER = (263.570432e6 + 432.803840e6) / 512
 # producer design; summary under profiles/); None once the kernel has changed since that capture.
 # Layer 0 (constant node channels) reads no z slabs and moves less.
 LAYER_FUSED_DRAM_BYTES_PER_WALKER = (238.052864e6 + 108.800256e6) / 512
+# the same for one launch of the sender-tiled message kernel (layer 1 of C4H4 in BF16 mode, 256
+# walkers; summary under profiles/); None once the kernel has changed since that capture.
+MSG_LARGE_DRAM_BYTES_PER_WALKER = (1.637387e9 + 0.949968e9) / 256
 
 
 def gemm_shapes(wl, chunk):
@@ -409,7 +412,11 @@ def roofline_for(kind, ms, n, wl, chunk, pk, how, alu, steps):
         peak = alu["fp32_tflops"] if wl.precision != "fp64" else alu["fp64_tflops"]
         ach = flops / t / 1e12
         byts = (chunk * N * C * D * el * (L - 1) / L) + chunk * E * 3 * D * el + chunk * N * C * 3 * D * (2 if bf16 else el)
-        traffic = MSG_DRAM_BYTES_PER_WALKER * chunk if (wl.name == "n2_fp32" and MSG_DRAM_BYTES_PER_WALKER) else None
+        traffic = None
+        if wl.name == "n2_fp32" and MSG_DRAM_BYTES_PER_WALKER:
+            traffic = MSG_DRAM_BYTES_PER_WALKER * chunk
+        elif wl.name == "c4h4_bf16" and MSG_LARGE_DRAM_BYTES_PER_WALKER:
+            traffic = MSG_LARGE_DRAM_BYTES_PER_WALKER * chunk
         return {**base, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": traffic, "peak_source": "FMA rate of the CUDA cores measured in this run",
                 "flops_per_launch": flops, "bytes_per_launch": byts,
