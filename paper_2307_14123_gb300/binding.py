@@ -224,7 +224,7 @@ class Ansatz:
         keep_lk = self.layer_kernel_fused()
         self.set_max_chunk(4096)  # the largest candidate
         n = self.workspace_size(B, OP_LOCAL_ENERGY)
-        if self.precision == "fp32":
+        if self.precision in ("fp32", "bf16"):  # both modes have the fused and the separate layer path
             _check(self.lib.dq_set_layer_kernel(self.h, 2))  # the separate kernels' message buffer
             n = max(n, self.workspace_size(B, OP_LOCAL_ENERGY))
             _check(self.lib.dq_set_layer_kernel(self.h, 1 if keep_lk else 2))
